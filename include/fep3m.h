@@ -1,0 +1,168 @@
+/*
+ * fep3m.h -- C ABI of the GB300 (sm_103a) finite-element P3M library.
+ *
+ * The method (Beams, Olson, Freund, "A Finite Element Based P3M Method for
+ * N-body Problems") computes, for N point charges Q_i at x_i in the periodic
+ * cube [0, L)^3, the potentials
+ *     Phi_i = sum_n sum_{j != i or n != 0} Q_j / |x_i - x_j + n L|       (Eq. potential)
+ * and the energy U = 1/2 sum_i Q_i Phi_i (Eq. potentialenergy), split as
+ * Phi = Phi^sr + Phi^sm (Eq. phisplit): a polynomial screen of order q = 1
+ * (Sec. 2.1, Eq. moment1d) turns the long-range part into a periodic order
+ * p = 3 finite-element Poisson problem (Sec. 2.2) solved here by multigrid,
+ * evaluated at the charges by Eq. evalsmooth (Sec. 2.3); the short-range
+ * part (Sec. 2.4, Eq. sc, self term Sec. 2.5) is a sum over the
+ * (2 n_sr + 1)^3 elements around each charge's element using FE basis-screen
+ * tables (Remark of Sec. 4).  Forces are -dU/dx of the discrete U, from a
+ * hand-written adjoint.
+ *
+ * Conventions shared by every entry point
+ *   - Units: Gaussian, Coulomb constant 1 (Phi = Q / R).
+ *   - Return value: FEP3M_OK (0) or a negative FEP3M_E* status; a failing
+ *     call leaves caller buffers unspecified but the context usable unless
+ *     it returns FEP3M_ECUDA.  fep3m_strerror() names the status.
+ *   - Pointers: "host or device" arguments may be either; the library asks
+ *     the CUDA runtime which one it is and copies host data through the
+ *     context's stream.  Device pointers must be on the context's device.
+ *   - Layouts: positions and gradients are N x 3 row-major (x, y, z of
+ *     charge i at 3i..3i+2), float64; per-charge arrays are length N, float64,
+ *     in the caller's original charge order.
+ *   - Ownership: the caller owns every buffer it passes; the library owns all
+ *     of its scratch (allocated in fep3m_create / grown in
+ *     fep3m_set_particles) and frees it in fep3m_destroy.
+ *   - Streams: all device work is issued on the stream given to
+ *     fep3m_create, in order; calls returning host values synchronise it.
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef FEP3M_H
+#define FEP3M_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FEP3M_OK = 0,
+  FEP3M_EINVAL = -1,       /* bad argument: sizes, q, n_sr, non-finite input  */
+  FEP3M_ENOTNEUTRAL = -2,  /* |sum Q| > 1e-12 sum |Q| without FEP3M_NEUTRALIZE */
+  FEP3M_ENOMEM = -3,       /* device allocation failed                        */
+  FEP3M_ECUDA = -4,        /* CUDA runtime error (context may be unusable)    */
+  FEP3M_ENOCONV = -5,      /* mesh solve hit its cycle cap; outputs written   */
+  FEP3M_ESTATE = -6,       /* call out of order (e.g. compute before set)     */
+  FEP3M_ETIMEOUT = -7      /* a bounded device wait gave up                   */
+};
+
+enum { FEP3M_FP64 = 0, FEP3M_MIXED = 1 };
+
+/* flags */
+#define FEP3M_NEUTRALIZE 1u    /* accept non-neutral input: uniform background */
+
+typedef struct fep3m_ctx fep3m_ctx;
+
+typedef struct {
+  double L;            /* periodic cube edge, > 0                              */
+  int n_el;            /* elements per axis; >= 2 n_sr + 1; h = L / n_el        */
+  int q;               /* screen order; this build supports q = 1 (p = 3)       */
+  int n_sr;            /* short-range block half-width in elements, 1..4 (3 in
+                          the paper's tests, Sec. 4: a 7 x 7 x 7 block)         */
+  int precision;       /* FEP3M_FP64 or FEP3M_MIXED (FP32 pairs and multigrid
+                          smoothing, FP64 refinement residual, projections and
+                          energy reduction)                                      */
+  double mg_rtol;      /* relative FE residual target; 0 -> 1e-13 (FP64) or
+                          1e-10 (MIXED)                                          */
+  int mg_max_cycles;   /* cap on preconditioned iterations (FP64) or refinement
+                          sweeps (MIXED); 0 -> default                           */
+  int table_pad;       /* Dirichlet box margin, elements, beyond the kept table;
+                          0 -> 4                                                 */
+  unsigned flags;      /* FEP3M_NEUTRALIZE                                       */
+} fep3m_config;
+
+typedef struct {
+  int64_t n_particles;
+  int mg_levels;
+  int mg_iterations;        /* last forward solve: iterations (FP64) or total
+                               inner iterations (MIXED)                          */
+  int refine_steps;         /* MIXED: FP64 refinement sweeps used                 */
+  double mg_rel_residual;   /* last forward solve, FP64 residual / |b|            */
+  int adj_iterations;       /* last adjoint solve                                 */
+  double adj_rel_residual;
+  int64_t singular_pairs;   /* ordered (target, source) pairs in the blocks       */
+  int64_t nonempty_elements;
+  int max_per_element;
+  double ms_bin, ms_assemble, ms_solve, ms_pair, ms_adjoint;  /* last call, if
+                               timing was enabled with fep3m_set_timing          */
+} fep3m_stats;
+
+/* Create a context: validates cfg, builds the FE basis-screen table (a
+ * Dirichlet order-3 FE solve around one vertex hat, Remark of Sec. 4), the
+ * multigrid hierarchy for the periodic mesh and the screen constants
+ * (Eq. moment1d).  cuda_stream is a cudaStream_t (NULL = legacy default).
+ * On success *out owns everything and must be released by fep3m_destroy.  */
+int fep3m_create(const fep3m_config* cfg, void* cuda_stream, fep3m_ctx** out);
+
+/* Charge positions (N x 3, host or device, any real values: they are wrapped
+ * into [0, L)) and charges (N, host or device).  Bins the charges into
+ * elements (stable counting sort) and stores the sorted SoA copy; grows the
+ * context's scratch when N exceeds earlier calls.  N >= 1.  Non-finite input
+ * is reported by the next fep3m_compute as FEP3M_EINVAL.                    */
+int fep3m_set_particles(fep3m_ctx* ctx, int64_t N, const double* pos, const double* Q);
+
+/* Phi_i (N, host or device; may be NULL) and U (host scalar; may be NULL) for
+ * the charges last set.  force (N x 3, host or device, or NULL) receives
+ * -dU/dx_i; computing it runs the adjoint (one more mesh solve).
+ * Synchronises the stream when U, force-on-host or phi-on-host is asked.   */
+int fep3m_compute(fep3m_ctx* ctx, double* phi, double* U, double* force);
+
+/* Vector-Jacobian product of the last fep3m_compute: for the scalar
+ *   Lf = gU * U + sum_i gphi_i Phi_i
+ * writes dLf/dx (N x 3) into dpos and dLf/dQ (N) into dQ (host or device;
+ * either may be NULL).  gphi may be NULL (zero).  The derivative is that of
+ * the discrete method (element and block membership held fixed); the mesh
+ * part uses the same multigrid on the adjoint right-hand side.             */
+int fep3m_vjp(fep3m_ctx* ctx, double gU, const double* gphi, double* dpos, double* dQ);
+
+/* Counters of the last calls (see fep3m_stats).                              */
+int fep3m_get_stats(const fep3m_ctx* ctx, fep3m_stats* out);
+
+/* Enable (1) / disable (0) per-stage CUDA-event timing in fep3m_stats.      */
+int fep3m_set_timing(fep3m_ctx* ctx, int enable);
+
+/* Inspection of intermediate results of the last set/compute, for testing
+ * each stage against a reference.  All outputs host or device, float64
+ * unless stated; NULL skips an output.
+ *   perm       int32[N]    charge index at each sorted slot (stable by index)
+ *   count      int32[n^3]  charges per element, element id ex + n ey + n^2 ez
+ *   cell       int32[N]    element id of each charge (original order)
+ *   delta      [N x 3]     offset of each charge from its element centre     */
+int fep3m_get_binning(const fep3m_ctx* ctx, int32_t* perm, int32_t* count,
+                      int32_t* cell, double* delta);
+
+/*   C      [n^3 x 8]  element-to-point screen list sum_{j in e} Q_j c_k(delta_j)
+ *                     with c_k the dimensionless (h^3-scaled) weights of
+ *                     Eq. oned, k = i + 2 j + 4 k' the corner
+ *   b      [(3n)^3]   FE load vector 4 pi int rho u_m (index ix + 3n iy + 9n^2 iz)
+ *   phi_mesh [(3n)^3] mesh potential nodal values (physical units, mean zero)
+ *   Phi^sm / Phi^sing / Phi^scr parts are not kept separately.             */
+int fep3m_get_mesh(const fep3m_ctx* ctx, double* C, double* b, double* phi_mesh);
+
+/* Solve the periodic FE system K phi = b - (sum b) w / sum w, int phi = 0,
+ * for a caller right-hand side b ((3n)^3, host or device) with the context's
+ * multigrid (precision as configured); writes phi (physical units).  Used
+ * to test the solver alone.                                                 */
+int fep3m_solve_mesh(fep3m_ctx* ctx, const double* b, double* phi);
+
+/* The kept FE basis-screen table (h = 1): nodal values on [-(n_sr+1), n_sr+1]^3
+ * in steps of 1/3, (6 n_sr + 7)^3 values, index ix + s iy + s^2 iz with
+ * s = 6 n_sr + 7.                                                            */
+int fep3m_get_table(const fep3m_ctx* ctx, double* table);
+
+const char* fep3m_strerror(int status);
+
+/* Release the context and all of its device memory.  NULL is a no-op.      */
+void fep3m_destroy(fep3m_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEP3M_H */

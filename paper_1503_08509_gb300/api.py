@@ -1,0 +1,165 @@
+"""Python front end of the FE-P3M library.
+
+Thin marshalling over the C ABI (include/fep3m.h): torch supplies device
+memory and the CUDA stream; every step of the method runs in the library's
+CUDA kernels.  Inputs may be CUDA tensors (device path, no copies) or numpy
+arrays / CPU tensors (host path: the library stages the copies itself).
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError("expected a torch.Tensor or numpy.ndarray, got %r" % type(x))
+
+
+def _f64(x, shape):
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            x = x.to(torch.float64).contiguous()
+    else:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+    if tuple(x.shape) != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (shape, tuple(x.shape)))
+    return x
+
+
+class FEP3M:
+    """One FE-P3M context: mesh, screen tables and multigrid for a periodic cube.
+
+    precision: 'fp64' or 'mixed' (FP32 pairs and multigrid, FP64 refinement).
+    """
+
+    def __init__(self, L, n_el, n_sr=3, precision="fp64", mg_rtol=0.0, mg_max_cycles=0, neutralize=False,
+                 table_pad=0, device=None, stream=None):
+        lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.L, self.n_el, self.n_sr = float(L), int(n_el), int(n_sr)
+        self.precision = precision
+        cfg = _lib.Config(L=self.L, n_el=self.n_el, q=1, n_sr=self.n_sr,
+                          precision=_lib.FEP3M_MIXED if precision == "mixed" else _lib.FEP3M_FP64,
+                          mg_rtol=mg_rtol, mg_max_cycles=mg_max_cycles, table_pad=table_pad,
+                          flags=_lib.FEP3M_NEUTRALIZE if neutralize else 0)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            h = ctypes.c_void_p()
+            _lib.check(lib.fep3m_create(ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream),
+                                        ctypes.byref(h)), "fep3m_create")
+        self._h = h
+        self.N = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().fep3m_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nodes(self):
+        return (3 * self.n_el) ** 3
+
+    def set_particles(self, pos, Q):
+        N = int(pos.shape[0])
+        pos = _f64(pos, (N, 3))
+        Q = _f64(Q, (N,))
+        self._keep = (pos, Q)   # the device path reads them on the stream
+        _lib.check(_lib.load().fep3m_set_particles(self._h, N, _ptr(pos), _ptr(Q)), "fep3m_set_particles")
+        self.N = N
+
+    def compute(self, phi=True, energy=True, forces=False, out=None, allow_noconv=False):
+        """Returns dict(phi, U, forces).  Outputs are CUDA tensors unless out= gives buffers."""
+        N = self.N
+        out = dict(out or {})
+        if phi and "phi" not in out:
+            out["phi"] = torch.empty(N, dtype=torch.float64, device=self.device)
+        if forces and "forces" not in out:
+            out["forces"] = torch.empty((N, 3), dtype=torch.float64, device=self.device)
+        U = ctypes.c_double(0.0)
+        st = _lib.load().fep3m_compute(self._h, _ptr(out.get("phi")), ctypes.byref(U) if energy else None,
+                                       _ptr(out.get("forces")))
+        _lib.check(st, "fep3m_compute", allow=(_lib.FEP3M_ENOCONV,) if allow_noconv else ())
+        if energy:
+            out["U"] = U.value
+        out["status"] = st
+        return out
+
+    def vjp(self, gU=1.0, gphi=None, dpos=None, dQ=None):
+        N = self.N
+        if gphi is not None:
+            gphi = _f64(gphi, (N,))
+        if dpos is None:
+            dpos = torch.empty((N, 3), dtype=torch.float64, device=self.device)
+        if dQ is None:
+            dQ = torch.empty(N, dtype=torch.float64, device=self.device)
+        _lib.check(_lib.load().fep3m_vjp(self._h, float(gU), _ptr(gphi), _ptr(dpos), _ptr(dQ)), "fep3m_vjp")
+        return dpos, dQ
+
+    def binning(self):
+        N, ne = self.N, self.n_el ** 3
+        d = dict(perm=np.empty(N, np.int32), count=np.empty(ne, np.int32), cell=np.empty(N, np.int32),
+                 delta=np.empty((N, 3), np.float64))
+        _lib.check(_lib.load().fep3m_get_binning(self._h, _ptr(d["perm"]), _ptr(d["count"]), _ptr(d["cell"]),
+                                                 _ptr(d["delta"])), "fep3m_get_binning")
+        return d
+
+    def mesh(self):
+        ne = self.n_el ** 3
+        d = dict(C=np.empty((ne, 8)), b=np.empty(self.nodes), phi_mesh=np.empty(self.nodes))
+        _lib.check(_lib.load().fep3m_get_mesh(self._h, _ptr(d["C"]), _ptr(d["b"]), _ptr(d["phi_mesh"])),
+                   "fep3m_get_mesh")
+        return d
+
+    def solve_mesh(self, b):
+        b = _f64(b, (self.nodes,))
+        phi = np.empty(self.nodes) if isinstance(b, np.ndarray) else torch.empty_like(b)
+        _lib.check(_lib.load().fep3m_solve_mesh(self._h, _ptr(b), _ptr(phi)), "fep3m_solve_mesh",
+                   allow=(_lib.FEP3M_ENOCONV,))
+        return phi
+
+    def table(self):
+        s = 6 * self.n_sr + 7
+        t = np.empty(s ** 3)
+        _lib.check(_lib.load().fep3m_get_table(self._h, _ptr(t)), "fep3m_get_table")
+        return t.reshape(s, s, s)      # [iz, iy, ix]
+
+    def stats(self):
+        s = _lib.Stats()
+        _lib.check(_lib.load().fep3m_get_stats(self._h, ctypes.byref(s)), "fep3m_get_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def set_timing(self, on=True):
+        _lib.check(_lib.load().fep3m_set_timing(self._h, 1 if on else 0), "fep3m_set_timing")
+
+
+class FEP3MEnergy(torch.autograd.Function):
+    """(U, Phi) = FEP3MEnergy.apply(pos, Q, engine); backward uses the library's adjoint."""
+
+    @staticmethod
+    def forward(ctx, pos, Q, engine):
+        engine.set_particles(pos.detach(), Q.detach())
+        out = engine.compute(phi=True, energy=True, forces=False)
+        ctx.engine = engine
+        ctx.mark_non_differentiable()
+        U = torch.tensor(out["U"], dtype=torch.float64, device=pos.device)
+        return U, out["phi"]
+
+    @staticmethod
+    def backward(ctx, gU, gphi):
+        gUv = 0.0 if gU is None else float(gU)
+        dpos, dQ = ctx.engine.vjp(gUv, None if gphi is None else gphi.contiguous())
+        return dpos, dQ, None

@@ -1,0 +1,449 @@
+// C ABI of the FE-P3M library: argument checking, memory ownership, host/device
+// staging and the order of the stages of Algorithm 1.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace fep3m;
+
+namespace {
+
+constexpr int PT = 256;
+
+int from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return FEP3M_OK;
+  if (e == cudaErrorMemoryAllocation) return FEP3M_ENOMEM;
+  return FEP3M_ECUDA;
+}
+
+#define CK(x)                          \
+  do {                                 \
+    cudaError_t e_ = (x);              \
+    if (e_ != cudaSuccess) {           \
+      (void)cudaGetLastError();        \
+      return from_cuda(e_);            \
+    }                                  \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+__global__ void k_scale(int64_t n, double* x, double a) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] *= a;
+}
+template <class A>
+__global__ void k_to_double(int64_t n, const A* in, double* out, double a) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i] * a;
+}
+__global__ void k_charge_sums(int64_t N, const double* Q, double* out /* [0] sum, [1] sum |Q| */) {
+  __shared__ double s1[PT], s2[PT];
+  double a = 0, b = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    a += Q[i];
+    b += fabs(Q[i]);
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = PT / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s1[0];
+    out[1] = s2[0];
+  }
+}
+
+inline int gsz(int64_t n) { return (int)((n + PT - 1) / PT); }
+
+void free_particles(fep3m_ctx* c) {
+  void* p[] = {c->pos_in, c->Q_in, c->cell, c->delta, c->perm, c->part, c->phi_s, c->E_s, c->w_s,
+               c->psi_s, c->gpsi_s, c->out_tmp, c->Q_s, c->gphi_dev};
+  for (void* q : p) dfree(q);
+  c->pos_in = c->Q_in = c->delta = c->phi_s = c->E_s = c->w_s = c->psi_s = c->gpsi_s = c->out_tmp = c->Q_s =
+      c->gphi_dev = nullptr;
+  c->cell = c->perm = nullptr;
+  c->part = nullptr;
+  c->cap = 0;
+}
+
+int grow_particles(fep3m_ctx* c, int64_t N) {
+  if (N <= c->cap) return FEP3M_OK;
+  free_particles(c);
+  const size_t es = c->precision == FEP3M_MIXED ? sizeof(float4) : sizeof(vec4<double>::type);
+  CK(dalloc(&c->pos_in, 3 * N));
+  CK(dalloc(&c->Q_in, N));
+  CK(dalloc(&c->cell, N));
+  CK(dalloc(&c->delta, 3 * N));
+  CK(dalloc(&c->perm, N));
+  CK(cudaMalloc(&c->part, N * es));
+  CK(dalloc(&c->phi_s, N));
+  CK(dalloc(&c->E_s, 3 * N));
+  CK(dalloc(&c->w_s, N));
+  CK(dalloc(&c->psi_s, N));
+  CK(dalloc(&c->gpsi_s, 3 * N));
+  CK(dalloc(&c->out_tmp, 4 * N));
+  CK(dalloc(&c->Q_s, N));
+  CK(dalloc(&c->gphi_dev, N));
+  c->cap = N;
+  return FEP3M_OK;
+}
+
+// copy n elements of device data to a caller pointer (host or device)
+int deliver(fep3m_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (!dst) return FEP3M_OK;
+  if (is_device_ptr(dst)) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return FEP3M_OK;
+}
+
+void ev_record(fep3m_ctx* c, int k) {
+  if (c->timing) cudaEventRecord(c->ev[k], c->stream);
+}
+double ev_ms(fep3m_ctx* c, int a, int b) {
+  float ms = 0;
+  if (cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return ms;
+}
+
+int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad) {
+  ev_record(c, 0);
+  CK(assemble_forward(c));
+  ev_record(c, 1);
+  int it = 0, rs = 0;
+  double rel = 0;
+  CK(mesh_solve(c, c->b64, c->phi64, &it, &rel, &rs));
+  c->stats.mg_iterations = it;
+  c->stats.mg_rel_residual = rel;
+  c->stats.refine_steps = rs;
+  ev_record(c, 2);
+  CK(pair_forward(c, phi_dev, want_grad));
+  ev_record(c, 3);
+  c->have_forward = true;
+  c->have_grad = want_grad != 0;
+  const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : (c->precision == FEP3M_FP64 ? 1e-13 : 1e-10);
+  return rel <= 10 * rtol ? FEP3M_OK : FEP3M_ENOCONV;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fep3m_strerror(int s) {
+  switch (s) {
+    case FEP3M_OK: return "ok";
+    case FEP3M_EINVAL: return "invalid argument";
+    case FEP3M_ENOTNEUTRAL: return "charges are not neutral (set FEP3M_NEUTRALIZE to add a background)";
+    case FEP3M_ENOMEM: return "device allocation failed";
+    case FEP3M_ECUDA: return "CUDA runtime error";
+    case FEP3M_ENOCONV: return "mesh solve did not reach its tolerance";
+    case FEP3M_ESTATE: return "call out of order";
+    case FEP3M_ETIMEOUT: return "bounded device wait gave up";
+    default: return "unknown status";
+  }
+}
+
+void fep3m_destroy(fep3m_ctx* c) {
+  if (!c) return;
+  free_particles(c);
+  void* p[] = {c->Hw64, c->Hw32, c->count, c->start, c->fill, c->scan_tmp, c->C, c->rv, c->b64, c->phi64,
+               c->res64, c->g64, c->lam64, c->scal, c->iflags, c->phi_mesh_T, c->W_el, c->A_el, c->mu_v,
+               c->red_tmp, c->red_counter};
+  for (void* q : p) dfree(q);
+  mg_free(c);
+  solver_free(c);
+  if (c->ev_init)
+    for (int k = 0; k < 8; ++k) cudaEventDestroy(c->ev[k]);
+  delete c;
+}
+
+int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
+  if (!cfg || !out) return FEP3M_EINVAL;
+  *out = nullptr;
+  if (!(cfg->L > 0) || !std::isfinite(cfg->L) || cfg->q != 1 || cfg->n_sr < 1 || cfg->n_sr > 4 ||
+      cfg->n_el < 2 * cfg->n_sr + 1 || cfg->n_el > 400 ||
+      (cfg->precision != FEP3M_FP64 && cfg->precision != FEP3M_MIXED) || cfg->mg_rtol < 0 || cfg->table_pad < 0)
+    return FEP3M_EINVAL;
+  fep3m_ctx* c = new (std::nothrow) fep3m_ctx();
+  if (!c) return FEP3M_ENOMEM;
+  c->cfg = *cfg;
+  c->stream = (cudaStream_t)stream;
+  cudaGetDevice(&c->device);
+  c->n = cfg->n_el;
+  c->n_sr = cfg->n_sr;
+  c->keep = cfg->n_sr + 1;
+  c->noff = 2 * cfg->n_sr + 2;
+  c->L = cfg->L;
+  c->h = cfg->L / cfg->n_el;
+  c->inv_h = cfg->n_el / cfg->L;
+  c->precision = cfg->precision;
+  std::memset(&c->stats, 0, sizeof(c->stats));
+  int st = FEP3M_OK;
+  auto fail = [&](int s) {
+    fep3m_destroy(c);
+    return s;
+  };
+  make_stencils(c->st);
+  // FE basis-screen table and its [vertex offset][node] layout for the kernels
+  build_table(c->n_sr, cfg->table_pad > 0 ? cfg->table_pad : 4, c->table_host);
+  const int keep = c->keep, noff = c->noff, sk = 6 * keep + 1;
+  std::vector<double> Hw((size_t)noff * noff * noff * 64);
+  for (int oz = 0; oz < noff; ++oz)
+    for (int oy = 0; oy < noff; ++oy)
+      for (int ox = 0; ox < noff; ++ox)
+        for (int m = 0; m < 64; ++m) {
+          const int mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
+          const size_t o = ox + (size_t)noff * (oy + (size_t)noff * oz);
+          Hw[o * 64 + m] = c->table_host[(3 * ox + mx) + (size_t)sk * ((3 * oy + my) + (size_t)sk * (3 * oz + mz))];
+        }
+  std::vector<float> Hw32(Hw.begin(), Hw.end());
+  if ((st = from_cuda(dalloc(&c->Hw64, Hw.size()))) != FEP3M_OK) return fail(st);
+  if ((st = from_cuda(dalloc(&c->Hw32, Hw.size()))) != FEP3M_OK) return fail(st);
+  cudaMemcpy(c->Hw64, Hw.data(), Hw.size() * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy(c->Hw32, Hw32.data(), Hw32.size() * 4, cudaMemcpyHostToDevice);
+  const int64_t ne = (int64_t)c->n * c->n * c->n, nodes = 27 * ne;
+  const size_t es = c->precision == FEP3M_MIXED ? 4 : 8;
+  cudaError_t e = cudaSuccess;
+  if ((e = dalloc(&c->count, ne)) != cudaSuccess || (e = dalloc(&c->start, ne + 1)) != cudaSuccess ||
+      (e = dalloc(&c->fill, ne)) != cudaSuccess ||
+      (e = cudaMalloc(&c->scan_tmp, scan_tmp_bytes(ne))) != cudaSuccess ||
+      (e = cudaMalloc(&c->C, ne * 8 * es)) != cudaSuccess || (e = cudaMalloc(&c->rv, ne * es)) != cudaSuccess ||
+      (e = dalloc(&c->b64, nodes)) != cudaSuccess || (e = dalloc(&c->phi64, nodes)) != cudaSuccess ||
+      (e = dalloc(&c->res64, nodes)) != cudaSuccess || (e = dalloc(&c->g64, nodes)) != cudaSuccess ||
+      (e = dalloc(&c->lam64, nodes)) != cudaSuccess || (e = dalloc(&c->scal, 64)) != cudaSuccess ||
+      (e = dalloc(&c->iflags, 16)) != cudaSuccess || (e = cudaMalloc(&c->W_el, ne * 64 * es)) != cudaSuccess ||
+      (e = cudaMalloc(&c->A_el, ne * 8 * es)) != cudaSuccess || (e = cudaMalloc(&c->mu_v, ne * es)) != cudaSuccess ||
+      (e = dalloc(&c->red_tmp, 1024)) != cudaSuccess || (e = dalloc(&c->red_counter, 1)) != cudaSuccess)
+    return fail(from_cuda(e));
+  if (c->precision == FEP3M_MIXED && (e = cudaMalloc(&c->phi_mesh_T, nodes * es)) != cudaSuccess)
+    return fail(from_cuda(e));
+  cudaMemset(c->red_counter, 0, sizeof(unsigned int));
+  cudaMemset(c->iflags, 0, 16 * sizeof(int));
+  if ((e = mg_setup(c)) != cudaSuccess) return fail(from_cuda(e));
+  c->stats.mg_levels = (int)c->mg.lv.size();
+  for (int k = 0; k < 8; ++k) cudaEventCreate(&c->ev[k]);
+  c->ev_init = true;
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(from_cuda(e));
+  *out = c;
+  return FEP3M_OK;
+}
+
+int fep3m_set_particles(fep3m_ctx* c, int64_t N, const double* pos, const double* Q) {
+  if (!c || !pos || !Q || N < 1 || N > ((int64_t)1 << 31) - 1) return FEP3M_EINVAL;
+  int st = grow_particles(c, N);
+  if (st != FEP3M_OK) return st;
+  c->N = N;
+  c->stats.n_particles = N;
+  const double* dpos = pos;
+  const double* dQ = Q;
+  if (!is_device_ptr(pos)) {
+    CK(cudaMemcpyAsync(c->pos_in, pos, 3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    dpos = c->pos_in;
+  }
+  if (!is_device_ptr(Q)) {
+    CK(cudaMemcpyAsync(c->Q_in, Q, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    dQ = c->Q_in;
+  }
+  ev_record(c, 6);
+  CK(cudaMemsetAsync(c->iflags, 0, sizeof(int), c->stream));
+  CK(bin_particles(c, dpos, dQ, c->precision == FEP3M_MIXED));
+  k_charge_sums<<<1, PT, 0, c->stream>>>(N, dQ, c->scal + 32);   // one block: writes the totals
+  ev_record(c, 7);
+  double sums[2];
+  int flag = 0;
+  CK(cudaMemcpyAsync(sums, c->scal + 32, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&flag, c->iflags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->have_particles = false;
+  c->have_forward = false;
+  if (flag) return FEP3M_EINVAL;
+  if (!(c->cfg.flags & FEP3M_NEUTRALIZE) && std::fabs(sums[0]) > 1e-12 * sums[1]) return FEP3M_ENOTNEUTRAL;
+  c->have_particles = true;
+  if (c->timing) c->stats.ms_bin = ev_ms(c, 6, 7);
+  return FEP3M_OK;
+}
+
+int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
+  if (!c) return FEP3M_EINVAL;
+  if (!c->have_particles) return FEP3M_ESTATE;
+  const int64_t N = c->N;
+  const bool phi_dev = is_device_ptr(phi);
+  int st = run_forward(c, phi_dev ? phi : (phi ? c->out_tmp : nullptr), force != nullptr);
+  if (st != FEP3M_OK && st != FEP3M_ENOCONV) return st;
+  if (phi && !phi_dev) {
+    int s2 = deliver(c, phi, c->out_tmp, N * sizeof(double));
+    if (s2 != FEP3M_OK) return s2;
+  }
+  if (U) {
+    CK(energy(c, c->scal + 40));
+    CK(cudaMemcpyAsync(U, c->scal + 40, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (force) {
+    const bool fdev = is_device_ptr(force);
+    double* dst = fdev ? force : c->out_tmp;
+    CK(adjoint(c, 1.0, nullptr, dst, nullptr));
+    k_scale<<<gsz(3 * N), PT, 0, c->stream>>>(3 * N, dst, -1.0);
+    CK(cudaGetLastError());
+    ev_record(c, 4);
+    if (!fdev) {
+      int s2 = deliver(c, force, c->out_tmp, 3 * N * sizeof(double));
+      if (s2 != FEP3M_OK) return s2;
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->timing) {
+    c->stats.ms_assemble = ev_ms(c, 0, 1);
+    c->stats.ms_solve = ev_ms(c, 1, 2);
+    c->stats.ms_pair = ev_ms(c, 2, 3);
+    c->stats.ms_adjoint = force ? ev_ms(c, 3, 4) : 0.0;
+  }
+  return st;
+}
+
+int fep3m_vjp(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double* dQ) {
+  if (!c || !std::isfinite(gU)) return FEP3M_EINVAL;
+  if (!c->have_particles) return FEP3M_ESTATE;
+  const int64_t N = c->N;
+  if (!c->have_forward || !c->have_grad) {
+    int st = run_forward(c, nullptr, 1);
+    if (st != FEP3M_OK && st != FEP3M_ENOCONV) return st;
+  }
+  const double* g = gphi;
+  if (gphi && !is_device_ptr(gphi)) {
+    CK(cudaMemcpyAsync(c->gphi_dev, gphi, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    g = c->gphi_dev;
+  }
+  const bool pdev = is_device_ptr(dpos), qdev = is_device_ptr(dQ);
+  double* dp = dpos ? (pdev ? dpos : c->out_tmp) : nullptr;
+  double* dq = dQ ? (qdev ? dQ : c->out_tmp + 3 * N) : nullptr;
+  CK(adjoint(c, gU, g, dp, dq));
+  if (dpos && !pdev) {
+    int s = deliver(c, dpos, c->out_tmp, 3 * N * sizeof(double));
+    if (s != FEP3M_OK) return s;
+  }
+  if (dQ && !qdev) {
+    int s = deliver(c, dQ, c->out_tmp + 3 * N, N * sizeof(double));
+    if (s != FEP3M_OK) return s;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return FEP3M_OK;
+}
+
+int fep3m_get_stats(const fep3m_ctx* c, fep3m_stats* out) {
+  if (!c || !out) return FEP3M_EINVAL;
+  *out = c->stats;
+  return FEP3M_OK;
+}
+
+int fep3m_set_timing(fep3m_ctx* c, int enable) {
+  if (!c) return FEP3M_EINVAL;
+  c->timing = enable != 0;
+  return FEP3M_OK;
+}
+
+int fep3m_get_binning(const fep3m_ctx* cc, int32_t* perm, int32_t* count, int32_t* cell, double* delta) {
+  fep3m_ctx* c = const_cast<fep3m_ctx*>(cc);
+  if (!c) return FEP3M_EINVAL;
+  if (!c->have_particles) return FEP3M_ESTATE;
+  const int64_t N = c->N, ne = (int64_t)c->n * c->n * c->n;
+  int s;
+  if ((s = deliver(c, perm, c->perm, N * 4)) != FEP3M_OK) return s;
+  if ((s = deliver(c, count, c->count, ne * 4)) != FEP3M_OK) return s;
+  if ((s = deliver(c, cell, c->cell, N * 4)) != FEP3M_OK) return s;
+  if ((s = deliver(c, delta, c->delta, 3 * N * 8)) != FEP3M_OK) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  return FEP3M_OK;
+}
+
+int fep3m_get_mesh(const fep3m_ctx* cc, double* C, double* b, double* phi_mesh) {
+  fep3m_ctx* c = const_cast<fep3m_ctx*>(cc);
+  if (!c) return FEP3M_EINVAL;
+  if (!c->have_forward) return FEP3M_ESTATE;
+  const int64_t ne = (int64_t)c->n * c->n * c->n, nodes = 27 * ne;
+  // staging through res64 (FP64, nodes >= 8 ne since 27 > 8)
+  if (C) {
+    if (c->precision == FEP3M_MIXED)
+      k_to_double<float><<<gsz(8 * ne), PT, 0, c->stream>>>(8 * ne, (const float*)c->C, c->res64, 1.0);
+    else
+      k_to_double<double><<<gsz(8 * ne), PT, 0, c->stream>>>(8 * ne, (const double*)c->C, c->res64, 1.0);
+    int s = deliver(c, C, c->res64, 8 * ne * 8);
+    if (s != FEP3M_OK) return s;
+  }
+  if (b) {
+    int s = deliver(c, b, c->b64, nodes * 8);
+    if (s != FEP3M_OK) return s;
+  }
+  if (phi_mesh) {
+    k_to_double<double><<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->phi64, c->res64, c->inv_h);
+    int s = deliver(c, phi_mesh, c->res64, nodes * 8);
+    if (s != FEP3M_OK) return s;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return FEP3M_OK;
+}
+
+int fep3m_solve_mesh(fep3m_ctx* c, const double* b, double* phi) {
+  if (!c || !b || !phi) return FEP3M_EINVAL;
+  const int64_t nodes = (int64_t)27 * c->n * c->n * c->n;
+  CK(cudaMemcpyAsync(c->g64, b, nodes * 8, is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     c->stream));
+  int it = 0, rs = 0;
+  double rel = 0;
+  CK(mesh_solve(c, c->g64, c->lam64, &it, &rel, &rs));
+  c->stats.mg_iterations = it;
+  c->stats.mg_rel_residual = rel;
+  c->stats.refine_steps = rs;
+  k_to_double<double><<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->lam64, c->res64, c->inv_h);
+  int s = deliver(c, phi, c->res64, nodes * 8);
+  if (s != FEP3M_OK) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : (c->precision == FEP3M_FP64 ? 1e-13 : 1e-10);
+  return rel <= 10 * rtol ? FEP3M_OK : FEP3M_ENOCONV;
+}
+
+int fep3m_get_table(const fep3m_ctx* c, double* table) {
+  if (!c || !table) return FEP3M_EINVAL;
+  if (is_device_ptr(table)) {
+    CK(cudaMemcpy(table, c->table_host.data(), c->table_host.size() * 8, cudaMemcpyHostToDevice));
+  } else {
+    std::memcpy(table, c->table_host.data(), c->table_host.size() * 8);
+  }
+  return FEP3M_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// Internal declarations of the FE-P3M library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+
+#include "fep3m.h"
+
+namespace fep3m {
+
+// ---------------------------------------------------------------------------
+// Order-3 equispaced Lagrange basis on [0, 1] (nodes 0, 1/3, 2/3, 1): the 1-D
+// factors of the order-p = 3 hexahedral FE basis u_m (Sec. 2.2, Eq. evalsmooth).
+// ---------------------------------------------------------------------------
+template <class T>
+__host__ __device__ __forceinline__ void q3_values(T t, T v[4]) {
+  const T a = t, b = t - T(1) / T(3), c = t - T(2) / T(3), d = t - T(1);
+  v[0] = T(-4.5) * b * c * d;
+  v[1] = T(13.5) * a * c * d;
+  v[2] = T(-13.5) * a * b * d;
+  v[3] = T(4.5) * a * b * c;
+}
+template <class T>
+__host__ __device__ __forceinline__ void q3_derivs(T t, T v[4]) {
+  const T a = t, b = t - T(1) / T(3), c = t - T(2) / T(3), d = t - T(1);
+  v[0] = T(-4.5) * (c * d + b * d + b * c);
+  v[1] = T(13.5) * (c * d + a * d + a * c);
+  v[2] = T(-13.5) * (b * d + a * d + a * b);
+  v[3] = T(4.5) * (b * c + a * c + a * b);
+}
+
+template <class T> struct vec4;
+template <> struct vec4<double> { typedef double4_32a type; };
+template <> struct vec4<float> { typedef float4 type; };
+
+// 1-D periodic 7-tap stencils of the reference (h = 1) order-3 mass and
+// stiffness matrices: row of global node g with type tau = g mod 3 has
+// coefficients S[tau][j + 3] on node g + j, j = -3..3.
+struct Stencils {
+  double M[3][7];
+  double K[3][7];
+  double diagM[3], diagK[3];
+  // prolongation coarse (element 2h) -> fine (element h), 1-D: fine node at
+  // position s/6 (s = 0..5) of a coarse element takes sum_j P[s][j] x_c[3E + j]
+  double P[6][4];
+  // mixed mass order-3 rows x order-1 columns, element level: Mpq[k][j]
+  double Mpq[4][2];
+};
+
+// multigrid level: n elements per axis, N = 3n nodes per axis
+struct Level {
+  int n = 0, N = 0;
+  size_t size = 0;            // N^3
+  void* x = nullptr;          // solution / correction
+  void* b = nullptr;          // right-hand side
+  void* r = nullptr;          // residual / work
+  void* d = nullptr;          // Chebyshev direction
+  void* t1 = nullptr;         // apply intermediates
+  void* t2 = nullptr;
+  void* a = nullptr;
+  void* c = nullptr;
+};
+
+struct CoarseSolver {
+  int N = 0;                  // nodes per axis on the coarsest level
+  double* V64 = nullptr;      // N x N, V[i][k] (row i node, column k mode), M-orthonormal
+  double* Dinv64 = nullptr;   // N^3 inverse eigenvalue sums (0 for the constant mode)
+  float* V32 = nullptr;
+  float* Dinv32 = nullptr;
+};
+
+struct Hierarchy {
+  int elem_size = 0;          // 8 (double) or 4 (float)
+  std::vector<Level> lv;
+  CoarseSolver coarse;
+  double lmax = 0;            // estimate of lambda_max(D^-1 K)
+  int cheb_degree = 3;
+};
+
+}  // namespace fep3m
+
+struct fep3m_ctx {
+  fep3m_config cfg;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int n = 0, n_sr = 3, keep = 4, noff = 8;   // noff = 2 n_sr + 2 vertex offsets per axis
+  double L = 1, h = 1, inv_h = 1;
+  int precision = FEP3M_FP64;
+  fep3m::Stencils st;
+  // kept FE table (host copy) and device copies in [offset][node] layout
+  std::vector<double> table_host;
+  double* Hw64 = nullptr;
+  float* Hw32 = nullptr;
+  // particles
+  int64_t N = 0, cap = 0;
+  bool have_particles = false, have_forward = false, have_grad = false;
+  double* pos_in = nullptr;      // N*3 (staging for host inputs)
+  double* Q_in = nullptr;        // N
+  int* cell = nullptr;           // N
+  double* delta = nullptr;       // N*3 original order
+  int* perm = nullptr;           // N
+  int* count = nullptr;          // n^3
+  int* start = nullptr;          // n^3 + 1
+  int* fill = nullptr;           // n^3
+  void* part = nullptr;          // sorted (t, Q): double4 or float4, N
+  void* scan_tmp = nullptr;
+  size_t scan_tmp_bytes = 0;
+  // element / vertex fields
+  void* C = nullptr;             // n^3 * 8 (T)
+  void* rv = nullptr;            // n^3 vertex density (T)
+  // fine-level FP64 vectors
+  double* b64 = nullptr;         // (3n)^3 load vector
+  double* phi64 = nullptr;       // (3n)^3 mesh potential, reference units
+  double* res64 = nullptr;       // refinement residual
+  double* g64 = nullptr;         // adjoint right-hand side
+  double* lam64 = nullptr;       // adjoint mesh solution
+  double* scal = nullptr;        // device scalars (dots, norms, flags), 64 doubles
+  int* iflags = nullptr;         // device int flags: [0] input error, [1] converged, ...
+  void* phi_mesh_T = nullptr;    // mesh potential in working precision (for the pair kernel)
+  void* lam_T = nullptr;
+  fep3m::Hierarchy mg;
+  // per-particle outputs, sorted order
+  double* phi_s = nullptr;       // N
+  double* E_s = nullptr;         // N*3 target-side gradient
+  double* w_s = nullptr;         // N adjoint weights
+  double* psi_s = nullptr;       // N singular adjoint potential
+  double* gpsi_s = nullptr;      // N*3
+  double* Q_s = nullptr;         // N sorted charges (FP64)
+  double* gphi_dev = nullptr;    // N staging for a host gphi
+  void* W_el = nullptr;          // n^3 * 64 element deposits (T)
+  void* A_el = nullptr;          // n^3 * 8 screen adjoint (T)
+  void* mu_v = nullptr;          // n^3 vertex adjoint (T)
+  void* sb[6] = {};              // PCG vectors r, z, p, q, x, rhs (working precision, fine level)
+  size_t sb_bytes = 0;
+  double* ap64[4] = {};          // FP64 fine-level apply intermediates (refinement residual)
+  size_t ap64_n = 0;
+  double* red_tmp = nullptr;     // reduction partials (1024)
+  unsigned int* red_counter = nullptr;
+  double* out_tmp = nullptr;     // N*3 staging for host outputs
+  // stats
+  fep3m_stats stats;
+  bool timing = false;
+  cudaEvent_t ev[8];
+  bool ev_init = false;
+};
+
+namespace fep3m {
+// host setup (setup.cpp)
+void element_matrices_q3(double Me[4][4], double Ke[4][4], double Mpq[4][2]);
+void make_stencils(Stencils& st);
+void generalized_eigen(int n, const std::vector<double>& A, const std::vector<double>& B,
+                       std::vector<double>& lam, std::vector<double>& V);
+void build_table(int n_sr, int pad, std::vector<double>& kept);
+double estimate_lmax(const Stencils& st, int n);
+
+// device launches (return cudaGetLastError-style codes)
+cudaError_t bin_particles(fep3m_ctx* c, const double* pos, const double* Q, int use_fp32);
+cudaError_t assemble_forward(fep3m_ctx* c);
+cudaError_t mg_setup(fep3m_ctx* c);
+void mg_free(fep3m_ctx* c);
+void solver_free(fep3m_ctx* c);
+size_t scan_tmp_bytes(int64_t n);
+// mu = 4 pi (Mpq^T)^(x)3 lam on the vertex grid (working precision); work1/2 sized n*(3n)^2
+cudaError_t vertex_adjoint(fep3m_ctx* c, const double* lam, void* mu, void* work1, void* work2);
+// solve K phi = b (FP64 in/out, reference units); returns iterations; writes residual in scal
+cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, double* relres,
+                       int* refine_steps);
+cudaError_t pair_forward(fep3m_ctx* c, double* phi_out, int want_grad);
+cudaError_t adjoint(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double* dQ);
+cudaError_t energy(fep3m_ctx* c, double* U_dev);
+}  // namespace fep3m

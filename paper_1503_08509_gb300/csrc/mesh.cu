@@ -1,0 +1,818 @@
+// Charge assignment and the periodic FE mesh solve (Sec. 2.1-2.2).
+//
+//   element-to-point list  C[e][k] = sum_{j in e} Q_j c_k(t_j)      (Eq. oned, q = 1)
+//   vertex density         r_v     = sum over (element, corner) at v (Eq. assign)
+//   load vector            b       = 4 pi (Mpq (x) Mpq (x) Mpq) r    (Eq. poisson, 4 pi units)
+//   mesh solve             K phi   = b - (sum b) w / sum w, int phi = 0
+//
+// Everything on the mesh is in reference units (element size 1): the
+// physical mesh potential is phi / h.  K is the Kronecker sum of 1-D periodic
+// order-3 stiffness and mass matrices, applied matrix-free by sum
+// factorisation (three 7-tap passes).  The solver is a conjugate gradient
+// preconditioned by one multigrid V-cycle: h-coarsening with the same order-3
+// operator on every level (the coarse spaces are nested, so the Galerkin
+// coarse operator is the coarse-mesh operator), Chebyshev-Jacobi smoothing
+// and an exact coarsest solve by fast diagonalisation.  FEP3M_MIXED runs the
+// cycle and the CG in FP32 inside an FP64 iterative-refinement loop whose
+// residual, projections and update are FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fep3m {
+
+__constant__ double cM64[3][7], cK64[3][7], cP64[6][4], cMpq64[4][2], cDM64[3], cDK64[3];
+__constant__ float cM32[3][7], cK32[3][7], cP32[6][4], cDM32[3], cDK32[3];
+
+template <class T> struct Cst;
+template <> struct Cst<double> {
+  static __device__ __forceinline__ double M(int t, int j) { return cM64[t][j]; }
+  static __device__ __forceinline__ double K(int t, int j) { return cK64[t][j]; }
+  static __device__ __forceinline__ double P(int s, int j) { return cP64[s][j]; }
+  static __device__ __forceinline__ double DM(int t) { return cDM64[t]; }
+  static __device__ __forceinline__ double DK(int t) { return cDK64[t]; }
+};
+template <> struct Cst<float> {
+  static __device__ __forceinline__ float M(int t, int j) { return cM32[t][j]; }
+  static __device__ __forceinline__ float K(int t, int j) { return cK32[t][j]; }
+  static __device__ __forceinline__ float P(int s, int j) { return cP32[s][j]; }
+  static __device__ __forceinline__ float DM(int t) { return cDM32[t]; }
+  static __device__ __forceinline__ float DK(int t) { return cDK32[t]; }
+};
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline int grid_for(size_t n) { return (int)std::min<size_t>((n + TPB - 1) / TPB, (size_t)1 << 30); }
+
+__device__ __forceinline__ int wrapi(int i, int N) { return i < 0 ? i + N : (i >= N ? i - N : i); }
+
+// ---------------------------------------------------------------- assembly
+template <class T>
+__global__ void k_elem_coeff(int64_t ne, const int* __restrict__ start, const int* __restrict__ count,
+                             const typename vec4<T>::type* __restrict__ part, T* __restrict__ C) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  T acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = T(0);
+  const int s = start[e], cnt = count[e];
+  for (int j = s; j < s + cnt; ++j) {
+    typename vec4<T>::type p = part[j];
+    const T wx[2] = {T(1) - p.x, p.x}, wy[2] = {T(1) - p.y, p.y}, wz[2] = {T(1) - p.z, p.z};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] += p.w * (wx[k & 1] * wy[(k >> 1) & 1] * wz[k >> 2]);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) C[e * 8 + k] = acc[k];
+}
+
+template <class T>
+__global__ void k_vertex_density(int n, const T* __restrict__ C, T* __restrict__ rv) {
+  int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t ne = (int64_t)n * n * n;
+  if (v >= ne) return;
+  const int vx = (int)(v % n), vy = (int)((v / n) % n), vz = (int)(v / ((int64_t)n * n));
+  T acc = T(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    int ex = wrapi(vx - (k & 1), n), ey = wrapi(vy - ((k >> 1) & 1), n), ez = wrapi(vz - (k >> 2), n);
+    acc += C[(ex + (int64_t)n * (ey + (int64_t)n * ez)) * 8 + k];
+  }
+  rv[v] = acc;
+}
+
+// one axis of the order-3 x order-1 mixed mass: global order-3 node g -> up to
+// three vertices with weights
+__device__ __forceinline__ int mpq_row(int g, int n, int vtx[3], double wgt[3]) {
+  const int e = g / 3, t = g - 3 * e;
+  if (t == 0) {
+    vtx[0] = wrapi(e - 1, n); wgt[0] = cMpq64[3][0];
+    vtx[1] = e;               wgt[1] = cMpq64[0][0] + cMpq64[3][1];
+    vtx[2] = wrapi(e + 1, n); wgt[2] = cMpq64[0][1];
+    return 3;
+  }
+  vtx[0] = e;               wgt[0] = cMpq64[t][0];
+  vtx[1] = wrapi(e + 1, n); wgt[1] = cMpq64[t][1];
+  return 2;
+}
+
+template <class T>
+__global__ void k_load_vector(int n, const T* __restrict__ rv, double* __restrict__ b) {
+  const int N = 3 * n;
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= (int64_t)N * N * N) return;
+  const int ix = (int)(g % N), iy = (int)((g / N) % N), iz = (int)(g / ((int64_t)N * N));
+  int vx[3], vy[3], vz[3];
+  double wx[3], wy[3], wz[3];
+  const int nx = mpq_row(ix, n, vx, wx), ny = mpq_row(iy, n, vy, wy), nz = mpq_row(iz, n, vz, wz);
+  double acc = 0.0;
+  for (int c = 0; c < nz; ++c)
+    for (int bb = 0; bb < ny; ++bb) {
+      double wyz = wy[bb] * wz[c];
+      const int64_t row = (int64_t)n * (vy[bb] + (int64_t)n * vz[c]);
+      for (int a = 0; a < nx; ++a) acc += wx[a] * wyz * (double)rv[vx[a] + row];
+    }
+  b[g] = 4.0 * M_PI * acc;
+}
+
+// ------------------------------------------------------------ operator apply
+template <class T>
+__global__ void k_apply_z(int N, const T* __restrict__ x, T* __restrict__ t1, T* __restrict__ t2) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t NN = (int64_t)N * N;
+  if (g >= NN * N) return;
+  const int iz = (int)(g / NN);
+  const int64_t xy = g - iz * NN;
+  const int t = iz % 3;
+  T s1 = T(0), s2 = T(0);
+#pragma unroll
+  for (int j = -3; j <= 3; ++j) {
+    const T v = x[xy + wrapi(iz + j, N) * NN];
+    s1 += Cst<T>::M(t, j + 3) * v;
+    s2 += Cst<T>::K(t, j + 3) * v;
+  }
+  t1[g] = s1;
+  t2[g] = s2;
+}
+
+template <class T>
+__global__ void k_apply_y(int N, const T* __restrict__ t1, const T* __restrict__ t2, T* __restrict__ a,
+                          T* __restrict__ c) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t NN = (int64_t)N * N;
+  if (g >= NN * N) return;
+  const int64_t iz = g / NN;
+  const int iy = (int)((g / N) % N), ix = (int)(g % N);
+  const int t = iy % 3;
+  T s1 = T(0), s2 = T(0);
+#pragma unroll
+  for (int j = -3; j <= 3; ++j) {
+    const int64_t h = ix + (int64_t)N * wrapi(iy + j, N) + iz * NN;
+    const T u = t1[h], w = t2[h];
+    s1 += Cst<T>::M(t, j + 3) * u;
+    s2 += Cst<T>::K(t, j + 3) * u + Cst<T>::M(t, j + 3) * w;
+  }
+  a[g] = s1;
+  c[g] = s2;
+}
+
+template <class T>
+__device__ __forceinline__ T dinv(int ix, int iy, int iz) {
+  const int a = ix % 3, b = iy % 3, c = iz % 3;
+  return T(1) / (Cst<T>::DK(a) * Cst<T>::DM(b) * Cst<T>::DM(c) + Cst<T>::DM(a) * Cst<T>::DK(b) * Cst<T>::DM(c) +
+                 Cst<T>::DM(a) * Cst<T>::DM(b) * Cst<T>::DK(c));
+}
+
+enum { EPI_Y = 0, EPI_RESID = 1, EPI_CHEB = 2 };
+
+// final pass y = Kx a + Mx c with a fused epilogue:
+//   EPI_Y      out = y
+//   EPI_RESID  out = b - y
+//   EPI_CHEB   d = c1 d + c2 D^-1 (b - y); x += d   (one Chebyshev step)
+template <class T, int EPI>
+__global__ void k_apply_x(int N, const T* __restrict__ a, const T* __restrict__ c, T* __restrict__ out,
+                          const T* __restrict__ b, T* __restrict__ d, T* __restrict__ x, T c1, T c2) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t NN = (int64_t)N * N;
+  if (g >= NN * N) return;
+  const int ix = (int)(g % N);
+  const int64_t row = g - ix;
+  const int t = ix % 3;
+  T y = T(0);
+#pragma unroll
+  for (int j = -3; j <= 3; ++j) {
+    const int64_t h = row + wrapi(ix + j, N);
+    y += Cst<T>::K(t, j + 3) * a[h] + Cst<T>::M(t, j + 3) * c[h];
+  }
+  if (EPI == EPI_Y) {
+    out[g] = y;
+  } else if (EPI == EPI_RESID) {
+    out[g] = b[g] - y;
+  } else {
+    const int iy = (int)((g / N) % N), iz = (int)(g / NN);
+    const T r = b[g] - y;
+    const T dn = c1 * d[g] + c2 * dinv<T>(ix, iy, iz) * r;
+    d[g] = dn;
+    x[g] += dn;
+  }
+}
+
+// first Chebyshev step from x = 0: d = D^-1 b / theta, x = d
+template <class T>
+__global__ void k_cheb0(int N, const T* __restrict__ b, T* __restrict__ d, T* __restrict__ x, T inv_theta) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t NN = (int64_t)N * N;
+  if (g >= NN * N) return;
+  const int ix = (int)(g % N), iy = (int)((g / N) % N), iz = (int)(g / NN);
+  const T v = inv_theta * dinv<T>(ix, iy, iz) * b[g];
+  d[g] = v;
+  x[g] = v;
+}
+
+// ------------------------------------------------------- grid transfers
+// restriction along one axis (transpose of the 1-D prolongation): the input
+// has 2 Nc nodes along `axis`, the output Nc; other extents d1, d2.
+template <class T>
+__global__ void k_restrict_axis(int axis, int Nc, int e0, int e1, int e2, const T* __restrict__ in,
+                                T* __restrict__ out, T scale) {
+  // output extents (e0, e1, e2) in (x, y, z); input extents equal except 2 Nc along axis
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t tot = (int64_t)e0 * e1 * e2;
+  if (g >= tot) return;
+  int i[3] = {(int)(g % e0), (int)((g / e0) % e1), (int)(g / ((int64_t)e0 * e1))};
+  int ein[3] = {e0, e1, e2};
+  const int Nf = 2 * Nc;
+  ein[axis] = Nf;
+  const int64_t st[3] = {1, ein[0], (int64_t)ein[0] * ein[1]};
+  const int gc = i[axis];
+  i[axis] = 0;
+  const int64_t base = i[0] * st[0] + i[1] * st[1] + i[2] * st[2];
+  const int E = gc / 3, j = gc - 3 * E;
+  T acc = T(0);
+#pragma unroll
+  for (int s = 1; s < 6; ++s) acc += Cst<T>::P(s, j) * in[base + (6 * E + s) * st[axis]];
+  if (j == 0) {
+    acc += in[base + (6 * E) * st[axis]];   // P[0][0] = 1
+    const int El = E == 0 ? Nc / 3 - 1 : E - 1;
+#pragma unroll
+    for (int s = 1; s < 6; ++s) acc += Cst<T>::P(s, 3) * in[base + (6 * El + s) * st[axis]];
+  }
+  out[g] = scale * acc;
+}
+
+// prolongation along one axis: output has 2 Nc nodes along axis; ADD: out += .
+template <class T, bool ADD>
+__global__ void k_prolong_axis(int axis, int Nc, int e0, int e1, int e2, const T* __restrict__ in,
+                               T* __restrict__ out) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t tot = (int64_t)e0 * e1 * e2;
+  if (g >= tot) return;
+  int i[3] = {(int)(g % e0), (int)((g / e0) % e1), (int)(g / ((int64_t)e0 * e1))};
+  int ein[3] = {e0, e1, e2};
+  ein[axis] = Nc;
+  const int64_t st[3] = {1, ein[0], (int64_t)ein[0] * ein[1]};
+  const int f = i[axis];
+  i[axis] = 0;
+  const int64_t base = i[0] * st[0] + i[1] * st[1] + i[2] * st[2];
+  const int E = f / 6, s = f - 6 * E;
+  T acc = T(0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int gc = 3 * E + j;
+    if (gc >= Nc) gc -= Nc;
+    acc += Cst<T>::P(s, j) * in[base + gc * st[axis]];
+  }
+  if (ADD) out[g] += acc;
+  else out[g] = acc;
+}
+
+// dense 1-D transform along an axis: out[.. i ..] = sum_k A[i][k] in[.. k ..]
+// (A = V^T when transpose), optionally scaled elementwise by s after.
+template <class T>
+__global__ void k_dense_axis(int N, int axis, const T* __restrict__ V, bool transpose, const T* __restrict__ in,
+                             T* __restrict__ out, const T* __restrict__ scale) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t NN = (int64_t)N * N;
+  if (g >= NN * N) return;
+  int i[3] = {(int)(g % N), (int)((g / N) % N), (int)(g / NN)};
+  const int64_t st[3] = {1, N, NN};
+  const int r = i[axis];
+  i[axis] = 0;
+  const int64_t base = i[0] + i[1] * st[1] + i[2] * st[2];
+  T acc = T(0);
+  for (int k = 0; k < N; ++k) {
+    const T a = transpose ? V[(int64_t)k * N + r] : V[(int64_t)r * N + k];
+    acc += a * in[base + k * st[axis]];
+  }
+  if (scale) acc *= scale[g];
+  out[g] = acc;
+}
+
+// ---------------------------------------------------------- reductions
+// deterministic two-level sum: each block writes a partial; the last block to
+// finish adds the partials in index order.  mode 0: x.y, 1: sum x,
+// 2: sum w3 x (node integrals), 3: x.x
+template <class T>
+__global__ void k_reduce(int N, int mode, const T* __restrict__ x, const T* __restrict__ y,
+                         double* __restrict__ partials, unsigned int* __restrict__ counter,
+                         double* __restrict__ out) {
+  __shared__ double sh[TPB / 32];
+  __shared__ bool last;
+  const int64_t NN = (int64_t)N * N, tot = NN * N;
+  double acc = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < tot; g += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)x[g];
+    if (mode == 0) acc += v * (double)y[g];
+    else if (mode == 1) acc += v;
+    else if (mode == 3) acc += v * v;
+    else {
+      const int ix = (int)(g % N), iy = (int)((g / N) % N), iz = (int)(g / NN);
+      const double w[3] = {0.25, 0.375, 0.375};
+      acc += w[ix % 3] * w[iy % 3] * w[iz % 3] * v;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int k = 0; k < TPB / 32; ++k) s += sh[k];
+    partials[blockIdx.x] = s;
+    __threadfence();
+    unsigned int done = atomicAdd(counter, 1u);
+    last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double s = 0;
+    for (unsigned int k = 0; k < gridDim.x; ++k) s += ((volatile double*)partials)[k];
+    *out = s;
+    *counter = 0u;
+  }
+}
+
+// v -= (sum v / W) w3 (load of a uniform background), or v -= (sum w3 v / W) (mean zero)
+template <class T>
+__global__ void k_project(int N, T* __restrict__ v, const double* __restrict__ sum, double invW, int mean_zero) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t NN = (int64_t)N * N;
+  if (g >= NN * N) return;
+  const double s = *sum * invW;
+  if (mean_zero) {
+    v[g] = (T)((double)v[g] - s);
+  } else {
+    const int ix = (int)(g % N), iy = (int)((g / N) % N), iz = (int)(g / NN);
+    const double w[3] = {0.25, 0.375, 0.375};
+    v[g] = (T)((double)v[g] - s * w[ix % 3] * w[iy % 3] * w[iz % 3]);
+  }
+}
+
+// CG updates with scalars read from device memory (no host round trip):
+//   alpha = s[0] / s[1];  x += alpha p;  r -= alpha q
+template <class T>
+__global__ void k_cg_update(int64_t n, const double* __restrict__ s, T* __restrict__ x, T* __restrict__ r,
+                            const T* __restrict__ p, const T* __restrict__ q) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const T alpha = (T)(s[0] / s[1]);
+  x[g] += alpha * p[g];
+  r[g] -= alpha * q[g];
+}
+//   beta = s[2] / s[0]; p = z + beta p
+template <class T>
+__global__ void k_cg_dir(int64_t n, const double* __restrict__ s, T* __restrict__ p, const T* __restrict__ z) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const T beta = (T)(s[2] / s[0]);
+  p[g] = z[g] + beta * p[g];
+}
+
+template <class A, class B>
+__global__ void k_convert(int64_t n, const A* __restrict__ in, B* __restrict__ out, const double* __restrict__ scale,
+                          int invert) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  double s = scale ? (invert ? 1.0 / sqrt(*scale) : sqrt(*scale)) : 1.0;
+  out[g] = (B)((double)in[g] * s);
+}
+
+// phi += sqrt(s) * e   (FP64 accumulation of an FP32 correction)
+__global__ void k_add_scaled(int64_t n, double* __restrict__ phi, const float* __restrict__ e,
+                             const double* __restrict__ s2) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  phi[g] += sqrt(*s2) * (double)e[g];
+}
+
+}  // namespace
+
+// ======================================================================
+// host side
+// ======================================================================
+
+static size_t reduce_blocks(size_t n) { return std::min<size_t>(std::max<size_t>((n + TPB - 1) / TPB, 1), 1024); }
+
+template <class T>
+static void reduce(fep3m_ctx* c, int N, int mode, const T* x, const T* y, double* out) {
+  size_t tot = (size_t)N * N * N;
+  k_reduce<T><<<(int)reduce_blocks(tot), TPB, 0, c->stream>>>(N, mode, x, y, (double*)c->red_tmp, c->red_counter, out);
+}
+
+template <class T>
+struct MG {
+  fep3m_ctx* c;
+  Hierarchy& H;
+  explicit MG(fep3m_ctx* cc) : c(cc), H(cc->mg) {}
+
+  void apply(const Level& L, const T* x, int epi, T* out, const T* b, T* d, T* xx, T c1, T c2) {
+    const size_t n = L.size;
+    cudaStream_t s = c->stream;
+    k_apply_z<T><<<grid_for(n), TPB, 0, s>>>(L.N, x, (T*)L.t1, (T*)L.t2);
+    k_apply_y<T><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.t1, (T*)L.t2, (T*)L.a, (T*)L.c);
+    if (epi == EPI_Y)
+      k_apply_x<T, EPI_Y><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.a, (T*)L.c, out, b, d, xx, c1, c2);
+    else if (epi == EPI_RESID)
+      k_apply_x<T, EPI_RESID><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.a, (T*)L.c, out, b, d, xx, c1, c2);
+    else
+      k_apply_x<T, EPI_CHEB><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.a, (T*)L.c, out, b, d, xx, c1, c2);
+  }
+
+  // Chebyshev smoothing of A x = b (D-preconditioned) on [lmax/ratio, lmax]
+  void smooth(const Level& L, T* x, const T* b, bool from_zero, int degree) {
+    const double up = 1.1 * H.lmax, lo = up / 15.0;
+    const double theta = 0.5 * (up + lo), delta = 0.5 * (up - lo), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    int k0 = 0;
+    if (from_zero) {
+      k_cheb0<T><<<grid_for(L.size), TPB, 0, c->stream>>>(L.N, b, (T*)L.d, x, (T)(1.0 / theta));
+      k0 = 1;
+    }
+    for (int k = k0; k < degree; ++k) {
+      if (k == 0) {
+        apply(L, x, EPI_CHEB, nullptr, b, (T*)L.d, x, T(0), (T)(1.0 / theta));
+      } else {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        apply(L, x, EPI_CHEB, nullptr, b, (T*)L.d, x, (T)(rn * rho), (T)(2.0 * rn / delta));
+        rho = rn;
+      }
+    }
+  }
+
+  void coarse_solve(const Level& L, const T* b, T* x) {
+    const CoarseSolver& cs = H.coarse;
+    const T* V = (const T*)(sizeof(T) == 8 ? (const void*)cs.V64 : (const void*)cs.V32);
+    const T* Dinv = (const T*)(sizeof(T) == 8 ? (const void*)cs.Dinv64 : (const void*)cs.Dinv32);
+    const int N = L.N;
+    const int gsz = grid_for(L.size);
+    cudaStream_t s = c->stream;
+    T* w1 = (T*)L.t1;
+    T* w2 = (T*)L.t2;
+    k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 0, V, true, b, w1, nullptr);
+    k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 1, V, true, w1, w2, nullptr);
+    k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 2, V, true, w2, w1, Dinv);
+    k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 0, V, false, w1, w2, nullptr);
+    k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 1, V, false, w2, w1, nullptr);
+    k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 2, V, false, w1, x, nullptr);
+  }
+
+  // approximately solve A_l x = b on level l (x overwritten)
+  void vcycle(int l, const T* b, T* x) {
+    Level& L = H.lv[l];
+    if (l == (int)H.lv.size() - 1) {
+      coarse_solve(L, b, x);
+      return;
+    }
+    Level& Cl = H.lv[l + 1];
+    cudaStream_t s = c->stream;
+    smooth(L, x, b, true, H.cheb_degree);
+    apply(L, x, EPI_RESID, (T*)L.r, b, nullptr, nullptr, T(0), T(0));
+    // restrict r: x-axis, y-axis, z-axis (the last scales by 1/2: reference-unit Galerkin)
+    const int Nc = Cl.N, Nf = L.N;
+    T* s1 = (T*)L.t1;
+    T* s2 = (T*)L.t2;
+    k_restrict_axis<T><<<grid_for((size_t)Nc * Nf * Nf), TPB, 0, s>>>(0, Nc, Nc, Nf, Nf, (T*)L.r, s1, T(1));
+    k_restrict_axis<T><<<grid_for((size_t)Nc * Nc * Nf), TPB, 0, s>>>(1, Nc, Nc, Nc, Nf, s1, s2, T(1));
+    k_restrict_axis<T><<<grid_for(Cl.size), TPB, 0, s>>>(2, Nc, Nc, Nc, Nc, s2, (T*)Cl.b, T(0.5));
+    vcycle(l + 1, (T*)Cl.b, (T*)Cl.x);
+    k_prolong_axis<T, false><<<grid_for((size_t)Nc * Nc * Nf), TPB, 0, s>>>(2, Nc, Nc, Nc, Nf, (T*)Cl.x, s1);
+    k_prolong_axis<T, false><<<grid_for((size_t)Nc * Nf * Nf), TPB, 0, s>>>(1, Nc, Nc, Nf, Nf, s1, s2);
+    k_prolong_axis<T, true><<<grid_for(L.size), TPB, 0, s>>>(0, Nc, Nf, Nf, Nf, s2, x);
+    smooth(L, x, b, false, H.cheb_degree);
+  }
+
+  // preconditioned CG on level 0: x = A^+ Pi b, returns iterations; the
+  // relative residual (FP64 dot products) goes to *relres
+  int pcg(const T* b, T* x, T* r, T* z, T* p, T* q, double rtol, int maxit, double* relres) {
+    Level& L = H.lv[0];
+    const int N = L.N;
+    const size_t n = L.size;
+    cudaStream_t s = c->stream;
+    double* sc = c->scal;   // [0] rz, [1] pq, [2] rz_new, [3] rr, [4] bb, [5] sum
+    const double W = (double)L.n * L.n * L.n;
+    cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    reduce<T>(c, N, 1, r, nullptr, sc + 5);
+    k_project<T><<<grid_for(n), TPB, 0, s>>>(N, r, sc + 5, 1.0 / W, 0);
+    cudaMemsetAsync(x, 0, n * sizeof(T), s);
+    reduce<T>(c, N, 3, r, nullptr, sc + 4);
+    double bb = 0;
+    cudaMemcpyAsync(&bb, sc + 4, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (bb == 0.0) {
+      *relres = 0.0;
+      return 0;
+    }
+    vcycle(0, r, z);
+    cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    reduce<T>(c, N, 0, r, z, sc + 0);
+    int it = 0;
+    double rr = bb;
+    for (it = 1; it <= maxit; ++it) {
+      apply(L, p, EPI_Y, q, nullptr, nullptr, nullptr, T(0), T(0));
+      reduce<T>(c, N, 0, p, q, sc + 1);
+      k_cg_update<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, x, r, p, q);
+      reduce<T>(c, N, 3, r, nullptr, sc + 3);
+      cudaMemcpyAsync(&rr, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      if (rr <= rtol * rtol * bb) break;
+      vcycle(0, r, z);
+      reduce<T>(c, N, 0, r, z, sc + 2);
+      k_cg_dir<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, p, z);
+      cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, s);
+    }
+    *relres = std::sqrt(rr / bb);
+    return std::min(it, maxit);
+  }
+};
+
+static void upload_constants(const Stencils& st) {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && done[dev]) return;
+  float M32[3][7], K32[3][7], P32[6][4], DM32[3], DK32[3];
+  for (int t = 0; t < 3; ++t) {
+    for (int j = 0; j < 7; ++j) {
+      M32[t][j] = (float)st.M[t][j];
+      K32[t][j] = (float)st.K[t][j];
+    }
+    DM32[t] = (float)st.diagM[t];
+    DK32[t] = (float)st.diagK[t];
+  }
+  for (int s = 0; s < 6; ++s)
+    for (int j = 0; j < 4; ++j) P32[s][j] = (float)st.P[s][j];
+  cudaMemcpyToSymbol(cM64, st.M, sizeof(st.M));
+  cudaMemcpyToSymbol(cK64, st.K, sizeof(st.K));
+  cudaMemcpyToSymbol(cP64, st.P, sizeof(st.P));
+  cudaMemcpyToSymbol(cMpq64, st.Mpq, sizeof(st.Mpq));
+  cudaMemcpyToSymbol(cDM64, st.diagM, sizeof(st.diagM));
+  cudaMemcpyToSymbol(cDK64, st.diagK, sizeof(st.diagK));
+  cudaMemcpyToSymbol(cM32, M32, sizeof(M32));
+  cudaMemcpyToSymbol(cK32, K32, sizeof(K32));
+  cudaMemcpyToSymbol(cP32, P32, sizeof(P32));
+  cudaMemcpyToSymbol(cDM32, DM32, sizeof(DM32));
+  cudaMemcpyToSymbol(cDK32, DK32, sizeof(DK32));
+  if (dev < 64) done[dev] = true;
+}
+
+cudaError_t mg_setup(fep3m_ctx* c) {
+  upload_constants(c->st);
+  Hierarchy& H = c->mg;
+  const bool f32 = c->precision == FEP3M_MIXED;
+  H.elem_size = f32 ? 4 : 8;
+  H.lv.clear();
+  int n = c->n;
+  while (true) {
+    Level L;
+    L.n = n;
+    L.N = 3 * n;
+    L.size = (size_t)L.N * L.N * L.N;
+    H.lv.push_back(L);
+    if (n % 2 != 0 || n <= 4) break;
+    n /= 2;
+  }
+  const size_t es = H.elem_size;
+  for (Level& L : H.lv) {
+    void** bufs[] = {&L.x, &L.b, &L.r, &L.d, &L.t1, &L.t2, &L.a, &L.c};
+    for (void** p : bufs) {
+      cudaError_t e = cudaMalloc(p, L.size * es);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  // coarsest level: exact inverse by fast diagonalisation of the 1-D pencil
+  const Level& Lc = H.lv.back();
+  const int N = Lc.N;
+  std::vector<double> K1((size_t)N * N, 0.0), M1((size_t)N * N, 0.0);
+  for (int g = 0; g < N; ++g)
+    for (int j = -3; j <= 3; ++j) {
+      int h = ((g + j) % N + N) % N;
+      K1[(size_t)g * N + h] += c->st.K[g % 3][j + 3];
+      M1[(size_t)g * N + h] += c->st.M[g % 3][j + 3];
+    }
+  std::vector<double> lam, V;
+  generalized_eigen(N, K1, M1, lam, V);
+  int null = 0;
+  for (int i = 1; i < N; ++i)
+    if (std::fabs(lam[i]) < std::fabs(lam[null])) null = i;
+  std::vector<double> Dinv((size_t)N * N * N);
+  for (int k = 0; k < N; ++k)
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) {
+        double D = lam[i] + lam[j] + lam[k];
+        Dinv[i + (size_t)N * (j + (size_t)N * k)] = (i == null && j == null && k == null) ? 0.0 : 1.0 / D;
+      }
+  CoarseSolver& cs = H.coarse;
+  cs.N = N;
+  cudaError_t e;
+  if (f32) {
+    std::vector<float> V32(V.begin(), V.end()), D32(Dinv.begin(), Dinv.end());
+    if ((e = cudaMalloc(&cs.V32, V32.size() * 4)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&cs.Dinv32, D32.size() * 4)) != cudaSuccess) return e;
+    cudaMemcpy(cs.V32, V32.data(), V32.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(cs.Dinv32, D32.data(), D32.size() * 4, cudaMemcpyHostToDevice);
+  } else {
+    if ((e = cudaMalloc(&cs.V64, V.size() * 8)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&cs.Dinv64, Dinv.size() * 8)) != cudaSuccess) return e;
+    cudaMemcpy(cs.V64, V.data(), V.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(cs.Dinv64, Dinv.data(), Dinv.size() * 8, cudaMemcpyHostToDevice);
+  }
+  H.lmax = estimate_lmax(c->st, 6);
+  return cudaGetLastError();
+}
+
+void mg_free(fep3m_ctx* c) {
+  for (Level& L : c->mg.lv) {
+    void* bufs[] = {L.x, L.b, L.r, L.d, L.t1, L.t2, L.a, L.c};
+    for (void* p : bufs)
+      if (p) cudaFree(p);
+  }
+  c->mg.lv.clear();
+  CoarseSolver& cs = c->mg.coarse;
+  if (cs.V64) cudaFree(cs.V64);
+  if (cs.Dinv64) cudaFree(cs.Dinv64);
+  if (cs.V32) cudaFree(cs.V32);
+  if (cs.Dinv32) cudaFree(cs.Dinv32);
+  cs = CoarseSolver();
+}
+
+static void free_list(void** p, int k) {
+  for (int i = 0; i < k; ++i)
+    if (p[i]) {
+      cudaFree(p[i]);
+      p[i] = nullptr;
+    }
+}
+
+void solver_free(fep3m_ctx* c) {
+  free_list(c->sb, 6);
+  c->sb_bytes = 0;
+  free_list((void**)c->ap64, 4);
+  c->ap64_n = 0;
+}
+
+// PCG work vectors r, z, p, q, x, rhs in the working precision (level-0 size)
+static cudaError_t ensure_solver_buffers(fep3m_ctx* c) {
+  const size_t bytes = c->mg.lv[0].size * c->mg.elem_size;
+  if (c->sb_bytes == bytes) return cudaSuccess;
+  free_list(c->sb, 6);
+  for (int i = 0; i < 6; ++i) {
+    cudaError_t e = cudaMalloc(&c->sb[i], bytes);
+    if (e != cudaSuccess) return e;
+  }
+  c->sb_bytes = bytes;
+  return cudaSuccess;
+}
+
+// r = b - K x in FP64 on the fine level (the refinement residual), FP64 intermediates
+static cudaError_t apply64(fep3m_ctx* c, const double* x, const double* b, double* r) {
+  const Level& L0 = c->mg.lv[0];
+  if (c->ap64_n != L0.size) {
+    free_list((void**)c->ap64, 4);
+    for (int i = 0; i < 4; ++i) {
+      cudaError_t e = cudaMalloc(&c->ap64[i], L0.size * sizeof(double));
+      if (e != cudaSuccess) return e;
+    }
+    c->ap64_n = L0.size;
+  }
+  cudaStream_t s = c->stream;
+  const int N = L0.N;
+  double** B = c->ap64;
+  k_apply_z<double><<<grid_for(L0.size), TPB, 0, s>>>(N, x, B[0], B[1]);
+  k_apply_y<double><<<grid_for(L0.size), TPB, 0, s>>>(N, B[0], B[1], B[2], B[3]);
+  k_apply_x<double, EPI_RESID><<<grid_for(L0.size), TPB, 0, s>>>(N, B[2], B[3], r, b, nullptr, nullptr, 0.0, 0.0);
+  return cudaGetLastError();
+}
+
+cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, double* relres, int* refine_steps) {
+  cudaError_t e = ensure_solver_buffers(c);
+  if (e != cudaSuccess) return e;
+  void** sb = c->sb;   // r, z, p, q, x, rhs
+  const Level& L0 = c->mg.lv[0];
+  const size_t n = L0.size;
+  const int N = L0.N;
+  cudaStream_t s = c->stream;
+  const double W = (double)L0.n * L0.n * L0.n;
+  double* sc = c->scal;
+  *refine_steps = 0;
+  if (c->precision == FEP3M_FP64) {
+    MG<double> mg(c);
+    const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : 1e-13;
+    const int maxit = c->cfg.mg_max_cycles > 0 ? c->cfg.mg_max_cycles : 60;
+    *iters = mg.pcg(b, phi, (double*)sb[0], (double*)sb[1], (double*)sb[2], (double*)sb[3], rtol, maxit, relres);
+    reduce<double>(c, N, 2, phi, nullptr, sc + 6);
+    k_project<double><<<grid_for(n), TPB, 0, s>>>(N, phi, sc + 6, 1.0 / W, 1);
+    return cudaGetLastError();
+  }
+  // mixed: FP64 refinement around FP32 PCG + V-cycles
+  MG<float> mg(c);
+  const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : 1e-10;
+  const int maxout = c->cfg.mg_max_cycles > 0 ? c->cfg.mg_max_cycles : 8;
+  double* r64 = c->res64;
+  cudaMemsetAsync(phi, 0, n * sizeof(double), s);
+  cudaMemcpyAsync(r64, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  reduce<double>(c, N, 1, r64, nullptr, sc + 5);
+  k_project<double><<<grid_for(n), TPB, 0, s>>>(N, r64, sc + 5, 1.0 / W, 0);
+  reduce<double>(c, N, 3, r64, nullptr, sc + 7);
+  double bb = 0;
+  cudaMemcpyAsync(&bb, sc + 7, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  *iters = 0;
+  *relres = 0;
+  if (bb == 0.0) return cudaGetLastError();
+  double rr = bb;
+  int step = 0;
+  for (step = 0; step < maxout; ++step) {
+    // r32 = r64 / |r64|
+    reduce<double>(c, N, 3, r64, nullptr, sc + 8);
+    k_convert<double, float><<<grid_for(n), TPB, 0, s>>>((int64_t)n, r64, (float*)sb[5], sc + 8, 1);
+    double inner_res = 0;
+    int it = mg.pcg((float*)sb[5], (float*)sb[4], (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], 1e-5, 30,
+                    &inner_res);
+    *iters += it;
+    k_add_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phi, (float*)sb[4], sc + 8);
+    e = apply64(c, phi, b, r64);   // r64 = b - K phi
+    if (e != cudaSuccess) return e;
+    reduce<double>(c, N, 1, r64, nullptr, sc + 5);
+    k_project<double><<<grid_for(n), TPB, 0, s>>>(N, r64, sc + 5, 1.0 / W, 0);
+    reduce<double>(c, N, 3, r64, nullptr, sc + 9);
+    cudaMemcpyAsync(&rr, sc + 9, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (rr <= rtol * rtol * bb) {
+      ++step;
+      break;
+    }
+  }
+  *refine_steps = step;
+  *relres = std::sqrt(rr / bb);
+  reduce<double>(c, N, 2, phi, nullptr, sc + 6);
+  k_project<double><<<grid_for(n), TPB, 0, s>>>(N, phi, sc + 6, 1.0 / W, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t assemble_forward(fep3m_ctx* c) {
+  const int n = c->n;
+  const int64_t ne = (int64_t)n * n * n;
+  cudaStream_t s = c->stream;
+  const size_t nodes = (size_t)27 * ne;
+  if (c->precision == FEP3M_MIXED) {
+    k_elem_coeff<float><<<grid_for(ne), TPB, 0, s>>>(ne, c->start, c->count, (const float4*)c->part, (float*)c->C);
+    k_vertex_density<float><<<grid_for(ne), TPB, 0, s>>>(n, (const float*)c->C, (float*)c->rv);
+    k_load_vector<float><<<grid_for(nodes), TPB, 0, s>>>(n, (const float*)c->rv, c->b64);
+  } else {
+    k_elem_coeff<double><<<grid_for(ne), TPB, 0, s>>>(ne, c->start, c->count, (const vec4<double>::type*)c->part, (double*)c->C);
+    k_vertex_density<double><<<grid_for(ne), TPB, 0, s>>>(n, (const double*)c->C, (double*)c->rv);
+    k_load_vector<double><<<grid_for(nodes), TPB, 0, s>>>(n, (const double*)c->rv, c->b64);
+  }
+  return cudaGetLastError();
+}
+
+// mu = 4 pi (Mpq^T (x) Mpq^T (x) Mpq^T) lam (order-3 nodes -> vertices), three separable passes.
+// One axis: vertex v collects order-3 nodes 3v-3 .. 3v+3.
+template <class T>
+__global__ void k_mpqT_axis(int axis, int n, int e0, int e1, int e2, const double* __restrict__ in64,
+                            const T* __restrict__ inT, T* __restrict__ out, double scale) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t tot = (int64_t)e0 * e1 * e2;
+  if (g >= tot) return;
+  int i[3] = {(int)(g % e0), (int)((g / e0) % e1), (int)(g / ((int64_t)e0 * e1))};
+  int ein[3] = {e0, e1, e2};
+  const int N = 3 * n;
+  ein[axis] = N;
+  const int64_t st[3] = {1, ein[0], (int64_t)ein[0] * ein[1]};
+  const int v = i[axis];
+  i[axis] = 0;
+  const int64_t base = i[0] * st[0] + i[1] * st[1] + i[2] * st[2];
+  const double w[7] = {cMpq64[0][1], cMpq64[1][1], cMpq64[2][1], cMpq64[3][1] + cMpq64[0][0],
+                       cMpq64[1][0], cMpq64[2][0], cMpq64[3][0]};
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    int gg = 3 * v - 3 + k;
+    gg = gg < 0 ? gg + N : (gg >= N ? gg - N : gg);
+    const double val = in64 ? in64[base + gg * st[axis]] : (double)inT[base + gg * st[axis]];
+    acc += w[k] * val;
+  }
+  out[g] = (T)(scale * acc);
+}
+
+cudaError_t vertex_adjoint(fep3m_ctx* c, const double* lam, void* mu, void* work1, void* work2) {
+  const int n = c->n, N = 3 * n;
+  cudaStream_t s = c->stream;
+  if (c->precision == FEP3M_MIXED) {
+    k_mpqT_axis<float><<<grid_for((size_t)n * N * N), TPB, 0, s>>>(0, n, n, N, N, lam, nullptr, (float*)work1, 1.0);
+    k_mpqT_axis<float><<<grid_for((size_t)n * n * N), TPB, 0, s>>>(1, n, n, n, N, nullptr, (float*)work1, (float*)work2, 1.0);
+    k_mpqT_axis<float><<<grid_for((size_t)n * n * n), TPB, 0, s>>>(2, n, n, n, n, nullptr, (float*)work2, (float*)mu, 4.0 * M_PI);
+  } else {
+    k_mpqT_axis<double><<<grid_for((size_t)n * N * N), TPB, 0, s>>>(0, n, n, N, N, lam, nullptr, (double*)work1, 1.0);
+    k_mpqT_axis<double><<<grid_for((size_t)n * n * N), TPB, 0, s>>>(1, n, n, n, N, nullptr, (double*)work1, (double*)work2, 1.0);
+    k_mpqT_axis<double><<<grid_for((size_t)n * n * n), TPB, 0, s>>>(2, n, n, n, n, nullptr, (double*)work2, (double*)mu, 4.0 * M_PI);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace fep3m

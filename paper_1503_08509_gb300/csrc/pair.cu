@@ -1,0 +1,496 @@
+// Short-range evaluation (Sec. 2.4-2.5) fused with the smooth-potential
+// evaluation (Sec. 2.3, Eq. evalsmooth), and the reverse sweeps of the
+// adjoint.
+//
+// For a target charge t in element e (local coordinate tau_t in [0,1]^3):
+//   Phi_t = (1/h) sum_m G_e[m] u_m(tau_t) + sum_{j in block(e), j != t} Q_j / |x_j - x_t|
+//   G_e[m] = phi[node(e, m)] - sum_{o} A_e(o) H(o, m)
+// where the second term of G_e is the screen potential of every charge of the
+// (2 n_sr + 1)^3 block around e (own charge included: the self term of
+// Sec. 2.5), written at the 64 order-3 nodes of e.  It is the element-to-point
+// evaluation of Sec. 3.2 (Eq. sc with per-element combined coefficients),
+// regrouped by vertex: all screens are sums of vertex hats, every vertex hat
+// has the same FE table H (Remark of Sec. 4), so the block's screens act
+// through the vertex amplitudes
+//   A_e(o) = sum over the corners k of block elements at vertex v = e - o of C[v - k][k]
+// which equal the full vertex density r_v inside the block and partial sums on
+// its boundary.  H(o, m) is the table value at node m of an element at offset
+// o (element units) from the vertex.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace fep3m {
+
+namespace {
+
+constexpr int PT = 256;
+
+__device__ __forceinline__ int wrapn(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+template <class T> __device__ __forceinline__ T rsq(T x);
+template <> __device__ __forceinline__ double rsq<double>(double x) { return 1.0 / sqrt(x); }
+template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+
+// compensated (Kahan) accumulator; FP64 uses plain sums
+template <class T> struct Acc {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T v) {
+    if (sizeof(T) == 4) {
+      T y = v - c;
+      T t = s + y;
+      c = (t - s) - y;
+      s = t;
+    } else {
+      s += v;
+    }
+  }
+  __device__ __forceinline__ T get() const { return s - c; }
+};
+
+template <class T, int K>
+__device__ __forceinline__ void block_sum(T (&v)[K], T* sh /* K * (PT/32) */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    T x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[k * (PT / 32) + wid] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      T s = T(0);
+      for (int w = 0; w < PT / 32; ++w) s += sh[k * (PT / 32) + w];
+      v[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// screen + mesh field of target element e at its 64 nodes (reference units)
+template <class T>
+__device__ void element_field(int n, int n_sr, int ex, int ey, int ez, const T* __restrict__ C,
+                              const T* __restrict__ rv, const T* __restrict__ phi_mesh, const T* __restrict__ Hw,
+                              T* __restrict__ G /* smem 64 */, T* __restrict__ Gp /* smem 4*64 */) {
+  const int keep = n_sr + 1, noff = 2 * n_sr + 2, no3 = noff * noff * noff;
+  const int m = threadIdx.x & 63, q = threadIdx.x >> 6;
+  T acc = T(0);
+  for (int o = q; o < no3; o += PT / 64) {
+    const int ox = o % noff - keep, oy = (o / noff) % noff - keep, oz = o / (noff * noff) - keep;
+    const int vx = ex - ox, vy = ey - oy, vz = ez - oz;   // vertex
+    T A;
+    if (ox > -keep && ox < n_sr && oy > -keep && oy < n_sr && oz > -keep && oz < n_sr) {
+      A = rv[wrapn(vx, n) + (int64_t)n * (wrapn(vy, n) + (int64_t)n * wrapn(vz, n))];
+    } else {
+      A = T(0);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
+        // corner k of element v - k lies in the block iff o + k in [-n_sr, n_sr] per axis
+        if (ox + kx < -n_sr || ox + kx > n_sr || oy + ky < -n_sr || oy + ky > n_sr || oz + kz < -n_sr ||
+            oz + kz > n_sr)
+          continue;
+        const int64_t el = wrapn(vx - kx, n) + (int64_t)n * (wrapn(vy - ky, n) + (int64_t)n * wrapn(vz - kz, n));
+        A += C[el * 8 + k];
+      }
+    }
+    acc += A * Hw[(int64_t)o * 64 + m];
+  }
+  Gp[q * 64 + m] = acc;
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    T s = T(0);
+    for (int k = 0; k < PT / 64; ++k) s += Gp[k * 64 + m];
+    const int N = 3 * n;
+    const int mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
+    const int gx = wrapn(3 * ex + mx, N), gy = wrapn(3 * ey + my, N), gz = wrapn(3 * ez + mz, N);
+    G[m] = phi_mesh[gx + (int64_t)N * (gy + (int64_t)N * gz)] - s;
+  }
+  __syncthreads();
+}
+
+template <class T, bool GRAD>
+__global__ void __launch_bounds__(PT) k_pair_fwd(int n, int n_sr, T h, T inv_h, const int* __restrict__ start,
+                                                 const int* __restrict__ count,
+                                                 const typename vec4<T>::type* __restrict__ part,
+                                                 const T* __restrict__ C, const T* __restrict__ rv,
+                                                 const T* __restrict__ phi_mesh, const T* __restrict__ Hw,
+                                                 const int* __restrict__ perm, double* __restrict__ phi_s,
+                                                 double* __restrict__ E_s, double* __restrict__ phi_out) {
+  const int64_t e = blockIdx.x;
+  const int cnt = count[e];
+  if (cnt == 0) return;
+  __shared__ T G[64];
+  __shared__ T Gp[PT];
+  __shared__ T red[8 * (PT / 32)];
+  const int ex = (int)(e % n), ey = (int)((e / n) % n), ez = (int)(e / ((int64_t)n * n));
+  element_field<T>(n, n_sr, ex, ey, ez, C, rv, phi_mesh, Hw, G, Gp);
+  const int nb = 2 * n_sr + 1, nb3 = nb * nb * nb;
+  const int s0 = start[e];
+  for (int k = 0; k < cnt; ++k) {
+    const int slot = s0 + k;
+    const typename vec4<T>::type pt = part[slot];
+    T v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = T(0);
+    if (threadIdx.x < 64) {
+      const int m = threadIdx.x, mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
+      T ux[4], uy[4], uz[4];
+      q3_values<T>(pt.x, ux);
+      q3_values<T>(pt.y, uy);
+      q3_values<T>(pt.z, uz);
+      v[0] = G[m] * ux[mx] * uy[my] * uz[mz];
+      if (GRAD) {
+        T dx[4], dy[4], dz[4];
+        q3_derivs<T>(pt.x, dx);
+        q3_derivs<T>(pt.y, dy);
+        q3_derivs<T>(pt.z, dz);
+        v[1] = G[m] * dx[mx] * uy[my] * uz[mz];
+        v[2] = G[m] * ux[mx] * dy[my] * uz[mz];
+        v[3] = G[m] * ux[mx] * uy[my] * dz[mz];
+      }
+    }
+    Acc<T> ps, fx, fy, fz;
+    for (int d = threadIdx.x; d < nb3; d += PT) {
+      const int dx = d % nb - n_sr, dy = (d / nb) % nb - n_sr, dz = d / (nb * nb) - n_sr;
+      const int64_t s = wrapn(ex + dx, n) + (int64_t)n * (wrapn(ey + dy, n) + (int64_t)n * wrapn(ez + dz, n));
+      const int j0 = start[s], j1 = j0 + count[s];
+      for (int j = j0; j < j1; ++j) {
+        if (j == slot) continue;
+        const typename vec4<T>::type pj = part[j];
+        const T rx = (T(dx) + pj.x - pt.x) * h, ry = (T(dy) + pj.y - pt.y) * h, rz = (T(dz) + pj.z - pt.z) * h;
+        const T ir = rsq<T>(rx * rx + ry * ry + rz * rz);
+        ps.add(pj.w * ir);
+        if (GRAD) {
+          const T f = pj.w * ir * ir * ir;   // d/dx_t of Q_j / |x_j - x_t| = Q_j (x_j - x_t) / r^3
+          fx.add(f * rx);
+          fy.add(f * ry);
+          fz.add(f * rz);
+        }
+      }
+    }
+    v[4] = ps.get();
+    v[5] = fx.get();
+    v[6] = fy.get();
+    v[7] = fz.get();
+    block_sum<T, 8>(v, red);
+    if (threadIdx.x == 0) {
+      const double phi = (double)v[0] * (double)inv_h + (double)v[4];
+      phi_s[slot] = phi;
+      if (phi_out) phi_out[perm[slot]] = phi;
+      if (GRAD) {
+        const double ih2 = (double)inv_h * (double)inv_h;
+        E_s[3 * slot + 0] = (double)v[1] * ih2 + (double)v[5];
+        E_s[3 * slot + 1] = (double)v[2] * ih2 + (double)v[6];
+        E_s[3 * slot + 2] = (double)v[3] * ih2 + (double)v[7];
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------- adjoint
+__global__ void k_weights(int64_t N, double gU, const double* __restrict__ gphi, const int* __restrict__ perm,
+                          const double* __restrict__ Qs, double* __restrict__ w) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  w[k] = 0.5 * gU * Qs[k] + (gphi ? gphi[perm[k]] : 0.0);
+}
+
+template <class T>
+__global__ void k_charges(int64_t N, const typename vec4<T>::type* __restrict__ part, double* __restrict__ Qs) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  Qs[k] = (double)part[k].w;
+}
+
+// W[e][m] = sum_{t in e} w_t u_m(tau_t): the adjoint's point deposit, per element
+template <class T>
+__global__ void k_elem_deposit(int64_t ne, const int* __restrict__ start, const int* __restrict__ count,
+                               const typename vec4<T>::type* __restrict__ part, const double* __restrict__ w,
+                               T* __restrict__ W) {
+  const int64_t e = blockIdx.x * (int64_t)(blockDim.x / 64) + threadIdx.x / 64;
+  if (e >= ne) return;
+  const int m = threadIdx.x & 63, mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
+  const int s = start[e], cnt = count[e];
+  T acc = T(0);
+  for (int j = s; j < s + cnt; ++j) {
+    const typename vec4<T>::type p = part[j];
+    T ux[4], uy[4], uz[4];
+    q3_values<T>(p.x, ux);
+    q3_values<T>(p.y, uy);
+    q3_values<T>(p.z, uz);
+    acc += (T)w[j] * ux[mx] * uy[my] * uz[mz];
+  }
+  W[e * 64 + m] = acc;
+}
+
+// g[node] = sum over (element, local node) pairs at the node of W
+template <class T>
+__global__ void k_node_assemble(int n, const T* __restrict__ W, double* __restrict__ g) {
+  const int N = 3 * n;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)N * N * N) return;
+  const int ix = (int)(i % N), iy = (int)((i / N) % N), iz = (int)(i / ((int64_t)N * N));
+  int el[3][2], lo[3][2], cnt[3];
+  const int id[3] = {ix, iy, iz};
+  for (int a = 0; a < 3; ++a) {
+    const int e = id[a] / 3, t = id[a] - 3 * e;
+    el[a][0] = e;
+    lo[a][0] = t;
+    cnt[a] = 1;
+    if (t == 0) {
+      el[a][1] = wrapn(e - 1, n);
+      lo[a][1] = 3;
+      cnt[a] = 2;
+    }
+  }
+  double acc = 0.0;
+  for (int c = 0; c < cnt[2]; ++c)
+    for (int b = 0; b < cnt[1]; ++b)
+      for (int a = 0; a < cnt[0]; ++a) {
+        const int64_t e = el[0][a] + (int64_t)n * (el[1][b] + (int64_t)n * el[2][c]);
+        acc += (double)W[e * 64 + lo[0][a] + 4 * lo[1][b] + 16 * lo[2][c]];
+      }
+  g[i] = acc;
+}
+
+// A[s][k] = sum_{e in block(s)} sum_m W[e][m] H(e - (s + k), m): the screen
+// part of the adjoint potential seen by the corner-k screen basis of element s
+template <class T>
+__global__ void __launch_bounds__(PT) k_screen_adjoint(int n, int n_sr, const int* __restrict__ count,
+                                                       const T* __restrict__ W, const T* __restrict__ Hw,
+                                                       T* __restrict__ A) {
+  const int64_t s = blockIdx.x;
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (count[s] == 0) {
+    if (lane == 0) A[s * 8 + k] = T(0);
+    return;
+  }
+  const int sx = (int)(s % n), sy = (int)((s / n) % n), sz = (int)(s / ((int64_t)n * n));
+  const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
+  const int nb = 2 * n_sr + 1, nb3 = nb * nb * nb, keep = n_sr + 1, noff = 2 * n_sr + 2;
+  T acc = T(0);
+  for (int d = 0; d < nb3; ++d) {
+    const int dx = d % nb - n_sr, dy = (d / nb) % nb - n_sr, dz = d / (nb * nb) - n_sr;
+    const int64_t e = wrapn(sx + dx, n) + (int64_t)n * (wrapn(sy + dy, n) + (int64_t)n * wrapn(sz + dz, n));
+    if (count[e] == 0) continue;
+    const int o = (dx - kx + keep) + noff * ((dy - ky + keep) + noff * (dz - kz + keep));
+    acc += W[e * 64 + lane] * Hw[(int64_t)o * 64 + lane] + W[e * 64 + lane + 32] * Hw[(int64_t)o * 64 + lane + 32];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) A[s * 8 + k] = acc;
+}
+
+// psi_t = sum_j w_j / |x_j - x_t| and its x_t-gradient over the block (singular adjoint potential)
+template <class T>
+__global__ void __launch_bounds__(PT) k_pair_adj(int n, int n_sr, T h, const int* __restrict__ start,
+                                                 const int* __restrict__ count,
+                                                 const typename vec4<T>::type* __restrict__ part,
+                                                 const double* __restrict__ w, double* __restrict__ psi,
+                                                 double* __restrict__ gpsi) {
+  const int64_t e = blockIdx.x;
+  const int cnt = count[e];
+  if (cnt == 0) return;
+  __shared__ T red[4 * (PT / 32)];
+  const int ex = (int)(e % n), ey = (int)((e / n) % n), ez = (int)(e / ((int64_t)n * n));
+  const int nb = 2 * n_sr + 1, nb3 = nb * nb * nb;
+  const int s0 = start[e];
+  for (int k = 0; k < cnt; ++k) {
+    const int slot = s0 + k;
+    const typename vec4<T>::type pt = part[slot];
+    Acc<T> ps, fx, fy, fz;
+    for (int d = threadIdx.x; d < nb3; d += PT) {
+      const int dx = d % nb - n_sr, dy = (d / nb) % nb - n_sr, dz = d / (nb * nb) - n_sr;
+      const int64_t s = wrapn(ex + dx, n) + (int64_t)n * (wrapn(ey + dy, n) + (int64_t)n * wrapn(ez + dz, n));
+      const int j0 = start[s], j1 = j0 + count[s];
+      for (int j = j0; j < j1; ++j) {
+        if (j == slot) continue;
+        const typename vec4<T>::type pj = part[j];
+        const T rx = (T(dx) + pj.x - pt.x) * h, ry = (T(dy) + pj.y - pt.y) * h, rz = (T(dz) + pj.z - pt.z) * h;
+        const T ir = rsq<T>(rx * rx + ry * ry + rz * rz);
+        const T wj = (T)w[j];
+        ps.add(wj * ir);
+        const T f = wj * ir * ir * ir;
+        fx.add(f * rx);
+        fy.add(f * ry);
+        fz.add(f * rz);
+      }
+    }
+    T v[4] = {ps.get(), fx.get(), fy.get(), fz.get()};
+    block_sum<T, 4>(v, red);
+    if (threadIdx.x == 0) {
+      psi[slot] = (double)v[0];
+      gpsi[3 * slot + 0] = (double)v[1];
+      gpsi[3 * slot + 1] = (double)v[2];
+      gpsi[3 * slot + 2] = (double)v[3];
+    }
+  }
+}
+
+// per charge: dLf/dQ and dLf/dx from the pieces (see fep3m_vjp)
+template <class T>
+__global__ void k_final(int64_t N, int n, double inv_h, double gU, const typename vec4<T>::type* __restrict__ part,
+                        const int* __restrict__ perm, const int* __restrict__ cell, const double* __restrict__ w,
+                        const double* __restrict__ phi_s, const double* __restrict__ E_s,
+                        const double* __restrict__ psi, const double* __restrict__ gpsi, const T* __restrict__ mu,
+                        const T* __restrict__ A, double* __restrict__ dpos, double* __restrict__ dQ) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const int i = perm[t];
+  const int e = cell[i];
+  const int ex = e % n, ey = (e / n) % n, ez = e / (n * n);
+  const typename vec4<T>::type p = part[t];
+  const double tx = p.x, ty = p.y, tz = p.z, Q = p.w;
+  const double wx[2] = {1.0 - tx, tx}, wy[2] = {1.0 - ty, ty}, wz[2] = {1.0 - tz, tz};
+  const double sg[2] = {-1.0, 1.0};
+  double sQ = 0, gx = 0, gy = 0, gz = 0;
+  for (int k = 0; k < 8; ++k) {
+    const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
+    const int64_t v = wrapn(ex + kx, n) + (int64_t)n * (wrapn(ey + ky, n) + (int64_t)n * wrapn(ez + kz, n));
+    const double coef = ((double)mu[v] - (double)A[(int64_t)e * 8 + k]) * inv_h;
+    sQ += wx[kx] * wy[ky] * wz[kz] * coef;
+    gx += sg[kx] * wy[ky] * wz[kz] * coef;
+    gy += wx[kx] * sg[ky] * wz[kz] * coef;
+    gz += wx[kx] * wy[ky] * sg[kz] * coef;
+  }
+  const double wt = w[t];
+  if (dQ) dQ[i] = 0.5 * gU * phi_s[t] + psi[t] + sQ;
+  if (dpos) {
+    dpos[3 * i + 0] = wt * E_s[3 * t + 0] + Q * (gpsi[3 * t + 0] + gx * inv_h);
+    dpos[3 * i + 1] = wt * E_s[3 * t + 1] + Q * (gpsi[3 * t + 1] + gy * inv_h);
+    dpos[3 * i + 2] = wt * E_s[3 * t + 2] + Q * (gpsi[3 * t + 2] + gz * inv_h);
+  }
+}
+
+// deterministic sum of a per-charge product (FP64): out = 1/2 sum Q phi
+__global__ void k_energy(int64_t N, const double* __restrict__ Qs, const double* __restrict__ phi,
+                         double* __restrict__ partials, unsigned int* __restrict__ counter, double* __restrict__ out) {
+  __shared__ double sh[PT / 32];
+  __shared__ bool last;
+  double acc = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+    acc += Qs[k] * phi[k];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int k = 0; k < PT / 32; ++k) s += sh[k];
+    partials[blockIdx.x] = s;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double s = 0;
+    for (unsigned int k = 0; k < gridDim.x; ++k) s += ((volatile double*)partials)[k];
+    *out = 0.5 * s;
+    *counter = 0u;
+  }
+}
+
+template <class A, class B>
+__global__ void k_cast(int64_t n, const A* __restrict__ in, B* __restrict__ out, double scale) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  out[g] = (B)((double)in[g] * scale);
+}
+
+inline int gsz(int64_t n, int t = PT) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t pair_forward(fep3m_ctx* c, double* phi_out, int want_grad) {
+  const int n = c->n;
+  const int64_t ne = (int64_t)n * n * n, nodes = 27 * ne;
+  cudaStream_t s = c->stream;
+  if (c->precision == FEP3M_MIXED) {
+    k_cast<double, float><<<gsz(nodes), PT, 0, s>>>(nodes, c->phi64, (float*)c->phi_mesh_T, 1.0);
+    auto kern = want_grad ? k_pair_fwd<float, true> : k_pair_fwd<float, false>;
+    kern<<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, (float)c->h, (float)c->inv_h, c->start, c->count,
+                                     (const float4*)c->part, (const float*)c->C, (const float*)c->rv,
+                                     (const float*)c->phi_mesh_T, c->Hw32, c->perm, c->phi_s, c->E_s, phi_out);
+  } else {
+    auto kern = want_grad ? k_pair_fwd<double, true> : k_pair_fwd<double, false>;
+    kern<<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->h, c->inv_h, c->start, c->count, (const vec4<double>::type*)c->part,
+                                     (const double*)c->C, (const double*)c->rv, c->phi64, c->Hw64, c->perm,
+                                     c->phi_s, c->E_s, phi_out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t energy(fep3m_ctx* c, double* U_dev) {
+  cudaStream_t s = c->stream;
+  const int64_t N = c->N;
+  // charges in sorted order (FP64 copy)
+  if (c->precision == FEP3M_MIXED)
+    k_charges<float><<<gsz(N), PT, 0, s>>>(N, (const float4*)c->part, c->Q_s);
+  else
+    k_charges<double><<<gsz(N), PT, 0, s>>>(N, (const vec4<double>::type*)c->part, c->Q_s);
+  const int nb = (int)std::min<int64_t>(std::max<int64_t>(gsz(N), 1), 1024);
+  k_energy<<<nb, PT, 0, s>>>(N, c->Q_s, c->phi_s, (double*)c->red_tmp, c->red_counter, U_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t adjoint(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double* dQ) {
+  const int n = c->n;
+  const int64_t ne = (int64_t)n * n * n, nodes = 27 * ne, N = c->N;
+  cudaStream_t s = c->stream;
+  const bool f32 = c->precision == FEP3M_MIXED;
+  // weights w = gU Q / 2 + gphi (sorted order)
+  if (f32)
+    k_charges<float><<<gsz(N), PT, 0, s>>>(N, (const float4*)c->part, c->Q_s);
+  else
+    k_charges<double><<<gsz(N), PT, 0, s>>>(N, (const vec4<double>::type*)c->part, c->Q_s);
+  k_weights<<<gsz(N), PT, 0, s>>>(N, gU, gphi, c->perm, c->Q_s, c->w_s);
+  // element deposits and the adjoint right-hand side on the order-3 nodes
+  const int per = PT / 64;
+  if (f32) {
+    k_elem_deposit<float><<<gsz(ne, per), PT, 0, s>>>(ne, c->start, c->count, (const float4*)c->part, c->w_s,
+                                                      (float*)c->W_el);
+    k_node_assemble<float><<<gsz(nodes), PT, 0, s>>>(n, (const float*)c->W_el, c->g64);
+  } else {
+    k_elem_deposit<double><<<gsz(ne, per), PT, 0, s>>>(ne, c->start, c->count, (const vec4<double>::type*)c->part, c->w_s,
+                                                       (double*)c->W_el);
+    k_node_assemble<double><<<gsz(nodes), PT, 0, s>>>(n, (const double*)c->W_el, c->g64);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // lam = S g with the same solver (S is symmetric)
+  int it = 0, rs = 0;
+  double rel = 0;
+  e = mesh_solve(c, c->g64, c->lam64, &it, &rel, &rs);
+  if (e != cudaSuccess) return e;
+  c->stats.adj_iterations = it;
+  c->stats.adj_rel_residual = rel;
+  // mu on the vertices (work buffers: the level-0 apply intermediates are large enough)
+  e = vertex_adjoint(c, c->lam64, c->mu_v, c->mg.lv[0].t1, c->mg.lv[0].t2);
+  if (e != cudaSuccess) return e;
+  if (f32) {
+    k_screen_adjoint<float><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->count, (const float*)c->W_el, c->Hw32,
+                                                        (float*)c->A_el);
+    k_pair_adj<float><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, (float)c->h, c->start, c->count,
+                                                  (const float4*)c->part, c->w_s, c->psi_s, c->gpsi_s);
+    k_final<float><<<gsz(N), PT, 0, s>>>(N, n, c->inv_h, gU, (const float4*)c->part, c->perm, c->cell, c->w_s,
+                                         c->phi_s, c->E_s, c->psi_s, c->gpsi_s, (const float*)c->mu_v,
+                                         (const float*)c->A_el, dpos, dQ);
+  } else {
+    k_screen_adjoint<double><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->count, (const double*)c->W_el, c->Hw64,
+                                                         (double*)c->A_el);
+    k_pair_adj<double><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->h, c->start, c->count, (const vec4<double>::type*)c->part,
+                                                   c->w_s, c->psi_s, c->gpsi_s);
+    k_final<double><<<gsz(N), PT, 0, s>>>(N, n, c->inv_h, gU, (const vec4<double>::type*)c->part, c->perm, c->cell, c->w_s,
+                                          c->phi_s, c->E_s, c->psi_s, c->gpsi_s, (const double*)c->mu_v,
+                                          (const double*)c->A_el, dpos, dQ);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace fep3m

@@ -1,0 +1,211 @@
+"""CUDA path vs the CPU oracle on the same seeded inputs, through the C ABI.
+
+Tolerances: binning bit-exact; FP64 path max|d Phi| / max|Phi| <= 1e-11;
+mixed path relative RMS (normwise) 1e-6 for Phi and 1e-5 for forces.
+"""
+import numpy as np
+import pytest
+
+from oracle import fep3m as ofe
+from oracle import tables as otab
+from paper_1503_08509_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_08509_gb300 import api as a, build
+    build.build()
+    return a
+
+
+def maxrel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def normrel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+CASES = {
+    "uniform1k": lambda: workloads.workload("uniform1k"),
+    "nacl16": lambda: dict(zip(("pos", "Q"), workloads.rock_salt(16, jitter=1e-3, seed=2)), L=1.0, n_el=16),
+    "blobs3k": lambda: dict(zip(("pos", "Q"), workloads.gaussian_blobs(3000, n_blobs=4, sigma=0.05, seed=5)),
+                            L=1.0, n_el=12),
+    "odd9": lambda: dict(zip(("pos", "Q"), workloads.uniform_pm(300, seed=13)), L=2.5, n_el=9),
+}
+
+
+_oracle_cache = {}
+
+
+def oracle(name):
+    if name not in _oracle_cache:
+        d = CASES[name]()
+        ref = ofe.forward(d["pos"], d["Q"], d["L"], d["n_el"], want_grad=True)
+        dx, dQ, _ = ofe.vjp(ref, d["Q"])
+        _oracle_cache[name] = (d, ref, dx)
+    return _oracle_cache[name]
+
+
+def run(api, d, precision, forces=True):
+    import torch
+    eng = api.FEP3M(d["L"], d["n_el"], precision=precision)
+    eng.set_particles(torch.tensor(d["pos"], device="cuda"), torch.tensor(d["Q"], device="cuda"))
+    out = eng.compute(forces=forces)
+    res = dict(phi=out["phi"].cpu().numpy(), U=out["U"], eng=eng)
+    if forces:
+        res["F"] = out["forces"].cpu().numpy()
+    return res
+
+
+def test_table_matches_oracle(api):
+    eng = api.FEP3M(1.0, 16)
+    t = eng.table().transpose(2, 1, 0)     # -> [ix, iy, iz]
+    ref = otab.kept_table(3, half_width=8, keep=4)
+    # two independent exact solvers (generalised eigen-decompositions) agree to rounding
+    assert np.abs(t - ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_binning_bit_exact(api, name):
+    d, ref, _ = oracle(name)
+    r = run(api, d, "fp64", forces=False)
+    b = r["eng"].binning()
+    ob = ref["bins"]
+    assert np.array_equal(b["perm"], ob["perm"])
+    assert np.array_equal(b["count"], ob["count"])
+    assert np.array_equal(b["cell"], ob["cell"])
+    assert np.array_equal(b["delta"], ob["delta"])      # bit-exact FP64 offsets
+
+
+def test_binning_edge_cases(api):
+    import torch
+    L, n = 2.0, 8
+    pos = np.array([[0.0, 0.0, 0.0], [2.0, 2.0, 2.0], [-2.0, -0.25, 4.25], [0.25, 0.5, 0.75],
+                    [1.9999999999999998, 1e-300, -1e-300], [0.25 - 1e-17, 0.25 + 1e-17, 1.0],
+                    [3.75, -1.75, 0.125]])
+    Q = np.array([1.0, -1.0, 1.0, -1.0, 1.0, -1.0, 0.0])
+    eng = api.FEP3M(L, n)
+    eng.set_particles(torch.tensor(pos, device="cuda"), torch.tensor(Q, device="cuda"))
+    b = eng.binning()
+    ob = ofe.bin_particles(pos, L, n)
+    assert np.array_equal(b["cell"], ob["cell"]) and np.array_equal(b["delta"], ob["delta"])
+    assert np.array_equal(b["perm"], ob["perm"]) and np.array_equal(b["count"], ob["count"])
+
+
+@pytest.mark.parametrize("name", ["uniform1k", "blobs3k"])
+def test_coefficients_and_load_vector(api, name):
+    d, ref, _ = oracle(name)
+    r = run(api, d, "fp64", forces=False)
+    m = r["eng"].mesh()
+    h = d["L"] / d["n_el"]
+    assert np.abs(m["C"] - ref["C"] * h ** 3).max() < 1e-13 * max(1.0, np.abs(ref["C"] * h ** 3).max())
+    bref = ref["b"].transpose(2, 1, 0).ravel()
+    assert np.abs(m["b"] - bref).max() < 1e-12 * np.abs(bref).max()
+    pm = ref["phi_mesh"].transpose(2, 1, 0).ravel()
+    assert maxrel(m["phi_mesh"], pm) < 1e-11
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-7)])
+def test_mesh_solve(api, precision, tol):
+    d, ref, _ = oracle("uniform1k")
+    eng = api.FEP3M(d["L"], d["n_el"], precision=precision)
+    phi = eng.solve_mesh(ref["b"].transpose(2, 1, 0).ravel())
+    pm = ref["phi_mesh"].transpose(2, 1, 0).ravel()
+    assert maxrel(phi, pm) < tol, (maxrel(phi, pm), eng.stats())
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_matches_oracle(api, name):
+    d, ref, dx = oracle(name)
+    r = run(api, d, "fp64")
+    assert maxrel(r["phi"], ref["phi"]) < 1e-11
+    assert abs(r["U"] - ref["U"]) < 1e-11 * abs(ref["U"])
+    assert maxrel(r["F"], -dx) < 1e-10
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_matches_oracle(api, name):
+    d, ref, dx = oracle(name)
+    r = run(api, d, "mixed", forces=False)
+    assert normrel(r["phi"], ref["phi"]) < 1e-6, normrel(r["phi"], ref["phi"])
+    assert abs(r["U"] - ref["U"]) < 1e-6 * abs(ref["U"])
+
+
+NACL_FP32 = pytest.mark.xfail(strict=True, reason="rock-salt forces are ~4% of the nearest-neighbour pair "
+                              "forces; the per-element field stored in FP32 limits them to ~1e-4")
+
+
+@pytest.mark.parametrize("name", [pytest.param(k, marks=NACL_FP32) if k == "nacl16" else k for k in CASES])
+def test_mixed_forces_match_oracle(api, name):
+    d, ref, dx = oracle(name)
+    r = run(api, d, "mixed")
+    assert normrel(r["F"], -dx) < 1e-5, normrel(r["F"], -dx)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_general_vjp(api, precision, tol):
+    import torch
+    d, ref, _ = oracle("uniform1k")
+    rng = np.random.default_rng(4)
+    gphi = rng.normal(size=len(d["Q"]))
+    dx, dQ, _ = ofe.vjp(ref, d["Q"], gU=0.3, gphi=gphi)
+    r = run(api, d, precision, forces=False)
+    gdx, gdQ = r["eng"].vjp(0.3, torch.tensor(gphi, device="cuda"))
+    assert normrel(gdx.cpu().numpy(), dx) < tol
+    assert normrel(gdQ.cpu().numpy(), dQ) < tol
+
+
+def test_host_buffers_match_device_buffers(api):
+    d, ref, _ = oracle("uniform1k")
+    eng = api.FEP3M(d["L"], d["n_el"])
+    eng.set_particles(d["pos"], d["Q"])             # numpy: host path
+    phi = np.empty(len(d["Q"]))
+    F = np.empty((len(d["Q"]), 3))
+    out = eng.compute(forces=True, out=dict(phi=phi, forces=F))
+    assert maxrel(phi, ref["phi"]) < 1e-11 and abs(out["U"] - ref["U"]) < 1e-11 * abs(ref["U"])
+
+
+def test_fp64_is_deterministic(api):
+    d, _, _ = oracle("blobs3k")
+    a = run(api, d, "fp64")
+    b = run(api, d, "fp64")
+    assert np.array_equal(a["phi"], b["phi"]) and np.array_equal(a["F"], b["F"]) and a["U"] == b["U"]
+
+
+def test_status_codes(api):
+    import torch
+    from paper_1503_08509_gb300 import _lib
+    eng = api.FEP3M(1.0, 8)
+    with pytest.raises(_lib.FEP3MError) as e:
+        eng.compute()
+    assert e.value.status == _lib.FEP3M_ESTATE
+    pos = torch.rand(10, 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.FEP3MError) as e:
+        eng.set_particles(pos, torch.ones(10, dtype=torch.float64, device="cuda"))
+    assert e.value.status == _lib.FEP3M_ENOTNEUTRAL
+    bad = pos.clone()
+    bad[3, 1] = float("nan")
+    with pytest.raises(_lib.FEP3MError) as e:
+        eng.set_particles(bad, torch.tensor([1.0, -1.0] * 5, dtype=torch.float64, device="cuda"))
+    assert e.value.status == _lib.FEP3M_EINVAL
+    neu = api.FEP3M(1.0, 8, neutralize=True)
+    neu.set_particles(pos, torch.ones(10, dtype=torch.float64, device="cuda"))
+    neu.compute()
+
+
+def test_autograd_function(api):
+    import torch
+    d, ref, dx = oracle("uniform1k")
+    eng = api.FEP3M(d["L"], d["n_el"])
+    pos = torch.tensor(d["pos"], device="cuda", requires_grad=True)
+    Q = torch.tensor(d["Q"], device="cuda", requires_grad=True)
+    U, phi = api.FEP3MEnergy.apply(pos, Q, eng)
+    U.backward()
+    assert maxrel(pos.grad.cpu().numpy(), dx) < 1e-10
+    assert abs(U.item() - ref["U"]) < 1e-11 * abs(ref["U"])
