@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the FE-P3M library: particles/s for Phi_i + forces.
+
+Workload: the jittered rock-salt lattice, 32^3 = 32,768 ions (+/-1 on a simple
+cubic grid of spacing L/32, each coordinate jittered by U[-1e-3, 1e-3] L,
+seed 2), on a periodic 32^3-element mesh (q = 1, p = 3, 7^3 short-range block).
+One step = set_particles (binning) + compute(Phi, U, forces) through the C ABI:
+assembly, forward multigrid solve, pair kernel, energy, adjoint solve and
+reverse sweeps.  The headline is the mixed-precision path; the FP64 path is
+timed beside it.  Inputs are far smaller than L2, so a 256 MB buffer is written
+between timed steps (L2 flush, untimed).
+
+--impl reference times the CPU oracle (the plain FP64 implementation) on the
+same workload.  With torchrun (N > 1) every rank runs an independent replica
+(the method is not sharded across GPUs in this build); rank 0 prints.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/sec for Phi_i+forces at stated RMS error vs Ewald; mixed vs FP64; % roofline"
+WORKLOAD = "nacl32"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "nacl32_sample.txt")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def load_golden():
+    U = None
+    with open(GOLDEN) as fh:
+        for line in fh:
+            if line.startswith("# U_fep3m_oracle"):
+                U = float(line.split()[-1])
+    a = np.loadtxt(GOLDEN)
+    return dict(idx=a[:, 0].astype(int), phi_e=a[:, 1], F_e=a[:, 2:5], phi_o=a[:, 5], F_o=a[:, 6:9], U_o=U)
+
+
+def rel_rms(x, ref, shift=False):
+    d = x - ref
+    if shift:
+        d = d - d.mean()       # potentials are compared up to a constant (Sec. 4)
+    return float(np.linalg.norm(d) / np.linalg.norm(ref))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def fp32_peak_tflops(n_sm, mhz):
+    # FP32 FMA: 128 lanes per SM, 2 flops per FMA
+    return n_sm * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def time_engine(eng, pos, Q, out, steps, warmup, flush, torch, host=False):
+    """Run warmup + timed steps; returns (list of ms per step, list of pair-kernel ms, launches per step)."""
+    stream = eng.stream
+    for _ in range(warmup):
+        eng.set_particles(pos, Q)
+        eng.compute(phi=True, energy=True, forces=True, out=out)
+    torch.cuda.synchronize()
+    l0 = eng.stats()["kernel_launches"]
+    ms, pair = [], []
+    for _ in range(steps):
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        eng.set_particles(pos, Q)
+        r = eng.compute(phi=True, energy=True, forces=True, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        pair.append(eng.stats()["ms_pair"])
+    launches = (eng.stats()["kernel_launches"] - l0) / steps
+    return ms, pair, launches, r
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist()
+    if ws > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_1503_08509_gb300 import api, build, workloads
+    build.build()
+    d = workloads.workload(WORKLOAD)
+    N = len(d["Q"])
+    pos = torch.tensor(d["pos"], device=dev)
+    Q = torch.tensor(d["Q"], device=dev)
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    results = {}
+    for prec in ([args.precision] + (["fp64"] if args.precision == "mixed" else [])):
+        eng = api.FEP3M(d["L"], d["n_el"], precision=prec, device=dev.index)
+        eng.set_timing(True)
+        out = dict(phi=torch.empty(N, dtype=torch.float64, device=dev),
+                   forces=torch.empty((N, 3), dtype=torch.float64, device=dev))
+        main = prec == args.precision
+        steps = args.steps if main else max(3, args.steps // 4)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else dev.index)
+        if main:
+            clocks.start()
+        ms, pair, launches, r = time_engine(eng, pos, Q, out, steps, args.warmup, flush, torch)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        ck = clocks.stop() if main else None
+        total = sum(ms)
+        if ws > 1:
+            t = torch.tensor([total], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+        st = eng.stats()
+        results[prec] = dict(ms=ms, total=total, steps=steps, pair=pair, launches=launches, stats=st, clocks=ck,
+                             phi=out["phi"].cpu().numpy(), F=out["forces"].cpu().numpy(), U=r["U"], eng=eng)
+
+    main = results[args.precision]
+    value = ws * N * main["steps"] / (main["total"] / 1e3)
+
+    # end to end through the public API with pinned host buffers (H2D inputs, D2H Phi/forces/U)
+    eng = main["eng"]
+    pos_h = torch.tensor(d["pos"]).pin_memory().numpy()
+    Q_h = torch.tensor(d["Q"]).pin_memory().numpy()
+    phi_h = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    F_h = torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
+    for _ in range(args.warmup):
+        eng.set_particles(pos_h, Q_h)
+        eng.compute(forces=True, out=dict(phi=phi_h, forces=F_h))
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eng.set_particles(pos_h, Q_h)
+        eng.compute(forces=True, out=dict(phi=phi_h, forces=F_h))
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = sum(e2e_ms)
+    if ws > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = ws * N * args.steps / (e2e_total / 1e3)
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # accuracy against the stored oracle / Ewald sample and between the two precisions
+    g = load_golden()
+    acc = {}
+    for prec, rr in results.items():
+        acc[prec] = dict(
+            phi_rel_rms_vs_ewald=rel_rms(rr["phi"][g["idx"]], g["phi_e"], shift=True),
+            force_rel_rms_vs_ewald=rel_rms(rr["F"][g["idx"]], g["F_e"]),
+            phi_rel_rms_vs_oracle=rel_rms(rr["phi"][g["idx"]], g["phi_o"]),
+            force_rel_rms_vs_oracle=rel_rms(rr["F"][g["idx"]], g["F_o"]),
+            U_rel_vs_oracle=abs(rr["U"] - g["U_o"]) / abs(g["U_o"]))
+    if "fp64" in results and args.precision == "mixed":
+        acc["mixed_vs_fp64"] = dict(phi_rel_rms=rel_rms(results["mixed"]["phi"], results["fp64"]["phi"]),
+                                    force_rel_rms=rel_rms(results["mixed"]["F"], results["fp64"]["F"]))
+
+    # roofline of the dominant hot-path kernel: the short-range pair kernel (FP32 FMA bound)
+    st = main["stats"]
+    ne_nonempty = st["nonempty_elements"]
+    pairs = st["singular_pairs"]
+    flops = ne_nonempty * 512 * 64 * 2 + N * 64 * 2 * 4 + pairs * 20
+    pair_ms = statistics.mean(main["pair"])
+    achieved = flops / (pair_ms * 1e-3) / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    roof = {"kernel": "k_pair_fwd (short-range pair + screen field + smooth evaluation)", "bound": "alu",
+            "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_note": "FP32 FMA peak derived: %d SMs x 128 lanes x 2 flops x %.0f MHz (max SM clock)"
+                         % (props.multi_processor_count, sm_max),
+            "flops_per_launch": flops, "ms_per_launch": round(pair_ms, 4)}
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(main["total"] / main["steps"], 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": "jittered rock salt 32^3 = 32768 ions (+/-1, spacing L/32, jitter 1e-3 L), "
+                               "periodic 32^3 hex mesh, q=1 (p=3), 7^3 short-range block",
+                   "precision": args.precision, "step": "set_particles + compute(Phi, U, forces)",
+                   "l2": "256 MB buffer written between timed steps (inputs < L2)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "accuracy": acc,
+        "fp64": ({"value": round(ws * N * results["fp64"]["steps"] / (results["fp64"]["total"] / 1e3), 1),
+                  "ms_per_step": round(results["fp64"]["total"] / results["fp64"]["steps"], 4)}
+                 if "fp64" in results and args.precision == "mixed" else None),
+        "stages_ms": {k: round(st[k], 4) for k in ("ms_bin", "ms_assemble", "ms_solve", "ms_pair", "ms_adjoint")},
+        "mg": {"levels": st["mg_levels"], "iterations": st["mg_iterations"], "refine_steps": st["refine_steps"],
+               "rel_residual": st["mg_rel_residual"], "adj_iterations": st["adj_iterations"]},
+        "roofline": roof,
+        "e2e": {"value": round(e2e_value, 1), "unit": "particles/s", "h2d_bytes_per_step": N * 32,
+                "d2h_bytes_per_step": N * 8 + N * 24 + 8},
+        "gpu_launches": int(round(main["launches"])),
+        "clocks": main["clocks"],
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def oracle_step(d):
+    from oracle import fep3m as ofe
+    f = ofe.forward(d["pos"], d["Q"], d["L"], d["n_el"], want_grad=True)
+    dx, _, _ = ofe.vjp(f, d["Q"])
+    return f["U"], dx
+
+
+def cpu_baseline():
+    """The CPU oracle, as it stands, on the full workload (one step: Phi, U and forces)."""
+    from oracle import tables
+    from paper_1503_08509_gb300 import workloads
+    d = workloads.workload(WORKLOAD)
+    tables.kept_table()                     # create-time table, not timed (as on the GPU)
+    t0 = time.perf_counter()
+    oracle_step(d)
+    dt = time.perf_counter() - t0
+    return {"value": round(len(d["Q"]) / dt, 1), "unit": "particles/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "full workload, one step (numpy/scipy FP64; BLAS threads = all cores)",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return
+    from oracle import tables
+    from paper_1503_08509_gb300 import workloads
+    d = workloads.workload(WORKLOAD)
+    N = len(d["Q"])
+    tables.kept_table()
+    for _ in range(min(args.warmup, 1)):
+        oracle_step(d)
+    times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        t0 = time.perf_counter()
+        oracle_step(d)
+        times.append(time.perf_counter() - t0)
+    value = N * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "particles/s",
+            "n_gpus": ws, "steps": len(times), "warmup": min(args.warmup, 1),
+            "ms_per_step": round(1e3 * sum(times) / len(times), 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "jittered rock salt 32^3 = 32768 ions, periodic 32^3 hex mesh, q=1, 7^3 block",
+                       "step": "oracle forward (Phi, U) + adjoint forces"},
+            "cpu_baseline": {"value": round(value, 1), "unit": "particles/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": "full workload per step; steps capped at 3"},
+            "e2e": {"value": round(value, 1), "unit": "particles/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -91,7 +91,10 @@ typedef struct {
   int64_t nonempty_elements;
   int max_per_element;
   double ms_bin, ms_assemble, ms_solve, ms_pair, ms_adjoint;  /* last call, if
-                               timing was enabled with fep3m_set_timing          */
+                               timing was enabled with fep3m_set_timing; ms_pair
+                               covers the short-range pair kernel launch alone   */
+  int64_t kernel_launches;  /* CUDA kernels launched by this library in this
+                               process so far (all contexts)                     */
 } fep3m_stats;
 
 /* Create a context: validates cfg, builds the FE basis-screen table (a
@@ -104,8 +107,10 @@ int fep3m_create(const fep3m_config* cfg, void* cuda_stream, fep3m_ctx** out);
 /* Charge positions (N x 3, host or device, any real values: they are wrapped
  * into [0, L)) and charges (N, host or device).  Bins the charges into
  * elements (stable counting sort) and stores the sorted SoA copy; grows the
- * context's scratch when N exceeds earlier calls.  N >= 1.  Non-finite input
- * is reported by the next fep3m_compute as FEP3M_EINVAL.                    */
+ * context's scratch when N exceeds earlier calls.  N >= 1.  Returns
+ * FEP3M_EINVAL for non-finite input and FEP3M_ENOTNEUTRAL for a net charge
+ * (unless FEP3M_NEUTRALIZE); either leaves no particles set.  Synchronises
+ * the stream.                                                                */
 int fep3m_set_particles(fep3m_ctx* ctx, int64_t N, const double* pos, const double* Q);
 
 /* Phi_i (N, host or device; may be NULL) and U (host scalar; may be NULL) for

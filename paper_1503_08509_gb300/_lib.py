@@ -23,7 +23,8 @@ class Stats(ctypes.Structure):
                 ("adj_iterations", ctypes.c_int), ("adj_rel_residual", ctypes.c_double),
                 ("singular_pairs", ctypes.c_int64), ("nonempty_elements", ctypes.c_int64),
                 ("max_per_element", ctypes.c_int), ("ms_bin", ctypes.c_double), ("ms_assemble", ctypes.c_double),
-                ("ms_solve", ctypes.c_double), ("ms_pair", ctypes.c_double), ("ms_adjoint", ctypes.c_double)]
+                ("ms_solve", ctypes.c_double), ("ms_pair", ctypes.c_double), ("ms_adjoint", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 P = ctypes.c_void_p

@@ -10,6 +10,10 @@
 
 using namespace fep3m;
 
+namespace fep3m {
+unsigned long long g_kernel_launches = 0;
+}
+
 namespace {
 
 constexpr int PT = 256;
@@ -151,6 +155,7 @@ int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad) {
   c->stats.mg_iterations = it;
   c->stats.mg_rel_residual = rel;
   c->stats.refine_steps = rs;
+  CK(pair_prepare(c));
   ev_record(c, 2);
   CK(pair_forward(c, phi_dev, want_grad));
   ev_record(c, 3);
@@ -282,15 +287,21 @@ int fep3m_set_particles(fep3m_ctx* c, int64_t N, const double* pos, const double
   ev_record(c, 6);
   CK(cudaMemsetAsync(c->iflags, 0, sizeof(int), c->stream));
   CK(bin_particles(c, dpos, dQ, c->precision == FEP3M_MIXED));
-  k_charge_sums<<<1, PT, 0, c->stream>>>(N, dQ, c->scal + 32);   // one block: writes the totals
+  FEP3M_CL k_charge_sums<<<1, PT, 0, c->stream>>>(N, dQ, c->scal + 32);   // one block: writes the totals
   ev_record(c, 7);
+  CK(pair_counts(c, (unsigned long long*)(c->scal + 48)));
   double sums[2];
+  unsigned long long cnt3[3];
   int flag = 0;
+  CK(cudaMemcpyAsync(cnt3, c->scal + 48, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(sums, c->scal + 32, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(&flag, c->iflags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->have_particles = false;
   c->have_forward = false;
+  c->stats.singular_pairs = (int64_t)cnt3[0];
+  c->stats.nonempty_elements = (int64_t)cnt3[1];
+  c->stats.max_per_element = (int)cnt3[2];
   if (flag) return FEP3M_EINVAL;
   if (!(c->cfg.flags & FEP3M_NEUTRALIZE) && std::fabs(sums[0]) > 1e-12 * sums[1]) return FEP3M_ENOTNEUTRAL;
   c->have_particles = true;
@@ -317,7 +328,7 @@ int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
     const bool fdev = is_device_ptr(force);
     double* dst = fdev ? force : c->out_tmp;
     CK(adjoint(c, 1.0, nullptr, dst, nullptr));
-    k_scale<<<gsz(3 * N), PT, 0, c->stream>>>(3 * N, dst, -1.0);
+    FEP3M_CL k_scale<<<gsz(3 * N), PT, 0, c->stream>>>(3 * N, dst, -1.0);
     CK(cudaGetLastError());
     ev_record(c, 4);
     if (!fdev) {
@@ -367,6 +378,7 @@ int fep3m_vjp(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double*
 int fep3m_get_stats(const fep3m_ctx* c, fep3m_stats* out) {
   if (!c || !out) return FEP3M_EINVAL;
   *out = c->stats;
+  out->kernel_launches = (int64_t)g_kernel_launches;
   return FEP3M_OK;
 }
 
@@ -398,9 +410,9 @@ int fep3m_get_mesh(const fep3m_ctx* cc, double* C, double* b, double* phi_mesh) 
   // staging through res64 (FP64, nodes >= 8 ne since 27 > 8)
   if (C) {
     if (c->precision == FEP3M_MIXED)
-      k_to_double<float><<<gsz(8 * ne), PT, 0, c->stream>>>(8 * ne, (const float*)c->C, c->res64, 1.0);
+      FEP3M_CL k_to_double<float><<<gsz(8 * ne), PT, 0, c->stream>>>(8 * ne, (const float*)c->C, c->res64, 1.0);
     else
-      k_to_double<double><<<gsz(8 * ne), PT, 0, c->stream>>>(8 * ne, (const double*)c->C, c->res64, 1.0);
+      FEP3M_CL k_to_double<double><<<gsz(8 * ne), PT, 0, c->stream>>>(8 * ne, (const double*)c->C, c->res64, 1.0);
     int s = deliver(c, C, c->res64, 8 * ne * 8);
     if (s != FEP3M_OK) return s;
   }
@@ -409,7 +421,7 @@ int fep3m_get_mesh(const fep3m_ctx* cc, double* C, double* b, double* phi_mesh) 
     if (s != FEP3M_OK) return s;
   }
   if (phi_mesh) {
-    k_to_double<double><<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->phi64, c->res64, c->inv_h);
+    FEP3M_CL k_to_double<double><<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->phi64, c->res64, c->inv_h);
     int s = deliver(c, phi_mesh, c->res64, nodes * 8);
     if (s != FEP3M_OK) return s;
   }
@@ -428,7 +440,7 @@ int fep3m_solve_mesh(fep3m_ctx* c, const double* b, double* phi) {
   c->stats.mg_iterations = it;
   c->stats.mg_rel_residual = rel;
   c->stats.refine_steps = rs;
-  k_to_double<double><<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->lam64, c->res64, c->inv_h);
+  FEP3M_CL k_to_double<double><<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->lam64, c->res64, c->inv_h);
   int s = deliver(c, phi, c->res64, nodes * 8);
   if (s != FEP3M_OK) return s;
   CK(cudaStreamSynchronize(c->stream));

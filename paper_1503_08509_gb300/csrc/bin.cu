@@ -169,9 +169,9 @@ __global__ void k_gather(int64_t N, const int* __restrict__ perm, const double* 
 
 static cudaError_t exclusive_scan(const int* in, int64_t n, int* out, int* tmp, cudaStream_t s) {
   int nb = (int)((n + kScanTile - 1) / kScanTile);
-  k_scan_sums<<<nb, kScanThreads, 0, s>>>(in, n, tmp);
-  k_scan_block_sums<<<1, kScanThreads, 0, s>>>(tmp, nb);
-  k_scan_final<<<nb, kScanThreads, 0, s>>>(in, n, tmp, out);
+  FEP3M_CL k_scan_sums<<<nb, kScanThreads, 0, s>>>(in, n, tmp);
+  FEP3M_CL k_scan_block_sums<<<1, kScanThreads, 0, s>>>(tmp, nb);
+  FEP3M_CL k_scan_final<<<nb, kScanThreads, 0, s>>>(in, n, tmp, out);
   return cudaGetLastError();
 }
 
@@ -184,15 +184,15 @@ cudaError_t bin_particles(fep3m_ctx* c, const double* pos, const double* Q, int 
   cudaMemsetAsync(c->fill, 0, sizeof(int) * ne, s);
   const int T = 256;
   const int gN = (int)((c->N + T - 1) / T), gE = (int)((ne + T - 1) / T);
-  k_bin<<<gN, T, 0, s>>>(pos, Q, c->N, c->L, c->n, c->h, c->inv_h, c->cell, c->delta, c->count, c->iflags);
+  FEP3M_CL k_bin<<<gN, T, 0, s>>>(pos, Q, c->N, c->L, c->n, c->h, c->inv_h, c->cell, c->delta, c->count, c->iflags);
   cudaError_t e = exclusive_scan(c->count, ne, c->start, (int*)c->scan_tmp, s);
   if (e != cudaSuccess) return e;
-  k_scatter<<<gN, T, 0, s>>>(c->cell, c->N, c->start, c->fill, c->perm);
-  k_sort_segments<<<gE, T, 0, s>>>(ne, c->start, c->count, c->perm);
+  FEP3M_CL k_scatter<<<gN, T, 0, s>>>(c->cell, c->N, c->start, c->fill, c->perm);
+  FEP3M_CL k_sort_segments<<<gE, T, 0, s>>>(ne, c->start, c->count, c->perm);
   if (use_fp32)
-    k_gather<float><<<gN, T, 0, s>>>(c->N, c->perm, c->delta, Q, c->inv_h, (float4*)c->part);
+    FEP3M_CL k_gather<float><<<gN, T, 0, s>>>(c->N, c->perm, c->delta, Q, c->inv_h, (float4*)c->part);
   else
-    k_gather<double><<<gN, T, 0, s>>>(c->N, c->perm, c->delta, Q, c->inv_h, (vec4<double>::type*)c->part);
+    FEP3M_CL k_gather<double><<<gN, T, 0, s>>>(c->N, c->perm, c->delta, Q, c->inv_h, (vec4<double>::type*)c->part);
   return cudaGetLastError();
 }
 

@@ -9,6 +9,10 @@
 
 namespace fep3m {
 
+// every kernel launch of the library is prefixed with FEP3M_CL, which counts it
+extern unsigned long long g_kernel_launches;
+#define FEP3M_CL (void)++::fep3m::g_kernel_launches,
+
 // ---------------------------------------------------------------------------
 // Order-3 equispaced Lagrange basis on [0, 1] (nodes 0, 1/3, 2/3, 1): the 1-D
 // factors of the order-p = 3 hexahedral FE basis u_m (Sec. 2.2, Eq. evalsmooth).
@@ -166,6 +170,8 @@ cudaError_t vertex_adjoint(fep3m_ctx* c, const double* lam, void* mu, void* work
 // solve K phi = b (FP64 in/out, reference units); returns iterations; writes residual in scal
 cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, double* relres,
                        int* refine_steps);
+cudaError_t pair_prepare(fep3m_ctx* c);
+cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev3);
 cudaError_t pair_forward(fep3m_ctx* c, double* phi_out, int want_grad);
 cudaError_t adjoint(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double* dQ);
 cudaError_t energy(fep3m_ctx* c, double* U_dev);

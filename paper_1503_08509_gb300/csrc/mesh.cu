@@ -401,7 +401,7 @@ static size_t reduce_blocks(size_t n) { return std::min<size_t>(std::max<size_t>
 template <class T>
 static void reduce(fep3m_ctx* c, int N, int mode, const T* x, const T* y, double* out) {
   size_t tot = (size_t)N * N * N;
-  k_reduce<T><<<(int)reduce_blocks(tot), TPB, 0, c->stream>>>(N, mode, x, y, (double*)c->red_tmp, c->red_counter, out);
+  FEP3M_CL k_reduce<T><<<(int)reduce_blocks(tot), TPB, 0, c->stream>>>(N, mode, x, y, (double*)c->red_tmp, c->red_counter, out);
 }
 
 template <class T>
@@ -413,14 +413,14 @@ struct MG {
   void apply(const Level& L, const T* x, int epi, T* out, const T* b, T* d, T* xx, T c1, T c2) {
     const size_t n = L.size;
     cudaStream_t s = c->stream;
-    k_apply_z<T><<<grid_for(n), TPB, 0, s>>>(L.N, x, (T*)L.t1, (T*)L.t2);
-    k_apply_y<T><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.t1, (T*)L.t2, (T*)L.a, (T*)L.c);
+    FEP3M_CL k_apply_z<T><<<grid_for(n), TPB, 0, s>>>(L.N, x, (T*)L.t1, (T*)L.t2);
+    FEP3M_CL k_apply_y<T><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.t1, (T*)L.t2, (T*)L.a, (T*)L.c);
     if (epi == EPI_Y)
-      k_apply_x<T, EPI_Y><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.a, (T*)L.c, out, b, d, xx, c1, c2);
+      FEP3M_CL k_apply_x<T, EPI_Y><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.a, (T*)L.c, out, b, d, xx, c1, c2);
     else if (epi == EPI_RESID)
-      k_apply_x<T, EPI_RESID><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.a, (T*)L.c, out, b, d, xx, c1, c2);
+      FEP3M_CL k_apply_x<T, EPI_RESID><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.a, (T*)L.c, out, b, d, xx, c1, c2);
     else
-      k_apply_x<T, EPI_CHEB><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.a, (T*)L.c, out, b, d, xx, c1, c2);
+      FEP3M_CL k_apply_x<T, EPI_CHEB><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.a, (T*)L.c, out, b, d, xx, c1, c2);
   }
 
   // Chebyshev smoothing of A x = b (D-preconditioned) on [lmax/ratio, lmax]
@@ -430,7 +430,7 @@ struct MG {
     double rho = 1.0 / sigma;
     int k0 = 0;
     if (from_zero) {
-      k_cheb0<T><<<grid_for(L.size), TPB, 0, c->stream>>>(L.N, b, (T*)L.d, x, (T)(1.0 / theta));
+      FEP3M_CL k_cheb0<T><<<grid_for(L.size), TPB, 0, c->stream>>>(L.N, b, (T*)L.d, x, (T)(1.0 / theta));
       k0 = 1;
     }
     for (int k = k0; k < degree; ++k) {
@@ -453,12 +453,12 @@ struct MG {
     cudaStream_t s = c->stream;
     T* w1 = (T*)L.t1;
     T* w2 = (T*)L.t2;
-    k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 0, V, true, b, w1, nullptr);
-    k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 1, V, true, w1, w2, nullptr);
-    k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 2, V, true, w2, w1, Dinv);
-    k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 0, V, false, w1, w2, nullptr);
-    k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 1, V, false, w2, w1, nullptr);
-    k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 2, V, false, w1, x, nullptr);
+    FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 0, V, true, b, w1, nullptr);
+    FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 1, V, true, w1, w2, nullptr);
+    FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 2, V, true, w2, w1, Dinv);
+    FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 0, V, false, w1, w2, nullptr);
+    FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 1, V, false, w2, w1, nullptr);
+    FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 2, V, false, w1, x, nullptr);
   }
 
   // approximately solve A_l x = b on level l (x overwritten)
@@ -476,13 +476,13 @@ struct MG {
     const int Nc = Cl.N, Nf = L.N;
     T* s1 = (T*)L.t1;
     T* s2 = (T*)L.t2;
-    k_restrict_axis<T><<<grid_for((size_t)Nc * Nf * Nf), TPB, 0, s>>>(0, Nc, Nc, Nf, Nf, (T*)L.r, s1, T(1));
-    k_restrict_axis<T><<<grid_for((size_t)Nc * Nc * Nf), TPB, 0, s>>>(1, Nc, Nc, Nc, Nf, s1, s2, T(1));
-    k_restrict_axis<T><<<grid_for(Cl.size), TPB, 0, s>>>(2, Nc, Nc, Nc, Nc, s2, (T*)Cl.b, T(0.5));
+    FEP3M_CL k_restrict_axis<T><<<grid_for((size_t)Nc * Nf * Nf), TPB, 0, s>>>(0, Nc, Nc, Nf, Nf, (T*)L.r, s1, T(1));
+    FEP3M_CL k_restrict_axis<T><<<grid_for((size_t)Nc * Nc * Nf), TPB, 0, s>>>(1, Nc, Nc, Nc, Nf, s1, s2, T(1));
+    FEP3M_CL k_restrict_axis<T><<<grid_for(Cl.size), TPB, 0, s>>>(2, Nc, Nc, Nc, Nc, s2, (T*)Cl.b, T(0.5));
     vcycle(l + 1, (T*)Cl.b, (T*)Cl.x);
-    k_prolong_axis<T, false><<<grid_for((size_t)Nc * Nc * Nf), TPB, 0, s>>>(2, Nc, Nc, Nc, Nf, (T*)Cl.x, s1);
-    k_prolong_axis<T, false><<<grid_for((size_t)Nc * Nf * Nf), TPB, 0, s>>>(1, Nc, Nc, Nf, Nf, s1, s2);
-    k_prolong_axis<T, true><<<grid_for(L.size), TPB, 0, s>>>(0, Nc, Nf, Nf, Nf, s2, x);
+    FEP3M_CL k_prolong_axis<T, false><<<grid_for((size_t)Nc * Nc * Nf), TPB, 0, s>>>(2, Nc, Nc, Nc, Nf, (T*)Cl.x, s1);
+    FEP3M_CL k_prolong_axis<T, false><<<grid_for((size_t)Nc * Nf * Nf), TPB, 0, s>>>(1, Nc, Nc, Nf, Nf, s1, s2);
+    FEP3M_CL k_prolong_axis<T, true><<<grid_for(L.size), TPB, 0, s>>>(0, Nc, Nf, Nf, Nf, s2, x);
     smooth(L, x, b, false, H.cheb_degree);
   }
 
@@ -497,7 +497,7 @@ struct MG {
     const double W = (double)L.n * L.n * L.n;
     cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
     reduce<T>(c, N, 1, r, nullptr, sc + 5);
-    k_project<T><<<grid_for(n), TPB, 0, s>>>(N, r, sc + 5, 1.0 / W, 0);
+    FEP3M_CL k_project<T><<<grid_for(n), TPB, 0, s>>>(N, r, sc + 5, 1.0 / W, 0);
     cudaMemsetAsync(x, 0, n * sizeof(T), s);
     reduce<T>(c, N, 3, r, nullptr, sc + 4);
     double bb = 0;
@@ -515,14 +515,14 @@ struct MG {
     for (it = 1; it <= maxit; ++it) {
       apply(L, p, EPI_Y, q, nullptr, nullptr, nullptr, T(0), T(0));
       reduce<T>(c, N, 0, p, q, sc + 1);
-      k_cg_update<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, x, r, p, q);
+      FEP3M_CL k_cg_update<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, x, r, p, q);
       reduce<T>(c, N, 3, r, nullptr, sc + 3);
       cudaMemcpyAsync(&rr, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s);
       cudaStreamSynchronize(s);
       if (rr <= rtol * rtol * bb) break;
       vcycle(0, r, z);
       reduce<T>(c, N, 0, r, z, sc + 2);
-      k_cg_dir<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, p, z);
+      FEP3M_CL k_cg_dir<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, p, z);
       cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, s);
     }
     *relres = std::sqrt(rr / bb);
@@ -682,9 +682,9 @@ static cudaError_t apply64(fep3m_ctx* c, const double* x, const double* b, doubl
   cudaStream_t s = c->stream;
   const int N = L0.N;
   double** B = c->ap64;
-  k_apply_z<double><<<grid_for(L0.size), TPB, 0, s>>>(N, x, B[0], B[1]);
-  k_apply_y<double><<<grid_for(L0.size), TPB, 0, s>>>(N, B[0], B[1], B[2], B[3]);
-  k_apply_x<double, EPI_RESID><<<grid_for(L0.size), TPB, 0, s>>>(N, B[2], B[3], r, b, nullptr, nullptr, 0.0, 0.0);
+  FEP3M_CL k_apply_z<double><<<grid_for(L0.size), TPB, 0, s>>>(N, x, B[0], B[1]);
+  FEP3M_CL k_apply_y<double><<<grid_for(L0.size), TPB, 0, s>>>(N, B[0], B[1], B[2], B[3]);
+  FEP3M_CL k_apply_x<double, EPI_RESID><<<grid_for(L0.size), TPB, 0, s>>>(N, B[2], B[3], r, b, nullptr, nullptr, 0.0, 0.0);
   return cudaGetLastError();
 }
 
@@ -705,7 +705,7 @@ cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, d
     const int maxit = c->cfg.mg_max_cycles > 0 ? c->cfg.mg_max_cycles : 60;
     *iters = mg.pcg(b, phi, (double*)sb[0], (double*)sb[1], (double*)sb[2], (double*)sb[3], rtol, maxit, relres);
     reduce<double>(c, N, 2, phi, nullptr, sc + 6);
-    k_project<double><<<grid_for(n), TPB, 0, s>>>(N, phi, sc + 6, 1.0 / W, 1);
+    FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, phi, sc + 6, 1.0 / W, 1);
     return cudaGetLastError();
   }
   // mixed: FP64 refinement around FP32 PCG + V-cycles
@@ -716,7 +716,7 @@ cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, d
   cudaMemsetAsync(phi, 0, n * sizeof(double), s);
   cudaMemcpyAsync(r64, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
   reduce<double>(c, N, 1, r64, nullptr, sc + 5);
-  k_project<double><<<grid_for(n), TPB, 0, s>>>(N, r64, sc + 5, 1.0 / W, 0);
+  FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, r64, sc + 5, 1.0 / W, 0);
   reduce<double>(c, N, 3, r64, nullptr, sc + 7);
   double bb = 0;
   cudaMemcpyAsync(&bb, sc + 7, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -729,16 +729,16 @@ cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, d
   for (step = 0; step < maxout; ++step) {
     // r32 = r64 / |r64|
     reduce<double>(c, N, 3, r64, nullptr, sc + 8);
-    k_convert<double, float><<<grid_for(n), TPB, 0, s>>>((int64_t)n, r64, (float*)sb[5], sc + 8, 1);
+    FEP3M_CL k_convert<double, float><<<grid_for(n), TPB, 0, s>>>((int64_t)n, r64, (float*)sb[5], sc + 8, 1);
     double inner_res = 0;
     int it = mg.pcg((float*)sb[5], (float*)sb[4], (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], 1e-5, 30,
                     &inner_res);
     *iters += it;
-    k_add_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phi, (float*)sb[4], sc + 8);
+    FEP3M_CL k_add_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phi, (float*)sb[4], sc + 8);
     e = apply64(c, phi, b, r64);   // r64 = b - K phi
     if (e != cudaSuccess) return e;
     reduce<double>(c, N, 1, r64, nullptr, sc + 5);
-    k_project<double><<<grid_for(n), TPB, 0, s>>>(N, r64, sc + 5, 1.0 / W, 0);
+    FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, r64, sc + 5, 1.0 / W, 0);
     reduce<double>(c, N, 3, r64, nullptr, sc + 9);
     cudaMemcpyAsync(&rr, sc + 9, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
@@ -750,7 +750,7 @@ cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, d
   *refine_steps = step;
   *relres = std::sqrt(rr / bb);
   reduce<double>(c, N, 2, phi, nullptr, sc + 6);
-  k_project<double><<<grid_for(n), TPB, 0, s>>>(N, phi, sc + 6, 1.0 / W, 1);
+  FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, phi, sc + 6, 1.0 / W, 1);
   return cudaGetLastError();
 }
 
@@ -760,13 +760,13 @@ cudaError_t assemble_forward(fep3m_ctx* c) {
   cudaStream_t s = c->stream;
   const size_t nodes = (size_t)27 * ne;
   if (c->precision == FEP3M_MIXED) {
-    k_elem_coeff<float><<<grid_for(ne), TPB, 0, s>>>(ne, c->start, c->count, (const float4*)c->part, (float*)c->C);
-    k_vertex_density<float><<<grid_for(ne), TPB, 0, s>>>(n, (const float*)c->C, (float*)c->rv);
-    k_load_vector<float><<<grid_for(nodes), TPB, 0, s>>>(n, (const float*)c->rv, c->b64);
+    FEP3M_CL k_elem_coeff<float><<<grid_for(ne), TPB, 0, s>>>(ne, c->start, c->count, (const float4*)c->part, (float*)c->C);
+    FEP3M_CL k_vertex_density<float><<<grid_for(ne), TPB, 0, s>>>(n, (const float*)c->C, (float*)c->rv);
+    FEP3M_CL k_load_vector<float><<<grid_for(nodes), TPB, 0, s>>>(n, (const float*)c->rv, c->b64);
   } else {
-    k_elem_coeff<double><<<grid_for(ne), TPB, 0, s>>>(ne, c->start, c->count, (const vec4<double>::type*)c->part, (double*)c->C);
-    k_vertex_density<double><<<grid_for(ne), TPB, 0, s>>>(n, (const double*)c->C, (double*)c->rv);
-    k_load_vector<double><<<grid_for(nodes), TPB, 0, s>>>(n, (const double*)c->rv, c->b64);
+    FEP3M_CL k_elem_coeff<double><<<grid_for(ne), TPB, 0, s>>>(ne, c->start, c->count, (const vec4<double>::type*)c->part, (double*)c->C);
+    FEP3M_CL k_vertex_density<double><<<grid_for(ne), TPB, 0, s>>>(n, (const double*)c->C, (double*)c->rv);
+    FEP3M_CL k_load_vector<double><<<grid_for(nodes), TPB, 0, s>>>(n, (const double*)c->rv, c->b64);
   }
   return cudaGetLastError();
 }
@@ -804,13 +804,13 @@ cudaError_t vertex_adjoint(fep3m_ctx* c, const double* lam, void* mu, void* work
   const int n = c->n, N = 3 * n;
   cudaStream_t s = c->stream;
   if (c->precision == FEP3M_MIXED) {
-    k_mpqT_axis<float><<<grid_for((size_t)n * N * N), TPB, 0, s>>>(0, n, n, N, N, lam, nullptr, (float*)work1, 1.0);
-    k_mpqT_axis<float><<<grid_for((size_t)n * n * N), TPB, 0, s>>>(1, n, n, n, N, nullptr, (float*)work1, (float*)work2, 1.0);
-    k_mpqT_axis<float><<<grid_for((size_t)n * n * n), TPB, 0, s>>>(2, n, n, n, n, nullptr, (float*)work2, (float*)mu, 4.0 * M_PI);
+    FEP3M_CL k_mpqT_axis<float><<<grid_for((size_t)n * N * N), TPB, 0, s>>>(0, n, n, N, N, lam, nullptr, (float*)work1, 1.0);
+    FEP3M_CL k_mpqT_axis<float><<<grid_for((size_t)n * n * N), TPB, 0, s>>>(1, n, n, n, N, nullptr, (float*)work1, (float*)work2, 1.0);
+    FEP3M_CL k_mpqT_axis<float><<<grid_for((size_t)n * n * n), TPB, 0, s>>>(2, n, n, n, n, nullptr, (float*)work2, (float*)mu, 4.0 * M_PI);
   } else {
-    k_mpqT_axis<double><<<grid_for((size_t)n * N * N), TPB, 0, s>>>(0, n, n, N, N, lam, nullptr, (double*)work1, 1.0);
-    k_mpqT_axis<double><<<grid_for((size_t)n * n * N), TPB, 0, s>>>(1, n, n, n, N, nullptr, (double*)work1, (double*)work2, 1.0);
-    k_mpqT_axis<double><<<grid_for((size_t)n * n * n), TPB, 0, s>>>(2, n, n, n, n, nullptr, (double*)work2, (double*)mu, 4.0 * M_PI);
+    FEP3M_CL k_mpqT_axis<double><<<grid_for((size_t)n * N * N), TPB, 0, s>>>(0, n, n, N, N, lam, nullptr, (double*)work1, 1.0);
+    FEP3M_CL k_mpqT_axis<double><<<grid_for((size_t)n * n * N), TPB, 0, s>>>(1, n, n, n, N, nullptr, (double*)work1, (double*)work2, 1.0);
+    FEP3M_CL k_mpqT_axis<double><<<grid_for((size_t)n * n * n), TPB, 0, s>>>(2, n, n, n, n, nullptr, (double*)work2, (double*)mu, 4.0 * M_PI);
   }
   return cudaGetLastError();
 }

@@ -407,19 +407,50 @@ inline int gsz(int64_t n, int t = PT) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
+// the mesh potential in the working precision of the pair kernel
+cudaError_t pair_prepare(fep3m_ctx* c) {
+  const int64_t nodes = (int64_t)27 * c->n * c->n * c->n;
+  if (c->precision == FEP3M_MIXED)
+    FEP3M_CL k_cast<double, float><<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->phi64, (float*)c->phi_mesh_T, 1.0);
+  return cudaGetLastError();
+}
+
+// ordered singular pairs, non-empty elements and the largest element population
+__global__ void k_pair_count(int n, int n_sr, const int* __restrict__ count, unsigned long long* __restrict__ out) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n * n) return;
+  const int c0 = count[e];
+  if (c0 == 0) return;
+  const int ex = (int)(e % n), ey = (int)((e / n) % n), ez = (int)(e / ((int64_t)n * n));
+  long long s = 0;
+  for (int dz = -n_sr; dz <= n_sr; ++dz)
+    for (int dy = -n_sr; dy <= n_sr; ++dy)
+      for (int dx = -n_sr; dx <= n_sr; ++dx)
+        s += count[wrapn(ex + dx, n) + (int64_t)n * (wrapn(ey + dy, n) + (int64_t)n * wrapn(ez + dz, n))];
+  atomicAdd(&out[0], (unsigned long long)((long long)c0 * s - c0));
+  atomicAdd(&out[1], 1ull);
+  atomicMax(&out[2], (unsigned long long)c0);
+}
+
+cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev3) {
+  const int64_t ne = (int64_t)c->n * c->n * c->n;
+  cudaMemsetAsync(dev3, 0, 3 * sizeof(unsigned long long), c->stream);
+  FEP3M_CL k_pair_count<<<gsz(ne), PT, 0, c->stream>>>(c->n, c->n_sr, c->count, dev3);
+  return cudaGetLastError();
+}
+
 cudaError_t pair_forward(fep3m_ctx* c, double* phi_out, int want_grad) {
   const int n = c->n;
-  const int64_t ne = (int64_t)n * n * n, nodes = 27 * ne;
+  const int64_t ne = (int64_t)n * n * n;
   cudaStream_t s = c->stream;
   if (c->precision == FEP3M_MIXED) {
-    k_cast<double, float><<<gsz(nodes), PT, 0, s>>>(nodes, c->phi64, (float*)c->phi_mesh_T, 1.0);
     auto kern = want_grad ? k_pair_fwd<float, true> : k_pair_fwd<float, false>;
-    kern<<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, (float)c->h, (float)c->inv_h, c->start, c->count,
+    FEP3M_CL kern<<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, (float)c->h, (float)c->inv_h, c->start, c->count,
                                      (const float4*)c->part, (const float*)c->C, (const float*)c->rv,
                                      (const float*)c->phi_mesh_T, c->Hw32, c->perm, c->phi_s, c->E_s, phi_out);
   } else {
     auto kern = want_grad ? k_pair_fwd<double, true> : k_pair_fwd<double, false>;
-    kern<<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->h, c->inv_h, c->start, c->count, (const vec4<double>::type*)c->part,
+    FEP3M_CL kern<<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->h, c->inv_h, c->start, c->count, (const vec4<double>::type*)c->part,
                                      (const double*)c->C, (const double*)c->rv, c->phi64, c->Hw64, c->perm,
                                      c->phi_s, c->E_s, phi_out);
   }
@@ -431,11 +462,11 @@ cudaError_t energy(fep3m_ctx* c, double* U_dev) {
   const int64_t N = c->N;
   // charges in sorted order (FP64 copy)
   if (c->precision == FEP3M_MIXED)
-    k_charges<float><<<gsz(N), PT, 0, s>>>(N, (const float4*)c->part, c->Q_s);
+    FEP3M_CL k_charges<float><<<gsz(N), PT, 0, s>>>(N, (const float4*)c->part, c->Q_s);
   else
-    k_charges<double><<<gsz(N), PT, 0, s>>>(N, (const vec4<double>::type*)c->part, c->Q_s);
+    FEP3M_CL k_charges<double><<<gsz(N), PT, 0, s>>>(N, (const vec4<double>::type*)c->part, c->Q_s);
   const int nb = (int)std::min<int64_t>(std::max<int64_t>(gsz(N), 1), 1024);
-  k_energy<<<nb, PT, 0, s>>>(N, c->Q_s, c->phi_s, (double*)c->red_tmp, c->red_counter, U_dev);
+  FEP3M_CL k_energy<<<nb, PT, 0, s>>>(N, c->Q_s, c->phi_s, (double*)c->red_tmp, c->red_counter, U_dev);
   return cudaGetLastError();
 }
 
@@ -446,20 +477,20 @@ cudaError_t adjoint(fep3m_ctx* c, double gU, const double* gphi, double* dpos, d
   const bool f32 = c->precision == FEP3M_MIXED;
   // weights w = gU Q / 2 + gphi (sorted order)
   if (f32)
-    k_charges<float><<<gsz(N), PT, 0, s>>>(N, (const float4*)c->part, c->Q_s);
+    FEP3M_CL k_charges<float><<<gsz(N), PT, 0, s>>>(N, (const float4*)c->part, c->Q_s);
   else
-    k_charges<double><<<gsz(N), PT, 0, s>>>(N, (const vec4<double>::type*)c->part, c->Q_s);
-  k_weights<<<gsz(N), PT, 0, s>>>(N, gU, gphi, c->perm, c->Q_s, c->w_s);
+    FEP3M_CL k_charges<double><<<gsz(N), PT, 0, s>>>(N, (const vec4<double>::type*)c->part, c->Q_s);
+  FEP3M_CL k_weights<<<gsz(N), PT, 0, s>>>(N, gU, gphi, c->perm, c->Q_s, c->w_s);
   // element deposits and the adjoint right-hand side on the order-3 nodes
   const int per = PT / 64;
   if (f32) {
-    k_elem_deposit<float><<<gsz(ne, per), PT, 0, s>>>(ne, c->start, c->count, (const float4*)c->part, c->w_s,
+    FEP3M_CL k_elem_deposit<float><<<gsz(ne, per), PT, 0, s>>>(ne, c->start, c->count, (const float4*)c->part, c->w_s,
                                                       (float*)c->W_el);
-    k_node_assemble<float><<<gsz(nodes), PT, 0, s>>>(n, (const float*)c->W_el, c->g64);
+    FEP3M_CL k_node_assemble<float><<<gsz(nodes), PT, 0, s>>>(n, (const float*)c->W_el, c->g64);
   } else {
-    k_elem_deposit<double><<<gsz(ne, per), PT, 0, s>>>(ne, c->start, c->count, (const vec4<double>::type*)c->part, c->w_s,
+    FEP3M_CL k_elem_deposit<double><<<gsz(ne, per), PT, 0, s>>>(ne, c->start, c->count, (const vec4<double>::type*)c->part, c->w_s,
                                                        (double*)c->W_el);
-    k_node_assemble<double><<<gsz(nodes), PT, 0, s>>>(n, (const double*)c->W_el, c->g64);
+    FEP3M_CL k_node_assemble<double><<<gsz(nodes), PT, 0, s>>>(n, (const double*)c->W_el, c->g64);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -474,19 +505,19 @@ cudaError_t adjoint(fep3m_ctx* c, double gU, const double* gphi, double* dpos, d
   e = vertex_adjoint(c, c->lam64, c->mu_v, c->mg.lv[0].t1, c->mg.lv[0].t2);
   if (e != cudaSuccess) return e;
   if (f32) {
-    k_screen_adjoint<float><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->count, (const float*)c->W_el, c->Hw32,
+    FEP3M_CL k_screen_adjoint<float><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->count, (const float*)c->W_el, c->Hw32,
                                                         (float*)c->A_el);
-    k_pair_adj<float><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, (float)c->h, c->start, c->count,
+    FEP3M_CL k_pair_adj<float><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, (float)c->h, c->start, c->count,
                                                   (const float4*)c->part, c->w_s, c->psi_s, c->gpsi_s);
-    k_final<float><<<gsz(N), PT, 0, s>>>(N, n, c->inv_h, gU, (const float4*)c->part, c->perm, c->cell, c->w_s,
+    FEP3M_CL k_final<float><<<gsz(N), PT, 0, s>>>(N, n, c->inv_h, gU, (const float4*)c->part, c->perm, c->cell, c->w_s,
                                          c->phi_s, c->E_s, c->psi_s, c->gpsi_s, (const float*)c->mu_v,
                                          (const float*)c->A_el, dpos, dQ);
   } else {
-    k_screen_adjoint<double><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->count, (const double*)c->W_el, c->Hw64,
+    FEP3M_CL k_screen_adjoint<double><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->count, (const double*)c->W_el, c->Hw64,
                                                          (double*)c->A_el);
-    k_pair_adj<double><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->h, c->start, c->count, (const vec4<double>::type*)c->part,
+    FEP3M_CL k_pair_adj<double><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->h, c->start, c->count, (const vec4<double>::type*)c->part,
                                                    c->w_s, c->psi_s, c->gpsi_s);
-    k_final<double><<<gsz(N), PT, 0, s>>>(N, n, c->inv_h, gU, (const vec4<double>::type*)c->part, c->perm, c->cell, c->w_s,
+    FEP3M_CL k_final<double><<<gsz(N), PT, 0, s>>>(N, n, c->inv_h, gU, (const vec4<double>::type*)c->part, c->perm, c->cell, c->w_s,
                                           c->phi_s, c->E_s, c->psi_s, c->gpsi_s, (const double*)c->mu_v,
                                           (const double*)c->A_el, dpos, dQ);
   }
