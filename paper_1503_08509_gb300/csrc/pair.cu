@@ -8,7 +8,7 @@
 // where the second term of G_e is the screen potential of every charge of the
 // (2 n_sr + 1)^3 block around e (own charge included: the self term of
 // Sec. 2.5), written at the 64 order-3 nodes of e.  It is the element-to-point
-// evaluation of Sec. 3.2 (Eq. sc with per-element combined coefficients),
+// evaluation of Sec. 3.1.2 (Eq. sc with per-element combined coefficients),
 // regrouped by vertex: all screens are sums of vertex hats, every vertex hat
 // has the same FE table H (Remark of Sec. 4), so the block's screens act
 // through the vertex amplitudes
