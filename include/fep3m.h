@@ -162,6 +162,27 @@ int fep3m_solve_mesh(fep3m_ctx* ctx, const double* b, double* phi);
  * s = 6 n_sr + 7.                                                            */
 int fep3m_get_table(const fep3m_ctx* ctx, double* table);
 
+/* Load vector without any allocation (the paper has no counterpart; this is a
+ * service for callers that cannot allocate device memory: work issued while a
+ * stream is being captured into a CUDA graph, applications whose memory
+ * manager owns the whole device, loops that cannot afford cudaMalloc's
+ * implicit synchronisation).  Computes the same b as fep3m_get_mesh after a
+ * compute: b = 4 pi (Mpq (x) Mpq (x) Mpq) r, r the order-1 vertex density of
+ * the charges' screens, index ix + 3n iy + 9n^2 iz, without the neutrality
+ * projection.  pos (N x 3), Q (N) and b ((3 n_el)^3) must be device pointers
+ * on the current device; cuda_stream is a cudaStream_t (NULL = default).
+ * Scratch is a file-scope device array of FEP3M_STATIC_MAX_NEL^3 doubles
+ * (2 MiB) held by every GPU that loads the library until the process exits;
+ * n_el > FEP3M_STATIC_MAX_NEL returns FEP3M_EINVAL.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), so make
+ * the first call on each device before any stream capture.  Every call
+ * clears and reuses the same array: calls that overlap on the GPU (other
+ * streams, other host threads) race and give wrong results.  Accumulation
+ * uses atomics, so b may differ from the context path in the last bits.     */
+#define FEP3M_STATIC_MAX_NEL 64
+int fep3m_load_vector_static(double L, int n_el, int64_t N, const double* pos, const double* Q, double* b,
+                             void* cuda_stream);
+
 const char* fep3m_strerror(int status);
 
 /* Release the context and all of its device memory.  NULL is a no-op.      */
