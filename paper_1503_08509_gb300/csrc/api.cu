@@ -89,12 +89,12 @@ __global__ void k_charge_sums(int64_t N, const double* Q, double* out /* [0] sum
 inline int gsz(int64_t n) { return (int)((n + PT - 1) / PT); }
 
 void free_particles(fep3m_ctx* c) {
-  void* p[] = {c->pos_in, c->Q_in, c->cell, c->delta, c->perm, c->part, c->phi_s, c->E_s, c->w_s,
+  void* p[] = {c->pos_in, c->Q_in, c->cell, c->delta, c->perm, c->ecoord, c->part, c->phi_s, c->E_s, c->w_s,
                c->psi_s, c->gpsi_s, c->out_tmp, c->Q_s, c->gphi_dev};
   for (void* q : p) dfree(q);
   c->pos_in = c->Q_in = c->delta = c->phi_s = c->E_s = c->w_s = c->psi_s = c->gpsi_s = c->out_tmp = c->Q_s =
       c->gphi_dev = nullptr;
-  c->cell = c->perm = nullptr;
+  c->cell = c->perm = c->ecoord = nullptr;
   c->part = nullptr;
   c->cap = 0;
 }
@@ -108,6 +108,7 @@ int grow_particles(fep3m_ctx* c, int64_t N) {
   CK(dalloc(&c->cell, N));
   CK(dalloc(&c->delta, 3 * N));
   CK(dalloc(&c->perm, N));
+  CK(dalloc(&c->ecoord, N));
   CK(cudaMalloc(&c->part, N * es));
   CK(dalloc(&c->phi_s, N));
   CK(dalloc(&c->E_s, 3 * N));
@@ -190,6 +191,7 @@ void fep3m_destroy(fep3m_ctx* c) {
                c->res64, c->g64, c->lam64, c->scal, c->iflags, c->phi_mesh_T, c->W_el, c->A_el, c->mu_v,
                c->red_tmp, c->red_counter};
   for (void* q : p) dfree(q);
+  solver_plan_free(c);
   mg_free(c);
   solver_free(c);
   if (c->ev_init)

@@ -104,6 +104,7 @@ struct fep3m_ctx {
   int* cell = nullptr;           // N
   double* delta = nullptr;       // N*3 original order
   int* perm = nullptr;           // N
+  int* ecoord = nullptr;         // N sorted: element coords ex | ey << 10 | ez << 20
   int* count = nullptr;          // n^3
   int* start = nullptr;          // n^3 + 1
   int* fill = nullptr;           // n^3
@@ -139,6 +140,13 @@ struct fep3m_ctx {
   size_t sb_bytes = 0;
   double* ap64[4] = {};          // FP64 fine-level apply intermediates (refinement residual)
   size_t ap64_n = 0;
+  // replayed solve: iteration counts calibrated on the first solve, captured as a graph
+  int plan_k = 0, plan_kin = 0, plan_kout = 0;
+  cudaGraphExec_t solve_exec = nullptr;
+  int solve_graph_kernels = 0;
+  cudaStream_t cap_stream = nullptr;
+  double* in64 = nullptr;        // solver input / output (fixed addresses for the graph)
+  double* out64 = nullptr;
   double* red_tmp = nullptr;     // reduction partials (1024)
   unsigned int* red_counter = nullptr;
   double* out_tmp = nullptr;     // N*3 staging for host outputs
@@ -164,6 +172,7 @@ cudaError_t assemble_forward(fep3m_ctx* c);
 cudaError_t mg_setup(fep3m_ctx* c);
 void mg_free(fep3m_ctx* c);
 void solver_free(fep3m_ctx* c);
+void solver_plan_free(fep3m_ctx* c);
 size_t scan_tmp_bytes(int64_t n);
 // mu = 4 pi (Mpq^T)^(x)3 lam on the vertex grid (working precision); work1/2 sized n*(3n)^2
 cudaError_t vertex_adjoint(fep3m_ctx* c, const double* lam, void* mu, void* work1, void* work2);

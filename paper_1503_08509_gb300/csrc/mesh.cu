@@ -328,12 +328,20 @@ __global__ void k_reduce(int N, int mode, const T* __restrict__ x, const T* __re
     last = (done == gridDim.x - 1);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
+  if (last) {
+    // the last block adds the partials in a fixed order (deterministic)
     __threadfence();
     double s = 0;
-    for (unsigned int k = 0; k < gridDim.x; ++k) s += ((volatile double*)partials)[k];
-    *out = s;
-    *counter = 0u;
+    for (unsigned int k = threadIdx.x; k < gridDim.x; k += blockDim.x) s += ((volatile double*)partials)[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int k = 0; k < TPB / 32; ++k) t += sh[k];
+      *out = t;
+      *counter = 0u;
+    }
   }
 }
 
@@ -360,7 +368,7 @@ __global__ void k_cg_update(int64_t n, const double* __restrict__ s, T* __restri
                             const T* __restrict__ p, const T* __restrict__ q) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
-  const T alpha = (T)(s[0] / s[1]);
+  const T alpha = s[1] != 0.0 ? (T)(s[0] / s[1]) : T(0);
   x[g] += alpha * p[g];
   r[g] -= alpha * q[g];
 }
@@ -369,7 +377,7 @@ template <class T>
 __global__ void k_cg_dir(int64_t n, const double* __restrict__ s, T* __restrict__ p, const T* __restrict__ z) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
-  const T beta = (T)(s[2] / s[0]);
+  const T beta = s[0] != 0.0 ? (T)(s[2] / s[0]) : T(0);
   p[g] = z[g] + beta * p[g];
 }
 
@@ -378,7 +386,7 @@ __global__ void k_convert(int64_t n, const A* __restrict__ in, B* __restrict__ o
                           int invert) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
-  double s = scale ? (invert ? 1.0 / sqrt(*scale) : sqrt(*scale)) : 1.0;
+  double s = scale ? (invert ? (*scale > 0.0 ? 1.0 / sqrt(*scale) : 0.0) : sqrt(*scale)) : 1.0;
   out[g] = (B)((double)in[g] * s);
 }
 
@@ -396,7 +404,7 @@ __global__ void k_add_scaled(int64_t n, double* __restrict__ phi, const float* _
 // host side
 // ======================================================================
 
-static size_t reduce_blocks(size_t n) { return std::min<size_t>(std::max<size_t>((n + TPB - 1) / TPB, 1), 1024); }
+static size_t reduce_blocks(size_t n) { return std::min<size_t>(std::max<size_t>((n + 4 * TPB - 1) / (4 * TPB), 1), 608); }
 
 template <class T>
 static void reduce(fep3m_ctx* c, int N, int mode, const T* x, const T* y, double* out) {
@@ -527,6 +535,36 @@ struct MG {
     }
     *relres = std::sqrt(rr / bb);
     return std::min(it, maxit);
+  }
+
+  // the same iteration with a fixed count and no host round trip (graph-capturable);
+  // leaves |Pi b|^2 in scal[4] and the final |r|^2 in scal[3]
+  void pcg_fixed(const T* b, T* x, T* r, T* z, T* p, T* q, int k) {
+    Level& L = H.lv[0];
+    const int N = L.N;
+    const size_t n = L.size;
+    cudaStream_t s = c->stream;
+    double* sc = c->scal;
+    const double W = (double)L.n * L.n * L.n;
+    cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    reduce<T>(c, N, 1, r, nullptr, sc + 5);
+    FEP3M_CL k_project<T><<<grid_for(n), TPB, 0, s>>>(N, r, sc + 5, 1.0 / W, 0);
+    cudaMemsetAsync(x, 0, n * sizeof(T), s);
+    reduce<T>(c, N, 3, r, nullptr, sc + 4);
+    vcycle(0, r, z);
+    cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    reduce<T>(c, N, 0, r, z, sc + 0);
+    for (int it = 1; it <= k; ++it) {
+      apply(L, p, EPI_Y, q, nullptr, nullptr, nullptr, T(0), T(0));
+      reduce<T>(c, N, 0, p, q, sc + 1);
+      FEP3M_CL k_cg_update<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, x, r, p, q);
+      reduce<T>(c, N, 3, r, nullptr, sc + 3);
+      if (it == k) break;
+      vcycle(0, r, z);
+      reduce<T>(c, N, 0, r, z, sc + 2);
+      FEP3M_CL k_cg_dir<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, p, z);
+      cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, s);
+    }
   }
 };
 
@@ -688,9 +726,10 @@ static cudaError_t apply64(fep3m_ctx* c, const double* x, const double* b, doubl
   return cudaGetLastError();
 }
 
-cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, double* relres, int* refine_steps) {
-  cudaError_t e = ensure_solver_buffers(c);
-  if (e != cudaSuccess) return e;
+// host-checked solve (used once to calibrate the iteration counts, and as the
+// fallback when a replayed solve misses its tolerance)
+static cudaError_t solve_checked(fep3m_ctx* c, const double* b, double* phi, int* iters, double* relres,
+                                 int* refine_steps, int* k_inner_max) {
   void** sb = c->sb;   // r, z, p, q, x, rhs
   const Level& L0 = c->mg.lv[0];
   const size_t n = L0.size;
@@ -699,6 +738,7 @@ cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, d
   const double W = (double)L0.n * L0.n * L0.n;
   double* sc = c->scal;
   *refine_steps = 0;
+  *k_inner_max = 0;
   if (c->precision == FEP3M_FP64) {
     MG<double> mg(c);
     const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : 1e-13;
@@ -708,7 +748,6 @@ cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, d
     FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, phi, sc + 6, 1.0 / W, 1);
     return cudaGetLastError();
   }
-  // mixed: FP64 refinement around FP32 PCG + V-cycles
   MG<float> mg(c);
   const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : 1e-10;
   const int maxout = c->cfg.mg_max_cycles > 0 ? c->cfg.mg_max_cycles : 8;
@@ -727,15 +766,15 @@ cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, d
   double rr = bb;
   int step = 0;
   for (step = 0; step < maxout; ++step) {
-    // r32 = r64 / |r64|
     reduce<double>(c, N, 3, r64, nullptr, sc + 8);
     FEP3M_CL k_convert<double, float><<<grid_for(n), TPB, 0, s>>>((int64_t)n, r64, (float*)sb[5], sc + 8, 1);
     double inner_res = 0;
     int it = mg.pcg((float*)sb[5], (float*)sb[4], (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], 1e-5, 30,
                     &inner_res);
     *iters += it;
+    *k_inner_max = std::max(*k_inner_max, it);
     FEP3M_CL k_add_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phi, (float*)sb[4], sc + 8);
-    e = apply64(c, phi, b, r64);   // r64 = b - K phi
+    cudaError_t e = apply64(c, phi, b, r64);   // r64 = b - K phi
     if (e != cudaSuccess) return e;
     reduce<double>(c, N, 1, r64, nullptr, sc + 5);
     FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, r64, sc + 5, 1.0 / W, 0);
@@ -752,6 +791,142 @@ cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, d
   reduce<double>(c, N, 2, phi, nullptr, sc + 6);
   FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, phi, sc + 6, 1.0 / W, 1);
   return cudaGetLastError();
+}
+
+// fixed-count solve from c->in64 into c->out64, no host round trip; leaves
+// |Pi b|^2 in scal[10] and the final residual |r|^2 in scal[11]
+static cudaError_t solve_fixed(fep3m_ctx* c) {
+  void** sb = c->sb;
+  const Level& L0 = c->mg.lv[0];
+  const size_t n = L0.size;
+  const int N = L0.N;
+  cudaStream_t s = c->stream;
+  const double W = (double)L0.n * L0.n * L0.n;
+  double* sc = c->scal;
+  if (c->precision == FEP3M_FP64) {
+    MG<double> mg(c);
+    mg.pcg_fixed(c->in64, c->out64, (double*)sb[0], (double*)sb[1], (double*)sb[2], (double*)sb[3], c->plan_k);
+    cudaMemcpyAsync(sc + 10, sc + 4, sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(sc + 11, sc + 3, sizeof(double), cudaMemcpyDeviceToDevice, s);
+    reduce<double>(c, N, 2, c->out64, nullptr, sc + 6);
+    FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, c->out64, sc + 6, 1.0 / W, 1);
+    return cudaGetLastError();
+  }
+  MG<float> mg(c);
+  double* r64 = c->res64;
+  double* phi = c->out64;
+  cudaMemsetAsync(phi, 0, n * sizeof(double), s);
+  cudaMemcpyAsync(r64, c->in64, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  reduce<double>(c, N, 1, r64, nullptr, sc + 5);
+  FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, r64, sc + 5, 1.0 / W, 0);
+  reduce<double>(c, N, 3, r64, nullptr, sc + 10);
+  for (int step = 0; step < c->plan_kout; ++step) {
+    reduce<double>(c, N, 3, r64, nullptr, sc + 8);
+    FEP3M_CL k_convert<double, float><<<grid_for(n), TPB, 0, s>>>((int64_t)n, r64, (float*)sb[5], sc + 8, 1);
+    mg.pcg_fixed((float*)sb[5], (float*)sb[4], (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3],
+                 c->plan_kin);
+    FEP3M_CL k_add_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phi, (float*)sb[4], sc + 8);
+    cudaError_t e = apply64(c, phi, c->in64, r64);
+    if (e != cudaSuccess) return e;
+    reduce<double>(c, N, 1, r64, nullptr, sc + 5);
+    FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, r64, sc + 5, 1.0 / W, 0);
+  }
+  reduce<double>(c, N, 3, r64, nullptr, sc + 11);
+  reduce<double>(c, N, 2, phi, nullptr, sc + 6);
+  FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, phi, sc + 6, 1.0 / W, 1);
+  return cudaGetLastError();
+}
+
+static void destroy_plan(fep3m_ctx* c) {
+  if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+  c->solve_exec = nullptr;
+  c->solve_graph_kernels = 0;
+}
+
+// capture solve_fixed into a graph on the library's private stream
+static cudaError_t build_plan(fep3m_ctx* c) {
+  destroy_plan(c);
+  cudaStream_t user = c->stream;
+  const unsigned long long l0 = g_kernel_launches;
+  c->stream = c->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = solve_fixed(c);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e == cudaSuccess) e = e1;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->solve_exec, g, 0);
+    if (g) {
+      size_t nn = 0;
+      cudaGraphGetNodes(g, nullptr, &nn);
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+      int kn = 0;
+      for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kn;
+      }
+      c->solve_graph_kernels = kn;
+      cudaGraphDestroy(g);
+    }
+  }
+  c->stream = user;
+  g_kernel_launches = l0;   // captured launches run when the graph is replayed
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    destroy_plan(c);
+  }
+  return e;
+}
+
+cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, double* relres, int* refine_steps) {
+  cudaError_t e = ensure_solver_buffers(c);
+  if (e != cudaSuccess) return e;
+  const size_t n = c->mg.lv[0].size;
+  const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : (c->precision == FEP3M_FP64 ? 1e-13 : 1e-10);
+  if (c->solve_exec) {
+    cudaStream_t s = c->stream;
+    cudaMemcpyAsync(c->in64, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if ((e = cudaGraphLaunch(c->solve_exec, s)) != cudaSuccess) return e;
+    g_kernel_launches += c->solve_graph_kernels;
+    cudaMemcpyAsync(phi, c->out64, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    double bb_rr[2];
+    cudaMemcpyAsync(bb_rr, c->scal + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    const double rel = bb_rr[0] > 0 ? std::sqrt(bb_rr[1] / bb_rr[0]) : 0.0;
+    if (rel <= rtol) {
+      *relres = rel;
+      *iters = c->precision == FEP3M_FP64 ? c->plan_k : c->plan_kin * c->plan_kout;
+      *refine_steps = c->precision == FEP3M_FP64 ? 0 : c->plan_kout;
+      return cudaSuccess;
+    }
+    destroy_plan(c);   // this right-hand side needs more iterations: recalibrate below
+  }
+  int kin = 0;
+  e = solve_checked(c, b, phi, iters, relres, refine_steps, &kin);
+  if (e != cudaSuccess || *relres > rtol) return e;
+  // forward and adjoint solves share the plan: keep the larger counts
+  if (c->precision == FEP3M_FP64) {
+    c->plan_k = std::max(c->plan_k, *iters + 1);
+  } else {
+    c->plan_kin = std::max(c->plan_kin, kin);
+    c->plan_kout = std::max(c->plan_kout, *refine_steps + 1);
+  }
+  if (!c->in64 && (e = cudaMalloc(&c->in64, n * sizeof(double))) != cudaSuccess) return e;
+  if (!c->out64 && (e = cudaMalloc(&c->out64, n * sizeof(double))) != cudaSuccess) return e;
+  if (!c->cap_stream && (e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return e;
+  if (build_plan(c) != cudaSuccess) (void)cudaGetLastError();   // keep the checked path if capture fails
+  return cudaSuccess;
+}
+
+void solver_plan_free(fep3m_ctx* c) {
+  destroy_plan(c);
+  if (c->in64) cudaFree(c->in64);
+  if (c->out64) cudaFree(c->out64);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->in64 = c->out64 = nullptr;
+  c->cap_stream = nullptr;
 }
 
 cudaError_t assemble_forward(fep3m_ctx* c) {

@@ -194,6 +194,302 @@ __global__ void __launch_bounds__(PT) k_pair_fwd(int n, int n_sr, T h, T inv_h, 
   }
 }
 
+// ------------------------------------------------------------------- v2
+// One CTA per brick of BX x BY x BZ target elements.
+//  (1) stage the brick's vertex densities and the element coefficients of its
+//      short-range halo in shared memory;
+//  (2) accumulate the screen field of all brick elements at their 64 nodes,
+//      G[e][m] = sum_o A(e, o) H(o, m), as 512 rank-1 updates of a 64 x 64
+//      tile (4 x 4 register tile per thread), staging A and H in chunks of 32
+//      offsets; add the mesh potential;
+//  (3) one warp per target charge: evaluate sum_m G u_m and its gradient, and
+//      the singular sum over the 49 contiguous element rows of its block.
+constexpr int BX = 4, BY = 4, BZ = 4, BE = BX * BY * BZ;   // 64 elements per brick
+constexpr int OCH = 32;                                      // offsets per chunk
+constexpr int MAXRUN = 2 * 81;                               // rows of the block (n_sr <= 4), 2 runs each
+
+struct BrickGeom {
+  int n, n_sr, keep, noff;
+  int E0x, E0y, E0z;        // brick origin (element coords)
+  int VW;                   // vertex tile width: BX + 2 n_sr + 1
+  int CW;                   // element tile width: BX + 2 n_sr
+};
+
+template <class T>
+struct PairSmem {
+  // sizes in elements of T, laid out in one dynamic buffer
+  static size_t bytes(int n_sr) {
+    const int VW = BX + 2 * n_sr + 1, CW = BX + 2 * n_sr;
+    size_t t = (size_t)VW * VW * VW + (size_t)CW * CW * CW * 8 + 2 * (size_t)OCH * 64;   // r, C, A chunk, H chunk
+    size_t ints = (BE + 1) + 8 * 2 * MAXRUN + 8 * (MAXRUN + 1);
+    return t * sizeof(T) + ints * sizeof(int) + 64;
+  }
+};
+
+// source weights of the singular sum: the charge itself, or an adjoint weight array
+template <class T> struct WeightQ {
+  __device__ __forceinline__ T operator()(int, const typename vec4<T>::type& pj) const { return pj.w; }
+};
+template <class T> struct WeightArr {
+  const double* w;
+  __device__ __forceinline__ T operator()(int j, const typename vec4<T>::type&) const { return (T)w[j]; }
+};
+
+template <class T>
+__device__ __forceinline__ void warp_sum(T& v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+}
+
+// singular sum for one target over its block, lanes of one warp in parallel.
+// W(j) = source weight (Q_j, or the adjoint weight); returns sum W/r and
+// sum W (x_j - x_t)/r^3 in every lane.
+template <class T, bool GRAD, class WeightF>
+__device__ __forceinline__ void warp_singular(int n, int n_sr, T h, int ex, int ey, int ez, int slot,
+                                              typename vec4<T>::type pt, const int* __restrict__ start,
+                                              const typename vec4<T>::type* __restrict__ part,
+                                              const int* __restrict__ ecoord, int* runs /* 2*MAXRUN */,
+                                              int* pre /* MAXRUN+1 */, WeightF W, T out[4]) {
+  const int lane = threadIdx.x & 31;
+  const int nb = 2 * n_sr + 1, rows = nb * nb;
+  // runs of consecutive element ids (split where the row wraps)
+  for (int r = lane; r < rows; r += 32) {
+    const int dy = r % nb - n_sr, dz = r / nb - n_sr;
+    const int yy = wrapn(ey + dy, n), zz = wrapn(ez + dz, n);
+    const int64_t rowbase = (int64_t)n * (yy + (int64_t)n * zz);
+    int x0 = ex - n_sr, x1 = ex + n_sr;
+    int a0, a1, b0 = 0, b1 = 0;
+    if (x0 < 0) {
+      a0 = start[rowbase + x0 + n]; a1 = start[rowbase + n];        // x0+n .. n-1
+      b0 = start[rowbase];          b1 = start[rowbase + x1 + 1];   // 0 .. x1
+    } else if (x1 >= n) {
+      a0 = start[rowbase + x0];     a1 = start[rowbase + n];        // x0 .. n-1
+      b0 = start[rowbase];          b1 = start[rowbase + x1 - n + 1];
+    } else {
+      a0 = start[rowbase + x0];     a1 = start[rowbase + x1 + 1];
+    }
+    runs[4 * r + 0] = a0; runs[4 * r + 1] = a1 - a0;
+    runs[4 * r + 2] = b0; runs[4 * r + 3] = b1 - b0;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    int acc = 0;
+    for (int k = 0; k < 2 * rows; ++k) {
+      pre[k] = acc;
+      acc += runs[2 * k + 1];
+    }
+    pre[2 * rows] = acc;
+  }
+  __syncwarp();
+  const int total = pre[2 * rows];
+  Acc<T> ps, fx, fy, fz;
+  int k = 0;
+  for (int f = lane; f < total; f += 32) {
+    while (pre[k + 1] <= f) ++k;
+    const int j = runs[2 * k] + (f - pre[k]);
+    if (j == slot) continue;
+    const typename vec4<T>::type pj = part[j];
+    const int ec = ecoord[j];
+    int dx = (ec & 1023) - ex, dy = ((ec >> 10) & 1023) - ey, dz = (ec >> 20) - ez;
+    dx = dx > n_sr ? dx - n : (dx < -n_sr ? dx + n : dx);
+    dy = dy > n_sr ? dy - n : (dy < -n_sr ? dy + n : dy);
+    dz = dz > n_sr ? dz - n : (dz < -n_sr ? dz + n : dz);
+    const T rx = (T(dx) + (pj.x - pt.x)) * h, ry = (T(dy) + (pj.y - pt.y)) * h, rz = (T(dz) + (pj.z - pt.z)) * h;
+    const T ir = rsq<T>(rx * rx + ry * ry + rz * rz);
+    const T wj = W(j, pj);
+    ps.add(wj * ir);
+    if (GRAD) {
+      const T f3 = wj * ir * ir * ir;
+      fx.add(f3 * rx);
+      fy.add(f3 * ry);
+      fz.add(f3 * rz);
+    }
+  }
+  out[0] = ps.get();
+  out[1] = fx.get();
+  out[2] = fy.get();
+  out[3] = fz.get();
+  for (int i = 0; i < 4; ++i) warp_sum(out[i]);
+  __syncwarp();
+}
+
+template <class T, bool GRAD>
+__global__ void __launch_bounds__(PT) k_pair_brick(int n, int n_sr, T h, T inv_h, const int* __restrict__ start,
+                                                   const int* __restrict__ count,
+                                                   const typename vec4<T>::type* __restrict__ part,
+                                                   const int* __restrict__ ecoord, const T* __restrict__ C,
+                                                   const T* __restrict__ rv, const T* __restrict__ phi_mesh,
+                                                   const T* __restrict__ Hw, const int* __restrict__ perm,
+                                                   double* __restrict__ phi_s, double* __restrict__ E_s,
+                                                   double* __restrict__ phi_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nbx = (n + BX - 1) / BX, nby = (n + BY - 1) / BY;
+  const int E0x = (blockIdx.x % nbx) * BX, E0y = ((blockIdx.x / nbx) % nby) * BY, E0z = (blockIdx.x / (nbx * nby)) * BZ;
+  const int keep = n_sr + 1, noff = 2 * n_sr + 2, no3 = noff * noff * noff;
+  const int VW = BX + 2 * n_sr + 1, CW = BX + 2 * n_sr;
+  T* r_t = (T*)smem_raw;                              // VW^3 vertex densities, origin E0 - n_sr
+  T* C_t = r_t + VW * VW * VW;                        // CW^3 x 8 element coefficients, origin E0 - n_sr
+  T* A_c = C_t + CW * CW * CW * 8;                    // [OCH][64]
+  T* H_c = A_c + OCH * 64;                            // [OCH][64]
+  int* epre = (int*)(H_c + OCH * 64);                 // BE + 1 target prefix over brick elements
+  int* runs_all = epre + BE + 1;                      // 8 warps x 2*MAXRUN
+  int* pre_all = runs_all + 8 * 2 * MAXRUN;           // 8 warps x (MAXRUN+1)
+  const int tid = threadIdx.x;
+  // targets in the brick
+  if (tid == 0) {
+    int acc = 0;
+    for (int l = 0; l < BE; ++l) {
+      epre[l] = acc;
+      const int lx = E0x + (l % BX), ly = E0y + (l / BX) % BY, lz = E0z + l / (BX * BY);
+      if (lx < n && ly < n && lz < n) acc += count[lx + (int64_t)n * (ly + (int64_t)n * lz)];
+    }
+    epre[BE] = acc;
+  }
+  __syncthreads();
+  const int ntarget = epre[BE];
+  if (ntarget == 0) return;
+  // (1) stage vertex densities and element coefficients of the halo
+  for (int i = tid; i < VW * VW * VW; i += PT) {
+    const int vx = i % VW, vy = (i / VW) % VW, vz = i / (VW * VW);
+    r_t[i] = rv[wrapn(E0x - n_sr + vx, n) + (int64_t)n * (wrapn(E0y - n_sr + vy, n) + (int64_t)n * wrapn(E0z - n_sr + vz, n))];
+  }
+  for (int i = tid; i < CW * CW * CW * 8; i += PT) {
+    const int k = i & 7, el = i >> 3;
+    const int cx = el % CW, cy = (el / CW) % CW, cz = el / (CW * CW);
+    C_t[i] = C[(wrapn(E0x - n_sr + cx, n) + (int64_t)n * (wrapn(E0y - n_sr + cy, n) + (int64_t)n * wrapn(E0z - n_sr + cz, n))) * 8 + k];
+  }
+  // (2) screen field, 4 x 4 register tile: elements 4 eb .. 4 eb + 3, nodes 4 mb .. 4 mb + 3
+  const int eb = tid >> 4, mb = tid & 15;
+  // per-chunk partial sums are added into a separate total: rounding grows with
+  // the 32-term chunks instead of all 512 terms
+  T acc[4][4], tot[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tot[i][j] = T(0);
+  for (int o0 = 0; o0 < no3; o0 += OCH) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    __syncthreads();
+    for (int i = tid; i < OCH * 64; i += PT) {
+      const int oi = i >> 6, m = i & 63, o = o0 + oi;
+      H_c[i] = o < no3 ? Hw[(int64_t)o * 64 + m] : T(0);
+      // vertex amplitude A(e, o) for brick element l = m (64 elements)
+      T A = T(0);
+      if (o < no3) {
+        const int l = m;
+        const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
+        const int ox = o % noff - keep, oy = (o / noff) % noff - keep, oz = o / (noff * noff) - keep;
+        // vertex v = e - o in tile coords (tile origin E0 - n_sr)
+        const int tx = lx - ox + n_sr, ty = ly - oy + n_sr, tz = lz - oz + n_sr;
+        if (ox > -keep && ox < n_sr && oy > -keep && oy < n_sr && oz > -keep && oz < n_sr) {
+          A = r_t[tx + VW * (ty + VW * tz)];
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
+            if (ox + kx < -n_sr || ox + kx > n_sr || oy + ky < -n_sr || oy + ky > n_sr || oz + kz < -n_sr ||
+                oz + kz > n_sr)
+              continue;
+            A += C_t[((tx - kx) + CW * ((ty - ky) + CW * (tz - kz))) * 8 + k];
+          }
+        }
+      }
+      A_c[i] = A;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int oi = 0; oi < OCH; ++oi) {
+      T a[4], hh[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = A_c[oi * 64 + 4 * eb + i];
+        hh[i] = H_c[oi * 64 + 4 * mb + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * hh[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j];
+  }
+  __syncthreads();
+  // G = mesh potential - screen field, into the A chunk buffer ([64 elements][64 nodes] = 2 chunks)
+  T* G = A_c;
+  {
+    const int N = 3 * n;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int l = 4 * eb + i;
+      const int ex = E0x + l % BX, ey = E0y + (l / BX) % BY, ez = E0z + l / (BX * BY);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int m = 4 * mb + j, mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
+        T val = T(0);
+        if (ex < n && ey < n && ez < n) {
+          const int gx = wrapn(3 * ex + mx, N), gy = wrapn(3 * ey + my, N), gz = wrapn(3 * ez + mz, N);
+          val = phi_mesh[gx + (int64_t)N * (gy + (int64_t)N * gz)] - tot[i][j];
+        }
+        G[l * 64 + m] = val;
+      }
+    }
+  }
+  __syncthreads();
+  // (3) one warp per target
+  const int warp = tid >> 5, lane = tid & 31;
+  int* runs = runs_all + warp * 2 * MAXRUN;
+  int* pre = pre_all + warp * (MAXRUN + 1);
+  for (int k = warp; k < ntarget; k += PT / 32) {
+    int l = 0;
+    while (epre[l + 1] <= k) ++l;
+    const int ex = E0x + l % BX, ey = E0y + (l / BX) % BY, ez = E0z + l / (BX * BY);
+    const int64_t e = ex + (int64_t)n * (ey + (int64_t)n * ez);
+    const int slot = start[e] + (k - epre[l]);
+    const typename vec4<T>::type pt = part[slot];
+    T ux[4], uy[4], uz[4], dx4[4], dy4[4], dz4[4];
+    q3_values<T>(pt.x, ux);
+    q3_values<T>(pt.y, uy);
+    q3_values<T>(pt.z, uz);
+    if (GRAD) {
+      q3_derivs<T>(pt.x, dx4);
+      q3_derivs<T>(pt.y, dy4);
+      q3_derivs<T>(pt.z, dz4);
+    }
+    T ev[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const int m = lane + 32 * h2, mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
+      const T g = G[l * 64 + m];
+      ev[0] += g * ux[mx] * uy[my] * uz[mz];
+      if (GRAD) {
+        ev[1] += g * dx4[mx] * uy[my] * uz[mz];
+        ev[2] += g * ux[mx] * dy4[my] * uz[mz];
+        ev[3] += g * ux[mx] * uy[my] * dz4[mz];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) warp_sum(ev[i]);
+    T sg[4];
+    warp_singular<T, GRAD>(n, n_sr, h, ex, ey, ez, slot, pt, start, part, ecoord, runs, pre,
+                           WeightQ<T>(), sg);
+    if (lane == 0) {
+      const double phi = (double)ev[0] * (double)inv_h + (double)sg[0];
+      phi_s[slot] = phi;
+      if (phi_out) phi_out[perm[slot]] = phi;
+      if (GRAD) {
+        const double ih2 = (double)inv_h * (double)inv_h;
+        E_s[3 * slot + 0] = (double)ev[1] * ih2 + (double)sg[1];
+        E_s[3 * slot + 1] = (double)ev[2] * ih2 + (double)sg[2];
+        E_s[3 * slot + 2] = (double)ev[3] * ih2 + (double)sg[3];
+      }
+    }
+  }
+}
+
 // ----------------------------------------------------------------- adjoint
 __global__ void k_weights(int64_t N, double gU, const double* __restrict__ gphi, const int* __restrict__ perm,
                           const double* __restrict__ Qs, double* __restrict__ w) {
@@ -439,22 +735,28 @@ cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev3) {
   return cudaGetLastError();
 }
 
-cudaError_t pair_forward(fep3m_ctx* c, double* phi_out, int want_grad) {
+template <class T, bool GRAD>
+static cudaError_t launch_pair_brick(fep3m_ctx* c, const T* phi_mesh, const T* Hw, double* phi_out) {
   const int n = c->n;
-  const int64_t ne = (int64_t)n * n * n;
-  cudaStream_t s = c->stream;
-  if (c->precision == FEP3M_MIXED) {
-    auto kern = want_grad ? k_pair_fwd<float, true> : k_pair_fwd<float, false>;
-    FEP3M_CL kern<<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, (float)c->h, (float)c->inv_h, c->start, c->count,
-                                     (const float4*)c->part, (const float*)c->C, (const float*)c->rv,
-                                     (const float*)c->phi_mesh_T, c->Hw32, c->perm, c->phi_s, c->E_s, phi_out);
-  } else {
-    auto kern = want_grad ? k_pair_fwd<double, true> : k_pair_fwd<double, false>;
-    FEP3M_CL kern<<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->h, c->inv_h, c->start, c->count, (const vec4<double>::type*)c->part,
-                                     (const double*)c->C, (const double*)c->rv, c->phi64, c->Hw64, c->perm,
-                                     c->phi_s, c->E_s, phi_out);
-  }
+  const int nbx = (n + BX - 1) / BX, nby = (n + BY - 1) / BY, nbz = (n + BZ - 1) / BZ;
+  const size_t smem = PairSmem<T>::bytes(c->n_sr);
+  auto kern = k_pair_brick<T, GRAD>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  FEP3M_CL kern<<<(unsigned)(nbx * nby * nbz), PT, smem, c->stream>>>(
+      n, c->n_sr, (T)c->h, (T)c->inv_h, c->start, c->count, (const typename vec4<T>::type*)c->part, c->ecoord,
+      (const T*)c->C, (const T*)c->rv, phi_mesh, Hw, c->perm, c->phi_s, c->E_s, phi_out);
   return cudaGetLastError();
+}
+
+cudaError_t pair_forward(fep3m_ctx* c, double* phi_out, int want_grad) {
+  if (c->precision == FEP3M_MIXED) {
+    const float* pm = (const float*)c->phi_mesh_T;
+    return want_grad ? launch_pair_brick<float, true>(c, pm, c->Hw32, phi_out)
+                     : launch_pair_brick<float, false>(c, pm, c->Hw32, phi_out);
+  }
+  return want_grad ? launch_pair_brick<double, true>(c, c->phi64, c->Hw64, phi_out)
+                   : launch_pair_brick<double, false>(c, c->phi64, c->Hw64, phi_out);
 }
 
 cudaError_t energy(fep3m_ctx* c, double* U_dev) {
