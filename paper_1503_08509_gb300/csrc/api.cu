@@ -189,7 +189,7 @@ void fep3m_destroy(fep3m_ctx* c) {
   free_particles(c);
   void* p[] = {c->Hw64, c->Hw32, c->count, c->start, c->fill, c->scan_tmp, c->C, c->rv, c->b64, c->phi64,
                c->res64, c->g64, c->lam64, c->scal, c->iflags, c->phi_mesh_T, c->W_el, c->A_el, c->mu_v,
-               c->red_tmp, c->red_counter};
+               c->red_tmp, c->red_counter, c->D_adj};
   for (void* q : p) dfree(q);
   solver_plan_free(c);
   mg_free(c);

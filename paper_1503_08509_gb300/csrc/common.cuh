@@ -72,6 +72,8 @@ struct CoarseSolver {
   double* Dinv64 = nullptr;   // N^3 inverse eigenvalue sums (0 for the constant mode)
   float* V32 = nullptr;
   float* Dinv32 = nullptr;
+  double* VT64 = nullptr;     // V^T copies (coalesced loads of the forward transform)
+  float* VT32 = nullptr;
 };
 
 struct Hierarchy {
@@ -135,6 +137,8 @@ struct fep3m_ctx {
   double* gphi_dev = nullptr;    // N staging for a host gphi
   void* W_el = nullptr;          // n^3 * 64 element deposits (T)
   void* A_el = nullptr;          // n^3 * 8 screen adjoint (T)
+  void* D_adj = nullptr;         // adjoint table-field GEMM output, chunk of offsets x n^3 (T)
+  size_t D_bytes = 0;
   void* mu_v = nullptr;          // n^3 vertex adjoint (T)
   void* sb[6] = {};              // PCG vectors r, z, p, q, x, rhs (working precision, fine level)
   size_t sb_bytes = 0;

@@ -202,6 +202,157 @@ __global__ void k_apply_x(int N, const T* __restrict__ a, const T* __restrict__ 
   }
 }
 
+
+// Fused apply y = K x in one kernel (2.5-D tiling): a CTA owns an FX x FY
+// column of output nodes and marches FZ planes in z, keeping the 7 input
+// planes the z stencil needs in a shared ring buffer (3-node halo in x and y),
+// and runs the three sum-factorisation passes on shared tiles.  The epilogue
+// is as in k_apply_x, except that the Chebyshev step writes the new iterate to
+// xo (not in place: neighbouring tiles still read x as their halo).
+constexpr int FX = 32, FY = 4, FZ = 4;
+constexpr int HXS = FX + 6, HYS = FY + 6, HPS = HXS * HYS;
+constexpr int FT = FX * FY;                          // threads per CTA
+constexpr int PLD = (HPS + FT - 1) / FT;             // plane values loaded per thread
+
+// Fused apply y = K x in one kernel (2.5-D tiling): a CTA owns an FX x FY
+// column of output nodes and marches FZ planes in z, keeping the 7 input
+// planes the z stencil needs in a shared ring buffer (3-node halo in x and y;
+// the next plane is fetched into registers while the current one is used),
+// and runs the three sum-factorisation passes on shared tiles.  The epilogue
+// options are as in k_apply_x, except that the Chebyshev step writes the new
+// iterate to xo (not in place: neighbouring tiles still read x as their halo).
+template <class T, int EPI>
+__global__ void __launch_bounds__(FT) k_apply_fused(int N, const T* __restrict__ x, T* __restrict__ out,
+                                                    const T* __restrict__ b, T* __restrict__ d,
+                                                    T* __restrict__ xo, T c1, T c2) {
+  __shared__ T ring[7][HPS];
+  __shared__ T t1s[HPS], t2s[HPS];
+  __shared__ T as_[FY][HXS], cs_[FY][HXS];
+  const int64_t NN = (int64_t)N * N;
+  const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY, z0 = blockIdx.z * FZ;
+  const int tid = threadIdx.x, tx = tid % FX, ty = tid / FX;
+  const int gx = x0 + tx, gy = y0 + ty;
+  // node types are fixed per thread in the x and y passes: stencils in registers
+  const int tx3 = gx % 3, ty3 = gy % 3;
+  T kx[7], mx[7], ky[7], my[7];
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    kx[j] = Cst<T>::K(tx3, j);
+    mx[j] = Cst<T>::M(tx3, j);
+    ky[j] = Cst<T>::K(ty3, j);
+    my[j] = Cst<T>::M(ty3, j);
+  }
+  T dv[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) dv[t] = dinv<T>(tx3, ty3, t);
+  int64_t off[PLD];
+#pragma unroll
+  for (int k = 0; k < PLD; ++k) {
+    const int i = tid + k * FT;
+    const int hx = i % HXS, hy = i / HXS;
+    const int ggx = ((x0 + hx - 3) % N + N) % N, ggy = ((y0 + hy - 3) % N + N) % N;
+    off[k] = i < HPS ? (int64_t)ggy * N + ggx : -1;
+  }
+  T pf[PLD];
+  auto fetch = [&](int z) {
+    const int64_t zo = (int64_t)(((z % N) + N) % N) * NN;
+#pragma unroll
+    for (int k = 0; k < PLD; ++k) pf[k] = off[k] >= 0 ? x[zo + off[k]] : T(0);
+  };
+  auto store = [&](int slot) {
+#pragma unroll
+    for (int k = 0; k < PLD; ++k) {
+      const int i = tid + k * FT;
+      if (i < HPS) ring[slot][i] = pf[k];
+    }
+  };
+  for (int k = 0; k < 6; ++k) {
+    fetch(z0 - 3 + k);
+    store(k);
+  }
+  fetch(z0 + 3);
+  const bool inside = gx < N && gy < N;
+  int slot_new = 6;                    // ring slot of plane z + 3
+  for (int zi = 0; zi < FZ; ++zi) {
+    const int z = z0 + zi;
+    if (z >= N) break;
+    store(slot_new);
+    __syncthreads();
+    if (zi + 1 < FZ && z + 1 < N) fetch(z + 4);     // in flight while this plane is computed
+    const int64_t g = inside ? gx + (int64_t)N * gy + NN * z : 0;
+    T eb = T(0), ed = T(0), ex = T(0);
+    if (inside && EPI != EPI_Y) eb = b[g];
+    if (inside && EPI == EPI_CHEB) {
+      ed = d[g];
+      ex = x[g];
+    }
+    // z pass over the halo plane: plane z + j sits in slot (slot_new - 3 + j) mod 7
+    const int tz = z % 3;
+    T kz[7], mz[7];
+    const T* rp[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      kz[j] = Cst<T>::K(tz, j);
+      mz[j] = Cst<T>::M(tz, j);
+      int sl = slot_new - 6 + j;
+      sl += sl < 0 ? 7 : 0;
+      rp[j] = ring[sl];
+    }
+#pragma unroll
+    for (int k = 0; k < PLD; ++k) {
+      const int i = tid + k * FT;
+      if (i < HPS) {
+        T s1 = T(0), s2 = T(0);
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+          const T v = rp[j][i];
+          s1 += mz[j] * v;
+          s2 += kz[j] * v;
+        }
+        t1s[i] = s1;
+        t2s[i] = s2;
+      }
+    }
+    __syncthreads();
+    // y pass: row ty, columns tx and tx + FX (of the HXS halo columns)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int hx = tx + h * FX;
+      if (hx < HXS) {
+        T s1 = T(0), s2 = T(0);
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+          const int q = (ty + j) * HXS + hx;
+          const T u = t1s[q], w = t2s[q];
+          s1 += my[j] * u;
+          s2 += ky[j] * u + my[j] * w;
+        }
+        as_[ty][hx] = s1;
+        cs_[ty][hx] = s2;
+      }
+    }
+    __syncthreads();
+    if (inside) {
+      T y = T(0);
+#pragma unroll
+      for (int j = 0; j < 7; ++j) y += kx[j] * as_[ty][tx + j] + mx[j] * cs_[ty][tx + j];
+      if (EPI == EPI_Y) {
+        out[g] = y;
+      } else if (EPI == EPI_RESID) {
+        out[g] = eb - y;
+      } else {
+        const T r = eb - y;
+        const T dn = c1 * ed + c2 * dv[tz] * r;
+        d[g] = dn;
+        xo[g] = ex + dn;
+      }
+    }
+    slot_new = slot_new == 6 ? 0 : slot_new + 1;
+  }
+}
+
+static inline int apply_fz(int) { return FZ; }
+
 // first Chebyshev step from x = 0: d = D^-1 b / theta, x = d
 template <class T>
 __global__ void k_cheb0(int N, const T* __restrict__ b, T* __restrict__ d, T* __restrict__ x, T inv_theta) {
@@ -291,6 +442,68 @@ __global__ void k_dense_axis(int N, int axis, const T* __restrict__ V, bool tran
   }
   if (scale) acc *= scale[g];
   out[g] = acc;
+}
+
+
+// Coalesced dense 1-D transform along one axis of an N^3 array (N <= 48):
+// out[.. i ..] = sum_k A[i][k] in[.. k ..] (A = V^T when transpose), optionally
+// scaled elementwise after.  The array is viewed as [outer][N along axis][inner];
+// a CTA takes 32 consecutive inner indices (or, for the x axis, 32 consecutive
+// pencils) so global loads and stores are contiguous; A lives in shared memory.
+constexpr int DT = 8;
+template <class T>
+__global__ void __launch_bounds__(256) k_dense_tile(int N, int axis, const T* __restrict__ V, int transpose,
+                                                    const T* __restrict__ in, T* __restrict__ out,
+                                                    const T* __restrict__ scale) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T* As = (T*)dsm;              // N x N
+  T* tile = As + N * N;         // DT x (N + 1)
+  const int64_t NN = (int64_t)N * N;
+  (void)transpose;   // V is passed already oriented (row r = output r)
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) As[i] = V[i];
+  // element (p, k) of the tile: pencil p of the block, position k along the axis
+  int64_t base;
+  int64_t pstride, kstride;
+  if (axis == 0) {               // pencils are rows: 32 consecutive rows
+    base = (int64_t)blockIdx.x * DT * N;
+    pstride = N;
+    kstride = 1;
+  } else if (axis == 1) {        // inner = x (N values), outer = z
+    const int nxb = (N + DT - 1) / DT;
+    const int zb = blockIdx.x / nxb, xb = blockIdx.x % nxb;
+    base = (int64_t)zb * NN + (int64_t)xb * DT;
+    pstride = 1;
+    kstride = N;
+  } else {                       // inner = x + N y (N^2 values)
+    base = (int64_t)blockIdx.x * DT;
+    pstride = 1;
+    kstride = NN;
+  }
+  int64_t npen;                  // pencils available in this block
+  if (axis == 0) npen = NN - (int64_t)blockIdx.x * DT;
+  else if (axis == 1) npen = N - (int64_t)(blockIdx.x % ((N + DT - 1) / DT)) * DT;
+  else npen = NN - (int64_t)blockIdx.x * DT;
+  const int np = (int)(npen < DT ? npen : DT);
+  for (int i = threadIdx.x; i < DT * N; i += blockDim.x) {
+    int p, k;
+    if (axis == 0) { p = i / N; k = i % N; }
+    else { k = i / DT; p = i % DT; }
+    tile[p * (N + 1) + k] = p < np ? in[base + p * pstride + k * kstride] : T(0);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < DT * N; i += blockDim.x) {
+    int p, r;
+    if (axis == 0) { p = i / N; r = i % N; }
+    else { r = i / DT; p = i % DT; }
+    if (p >= np) continue;
+    T acc = T(0);
+    const T* arow = As + r * N;
+    const T* tp = tile + p * (N + 1);
+    for (int k = 0; k < N; ++k) acc += arow[k] * tp[k];
+    const int64_t g = base + p * pstride + (int64_t)r * kstride;
+    if (scale) acc *= scale[g];
+    out[g] = acc;
+  }
 }
 
 // ---------------------------------------------------------- reductions
@@ -418,17 +631,17 @@ struct MG {
   Hierarchy& H;
   explicit MG(fep3m_ctx* cc) : c(cc), H(cc->mg) {}
 
-  void apply(const Level& L, const T* x, int epi, T* out, const T* b, T* d, T* xx, T c1, T c2) {
-    const size_t n = L.size;
+  // one fused apply; EPI_CHEB reads x and writes the new iterate to xo (xo != x)
+  void apply(const Level& L, const T* x, int epi, T* out, const T* b, T* d, T* xo, T c1, T c2) {
     cudaStream_t s = c->stream;
-    FEP3M_CL k_apply_z<T><<<grid_for(n), TPB, 0, s>>>(L.N, x, (T*)L.t1, (T*)L.t2);
-    FEP3M_CL k_apply_y<T><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.t1, (T*)L.t2, (T*)L.a, (T*)L.c);
+    const int fz = apply_fz(L.N);
+    const dim3 grid((L.N + FX - 1) / FX, (L.N + FY - 1) / FY, (L.N + fz - 1) / fz);
     if (epi == EPI_Y)
-      FEP3M_CL k_apply_x<T, EPI_Y><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.a, (T*)L.c, out, b, d, xx, c1, c2);
+      FEP3M_CL k_apply_fused<T, EPI_Y><<<grid, FT, 0, s>>>(L.N, x, out, b, d, xo, c1, c2);
     else if (epi == EPI_RESID)
-      FEP3M_CL k_apply_x<T, EPI_RESID><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.a, (T*)L.c, out, b, d, xx, c1, c2);
+      FEP3M_CL k_apply_fused<T, EPI_RESID><<<grid, FT, 0, s>>>(L.N, x, out, b, d, xo, c1, c2);
     else
-      FEP3M_CL k_apply_x<T, EPI_CHEB><<<grid_for(n), TPB, 0, s>>>(L.N, (T*)L.a, (T*)L.c, out, b, d, xx, c1, c2);
+      FEP3M_CL k_apply_fused<T, EPI_CHEB><<<grid, FT, 0, s>>>(L.N, x, out, b, d, xo, c1, c2);
   }
 
   // Chebyshev smoothing of A x = b (D-preconditioned) on [lmax/ratio, lmax]
@@ -441,26 +654,48 @@ struct MG {
       FEP3M_CL k_cheb0<T><<<grid_for(L.size), TPB, 0, c->stream>>>(L.N, b, (T*)L.d, x, (T)(1.0 / theta));
       k0 = 1;
     }
+    // iterates alternate between x and the level's spare buffer
+    T* cur = x;
+    T* oth = (T*)L.a;
     for (int k = k0; k < degree; ++k) {
       if (k == 0) {
-        apply(L, x, EPI_CHEB, nullptr, b, (T*)L.d, x, T(0), (T)(1.0 / theta));
+        apply(L, cur, EPI_CHEB, nullptr, b, (T*)L.d, oth, T(0), (T)(1.0 / theta));
       } else {
         const double rn = 1.0 / (2.0 * sigma - rho);
-        apply(L, x, EPI_CHEB, nullptr, b, (T*)L.d, x, (T)(rn * rho), (T)(2.0 * rn / delta));
+        apply(L, cur, EPI_CHEB, nullptr, b, (T*)L.d, oth, (T)(rn * rho), (T)(2.0 * rn / delta));
         rho = rn;
       }
+      T* t = cur;
+      cur = oth;
+      oth = t;
     }
+    if (cur != x) cudaMemcpyAsync(x, cur, L.size * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
   }
 
   void coarse_solve(const Level& L, const T* b, T* x) {
     const CoarseSolver& cs = H.coarse;
     const T* V = (const T*)(sizeof(T) == 8 ? (const void*)cs.V64 : (const void*)cs.V32);
+    const T* VT = (const T*)(sizeof(T) == 8 ? (const void*)cs.VT64 : (const void*)cs.VT32);
     const T* Dinv = (const T*)(sizeof(T) == 8 ? (const void*)cs.Dinv64 : (const void*)cs.Dinv32);
     const int N = L.N;
-    const int gsz = grid_for(L.size);
     cudaStream_t s = c->stream;
     T* w1 = (T*)L.t1;
     T* w2 = (T*)L.t2;
+    if (N <= 48) {   // A and the tile fit the default 48 KB of dynamic shared memory
+      const size_t sm = ((size_t)N * N + (size_t)DT * (N + 1)) * sizeof(T);
+      const int64_t NN = (int64_t)N * N;
+      const unsigned g0 = (unsigned)((NN + DT - 1) / DT);
+      const unsigned g1 = (unsigned)(N * ((N + DT - 1) / DT));
+      const unsigned g2 = (unsigned)((NN + DT - 1) / DT);
+      FEP3M_CL k_dense_tile<T><<<g0, 256, sm, s>>>(N, 0, VT, 1, b, w1, nullptr);
+      FEP3M_CL k_dense_tile<T><<<g1, 256, sm, s>>>(N, 1, VT, 1, w1, w2, nullptr);
+      FEP3M_CL k_dense_tile<T><<<g2, 256, sm, s>>>(N, 2, VT, 1, w2, w1, Dinv);
+      FEP3M_CL k_dense_tile<T><<<g0, 256, sm, s>>>(N, 0, V, 0, w1, w2, nullptr);
+      FEP3M_CL k_dense_tile<T><<<g1, 256, sm, s>>>(N, 1, V, 0, w2, w1, nullptr);
+      FEP3M_CL k_dense_tile<T><<<g2, 256, sm, s>>>(N, 2, V, 0, w1, x, nullptr);
+      return;
+    }
+    const int gsz = grid_for(L.size);
     FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 0, V, true, b, w1, nullptr);
     FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 1, V, true, w1, w2, nullptr);
     FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 2, V, true, w2, w1, Dinv);
@@ -611,7 +846,7 @@ cudaError_t mg_setup(fep3m_ctx* c) {
     L.N = 3 * n;
     L.size = (size_t)L.N * L.N * L.N;
     H.lv.push_back(L);
-    if (n % 2 != 0 || n <= 4) break;
+    if (n % 2 != 0 || n <= 16) break;   // the coarsest level (<= 48^3 nodes) is solved exactly
     n /= 2;
   }
   const size_t es = H.elem_size;
@@ -647,16 +882,23 @@ cudaError_t mg_setup(fep3m_ctx* c) {
   CoarseSolver& cs = H.coarse;
   cs.N = N;
   cudaError_t e;
+  std::vector<double> VT((size_t)N * N);
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < N; ++k) VT[(size_t)i * N + k] = V[(size_t)k * N + i];
   if (f32) {
-    std::vector<float> V32(V.begin(), V.end()), D32(Dinv.begin(), Dinv.end());
+    std::vector<float> V32(V.begin(), V.end()), VT32(VT.begin(), VT.end()), D32(Dinv.begin(), Dinv.end());
     if ((e = cudaMalloc(&cs.V32, V32.size() * 4)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&cs.VT32, VT32.size() * 4)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&cs.Dinv32, D32.size() * 4)) != cudaSuccess) return e;
     cudaMemcpy(cs.V32, V32.data(), V32.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(cs.VT32, VT32.data(), VT32.size() * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(cs.Dinv32, D32.data(), D32.size() * 4, cudaMemcpyHostToDevice);
   } else {
     if ((e = cudaMalloc(&cs.V64, V.size() * 8)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&cs.VT64, VT.size() * 8)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&cs.Dinv64, Dinv.size() * 8)) != cudaSuccess) return e;
     cudaMemcpy(cs.V64, V.data(), V.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(cs.VT64, VT.data(), VT.size() * 8, cudaMemcpyHostToDevice);
     cudaMemcpy(cs.Dinv64, Dinv.data(), Dinv.size() * 8, cudaMemcpyHostToDevice);
   }
   H.lmax = estimate_lmax(c->st, 6);
@@ -672,6 +914,8 @@ void mg_free(fep3m_ctx* c) {
   c->mg.lv.clear();
   CoarseSolver& cs = c->mg.coarse;
   if (cs.V64) cudaFree(cs.V64);
+  if (cs.VT64) cudaFree(cs.VT64);
+  if (cs.VT32) cudaFree(cs.VT32);
   if (cs.Dinv64) cudaFree(cs.Dinv64);
   if (cs.V32) cudaFree(cs.V32);
   if (cs.Dinv32) cudaFree(cs.Dinv32);
@@ -720,9 +964,10 @@ static cudaError_t apply64(fep3m_ctx* c, const double* x, const double* b, doubl
   cudaStream_t s = c->stream;
   const int N = L0.N;
   double** B = c->ap64;
-  FEP3M_CL k_apply_z<double><<<grid_for(L0.size), TPB, 0, s>>>(N, x, B[0], B[1]);
-  FEP3M_CL k_apply_y<double><<<grid_for(L0.size), TPB, 0, s>>>(N, B[0], B[1], B[2], B[3]);
-  FEP3M_CL k_apply_x<double, EPI_RESID><<<grid_for(L0.size), TPB, 0, s>>>(N, B[2], B[3], r, b, nullptr, nullptr, 0.0, 0.0);
+  (void)B;
+  const int fz = apply_fz(N);
+  const dim3 grid((N + FX - 1) / FX, (N + FY - 1) / FY, (N + fz - 1) / fz);
+  FEP3M_CL k_apply_fused<double, EPI_RESID><<<grid, FT, 0, s>>>(N, x, r, b, nullptr, nullptr, 0.0, 0.0);
   return cudaGetLastError();
 }
 
@@ -900,17 +1145,20 @@ cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, d
       *refine_steps = c->precision == FEP3M_FP64 ? 0 : c->plan_kout;
       return cudaSuccess;
     }
-    destroy_plan(c);   // this right-hand side needs more iterations: recalibrate below
+    // this right-hand side needs more iterations: one more sweep next time
+    if (c->precision == FEP3M_FP64) ++c->plan_k;
+    else ++c->plan_kout;
+    destroy_plan(c);
   }
   int kin = 0;
   e = solve_checked(c, b, phi, iters, relres, refine_steps, &kin);
   if (e != cudaSuccess || *relres > rtol) return e;
   // forward and adjoint solves share the plan: keep the larger counts
   if (c->precision == FEP3M_FP64) {
-    c->plan_k = std::max(c->plan_k, *iters + 1);
+    c->plan_k = std::max(c->plan_k, *iters);
   } else {
     c->plan_kin = std::max(c->plan_kin, kin);
-    c->plan_kout = std::max(c->plan_kout, *refine_steps + 1);
+    c->plan_kout = std::max(c->plan_kout, *refine_steps);
   }
   if (!c->in64 && (e = cudaMalloc(&c->in64, n * sizeof(double))) != cudaSuccess) return e;
   if (!c->out64 && (e = cudaMalloc(&c->out64, n * sizeof(double))) != cudaSuccess) return e;

@@ -629,6 +629,110 @@ __global__ void __launch_bounds__(PT) k_pair_adj(int n, int n_sr, T h, const int
   }
 }
 
+// Screen part of the adjoint, as a GEMM and a gather (deterministic, no atomics):
+//   D[o][e] = sum_m W[e][m] H(o, m)               (every element e, every vertex offset o)
+//   A[s][k] = sum_{o : o + k in block} D[o][s + k + o]
+// D[o][e] is the table field of element e's deposit seen from the vertex e - o.
+constexpr int GT = 64;   // GEMM tile: 64 elements x 64 offsets, K = 64 nodes
+
+template <class T>
+__global__ void __launch_bounds__(PT) k_adj_gemm(int64_t ne, int o0, int no, const T* __restrict__ W,
+                                                 const T* __restrict__ Hw, T* __restrict__ D) {
+  __shared__ T Ws[64][GT + 1];   // [m][element]
+  __shared__ T Hs[64][GT + 1];   // [m][offset]
+  const int64_t e0 = (int64_t)blockIdx.x * GT;
+  const int oo0 = o0 + blockIdx.y * GT;
+  for (int i = threadIdx.x; i < GT * 64; i += PT) {
+    const int r = i >> 6, m = i & 63;
+    const int64_t e = e0 + r;
+    Ws[m][r] = e < ne ? W[e * 64 + m] : T(0);
+    const int o = oo0 + r;
+    Hs[m][r] = (o < o0 + no) ? Hw[(int64_t)o * 64 + m] : T(0);
+  }
+  __syncthreads();
+  const int te = threadIdx.x & 15, to = threadIdx.x >> 4;   // 4 elements x 4 offsets per thread
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+#pragma unroll 8
+  for (int m = 0; m < 64; ++m) {
+    T a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      a[i] = Ws[m][te + 16 * i];
+      b[i] = Hs[m][to + 16 * i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int o = oo0 + to + 16 * j;
+    if (o >= o0 + no) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t e = e0 + te + 16 * i;
+      if (e < ne) D[(int64_t)(o - o0) * ne + e] = acc[i][j];
+    }
+  }
+}
+
+// A[s][k] (+)= sum over offsets o in [o0, o0 + no) with o + k inside the block of D[o][s + k + o]
+template <class T>
+__global__ void k_adj_gather(int n, int n_sr, int o0, int no, int first, const int* __restrict__ count,
+                             const T* __restrict__ D, T* __restrict__ A) {
+  const int64_t ne = (int64_t)n * n * n;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= 8 * ne) return;
+  const int k = (int)(gid / ne);
+  const int64_t s = gid - k * ne;
+  T acc = first ? T(0) : A[s * 8 + k];
+  if (count[s] != 0) {
+    const int keep = n_sr + 1, noff = 2 * n_sr + 2;
+    const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
+    const int sx = (int)(s % n), sy = (int)((s / n) % n), sz = (int)(s / ((int64_t)n * n));
+    for (int oi = 0; oi < no; ++oi) {
+      const int o = o0 + oi;
+      const int ox = o % noff - keep, oy = (o / noff) % noff - keep, oz = o / (noff * noff) - keep;
+      if (ox + kx < -n_sr || ox + kx > n_sr || oy + ky < -n_sr || oy + ky > n_sr || oz + kz < -n_sr ||
+          oz + kz > n_sr)
+        continue;
+      const int64_t e = wrapn(sx + kx + ox, n) + (int64_t)n * (wrapn(sy + ky + oy, n) + (int64_t)n * wrapn(sz + kz + oz, n));
+      acc += D[(int64_t)oi * ne + e];
+    }
+  }
+  A[s * 8 + k] = acc;
+}
+
+// singular adjoint potential, one warp per charge
+template <class T>
+__global__ void __launch_bounds__(PT) k_pair_adj_warp(int64_t N, int n, int n_sr, T h, const int* __restrict__ start,
+                                                      const typename vec4<T>::type* __restrict__ part,
+                                                      const int* __restrict__ ecoord, const double* __restrict__ w,
+                                                      double* __restrict__ psi, double* __restrict__ gpsi) {
+  __shared__ int runs_all[8 * 2 * MAXRUN];
+  __shared__ int pre_all[8 * (MAXRUN + 1)];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t = blockIdx.x * (int64_t)(PT / 32) + warp;
+  if (t >= N) return;
+  const typename vec4<T>::type pt = part[t];
+  const int ec = ecoord[t];
+  T sg[4];
+  WeightArr<T> wf{w};
+  warp_singular<T, true>(n, n_sr, h, ec & 1023, (ec >> 10) & 1023, ec >> 20, (int)t, pt, start, part, ecoord,
+                         runs_all + warp * 2 * MAXRUN, pre_all + warp * (MAXRUN + 1), wf, sg);
+  if (lane == 0) {
+    psi[t] = (double)sg[0];
+    gpsi[3 * t + 0] = (double)sg[1];
+    gpsi[3 * t + 1] = (double)sg[2];
+    gpsi[3 * t + 2] = (double)sg[3];
+  }
+}
+
 // per charge: dLf/dQ and dLf/dx from the pieces (see fep3m_vjp)
 template <class T>
 __global__ void k_final(int64_t N, int n, double inv_h, double gU, const typename vec4<T>::type* __restrict__ part,
@@ -772,6 +876,33 @@ cudaError_t energy(fep3m_ctx* c, double* U_dev) {
   return cudaGetLastError();
 }
 
+// D-GEMM + gather over offset chunks sized so D stays within a memory budget
+template <class T>
+static cudaError_t screen_adjoint(fep3m_ctx* c, const T* W, const T* Hw, T* A) {
+  const int n = c->n;
+  const int64_t ne = (int64_t)n * n * n;
+  const int no3 = c->noff * c->noff * c->noff;
+  const size_t budget = (size_t)1 << 31;   // bytes of D held at once
+  int chunk = (int)std::min<int64_t>(no3, std::max<int64_t>(GT, (int64_t)(budget / (ne * sizeof(T))) / GT * GT));
+  const size_t need = (size_t)chunk * ne * sizeof(T);
+  if (c->D_bytes < need) {
+    if (c->D_adj) cudaFree(c->D_adj);
+    c->D_adj = nullptr;
+    c->D_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->D_adj, need);
+    if (e != cudaSuccess) return e;
+    c->D_bytes = need;
+  }
+  cudaStream_t s = c->stream;
+  for (int o0 = 0; o0 < no3; o0 += chunk) {
+    const int no = std::min(chunk, no3 - o0);
+    dim3 grid((unsigned)((ne + GT - 1) / GT), (unsigned)((no + GT - 1) / GT));
+    FEP3M_CL k_adj_gemm<T><<<grid, PT, 0, s>>>(ne, o0, no, W, Hw, (T*)c->D_adj);
+    FEP3M_CL k_adj_gather<T><<<gsz(8 * ne), PT, 0, s>>>(n, c->n_sr, o0, no, o0 == 0, c->count, (const T*)c->D_adj, A);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t adjoint(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double* dQ) {
   const int n = c->n;
   const int64_t ne = (int64_t)n * n * n, nodes = 27 * ne, N = c->N;
@@ -807,18 +938,17 @@ cudaError_t adjoint(fep3m_ctx* c, double gU, const double* gphi, double* dpos, d
   e = vertex_adjoint(c, c->lam64, c->mu_v, c->mg.lv[0].t1, c->mg.lv[0].t2);
   if (e != cudaSuccess) return e;
   if (f32) {
-    FEP3M_CL k_screen_adjoint<float><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->count, (const float*)c->W_el, c->Hw32,
-                                                        (float*)c->A_el);
-    FEP3M_CL k_pair_adj<float><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, (float)c->h, c->start, c->count,
-                                                  (const float4*)c->part, c->w_s, c->psi_s, c->gpsi_s);
+    if ((e = screen_adjoint<float>(c, (const float*)c->W_el, c->Hw32, (float*)c->A_el)) != cudaSuccess) return e;
+    FEP3M_CL k_pair_adj_warp<float><<<(unsigned)((N + 7) / 8), PT, 0, s>>>(N, n, c->n_sr, (float)c->h, c->start,
+                                                       (const float4*)c->part, c->ecoord, c->w_s, c->psi_s, c->gpsi_s);
     FEP3M_CL k_final<float><<<gsz(N), PT, 0, s>>>(N, n, c->inv_h, gU, (const float4*)c->part, c->perm, c->cell, c->w_s,
                                          c->phi_s, c->E_s, c->psi_s, c->gpsi_s, (const float*)c->mu_v,
                                          (const float*)c->A_el, dpos, dQ);
   } else {
-    FEP3M_CL k_screen_adjoint<double><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->count, (const double*)c->W_el, c->Hw64,
-                                                         (double*)c->A_el);
-    FEP3M_CL k_pair_adj<double><<<(unsigned)ne, PT, 0, s>>>(n, c->n_sr, c->h, c->start, c->count, (const vec4<double>::type*)c->part,
-                                                   c->w_s, c->psi_s, c->gpsi_s);
+    if ((e = screen_adjoint<double>(c, (const double*)c->W_el, c->Hw64, (double*)c->A_el)) != cudaSuccess) return e;
+    FEP3M_CL k_pair_adj_warp<double><<<(unsigned)((N + 7) / 8), PT, 0, s>>>(N, n, c->n_sr, c->h, c->start,
+                                                        (const vec4<double>::type*)c->part, c->ecoord, c->w_s,
+                                                        c->psi_s, c->gpsi_s);
     FEP3M_CL k_final<double><<<gsz(N), PT, 0, s>>>(N, n, c->inv_h, gU, (const vec4<double>::type*)c->part, c->perm, c->cell, c->w_s,
                                           c->phi_s, c->E_s, c->psi_s, c->gpsi_s, (const double*)c->mu_v,
                                           (const double*)c->A_el, dpos, dQ);

@@ -120,6 +120,21 @@ def test_mesh_solve(api, precision, tol):
     assert maxrel(phi, pm) < tol, (maxrel(phi, pm), eng.stats())
 
 
+@pytest.mark.parametrize("n", [32, 40])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-7)])
+def test_multilevel_solve(api, n, precision, tol):
+    # meshes above 16 elements per axis use the multigrid hierarchy (40 -> 20 -> 10)
+    ops = ofe.MeshOperators(1.3, n)
+    rng = np.random.default_rng(n)
+    b = ops.neutralise(rng.normal(size=(3 * n,) * 3))
+    ref = ops.solve(b)
+    eng = api.FEP3M(1.3, n, precision=precision)
+    for _ in range(2):       # first call calibrates, second replays the captured solve
+        phi = eng.solve_mesh(b.transpose(2, 1, 0).ravel())
+        assert maxrel(phi, ref.transpose(2, 1, 0).ravel()) < tol, eng.stats()
+    assert eng.stats()["mg_levels"] >= 2
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_fp64_matches_oracle(api, name):
     d, ref, dx = oracle(name)
