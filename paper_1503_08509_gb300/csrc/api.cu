@@ -115,7 +115,7 @@ int grow_particles(fep3m_ctx* c, int64_t N) {
   CK(dalloc(&c->w_s, N));
   CK(dalloc(&c->psi_s, N));
   CK(dalloc(&c->gpsi_s, 3 * N));
-  CK(dalloc(&c->out_tmp, 4 * N));
+  CK(dalloc(&c->out_tmp, 5 * N));
   CK(dalloc(&c->Q_s, N));
   CK(dalloc(&c->gphi_dev, N));
   c->cap = N;
@@ -146,24 +146,53 @@ double ev_ms(fep3m_ctx* c, int a, int b) {
   return ms;
 }
 
-int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad) {
+void solve_stats(fep3m_ctx* c) {
+  const fep3m::Solver& F = c->solv[0];
+  c->stats.mg_iterations = F.iters;
+  c->stats.mg_rel_residual = F.relres;
+  c->stats.refine_steps = F.refine_steps;
+}
+
+// The forward chain (assembly, mesh solve, pair kernel) on the context's stream.
+// With force_dev, the adjoint chain for forces (weights Q/2 need nothing from
+// the forward solve) runs concurrently on the auxiliary stream: deposit,
+// adjoint mesh solve, vertex adjoint, screen and singular adjoint sweeps; the
+// per-charge assembly joins both chains.
+int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev) {
+  fep3m::Solver* F = &c->solv[0];
+  fep3m::Solver* A = &c->solv[1];
+  F->stream = c->stream;
+  if (force_dev) {
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
+    CK(adjoint_pre(c, 1.0, nullptr, c->aux_stream));
+    CK(mesh_solve_begin(A, c->g64, c->lam64));
+  }
   ev_record(c, 0);
   CK(assemble_forward(c));
   ev_record(c, 1);
-  int it = 0, rs = 0;
-  double rel = 0;
-  CK(mesh_solve(c, c->b64, c->phi64, &it, &rel, &rs));
-  c->stats.mg_iterations = it;
-  c->stats.mg_rel_residual = rel;
-  c->stats.refine_steps = rs;
+  CK(mesh_solve_begin(F, c->b64, c->phi64));
+  CK(mesh_solve_end(F));
+  solve_stats(c);
   CK(pair_prepare(c));
   ev_record(c, 2);
   CK(pair_forward(c, phi_dev, want_grad));
   ev_record(c, 3);
   c->have_forward = true;
   c->have_grad = want_grad != 0;
+  if (force_dev) {
+    CK(mesh_solve_end(A));
+    c->stats.adj_iterations = A->iters;
+    c->stats.adj_rel_residual = A->relres;
+    CK(adjoint_mid(c, c->aux_stream));
+    CK(cudaEventRecord(c->ev_join, c->aux_stream));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    CK(adjoint_final(c, 1.0, force_dev, nullptr, -1.0, c->stream));
+    ev_record(c, 4);
+  }
   const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : (c->precision == FEP3M_FP64 ? 1e-13 : 1e-10);
-  return rel <= 10 * rtol ? FEP3M_OK : FEP3M_ENOCONV;
+  const bool ok = F->relres <= 10 * rtol && (!force_dev || A->relres <= 10 * rtol);
+  return ok ? FEP3M_OK : FEP3M_ENOCONV;
 }
 
 }  // namespace
@@ -191,9 +220,11 @@ void fep3m_destroy(fep3m_ctx* c) {
                c->res64, c->g64, c->lam64, c->scal, c->iflags, c->phi_mesh_T, c->W_el, c->A_el, c->mu_v,
                c->red_tmp, c->red_counter, c->D_adj};
   for (void* q : p) dfree(q);
-  solver_plan_free(c);
-  mg_free(c);
-  solver_free(c);
+  fep3m::solver_destroy(&c->solv[0]);
+  fep3m::solver_destroy(&c->solv[1]);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->ev_init)
     for (int k = 0; k < 8; ++k) cudaEventDestroy(c->ev[k]);
   delete c;
@@ -261,8 +292,13 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
     return fail(from_cuda(e));
   cudaMemset(c->red_counter, 0, sizeof(unsigned int));
   cudaMemset(c->iflags, 0, 16 * sizeof(int));
-  if ((e = mg_setup(c)) != cudaSuccess) return fail(from_cuda(e));
-  c->stats.mg_levels = (int)c->mg.lv.size();
+  if ((e = cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+    return fail(from_cuda(e));
+  if ((e = solver_init(&c->solv[0], c, c->stream)) != cudaSuccess) return fail(from_cuda(e));
+  if ((e = solver_init(&c->solv[1], c, c->aux_stream)) != cudaSuccess) return fail(from_cuda(e));
+  c->stats.mg_levels = (int)c->solv[0].mg.lv.size();
   for (int k = 0; k < 8; ++k) cudaEventCreate(&c->ev[k]);
   c->ev_init = true;
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(from_cuda(e));
@@ -289,6 +325,7 @@ int fep3m_set_particles(fep3m_ctx* c, int64_t N, const double* pos, const double
   ev_record(c, 6);
   CK(cudaMemsetAsync(c->iflags, 0, sizeof(int), c->stream));
   CK(bin_particles(c, dpos, dQ, c->precision == FEP3M_MIXED));
+  CK(sorted_charges(c));
   FEP3M_CL k_charge_sums<<<1, PT, 0, c->stream>>>(N, dQ, c->scal + 32);   // one block: writes the totals
   ev_record(c, 7);
   CK(pair_counts(c, (unsigned long long*)(c->scal + 48)));
@@ -316,7 +353,9 @@ int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
   if (!c->have_particles) return FEP3M_ESTATE;
   const int64_t N = c->N;
   const bool phi_dev = is_device_ptr(phi);
-  int st = run_forward(c, phi_dev ? phi : (phi ? c->out_tmp : nullptr), force != nullptr);
+  const bool fdev = force && is_device_ptr(force);
+  double* fdst = force ? (fdev ? force : c->out_tmp + N) : nullptr;
+  int st = run_forward(c, phi_dev ? phi : (phi ? c->out_tmp : nullptr), force != nullptr, fdst);
   if (st != FEP3M_OK && st != FEP3M_ENOCONV) return st;
   if (phi && !phi_dev) {
     int s2 = deliver(c, phi, c->out_tmp, N * sizeof(double));
@@ -326,17 +365,9 @@ int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
     CK(energy(c, c->scal + 40));
     CK(cudaMemcpyAsync(U, c->scal + 40, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   }
-  if (force) {
-    const bool fdev = is_device_ptr(force);
-    double* dst = fdev ? force : c->out_tmp;
-    CK(adjoint(c, 1.0, nullptr, dst, nullptr));
-    FEP3M_CL k_scale<<<gsz(3 * N), PT, 0, c->stream>>>(3 * N, dst, -1.0);
-    CK(cudaGetLastError());
-    ev_record(c, 4);
-    if (!fdev) {
-      int s2 = deliver(c, force, c->out_tmp, 3 * N * sizeof(double));
-      if (s2 != FEP3M_OK) return s2;
-    }
+  if (force && !fdev) {
+    int s2 = deliver(c, force, fdst, 3 * N * sizeof(double));
+    if (s2 != FEP3M_OK) return s2;
   }
   CK(cudaStreamSynchronize(c->stream));
   if (c->timing) {
@@ -353,7 +384,7 @@ int fep3m_vjp(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double*
   if (!c->have_particles) return FEP3M_ESTATE;
   const int64_t N = c->N;
   if (!c->have_forward || !c->have_grad) {
-    int st = run_forward(c, nullptr, 1);
+    int st = run_forward(c, nullptr, 1, nullptr);
     if (st != FEP3M_OK && st != FEP3M_ENOCONV) return st;
   }
   const double* g = gphi;
@@ -362,15 +393,24 @@ int fep3m_vjp(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double*
     g = c->gphi_dev;
   }
   const bool pdev = is_device_ptr(dpos), qdev = is_device_ptr(dQ);
-  double* dp = dpos ? (pdev ? dpos : c->out_tmp) : nullptr;
-  double* dq = dQ ? (qdev ? dQ : c->out_tmp + 3 * N) : nullptr;
-  CK(adjoint(c, gU, g, dp, dq));
+  double* dp = dpos ? (pdev ? dpos : c->out_tmp + N) : nullptr;
+  double* dq = dQ ? (qdev ? dQ : c->out_tmp + 4 * N) : nullptr;
+  CK(cudaEventRecord(c->ev_fork, c->stream));
+  CK(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
+  CK(adjoint_pre(c, gU, g, c->aux_stream));
+  CK(mesh_solve(&c->solv[1], c->g64, c->lam64));
+  c->stats.adj_iterations = c->solv[1].iters;
+  c->stats.adj_rel_residual = c->solv[1].relres;
+  CK(adjoint_mid(c, c->aux_stream));
+  CK(cudaEventRecord(c->ev_join, c->aux_stream));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  CK(adjoint_final(c, gU, dp, dq, 1.0, c->stream));
   if (dpos && !pdev) {
-    int s = deliver(c, dpos, c->out_tmp, 3 * N * sizeof(double));
+    int s = deliver(c, dpos, c->out_tmp + N, 3 * N * sizeof(double));
     if (s != FEP3M_OK) return s;
   }
   if (dQ && !qdev) {
-    int s = deliver(c, dQ, c->out_tmp + 3 * N, N * sizeof(double));
+    int s = deliver(c, dQ, c->out_tmp + 4 * N, N * sizeof(double));
     if (s != FEP3M_OK) return s;
   }
   CK(cudaStreamSynchronize(c->stream));
@@ -436,12 +476,10 @@ int fep3m_solve_mesh(fep3m_ctx* c, const double* b, double* phi) {
   const int64_t nodes = (int64_t)27 * c->n * c->n * c->n;
   CK(cudaMemcpyAsync(c->g64, b, nodes * 8, is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      c->stream));
-  int it = 0, rs = 0;
-  double rel = 0;
-  CK(mesh_solve(c, c->g64, c->lam64, &it, &rel, &rs));
-  c->stats.mg_iterations = it;
-  c->stats.mg_rel_residual = rel;
-  c->stats.refine_steps = rs;
+  c->solv[0].stream = c->stream;
+  CK(mesh_solve(&c->solv[0], c->g64, c->lam64));
+  solve_stats(c);
+  const double rel = c->solv[0].relres;
   FEP3M_CL k_to_double<double><<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->lam64, c->res64, c->inv_h);
   int s = deliver(c, phi, c->res64, nodes * 8);
   if (s != FEP3M_OK) return s;

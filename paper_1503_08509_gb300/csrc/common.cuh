@@ -84,6 +84,35 @@ struct Hierarchy {
   int cheb_degree = 3;
 };
 
+// One multigrid solver instance (the context holds two, so that the forward
+// and adjoint mesh solves can run concurrently on different streams).
+struct Solver {
+  fep3m_config cfg;
+  int n = 0, precision = 0;
+  Stencils st;
+  cudaStream_t stream = nullptr;   // stream the solver's work is issued on
+  Hierarchy mg;
+  void* sb[6] = {};                // CG vectors r, z, p, q, x, rhs (working precision, fine level)
+  size_t sb_bytes = 0;
+  double* scal = nullptr;          // device scalars (64)
+  double* red_tmp = nullptr;       // reduction partials (1024)
+  unsigned int* red_counter = nullptr;
+  double* res64 = nullptr;         // FP64 refinement residual
+  // replayed solve: iteration counts calibrated on the first solve, captured as a graph
+  int plan_k = 0, plan_kin = 0, plan_kout = 0;
+  cudaGraphExec_t solve_exec = nullptr;
+  int solve_graph_kernels = 0;
+  cudaStream_t cap_stream = nullptr;
+  double* in64 = nullptr;          // solver input / output (fixed addresses for the graph)
+  double* out64 = nullptr;
+  double* host_res = nullptr;      // pinned: |Pi b|^2 and |r|^2 of a replayed solve
+  bool pending = false;            // a replayed solve whose residual is not yet checked
+  const double* pend_b = nullptr;
+  double* pend_phi = nullptr;
+  int iters = 0, refine_steps = 0;
+  double relres = 0;
+};
+
 }  // namespace fep3m
 
 struct fep3m_ctx {
@@ -126,7 +155,6 @@ struct fep3m_ctx {
   int* iflags = nullptr;         // device int flags: [0] input error, [1] converged, ...
   void* phi_mesh_T = nullptr;    // mesh potential in working precision (for the pair kernel)
   void* lam_T = nullptr;
-  fep3m::Hierarchy mg;
   // per-particle outputs, sorted order
   double* phi_s = nullptr;       // N
   double* E_s = nullptr;         // N*3 target-side gradient
@@ -140,20 +168,12 @@ struct fep3m_ctx {
   void* D_adj = nullptr;         // adjoint table-field GEMM output, chunk of offsets x n^3 (T)
   size_t D_bytes = 0;
   void* mu_v = nullptr;          // n^3 vertex adjoint (T)
-  void* sb[6] = {};              // PCG vectors r, z, p, q, x, rhs (working precision, fine level)
-  size_t sb_bytes = 0;
-  double* ap64[4] = {};          // FP64 fine-level apply intermediates (refinement residual)
-  size_t ap64_n = 0;
-  // replayed solve: iteration counts calibrated on the first solve, captured as a graph
-  int plan_k = 0, plan_kin = 0, plan_kout = 0;
-  cudaGraphExec_t solve_exec = nullptr;
-  int solve_graph_kernels = 0;
-  cudaStream_t cap_stream = nullptr;
-  double* in64 = nullptr;        // solver input / output (fixed addresses for the graph)
-  double* out64 = nullptr;
   double* red_tmp = nullptr;     // reduction partials (1024)
   unsigned int* red_counter = nullptr;
   double* out_tmp = nullptr;     // N*3 staging for host outputs
+  fep3m::Solver solv[2];          // [0] forward mesh solve, [1] adjoint mesh solve
+  cudaStream_t aux_stream = nullptr;   // adjoint chain, concurrent with the forward one
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // stats
   fep3m_stats stats;
   bool timing = false;
@@ -173,19 +193,25 @@ double estimate_lmax(const Stencils& st, int n);
 // device launches (return cudaGetLastError-style codes)
 cudaError_t bin_particles(fep3m_ctx* c, const double* pos, const double* Q, int use_fp32);
 cudaError_t assemble_forward(fep3m_ctx* c);
-cudaError_t mg_setup(fep3m_ctx* c);
-void mg_free(fep3m_ctx* c);
-void solver_free(fep3m_ctx* c);
-void solver_plan_free(fep3m_ctx* c);
+cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream);
+void solver_destroy(Solver* s);
 size_t scan_tmp_bytes(int64_t n);
 // mu = 4 pi (Mpq^T)^(x)3 lam on the vertex grid (working precision); work1/2 sized n*(3n)^2
-cudaError_t vertex_adjoint(fep3m_ctx* c, const double* lam, void* mu, void* work1, void* work2);
-// solve K phi = b (FP64 in/out, reference units); returns iterations; writes residual in scal
-cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, double* relres,
-                       int* refine_steps);
+cudaError_t vertex_adjoint(fep3m_ctx* c, const double* lam, void* mu, void* work1, void* work2, cudaStream_t s);
+// solve K phi = b (FP64 in/out, reference units) on the solver's stream; begin
+// may return before the solve has finished (a replayed graph), end waits for
+// it, checks the residual and re-solves if needed.  Results in s->iters etc.
+cudaError_t mesh_solve_begin(Solver* s, const double* b, double* phi);
+cudaError_t mesh_solve_end(Solver* s);
+cudaError_t mesh_solve(Solver* s, const double* b, double* phi);
 cudaError_t pair_prepare(fep3m_ctx* c);
 cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev3);
 cudaError_t pair_forward(fep3m_ctx* c, double* phi_out, int want_grad);
-cudaError_t adjoint(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double* dQ);
+// adjoint in three parts: weights and deposit (-> g64), the parts that need
+// lam (vertex adjoint, screen sweep, singular adjoint), and the per-charge assembly
+cudaError_t adjoint_pre(fep3m_ctx* c, double gU, const double* gphi, cudaStream_t s);
+cudaError_t adjoint_mid(fep3m_ctx* c, cudaStream_t s);
+cudaError_t adjoint_final(fep3m_ctx* c, double gU, double* dpos, double* dQ, double sign, cudaStream_t s);
 cudaError_t energy(fep3m_ctx* c, double* U_dev);
+cudaError_t sorted_charges(fep3m_ctx* c);
 }  // namespace fep3m

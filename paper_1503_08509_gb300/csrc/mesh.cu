@@ -620,16 +620,16 @@ __global__ void k_add_scaled(int64_t n, double* __restrict__ phi, const float* _
 static size_t reduce_blocks(size_t n) { return std::min<size_t>(std::max<size_t>((n + 4 * TPB - 1) / (4 * TPB), 1), 608); }
 
 template <class T>
-static void reduce(fep3m_ctx* c, int N, int mode, const T* x, const T* y, double* out) {
+static void reduce(Solver* c, int N, int mode, const T* x, const T* y, double* out) {
   size_t tot = (size_t)N * N * N;
   FEP3M_CL k_reduce<T><<<(int)reduce_blocks(tot), TPB, 0, c->stream>>>(N, mode, x, y, (double*)c->red_tmp, c->red_counter, out);
 }
 
 template <class T>
 struct MG {
-  fep3m_ctx* c;
+  Solver* c;
   Hierarchy& H;
-  explicit MG(fep3m_ctx* cc) : c(cc), H(cc->mg) {}
+  explicit MG(Solver* cc) : c(cc), H(cc->mg) {}
 
   // one fused apply; EPI_CHEB reads x and writes the new iterate to xo (xo != x)
   void apply(const Level& L, const T* x, int epi, T* out, const T* b, T* d, T* xo, T c1, T c2) {
@@ -833,7 +833,7 @@ static void upload_constants(const Stencils& st) {
   if (dev < 64) done[dev] = true;
 }
 
-cudaError_t mg_setup(fep3m_ctx* c) {
+static cudaError_t mg_setup(Solver* c) {
   upload_constants(c->st);
   Hierarchy& H = c->mg;
   const bool f32 = c->precision == FEP3M_MIXED;
@@ -905,7 +905,7 @@ cudaError_t mg_setup(fep3m_ctx* c) {
   return cudaGetLastError();
 }
 
-void mg_free(fep3m_ctx* c) {
+static void mg_free(Solver* c) {
   for (Level& L : c->mg.lv) {
     void* bufs[] = {L.x, L.b, L.r, L.d, L.t1, L.t2, L.a, L.c};
     for (void* p : bufs)
@@ -930,15 +930,13 @@ static void free_list(void** p, int k) {
     }
 }
 
-void solver_free(fep3m_ctx* c) {
+static void solver_free(Solver* c) {
   free_list(c->sb, 6);
   c->sb_bytes = 0;
-  free_list((void**)c->ap64, 4);
-  c->ap64_n = 0;
 }
 
 // PCG work vectors r, z, p, q, x, rhs in the working precision (level-0 size)
-static cudaError_t ensure_solver_buffers(fep3m_ctx* c) {
+static cudaError_t ensure_solver_buffers(Solver* c) {
   const size_t bytes = c->mg.lv[0].size * c->mg.elem_size;
   if (c->sb_bytes == bytes) return cudaSuccess;
   free_list(c->sb, 6);
@@ -950,30 +948,18 @@ static cudaError_t ensure_solver_buffers(fep3m_ctx* c) {
   return cudaSuccess;
 }
 
-// r = b - K x in FP64 on the fine level (the refinement residual), FP64 intermediates
-static cudaError_t apply64(fep3m_ctx* c, const double* x, const double* b, double* r) {
+// r = b - K x in FP64 on the fine level (the refinement residual)
+static cudaError_t apply64(Solver* c, const double* x, const double* b, double* r) {
   const Level& L0 = c->mg.lv[0];
-  if (c->ap64_n != L0.size) {
-    free_list((void**)c->ap64, 4);
-    for (int i = 0; i < 4; ++i) {
-      cudaError_t e = cudaMalloc(&c->ap64[i], L0.size * sizeof(double));
-      if (e != cudaSuccess) return e;
-    }
-    c->ap64_n = L0.size;
-  }
-  cudaStream_t s = c->stream;
   const int N = L0.N;
-  double** B = c->ap64;
-  (void)B;
-  const int fz = apply_fz(N);
-  const dim3 grid((N + FX - 1) / FX, (N + FY - 1) / FY, (N + fz - 1) / fz);
-  FEP3M_CL k_apply_fused<double, EPI_RESID><<<grid, FT, 0, s>>>(N, x, r, b, nullptr, nullptr, 0.0, 0.0);
+  const dim3 grid((N + FX - 1) / FX, (N + FY - 1) / FY, (N + FZ - 1) / FZ);
+  FEP3M_CL k_apply_fused<double, EPI_RESID><<<grid, FT, 0, c->stream>>>(N, x, r, b, nullptr, nullptr, 0.0, 0.0);
   return cudaGetLastError();
 }
 
 // host-checked solve (used once to calibrate the iteration counts, and as the
 // fallback when a replayed solve misses its tolerance)
-static cudaError_t solve_checked(fep3m_ctx* c, const double* b, double* phi, int* iters, double* relres,
+static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* iters, double* relres,
                                  int* refine_steps, int* k_inner_max) {
   void** sb = c->sb;   // r, z, p, q, x, rhs
   const Level& L0 = c->mg.lv[0];
@@ -1040,7 +1026,7 @@ static cudaError_t solve_checked(fep3m_ctx* c, const double* b, double* phi, int
 
 // fixed-count solve from c->in64 into c->out64, no host round trip; leaves
 // |Pi b|^2 in scal[10] and the final residual |r|^2 in scal[11]
-static cudaError_t solve_fixed(fep3m_ctx* c) {
+static cudaError_t solve_fixed(Solver* c) {
   void** sb = c->sb;
   const Level& L0 = c->mg.lv[0];
   const size_t n = L0.size;
@@ -1082,14 +1068,14 @@ static cudaError_t solve_fixed(fep3m_ctx* c) {
   return cudaGetLastError();
 }
 
-static void destroy_plan(fep3m_ctx* c) {
+static void destroy_plan(Solver* c) {
   if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
   c->solve_exec = nullptr;
   c->solve_graph_kernels = 0;
 }
 
 // capture solve_fixed into a graph on the library's private stream
-static cudaError_t build_plan(fep3m_ctx* c) {
+static cudaError_t build_plan(Solver* c) {
   destroy_plan(c);
   cudaStream_t user = c->stream;
   const unsigned long long l0 = g_kernel_launches;
@@ -1124,42 +1110,22 @@ static cudaError_t build_plan(fep3m_ctx* c) {
   return e;
 }
 
-cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, double* relres, int* refine_steps) {
-  cudaError_t e = ensure_solver_buffers(c);
-  if (e != cudaSuccess) return e;
-  const size_t n = c->mg.lv[0].size;
-  const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : (c->precision == FEP3M_FP64 ? 1e-13 : 1e-10);
-  if (c->solve_exec) {
-    cudaStream_t s = c->stream;
-    cudaMemcpyAsync(c->in64, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    if ((e = cudaGraphLaunch(c->solve_exec, s)) != cudaSuccess) return e;
-    g_kernel_launches += c->solve_graph_kernels;
-    cudaMemcpyAsync(phi, c->out64, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    double bb_rr[2];
-    cudaMemcpyAsync(bb_rr, c->scal + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    const double rel = bb_rr[0] > 0 ? std::sqrt(bb_rr[1] / bb_rr[0]) : 0.0;
-    if (rel <= rtol) {
-      *relres = rel;
-      *iters = c->precision == FEP3M_FP64 ? c->plan_k : c->plan_kin * c->plan_kout;
-      *refine_steps = c->precision == FEP3M_FP64 ? 0 : c->plan_kout;
-      return cudaSuccess;
-    }
-    // this right-hand side needs more iterations: one more sweep next time
-    if (c->precision == FEP3M_FP64) ++c->plan_k;
-    else ++c->plan_kout;
-    destroy_plan(c);
-  }
+static double solver_rtol(const Solver* c) {
+  return c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : (c->precision == FEP3M_FP64 ? 1e-13 : 1e-10);
+}
+
+// synchronous calibrated solve; records the counts and captures the replay graph
+static cudaError_t solve_calibrate(Solver* c, const double* b, double* phi) {
   int kin = 0;
-  e = solve_checked(c, b, phi, iters, relres, refine_steps, &kin);
-  if (e != cudaSuccess || *relres > rtol) return e;
-  // forward and adjoint solves share the plan: keep the larger counts
+  cudaError_t e = solve_checked(c, b, phi, &c->iters, &c->relres, &c->refine_steps, &kin);
+  if (e != cudaSuccess || c->relres > solver_rtol(c)) return e;
   if (c->precision == FEP3M_FP64) {
-    c->plan_k = std::max(c->plan_k, *iters);
+    c->plan_k = std::max(c->plan_k, c->iters);
   } else {
     c->plan_kin = std::max(c->plan_kin, kin);
-    c->plan_kout = std::max(c->plan_kout, *refine_steps);
+    c->plan_kout = std::max(c->plan_kout, c->refine_steps);
   }
+  const size_t n = c->mg.lv[0].size;
   if (!c->in64 && (e = cudaMalloc(&c->in64, n * sizeof(double))) != cudaSuccess) return e;
   if (!c->out64 && (e = cudaMalloc(&c->out64, n * sizeof(double))) != cudaSuccess) return e;
   if (!c->cap_stream && (e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -1168,13 +1134,88 @@ cudaError_t mesh_solve(fep3m_ctx* c, const double* b, double* phi, int* iters, d
   return cudaSuccess;
 }
 
-void solver_plan_free(fep3m_ctx* c) {
+cudaError_t mesh_solve_begin(Solver* c, const double* b, double* phi) {
+  cudaError_t e = ensure_solver_buffers(c);
+  if (e != cudaSuccess) return e;
+  c->pending = false;
+  if (!c->solve_exec) return solve_calibrate(c, b, phi);
+  const size_t n = c->mg.lv[0].size;
+  cudaStream_t s = c->stream;
+  cudaMemcpyAsync(c->in64, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if ((e = cudaGraphLaunch(c->solve_exec, s)) != cudaSuccess) return e;
+  g_kernel_launches += c->solve_graph_kernels;
+  cudaMemcpyAsync(phi, c->out64, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(c->host_res, c->scal + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  c->pending = true;
+  c->pend_b = b;
+  c->pend_phi = phi;
+  return cudaGetLastError();
+}
+
+cudaError_t mesh_solve_end(Solver* c) {
+  if (!c->pending) return cudaSuccess;
+  c->pending = false;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return e;
+  const double bb = c->host_res[0], rr = c->host_res[1];
+  const double rel = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  if (rel <= solver_rtol(c)) {
+    c->relres = rel;
+    c->iters = c->precision == FEP3M_FP64 ? c->plan_k : c->plan_kin * c->plan_kout;
+    c->refine_steps = c->precision == FEP3M_FP64 ? 0 : c->plan_kout;
+    return cudaSuccess;
+  }
+  // this right-hand side needs more iterations: one more sweep from now on
+  if (c->precision == FEP3M_FP64) ++c->plan_k;
+  else ++c->plan_kout;
+  destroy_plan(c);
+  return solve_calibrate(c, c->pend_b, c->pend_phi);
+}
+
+cudaError_t mesh_solve(Solver* c, const double* b, double* phi) {
+  cudaError_t e = mesh_solve_begin(c, b, phi);
+  if (e != cudaSuccess) return e;
+  return mesh_solve_end(c);
+}
+
+static void solver_plan_free(Solver* c) {
   destroy_plan(c);
   if (c->in64) cudaFree(c->in64);
   if (c->out64) cudaFree(c->out64);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->in64 = c->out64 = nullptr;
   c->cap_stream = nullptr;
+}
+
+cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream) {
+  s->cfg = c->cfg;
+  s->n = c->n;
+  s->precision = c->precision;
+  s->st = c->st;
+  s->stream = stream;
+  const size_t nodes = (size_t)27 * c->n * c->n * c->n;
+  cudaError_t e;
+  if ((e = cudaMalloc(&s->scal, 64 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&s->red_tmp, 1024 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&s->red_counter, sizeof(unsigned int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&s->res64, nodes * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&s->host_res, 2 * sizeof(double))) != cudaSuccess) return e;
+  cudaMemset(s->red_counter, 0, sizeof(unsigned int));
+  cudaMemset(s->scal, 0, 64 * sizeof(double));
+  return mg_setup(s);
+}
+
+void solver_destroy(Solver* s) {
+  solver_plan_free(s);
+  mg_free(s);
+  solver_free(s);
+  if (s->scal) cudaFree(s->scal);
+  if (s->red_tmp) cudaFree(s->red_tmp);
+  if (s->red_counter) cudaFree(s->red_counter);
+  if (s->res64) cudaFree(s->res64);
+  if (s->host_res) cudaFreeHost(s->host_res);
+  s->scal = s->red_tmp = s->res64 = s->host_res = nullptr;
+  s->red_counter = nullptr;
 }
 
 cudaError_t assemble_forward(fep3m_ctx* c) {
@@ -1223,9 +1264,8 @@ __global__ void k_mpqT_axis(int axis, int n, int e0, int e1, int e2, const doubl
   out[g] = (T)(scale * acc);
 }
 
-cudaError_t vertex_adjoint(fep3m_ctx* c, const double* lam, void* mu, void* work1, void* work2) {
+cudaError_t vertex_adjoint(fep3m_ctx* c, const double* lam, void* mu, void* work1, void* work2, cudaStream_t s) {
   const int n = c->n, N = 3 * n;
-  cudaStream_t s = c->stream;
   if (c->precision == FEP3M_MIXED) {
     FEP3M_CL k_mpqT_axis<float><<<grid_for((size_t)n * N * N), TPB, 0, s>>>(0, n, n, N, N, lam, nullptr, (float*)work1, 1.0);
     FEP3M_CL k_mpqT_axis<float><<<grid_for((size_t)n * n * N), TPB, 0, s>>>(1, n, n, n, N, nullptr, (float*)work1, (float*)work2, 1.0);

@@ -735,7 +735,8 @@ __global__ void __launch_bounds__(PT) k_pair_adj_warp(int64_t N, int n, int n_sr
 
 // per charge: dLf/dQ and dLf/dx from the pieces (see fep3m_vjp)
 template <class T>
-__global__ void k_final(int64_t N, int n, double inv_h, double gU, const typename vec4<T>::type* __restrict__ part,
+__global__ void k_final(int64_t N, int n, double inv_h, double gU, double sign,
+                        const typename vec4<T>::type* __restrict__ part,
                         const int* __restrict__ perm, const int* __restrict__ cell, const double* __restrict__ w,
                         const double* __restrict__ phi_s, const double* __restrict__ E_s,
                         const double* __restrict__ psi, const double* __restrict__ gpsi, const T* __restrict__ mu,
@@ -762,9 +763,9 @@ __global__ void k_final(int64_t N, int n, double inv_h, double gU, const typenam
   const double wt = w[t];
   if (dQ) dQ[i] = 0.5 * gU * phi_s[t] + psi[t] + sQ;
   if (dpos) {
-    dpos[3 * i + 0] = wt * E_s[3 * t + 0] + Q * (gpsi[3 * t + 0] + gx * inv_h);
-    dpos[3 * i + 1] = wt * E_s[3 * t + 1] + Q * (gpsi[3 * t + 1] + gy * inv_h);
-    dpos[3 * i + 2] = wt * E_s[3 * t + 2] + Q * (gpsi[3 * t + 2] + gz * inv_h);
+    dpos[3 * i + 0] = sign * (wt * E_s[3 * t + 0] + Q * (gpsi[3 * t + 0] + gx * inv_h));
+    dpos[3 * i + 1] = sign * (wt * E_s[3 * t + 1] + Q * (gpsi[3 * t + 1] + gy * inv_h));
+    dpos[3 * i + 2] = sign * (wt * E_s[3 * t + 2] + Q * (gpsi[3 * t + 2] + gz * inv_h));
   }
 }
 
@@ -863,16 +864,19 @@ cudaError_t pair_forward(fep3m_ctx* c, double* phi_out, int want_grad) {
                    : launch_pair_brick<double, false>(c, c->phi64, c->Hw64, phi_out);
 }
 
-cudaError_t energy(fep3m_ctx* c, double* U_dev) {
-  cudaStream_t s = c->stream;
+cudaError_t sorted_charges(fep3m_ctx* c) {
   const int64_t N = c->N;
-  // charges in sorted order (FP64 copy)
   if (c->precision == FEP3M_MIXED)
-    FEP3M_CL k_charges<float><<<gsz(N), PT, 0, s>>>(N, (const float4*)c->part, c->Q_s);
+    FEP3M_CL k_charges<float><<<gsz(N), PT, 0, c->stream>>>(N, (const float4*)c->part, c->Q_s);
   else
-    FEP3M_CL k_charges<double><<<gsz(N), PT, 0, s>>>(N, (const vec4<double>::type*)c->part, c->Q_s);
+    FEP3M_CL k_charges<double><<<gsz(N), PT, 0, c->stream>>>(N, (const vec4<double>::type*)c->part, c->Q_s);
+  return cudaGetLastError();
+}
+
+cudaError_t energy(fep3m_ctx* c, double* U_dev) {
+  const int64_t N = c->N;
   const int nb = (int)std::min<int64_t>(std::max<int64_t>(gsz(N), 1), 1024);
-  FEP3M_CL k_energy<<<nb, PT, 0, s>>>(N, c->Q_s, c->phi_s, (double*)c->red_tmp, c->red_counter, U_dev);
+  FEP3M_CL k_energy<<<nb, PT, 0, c->stream>>>(N, c->Q_s, c->phi_s, (double*)c->red_tmp, c->red_counter, U_dev);
   return cudaGetLastError();
 }
 
@@ -903,56 +907,61 @@ static cudaError_t screen_adjoint(fep3m_ctx* c, const T* W, const T* Hw, T* A) {
   return cudaGetLastError();
 }
 
-cudaError_t adjoint(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double* dQ) {
+// weights w = gU Q / 2 + gphi (sorted order), element deposits, adjoint right-hand side g64
+cudaError_t adjoint_pre(fep3m_ctx* c, double gU, const double* gphi, cudaStream_t s) {
   const int n = c->n;
   const int64_t ne = (int64_t)n * n * n, nodes = 27 * ne, N = c->N;
-  cudaStream_t s = c->stream;
-  const bool f32 = c->precision == FEP3M_MIXED;
-  // weights w = gU Q / 2 + gphi (sorted order)
-  if (f32)
-    FEP3M_CL k_charges<float><<<gsz(N), PT, 0, s>>>(N, (const float4*)c->part, c->Q_s);
-  else
-    FEP3M_CL k_charges<double><<<gsz(N), PT, 0, s>>>(N, (const vec4<double>::type*)c->part, c->Q_s);
   FEP3M_CL k_weights<<<gsz(N), PT, 0, s>>>(N, gU, gphi, c->perm, c->Q_s, c->w_s);
-  // element deposits and the adjoint right-hand side on the order-3 nodes
   const int per = PT / 64;
-  if (f32) {
+  if (c->precision == FEP3M_MIXED) {
     FEP3M_CL k_elem_deposit<float><<<gsz(ne, per), PT, 0, s>>>(ne, c->start, c->count, (const float4*)c->part, c->w_s,
                                                       (float*)c->W_el);
     FEP3M_CL k_node_assemble<float><<<gsz(nodes), PT, 0, s>>>(n, (const float*)c->W_el, c->g64);
   } else {
-    FEP3M_CL k_elem_deposit<double><<<gsz(ne, per), PT, 0, s>>>(ne, c->start, c->count, (const vec4<double>::type*)c->part, c->w_s,
-                                                       (double*)c->W_el);
+    FEP3M_CL k_elem_deposit<double><<<gsz(ne, per), PT, 0, s>>>(ne, c->start, c->count, (const vec4<double>::type*)c->part,
+                                                       c->w_s, (double*)c->W_el);
     FEP3M_CL k_node_assemble<double><<<gsz(nodes), PT, 0, s>>>(n, (const double*)c->W_el, c->g64);
   }
-  cudaError_t e = cudaGetLastError();
+  return cudaGetLastError();
+}
+
+// the parts that need lam: vertex adjoint mu, screen sweep A, singular adjoint potential
+cudaError_t adjoint_mid(fep3m_ctx* c, cudaStream_t s) {
+  const int n = c->n;
+  const int64_t N = c->N;
+  const fep3m::Level& L0 = c->solv[1].mg.lv[0];
+  cudaError_t e = vertex_adjoint(c, c->lam64, c->mu_v, L0.t1, L0.t2, s);
   if (e != cudaSuccess) return e;
-  // lam = S g with the same solver (S is symmetric)
-  int it = 0, rs = 0;
-  double rel = 0;
-  e = mesh_solve(c, c->g64, c->lam64, &it, &rel, &rs);
-  if (e != cudaSuccess) return e;
-  c->stats.adj_iterations = it;
-  c->stats.adj_rel_residual = rel;
-  // mu on the vertices (work buffers: the level-0 apply intermediates are large enough)
-  e = vertex_adjoint(c, c->lam64, c->mu_v, c->mg.lv[0].t1, c->mg.lv[0].t2);
-  if (e != cudaSuccess) return e;
-  if (f32) {
-    if ((e = screen_adjoint<float>(c, (const float*)c->W_el, c->Hw32, (float*)c->A_el)) != cudaSuccess) return e;
-    FEP3M_CL k_pair_adj_warp<float><<<(unsigned)((N + 7) / 8), PT, 0, s>>>(N, n, c->n_sr, (float)c->h, c->start,
-                                                       (const float4*)c->part, c->ecoord, c->w_s, c->psi_s, c->gpsi_s);
-    FEP3M_CL k_final<float><<<gsz(N), PT, 0, s>>>(N, n, c->inv_h, gU, (const float4*)c->part, c->perm, c->cell, c->w_s,
-                                         c->phi_s, c->E_s, c->psi_s, c->gpsi_s, (const float*)c->mu_v,
-                                         (const float*)c->A_el, dpos, dQ);
+  cudaStream_t keep = c->stream;
+  c->stream = s;   // screen_adjoint issues on c->stream
+  if (c->precision == FEP3M_MIXED) {
+    e = screen_adjoint<float>(c, (const float*)c->W_el, c->Hw32, (float*)c->A_el);
+    if (e == cudaSuccess)
+      FEP3M_CL k_pair_adj_warp<float><<<(unsigned)((N + 7) / 8), PT, 0, s>>>(N, n, c->n_sr, (float)c->h, c->start,
+                                                         (const float4*)c->part, c->ecoord, c->w_s, c->psi_s, c->gpsi_s);
   } else {
-    if ((e = screen_adjoint<double>(c, (const double*)c->W_el, c->Hw64, (double*)c->A_el)) != cudaSuccess) return e;
-    FEP3M_CL k_pair_adj_warp<double><<<(unsigned)((N + 7) / 8), PT, 0, s>>>(N, n, c->n_sr, c->h, c->start,
-                                                        (const vec4<double>::type*)c->part, c->ecoord, c->w_s,
-                                                        c->psi_s, c->gpsi_s);
-    FEP3M_CL k_final<double><<<gsz(N), PT, 0, s>>>(N, n, c->inv_h, gU, (const vec4<double>::type*)c->part, c->perm, c->cell, c->w_s,
-                                          c->phi_s, c->E_s, c->psi_s, c->gpsi_s, (const double*)c->mu_v,
-                                          (const double*)c->A_el, dpos, dQ);
+    e = screen_adjoint<double>(c, (const double*)c->W_el, c->Hw64, (double*)c->A_el);
+    if (e == cudaSuccess)
+      FEP3M_CL k_pair_adj_warp<double><<<(unsigned)((N + 7) / 8), PT, 0, s>>>(N, n, c->n_sr, c->h, c->start,
+                                                          (const vec4<double>::type*)c->part, c->ecoord, c->w_s,
+                                                          c->psi_s, c->gpsi_s);
   }
+  c->stream = keep;
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// per-charge dLf/dx (times sign) and dLf/dQ
+cudaError_t adjoint_final(fep3m_ctx* c, double gU, double* dpos, double* dQ, double sign, cudaStream_t s) {
+  const int64_t N = c->N;
+  if (c->precision == FEP3M_MIXED)
+    FEP3M_CL k_final<float><<<gsz(N), PT, 0, s>>>(N, c->n, c->inv_h, gU, sign, (const float4*)c->part, c->perm, c->cell,
+                                         c->w_s, c->phi_s, c->E_s, c->psi_s, c->gpsi_s, (const float*)c->mu_v,
+                                         (const float*)c->A_el, dpos, dQ);
+  else
+    FEP3M_CL k_final<double><<<gsz(N), PT, 0, s>>>(N, c->n, c->inv_h, gU, sign, (const vec4<double>::type*)c->part, c->perm,
+                                          c->cell, c->w_s, c->phi_s, c->E_s, c->psi_s, c->gpsi_s,
+                                          (const double*)c->mu_v, (const double*)c->A_el, dpos, dQ);
   return cudaGetLastError();
 }
 
