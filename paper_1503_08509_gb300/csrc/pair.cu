@@ -34,7 +34,11 @@ __device__ __forceinline__ int wrapn(int i, int n) {
 
 template <class T> __device__ __forceinline__ T rsq(T x);
 template <> __device__ __forceinline__ double rsq<double>(double x) { return 1.0 / sqrt(x); }
-template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+// the hardware reciprocal square root refined by one Newton step, y (3 - x y^2) / 2
+template <> __device__ __forceinline__ float rsq<float>(float x) {
+  const float y = rsqrtf(x);
+  return y * fmaf(-0.5f * x, y * y, 1.5f);
+}
 
 // compensated (Kahan) accumulator; FP64 uses plain sums
 template <class T> struct Acc {
@@ -490,6 +494,393 @@ __global__ void __launch_bounds__(PT) k_pair_brick(int n, int n_sr, T h, T inv_h
   }
 }
 
+// ------------------------------------------------------------------- v3
+// Same decomposition as k_pair_brick, with two changes:
+//  * the vertex amplitudes come from an "extended vertex field" R built once
+//    per brick: per axis SW = 3 BX + 2 n_sr - 1 slots, the first SF = BX + 2 n_sr - 1
+//    the full vertex densities of the vertices interior offsets reach, then BX
+//    slots of corner-1-only sums (offset -(n_sr+1), vertex e + n_sr + 1) and BX
+//    of corner-0-only sums (offset n_sr, vertex e - n_sr).  A(e, o) is then the
+//    single value R[beta(o) + lambda(e)];
+//  * the charges of the brick's halo elements are staged in shared memory
+//    (when they fit) and each target's singular sum walks its 343 elements
+//    there; otherwise the row-run walk over global memory is used.
+template <class T>
+struct Pair3Smem {
+  __host__ __device__ static int SW(int n_sr) { return 3 * BX + 2 * n_sr - 1; }
+  __host__ __device__ static int HW(int n_sr) { return BX + 2 * n_sr; }
+  __host__ __device__ static size_t region1(int n_sr) {
+    const int sw = SW(n_sr);
+    const size_t r = (size_t)sw * sw * sw * sizeof(T);
+    const size_t runs = (size_t)8 * (2 * MAXRUN + MAXRUN + 1) * sizeof(int);
+    return (((r > runs ? r : runs) + 15) / 16) * 16;
+  }
+  // charges that can be staged: region 1 holds R first, then the charges
+  __host__ __device__ static int cap(int n_sr) { return (int)(region1(n_sr) / sizeof(typename vec4<T>::type)); }
+  static size_t bytes(int n_sr) {
+    const int hw = HW(n_sr);
+    const int noff = 2 * n_sr + 2, nb = 2 * n_sr + 1, sw = SW(n_sr);
+    const size_t ints = (size_t)hw * hw * hw + 1 + BE + 1 + 1 + PT / 32 + 1 + (size_t)noff * noff * noff +
+                        2 * (size_t)nb * nb * nb + 3 * sw + 3 * hw + 32;
+    return region1(n_sr) + 2 * (size_t)OCH * 64 * sizeof(T) + ints * sizeof(int);
+  }
+};
+
+// exclusive scan of one int per thread over the block (PT threads); returns the
+// thread's prefix and writes the total to *total
+__device__ __forceinline__ int block_scan_excl(int v, int* wsum /* PT/32 + 1 */, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0;
+    for (int w = 0; w < PT / 32; ++w) {
+      const int t = wsum[w];
+      wsum[w] = a;
+      a += t;
+    }
+    wsum[PT / 32] = a;
+  }
+  __syncthreads();
+  const int res = wsum[wid] + x - v;
+  *total = wsum[PT / 32];
+  __syncthreads();
+  return res;
+}
+
+template <class T, bool GRAD>
+__global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_h, const int* __restrict__ start,
+                                                    const int* __restrict__ count,
+                                                    const typename vec4<T>::type* __restrict__ part,
+                                                    const int* __restrict__ ecoord, const T* __restrict__ C,
+                                                    const T* __restrict__ rv, const T* __restrict__ phi_mesh,
+                                                    const T* __restrict__ Hw, const int* __restrict__ perm,
+                                                    double* __restrict__ phi_s, double* __restrict__ E_s,
+                                                    double* __restrict__ phi_out) {
+  typedef typename vec4<T>::type V4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nbx = (n + BX - 1) / BX, nby = (n + BY - 1) / BY;
+  const int E0x = (blockIdx.x % nbx) * BX, E0y = ((blockIdx.x / nbx) % nby) * BY, E0z = (blockIdx.x / (nbx * nby)) * BZ;
+  const int keep = n_sr + 1, noff = 2 * n_sr + 2, no3 = noff * noff * noff;
+  const int SW = 3 * BX + 2 * n_sr - 1, SF = BX + 2 * n_sr - 1, HW = BX + 2 * n_sr;
+  const int nb = 2 * n_sr + 1, nb3 = nb * nb * nb;
+  const size_t r1 = Pair3Smem<T>::region1(n_sr);
+  T* R = (T*)smem_raw;                                    // region 1: R, later the staged charges
+  V4* stg = (V4*)smem_raw;
+  int* runs_all = (int*)smem_raw;                         // (fallback) region 1 as run tables
+  T* A_c = (T*)(smem_raw + r1);                           // [OCH][64], then G [64][64] with H_c
+  T* H_c = A_c + OCH * 64;
+  int* hs = (int*)(H_c + OCH * 64);                       // halo element prefix, HW^3 + 1
+  int* epre = hs + HW * HW * HW + 1;                      // BE + 1
+  int* flag = epre + BE + 1;
+  int* wsum = flag + 1;                                   // PT/32 + 1 scan scratch
+  int* otab = wsum + PT / 32 + 1;                         // no3: R base index of each offset
+  int* dtab = otab + no3;                                 // nb3: halo offset of each block element
+  int* dpk = dtab + nb3;                                  // nb3: packed (dx, dy, dz) + n_sr
+  int* wv = dpk + nb3;                                    // 3 x SW wrapped vertex coords
+  int* we = wv + 3 * SW;                                  // 3 x HW wrapped halo element coords
+  const int tid = threadIdx.x;
+  int ntarget;
+  {
+    int c0 = 0;
+    if (tid < BE) {
+      const int lx = E0x + (tid % BX), ly = E0y + (tid / BX) % BY, lz = E0z + tid / (BX * BY);
+      if (lx < n && ly < n && lz < n) c0 = count[lx + (int64_t)n * (ly + (int64_t)n * lz)];
+    }
+    const int pre = block_scan_excl(c0, wsum, &ntarget);
+    if (tid < BE) epre[tid] = pre;
+    if (tid == 0) epre[BE] = ntarget;
+  }
+  if (ntarget == 0) return;
+  // index tables (no divisions in the hot loops below)
+  for (int o = tid; o < no3; o += PT) {
+    const int ox = o % noff - keep, oy = (o / noff) % noff - keep, oz = o / (noff * noff) - keep;
+    const int bx = ox == -keep ? SF : (ox == n_sr ? SF + BX : n_sr - 1 - ox);
+    const int by = oy == -keep ? SF : (oy == n_sr ? SF + BX : n_sr - 1 - oy);
+    const int bz = oz == -keep ? SF : (oz == n_sr ? SF + BX : n_sr - 1 - oz);
+    otab[o] = bx + SW * (by + SW * bz);
+  }
+  for (int d = tid; d < nb3; d += PT) {
+    const int dx = d % nb, dy = (d / nb) % nb, dz = d / (nb * nb);
+    dtab[d] = dx + HW * (dy + HW * dz);
+    dpk[d] = dx | (dy << 8) | (dz << 16);
+  }
+  {
+    const int E0[3] = {E0x, E0y, E0z};
+    for (int i = tid; i < 3 * SW; i += PT) {
+      const int a = i / SW, sa = i % SW;
+      int v;
+      if (sa < SF) v = E0[a] + sa - (n_sr - 1);
+      else if (sa < SF + BX) v = E0[a] + (sa - SF) + keep;
+      else v = E0[a] + (sa - SF - BX) - n_sr;
+      wv[i] = wrapn(v, n);
+    }
+    for (int i = tid; i < 3 * HW; i += PT) {
+      const int a = i / HW, ha = i % HW;
+      we[i] = wrapn(E0[a] - n_sr + ha, n);
+    }
+  }
+  __syncthreads();
+  // (1) extended vertex field
+  for (int i = tid; i < SW * SW * SW; i += PT) {
+    const int sx = i % SW, sy = (i / SW) % SW, sz = i / (SW * SW);
+    const int tx = sx < SF ? 3 : (sx < SF + BX ? 2 : 1);     // allowed corners (bit0: 0, bit1: 1)
+    const int ty = sy < SF ? 3 : (sy < SF + BX ? 2 : 1);
+    const int tz = sz < SF ? 3 : (sz < SF + BX ? 2 : 1);
+    const int vx = wv[sx], vy = wv[SW + sy], vz = wv[2 * SW + sz];
+    T val = T(0);
+    if ((tx & ty & tz) == 3) {
+      val = rv[vx + (int64_t)n * (vy + (int64_t)n * vz)];
+    } else {
+      const int vxm = vx == 0 ? n - 1 : vx - 1, vym = vy == 0 ? n - 1 : vy - 1, vzm = vz == 0 ? n - 1 : vz - 1;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
+        if (!((tx >> kx) & 1) || !((ty >> ky) & 1) || !((tz >> kz) & 1)) continue;
+        const int ex = kx ? vxm : vx, ey = ky ? vym : vy, ez = kz ? vzm : vz;
+        val += C[(ex + (int64_t)n * (ey + (int64_t)n * ez)) * 8 + k];
+      }
+    }
+    R[i] = val;
+  }
+  // (2) screen field: 4 x 4 register tile, per-chunk partial sums added into a total
+  const int eb = tid >> 4, mb = tid & 15;
+  T acc[4][4], tot[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tot[i][j] = T(0);
+  // this thread stages entries i = tid + k PT: element l = i & 63 is fixed per thread
+  const int lst = tid & 63;
+  const int lam = (lst % BX) + SW * (((lst / BX) % BY) + SW * (lst / (BX * BY)));
+  constexpr int SPT = OCH * 64 / PT;   // staged entries per thread per chunk
+  T hpf[SPT];                          // next chunk's table values, fetched during this chunk
+#pragma unroll
+  for (int k = 0; k < SPT; ++k) {
+    const int i = tid + k * PT, o = i >> 6;
+    hpf[k] = o < no3 ? Hw[(int64_t)o * 64 + (i & 63)] : T(0);
+  }
+  for (int o0 = 0; o0 < no3; o0 += OCH) {
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+      const int i = tid + k * PT;
+      const int o = o0 + (i >> 6);
+      H_c[i] = hpf[k];
+      A_c[i] = o < no3 ? R[otab[o] + lam] : T(0);
+    }
+    __syncthreads();
+    if (o0 + OCH < no3) {
+#pragma unroll
+      for (int k = 0; k < SPT; ++k) {
+        const int i = tid + k * PT, o = o0 + OCH + (i >> 6);
+        hpf[k] = o < no3 ? Hw[(int64_t)o * 64 + (i & 63)] : T(0);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+#pragma unroll 4
+    for (int oi = 0; oi < OCH; ++oi) {
+      T a[4], hh[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = A_c[oi * 64 + 4 * eb + i];
+        hh[i] = H_c[oi * 64 + 4 * mb + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * hh[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j];
+  }
+  __syncthreads();
+  T* G = A_c;
+  {
+    const int N = 3 * n;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int l = 4 * eb + i;
+      const int ex = E0x + l % BX, ey = E0y + (l / BX) % BY, ez = E0z + l / (BX * BY);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int m = 4 * mb + j, mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
+        T val = T(0);
+        if (ex < n && ey < n && ez < n) {
+          const int gx = 3 * ex + mx, gy = 3 * ey + my, gz = 3 * ez + mz;   // < 3n + 3
+          val = phi_mesh[(gx >= N ? gx - N : gx) + (int64_t)N * ((gy >= N ? gy - N : gy) + (int64_t)N * (gz >= N ? gz - N : gz))] -
+                tot[i][j];
+        }
+        G[l * 64 + m] = val;
+      }
+    }
+  }
+  // (3) stage the halo charges if they fit (region 1 is free now)
+  const int nh = HW * HW * HW;
+  {
+    const int per = (nh + PT - 1) / PT, i0 = tid * per;
+    int cnt[8], gid[8];   // per <= 8 for n_sr <= 4 (nh <= 1728)
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = i0 + k;
+      cnt[k] = 0;
+      gid[k] = 0;
+      if (k < per && i < nh) {
+        const int hx = i % HW, hy = (i / HW) % HW, hz = i / (HW * HW);
+        gid[k] = we[hx] + n * (we[HW + hy] + n * we[2 * HW + hz]);
+        cnt[k] = count[gid[k]];
+      }
+      sum += cnt[k];
+    }
+    int total;
+    int run = block_scan_excl(sum, wsum, &total);
+    const bool fits = total <= Pair3Smem<T>::cap(n_sr);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = i0 + k;
+      if (k < per && i < nh) {
+        hs[i] = run;
+        if (fits) {
+          const int j0 = start[gid[k]];
+          for (int q = 0; q < cnt[k]; ++q) stg[run + q] = part[j0 + q];
+        }
+      }
+      run += cnt[k];
+    }
+    if (tid == 0) {
+      hs[nh] = total;
+      flag[0] = fits;
+    }
+  }
+  __syncthreads();
+  const bool staged = flag[0] != 0;
+  // (4) four threads per target: each takes 16 of the 64 nodes and a quarter
+  // of the block's elements; a two-step shuffle combines the quarters
+  const int q = tid & 3;
+  const int d0 = (q * nb3) / 4, d1 = ((q + 1) * nb3) / 4;
+  for (int tb = 0; tb < ntarget; tb += PT / 4) {
+    const int k = tb + (tid >> 2);
+    const bool valid = k < ntarget;
+    T v8[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v8[i] = T(0);
+    int slot = 0;
+    if (valid) {
+      int lo = 0, hi2 = BE;                 // element of target k: epre[l] <= k < epre[l + 1]
+      while (hi2 - lo > 1) {
+        const int mid = (lo + hi2) >> 1;
+        if (epre[mid] <= k) lo = mid;
+        else hi2 = mid;
+      }
+      const int l = lo;
+      const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
+      const int ex = E0x + lx, ey = E0y + ly, ez = E0z + lz;
+      const int kk = k - epre[l];
+      slot = start[ex + (int64_t)n * (ey + (int64_t)n * ez)] + kk;
+      const V4 pt = part[slot];
+      T ux[4], uy[4], uz[4], dx4[4], dy4[4], dz4[4];
+      q3_values<T>(pt.x, ux);
+      q3_values<T>(pt.y, uy);
+      q3_values<T>(pt.z, uz);
+      if (GRAD) {
+        q3_derivs<T>(pt.x, dx4);
+        q3_derivs<T>(pt.y, dy4);
+        q3_derivs<T>(pt.z, dz4);
+      }
+      // nodes 16 q .. 16 q + 15: mz = q, (mx, my) over 4 x 4
+#pragma unroll
+      for (int my = 0; my < 4; ++my)
+#pragma unroll
+        for (int mx = 0; mx < 4; ++mx) {
+          const T g = G[l * 64 + 16 * q + 4 * my + mx];
+          const T wyz = uy[my] * uz[q];
+          v8[0] += g * ux[mx] * wyz;
+          if (GRAD) {
+            v8[1] += g * dx4[mx] * wyz;
+            v8[2] += g * ux[mx] * dy4[my] * uz[q];
+            v8[3] += g * ux[mx] * uy[my] * dz4[q];
+          }
+        }
+      const int base = lx + HW * (ly + HW * lz);          // halo index of block offset (-n_sr, -n_sr, -n_sr)
+      Acc<T> ps, fx, fy, fz;
+      if (staged) {
+        const int self = hs[base + n_sr * (1 + HW + HW * HW)] + kk;
+        for (int d = d0; d < d1; ++d) {
+          const int hidx = base + dtab[d];
+          const int pk = dpk[d];
+          const T ddx = T((pk & 255) - n_sr), ddy = T(((pk >> 8) & 255) - n_sr), ddz = T((pk >> 16) - n_sr);
+          const int j1 = hs[hidx + 1];
+          for (int j = hs[hidx]; j < j1; ++j) {
+            if (j == self) continue;
+            const V4 pj = stg[j];
+            const T rx = (ddx + (pj.x - pt.x)) * h, ry = (ddy + (pj.y - pt.y)) * h, rz = (ddz + (pj.z - pt.z)) * h;
+            const T ir = rsq<T>(rx * rx + ry * ry + rz * rz);
+            ps.add(pj.w * ir);
+            if (GRAD) {
+              const T f3 = pj.w * ir * ir * ir;
+              fx.add(f3 * rx);
+              fy.add(f3 * ry);
+              fz.add(f3 * rz);
+            }
+          }
+        }
+      } else {
+        for (int d = d0; d < d1; ++d) {
+          const int pk = dpk[d];
+          const int ax = pk & 255, ay = (pk >> 8) & 255, az = pk >> 16;   // 0 .. 2 n_sr
+          const int64_t g = we[lx + ax] + (int64_t)n * (we[HW + ly + ay] + (int64_t)n * we[2 * HW + lz + az]);
+          const T ddx = T(ax - n_sr), ddy = T(ay - n_sr), ddz = T(az - n_sr);
+          const int j0 = start[g], j1 = j0 + count[g];
+          for (int j = j0; j < j1; ++j) {
+            if (j == slot) continue;
+            const V4 pj = part[j];
+            const T rx = (ddx + (pj.x - pt.x)) * h, ry = (ddy + (pj.y - pt.y)) * h, rz = (ddz + (pj.z - pt.z)) * h;
+            const T ir = rsq<T>(rx * rx + ry * ry + rz * rz);
+            ps.add(pj.w * ir);
+            if (GRAD) {
+              const T f3 = pj.w * ir * ir * ir;
+              fx.add(f3 * rx);
+              fy.add(f3 * ry);
+              fz.add(f3 * rz);
+            }
+          }
+        }
+      }
+      v8[4] = ps.get();
+      v8[5] = fx.get();
+      v8[6] = fy.get();
+      v8[7] = fz.get();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      v8[i] += __shfl_xor_sync(0xffffffffu, v8[i], 1);
+      v8[i] += __shfl_xor_sync(0xffffffffu, v8[i], 2);
+    }
+    if (valid && q == 0) {
+      const double phi = (double)v8[0] * (double)inv_h + (double)v8[4];
+      phi_s[slot] = phi;
+      if (phi_out) phi_out[perm[slot]] = phi;
+      if (GRAD) {
+        const double ih2 = (double)inv_h * (double)inv_h;
+        E_s[3 * slot + 0] = (double)v8[1] * ih2 + (double)v8[5];
+        E_s[3 * slot + 1] = (double)v8[2] * ih2 + (double)v8[6];
+        E_s[3 * slot + 2] = (double)v8[3] * ih2 + (double)v8[7];
+      }
+    }
+  }
+}
+
 // ----------------------------------------------------------------- adjoint
 __global__ void k_weights(int64_t N, double gU, const double* __restrict__ gphi, const int* __restrict__ perm,
                           const double* __restrict__ Qs, double* __restrict__ w) {
@@ -844,8 +1235,8 @@ template <class T, bool GRAD>
 static cudaError_t launch_pair_brick(fep3m_ctx* c, const T* phi_mesh, const T* Hw, double* phi_out) {
   const int n = c->n;
   const int nbx = (n + BX - 1) / BX, nby = (n + BY - 1) / BY, nbz = (n + BZ - 1) / BZ;
-  const size_t smem = PairSmem<T>::bytes(c->n_sr);
-  auto kern = k_pair_brick<T, GRAD>;
+  const size_t smem = Pair3Smem<T>::bytes(c->n_sr);
+  auto kern = k_pair_brick3<T, GRAD>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   FEP3M_CL kern<<<(unsigned)(nbx * nby * nbz), PT, smem, c->stream>>>(
