@@ -225,7 +225,6 @@ template <class T, int EPI>
 __global__ void __launch_bounds__(FT) k_apply_fused(int N, const T* __restrict__ x, T* __restrict__ out,
                                                     const T* __restrict__ b, T* __restrict__ d,
                                                     T* __restrict__ xo, T c1, T c2) {
-  __shared__ T ring[7][HPS];
   __shared__ T t1s[HPS], t2s[HPS];
   __shared__ T as_[FY][HXS], cs_[FY][HXS];
   const int64_t NN = (int64_t)N * N;
@@ -245,40 +244,26 @@ __global__ void __launch_bounds__(FT) k_apply_fused(int N, const T* __restrict__
   T dv[3];
 #pragma unroll
   for (int t = 0; t < 3; ++t) dv[t] = dinv<T>(tx3, ty3, t);
-  int64_t off[PLD];
+  // every input plane this CTA needs (z0 - 3 .. z0 + FZ + 2) at this thread's
+  // halo positions, loaded up front: the z pass then reads registers only
+  T win[PLD][FZ + 6];
 #pragma unroll
   for (int k = 0; k < PLD; ++k) {
     const int i = tid + k * FT;
     const int hx = i % HXS, hy = i / HXS;
     const int ggx = ((x0 + hx - 3) % N + N) % N, ggy = ((y0 + hy - 3) % N + N) % N;
-    off[k] = i < HPS ? (int64_t)ggy * N + ggx : -1;
-  }
-  T pf[PLD];
-  auto fetch = [&](int z) {
-    const int64_t zo = (int64_t)(((z % N) + N) % N) * NN;
+    const int64_t off = (int64_t)ggy * N + ggx;
 #pragma unroll
-    for (int k = 0; k < PLD; ++k) pf[k] = off[k] >= 0 ? x[zo + off[k]] : T(0);
-  };
-  auto store = [&](int slot) {
-#pragma unroll
-    for (int k = 0; k < PLD; ++k) {
-      const int i = tid + k * FT;
-      if (i < HPS) ring[slot][i] = pf[k];
+    for (int p = 0; p < FZ + 6; ++p) {
+      const int zz = (((z0 - 3 + p) % N) + N) % N;
+      win[k][p] = i < HPS ? x[(int64_t)zz * NN + off] : T(0);
     }
-  };
-  for (int k = 0; k < 6; ++k) {
-    fetch(z0 - 3 + k);
-    store(k);
   }
-  fetch(z0 + 3);
   const bool inside = gx < N && gy < N;
-  int slot_new = 6;                    // ring slot of plane z + 3
+#pragma unroll
   for (int zi = 0; zi < FZ; ++zi) {
     const int z = z0 + zi;
     if (z >= N) break;
-    store(slot_new);
-    __syncthreads();
-    if (zi + 1 < FZ && z + 1 < N) fetch(z + 4);     // in flight while this plane is computed
     const int64_t g = inside ? gx + (int64_t)N * gy + NN * z : 0;
     T eb = T(0), ed = T(0), ex = T(0);
     if (inside && EPI != EPI_Y) eb = b[g];
@@ -286,18 +271,14 @@ __global__ void __launch_bounds__(FT) k_apply_fused(int N, const T* __restrict__
       ed = d[g];
       ex = x[g];
     }
-    // z pass over the halo plane: plane z + j sits in slot (slot_new - 3 + j) mod 7
     const int tz = z % 3;
     T kz[7], mz[7];
-    const T* rp[7];
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
       kz[j] = Cst<T>::K(tz, j);
       mz[j] = Cst<T>::M(tz, j);
-      int sl = slot_new - 6 + j;
-      sl += sl < 0 ? 7 : 0;
-      rp[j] = ring[sl];
     }
+    if (zi > 0) __syncthreads();   // the previous plane's y pass is done with t1s, t2s
 #pragma unroll
     for (int k = 0; k < PLD; ++k) {
       const int i = tid + k * FT;
@@ -305,7 +286,7 @@ __global__ void __launch_bounds__(FT) k_apply_fused(int N, const T* __restrict__
         T s1 = T(0), s2 = T(0);
 #pragma unroll
         for (int j = 0; j < 7; ++j) {
-          const T v = rp[j][i];
+          const T v = win[k][zi + j];
           s1 += mz[j] * v;
           s2 += kz[j] * v;
         }
@@ -314,7 +295,6 @@ __global__ void __launch_bounds__(FT) k_apply_fused(int N, const T* __restrict__
       }
     }
     __syncthreads();
-    // y pass: row ty, columns tx and tx + FX (of the HXS halo columns)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int hx = tx + h * FX;
@@ -347,7 +327,6 @@ __global__ void __launch_bounds__(FT) k_apply_fused(int N, const T* __restrict__
         xo[g] = ex + dn;
       }
     }
-    slot_new = slot_new == 6 ? 0 : slot_new + 1;
   }
 }
 
