@@ -218,8 +218,12 @@ def singular_sums(bins, Q, n, n_sr, weights=None):
     return phi, grad
 
 
-def forward(pos, Q, L, n, n_sr=3, neutralise=True, chunk=4096, want_grad=False):
-    """Phi_i and U for charges Q at pos (N x 3), with all intermediates (Algorithm 1)."""
+def forward(pos, Q, L, n, n_sr=3, neutralise=True, chunk=4096, want_grad=False, targets=None):
+    """Phi_i and U for charges Q at pos (N x 3), with all intermediates (Algorithm 1).
+
+    targets (optional index array): evaluate Phi only at these charges (the mesh
+    solve still uses every charge); then phi and its parts have len(targets)
+    entries and U is not formed."""
     pos = np.asarray(pos, dtype=np.float64)
     Q = np.asarray(Q, dtype=np.float64)
     assert n >= 2 * n_sr + 1, "the short-range block must not wrap onto itself"
@@ -232,6 +236,8 @@ def forward(pos, Q, L, n, n_sr=3, neutralise=True, chunk=4096, want_grad=False):
     if neutralise:
         b = ops.neutralise(b)
     phi_mesh = ops.solve(b)
+    if targets is not None:
+        return _forward_targets(bins, C, Q, n, n_sr, phi_mesh, np.asarray(targets), chunk)
     U3, G3 = q3_basis(bins)
     ix, iy, iz = element_node_index(bins['c3'], n)
     phi_nodes = phi_mesh[ix, iy, iz]                            # (N, 64)
@@ -255,6 +261,40 @@ def forward(pos, Q, L, n, n_sr=3, neutralise=True, chunk=4096, want_grad=False):
     if want_grad:
         out['grad_field'] = grad_field + grad_sing              # d/dx of (sum_j Q_j K(x, j)) at x_i
     return out
+
+
+def _forward_targets(bins, C, Q, n, n_sr, phi_mesh, tg, chunk):
+    """Phi at the charges tg only: the same three parts as forward(), restricted."""
+    h = bins['h']
+    sub = dict(bins)
+    for k in ('c3', 'cell', 'delta'):
+        sub[k] = bins[k][tg]
+    U3, _ = q3_basis(sub)
+    ix, iy, iz = element_node_index(sub['c3'], n)
+    phi_sm = np.einsum('nm,nm->n', phi_mesh[ix, iy, iz], U3)
+    # singular sums with the targets' own indices excluded
+    phi_sing = np.zeros(len(tg))
+    perm, start, count = bins['perm'], bins['start'], bins['count']
+    for d in block_offsets(n_sr):
+        src = (sub['c3'] + d) % n
+        s = src[:, 0] + n * src[:, 1] + n * n * src[:, 2]
+        cnt = count[s]
+        for k in range(int(cnt.max()) if len(tg) else 0):
+            valid = k < cnt
+            j = perm[np.where(valid, start[s] + k, 0)]
+            valid &= j != tg
+            rel = d * h + bins['delta'][j] - sub['delta']
+            R = np.where(valid, np.sqrt(np.einsum('nk,nk->n', rel, rel)), 1.0)
+            phi_sing += np.where(valid, Q[j], 0.0) / R
+    Wmat = screen_window_matrix(n_sr)
+    offs = block_offsets(n_sr)
+    phi_scr = np.zeros(len(tg))
+    for s0 in range(0, len(tg), chunk):
+        sl = slice(s0, s0 + chunk)
+        Cblk = gather_block_coefficients(C, sub['c3'][sl], n, offs)
+        phi_scr[sl] = np.einsum('nm,nm->n', (h * h) * (Cblk @ Wmat), U3[sl])
+    return dict(phi=phi_sm + phi_sing - phi_scr, phi_sm=phi_sm, phi_sing=phi_sing, phi_scr=phi_scr,
+                phi_mesh=phi_mesh, bins=bins, C=C)
 
 
 def vjp(fwd, Q, gU=1.0, gphi=None, n_sr=3, chunk=4096):

@@ -72,10 +72,12 @@ def hat_potential_continuum(points, ngl=8):
 
 
 def kron_apply(A, B, C, X):
-    """(A (x) B (x) C) X on an array indexed [ix, iy, iz]: A acts on x, B on y, C on z."""
-    Y = np.einsum('ai,ijk->ajk', A, X)
-    Y = np.einsum('bj,ajk->abk', B, Y)
-    return np.einsum('ck,abk->abc', C, Y)
+    """(A (x) B (x) C) X on an array indexed [ix, iy, iz]: A acts on x, B on y, C on z.
+
+    Each factor is one matrix product over its axis (tensordot, i.e. BLAS)."""
+    Y = np.tensordot(A, X, axes=(1, 0))                          # [a, j, k]
+    Y = np.moveaxis(np.tensordot(B, Y, axes=(1, 1)), 0, 1)       # [a, b, k]
+    return np.tensordot(Y, C, axes=(2, 1))                       # [a, b, c]
 
 
 def stiffness_apply(K1, M1, X):
