@@ -203,134 +203,248 @@ __global__ void k_apply_x(int N, const T* __restrict__ a, const T* __restrict__ 
 }
 
 
-// Fused apply y = K x in one kernel (2.5-D tiling): a CTA owns an FX x FY
-// column of output nodes and marches FZ planes in z, keeping the 7 input
-// planes the z stencil needs in a shared ring buffer (3-node halo in x and y),
-// and runs the three sum-factorisation passes on shared tiles.  The epilogue
-// is as in k_apply_x, except that the Chebyshev step writes the new iterate to
-// xo (not in place: neighbouring tiles still read x as their halo).
-constexpr int FX = 32, FY = 4, FZ = 4;
-constexpr int HXS = FX + 6, HYS = FY + 6, HPS = HXS * HYS;
-constexpr int FT = FX * FY;                          // threads per CTA
-constexpr int PLD = (HPS + FT - 1) / FT;             // plane values loaded per thread
+// Fused apply y = K x, tiled by elements (2.5-D).  A CTA owns an AFX x AFY
+// column of output nodes (AEX x AEY elements, origin on a vertex) and marches
+// in z one element (three planes) at a time.  Since tiles and z steps start on
+// vertices, the node type (vertex, or the first or second interior node of an
+// element) is a compile-time constant in all three passes, and the interior
+// nodes' 1-D stencils run with their 4 nonzero taps (7 for a vertex):
+//   z pass (registers)  t1 = Mz x, t2 = Kz x            on (AFX+6) x (AFY+6)
+//   y pass (shared)     a = My t1, c = Ky t1 + My t2     on (AFX+6) x AFY
+//   x pass (shared)     y = Kx a + Mx c                  on AFX x AFY
+// Each thread keeps, for each of its halo columns, the 7 input planes of the
+// current element's three output planes in registers and prefetches the next
+// element's three new planes while it computes.  The epilogue:
+//   EPI_Y      out = y
+//   EPI_RESID  out = b - y
+//   EPI_CHEB   d = c1 d + c2 D^-1 (b - y); xo = x + d   (one Chebyshev step;
+//              not in place: neighbouring tiles still read x as their halo)
+constexpr int AEX = 16, AEY = 4;                  // elements per tile in x, y
+constexpr int AFX = 3 * AEX, AFY = 3 * AEY;       // output nodes per tile
+constexpr int AHX = AFX + 6, AHY = AFY + 6;       // halo column extents
+constexpr int ANC = AHX * AHY;                    // halo columns per tile
+constexpr int AT = 256;                           // threads per CTA
+constexpr int APL = (ANC + AT - 1) / AT;          // halo columns per thread
+static_assert(AHX * AEY <= AT && AEX * AFY <= AT, "one y item and one x item per thread");
 
-// Fused apply y = K x in one kernel (2.5-D tiling): a CTA owns an FX x FY
-// column of output nodes and marches FZ planes in z, keeping the 7 input
-// planes the z stencil needs in a shared ring buffer (3-node halo in x and y;
-// the next plane is fetched into registers while the current one is used),
-// and runs the three sum-factorisation passes on shared tiles.  The epilogue
-// options are as in k_apply_x, except that the Chebyshev step writes the new
-// iterate to xo (not in place: neighbouring tiles still read x as their halo).
-template <class T, int EPI>
-__global__ void __launch_bounds__(FT) k_apply_fused(int N, const T* __restrict__ x, T* __restrict__ out,
-                                                    const T* __restrict__ b, T* __restrict__ d,
-                                                    T* __restrict__ xo, T c1, T c2) {
-  __shared__ T t1s[HPS], t2s[HPS];
-  __shared__ T as_[FY][HXS], cs_[FY][HXS];
-  const int64_t NN = (int64_t)N * N;
-  const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY, z0 = blockIdx.z * FZ;
-  const int tid = threadIdx.x, tx = tid % FX, ty = tid / FX;
-  const int gx = x0 + tx, gy = y0 + ty;
-  // node types are fixed per thread in the x and y passes: stencils in registers
-  const int tx3 = gx % 3, ty3 = gy % 3;
-  T kx[7], mx[7], ky[7], my[7];
+template <class T>
+struct ApplySmem {
+  T t1[3][AHY][AHX], t2[3][AHY][AHX];
+  T a[3][AFY][AHX], c[3][AFY][AHX];
+  T dinv[27];   // D^-1 by node types: x + 3 y + 9 z
+};
+
+// nonzero taps j (offset j - 3) of the 1-D stencil of a node of type t
+template <int t> struct Taps {
+  static constexpr int lo = t == 0 ? 0 : (t == 1 ? 2 : 1);
+  static constexpr int hi = t == 0 ? 6 : (t == 1 ? 5 : 4);
+};
+
+// sum_j M(t, j) v[j] and sum_j K(t, j) v[j]; v[j] is the value at offset j - 3
+template <class T, int t>
+__device__ __forceinline__ void st_MK(const T* v, T& sm, T& sk) {
+  constexpr int lo = Taps<t>::lo, hi = Taps<t>::hi;
+  sm = Cst<T>::M(t, lo) * v[lo];
+  sk = Cst<T>::K(t, lo) * v[lo];
 #pragma unroll
-  for (int j = 0; j < 7; ++j) {
-    kx[j] = Cst<T>::K(tx3, j);
-    mx[j] = Cst<T>::M(tx3, j);
-    ky[j] = Cst<T>::K(ty3, j);
-    my[j] = Cst<T>::M(ty3, j);
-  }
-  T dv[3];
-#pragma unroll
-  for (int t = 0; t < 3; ++t) dv[t] = dinv<T>(tx3, ty3, t);
-  // every input plane this CTA needs (z0 - 3 .. z0 + FZ + 2) at this thread's
-  // halo positions, loaded up front: the z pass then reads registers only
-  T win[PLD][FZ + 6];
-#pragma unroll
-  for (int k = 0; k < PLD; ++k) {
-    const int i = tid + k * FT;
-    const int hx = i % HXS, hy = i / HXS;
-    const int ggx = ((x0 + hx - 3) % N + N) % N, ggy = ((y0 + hy - 3) % N + N) % N;
-    const int64_t off = (int64_t)ggy * N + ggx;
-#pragma unroll
-    for (int p = 0; p < FZ + 6; ++p) {
-      const int zz = (((z0 - 3 + p) % N) + N) % N;
-      win[k][p] = i < HPS ? x[(int64_t)zz * NN + off] : T(0);
-    }
-  }
-  const bool inside = gx < N && gy < N;
-#pragma unroll
-  for (int zi = 0; zi < FZ; ++zi) {
-    const int z = z0 + zi;
-    if (z >= N) break;
-    const int64_t g = inside ? gx + (int64_t)N * gy + NN * z : 0;
-    T eb = T(0), ed = T(0), ex = T(0);
-    if (inside && EPI != EPI_Y) eb = b[g];
-    if (inside && EPI == EPI_CHEB) {
-      ed = d[g];
-      ex = x[g];
-    }
-    const int tz = z % 3;
-    T kz[7], mz[7];
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-      kz[j] = Cst<T>::K(tz, j);
-      mz[j] = Cst<T>::M(tz, j);
-    }
-    if (zi > 0) __syncthreads();   // the previous plane's y pass is done with t1s, t2s
-#pragma unroll
-    for (int k = 0; k < PLD; ++k) {
-      const int i = tid + k * FT;
-      if (i < HPS) {
-        T s1 = T(0), s2 = T(0);
-#pragma unroll
-        for (int j = 0; j < 7; ++j) {
-          const T v = win[k][zi + j];
-          s1 += mz[j] * v;
-          s2 += kz[j] * v;
-        }
-        t1s[i] = s1;
-        t2s[i] = s2;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int hx = tx + h * FX;
-      if (hx < HXS) {
-        T s1 = T(0), s2 = T(0);
-#pragma unroll
-        for (int j = 0; j < 7; ++j) {
-          const int q = (ty + j) * HXS + hx;
-          const T u = t1s[q], w = t2s[q];
-          s1 += my[j] * u;
-          s2 += ky[j] * u + my[j] * w;
-        }
-        as_[ty][hx] = s1;
-        cs_[ty][hx] = s2;
-      }
-    }
-    __syncthreads();
-    if (inside) {
-      T y = T(0);
-#pragma unroll
-      for (int j = 0; j < 7; ++j) y += kx[j] * as_[ty][tx + j] + mx[j] * cs_[ty][tx + j];
-      if (EPI == EPI_Y) {
-        out[g] = y;
-      } else if (EPI == EPI_RESID) {
-        out[g] = eb - y;
-      } else {
-        const T r = eb - y;
-        const T dn = c1 * ed + c2 * dv[tz] * r;
-        d[g] = dn;
-        xo[g] = ex + dn;
-      }
-    }
+  for (int j = lo + 1; j <= hi; ++j) {
+    sm += Cst<T>::M(t, j) * v[j];
+    sk += Cst<T>::K(t, j) * v[j];
   }
 }
 
-static inline int apply_fz(int) { return FZ; }
+// sum_j M(t, j) u[j]
+template <class T, int t>
+__device__ __forceinline__ T st_M(const T* u) {
+  constexpr int lo = Taps<t>::lo, hi = Taps<t>::hi;
+  T s = Cst<T>::M(t, lo) * u[lo];
+#pragma unroll
+  for (int j = lo + 1; j <= hi; ++j) s += Cst<T>::M(t, j) * u[j];
+  return s;
+}
+
+// sum_j K(t, j) u[j] + M(t, j) w[j]
+template <class T, int t>
+__device__ __forceinline__ T st_KM(const T* u, const T* w) {
+  constexpr int lo = Taps<t>::lo, hi = Taps<t>::hi;
+  T s = Cst<T>::K(t, lo) * u[lo];
+  s += Cst<T>::M(t, lo) * w[lo];
+#pragma unroll
+  for (int j = lo + 1; j <= hi; ++j) {
+    s += Cst<T>::K(t, j) * u[j];
+    s += Cst<T>::M(t, j) * w[j];
+  }
+  return s;
+}
+
+template <class T, int EPI>
+__device__ __forceinline__ void apply_epilogue(int64_t g, T y, T* __restrict__ out, const T* __restrict__ b,
+                                               T* __restrict__ d, const T* __restrict__ x, T* __restrict__ xo,
+                                               T c1, T c2, T dv) {
+  if (EPI == EPI_Y) {
+    out[g] = y;
+  } else if (EPI == EPI_RESID) {
+    out[g] = b[g] - y;
+  } else {
+    const T dn = c1 * d[g] + c2 * dv * (b[g] - y);
+    d[g] = dn;
+    xo[g] = x[g] + dn;
+  }
+}
+
+// grid: (ceil(N / AFX), ceil(N / AFY), ceil(n / steps)), AT threads, dynamic
+// shared memory sizeof(ApplySmem<T>); N = 3 n with n >= 3
+template <class T, int EPI>
+__global__ void __launch_bounds__(AT) k_apply_el(int N, int steps, const T* __restrict__ x, T* __restrict__ out,
+                                                 const T* __restrict__ b, T* __restrict__ d, T* __restrict__ xo,
+                                                 T c1, T c2) {
+  extern __shared__ __align__(16) unsigned char apply_smem_raw[];
+  ApplySmem<T>& S = *reinterpret_cast<ApplySmem<T>*>(apply_smem_raw);
+  const int n = N / 3;
+  const int64_t NN = (int64_t)N * N;
+  const int x0 = blockIdx.x * AFX, y0 = blockIdx.y * AFY;
+  const int e0 = blockIdx.z * steps, e1 = min(n, e0 + steps);
+  const int tid = threadIdx.x;
+  if (tid < 27) {
+    const int a = tid % 3, bb = (tid / 3) % 3, cz = tid / 9;
+    S.dinv[tid] = T(1) / (Cst<T>::DK(a) * Cst<T>::DM(bb) * Cst<T>::DM(cz) +
+                          Cst<T>::DM(a) * Cst<T>::DK(bb) * Cst<T>::DM(cz) +
+                          Cst<T>::DM(a) * Cst<T>::DM(bb) * Cst<T>::DK(cz));
+  }
+  // this thread's halo columns (periodic in x and y); columns past the halo
+  // read column 0 and store nothing
+  int coff[APL];
+#pragma unroll
+  for (int k = 0; k < APL; ++k) {
+    const int i = tid + k * AT;
+    const int hy = i / AHX, hx = i - hy * AHX;
+    const int gx = ((x0 + hx - 3) % N + N) % N, gy = ((y0 + hy - 3) % N + N) % N;
+    coff[k] = i < ANC ? gy * N + gx : 0;
+  }
+  // window slot s holds plane 3e - 3 + s (wrapped); N >= 9, so one wrap suffices
+  int zs = 3 * e0 - 3;
+  if (zs < 0) zs += N;
+  T w[APL][7], nx[APL][3];
+#pragma unroll
+  for (int s = 0; s < 7; ++s) {
+    int zz = zs + s;
+    if (zz >= N) zz -= N;
+    const T* xp = x + zz * NN;
+#pragma unroll
+    for (int k = 0; k < APL; ++k) w[k][s] = xp[coff[k]];
+  }
+  // y item: halo column hx, element row ey; x item: row yy, element column ex
+  const int y_ey = tid / AHX, y_hx = tid - y_ey * AHX;
+  const bool y_on = tid < AHX * AEY;
+  const int x_yy = tid / AEX, x_ex = tid - x_yy * AEX;
+  const bool x_on = tid < AEX * AFY && x0 + 3 * x_ex < N && y0 + x_yy < N;
+  const int gx0 = x0 + 3 * x_ex, gy = y0 + x_yy, ty3 = x_yy % 3;
+
+#pragma unroll 1
+  for (int e = e0; e < e1; ++e) {
+    // prefetch planes 3e + 4 .. 3e + 6 for the next element
+    if (e + 1 < e1) {
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        int zz = zs + 7 + s;
+        if (zz >= N) zz -= N;
+        const T* xp = x + zz * NN;
+#pragma unroll
+        for (int k = 0; k < APL; ++k) nx[k][s] = xp[coff[k]];
+      }
+    }
+    // z pass: planes 3e, 3e + 1, 3e + 2 are a vertex and the two interior nodes
+#pragma unroll
+    for (int k = 0; k < APL; ++k) {
+      const int i = tid + k * AT;
+      if (i < ANC) {
+        T m0, k0, m1, k1, m2, k2;
+        st_MK<T, 0>(w[k], m0, k0);
+        st_MK<T, 1>(w[k] + 1, m1, k1);
+        st_MK<T, 2>(w[k] + 2, m2, k2);
+        (&S.t1[0][0][0])[i] = m0;
+        (&S.t2[0][0][0])[i] = k0;
+        (&S.t1[1][0][0])[i] = m1;
+        (&S.t2[1][0][0])[i] = k1;
+        (&S.t1[2][0][0])[i] = m2;
+        (&S.t2[2][0][0])[i] = k2;
+      }
+    }
+    __syncthreads();
+    // y pass: rows 3 ey .. 3 ey + 2 of column hx, for the three planes
+    if (y_on) {
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        T u[7], v[7];
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+          u[j] = S.t1[p][3 * y_ey + j][y_hx];
+          v[j] = S.t2[p][3 * y_ey + j][y_hx];
+        }
+        S.a[p][3 * y_ey + 0][y_hx] = st_M<T, 0>(u);
+        S.c[p][3 * y_ey + 0][y_hx] = st_KM<T, 0>(u, v);
+        S.a[p][3 * y_ey + 1][y_hx] = st_M<T, 1>(u + 1);
+        S.c[p][3 * y_ey + 1][y_hx] = st_KM<T, 1>(u + 1, v + 1);
+        S.a[p][3 * y_ey + 2][y_hx] = st_M<T, 2>(u + 2);
+        S.c[p][3 * y_ey + 2][y_hx] = st_KM<T, 2>(u + 2, v + 2);
+      }
+    }
+    __syncthreads();
+    // x pass and epilogue: nodes 3 ex .. 3 ex + 2 of row yy, for the three planes
+    if (x_on) {
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        T u[7], v[7];
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+          u[j] = S.a[p][x_yy][3 * x_ex + j];
+          v[j] = S.c[p][x_yy][3 * x_ex + j];
+        }
+        const int64_t g = (int64_t)(3 * e + p) * NN + (int64_t)gy * N + gx0;
+        const T* dv = S.dinv + 3 * ty3 + 9 * p;
+        apply_epilogue<T, EPI>(g, st_KM<T, 0>(u, v), out, b, d, x, xo, c1, c2, dv[0]);
+        apply_epilogue<T, EPI>(g + 1, st_KM<T, 1>(u + 1, v + 1), out, b, d, x, xo, c1, c2, dv[1]);
+        apply_epilogue<T, EPI>(g + 2, st_KM<T, 2>(u + 2, v + 2), out, b, d, x, xo, c1, c2, dv[2]);
+      }
+    }
+    // next element: slots 0..3 <- 3..6, slots 4..6 <- the prefetched planes
+#pragma unroll
+    for (int k = 0; k < APL; ++k) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) w[k][s] = w[k][s + 3];
+#pragma unroll
+      for (int s = 0; s < 3; ++s) w[k][4 + s] = nx[k][s];
+    }
+    zs += 3;
+    if (zs >= N) zs -= N;
+  }
+}
+
+template <class T>
+static cudaError_t apply_set_smem_t() {
+  const int sm = (int)sizeof(ApplySmem<T>);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_apply_el<T, EPI_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_apply_el<T, EPI_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
+      cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_apply_el<T, EPI_CHEB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
+// the FP64 tiles need more than the default 48 KB of dynamic shared memory
+static cudaError_t apply_set_smem() {
+  cudaError_t e = apply_set_smem_t<float>();
+  return e != cudaSuccess ? e : apply_set_smem_t<double>();
+}
+
+// elements per CTA in z: enough CTAs to fill the GPU a few times over
+static inline int apply_steps(int N) {
+  const int n = N / 3;
+  const int64_t cols = (int64_t)((N + AFX - 1) / AFX) * ((N + AFY - 1) / AFY);
+  const int64_t s = cols * n / (152 * 6);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(16, n), s));
+}
 
 // first Chebyshev step from x = 0: d = D^-1 b / theta, x = d
 template <class T>
@@ -613,14 +727,15 @@ struct MG {
   // one fused apply; EPI_CHEB reads x and writes the new iterate to xo (xo != x)
   void apply(const Level& L, const T* x, int epi, T* out, const T* b, T* d, T* xo, T c1, T c2) {
     cudaStream_t s = c->stream;
-    const int fz = apply_fz(L.N);
-    const dim3 grid((L.N + FX - 1) / FX, (L.N + FY - 1) / FY, (L.N + fz - 1) / fz);
+    const int steps = apply_steps(L.N);
+    const dim3 grid((L.N + AFX - 1) / AFX, (L.N + AFY - 1) / AFY, (L.n + steps - 1) / steps);
+    const size_t sm = sizeof(ApplySmem<T>);
     if (epi == EPI_Y)
-      FEP3M_CL k_apply_fused<T, EPI_Y><<<grid, FT, 0, s>>>(L.N, x, out, b, d, xo, c1, c2);
+      FEP3M_CL k_apply_el<T, EPI_Y><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c1, c2);
     else if (epi == EPI_RESID)
-      FEP3M_CL k_apply_fused<T, EPI_RESID><<<grid, FT, 0, s>>>(L.N, x, out, b, d, xo, c1, c2);
+      FEP3M_CL k_apply_el<T, EPI_RESID><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c1, c2);
     else
-      FEP3M_CL k_apply_fused<T, EPI_CHEB><<<grid, FT, 0, s>>>(L.N, x, out, b, d, xo, c1, c2);
+      FEP3M_CL k_apply_el<T, EPI_CHEB><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c1, c2);
   }
 
   // Chebyshev smoothing of A x = b (D-preconditioned) on [lmax/ratio, lmax]
@@ -931,8 +1046,10 @@ static cudaError_t ensure_solver_buffers(Solver* c) {
 static cudaError_t apply64(Solver* c, const double* x, const double* b, double* r) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
-  const dim3 grid((N + FX - 1) / FX, (N + FY - 1) / FY, (N + FZ - 1) / FZ);
-  FEP3M_CL k_apply_fused<double, EPI_RESID><<<grid, FT, 0, c->stream>>>(N, x, r, b, nullptr, nullptr, 0.0, 0.0);
+  const int steps = apply_steps(N);
+  const dim3 grid((N + AFX - 1) / AFX, (N + AFY - 1) / AFY, (L0.n + steps - 1) / steps);
+  FEP3M_CL k_apply_el<double, EPI_RESID><<<grid, AT, sizeof(ApplySmem<double>), c->stream>>>(
+      N, steps, x, r, b, nullptr, nullptr, 0.0, 0.0);
   return cudaGetLastError();
 }
 
@@ -1181,6 +1298,7 @@ cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream) {
   if ((e = cudaMallocHost(&s->host_res, 2 * sizeof(double))) != cudaSuccess) return e;
   cudaMemset(s->red_counter, 0, sizeof(unsigned int));
   cudaMemset(s->scal, 0, 64 * sizeof(double));
+  if ((e = apply_set_smem()) != cudaSuccess) return e;
   return mg_setup(s);
 }
 
