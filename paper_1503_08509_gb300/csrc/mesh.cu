@@ -26,6 +26,9 @@ namespace fep3m {
 
 __constant__ double cM64[3][7], cK64[3][7], cP64[6][4], cMpq64[4][2], cDM64[3], cDK64[3];
 __constant__ float cM32[3][7], cK32[3][7], cP32[6][4], cDM32[3], cDK32[3];
+// inverse diagonal of K by node types, index x + 3 y + 9 z
+__constant__ double cDinv64[27];
+__constant__ float cDinv32[27];
 
 template <class T> struct Cst;
 template <> struct Cst<double> {
@@ -34,6 +37,7 @@ template <> struct Cst<double> {
   static __device__ __forceinline__ double P(int s, int j) { return cP64[s][j]; }
   static __device__ __forceinline__ double DM(int t) { return cDM64[t]; }
   static __device__ __forceinline__ double DK(int t) { return cDK64[t]; }
+  static __device__ __forceinline__ double Dinv(int k) { return cDinv64[k]; }
 };
 template <> struct Cst<float> {
   static __device__ __forceinline__ float M(int t, int j) { return cM32[t][j]; }
@@ -41,6 +45,7 @@ template <> struct Cst<float> {
   static __device__ __forceinline__ float P(int s, int j) { return cP32[s][j]; }
   static __device__ __forceinline__ float DM(int t) { return cDM32[t]; }
   static __device__ __forceinline__ float DK(int t) { return cDK32[t]; }
+  static __device__ __forceinline__ float Dinv(int k) { return cDinv32[k]; }
 };
 
 namespace {
@@ -121,87 +126,7 @@ __global__ void k_load_vector(int n, const T* __restrict__ rv, double* __restric
 }
 
 // ------------------------------------------------------------ operator apply
-template <class T>
-__global__ void k_apply_z(int N, const T* __restrict__ x, T* __restrict__ t1, T* __restrict__ t2) {
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t NN = (int64_t)N * N;
-  if (g >= NN * N) return;
-  const int iz = (int)(g / NN);
-  const int64_t xy = g - iz * NN;
-  const int t = iz % 3;
-  T s1 = T(0), s2 = T(0);
-#pragma unroll
-  for (int j = -3; j <= 3; ++j) {
-    const T v = x[xy + wrapi(iz + j, N) * NN];
-    s1 += Cst<T>::M(t, j + 3) * v;
-    s2 += Cst<T>::K(t, j + 3) * v;
-  }
-  t1[g] = s1;
-  t2[g] = s2;
-}
-
-template <class T>
-__global__ void k_apply_y(int N, const T* __restrict__ t1, const T* __restrict__ t2, T* __restrict__ a,
-                          T* __restrict__ c) {
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t NN = (int64_t)N * N;
-  if (g >= NN * N) return;
-  const int64_t iz = g / NN;
-  const int iy = (int)((g / N) % N), ix = (int)(g % N);
-  const int t = iy % 3;
-  T s1 = T(0), s2 = T(0);
-#pragma unroll
-  for (int j = -3; j <= 3; ++j) {
-    const int64_t h = ix + (int64_t)N * wrapi(iy + j, N) + iz * NN;
-    const T u = t1[h], w = t2[h];
-    s1 += Cst<T>::M(t, j + 3) * u;
-    s2 += Cst<T>::K(t, j + 3) * u + Cst<T>::M(t, j + 3) * w;
-  }
-  a[g] = s1;
-  c[g] = s2;
-}
-
-template <class T>
-__device__ __forceinline__ T dinv(int ix, int iy, int iz) {
-  const int a = ix % 3, b = iy % 3, c = iz % 3;
-  return T(1) / (Cst<T>::DK(a) * Cst<T>::DM(b) * Cst<T>::DM(c) + Cst<T>::DM(a) * Cst<T>::DK(b) * Cst<T>::DM(c) +
-                 Cst<T>::DM(a) * Cst<T>::DM(b) * Cst<T>::DK(c));
-}
-
-enum { EPI_Y = 0, EPI_RESID = 1, EPI_CHEB = 2 };
-
-// final pass y = Kx a + Mx c with a fused epilogue:
-//   EPI_Y      out = y
-//   EPI_RESID  out = b - y
-//   EPI_CHEB   d = c1 d + c2 D^-1 (b - y); x += d   (one Chebyshev step)
-template <class T, int EPI>
-__global__ void k_apply_x(int N, const T* __restrict__ a, const T* __restrict__ c, T* __restrict__ out,
-                          const T* __restrict__ b, T* __restrict__ d, T* __restrict__ x, T c1, T c2) {
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t NN = (int64_t)N * N;
-  if (g >= NN * N) return;
-  const int ix = (int)(g % N);
-  const int64_t row = g - ix;
-  const int t = ix % 3;
-  T y = T(0);
-#pragma unroll
-  for (int j = -3; j <= 3; ++j) {
-    const int64_t h = row + wrapi(ix + j, N);
-    y += Cst<T>::K(t, j + 3) * a[h] + Cst<T>::M(t, j + 3) * c[h];
-  }
-  if (EPI == EPI_Y) {
-    out[g] = y;
-  } else if (EPI == EPI_RESID) {
-    out[g] = b[g] - y;
-  } else {
-    const int iy = (int)((g / N) % N), iz = (int)(g / NN);
-    const T r = b[g] - y;
-    const T dn = c1 * d[g] + c2 * dinv<T>(ix, iy, iz) * r;
-    d[g] = dn;
-    x[g] += dn;
-  }
-}
-
+enum { EPI_Y = 0, EPI_RESID = 1, EPI_CHEB = 2, EPI_CHEB0 = 3 };
 
 // Fused apply y = K x, tiled by elements (2.5-D).  A CTA owns an AFX x AFY
 // column of output nodes (AEX x AEY elements, origin on a vertex) and marches
@@ -219,6 +144,9 @@ __global__ void k_apply_x(int N, const T* __restrict__ a, const T* __restrict__ 
 //   EPI_RESID  out = b - y
 //   EPI_CHEB   d = c1 d + c2 D^-1 (b - y); xo = x + d   (one Chebyshev step;
 //              not in place: neighbouring tiles still read x as their halo)
+//   EPI_CHEB0  the second Chebyshev step from a zero start, whose first step
+//              is d = x = c0 D^-1 b: the input is formed from b on the fly
+//              (x must point at b), then as EPI_CHEB with that d and x
 constexpr int AEX = 16, AEY = 4;                  // elements per tile in x, y
 constexpr int AFX = 3 * AEX, AFY = 3 * AEY;       // output nodes per tile
 constexpr int AHX = AFX + 6, AHY = AFY + 6;       // halo column extents
@@ -280,24 +208,29 @@ __device__ __forceinline__ T st_KM(const T* u, const T* w) {
 template <class T, int EPI>
 __device__ __forceinline__ void apply_epilogue(int64_t g, T y, T* __restrict__ out, const T* __restrict__ b,
                                                T* __restrict__ d, const T* __restrict__ x, T* __restrict__ xo,
-                                               T c1, T c2, T dv) {
+                                               T c0, T c1, T c2, T dv) {
   if (EPI == EPI_Y) {
     out[g] = y;
   } else if (EPI == EPI_RESID) {
     out[g] = b[g] - y;
-  } else {
+  } else if (EPI == EPI_CHEB) {
     const T dn = c1 * d[g] + c2 * dv * (b[g] - y);
     d[g] = dn;
     xo[g] = x[g] + dn;
+  } else {
+    const T bg = b[g], d0 = c0 * dv * bg;
+    const T dn = c1 * d0 + c2 * dv * (bg - y);
+    d[g] = dn;
+    xo[g] = d0 + dn;
   }
 }
 
 // grid: (ceil(N / AFX), ceil(N / AFY), ceil(n / steps)), AT threads, dynamic
 // shared memory sizeof(ApplySmem<T>); N = 3 n with n >= 3
 template <class T, int EPI>
-__global__ void __launch_bounds__(AT) k_apply_el(int N, int steps, const T* __restrict__ x, T* __restrict__ out,
+__global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, int steps, const T* __restrict__ x, T* __restrict__ out,
                                                  const T* __restrict__ b, T* __restrict__ d, T* __restrict__ xo,
-                                                 T c1, T c2) {
+                                                 T c0, T c1, T c2) {
   extern __shared__ __align__(16) unsigned char apply_smem_raw[];
   ApplySmem<T>& S = *reinterpret_cast<ApplySmem<T>*>(apply_smem_raw);
   const int n = N / 3;
@@ -324,6 +257,18 @@ __global__ void __launch_bounds__(AT) k_apply_el(int N, int steps, const T* __re
   // window slot s holds plane 3e - 3 + s (wrapped); N >= 9, so one wrap suffices
   int zs = 3 * e0 - 3;
   if (zs < 0) zs += N;
+  // EPI_CHEB0: input c0 D^-1 b, scaled per column and plane type (a halo
+  // column's x and y types are hx % 3 and hy % 3: the tile starts on a vertex)
+  T fs[EPI == EPI_CHEB0 ? APL : 1][3];
+  if (EPI == EPI_CHEB0) {
+#pragma unroll
+    for (int k = 0; k < APL; ++k) {
+      const int i = tid + k * AT;
+      const int hy = i / AHX, hx = i - hy * AHX;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) fs[k][t] = c0 * Cst<T>::Dinv(hx % 3 + 3 * (hy % 3) + 9 * t);
+    }
+  }
   T w[APL][7], nx[APL][3];
 #pragma unroll
   for (int s = 0; s < 7; ++s) {
@@ -331,7 +276,10 @@ __global__ void __launch_bounds__(AT) k_apply_el(int N, int steps, const T* __re
     if (zz >= N) zz -= N;
     const T* xp = x + zz * NN;
 #pragma unroll
-    for (int k = 0; k < APL; ++k) w[k][s] = xp[coff[k]];
+    for (int k = 0; k < APL; ++k) {
+      w[k][s] = xp[coff[k]];
+      if (EPI == EPI_CHEB0) w[k][s] *= fs[k][s % 3];
+    }
   }
   // y item: halo column hx, element row ey; x item: row yy, element column ex
   const int y_ey = tid / AHX, y_hx = tid - y_ey * AHX;
@@ -351,6 +299,13 @@ __global__ void __launch_bounds__(AT) k_apply_el(int N, int steps, const T* __re
         const T* xp = x + zz * NN;
 #pragma unroll
         for (int k = 0; k < APL; ++k) nx[k][s] = xp[coff[k]];
+      }
+    }
+    if (EPI == EPI_CHEB0 && e > e0) {   // planes 3e + 1 .. 3e + 3 arrived in the previous round
+#pragma unroll
+      for (int k = 0; k < APL; ++k) {
+#pragma unroll
+        for (int s = 4; s < 7; ++s) w[k][s] *= fs[k][s % 3];
       }
     }
     // z pass: planes 3e, 3e + 1, 3e + 2 are a vertex and the two interior nodes
@@ -402,9 +357,9 @@ __global__ void __launch_bounds__(AT) k_apply_el(int N, int steps, const T* __re
         }
         const int64_t g = (int64_t)(3 * e + p) * NN + (int64_t)gy * N + gx0;
         const T* dv = S.dinv + 3 * ty3 + 9 * p;
-        apply_epilogue<T, EPI>(g, st_KM<T, 0>(u, v), out, b, d, x, xo, c1, c2, dv[0]);
-        apply_epilogue<T, EPI>(g + 1, st_KM<T, 1>(u + 1, v + 1), out, b, d, x, xo, c1, c2, dv[1]);
-        apply_epilogue<T, EPI>(g + 2, st_KM<T, 2>(u + 2, v + 2), out, b, d, x, xo, c1, c2, dv[2]);
+        apply_epilogue<T, EPI>(g, st_KM<T, 0>(u, v), out, b, d, x, xo, c0, c1, c2, dv[0]);
+        apply_epilogue<T, EPI>(g + 1, st_KM<T, 1>(u + 1, v + 1), out, b, d, x, xo, c0, c1, c2, dv[1]);
+        apply_epilogue<T, EPI>(g + 2, st_KM<T, 2>(u + 2, v + 2), out, b, d, x, xo, c0, c1, c2, dv[2]);
       }
     }
     // next element: slots 0..3 <- 3..6, slots 4..6 <- the prefetched planes
@@ -429,7 +384,10 @@ static cudaError_t apply_set_smem_t() {
   if ((e = cudaFuncSetAttribute(k_apply_el<T, EPI_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
       cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(k_apply_el<T, EPI_CHEB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if ((e = cudaFuncSetAttribute(k_apply_el<T, EPI_CHEB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
+      cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_apply_el<T, EPI_CHEB0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 // the FP64 tiles need more than the default 48 KB of dynamic shared memory
@@ -446,33 +404,34 @@ static inline int apply_steps(int N) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(16, n), s));
 }
 
-// first Chebyshev step from x = 0: d = D^-1 b / theta, x = d
+// first Chebyshev step from x = 0: d = D^-1 b / theta, x = d (used alone
+// when the smoothing degree is 1); grid (ceil(N / 128), N, N)
 template <class T>
 __global__ void k_cheb0(int N, const T* __restrict__ b, T* __restrict__ d, T* __restrict__ x, T inv_theta) {
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t NN = (int64_t)N * N;
-  if (g >= NN * N) return;
-  const int ix = (int)(g % N), iy = (int)((g / N) % N), iz = (int)(g / NN);
-  const T v = inv_theta * dinv<T>(ix, iy, iz) * b[g];
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= N) return;
+  const int iy = blockIdx.y, iz = blockIdx.z;
+  const int64_t g = ix + (int64_t)N * (iy + (int64_t)N * iz);
+  const T v = inv_theta * Cst<T>::Dinv(ix % 3 + 3 * (iy % 3) + 9 * (iz % 3)) * b[g];
   d[g] = v;
   x[g] = v;
 }
 
 // ------------------------------------------------------- grid transfers
 // restriction along one axis (transpose of the 1-D prolongation): the input
-// has 2 Nc nodes along `axis`, the output Nc; other extents d1, d2.
+// has 2 Nc nodes along `axis`, the output Nc; output extents (e0, e1, e2) in
+// (x, y, z); grid (ceil(e0 / blockDim.x), e1, e2)
 template <class T>
 __global__ void k_restrict_axis(int axis, int Nc, int e0, int e1, int e2, const T* __restrict__ in,
                                 T* __restrict__ out, T scale) {
-  // output extents (e0, e1, e2) in (x, y, z); input extents equal except 2 Nc along axis
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t tot = (int64_t)e0 * e1 * e2;
-  if (g >= tot) return;
-  int i[3] = {(int)(g % e0), (int)((g / e0) % e1), (int)(g / ((int64_t)e0 * e1))};
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= e0) return;
+  int i[3] = {ix, (int)blockIdx.y, (int)blockIdx.z};
   int ein[3] = {e0, e1, e2};
   const int Nf = 2 * Nc;
   ein[axis] = Nf;
   const int64_t st[3] = {1, ein[0], (int64_t)ein[0] * ein[1]};
+  const int64_t g = ix + (int64_t)e0 * (i[1] + (int64_t)e1 * i[2]);
   const int gc = i[axis];
   i[axis] = 0;
   const int64_t base = i[0] * st[0] + i[1] * st[1] + i[2] * st[2];
@@ -489,17 +448,18 @@ __global__ void k_restrict_axis(int axis, int Nc, int e0, int e1, int e2, const 
   out[g] = scale * acc;
 }
 
-// prolongation along one axis: output has 2 Nc nodes along axis; ADD: out += .
+// prolongation along one axis: output has 2 Nc nodes along axis, extents
+// (e0, e1, e2); ADD: out = add + P in; grid (ceil(e0 / blockDim.x), e1, e2)
 template <class T, bool ADD>
 __global__ void k_prolong_axis(int axis, int Nc, int e0, int e1, int e2, const T* __restrict__ in,
-                               T* __restrict__ out) {
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t tot = (int64_t)e0 * e1 * e2;
-  if (g >= tot) return;
-  int i[3] = {(int)(g % e0), (int)((g / e0) % e1), (int)(g / ((int64_t)e0 * e1))};
+                               T* __restrict__ out, const T* __restrict__ add) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= e0) return;
+  int i[3] = {ix, (int)blockIdx.y, (int)blockIdx.z};
   int ein[3] = {e0, e1, e2};
   ein[axis] = Nc;
   const int64_t st[3] = {1, ein[0], (int64_t)ein[0] * ein[1]};
+  const int64_t g = ix + (int64_t)e0 * (i[1] + (int64_t)e1 * i[2]);
   const int f = i[axis];
   i[axis] = 0;
   const int64_t base = i[0] * st[0] + i[1] * st[1] + i[2] * st[2];
@@ -511,7 +471,7 @@ __global__ void k_prolong_axis(int axis, int Nc, int e0, int e1, int e2, const T
     if (gc >= Nc) gc -= Nc;
     acc += Cst<T>::P(s, j) * in[base + gc * st[axis]];
   }
-  if (ADD) out[g] += acc;
+  if (ADD) out[g] = add[g] + acc;
   else out[g] = acc;
 }
 
@@ -600,26 +560,68 @@ __global__ void __launch_bounds__(256) k_dense_tile(int N, int axis, const T* __
 }
 
 // ---------------------------------------------------------- reductions
-// deterministic two-level sum: each block writes a partial; the last block to
-// finish adds the partials in index order.  mode 0: x.y, 1: sum x,
-// 2: sum w3 x (node integrals), 3: x.x
-template <class T>
-__global__ void k_reduce(int N, int mode, const T* __restrict__ x, const T* __restrict__ y,
-                         double* __restrict__ partials, unsigned int* __restrict__ counter,
-                         double* __restrict__ out) {
+enum { RD_DOT = 0, RD_SUM = 1, RD_WSUM = 2, RD_NORM2 = 3 };
+// what the last block derives from the total t (written next to it, so that
+// the consumers read one ready scalar instead of recomputing it per node)
+enum { POST_NONE = 0, POST_ALPHA = 1, POST_BETA = 2, POST_MEAN = 3, POST_NORM = 4 };
+// derived scalars: doubles at scal[SC_DERIVED + k], floats at
+// ((float*)(scal + SC_DERIVED_F))[k]
+constexpr int SC_DERIVED = 16, SC_DERIVED_F = 32;
+enum { SD_ALPHA = 0, SD_BETA = 1, SD_MEAN = 2, SD_INV = 3, SD_RT = 4 };
+
+// node-integral weight of a node of the given types: (1/4 or 3/8 per axis)
+__device__ __forceinline__ double node_weight(int tx, int ty, int tz) {
+  const double w0 = 0.25, w1 = 0.375;
+  return (tx ? w1 : w0) * (ty ? w1 : w0) * (tz ? w1 : w0);
+}
+
+template <class T, int MODE>
+__device__ __forceinline__ T reduce_term(const T* __restrict__ x, const T* __restrict__ y, int64_t g) {
+  const T v = x[g];
+  if (MODE == RD_DOT) return v * y[g];
+  if (MODE == RD_NORM2) return v * v;
+  return v;
+}
+
+// deterministic two-level sum: each thread adds its nodes (four per round, in
+// the working precision) into an FP64 accumulator, each block writes a
+// partial, the last block to finish adds the partials in index order and
+// derives the post scalar.  MODE: x.y, sum x, sum w3 x (node integrals), x.x
+template <class T, int MODE>
+__global__ void k_reduce(int N, const T* __restrict__ x, const T* __restrict__ y, double* __restrict__ partials,
+                         unsigned int* __restrict__ counter, double* __restrict__ out, int post, double arg,
+                         double* __restrict__ scal) {
   __shared__ double sh[TPB / 32];
   __shared__ bool last;
   const int64_t NN = (int64_t)N * N, tot = NN * N;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < tot; g += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)x[g];
-    if (mode == 0) acc += v * (double)y[g];
-    else if (mode == 1) acc += v;
-    else if (mode == 3) acc += v * v;
-    else {
-      const int ix = (int)(g % N), iy = (int)((g / N) % N), iz = (int)(g / NN);
-      const double w[3] = {0.25, 0.375, 0.375};
-      acc += w[ix % 3] * w[iy % 3] * w[iz % 3] * v;
+  if (MODE == RD_WSUM) {
+    // whole rows per warp: the node types come from the row and the lane
+    const int64_t rows = NN;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nwarps = stride >> 5;
+    for (int64_t row = warp; row < rows; row += nwarps) {
+      const int iz = (int)(row / N), iy = (int)(row - (int64_t)iz * N);
+      const double wyz = node_weight(1, iy % 3, iz % 3) / 0.375;
+      const T* xr = x + row * N;
+      double s0 = 0.0, s1 = 0.0;   // vertex / interior columns
+      for (int ix = lane; ix < N; ix += 32) {
+        const double v = (double)xr[ix];
+        if (ix % 3 == 0) s0 += v;
+        else s1 += v;
+      }
+      acc += wyz * (0.25 * s0 + 0.375 * s1);
+    }
+  } else {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < tot; g += 4 * stride) {
+      T v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t h = g + u * stride;
+        v[u] = h < tot ? reduce_term<T, MODE>(x, y, h) : T(0);
+      }
+      acc += (double)((v[0] + v[1]) + (v[2] + v[3]));
     }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -647,61 +649,85 @@ __global__ void k_reduce(int N, int mode, const T* __restrict__ x, const T* __re
       for (int k = 0; k < TPB / 32; ++k) t += sh[k];
       *out = t;
       *counter = 0u;
+      double* dd = scal + SC_DERIVED;
+      float* df = (float*)(scal + SC_DERIVED_F);
+      if (post == POST_ALPHA) {          // alpha = (r.z) / (p.q), t = p.q
+        const double a = t != 0.0 ? scal[0] / t : 0.0;
+        dd[SD_ALPHA] = a;
+        df[SD_ALPHA] = (float)a;
+      } else if (post == POST_BETA) {    // beta = (r.z)_new / (r.z), t = (r.z)_new
+        const double bta = scal[0] != 0.0 ? t / scal[0] : 0.0;
+        dd[SD_BETA] = bta;
+        df[SD_BETA] = (float)bta;
+        scal[0] = t;
+      } else if (post == POST_MEAN) {    // t * arg (arg = 1 / W)
+        dd[SD_MEAN] = t * arg;
+        df[SD_MEAN] = (float)(t * arg);
+      } else if (post == POST_NORM) {    // 1 / sqrt(t) and sqrt(t)
+        dd[SD_INV] = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+        dd[SD_RT] = sqrt(t);
+      }
     }
   }
 }
 
-// v -= (sum v / W) w3 (load of a uniform background), or v -= (sum w3 v / W) (mean zero)
 template <class T>
-__global__ void k_project(int N, T* __restrict__ v, const double* __restrict__ sum, double invW, int mean_zero) {
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t NN = (int64_t)N * N;
-  if (g >= NN * N) return;
-  const double s = *sum * invW;
+__device__ __forceinline__ T derived(const double* scal, int k) {
+  if (sizeof(T) == 8) return (T)scal[SC_DERIVED + k];
+  return (T)((const float*)(scal + SC_DERIVED_F))[k];
+}
+
+// v -= m w3 (removes the load of a uniform background, m = sum v / W), or
+// v -= m (mean zero, m = sum w3 v / W); grid (ceil(N / bx), N, N)
+template <class T>
+__global__ void k_project(int N, T* __restrict__ v, const double* __restrict__ scal, int mean_zero) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= N) return;
+  const int iy = blockIdx.y, iz = blockIdx.z;
+  const int64_t g = ix + (int64_t)N * (iy + (int64_t)N * iz);
+  const T m = derived<T>(scal, SD_MEAN);
   if (mean_zero) {
-    v[g] = (T)((double)v[g] - s);
+    v[g] -= m;
   } else {
-    const int ix = (int)(g % N), iy = (int)((g / N) % N), iz = (int)(g / NN);
-    const double w[3] = {0.25, 0.375, 0.375};
-    v[g] = (T)((double)v[g] - s * w[ix % 3] * w[iy % 3] * w[iz % 3]);
+    const T wx = ix % 3 ? T(0.375) : T(0.25), wy = iy % 3 ? T(0.375) : T(0.25), wz = iz % 3 ? T(0.375) : T(0.25);
+    v[g] -= m * (wx * wy * wz);
   }
 }
 
-// CG updates with scalars read from device memory (no host round trip):
-//   alpha = s[0] / s[1];  x += alpha p;  r -= alpha q
+// CG updates with scalars derived on the device (no host round trip):
+//   x += alpha p;  r -= alpha q
 template <class T>
-__global__ void k_cg_update(int64_t n, const double* __restrict__ s, T* __restrict__ x, T* __restrict__ r,
+__global__ void k_cg_update(int64_t n, const double* __restrict__ scal, T* __restrict__ x, T* __restrict__ r,
                             const T* __restrict__ p, const T* __restrict__ q) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
-  const T alpha = s[1] != 0.0 ? (T)(s[0] / s[1]) : T(0);
+  const T alpha = derived<T>(scal, SD_ALPHA);
   x[g] += alpha * p[g];
   r[g] -= alpha * q[g];
 }
-//   beta = s[2] / s[0]; p = z + beta p
+//   p = z + beta p
 template <class T>
-__global__ void k_cg_dir(int64_t n, const double* __restrict__ s, T* __restrict__ p, const T* __restrict__ z) {
+__global__ void k_cg_dir(int64_t n, const double* __restrict__ scal, T* __restrict__ p, const T* __restrict__ z) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
-  const T beta = s[0] != 0.0 ? (T)(s[2] / s[0]) : T(0);
+  const T beta = derived<T>(scal, SD_BETA);
   p[g] = z[g] + beta * p[g];
 }
 
-template <class A, class B>
-__global__ void k_convert(int64_t n, const A* __restrict__ in, B* __restrict__ out, const double* __restrict__ scale,
-                          int invert) {
+// out = in / |in| in FP32 (|in|^-1 derived by the preceding norm reduction)
+__global__ void k_to_f32_scaled(int64_t n, const double* __restrict__ in, float* __restrict__ out,
+                                const double* __restrict__ scal) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
-  double s = scale ? (invert ? (*scale > 0.0 ? 1.0 / sqrt(*scale) : 0.0) : sqrt(*scale)) : 1.0;
-  out[g] = (B)((double)in[g] * s);
+  out[g] = (float)in[g] * (float)scal[SC_DERIVED + SD_INV];
 }
 
-// phi += sqrt(s) * e   (FP64 accumulation of an FP32 correction)
+// phi += |r| e   (FP64 accumulation of an FP32 correction)
 __global__ void k_add_scaled(int64_t n, double* __restrict__ phi, const float* __restrict__ e,
-                             const double* __restrict__ s2) {
+                             const double* __restrict__ scal) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
-  phi[g] += sqrt(*s2) * (double)e[g];
+  phi[g] += scal[SC_DERIVED + SD_RT] * (double)e[g];
 }
 
 }  // namespace
@@ -713,9 +739,29 @@ __global__ void k_add_scaled(int64_t n, double* __restrict__ phi, const float* _
 static size_t reduce_blocks(size_t n) { return std::min<size_t>(std::max<size_t>((n + 4 * TPB - 1) / (4 * TPB), 1), 608); }
 
 template <class T>
-static void reduce(Solver* c, int N, int mode, const T* x, const T* y, double* out) {
-  size_t tot = (size_t)N * N * N;
-  FEP3M_CL k_reduce<T><<<(int)reduce_blocks(tot), TPB, 0, c->stream>>>(N, mode, x, y, (double*)c->red_tmp, c->red_counter, out);
+static void reduce(Solver* c, int N, int mode, const T* x, const T* y, double* out, int post = POST_NONE,
+                   double arg = 0.0) {
+  const size_t tot = (size_t)N * N * N;
+  const int nb = (int)reduce_blocks(tot);
+  double* tmp = (double*)c->red_tmp;
+  cudaStream_t s = c->stream;
+  if (mode == RD_DOT)
+    FEP3M_CL k_reduce<T, RD_DOT><<<nb, TPB, 0, s>>>(N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
+  else if (mode == RD_SUM)
+    FEP3M_CL k_reduce<T, RD_SUM><<<nb, TPB, 0, s>>>(N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
+  else if (mode == RD_WSUM)
+    FEP3M_CL k_reduce<T, RD_WSUM><<<nb, TPB, 0, s>>>(N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
+  else
+    FEP3M_CL k_reduce<T, RD_NORM2><<<nb, TPB, 0, s>>>(N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
+}
+
+// remove the background load (mean_zero 0) or the mean (1) with the scalar
+// that the preceding POST_MEAN reduction derived
+template <class T>
+static void project(Solver* c, int N, T* v, int mean_zero) {
+  const int bx = std::min(N, 256);
+  const dim3 grid((N + bx - 1) / bx, N, N);
+  FEP3M_CL k_project<T><<<grid, bx, 0, c->stream>>>(N, v, c->scal, mean_zero);
 }
 
 template <class T>
@@ -725,33 +771,44 @@ struct MG {
   explicit MG(Solver* cc) : c(cc), H(cc->mg) {}
 
   // one fused apply; EPI_CHEB reads x and writes the new iterate to xo (xo != x)
-  void apply(const Level& L, const T* x, int epi, T* out, const T* b, T* d, T* xo, T c1, T c2) {
+  void apply(const Level& L, const T* x, int epi, T* out, const T* b, T* d, T* xo, T c1, T c2, T c0 = T(0)) {
     cudaStream_t s = c->stream;
     const int steps = apply_steps(L.N);
     const dim3 grid((L.N + AFX - 1) / AFX, (L.N + AFY - 1) / AFY, (L.n + steps - 1) / steps);
     const size_t sm = sizeof(ApplySmem<T>);
     if (epi == EPI_Y)
-      FEP3M_CL k_apply_el<T, EPI_Y><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c1, c2);
+      FEP3M_CL k_apply_el<T, EPI_Y><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2);
     else if (epi == EPI_RESID)
-      FEP3M_CL k_apply_el<T, EPI_RESID><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c1, c2);
+      FEP3M_CL k_apply_el<T, EPI_RESID><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2);
+    else if (epi == EPI_CHEB)
+      FEP3M_CL k_apply_el<T, EPI_CHEB><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2);
     else
-      FEP3M_CL k_apply_el<T, EPI_CHEB><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c1, c2);
+      FEP3M_CL k_apply_el<T, EPI_CHEB0><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2);
   }
 
-  // Chebyshev smoothing of A x = b (D-preconditioned) on [lmax/ratio, lmax]
+  // Chebyshev smoothing of A x = b (D-preconditioned) on [lmax/ratio, lmax].
+  // from_zero: start from x = 0 (the first step, x = D^-1 b / theta, is folded
+  // into the second); otherwise the start iterate is in the level's spare
+  // buffer L.a.  Iterates alternate between L.a and x; the result is in x.
   void smooth(const Level& L, T* x, const T* b, bool from_zero, int degree) {
     const double up = 1.1 * H.lmax, lo = up / 15.0;
     const double theta = 0.5 * (up + lo), delta = 0.5 * (up - lo), sigma = theta / delta;
     double rho = 1.0 / sigma;
-    int k0 = 0;
+    T* cur = (T*)L.a;
+    T* oth = x;
     if (from_zero) {
-      FEP3M_CL k_cheb0<T><<<grid_for(L.size), TPB, 0, c->stream>>>(L.N, b, (T*)L.d, x, (T)(1.0 / theta));
-      k0 = 1;
+      if (degree <= 1) {
+        FEP3M_CL k_cheb0<T><<<dim3((L.N + 127) / 128, L.N, L.N), 128, 0, c->stream>>>(L.N, b, (T*)L.d, x,
+                                                                                      (T)(1.0 / theta));
+        return;
+      }
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      apply(L, b, EPI_CHEB0, nullptr, b, (T*)L.d, (T*)L.a, (T)(rn * rho), (T)(2.0 * rn / delta), (T)(1.0 / theta));
+      rho = rn;
+      cur = (T*)L.a;
+      oth = x;
     }
-    // iterates alternate between x and the level's spare buffer
-    T* cur = x;
-    T* oth = (T*)L.a;
-    for (int k = k0; k < degree; ++k) {
+    for (int k = from_zero ? 2 : 0; k < degree; ++k) {
       if (k == 0) {
         apply(L, cur, EPI_CHEB, nullptr, b, (T*)L.d, oth, T(0), (T)(1.0 / theta));
       } else {
@@ -813,14 +870,15 @@ struct MG {
     const int Nc = Cl.N, Nf = L.N;
     T* s1 = (T*)L.t1;
     T* s2 = (T*)L.t2;
-    FEP3M_CL k_restrict_axis<T><<<grid_for((size_t)Nc * Nf * Nf), TPB, 0, s>>>(0, Nc, Nc, Nf, Nf, (T*)L.r, s1, T(1));
-    FEP3M_CL k_restrict_axis<T><<<grid_for((size_t)Nc * Nc * Nf), TPB, 0, s>>>(1, Nc, Nc, Nc, Nf, s1, s2, T(1));
-    FEP3M_CL k_restrict_axis<T><<<grid_for(Cl.size), TPB, 0, s>>>(2, Nc, Nc, Nc, Nc, s2, (T*)Cl.b, T(0.5));
+    auto g3 = [](int e0, int e1, int e2) { return dim3((e0 + 127) / 128, e1, e2); };
+    FEP3M_CL k_restrict_axis<T><<<g3(Nc, Nf, Nf), 128, 0, s>>>(0, Nc, Nc, Nf, Nf, (T*)L.r, s1, T(1));
+    FEP3M_CL k_restrict_axis<T><<<g3(Nc, Nc, Nf), 128, 0, s>>>(1, Nc, Nc, Nc, Nf, s1, s2, T(1));
+    FEP3M_CL k_restrict_axis<T><<<g3(Nc, Nc, Nc), 128, 0, s>>>(2, Nc, Nc, Nc, Nc, s2, (T*)Cl.b, T(0.5));
     vcycle(l + 1, (T*)Cl.b, (T*)Cl.x);
-    FEP3M_CL k_prolong_axis<T, false><<<grid_for((size_t)Nc * Nc * Nf), TPB, 0, s>>>(2, Nc, Nc, Nc, Nf, (T*)Cl.x, s1);
-    FEP3M_CL k_prolong_axis<T, false><<<grid_for((size_t)Nc * Nf * Nf), TPB, 0, s>>>(1, Nc, Nc, Nf, Nf, s1, s2);
-    FEP3M_CL k_prolong_axis<T, true><<<grid_for(L.size), TPB, 0, s>>>(0, Nc, Nf, Nf, Nf, s2, x);
-    smooth(L, x, b, false, H.cheb_degree);
+    FEP3M_CL k_prolong_axis<T, false><<<g3(Nc, Nc, Nf), 128, 0, s>>>(2, Nc, Nc, Nc, Nf, (T*)Cl.x, s1, nullptr);
+    FEP3M_CL k_prolong_axis<T, false><<<g3(Nc, Nf, Nf), 128, 0, s>>>(1, Nc, Nc, Nf, Nf, s1, s2, nullptr);
+    FEP3M_CL k_prolong_axis<T, true><<<g3(Nf, Nf, Nf), 128, 0, s>>>(0, Nc, Nf, Nf, Nf, s2, (T*)L.a, x);
+    smooth(L, x, b, false, H.cheb_degree);   // starts from L.a = x + P e
   }
 
   // preconditioned CG on level 0: x = A^+ Pi b, returns iterations; the
@@ -833,10 +891,10 @@ struct MG {
     double* sc = c->scal;   // [0] rz, [1] pq, [2] rz_new, [3] rr, [4] bb, [5] sum
     const double W = (double)L.n * L.n * L.n;
     cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
-    reduce<T>(c, N, 1, r, nullptr, sc + 5);
-    FEP3M_CL k_project<T><<<grid_for(n), TPB, 0, s>>>(N, r, sc + 5, 1.0 / W, 0);
+    reduce<T>(c, N, RD_SUM, r, nullptr, sc + 5, POST_MEAN, 1.0 / W);
+    project<T>(c, N, r, 0);
     cudaMemsetAsync(x, 0, n * sizeof(T), s);
-    reduce<T>(c, N, 3, r, nullptr, sc + 4);
+    reduce<T>(c, N, RD_NORM2, r, nullptr, sc + 4);
     double bb = 0;
     cudaMemcpyAsync(&bb, sc + 4, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
@@ -846,21 +904,20 @@ struct MG {
     }
     vcycle(0, r, z);
     cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
-    reduce<T>(c, N, 0, r, z, sc + 0);
+    reduce<T>(c, N, RD_DOT, r, z, sc + 0);
     int it = 0;
     double rr = bb;
     for (it = 1; it <= maxit; ++it) {
       apply(L, p, EPI_Y, q, nullptr, nullptr, nullptr, T(0), T(0));
-      reduce<T>(c, N, 0, p, q, sc + 1);
+      reduce<T>(c, N, RD_DOT, p, q, sc + 1, POST_ALPHA);
       FEP3M_CL k_cg_update<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, x, r, p, q);
-      reduce<T>(c, N, 3, r, nullptr, sc + 3);
+      reduce<T>(c, N, RD_NORM2, r, nullptr, sc + 3);
       cudaMemcpyAsync(&rr, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s);
       cudaStreamSynchronize(s);
       if (rr <= rtol * rtol * bb) break;
       vcycle(0, r, z);
-      reduce<T>(c, N, 0, r, z, sc + 2);
+      reduce<T>(c, N, RD_DOT, r, z, sc + 2, POST_BETA);
       FEP3M_CL k_cg_dir<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, p, z);
-      cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, s);
     }
     *relres = std::sqrt(rr / bb);
     return std::min(it, maxit);
@@ -876,23 +933,22 @@ struct MG {
     double* sc = c->scal;
     const double W = (double)L.n * L.n * L.n;
     cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
-    reduce<T>(c, N, 1, r, nullptr, sc + 5);
-    FEP3M_CL k_project<T><<<grid_for(n), TPB, 0, s>>>(N, r, sc + 5, 1.0 / W, 0);
+    reduce<T>(c, N, RD_SUM, r, nullptr, sc + 5, POST_MEAN, 1.0 / W);
+    project<T>(c, N, r, 0);
     cudaMemsetAsync(x, 0, n * sizeof(T), s);
-    reduce<T>(c, N, 3, r, nullptr, sc + 4);
+    reduce<T>(c, N, RD_NORM2, r, nullptr, sc + 4);
     vcycle(0, r, z);
     cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
-    reduce<T>(c, N, 0, r, z, sc + 0);
+    reduce<T>(c, N, RD_DOT, r, z, sc + 0);
     for (int it = 1; it <= k; ++it) {
       apply(L, p, EPI_Y, q, nullptr, nullptr, nullptr, T(0), T(0));
-      reduce<T>(c, N, 0, p, q, sc + 1);
+      reduce<T>(c, N, RD_DOT, p, q, sc + 1, POST_ALPHA);
       FEP3M_CL k_cg_update<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, x, r, p, q);
-      reduce<T>(c, N, 3, r, nullptr, sc + 3);
+      reduce<T>(c, N, RD_NORM2, r, nullptr, sc + 3);
       if (it == k) break;
       vcycle(0, r, z);
-      reduce<T>(c, N, 0, r, z, sc + 2);
+      reduce<T>(c, N, RD_DOT, r, z, sc + 2, POST_BETA);
       FEP3M_CL k_cg_dir<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, p, z);
-      cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, s);
     }
   }
 };
@@ -924,6 +980,16 @@ static void upload_constants(const Stencils& st) {
   cudaMemcpyToSymbol(cP32, P32, sizeof(P32));
   cudaMemcpyToSymbol(cDM32, DM32, sizeof(DM32));
   cudaMemcpyToSymbol(cDK32, DK32, sizeof(DK32));
+  double Di64[27];
+  float Di32[27];
+  for (int k = 0; k < 27; ++k) {
+    const int a = k % 3, b = (k / 3) % 3, cz = k / 9;
+    Di64[k] = 1.0 / (st.diagK[a] * st.diagM[b] * st.diagM[cz] + st.diagM[a] * st.diagK[b] * st.diagM[cz] +
+                     st.diagM[a] * st.diagM[b] * st.diagK[cz]);
+    Di32[k] = 1.0f / (DK32[a] * DM32[b] * DM32[cz] + DM32[a] * DK32[b] * DM32[cz] + DM32[a] * DM32[b] * DK32[cz]);
+  }
+  cudaMemcpyToSymbol(cDinv64, Di64, sizeof(Di64));
+  cudaMemcpyToSymbol(cDinv32, Di32, sizeof(Di32));
   if (dev < 64) done[dev] = true;
 }
 
@@ -1049,7 +1115,7 @@ static cudaError_t apply64(Solver* c, const double* x, const double* b, double* 
   const int steps = apply_steps(N);
   const dim3 grid((N + AFX - 1) / AFX, (N + AFY - 1) / AFY, (L0.n + steps - 1) / steps);
   FEP3M_CL k_apply_el<double, EPI_RESID><<<grid, AT, sizeof(ApplySmem<double>), c->stream>>>(
-      N, steps, x, r, b, nullptr, nullptr, 0.0, 0.0);
+      N, steps, x, r, b, nullptr, nullptr, 0.0, 0.0, 0.0);
   return cudaGetLastError();
 }
 
@@ -1071,8 +1137,8 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
     const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : 1e-13;
     const int maxit = c->cfg.mg_max_cycles > 0 ? c->cfg.mg_max_cycles : 60;
     *iters = mg.pcg(b, phi, (double*)sb[0], (double*)sb[1], (double*)sb[2], (double*)sb[3], rtol, maxit, relres);
-    reduce<double>(c, N, 2, phi, nullptr, sc + 6);
-    FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, phi, sc + 6, 1.0 / W, 1);
+    reduce<double>(c, N, RD_WSUM, phi, nullptr, sc + 6, POST_MEAN, 1.0 / W);
+    project<double>(c, N, phi, 1);
     return cudaGetLastError();
   }
   MG<float> mg(c);
@@ -1081,9 +1147,9 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
   double* r64 = c->res64;
   cudaMemsetAsync(phi, 0, n * sizeof(double), s);
   cudaMemcpyAsync(r64, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  reduce<double>(c, N, 1, r64, nullptr, sc + 5);
-  FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, r64, sc + 5, 1.0 / W, 0);
-  reduce<double>(c, N, 3, r64, nullptr, sc + 7);
+  reduce<double>(c, N, RD_SUM, r64, nullptr, sc + 5, POST_MEAN, 1.0 / W);
+  project<double>(c, N, r64, 0);
+  reduce<double>(c, N, RD_NORM2, r64, nullptr, sc + 7);
   double bb = 0;
   cudaMemcpyAsync(&bb, sc + 7, sizeof(double), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
@@ -1093,19 +1159,19 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
   double rr = bb;
   int step = 0;
   for (step = 0; step < maxout; ++step) {
-    reduce<double>(c, N, 3, r64, nullptr, sc + 8);
-    FEP3M_CL k_convert<double, float><<<grid_for(n), TPB, 0, s>>>((int64_t)n, r64, (float*)sb[5], sc + 8, 1);
+    reduce<double>(c, N, RD_NORM2, r64, nullptr, sc + 8, POST_NORM);
+    FEP3M_CL k_to_f32_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, r64, (float*)sb[5], sc);
     double inner_res = 0;
     int it = mg.pcg((float*)sb[5], (float*)sb[4], (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], 1e-5, 30,
                     &inner_res);
     *iters += it;
     *k_inner_max = std::max(*k_inner_max, it);
-    FEP3M_CL k_add_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phi, (float*)sb[4], sc + 8);
+    FEP3M_CL k_add_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phi, (float*)sb[4], sc);
     cudaError_t e = apply64(c, phi, b, r64);   // r64 = b - K phi
     if (e != cudaSuccess) return e;
-    reduce<double>(c, N, 1, r64, nullptr, sc + 5);
-    FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, r64, sc + 5, 1.0 / W, 0);
-    reduce<double>(c, N, 3, r64, nullptr, sc + 9);
+    reduce<double>(c, N, RD_SUM, r64, nullptr, sc + 5, POST_MEAN, 1.0 / W);
+    project<double>(c, N, r64, 0);
+    reduce<double>(c, N, RD_NORM2, r64, nullptr, sc + 9);
     cudaMemcpyAsync(&rr, sc + 9, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     if (rr <= rtol * rtol * bb) {
@@ -1115,8 +1181,8 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
   }
   *refine_steps = step;
   *relres = std::sqrt(rr / bb);
-  reduce<double>(c, N, 2, phi, nullptr, sc + 6);
-  FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, phi, sc + 6, 1.0 / W, 1);
+  reduce<double>(c, N, RD_WSUM, phi, nullptr, sc + 6, POST_MEAN, 1.0 / W);
+  project<double>(c, N, phi, 1);
   return cudaGetLastError();
 }
 
@@ -1135,8 +1201,8 @@ static cudaError_t solve_fixed(Solver* c) {
     mg.pcg_fixed(c->in64, c->out64, (double*)sb[0], (double*)sb[1], (double*)sb[2], (double*)sb[3], c->plan_k);
     cudaMemcpyAsync(sc + 10, sc + 4, sizeof(double), cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(sc + 11, sc + 3, sizeof(double), cudaMemcpyDeviceToDevice, s);
-    reduce<double>(c, N, 2, c->out64, nullptr, sc + 6);
-    FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, c->out64, sc + 6, 1.0 / W, 1);
+    reduce<double>(c, N, RD_WSUM, c->out64, nullptr, sc + 6, POST_MEAN, 1.0 / W);
+    project<double>(c, N, c->out64, 1);
     return cudaGetLastError();
   }
   MG<float> mg(c);
@@ -1144,23 +1210,23 @@ static cudaError_t solve_fixed(Solver* c) {
   double* phi = c->out64;
   cudaMemsetAsync(phi, 0, n * sizeof(double), s);
   cudaMemcpyAsync(r64, c->in64, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  reduce<double>(c, N, 1, r64, nullptr, sc + 5);
-  FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, r64, sc + 5, 1.0 / W, 0);
-  reduce<double>(c, N, 3, r64, nullptr, sc + 10);
+  reduce<double>(c, N, RD_SUM, r64, nullptr, sc + 5, POST_MEAN, 1.0 / W);
+  project<double>(c, N, r64, 0);
+  reduce<double>(c, N, RD_NORM2, r64, nullptr, sc + 10);
   for (int step = 0; step < c->plan_kout; ++step) {
-    reduce<double>(c, N, 3, r64, nullptr, sc + 8);
-    FEP3M_CL k_convert<double, float><<<grid_for(n), TPB, 0, s>>>((int64_t)n, r64, (float*)sb[5], sc + 8, 1);
+    reduce<double>(c, N, RD_NORM2, r64, nullptr, sc + 8, POST_NORM);
+    FEP3M_CL k_to_f32_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, r64, (float*)sb[5], sc);
     mg.pcg_fixed((float*)sb[5], (float*)sb[4], (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3],
                  c->plan_kin);
-    FEP3M_CL k_add_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phi, (float*)sb[4], sc + 8);
+    FEP3M_CL k_add_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phi, (float*)sb[4], sc);
     cudaError_t e = apply64(c, phi, c->in64, r64);
     if (e != cudaSuccess) return e;
-    reduce<double>(c, N, 1, r64, nullptr, sc + 5);
-    FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, r64, sc + 5, 1.0 / W, 0);
+    reduce<double>(c, N, RD_SUM, r64, nullptr, sc + 5, POST_MEAN, 1.0 / W);
+    project<double>(c, N, r64, 0);
   }
-  reduce<double>(c, N, 3, r64, nullptr, sc + 11);
-  reduce<double>(c, N, 2, phi, nullptr, sc + 6);
-  FEP3M_CL k_project<double><<<grid_for(n), TPB, 0, s>>>(N, phi, sc + 6, 1.0 / W, 1);
+  reduce<double>(c, N, RD_NORM2, r64, nullptr, sc + 11);
+  reduce<double>(c, N, RD_WSUM, phi, nullptr, sc + 6, POST_MEAN, 1.0 / W);
+  project<double>(c, N, phi, 1);
   return cudaGetLastError();
 }
 
