@@ -97,7 +97,8 @@ struct Solver {
   double* scal = nullptr;          // device scalars (64)
   double* red_tmp = nullptr;       // reduction partials (1024)
   unsigned int* red_counter = nullptr;
-  double* res64 = nullptr;         // FP64 refinement residual
+  double* res64 = nullptr;         // refinement: projected b as float pairs (MIXED)
+  double* phidf = nullptr;         // refinement: the iterate as float pairs (MIXED)
   // replayed solve: iteration counts calibrated on the first solve, captured as a graph
   int plan_k = 0, plan_kin = 0, plan_kout = 0;
   cudaGraphExec_t solve_exec = nullptr;

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -30,6 +31,38 @@ __constant__ float cM32[3][7], cK32[3][7], cP32[6][4], cDM32[3], cDK32[3];
 __constant__ double cDinv64[27];
 __constant__ float cDinv32[27];
 
+// Double-float value h + l (two FP32 numbers, about 48 significant bits),
+// for the refinement residual: FP64 arithmetic is a small fraction of the
+// FP32 rate on this GPU.  A product keeps its exact rounding error (FMA
+// two-product) plus the cross terms; a sum keeps its exact rounding error
+// (two-sum, Knuth) in l.  Values stay unnormalised (|l| may exceed half an
+// ulp of h); the represented number is always h + l.
+struct dfv {
+  float h, l;
+};
+__device__ __forceinline__ dfv operator*(dfv c, dfv x) {
+  const float p = c.h * x.h;
+  float e = fmaf(c.h, x.h, -p);
+  e = fmaf(c.h, x.l, e);
+  e = fmaf(c.l, x.h, e);
+  return {p, e};
+}
+__device__ __forceinline__ dfv& operator+=(dfv& s, dfv t) {
+  const float a = s.h, b = t.h;
+  const float sum = a + b;
+  const float bv = sum - a;
+  const float err = (a - (sum - bv)) + (b - bv);
+  s.h = sum;
+  s.l = (s.l + t.l) + err;
+  return s;
+}
+__device__ __forceinline__ dfv& operator*=(dfv& s, dfv t) {
+  s = s * t;
+  return s;
+}
+
+__constant__ float cMh[3][7], cMl[3][7], cKh[3][7], cKl[3][7];
+
 template <class T> struct Cst;
 template <> struct Cst<double> {
   static __device__ __forceinline__ double M(int t, int j) { return cM64[t][j]; }
@@ -38,6 +71,11 @@ template <> struct Cst<double> {
   static __device__ __forceinline__ double DM(int t) { return cDM64[t]; }
   static __device__ __forceinline__ double DK(int t) { return cDK64[t]; }
   static __device__ __forceinline__ double Dinv(int k) { return cDinv64[k]; }
+};
+template <> struct Cst<dfv> {
+  static __device__ __forceinline__ dfv M(int t, int j) { return {cMh[t][j], cMl[t][j]}; }
+  static __device__ __forceinline__ dfv K(int t, int j) { return {cKh[t][j], cKl[t][j]}; }
+  static __device__ __forceinline__ dfv Dinv(int k) { return {cDinv32[k], 0.0f}; }
 };
 template <> struct Cst<float> {
   static __device__ __forceinline__ float M(int t, int j) { return cM32[t][j]; }
@@ -128,6 +166,11 @@ __global__ void k_load_vector(int n, const T* __restrict__ rv, double* __restric
 // ------------------------------------------------------------ operator apply
 enum { EPI_Y = 0, EPI_RESID = 1, EPI_CHEB = 2, EPI_CHEB0 = 3 };
 
+// scalars derived on the device by the reductions: doubles at
+// scal[SC_DERIVED + k], floats at ((float*)(scal + SC_DERIVED_F))[k]
+constexpr int SC_DERIVED = 16, SC_DERIVED_F = 32;
+enum { SD_ALPHA = 0, SD_BETA = 1, SD_MEAN = 2, SD_SCALE = 3, SD_INVSCALE = 4 };
+
 // Fused apply y = K x, tiled by elements (2.5-D).  A CTA owns an AFX x AFY
 // column of output nodes (AEX x AEY elements, origin on a vertex) and marches
 // in z one element (three planes) at a time.  Since tiles and z steps start on
@@ -208,12 +251,20 @@ __device__ __forceinline__ T st_KM(const T* u, const T* w) {
 template <class T, int EPI>
 __device__ __forceinline__ void apply_epilogue(int64_t g, T y, T* __restrict__ out, const T* __restrict__ b,
                                                T* __restrict__ d, const T* __restrict__ x, T* __restrict__ xo,
-                                               T c0, T c1, T c2, T dv) {
-  if (EPI == EPI_Y) {
+                                               T c0, T c1, T c2, T dv, float rs) {
+  if constexpr (std::is_same<T, dfv>::value) {
+    static_assert(EPI == EPI_RESID, "the double-float apply computes residuals only");
+    // FP32 output rs (b - y): the double-float difference (two-sum), rounded
+    const dfv bg = b[g];
+    const float sm = bg.h - y.h;
+    const float bv = sm - bg.h;
+    const float err = (bg.h - (sm - bv)) + (-y.h - bv);
+    reinterpret_cast<float*>(out)[g] = (sm + ((bg.l - y.l) + err)) * rs;
+  } else if constexpr (EPI == EPI_Y) {
     out[g] = y;
-  } else if (EPI == EPI_RESID) {
+  } else if constexpr (EPI == EPI_RESID) {
     out[g] = b[g] - y;
-  } else if (EPI == EPI_CHEB) {
+  } else if constexpr (EPI == EPI_CHEB) {
     const T dn = c1 * d[g] + c2 * dv * (b[g] - y);
     d[g] = dn;
     xo[g] = x[g] + dn;
@@ -226,11 +277,13 @@ __device__ __forceinline__ void apply_epilogue(int64_t g, T y, T* __restrict__ o
 }
 
 // grid: (ceil(N / AFX), ceil(N / AFY), ceil(n / steps)), AT threads, dynamic
-// shared memory sizeof(ApplySmem<T>); N = 3 n with n >= 3
+// shared memory sizeof(ApplySmem<T>); N = 3 n with n >= 3.  T = dfv: x and b
+// are float pairs, out is FP32 and receives the residual times the power of
+// two the scaling reduction derived (scal)
 template <class T, int EPI>
 __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, int steps, const T* __restrict__ x, T* __restrict__ out,
                                                  const T* __restrict__ b, T* __restrict__ d, T* __restrict__ xo,
-                                                 T c0, T c1, T c2) {
+                                                 T c0, T c1, T c2, const double* __restrict__ scal) {
   extern __shared__ __align__(16) unsigned char apply_smem_raw[];
   ApplySmem<T>& S = *reinterpret_cast<ApplySmem<T>*>(apply_smem_raw);
   const int n = N / 3;
@@ -238,11 +291,11 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, 
   const int x0 = blockIdx.x * AFX, y0 = blockIdx.y * AFY;
   const int e0 = blockIdx.z * steps, e1 = min(n, e0 + steps);
   const int tid = threadIdx.x;
-  if (tid < 27) {
-    const int a = tid % 3, bb = (tid / 3) % 3, cz = tid / 9;
-    S.dinv[tid] = T(1) / (Cst<T>::DK(a) * Cst<T>::DM(bb) * Cst<T>::DM(cz) +
-                          Cst<T>::DM(a) * Cst<T>::DK(bb) * Cst<T>::DM(cz) +
-                          Cst<T>::DM(a) * Cst<T>::DM(bb) * Cst<T>::DK(cz));
+  float rs = 0.0f;
+  if constexpr (std::is_same<T, dfv>::value) {
+    rs = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_SCALE];
+  } else {
+    if (tid < 27) S.dinv[tid] = Cst<T>::Dinv(tid);
   }
   // this thread's halo columns (periodic in x and y); columns past the halo
   // read column 0 and store nothing
@@ -357,9 +410,9 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, 
         }
         const int64_t g = (int64_t)(3 * e + p) * NN + (int64_t)gy * N + gx0;
         const T* dv = S.dinv + 3 * ty3 + 9 * p;
-        apply_epilogue<T, EPI>(g, st_KM<T, 0>(u, v), out, b, d, x, xo, c0, c1, c2, dv[0]);
-        apply_epilogue<T, EPI>(g + 1, st_KM<T, 1>(u + 1, v + 1), out, b, d, x, xo, c0, c1, c2, dv[1]);
-        apply_epilogue<T, EPI>(g + 2, st_KM<T, 2>(u + 2, v + 2), out, b, d, x, xo, c0, c1, c2, dv[2]);
+        apply_epilogue<T, EPI>(g, st_KM<T, 0>(u, v), out, b, d, x, xo, c0, c1, c2, dv[0], rs);
+        apply_epilogue<T, EPI>(g + 1, st_KM<T, 1>(u + 1, v + 1), out, b, d, x, xo, c0, c1, c2, dv[1], rs);
+        apply_epilogue<T, EPI>(g + 2, st_KM<T, 2>(u + 2, v + 2), out, b, d, x, xo, c0, c1, c2, dv[2], rs);
       }
     }
     // next element: slots 0..3 <- 3..6, slots 4..6 <- the prefetched planes
@@ -390,10 +443,15 @@ static cudaError_t apply_set_smem_t() {
   return cudaFuncSetAttribute(k_apply_el<T, EPI_CHEB0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
-// the FP64 tiles need more than the default 48 KB of dynamic shared memory
+// the FP64 and double-float tiles need more than the default 48 KB of
+// dynamic shared memory
 static cudaError_t apply_set_smem() {
   cudaError_t e = apply_set_smem_t<float>();
-  return e != cudaSuccess ? e : apply_set_smem_t<double>();
+  if (e == cudaSuccess) e = apply_set_smem_t<double>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_apply_el<dfv, EPI_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(ApplySmem<dfv>));
+  return e;
 }
 
 // elements per CTA in z: enough CTAs to fill the GPU a few times over
@@ -424,6 +482,11 @@ __global__ void k_cheb0(int N, const T* __restrict__ b, T* __restrict__ d, T* __
 template <class T>
 __global__ void k_restrict_axis(int axis, int Nc, int e0, int e1, int e2, const T* __restrict__ in,
                                 T* __restrict__ out, T scale) {
+  // the row of P depends on the lane: read it from shared memory, not from
+  // the constant bank (which serialises lanes that read different addresses)
+  __shared__ T Ps[6][4];
+  if (threadIdx.x < 24) Ps[threadIdx.x / 4][threadIdx.x % 4] = Cst<T>::P(threadIdx.x / 4, threadIdx.x % 4);
+  __syncthreads();
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
   if (ix >= e0) return;
   int i[3] = {ix, (int)blockIdx.y, (int)blockIdx.z};
@@ -438,12 +501,12 @@ __global__ void k_restrict_axis(int axis, int Nc, int e0, int e1, int e2, const 
   const int E = gc / 3, j = gc - 3 * E;
   T acc = T(0);
 #pragma unroll
-  for (int s = 1; s < 6; ++s) acc += Cst<T>::P(s, j) * in[base + (6 * E + s) * st[axis]];
+  for (int s = 1; s < 6; ++s) acc += Ps[s][j] * in[base + (6 * E + s) * st[axis]];
   if (j == 0) {
     acc += in[base + (6 * E) * st[axis]];   // P[0][0] = 1
     const int El = E == 0 ? Nc / 3 - 1 : E - 1;
 #pragma unroll
-    for (int s = 1; s < 6; ++s) acc += Cst<T>::P(s, 3) * in[base + (6 * El + s) * st[axis]];
+    for (int s = 1; s < 6; ++s) acc += Ps[s][3] * in[base + (6 * El + s) * st[axis]];
   }
   out[g] = scale * acc;
 }
@@ -453,6 +516,9 @@ __global__ void k_restrict_axis(int axis, int Nc, int e0, int e1, int e2, const 
 template <class T, bool ADD>
 __global__ void k_prolong_axis(int axis, int Nc, int e0, int e1, int e2, const T* __restrict__ in,
                                T* __restrict__ out, const T* __restrict__ add) {
+  __shared__ T Ps[6][4];
+  if (threadIdx.x < 24) Ps[threadIdx.x / 4][threadIdx.x % 4] = Cst<T>::P(threadIdx.x / 4, threadIdx.x % 4);
+  __syncthreads();
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
   if (ix >= e0) return;
   int i[3] = {ix, (int)blockIdx.y, (int)blockIdx.z};
@@ -469,7 +535,7 @@ __global__ void k_prolong_axis(int axis, int Nc, int e0, int e1, int e2, const T
   for (int j = 0; j < 4; ++j) {
     int gc = 3 * E + j;
     if (gc >= Nc) gc -= Nc;
-    acc += Cst<T>::P(s, j) * in[base + gc * st[axis]];
+    acc += Ps[s][j] * in[base + gc * st[axis]];
   }
   if (ADD) out[g] = add[g] + acc;
   else out[g] = acc;
@@ -563,11 +629,7 @@ __global__ void __launch_bounds__(256) k_dense_tile(int N, int axis, const T* __
 enum { RD_DOT = 0, RD_SUM = 1, RD_WSUM = 2, RD_NORM2 = 3 };
 // what the last block derives from the total t (written next to it, so that
 // the consumers read one ready scalar instead of recomputing it per node)
-enum { POST_NONE = 0, POST_ALPHA = 1, POST_BETA = 2, POST_MEAN = 3, POST_NORM = 4 };
-// derived scalars: doubles at scal[SC_DERIVED + k], floats at
-// ((float*)(scal + SC_DERIVED_F))[k]
-constexpr int SC_DERIVED = 16, SC_DERIVED_F = 32;
-enum { SD_ALPHA = 0, SD_BETA = 1, SD_MEAN = 2, SD_INV = 3, SD_RT = 4 };
+enum { POST_NONE = 0, POST_ALPHA = 1, POST_BETA = 2, POST_MEAN = 3, POST_SCALE = 4 };
 
 // node-integral weight of a node of the given types: (1/4 or 3/8 per axis)
 __device__ __forceinline__ double node_weight(int tx, int ty, int tz) {
@@ -663,9 +725,14 @@ __global__ void k_reduce(int N, const T* __restrict__ x, const T* __restrict__ y
       } else if (post == POST_MEAN) {    // t * arg (arg = 1 / W)
         dd[SD_MEAN] = t * arg;
         df[SD_MEAN] = (float)(t * arg);
-      } else if (post == POST_NORM) {    // 1 / sqrt(t) and sqrt(t)
-        dd[SD_INV] = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
-        dd[SD_RT] = sqrt(t);
+      } else if (post == POST_SCALE) {   // 2^-k with 2^k near the RMS sqrt(t arg)
+        const double rms = sqrt(t * arg);
+        int k = rms > 0.0 && isfinite(rms) ? ilogb(rms) : 0;
+        k = max(-100, min(100, k));
+        dd[SD_SCALE] = ldexp(1.0, -k);
+        dd[SD_INVSCALE] = ldexp(1.0, k);
+        df[SD_SCALE] = (float)ldexp(1.0, -k);
+        df[SD_INVSCALE] = (float)ldexp(1.0, k);
       }
     }
   }
@@ -714,20 +781,51 @@ __global__ void k_cg_dir(int64_t n, const double* __restrict__ scal, T* __restri
   p[g] = z[g] + beta * p[g];
 }
 
-// out = in / |in| in FP32 (|in|^-1 derived by the preceding norm reduction)
-__global__ void k_to_f32_scaled(int64_t n, const double* __restrict__ in, float* __restrict__ out,
-                                const double* __restrict__ scal) {
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  out[g] = (float)in[g] * (float)scal[SC_DERIVED + SD_INV];
+// ------------------------------------------- double-float refinement helpers
+// bdf = b - m w3 as float pairs (m = sum b / W from the preceding reduction);
+// grid (ceil(N / bx), N, N)
+__global__ void k_split_df(int N, const double* __restrict__ b, const double* __restrict__ scal, dfv* __restrict__ bdf) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= N) return;
+  const int iy = blockIdx.y, iz = blockIdx.z;
+  const int64_t g = ix + (int64_t)N * (iy + (int64_t)N * iz);
+  const double w = (ix % 3 ? 0.375 : 0.25) * (iy % 3 ? 0.375 : 0.25) * (iz % 3 ? 0.375 : 0.25);
+  const double v = b[g] - scal[SC_DERIVED + SD_MEAN] * w;
+  const float h = (float)v;
+  bdf[g] = {h, (float)(v - (double)h)};
 }
 
-// phi += |r| e   (FP64 accumulation of an FP32 correction)
-__global__ void k_add_scaled(int64_t n, double* __restrict__ phi, const float* __restrict__ e,
-                             const double* __restrict__ scal) {
+// r = s (h + l) rounded to FP32 (s the power-of-two scale)
+__global__ void k_df_round_scaled(int64_t n, const dfv* __restrict__ v, float* __restrict__ r,
+                                  const double* __restrict__ scal) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
-  phi[g] += scal[SC_DERIVED + SD_RT] * (double)e[g];
+  const float s = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_SCALE];
+  const dfv x = v[g];
+  r[g] = (x.h + x.l) * s;
+}
+
+// phi += e / s (exact: s is a power of two), two-sum then renormalised
+__global__ void k_df_update(int64_t n, dfv* __restrict__ phi, const float* __restrict__ e,
+                            const double* __restrict__ scal) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const float is = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_INVSCALE];
+  dfv p = phi[g];
+  const float t = e[g] * is;
+  const float sum = p.h + t;
+  const float bv = sum - p.h;
+  const float err = (p.h - (sum - bv)) + (t - bv);
+  const float lo = p.l + err;
+  const float h = sum + lo;
+  phi[g] = {h, lo - (h - sum)};
+}
+
+__global__ void k_df_to_double(int64_t n, const dfv* __restrict__ v, double* __restrict__ out) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const dfv x = v[g];
+  out[g] = (double)x.h + (double)x.l;
 }
 
 }  // namespace
@@ -777,13 +875,13 @@ struct MG {
     const dim3 grid((L.N + AFX - 1) / AFX, (L.N + AFY - 1) / AFY, (L.n + steps - 1) / steps);
     const size_t sm = sizeof(ApplySmem<T>);
     if (epi == EPI_Y)
-      FEP3M_CL k_apply_el<T, EPI_Y><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2);
+      FEP3M_CL k_apply_el<T, EPI_Y><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
     else if (epi == EPI_RESID)
-      FEP3M_CL k_apply_el<T, EPI_RESID><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2);
+      FEP3M_CL k_apply_el<T, EPI_RESID><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
     else if (epi == EPI_CHEB)
-      FEP3M_CL k_apply_el<T, EPI_CHEB><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2);
+      FEP3M_CL k_apply_el<T, EPI_CHEB><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
     else
-      FEP3M_CL k_apply_el<T, EPI_CHEB0><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2);
+      FEP3M_CL k_apply_el<T, EPI_CHEB0><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
   }
 
   // Chebyshev smoothing of A x = b (D-preconditioned) on [lmax/ratio, lmax].
@@ -989,6 +1087,19 @@ static void upload_constants(const Stencils& st) {
     Di32[k] = 1.0f / (DK32[a] * DM32[b] * DM32[cz] + DM32[a] * DK32[b] * DM32[cz] + DM32[a] * DM32[b] * DK32[cz]);
   }
   cudaMemcpyToSymbol(cDinv64, Di64, sizeof(Di64));
+  // double-float stencils: h = fl32(c), l = fl32(c - h)
+  float Mh[3][7], Ml[3][7], Kh[3][7], Kl[3][7];
+  for (int t = 0; t < 3; ++t)
+    for (int j = 0; j < 7; ++j) {
+      Mh[t][j] = (float)st.M[t][j];
+      Ml[t][j] = (float)(st.M[t][j] - (double)Mh[t][j]);
+      Kh[t][j] = (float)st.K[t][j];
+      Kl[t][j] = (float)(st.K[t][j] - (double)Kh[t][j]);
+    }
+  cudaMemcpyToSymbol(cMh, Mh, sizeof(Mh));
+  cudaMemcpyToSymbol(cMl, Ml, sizeof(Ml));
+  cudaMemcpyToSymbol(cKh, Kh, sizeof(Kh));
+  cudaMemcpyToSymbol(cKl, Kl, sizeof(Kl));
   cudaMemcpyToSymbol(cDinv32, Di32, sizeof(Di32));
   if (dev < 64) done[dev] = true;
 }
@@ -1108,15 +1219,45 @@ static cudaError_t ensure_solver_buffers(Solver* c) {
   return cudaSuccess;
 }
 
-// r = b - K x in FP64 on the fine level (the refinement residual)
-static cudaError_t apply64(Solver* c, const double* x, const double* b, double* r) {
+// r = s (b - K phi) in FP32 from the double-float phi and b (the refinement
+// residual; s the power-of-two scale in the derived scalars)
+static cudaError_t resid_df(Solver* c, const dfv* phi, const dfv* b, float* r) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
   const int steps = apply_steps(N);
   const dim3 grid((N + AFX - 1) / AFX, (N + AFY - 1) / AFY, (L0.n + steps - 1) / steps);
-  FEP3M_CL k_apply_el<double, EPI_RESID><<<grid, AT, sizeof(ApplySmem<double>), c->stream>>>(
-      N, steps, x, r, b, nullptr, nullptr, 0.0, 0.0, 0.0);
+  const dfv z = {0.0f, 0.0f};
+  FEP3M_CL k_apply_el<dfv, EPI_RESID><<<grid, AT, sizeof(ApplySmem<dfv>), c->stream>>>(
+      N, steps, phi, reinterpret_cast<dfv*>(r), b, nullptr, nullptr, z, z, z, c->scal);
   return cudaGetLastError();
+}
+
+// start of a MIXED solve: bdf = Pi b as float pairs, the power-of-two scale s
+// (2^-k with 2^k near the RMS of b), phidf = 0 and r = s Pi b in FP32
+static void refine_setup(Solver* c, const double* b, dfv* bdf, dfv* phidf, float* r) {
+  const Level& L0 = c->mg.lv[0];
+  const int N = L0.N;
+  const size_t n = L0.size;
+  const double W = (double)L0.n * L0.n * L0.n;
+  cudaStream_t s = c->stream;
+  double* sc = c->scal;
+  reduce<double>(c, N, RD_SUM, b, nullptr, sc + 5, POST_MEAN, 1.0 / W);
+  reduce<double>(c, N, RD_NORM2, b, nullptr, sc + 7, POST_SCALE, 1.0 / (double)n);
+  const int bx = std::min(N, 256);
+  FEP3M_CL k_split_df<<<dim3((N + bx - 1) / bx, N, N), bx, 0, s>>>(N, b, sc, bdf);
+  cudaMemsetAsync(phidf, 0, n * sizeof(dfv), s);
+  FEP3M_CL k_df_round_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, bdf, r, sc);
+}
+
+// end of a MIXED solve: phi = phidf in FP64, mean zero
+static void refine_finish(Solver* c, const dfv* phidf, double* phi) {
+  const Level& L0 = c->mg.lv[0];
+  const int N = L0.N;
+  const size_t n = L0.size;
+  const double W = (double)L0.n * L0.n * L0.n;
+  FEP3M_CL k_df_to_double<<<grid_for(n), TPB, 0, c->stream>>>((int64_t)n, phidf, phi);
+  reduce<double>(c, N, RD_WSUM, phi, nullptr, c->scal + 6, POST_MEAN, 1.0 / W);
+  project<double>(c, N, phi, 1);
 }
 
 // host-checked solve (used once to calibrate the iteration counts, and as the
@@ -1141,37 +1282,40 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
     project<double>(c, N, phi, 1);
     return cudaGetLastError();
   }
+  // MIXED: iterative refinement.  The iterate and Pi b are double-float, the
+  // residual is formed in double-float arithmetic and rounded to FP32, the
+  // correction comes from the FP32 multigrid-preconditioned CG.
   MG<float> mg(c);
   const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : 1e-10;
   const int maxout = c->cfg.mg_max_cycles > 0 ? c->cfg.mg_max_cycles : 8;
-  double* r64 = c->res64;
-  cudaMemsetAsync(phi, 0, n * sizeof(double), s);
-  cudaMemcpyAsync(r64, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  reduce<double>(c, N, RD_SUM, r64, nullptr, sc + 5, POST_MEAN, 1.0 / W);
-  project<double>(c, N, r64, 0);
-  reduce<double>(c, N, RD_NORM2, r64, nullptr, sc + 7);
+  dfv* bdf = reinterpret_cast<dfv*>(c->res64);
+  dfv* phd = reinterpret_cast<dfv*>(c->phidf);
+  float* r32 = (float*)sb[5];
+  float* e32 = (float*)sb[4];
+  refine_setup(c, b, bdf, phd, r32);
+  reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 10);
   double bb = 0;
-  cudaMemcpyAsync(&bb, sc + 7, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&bb, sc + 10, sizeof(double), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   *iters = 0;
   *relres = 0;
-  if (bb == 0.0) return cudaGetLastError();
+  if (bb == 0.0) {
+    refine_finish(c, phd, phi);
+    return cudaGetLastError();
+  }
   double rr = bb;
   int step = 0;
   for (step = 0; step < maxout; ++step) {
-    reduce<double>(c, N, RD_NORM2, r64, nullptr, sc + 8, POST_NORM);
-    FEP3M_CL k_to_f32_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, r64, (float*)sb[5], sc);
     double inner_res = 0;
-    int it = mg.pcg((float*)sb[5], (float*)sb[4], (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], 1e-5, 30,
-                    &inner_res);
+    int it = mg.pcg(r32, e32, (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], 1e-5, 30, &inner_res);
     *iters += it;
     *k_inner_max = std::max(*k_inner_max, it);
-    FEP3M_CL k_add_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phi, (float*)sb[4], sc);
-    cudaError_t e = apply64(c, phi, b, r64);   // r64 = b - K phi
+    FEP3M_CL k_df_update<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phd, e32, sc);
+    // the residual's sum is rounding noise (K has zero column sums), and the
+    // inner solve projects its right-hand side: no projection here
+    cudaError_t e = resid_df(c, phd, bdf, r32);
     if (e != cudaSuccess) return e;
-    reduce<double>(c, N, RD_SUM, r64, nullptr, sc + 5, POST_MEAN, 1.0 / W);
-    project<double>(c, N, r64, 0);
-    reduce<double>(c, N, RD_NORM2, r64, nullptr, sc + 9);
+    reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 9);
     cudaMemcpyAsync(&rr, sc + 9, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     if (rr <= rtol * rtol * bb) {
@@ -1181,8 +1325,7 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
   }
   *refine_steps = step;
   *relres = std::sqrt(rr / bb);
-  reduce<double>(c, N, RD_WSUM, phi, nullptr, sc + 6, POST_MEAN, 1.0 / W);
-  project<double>(c, N, phi, 1);
+  refine_finish(c, phd, phi);
   return cudaGetLastError();
 }
 
@@ -1206,27 +1349,20 @@ static cudaError_t solve_fixed(Solver* c) {
     return cudaGetLastError();
   }
   MG<float> mg(c);
-  double* r64 = c->res64;
-  double* phi = c->out64;
-  cudaMemsetAsync(phi, 0, n * sizeof(double), s);
-  cudaMemcpyAsync(r64, c->in64, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  reduce<double>(c, N, RD_SUM, r64, nullptr, sc + 5, POST_MEAN, 1.0 / W);
-  project<double>(c, N, r64, 0);
-  reduce<double>(c, N, RD_NORM2, r64, nullptr, sc + 10);
+  dfv* bdf = reinterpret_cast<dfv*>(c->res64);
+  dfv* phd = reinterpret_cast<dfv*>(c->phidf);
+  float* r32 = (float*)sb[5];
+  float* e32 = (float*)sb[4];
+  refine_setup(c, c->in64, bdf, phd, r32);
+  reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 10);
   for (int step = 0; step < c->plan_kout; ++step) {
-    reduce<double>(c, N, RD_NORM2, r64, nullptr, sc + 8, POST_NORM);
-    FEP3M_CL k_to_f32_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, r64, (float*)sb[5], sc);
-    mg.pcg_fixed((float*)sb[5], (float*)sb[4], (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3],
-                 c->plan_kin);
-    FEP3M_CL k_add_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phi, (float*)sb[4], sc);
-    cudaError_t e = apply64(c, phi, c->in64, r64);
+    mg.pcg_fixed(r32, e32, (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], c->plan_kin);
+    FEP3M_CL k_df_update<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phd, e32, sc);
+    cudaError_t e = resid_df(c, phd, bdf, r32);
     if (e != cudaSuccess) return e;
-    reduce<double>(c, N, RD_SUM, r64, nullptr, sc + 5, POST_MEAN, 1.0 / W);
-    project<double>(c, N, r64, 0);
   }
-  reduce<double>(c, N, RD_NORM2, r64, nullptr, sc + 11);
-  reduce<double>(c, N, RD_WSUM, phi, nullptr, sc + 6, POST_MEAN, 1.0 / W);
-  project<double>(c, N, phi, 1);
+  reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 11);
+  refine_finish(c, phd, c->out64);
   return cudaGetLastError();
 }
 
@@ -1361,6 +1497,7 @@ cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream) {
   if ((e = cudaMalloc(&s->red_tmp, 1024 * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&s->red_counter, sizeof(unsigned int))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&s->res64, nodes * sizeof(double))) != cudaSuccess) return e;
+  if (s->precision == FEP3M_MIXED && (e = cudaMalloc(&s->phidf, nodes * sizeof(dfv))) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&s->host_res, 2 * sizeof(double))) != cudaSuccess) return e;
   cudaMemset(s->red_counter, 0, sizeof(unsigned int));
   cudaMemset(s->scal, 0, 64 * sizeof(double));
@@ -1376,6 +1513,8 @@ void solver_destroy(Solver* s) {
   if (s->red_tmp) cudaFree(s->red_tmp);
   if (s->red_counter) cudaFree(s->red_counter);
   if (s->res64) cudaFree(s->res64);
+  if (s->phidf) cudaFree(s->phidf);
+  s->phidf = nullptr;
   if (s->host_res) cudaFreeHost(s->host_res);
   s->scal = s->red_tmp = s->res64 = s->host_res = nullptr;
   s->red_counter = nullptr;
