@@ -199,11 +199,34 @@ constexpr int APL = (ANC + AT - 1) / AT;          // halo columns per thread
 static_assert(AHX * AEY <= AT && AEX * AFY <= AT, "one y item and one x item per thread");
 
 template <class T>
-struct ApplySmem {
-  T t1[3][AHY][AHX], t2[3][AHY][AHX];
-  T a[3][AFY][AHX], c[3][AFY][AHX];
-  T dinv[27];   // D^-1 by node types: x + 3 y + 9 z
+struct Pair2 {
+  T a, b;
 };
+
+// operands of the epilogue staged in shared memory (cp.async): b for the
+// residual and the zero-start step; b, d and (single precision) x for a
+// Chebyshev step
+template <class T, int EPI>
+__host__ __device__ constexpr int apply_nst() {
+  return EPI == EPI_CHEB ? (sizeof(T) == 4 ? 3 : 2) : (EPI == EPI_Y ? 0 : 1);
+}
+
+template <class T, int EPI>
+struct ApplySmem {
+  Pair2<T> tz[3][AHY][AHX];        // z pass: (Mz x, Kz x)
+  Pair2<T> ac[3][AFY][AHX];        // y pass: (a, c)
+  T dinv[27];                      // D^-1 by node types: x + 3 y + 9 z
+  T stg[apply_nst<T, EPI>() > 0 ? apply_nst<T, EPI>() : 1][3][AFY][AFX];
+};
+
+// asynchronous global -> shared copy of one element (4, 8 or 16 bytes)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // nonzero taps j (offset j - 3) of the 1-D stencil of a node of type t
 template <int t> struct Taps {
@@ -248,14 +271,14 @@ __device__ __forceinline__ T st_KM(const T* u, const T* w) {
   return s;
 }
 
+// the epilogue at node g with y = (K x)_g and the staged b_g, d_g, x_g
 template <class T, int EPI>
-__device__ __forceinline__ void apply_epilogue(int64_t g, T y, T* __restrict__ out, const T* __restrict__ b,
-                                               T* __restrict__ d, const T* __restrict__ x, T* __restrict__ xo,
-                                               T c0, T c1, T c2, T dv, float rs) {
+__device__ __forceinline__ void apply_epilogue(int64_t g, T y, T bg, T dg, T xg, T* __restrict__ out,
+                                               T* __restrict__ d, T* __restrict__ xo, T c0, T c1, T c2, T dv,
+                                               float rs) {
   if constexpr (std::is_same<T, dfv>::value) {
     static_assert(EPI == EPI_RESID, "the double-float apply computes residuals only");
     // FP32 output rs (b - y): the double-float difference (two-sum), rounded
-    const dfv bg = b[g];
     const float sm = bg.h - y.h;
     const float bv = sm - bg.h;
     const float err = (bg.h - (sm - bv)) + (-y.h - bv);
@@ -263,13 +286,13 @@ __device__ __forceinline__ void apply_epilogue(int64_t g, T y, T* __restrict__ o
   } else if constexpr (EPI == EPI_Y) {
     out[g] = y;
   } else if constexpr (EPI == EPI_RESID) {
-    out[g] = b[g] - y;
+    out[g] = bg - y;
   } else if constexpr (EPI == EPI_CHEB) {
-    const T dn = c1 * d[g] + c2 * dv * (b[g] - y);
+    const T dn = c1 * dg + c2 * dv * (bg - y);
     d[g] = dn;
-    xo[g] = x[g] + dn;
+    xo[g] = xg + dn;
   } else {
-    const T bg = b[g], d0 = c0 * dv * bg;
+    const T d0 = c0 * dv * bg;
     const T dn = c1 * d0 + c2 * dv * (bg - y);
     d[g] = dn;
     xo[g] = d0 + dn;
@@ -277,7 +300,7 @@ __device__ __forceinline__ void apply_epilogue(int64_t g, T y, T* __restrict__ o
 }
 
 // grid: (ceil(N / AFX), ceil(N / AFY), ceil(n / steps)), AT threads, dynamic
-// shared memory sizeof(ApplySmem<T>); N = 3 n with n >= 3.  T = dfv: x and b
+// shared memory sizeof(ApplySmem<T, EPI>); N = 3 n with n >= 3.  T = dfv: x and b
 // are float pairs, out is FP32 and receives the residual times the power of
 // two the scaling reduction derived (scal)
 template <class T, int EPI>
@@ -285,7 +308,8 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, 
                                                  const T* __restrict__ b, T* __restrict__ d, T* __restrict__ xo,
                                                  T c0, T c1, T c2, const double* __restrict__ scal) {
   extern __shared__ __align__(16) unsigned char apply_smem_raw[];
-  ApplySmem<T>& S = *reinterpret_cast<ApplySmem<T>*>(apply_smem_raw);
+  ApplySmem<T, EPI>& S = *reinterpret_cast<ApplySmem<T, EPI>*>(apply_smem_raw);
+  constexpr int NST = apply_nst<T, EPI>();
   const int n = N / 3;
   const int64_t NN = (int64_t)N * N;
   const int x0 = blockIdx.x * AFX, y0 = blockIdx.y * AFY;
@@ -361,6 +385,21 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, 
         for (int s = 4; s < 7; ++s) w[k][s] *= fs[k][s % 3];
       }
     }
+    // stage this thread's epilogue operands for the step (its own nodes only,
+    // so its own wait makes them visible: no barrier needed)
+    if (NST > 0 && x_on) {
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const int64_t g = (int64_t)(3 * e + p) * NN + (int64_t)gy * N + gx0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          cp_async<sizeof(T)>(&S.stg[0][p][x_yy][3 * x_ex + r], b + g + r);
+          if constexpr (NST > 1) cp_async<sizeof(T)>(&S.stg[NST > 1 ? 1 : 0][p][x_yy][3 * x_ex + r], d + g + r);
+          if constexpr (NST > 2) cp_async<sizeof(T)>(&S.stg[NST > 2 ? 2 : 0][p][x_yy][3 * x_ex + r], x + g + r);
+        }
+      }
+    }
+    if (NST > 0) cp_async_commit();
     // z pass: planes 3e, 3e + 1, 3e + 2 are a vertex and the two interior nodes
 #pragma unroll
     for (int k = 0; k < APL; ++k) {
@@ -370,12 +409,9 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, 
         st_MK<T, 0>(w[k], m0, k0);
         st_MK<T, 1>(w[k] + 1, m1, k1);
         st_MK<T, 2>(w[k] + 2, m2, k2);
-        (&S.t1[0][0][0])[i] = m0;
-        (&S.t2[0][0][0])[i] = k0;
-        (&S.t1[1][0][0])[i] = m1;
-        (&S.t2[1][0][0])[i] = k1;
-        (&S.t1[2][0][0])[i] = m2;
-        (&S.t2[2][0][0])[i] = k2;
+        (&S.tz[0][0][0])[i] = {m0, k0};
+        (&S.tz[1][0][0])[i] = {m1, k1};
+        (&S.tz[2][0][0])[i] = {m2, k2};
       }
     }
     __syncthreads();
@@ -386,33 +422,43 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, 
         T u[7], v[7];
 #pragma unroll
         for (int j = 0; j < 7; ++j) {
-          u[j] = S.t1[p][3 * y_ey + j][y_hx];
-          v[j] = S.t2[p][3 * y_ey + j][y_hx];
+          const Pair2<T> q = S.tz[p][3 * y_ey + j][y_hx];
+          u[j] = q.a;
+          v[j] = q.b;
         }
-        S.a[p][3 * y_ey + 0][y_hx] = st_M<T, 0>(u);
-        S.c[p][3 * y_ey + 0][y_hx] = st_KM<T, 0>(u, v);
-        S.a[p][3 * y_ey + 1][y_hx] = st_M<T, 1>(u + 1);
-        S.c[p][3 * y_ey + 1][y_hx] = st_KM<T, 1>(u + 1, v + 1);
-        S.a[p][3 * y_ey + 2][y_hx] = st_M<T, 2>(u + 2);
-        S.c[p][3 * y_ey + 2][y_hx] = st_KM<T, 2>(u + 2, v + 2);
+        S.ac[p][3 * y_ey + 0][y_hx] = {st_M<T, 0>(u), st_KM<T, 0>(u, v)};
+        S.ac[p][3 * y_ey + 1][y_hx] = {st_M<T, 1>(u + 1), st_KM<T, 1>(u + 1, v + 1)};
+        S.ac[p][3 * y_ey + 2][y_hx] = {st_M<T, 2>(u + 2), st_KM<T, 2>(u + 2, v + 2)};
       }
     }
     __syncthreads();
     // x pass and epilogue: nodes 3 ex .. 3 ex + 2 of row yy, for the three planes
+    if (NST > 0) cp_async_wait_all();
     if (x_on) {
 #pragma unroll
       for (int p = 0; p < 3; ++p) {
         T u[7], v[7];
 #pragma unroll
         for (int j = 0; j < 7; ++j) {
-          u[j] = S.a[p][x_yy][3 * x_ex + j];
-          v[j] = S.c[p][x_yy][3 * x_ex + j];
+          const Pair2<T> q = S.ac[p][x_yy][3 * x_ex + j];
+          u[j] = q.a;
+          v[j] = q.b;
         }
         const int64_t g = (int64_t)(3 * e + p) * NN + (int64_t)gy * N + gx0;
         const T* dv = S.dinv + 3 * ty3 + 9 * p;
-        apply_epilogue<T, EPI>(g, st_KM<T, 0>(u, v), out, b, d, x, xo, c0, c1, c2, dv[0], rs);
-        apply_epilogue<T, EPI>(g + 1, st_KM<T, 1>(u + 1, v + 1), out, b, d, x, xo, c0, c1, c2, dv[1], rs);
-        apply_epilogue<T, EPI>(g + 2, st_KM<T, 2>(u + 2, v + 2), out, b, d, x, xo, c0, c1, c2, dv[2], rs);
+        T y[3];
+        y[0] = st_KM<T, 0>(u, v);
+        y[1] = st_KM<T, 1>(u + 1, v + 1);
+        y[2] = st_KM<T, 2>(u + 2, v + 2);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          T bg{}, dg{}, xg{};
+          if constexpr (NST > 0) bg = S.stg[0][p][x_yy][3 * x_ex + r];
+          if constexpr (NST > 1) dg = S.stg[NST > 1 ? 1 : 0][p][x_yy][3 * x_ex + r];
+          if constexpr (NST > 2) xg = S.stg[NST > 2 ? 2 : 0][p][x_yy][3 * x_ex + r];
+          if constexpr (EPI == EPI_CHEB && NST == 2) xg = x[g + r];
+          apply_epilogue<T, EPI>(g + r, y[r], bg, dg, xg, out, d, xo, c0, c1, c2, dv[r], rs);
+        }
       }
     }
     // next element: slots 0..3 <- 3..6, slots 4..6 <- the prefetched planes
@@ -428,29 +474,23 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, 
   }
 }
 
-template <class T>
-static cudaError_t apply_set_smem_t() {
-  const int sm = (int)sizeof(ApplySmem<T>);
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_apply_el<T, EPI_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_apply_el<T, EPI_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_apply_el<T, EPI_CHEB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
-      cudaSuccess)
-    return e;
-  return cudaFuncSetAttribute(k_apply_el<T, EPI_CHEB0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+template <class T, int EPI>
+static cudaError_t apply_set_smem_one() {
+  return cudaFuncSetAttribute(k_apply_el<T, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(ApplySmem<T, EPI>));
 }
 
-// the FP64 and double-float tiles need more than the default 48 KB of
-// dynamic shared memory
+// the tiles need more than the default 48 KB of dynamic shared memory
 static cudaError_t apply_set_smem() {
-  cudaError_t e = apply_set_smem_t<float>();
-  if (e == cudaSuccess) e = apply_set_smem_t<double>();
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_apply_el<dfv, EPI_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(ApplySmem<dfv>));
+  cudaError_t e = apply_set_smem_one<float, EPI_Y>();
+  if (e == cudaSuccess) e = apply_set_smem_one<float, EPI_RESID>();
+  if (e == cudaSuccess) e = apply_set_smem_one<float, EPI_CHEB>();
+  if (e == cudaSuccess) e = apply_set_smem_one<float, EPI_CHEB0>();
+  if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_Y>();
+  if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_RESID>();
+  if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_CHEB>();
+  if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_CHEB0>();
+  if (e == cudaSuccess) e = apply_set_smem_one<dfv, EPI_RESID>();
   return e;
 }
 
@@ -873,15 +913,14 @@ struct MG {
     cudaStream_t s = c->stream;
     const int steps = apply_steps(L.N);
     const dim3 grid((L.N + AFX - 1) / AFX, (L.N + AFY - 1) / AFY, (L.n + steps - 1) / steps);
-    const size_t sm = sizeof(ApplySmem<T>);
     if (epi == EPI_Y)
-      FEP3M_CL k_apply_el<T, EPI_Y><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
+      FEP3M_CL k_apply_el<T, EPI_Y><<<grid, AT, sizeof(ApplySmem<T, EPI_Y>), s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
     else if (epi == EPI_RESID)
-      FEP3M_CL k_apply_el<T, EPI_RESID><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
+      FEP3M_CL k_apply_el<T, EPI_RESID><<<grid, AT, sizeof(ApplySmem<T, EPI_RESID>), s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
     else if (epi == EPI_CHEB)
-      FEP3M_CL k_apply_el<T, EPI_CHEB><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
+      FEP3M_CL k_apply_el<T, EPI_CHEB><<<grid, AT, sizeof(ApplySmem<T, EPI_CHEB>), s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
     else
-      FEP3M_CL k_apply_el<T, EPI_CHEB0><<<grid, AT, sm, s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
+      FEP3M_CL k_apply_el<T, EPI_CHEB0><<<grid, AT, sizeof(ApplySmem<T, EPI_CHEB0>), s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
   }
 
   // Chebyshev smoothing of A x = b (D-preconditioned) on [lmax/ratio, lmax].
@@ -1227,7 +1266,7 @@ static cudaError_t resid_df(Solver* c, const dfv* phi, const dfv* b, float* r) {
   const int steps = apply_steps(N);
   const dim3 grid((N + AFX - 1) / AFX, (N + AFY - 1) / AFY, (L0.n + steps - 1) / steps);
   const dfv z = {0.0f, 0.0f};
-  FEP3M_CL k_apply_el<dfv, EPI_RESID><<<grid, AT, sizeof(ApplySmem<dfv>), c->stream>>>(
+  FEP3M_CL k_apply_el<dfv, EPI_RESID><<<grid, AT, sizeof(ApplySmem<dfv, EPI_RESID>), c->stream>>>(
       N, steps, phi, reinterpret_cast<dfv*>(r), b, nullptr, nullptr, z, z, z, c->scal);
   return cudaGetLastError();
 }

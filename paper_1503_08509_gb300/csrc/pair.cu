@@ -1072,7 +1072,10 @@ __global__ void __launch_bounds__(PT) k_adj_gemm(int64_t ne, int o0, int no, con
   }
 }
 
-// A[s][k] (+)= sum over offsets o in [o0, o0 + no) with o + k inside the block of D[o][s + k + o]
+// A[s][k] (+)= sum over offsets o in [o0, o0 + no) with o + k inside the block of D[o][s + k + o].
+// Written as a loop over the block element u = k + o (each axis in [-n_sr, n_sr], so o is
+// always a stored offset), with the wrapped element index advanced incrementally; the
+// terms are added in increasing o, as the offsets are stored.
 template <class T>
 __global__ void k_adj_gather(int n, int n_sr, int o0, int no, int first, const int* __restrict__ count,
                              const T* __restrict__ D, T* __restrict__ A) {
@@ -1086,14 +1089,20 @@ __global__ void k_adj_gather(int n, int n_sr, int o0, int no, int first, const i
     const int keep = n_sr + 1, noff = 2 * n_sr + 2;
     const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
     const int sx = (int)(s % n), sy = (int)((s / n) % n), sz = (int)(s / ((int64_t)n * n));
-    for (int oi = 0; oi < no; ++oi) {
-      const int o = o0 + oi;
-      const int ox = o % noff - keep, oy = (o / noff) % noff - keep, oz = o / (noff * noff) - keep;
-      if (ox + kx < -n_sr || ox + kx > n_sr || oy + ky < -n_sr || oy + ky > n_sr || oz + kz < -n_sr ||
-          oz + kz > n_sr)
-        continue;
-      const int64_t e = wrapn(sx + kx + ox, n) + (int64_t)n * (wrapn(sy + ky + oy, n) + (int64_t)n * wrapn(sz + kz + oz, n));
-      acc += D[(int64_t)oi * ne + e];
+    const int ex0 = wrapn(sx - n_sr, n);
+    for (int uz = -n_sr; uz <= n_sr; ++uz) {
+      const int64_t ez = wrapn(sz + uz, n);
+      const int oz = uz - kz + keep;
+      for (int uy = -n_sr; uy <= n_sr; ++uy) {
+        const int64_t row = (int64_t)n * (wrapn(sy + uy, n) + (int64_t)n * ez);
+        const int oyz = noff * ((uy - ky + keep) + noff * oz) - kx + keep - o0;   // o - o0 at ux = 0
+        int ex = ex0;
+        for (int ux = -n_sr; ux <= n_sr; ++ux) {
+          const int oi = oyz + ux;
+          if ((unsigned)oi < (unsigned)no) acc += D[(int64_t)oi * ne + row + ex];
+          if (++ex == n) ex = 0;
+        }
+      }
     }
   }
   A[s * 8 + k] = acc;
