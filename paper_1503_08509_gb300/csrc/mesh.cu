@@ -163,6 +163,96 @@ __global__ void k_load_vector(int n, const T* __restrict__ rv, double* __restric
   b[g] = 4.0 * M_PI * acc;
 }
 
+// Coarsest-level exact solve x = V (Dinv o (V^T b)) (V the 1-D generalized
+// eigenvectors, applied along every axis), in three launches for N <= CP_MAX:
+//   k_coarse_plane   one CTA per z plane: the x and y transforms in shared memory
+//   k_coarse_pencil  CP_PEN z pencils per CTA: z transform, Dinv, inverse z transform
+//   k_coarse_plane   the inverse x and y transforms
+constexpr int CP_MAX = 64, CP_PEN = 32;
+
+// out[z][r'][r] = sum_{j,k} A[r'][j] A[r][k] in[z][j][k] (A row r = output r);
+// dynamic shared memory (3 N (N + 1)) elements; grid N
+template <class T>
+__global__ void __launch_bounds__(256) k_coarse_plane(int N, const T* __restrict__ A, const T* __restrict__ in,
+                                                      T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char cpsm[];
+  const int P = N + 1;   // padded row
+  T* As = (T*)cpsm;      // A[r][k] at r P + k
+  T* X = As + N * P;     // plane [y][x]
+  T* Y = X + N * P;      // after the x transform [y][r]
+  const int64_t base = (int64_t)blockIdx.x * N * N;
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+    const int r = i / N, k = i - r * N;
+    As[r * P + k] = A[i];
+    X[r * P + k] = in[base + i];
+  }
+  __syncthreads();
+  // x transform: Y[y][r] = sum_k A[r][k] X[y][k]
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+    const int y = i / N, r = i - y * N;
+    const T* a = As + r * P;
+    const T* xr = X + y * P;
+    T acc = T(0);
+    for (int k = 0; k < N; ++k) acc += a[k] * xr[k];
+    Y[y * P + r] = acc;
+  }
+  __syncthreads();
+  // y transform: out[r'][x] = sum_k A[r'][k] Y[k][x]
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+    const int rp = i / N, x = i - rp * N;
+    const T* a = As + rp * P;
+    T acc = T(0);
+    for (int k = 0; k < N; ++k) acc += a[k] * Y[k * P + x];
+    out[base + i] = acc;
+  }
+}
+
+// for the CP_PEN pencils q = x + N y starting at blockIdx.x CP_PEN:
+//   u[z'] = sum_z VT[z'][z] in[z][q];  u[z'] *= Dinv[z'][q];  out[z][q] = sum_z' V[z][z'] u[z']
+// dynamic shared memory (2 N (N + 1) + 2 CP_PEN (N + 1)) elements; grid ceil(N^2 / CP_PEN)
+template <class T>
+__global__ void __launch_bounds__(256) k_coarse_pencil(int N, const T* __restrict__ VT, const T* __restrict__ V,
+                                                       const T* __restrict__ Dinv, const T* __restrict__ in,
+                                                       T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char cpsm[];
+  const int P = N + 1;
+  T* VTs = (T*)cpsm;
+  T* Vs = VTs + N * P;
+  T* U = Vs + N * P;          // [pencil][z]
+  T* W = U + CP_PEN * P;      // [pencil][z']
+  const int64_t NN = (int64_t)N * N;
+  const int64_t q0 = (int64_t)blockIdx.x * CP_PEN;
+  const int np = (int)min((int64_t)CP_PEN, NN - q0);
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+    const int r = i / N, k = i - r * N;
+    VTs[r * P + k] = VT[i];
+    Vs[r * P + k] = V[i];
+  }
+  for (int i = threadIdx.x; i < CP_PEN * N; i += blockDim.x) {
+    const int z = i / CP_PEN, p = i - z * CP_PEN;
+    U[p * P + z] = p < np ? in[z * NN + q0 + p] : T(0);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < CP_PEN * N; i += blockDim.x) {
+    const int zp = i / CP_PEN, p = i - zp * CP_PEN;
+    const T* a = VTs + zp * P;
+    const T* u = U + p * P;
+    T acc = T(0);
+    for (int k = 0; k < N; ++k) acc += a[k] * u[k];
+    W[p * P + zp] = p < np ? acc * Dinv[zp * NN + q0 + p] : T(0);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < CP_PEN * N; i += blockDim.x) {
+    const int z = i / CP_PEN, p = i - z * CP_PEN;
+    if (p >= np) continue;
+    const T* a = Vs + z * P;
+    const T* w = W + p * P;
+    T acc = T(0);
+    for (int k = 0; k < N; ++k) acc += a[k] * w[k];
+    out[z * NN + q0 + p] = acc;
+  }
+}
+
 // ------------------------------------------------------------ operator apply
 enum { EPI_Y = 0, EPI_RESID = 1, EPI_CHEB = 2, EPI_CHEB0 = 3 };
 
@@ -170,6 +260,75 @@ enum { EPI_Y = 0, EPI_RESID = 1, EPI_CHEB = 2, EPI_CHEB0 = 3 };
 // scal[SC_DERIVED + k], floats at ((float*)(scal + SC_DERIVED_F))[k]
 constexpr int SC_DERIVED = 16, SC_DERIVED_F = 32;
 enum { SD_ALPHA = 0, SD_BETA = 1, SD_MEAN = 2, SD_SCALE = 3, SD_INVSCALE = 4 };
+// what the last block derives from the total t (written next to it, so that
+// the consumers read one ready scalar instead of recomputing it per node)
+enum { POST_NONE = 0, POST_ALPHA = 1, POST_BETA = 2, POST_MEAN = 3, POST_SCALE = 4 };
+
+// Deterministic block-then-grid sum (blockDim.x == 256): the block's total goes
+// to partials[bid]; the last block to finish adds the partials in index order,
+// writes the total to *out and derives the post scalar from it.
+__device__ void block_sum_finish(double acc, unsigned bid, unsigned nblocks, double* __restrict__ partials,
+                                 unsigned int* __restrict__ counter, double* __restrict__ out, int post,
+                                 double arg, double* __restrict__ scal) {
+  __shared__ double sh[8];
+  __shared__ bool last;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int k = 0; k < 8; ++k) s += sh[k];
+    partials[bid] = s;
+    __threadfence();
+    unsigned int done = atomicAdd(counter, 1u);
+    last = (done == nblocks - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0;
+  for (unsigned int k = threadIdx.x; k < nblocks; k += blockDim.x) s += ((volatile double*)partials)[k];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double t = 0;
+  for (int k = 0; k < 8; ++k) t += sh[k];
+  *out = t;
+  *counter = 0u;
+  double* dd = scal + SC_DERIVED;
+  float* df = (float*)(scal + SC_DERIVED_F);
+  if (post == POST_ALPHA) {          // alpha = (r.z) / (p.q), t = p.q
+    const double a = t != 0.0 ? scal[0] / t : 0.0;
+    dd[SD_ALPHA] = a;
+    df[SD_ALPHA] = (float)a;
+  } else if (post == POST_BETA) {    // beta = (r.z)_new / (r.z), t = (r.z)_new
+    const double bta = scal[0] != 0.0 ? t / scal[0] : 0.0;
+    dd[SD_BETA] = bta;
+    df[SD_BETA] = (float)bta;
+    scal[0] = t;
+  } else if (post == POST_MEAN) {    // t * arg (arg = 1 / W)
+    dd[SD_MEAN] = t * arg;
+    df[SD_MEAN] = (float)(t * arg);
+  } else if (post == POST_SCALE) {   // 2^-k with 2^k near the RMS sqrt(t arg)
+    const double rms = sqrt(t * arg);
+    int k = rms > 0.0 && isfinite(rms) ? ilogb(rms) : 0;
+    k = max(-100, min(100, k));
+    dd[SD_SCALE] = ldexp(1.0, -k);
+    dd[SD_INVSCALE] = ldexp(1.0, k);
+    df[SD_SCALE] = (float)ldexp(1.0, -k);
+    df[SD_INVSCALE] = (float)ldexp(1.0, k);
+  }
+}
+
+// a dot product accumulated by an apply: block partials, counter, total, post
+struct ApplyDot {
+  double* partials;
+  unsigned int* counter;
+  double* out;
+  int post;
+};
+
 
 // Fused apply y = K x, tiled by elements (2.5-D).  A CTA owns an AFX x AFY
 // column of output nodes (AEX x AEY elements, origin on a vertex) and marches
@@ -206,17 +365,18 @@ struct Pair2 {
 // operands of the epilogue staged in shared memory (cp.async): b for the
 // residual and the zero-start step; b, d and (single precision) x for a
 // Chebyshev step
-template <class T, int EPI>
+// (with DOT, EPI_Y stages x for the dot x.Kx)
+template <class T, int EPI, bool DOT = false>
 __host__ __device__ constexpr int apply_nst() {
-  return EPI == EPI_CHEB ? (sizeof(T) == 4 ? 3 : 2) : (EPI == EPI_Y ? 0 : 1);
+  return EPI == EPI_CHEB ? (sizeof(T) == 4 ? 3 : 2) : (EPI == EPI_Y ? (DOT ? 1 : 0) : 1);
 }
 
-template <class T, int EPI>
+template <class T, int EPI, bool DOT = false>
 struct ApplySmem {
   Pair2<T> tz[3][AHY][AHX];        // z pass: (Mz x, Kz x)
   Pair2<T> ac[3][AFY][AHX];        // y pass: (a, c)
   T dinv[27];                      // D^-1 by node types: x + 3 y + 9 z
-  T stg[apply_nst<T, EPI>() > 0 ? apply_nst<T, EPI>() : 1][3][AFY][AFX];
+  T stg[apply_nst<T, EPI, DOT>() > 0 ? apply_nst<T, EPI, DOT>() : 1][3][AFY][AFX];
 };
 
 // asynchronous global -> shared copy of one element (4, 8 or 16 bytes)
@@ -272,8 +432,9 @@ __device__ __forceinline__ T st_KM(const T* u, const T* w) {
 }
 
 // the epilogue at node g with y = (K x)_g and the staged b_g, d_g, x_g
+// returns y (EPI_Y) or the new iterate (EPI_CHEB), the factor of the fused dots
 template <class T, int EPI>
-__device__ __forceinline__ void apply_epilogue(int64_t g, T y, T bg, T dg, T xg, T* __restrict__ out,
+__device__ __forceinline__ T apply_epilogue(int64_t g, T y, T bg, T dg, T xg, T* __restrict__ out,
                                                T* __restrict__ d, T* __restrict__ xo, T c0, T c1, T c2, T dv,
                                                float rs) {
   if constexpr (std::is_same<T, dfv>::value) {
@@ -283,19 +444,25 @@ __device__ __forceinline__ void apply_epilogue(int64_t g, T y, T bg, T dg, T xg,
     const float bv = sm - bg.h;
     const float err = (bg.h - (sm - bv)) + (-y.h - bv);
     reinterpret_cast<float*>(out)[g] = (sm + ((bg.l - y.l) + err)) * rs;
+    return y;
   } else if constexpr (EPI == EPI_Y) {
     out[g] = y;
+    return y;
   } else if constexpr (EPI == EPI_RESID) {
     out[g] = bg - y;
+    return y;
   } else if constexpr (EPI == EPI_CHEB) {
     const T dn = c1 * dg + c2 * dv * (bg - y);
+    const T xn = xg + dn;
     d[g] = dn;
-    xo[g] = xg + dn;
+    xo[g] = xn;
+    return xn;
   } else {
     const T d0 = c0 * dv * bg;
     const T dn = c1 * d0 + c2 * dv * (bg - y);
     d[g] = dn;
     xo[g] = d0 + dn;
+    return d0 + dn;
   }
 }
 
@@ -303,13 +470,19 @@ __device__ __forceinline__ void apply_epilogue(int64_t g, T y, T bg, T dg, T xg,
 // shared memory sizeof(ApplySmem<T, EPI>); N = 3 n with n >= 3.  T = dfv: x and b
 // are float pairs, out is FP32 and receives the residual times the power of
 // two the scaling reduction derived (scal)
-template <class T, int EPI>
-__global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, int steps, const T* __restrict__ x, T* __restrict__ out,
-                                                 const T* __restrict__ b, T* __restrict__ d, T* __restrict__ xo,
-                                                 T c0, T c1, T c2, const double* __restrict__ scal) {
+//
+// DOT (EPI_Y: x.(Kx); EPI_CHEB: b.(new iterate)): each thread accumulates its
+// nodes' products, then block_sum_finish with dt (partials indexed by the
+// linear block id).
+template <class T, int EPI, bool DOT = false>
+__global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
+    k_apply_el(int N, int steps, const T* __restrict__ x, T* __restrict__ out, const T* __restrict__ b,
+               T* __restrict__ d, T* __restrict__ xo, T c0, T c1, T c2, double* __restrict__ scal, ApplyDot dt) {
+  static_assert(!DOT || EPI == EPI_Y || EPI == EPI_CHEB, "fused dots: EPI_Y and EPI_CHEB");
   extern __shared__ __align__(16) unsigned char apply_smem_raw[];
-  ApplySmem<T, EPI>& S = *reinterpret_cast<ApplySmem<T, EPI>*>(apply_smem_raw);
-  constexpr int NST = apply_nst<T, EPI>();
+  ApplySmem<T, EPI, DOT>& S = *reinterpret_cast<ApplySmem<T, EPI, DOT>*>(apply_smem_raw);
+  constexpr int NST = apply_nst<T, EPI, DOT>();
+  double dacc = 0.0;
   const int n = N / 3;
   const int64_t NN = (int64_t)N * N;
   const int x0 = blockIdx.x * AFX, y0 = blockIdx.y * AFY;
@@ -393,7 +566,7 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, 
         const int64_t g = (int64_t)(3 * e + p) * NN + (int64_t)gy * N + gx0;
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-          cp_async<sizeof(T)>(&S.stg[0][p][x_yy][3 * x_ex + r], b + g + r);
+          cp_async<sizeof(T)>(&S.stg[0][p][x_yy][3 * x_ex + r], (EPI == EPI_Y ? x : b) + g + r);
           if constexpr (NST > 1) cp_async<sizeof(T)>(&S.stg[NST > 1 ? 1 : 0][p][x_yy][3 * x_ex + r], d + g + r);
           if constexpr (NST > 2) cp_async<sizeof(T)>(&S.stg[NST > 2 ? 2 : 0][p][x_yy][3 * x_ex + r], x + g + r);
         }
@@ -450,6 +623,7 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, 
         y[0] = st_KM<T, 0>(u, v);
         y[1] = st_KM<T, 1>(u + 1, v + 1);
         y[2] = st_KM<T, 2>(u + 2, v + 2);
+        T dsum{};
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
           T bg{}, dg{}, xg{};
@@ -457,8 +631,10 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, 
           if constexpr (NST > 1) dg = S.stg[NST > 1 ? 1 : 0][p][x_yy][3 * x_ex + r];
           if constexpr (NST > 2) xg = S.stg[NST > 2 ? 2 : 0][p][x_yy][3 * x_ex + r];
           if constexpr (EPI == EPI_CHEB && NST == 2) xg = x[g + r];
-          apply_epilogue<T, EPI>(g + r, y[r], bg, dg, xg, out, d, xo, c0, c1, c2, dv[r], rs);
+          const T f = apply_epilogue<T, EPI>(g + r, y[r], bg, dg, xg, out, d, xo, c0, c1, c2, dv[r], rs);
+          if constexpr (DOT) dsum = r == 0 ? bg * f : dsum + bg * f;   // EPI_Y stages x in the b slot
         }
+        if constexpr (DOT) dacc += (double)dsum;
       }
     }
     // next element: slots 0..3 <- 3..6, slots 4..6 <- the prefetched planes
@@ -472,12 +648,15 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2) k_apply_el(int N, 
     zs += 3;
     if (zs >= N) zs -= N;
   }
+  if constexpr (DOT)
+    block_sum_finish(dacc, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                     gridDim.x * gridDim.y * gridDim.z, dt.partials, dt.counter, dt.out, dt.post, 0.0, scal);
 }
 
-template <class T, int EPI>
+template <class T, int EPI, bool DOT = false>
 static cudaError_t apply_set_smem_one() {
-  return cudaFuncSetAttribute(k_apply_el<T, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(ApplySmem<T, EPI>));
+  return cudaFuncSetAttribute(k_apply_el<T, EPI, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(ApplySmem<T, EPI, DOT>));
 }
 
 // the tiles need more than the default 48 KB of dynamic shared memory
@@ -486,11 +665,26 @@ static cudaError_t apply_set_smem() {
   if (e == cudaSuccess) e = apply_set_smem_one<float, EPI_RESID>();
   if (e == cudaSuccess) e = apply_set_smem_one<float, EPI_CHEB>();
   if (e == cudaSuccess) e = apply_set_smem_one<float, EPI_CHEB0>();
+  if (e == cudaSuccess) e = apply_set_smem_one<float, EPI_Y, true>();
+  if (e == cudaSuccess) e = apply_set_smem_one<float, EPI_CHEB, true>();
   if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_Y>();
   if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_RESID>();
   if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_CHEB>();
   if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_CHEB0>();
+  if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_Y, true>();
+  if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_CHEB, true>();
   if (e == cudaSuccess) e = apply_set_smem_one<dfv, EPI_RESID>();
+  // coarsest-level kernels at N = CP_MAX in FP64
+  const int smp = 3 * CP_MAX * (CP_MAX + 1) * (int)sizeof(double);
+  const int smq = (2 * CP_MAX * (CP_MAX + 1) + 2 * CP_PEN * (CP_MAX + 1)) * (int)sizeof(double);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_coarse_plane<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smp);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_coarse_pencil<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smq);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_coarse_plane<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smp / 2);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_coarse_pencil<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smq / 2);
   return e;
 }
 
@@ -500,6 +694,10 @@ static inline int apply_steps(int N) {
   const int64_t cols = (int64_t)((N + AFX - 1) / AFX) * ((N + AFY - 1) / AFY);
   const int64_t s = cols * n / (152 * 6);
   return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(16, n), s));
+}
+
+static inline dim3 apply_grid(int N, int steps) {
+  return dim3((N + AFX - 1) / AFX, (N + AFY - 1) / AFY, (N / 3 + steps - 1) / steps);
 }
 
 // first Chebyshev step from x = 0: d = D^-1 b / theta, x = d (used alone
@@ -604,78 +802,8 @@ __global__ void k_dense_axis(int N, int axis, const T* __restrict__ V, bool tran
 }
 
 
-// Coalesced dense 1-D transform along one axis of an N^3 array (N <= 48):
-// out[.. i ..] = sum_k A[i][k] in[.. k ..] (A = V^T when transpose), optionally
-// scaled elementwise after.  The array is viewed as [outer][N along axis][inner];
-// a CTA takes 32 consecutive inner indices (or, for the x axis, 32 consecutive
-// pencils) so global loads and stores are contiguous; A lives in shared memory.
-constexpr int DT = 8;
-template <class T>
-__global__ void __launch_bounds__(256) k_dense_tile(int N, int axis, const T* __restrict__ V, int transpose,
-                                                    const T* __restrict__ in, T* __restrict__ out,
-                                                    const T* __restrict__ scale) {
-  extern __shared__ __align__(16) unsigned char dsm[];
-  T* As = (T*)dsm;              // N x N
-  T* tile = As + N * N;         // DT x (N + 1)
-  const int64_t NN = (int64_t)N * N;
-  (void)transpose;   // V is passed already oriented (row r = output r)
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) As[i] = V[i];
-  // element (p, k) of the tile: pencil p of the block, position k along the axis
-  int64_t base;
-  int64_t pstride, kstride;
-  if (axis == 0) {               // pencils are rows: 32 consecutive rows
-    base = (int64_t)blockIdx.x * DT * N;
-    pstride = N;
-    kstride = 1;
-  } else if (axis == 1) {        // inner = x (N values), outer = z
-    const int nxb = (N + DT - 1) / DT;
-    const int zb = blockIdx.x / nxb, xb = blockIdx.x % nxb;
-    base = (int64_t)zb * NN + (int64_t)xb * DT;
-    pstride = 1;
-    kstride = N;
-  } else {                       // inner = x + N y (N^2 values)
-    base = (int64_t)blockIdx.x * DT;
-    pstride = 1;
-    kstride = NN;
-  }
-  int64_t npen;                  // pencils available in this block
-  if (axis == 0) npen = NN - (int64_t)blockIdx.x * DT;
-  else if (axis == 1) npen = N - (int64_t)(blockIdx.x % ((N + DT - 1) / DT)) * DT;
-  else npen = NN - (int64_t)blockIdx.x * DT;
-  const int np = (int)(npen < DT ? npen : DT);
-  for (int i = threadIdx.x; i < DT * N; i += blockDim.x) {
-    int p, k;
-    if (axis == 0) { p = i / N; k = i % N; }
-    else { k = i / DT; p = i % DT; }
-    tile[p * (N + 1) + k] = p < np ? in[base + p * pstride + k * kstride] : T(0);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < DT * N; i += blockDim.x) {
-    int p, r;
-    if (axis == 0) { p = i / N; r = i % N; }
-    else { r = i / DT; p = i % DT; }
-    if (p >= np) continue;
-    T acc = T(0);
-    const T* arow = As + r * N;
-    const T* tp = tile + p * (N + 1);
-    for (int k = 0; k < N; ++k) acc += arow[k] * tp[k];
-    const int64_t g = base + p * pstride + (int64_t)r * kstride;
-    if (scale) acc *= scale[g];
-    out[g] = acc;
-  }
-}
-
 // ---------------------------------------------------------- reductions
 enum { RD_DOT = 0, RD_SUM = 1, RD_WSUM = 2, RD_NORM2 = 3 };
-// what the last block derives from the total t (written next to it, so that
-// the consumers read one ready scalar instead of recomputing it per node)
-enum { POST_NONE = 0, POST_ALPHA = 1, POST_BETA = 2, POST_MEAN = 3, POST_SCALE = 4 };
-
-// node-integral weight of a node of the given types: (1/4 or 3/8 per axis)
-__device__ __forceinline__ double node_weight(int tx, int ty, int tz) {
-  const double w0 = 0.25, w1 = 0.375;
-  return (tx ? w1 : w0) * (ty ? w1 : w0) * (tz ? w1 : w0);
-}
 
 template <class T, int MODE>
 __device__ __forceinline__ T reduce_term(const T* __restrict__ x, const T* __restrict__ y, int64_t g) {
@@ -685,16 +813,13 @@ __device__ __forceinline__ T reduce_term(const T* __restrict__ x, const T* __res
   return v;
 }
 
-// deterministic two-level sum: each thread adds its nodes (four per round, in
-// the working precision) into an FP64 accumulator, each block writes a
-// partial, the last block to finish adds the partials in index order and
-// derives the post scalar.  MODE: x.y, sum x, sum w3 x (node integrals), x.x
+// each thread adds its nodes (four per round, in the working precision) into
+// an FP64 accumulator; then block_sum_finish.  MODE: x.y, sum x, sum w3 x
+// (node integrals), x.x
 template <class T, int MODE>
 __global__ void k_reduce(int N, const T* __restrict__ x, const T* __restrict__ y, double* __restrict__ partials,
                          unsigned int* __restrict__ counter, double* __restrict__ out, int post, double arg,
                          double* __restrict__ scal) {
-  __shared__ double sh[TPB / 32];
-  __shared__ bool last;
   const int64_t NN = (int64_t)N * N, tot = NN * N;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
@@ -705,7 +830,7 @@ __global__ void k_reduce(int N, const T* __restrict__ x, const T* __restrict__ y
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nwarps = stride >> 5;
     for (int64_t row = warp; row < rows; row += nwarps) {
       const int iz = (int)(row / N), iy = (int)(row - (int64_t)iz * N);
-      const double wyz = node_weight(1, iy % 3, iz % 3) / 0.375;
+      const double wyz = (iy % 3 ? 0.375 : 0.25) * (iz % 3 ? 0.375 : 0.25);
       const T* xr = x + row * N;
       double s0 = 0.0, s1 = 0.0;   // vertex / interior columns
       for (int ix = lane; ix < N; ix += 32) {
@@ -726,56 +851,7 @@ __global__ void k_reduce(int N, const T* __restrict__ x, const T* __restrict__ y
       acc += (double)((v[0] + v[1]) + (v[2] + v[3]));
     }
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0;
-    for (int k = 0; k < TPB / 32; ++k) s += sh[k];
-    partials[blockIdx.x] = s;
-    __threadfence();
-    unsigned int done = atomicAdd(counter, 1u);
-    last = (done == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (last) {
-    // the last block adds the partials in a fixed order (deterministic)
-    __threadfence();
-    double s = 0;
-    for (unsigned int k = threadIdx.x; k < gridDim.x; k += blockDim.x) s += ((volatile double*)partials)[k];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0;
-      for (int k = 0; k < TPB / 32; ++k) t += sh[k];
-      *out = t;
-      *counter = 0u;
-      double* dd = scal + SC_DERIVED;
-      float* df = (float*)(scal + SC_DERIVED_F);
-      if (post == POST_ALPHA) {          // alpha = (r.z) / (p.q), t = p.q
-        const double a = t != 0.0 ? scal[0] / t : 0.0;
-        dd[SD_ALPHA] = a;
-        df[SD_ALPHA] = (float)a;
-      } else if (post == POST_BETA) {    // beta = (r.z)_new / (r.z), t = (r.z)_new
-        const double bta = scal[0] != 0.0 ? t / scal[0] : 0.0;
-        dd[SD_BETA] = bta;
-        df[SD_BETA] = (float)bta;
-        scal[0] = t;
-      } else if (post == POST_MEAN) {    // t * arg (arg = 1 / W)
-        dd[SD_MEAN] = t * arg;
-        df[SD_MEAN] = (float)(t * arg);
-      } else if (post == POST_SCALE) {   // 2^-k with 2^k near the RMS sqrt(t arg)
-        const double rms = sqrt(t * arg);
-        int k = rms > 0.0 && isfinite(rms) ? ilogb(rms) : 0;
-        k = max(-100, min(100, k));
-        dd[SD_SCALE] = ldexp(1.0, -k);
-        dd[SD_INVSCALE] = ldexp(1.0, k);
-        df[SD_SCALE] = (float)ldexp(1.0, -k);
-        df[SD_INVSCALE] = (float)ldexp(1.0, k);
-      }
-    }
-  }
+  block_sum_finish(acc, blockIdx.x, gridDim.x, partials, counter, out, post, arg, scal);
 }
 
 template <class T>
@@ -908,26 +984,45 @@ struct MG {
   Hierarchy& H;
   explicit MG(Solver* cc) : c(cc), H(cc->mg) {}
 
-  // one fused apply; EPI_CHEB reads x and writes the new iterate to xo (xo != x)
-  void apply(const Level& L, const T* x, int epi, T* out, const T* b, T* d, T* xo, T c1, T c2, T c0 = T(0)) {
+  // one fused apply; EPI_CHEB reads x and writes the new iterate to xo (xo != x);
+  // dot (EPI_Y, EPI_CHEB): also accumulate x.(Kx) or b.(new iterate)
+  void apply(const Level& L, const T* x, int epi, T* out, const T* b, T* d, T* xo, T c1, T c2, T c0 = T(0),
+             const ApplyDot* dot = nullptr) {
     cudaStream_t s = c->stream;
     const int steps = apply_steps(L.N);
-    const dim3 grid((L.N + AFX - 1) / AFX, (L.N + AFY - 1) / AFY, (L.n + steps - 1) / steps);
-    if (epi == EPI_Y)
-      FEP3M_CL k_apply_el<T, EPI_Y><<<grid, AT, sizeof(ApplySmem<T, EPI_Y>), s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
+    const dim3 grid = apply_grid(L.N, steps);
+    double* sc = c->scal;
+    const ApplyDot nd = {nullptr, nullptr, nullptr, 0};
+    if (epi == EPI_Y && dot)
+      FEP3M_CL k_apply_el<T, EPI_Y, true><<<grid, AT, sizeof(ApplySmem<T, EPI_Y, true>), s>>>(
+          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, *dot);
+    else if (epi == EPI_Y)
+      FEP3M_CL k_apply_el<T, EPI_Y><<<grid, AT, sizeof(ApplySmem<T, EPI_Y>), s>>>(L.N, steps, x, out, b, d, xo,
+                                                                                  c0, c1, c2, sc, nd);
     else if (epi == EPI_RESID)
-      FEP3M_CL k_apply_el<T, EPI_RESID><<<grid, AT, sizeof(ApplySmem<T, EPI_RESID>), s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
+      FEP3M_CL k_apply_el<T, EPI_RESID><<<grid, AT, sizeof(ApplySmem<T, EPI_RESID>), s>>>(
+          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, nd);
+    else if (epi == EPI_CHEB && dot)
+      FEP3M_CL k_apply_el<T, EPI_CHEB, true><<<grid, AT, sizeof(ApplySmem<T, EPI_CHEB, true>), s>>>(
+          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, *dot);
     else if (epi == EPI_CHEB)
-      FEP3M_CL k_apply_el<T, EPI_CHEB><<<grid, AT, sizeof(ApplySmem<T, EPI_CHEB>), s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
+      FEP3M_CL k_apply_el<T, EPI_CHEB><<<grid, AT, sizeof(ApplySmem<T, EPI_CHEB>), s>>>(
+          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, nd);
     else
-      FEP3M_CL k_apply_el<T, EPI_CHEB0><<<grid, AT, sizeof(ApplySmem<T, EPI_CHEB0>), s>>>(L.N, steps, x, out, b, d, xo, c0, c1, c2, nullptr);
+      FEP3M_CL k_apply_el<T, EPI_CHEB0><<<grid, AT, sizeof(ApplySmem<T, EPI_CHEB0>), s>>>(
+          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, nd);
+  }
+
+  ApplyDot dot_into(int slot, int post) const {
+    return {(double*)c->red_tmp, c->red_counter, c->scal + slot, post};
   }
 
   // Chebyshev smoothing of A x = b (D-preconditioned) on [lmax/ratio, lmax].
   // from_zero: start from x = 0 (the first step, x = D^-1 b / theta, is folded
   // into the second); otherwise the start iterate is in the level's spare
   // buffer L.a.  Iterates alternate between L.a and x; the result is in x.
-  void smooth(const Level& L, T* x, const T* b, bool from_zero, int degree) {
+  // dot: accumulate b.x (x the final iterate) in the last step (degree >= 2)
+  void smooth(const Level& L, T* x, const T* b, bool from_zero, int degree, const ApplyDot* dot = nullptr) {
     const double up = 1.1 * H.lmax, lo = up / 15.0;
     const double theta = 0.5 * (up + lo), delta = 0.5 * (up - lo), sigma = theta / delta;
     double rho = 1.0 / sigma;
@@ -946,11 +1041,12 @@ struct MG {
       oth = x;
     }
     for (int k = from_zero ? 2 : 0; k < degree; ++k) {
+      const ApplyDot* dk = k == degree - 1 ? dot : nullptr;
       if (k == 0) {
-        apply(L, cur, EPI_CHEB, nullptr, b, (T*)L.d, oth, T(0), (T)(1.0 / theta));
+        apply(L, cur, EPI_CHEB, nullptr, b, (T*)L.d, oth, T(0), (T)(1.0 / theta), T(0), dk);
       } else {
         const double rn = 1.0 / (2.0 * sigma - rho);
-        apply(L, cur, EPI_CHEB, nullptr, b, (T*)L.d, oth, (T)(rn * rho), (T)(2.0 * rn / delta));
+        apply(L, cur, EPI_CHEB, nullptr, b, (T*)L.d, oth, (T)(rn * rho), (T)(2.0 * rn / delta), T(0), dk);
         rho = rn;
       }
       T* t = cur;
@@ -969,18 +1065,13 @@ struct MG {
     cudaStream_t s = c->stream;
     T* w1 = (T*)L.t1;
     T* w2 = (T*)L.t2;
-    if (N <= 48) {   // A and the tile fit the default 48 KB of dynamic shared memory
-      const size_t sm = ((size_t)N * N + (size_t)DT * (N + 1)) * sizeof(T);
-      const int64_t NN = (int64_t)N * N;
-      const unsigned g0 = (unsigned)((NN + DT - 1) / DT);
-      const unsigned g1 = (unsigned)(N * ((N + DT - 1) / DT));
-      const unsigned g2 = (unsigned)((NN + DT - 1) / DT);
-      FEP3M_CL k_dense_tile<T><<<g0, 256, sm, s>>>(N, 0, VT, 1, b, w1, nullptr);
-      FEP3M_CL k_dense_tile<T><<<g1, 256, sm, s>>>(N, 1, VT, 1, w1, w2, nullptr);
-      FEP3M_CL k_dense_tile<T><<<g2, 256, sm, s>>>(N, 2, VT, 1, w2, w1, Dinv);
-      FEP3M_CL k_dense_tile<T><<<g0, 256, sm, s>>>(N, 0, V, 0, w1, w2, nullptr);
-      FEP3M_CL k_dense_tile<T><<<g1, 256, sm, s>>>(N, 1, V, 0, w2, w1, nullptr);
-      FEP3M_CL k_dense_tile<T><<<g2, 256, sm, s>>>(N, 2, V, 0, w1, x, nullptr);
+    if (N <= CP_MAX) {
+      const size_t smp = (size_t)3 * N * (N + 1) * sizeof(T);
+      const size_t smq = ((size_t)2 * N * (N + 1) + (size_t)2 * CP_PEN * (N + 1)) * sizeof(T);
+      const unsigned gq = (unsigned)(((int64_t)N * N + CP_PEN - 1) / CP_PEN);
+      FEP3M_CL k_coarse_plane<T><<<N, 256, smp, s>>>(N, VT, b, w1);
+      FEP3M_CL k_coarse_pencil<T><<<gq, 256, smq, s>>>(N, VT, V, Dinv, w1, w2);
+      FEP3M_CL k_coarse_plane<T><<<N, 256, smp, s>>>(N, V, w2, x);
       return;
     }
     const int gsz = grid_for(L.size);
@@ -993,10 +1084,12 @@ struct MG {
   }
 
   // approximately solve A_l x = b on level l (x overwritten)
-  void vcycle(int l, const T* b, T* x) {
+  // dot: accumulate b.x of the result (fused into the last smoothing step)
+  void vcycle(int l, const T* b, T* x, const ApplyDot* dot = nullptr) {
     Level& L = H.lv[l];
     if (l == (int)H.lv.size() - 1) {
       coarse_solve(L, b, x);
+      if (dot) reduce<T>(c, L.N, RD_DOT, b, x, dot->out, dot->post);
       return;
     }
     Level& Cl = H.lv[l + 1];
@@ -1015,11 +1108,12 @@ struct MG {
     FEP3M_CL k_prolong_axis<T, false><<<g3(Nc, Nc, Nf), 128, 0, s>>>(2, Nc, Nc, Nc, Nf, (T*)Cl.x, s1, nullptr);
     FEP3M_CL k_prolong_axis<T, false><<<g3(Nc, Nf, Nf), 128, 0, s>>>(1, Nc, Nc, Nf, Nf, s1, s2, nullptr);
     FEP3M_CL k_prolong_axis<T, true><<<g3(Nf, Nf, Nf), 128, 0, s>>>(0, Nc, Nf, Nf, Nf, s2, (T*)L.a, x);
-    smooth(L, x, b, false, H.cheb_degree);   // starts from L.a = x + P e
+    smooth(L, x, b, false, H.cheb_degree, dot);   // starts from L.a = x + P e
   }
 
   // preconditioned CG on level 0: x = A^+ Pi b, returns iterations; the
-  // relative residual (FP64 dot products) goes to *relres
+  // relative residual (FP64 dot products) goes to *relres.  The dot products
+  // p.q and r.z are accumulated by the apply and the last smoothing step.
   int pcg(const T* b, T* x, T* r, T* z, T* p, T* q, double rtol, int maxit, double* relres) {
     Level& L = H.lv[0];
     const int N = L.N;
@@ -1039,21 +1133,19 @@ struct MG {
       *relres = 0.0;
       return 0;
     }
-    vcycle(0, r, z);
+    const ApplyDot d_rz0 = dot_into(0, POST_NONE), d_pq = dot_into(1, POST_ALPHA), d_rz = dot_into(2, POST_BETA);
+    vcycle(0, r, z, &d_rz0);
     cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
-    reduce<T>(c, N, RD_DOT, r, z, sc + 0);
     int it = 0;
     double rr = bb;
     for (it = 1; it <= maxit; ++it) {
-      apply(L, p, EPI_Y, q, nullptr, nullptr, nullptr, T(0), T(0));
-      reduce<T>(c, N, RD_DOT, p, q, sc + 1, POST_ALPHA);
+      apply(L, p, EPI_Y, q, nullptr, nullptr, nullptr, T(0), T(0), T(0), &d_pq);
       FEP3M_CL k_cg_update<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, x, r, p, q);
       reduce<T>(c, N, RD_NORM2, r, nullptr, sc + 3);
       cudaMemcpyAsync(&rr, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s);
       cudaStreamSynchronize(s);
       if (rr <= rtol * rtol * bb) break;
-      vcycle(0, r, z);
-      reduce<T>(c, N, RD_DOT, r, z, sc + 2, POST_BETA);
+      vcycle(0, r, z, &d_rz);
       FEP3M_CL k_cg_dir<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, p, z);
     }
     *relres = std::sqrt(rr / bb);
@@ -1074,19 +1166,20 @@ struct MG {
     project<T>(c, N, r, 0);
     cudaMemsetAsync(x, 0, n * sizeof(T), s);
     reduce<T>(c, N, RD_NORM2, r, nullptr, sc + 4);
-    vcycle(0, r, z);
+    const ApplyDot d_rz0 = dot_into(0, POST_NONE), d_pq = dot_into(1, POST_ALPHA), d_rz = dot_into(2, POST_BETA);
+    vcycle(0, r, z, &d_rz0);
     cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
-    reduce<T>(c, N, RD_DOT, r, z, sc + 0);
     for (int it = 1; it <= k; ++it) {
-      apply(L, p, EPI_Y, q, nullptr, nullptr, nullptr, T(0), T(0));
-      reduce<T>(c, N, RD_DOT, p, q, sc + 1, POST_ALPHA);
+      apply(L, p, EPI_Y, q, nullptr, nullptr, nullptr, T(0), T(0), T(0), &d_pq);
       FEP3M_CL k_cg_update<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, x, r, p, q);
-      reduce<T>(c, N, RD_NORM2, r, nullptr, sc + 3);
-      if (it == k) break;
-      vcycle(0, r, z);
-      reduce<T>(c, N, RD_DOT, r, z, sc + 2, POST_BETA);
+      if (it == k) {
+        reduce<T>(c, N, RD_NORM2, r, nullptr, sc + 3);
+        break;
+      }
+      vcycle(0, r, z, &d_rz);
       FEP3M_CL k_cg_dir<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, p, z);
     }
+    if (k <= 0) reduce<T>(c, N, RD_NORM2, r, nullptr, sc + 3);
   }
 };
 
@@ -1264,10 +1357,10 @@ static cudaError_t resid_df(Solver* c, const dfv* phi, const dfv* b, float* r) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
   const int steps = apply_steps(N);
-  const dim3 grid((N + AFX - 1) / AFX, (N + AFY - 1) / AFY, (L0.n + steps - 1) / steps);
   const dfv z = {0.0f, 0.0f};
-  FEP3M_CL k_apply_el<dfv, EPI_RESID><<<grid, AT, sizeof(ApplySmem<dfv, EPI_RESID>), c->stream>>>(
-      N, steps, phi, reinterpret_cast<dfv*>(r), b, nullptr, nullptr, z, z, z, c->scal);
+  const ApplyDot nd = {nullptr, nullptr, nullptr, 0};
+  FEP3M_CL k_apply_el<dfv, EPI_RESID><<<apply_grid(N, steps), AT, sizeof(ApplySmem<dfv, EPI_RESID>), c->stream>>>(
+      N, steps, phi, reinterpret_cast<dfv*>(r), b, nullptr, nullptr, z, z, z, c->scal, nd);
   return cudaGetLastError();
 }
 
@@ -1533,7 +1626,13 @@ cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream) {
   const size_t nodes = (size_t)27 * c->n * c->n * c->n;
   cudaError_t e;
   if ((e = cudaMalloc(&s->scal, 64 * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&s->red_tmp, 1024 * sizeof(double))) != cudaSuccess) return e;
+  // reduction partials: one per block of k_reduce (<= 608) or of a fine-level apply with a fused dot
+  {
+    const int N0 = 3 * c->n;
+    const dim3 g = apply_grid(N0, apply_steps(N0));
+    const size_t nb = std::max<size_t>(1024, (size_t)g.x * g.y * g.z);
+    if ((e = cudaMalloc(&s->red_tmp, nb * sizeof(double))) != cudaSuccess) return e;
+  }
   if ((e = cudaMalloc(&s->red_counter, sizeof(unsigned int))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&s->res64, nodes * sizeof(double))) != cudaSuccess) return e;
   if (s->precision == FEP3M_MIXED && (e = cudaMalloc(&s->phidf, nodes * sizeof(dfv))) != cudaSuccess) return e;
