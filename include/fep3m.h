@@ -66,13 +66,15 @@ typedef struct {
   int q;               /* screen order; this build supports q = 1 (p = 3)       */
   int n_sr;            /* short-range block half-width in elements, 1..4 (3 in
                           the paper's tests, Sec. 4: a 7 x 7 x 7 block)         */
-  int precision;       /* FEP3M_FP64 or FEP3M_MIXED (FP32 pairs and multigrid
-                          smoothing, FP64 refinement residual, projections and
-                          energy reduction)                                      */
+  int precision;       /* FEP3M_FP64 or FEP3M_MIXED.  Both solve the mesh
+                          system by iterative refinement around an FP32
+                          multigrid-preconditioned CG; the iterate and residual
+                          are FP64 (FP64) or double-float pairs (MIXED).  Pair
+                          and screen sums run in FP64 (FP64) or FP32 (MIXED);
+                          projections and the energy reduction in FP64.         */
   double mg_rtol;      /* relative FE residual target; 0 -> 1e-13 (FP64) or
                           1e-10 (MIXED)                                          */
-  int mg_max_cycles;   /* cap on preconditioned iterations (FP64) or refinement
-                          sweeps (MIXED); 0 -> default                           */
+  int mg_max_cycles;   /* cap on refinement sweeps; 0 -> 10                      */
   int table_pad;       /* Dirichlet box margin, elements, beyond the kept table;
                           0 -> 4                                                 */
   unsigned flags;      /* FEP3M_NEUTRALIZE                                       */
@@ -81,9 +83,8 @@ typedef struct {
 typedef struct {
   int64_t n_particles;
   int mg_levels;
-  int mg_iterations;        /* last forward solve: iterations (FP64) or total
-                               inner iterations (MIXED)                          */
-  int refine_steps;         /* MIXED: FP64 refinement sweeps used                 */
+  int mg_iterations;        /* last forward solve: total inner CG iterations     */
+  int refine_steps;         /* last forward solve: refinement sweeps              */
   double mg_rel_residual;   /* last forward solve, FP64 residual / |b|            */
   int adj_iterations;       /* last adjoint solve                                 */
   double adj_rel_residual;

@@ -56,28 +56,24 @@ struct Stencils {
 struct Level {
   int n = 0, N = 0;
   size_t size = 0;            // N^3
-  void* x = nullptr;          // solution / correction
-  void* b = nullptr;          // right-hand side
-  void* r = nullptr;          // residual / work
-  void* d = nullptr;          // Chebyshev direction
-  void* t1 = nullptr;         // apply intermediates
+  void* x = nullptr;          // correction (levels >= 1)
+  void* b = nullptr;          // right-hand side (levels >= 1)
+  void* r = nullptr;          // residual (all but the coarsest)
+  void* d = nullptr;          // Chebyshev direction (all but the coarsest)
+  void* t1 = nullptr;         // grid-transfer and coarsest-solve scratch
   void* t2 = nullptr;
-  void* a = nullptr;
-  void* c = nullptr;
+  void* a = nullptr;          // second Chebyshev iterate (all but the coarsest)
 };
 
 struct CoarseSolver {
   int N = 0;                  // nodes per axis on the coarsest level
-  double* V64 = nullptr;      // N x N, V[i][k] (row i node, column k mode), M-orthonormal
-  double* Dinv64 = nullptr;   // N^3 inverse eigenvalue sums (0 for the constant mode)
-  float* V32 = nullptr;
-  float* Dinv32 = nullptr;
-  double* VT64 = nullptr;     // V^T copies (coalesced loads of the forward transform)
-  float* VT32 = nullptr;
+  float* V32 = nullptr;       // N x N, V[i][k] (row i node, column k mode), M-orthonormal
+  float* Dinv32 = nullptr;    // N^3 inverse eigenvalue sums (0 for the constant mode)
+  float* VT32 = nullptr;      // V^T (row k mode): the forward transform
 };
 
 struct Hierarchy {
-  int elem_size = 0;          // 8 (double) or 4 (float)
+  int elem_size = 0;          // 4: the multigrid runs in FP32
   std::vector<Level> lv;
   CoarseSolver coarse;
   double lmax = 0;            // estimate of lambda_max(D^-1 K)
@@ -100,7 +96,7 @@ struct Solver {
   double* res64 = nullptr;         // refinement: projected b as float pairs (MIXED)
   double* phidf = nullptr;         // refinement: the iterate as float pairs (MIXED)
   // replayed solve: iteration counts calibrated on the first solve, captured as a graph
-  int plan_k = 0, plan_kin = 0, plan_kout = 0;
+  int plan_kin = 0, plan_kout = 0;
   cudaGraphExec_t solve_exec = nullptr;
   int solve_graph_kernels = 0;
   cudaStream_t cap_stream = nullptr;

@@ -449,7 +449,8 @@ __device__ __forceinline__ T apply_epilogue(int64_t g, T y, T bg, T dg, T xg, T*
     out[g] = y;
     return y;
   } else if constexpr (EPI == EPI_RESID) {
-    out[g] = bg - y;
+    if constexpr (std::is_same<T, float>::value) out[g] = bg - y;
+    else reinterpret_cast<float*>(out)[g] = (float)((bg - y) * (double)rs);   // FP64 refinement residual
     return y;
   } else if constexpr (EPI == EPI_CHEB) {
     const T dn = c1 * dg + c2 * dv * (bg - y);
@@ -467,9 +468,9 @@ __device__ __forceinline__ T apply_epilogue(int64_t g, T y, T bg, T dg, T xg, T*
 }
 
 // grid: (ceil(N / AFX), ceil(N / AFY), ceil(n / steps)), AT threads, dynamic
-// shared memory sizeof(ApplySmem<T, EPI>); N = 3 n with n >= 3.  T = dfv: x and b
-// are float pairs, out is FP32 and receives the residual times the power of
-// two the scaling reduction derived (scal)
+// shared memory sizeof(ApplySmem<T, EPI>); N = 3 n with n >= 3.  T = double or
+// dfv (EPI_RESID only, the refinement residual): out is FP32 and receives the
+// residual times the power of two the scaling reduction derived (scal)
 //
 // DOT (EPI_Y: x.(Kx); EPI_CHEB: b.(new iterate)): each thread accumulates its
 // nodes' products, then block_sum_finish with dt (partials indexed by the
@@ -488,10 +489,9 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
   const int x0 = blockIdx.x * AFX, y0 = blockIdx.y * AFY;
   const int e0 = blockIdx.z * steps, e1 = min(n, e0 + steps);
   const int tid = threadIdx.x;
-  float rs = 0.0f;
-  if constexpr (std::is_same<T, dfv>::value) {
-    rs = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_SCALE];
-  } else {
+  float rs = 0.0f;   // power-of-two scale of the refinement residual (FP64, double-float)
+  if constexpr (!std::is_same<T, float>::value) rs = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_SCALE];
+  if constexpr (!std::is_same<T, dfv>::value) {
     if (tid < 27) S.dinv[tid] = Cst<T>::Dinv(tid);
   }
   // this thread's halo columns (periodic in x and y); columns past the halo
@@ -667,24 +667,15 @@ static cudaError_t apply_set_smem() {
   if (e == cudaSuccess) e = apply_set_smem_one<float, EPI_CHEB0>();
   if (e == cudaSuccess) e = apply_set_smem_one<float, EPI_Y, true>();
   if (e == cudaSuccess) e = apply_set_smem_one<float, EPI_CHEB, true>();
-  if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_Y>();
   if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_RESID>();
-  if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_CHEB>();
-  if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_CHEB0>();
-  if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_Y, true>();
-  if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_CHEB, true>();
   if (e == cudaSuccess) e = apply_set_smem_one<dfv, EPI_RESID>();
-  // coarsest-level kernels at N = CP_MAX in FP64
-  const int smp = 3 * CP_MAX * (CP_MAX + 1) * (int)sizeof(double);
-  const int smq = (2 * CP_MAX * (CP_MAX + 1) + 2 * CP_PEN * (CP_MAX + 1)) * (int)sizeof(double);
+  // coarsest-level kernels at N = CP_MAX
+  const int smp = 3 * CP_MAX * (CP_MAX + 1) * (int)sizeof(float);
+  const int smq = (2 * CP_MAX * (CP_MAX + 1) + 2 * CP_PEN * (CP_MAX + 1)) * (int)sizeof(float);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_coarse_plane<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smp);
+    e = cudaFuncSetAttribute(k_coarse_plane<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smp);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_coarse_pencil<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smq);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_coarse_plane<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smp / 2);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_coarse_pencil<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smq / 2);
+    e = cudaFuncSetAttribute(k_coarse_pencil<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smq);
   return e;
 }
 
@@ -937,6 +928,33 @@ __global__ void k_df_update(int64_t n, dfv* __restrict__ phi, const float* __res
   phi[g] = {h, lo - (h - sum)};
 }
 
+// FP64 refinement: bp = b - m w3 (m = sum b / W); grid (ceil(N / bx), N, N)
+__global__ void k_project_copy64(int N, const double* __restrict__ b, const double* __restrict__ scal,
+                                 double* __restrict__ bp) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= N) return;
+  const int iy = blockIdx.y, iz = blockIdx.z;
+  const int64_t g = ix + (int64_t)N * (iy + (int64_t)N * iz);
+  const double w = (ix % 3 ? 0.375 : 0.25) * (iy % 3 ? 0.375 : 0.25) * (iz % 3 ? 0.375 : 0.25);
+  bp[g] = b[g] - scal[SC_DERIVED + SD_MEAN] * w;
+}
+
+// r = s v rounded to FP32 (s the power-of-two scale)
+__global__ void k_round_scaled64(int64_t n, const double* __restrict__ v, float* __restrict__ r,
+                                 const double* __restrict__ scal) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  r[g] = (float)(v[g] * scal[SC_DERIVED + SD_SCALE]);
+}
+
+// phi += e / s (FP64 accumulation of an FP32 correction)
+__global__ void k_add_scaled(int64_t n, double* __restrict__ phi, const float* __restrict__ e,
+                             const double* __restrict__ scal) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  phi[g] += scal[SC_DERIVED + SD_INVSCALE] * (double)e[g];
+}
+
 __global__ void k_df_to_double(int64_t n, const dfv* __restrict__ v, double* __restrict__ out) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
@@ -1058,9 +1076,10 @@ struct MG {
 
   void coarse_solve(const Level& L, const T* b, T* x) {
     const CoarseSolver& cs = H.coarse;
-    const T* V = (const T*)(sizeof(T) == 8 ? (const void*)cs.V64 : (const void*)cs.V32);
-    const T* VT = (const T*)(sizeof(T) == 8 ? (const void*)cs.VT64 : (const void*)cs.VT32);
-    const T* Dinv = (const T*)(sizeof(T) == 8 ? (const void*)cs.Dinv64 : (const void*)cs.Dinv32);
+    static_assert(std::is_same<T, float>::value, "the multigrid runs in FP32");
+    const T* V = cs.V32;
+    const T* VT = cs.VT32;
+    const T* Dinv = cs.Dinv32;
     const int N = L.N;
     cudaStream_t s = c->stream;
     T* w1 = (T*)L.t1;
@@ -1239,8 +1258,7 @@ static void upload_constants(const Stencils& st) {
 static cudaError_t mg_setup(Solver* c) {
   upload_constants(c->st);
   Hierarchy& H = c->mg;
-  const bool f32 = c->precision == FEP3M_MIXED;
-  H.elem_size = f32 ? 4 : 8;
+  H.elem_size = 4;   // the multigrid runs in FP32 in both precisions (refinement supplies the rest)
   H.lv.clear();
   int n = c->n;
   while (true) {
@@ -1253,9 +1271,15 @@ static cudaError_t mg_setup(Solver* c) {
     n /= 2;
   }
   const size_t es = H.elem_size;
-  for (Level& L : H.lv) {
-    void** bufs[] = {&L.x, &L.b, &L.r, &L.d, &L.t1, &L.t2, &L.a, &L.c};
+  for (size_t l = 0; l < H.lv.size(); ++l) {
+    Level& L = H.lv[l];
+    const bool coarsest = l + 1 == H.lv.size();
+    // level 0 solves for the CG vectors (no x, b of its own); the coarsest
+    // level neither smooths nor restricts (no r, d, a)
+    void** bufs[] = {l > 0 ? &L.x : nullptr, l > 0 ? &L.b : nullptr, coarsest ? nullptr : &L.r,
+                     coarsest ? nullptr : &L.d, &L.t1, &L.t2, coarsest ? nullptr : &L.a};
     for (void** p : bufs) {
+      if (!p) continue;
       cudaError_t e = cudaMalloc(p, L.size * es);
       if (e != cudaSuccess) return e;
     }
@@ -1275,51 +1299,38 @@ static cudaError_t mg_setup(Solver* c) {
   int null = 0;
   for (int i = 1; i < N; ++i)
     if (std::fabs(lam[i]) < std::fabs(lam[null])) null = i;
-  std::vector<double> Dinv((size_t)N * N * N);
+  std::vector<float> D32((size_t)N * N * N);
   for (int k = 0; k < N; ++k)
     for (int j = 0; j < N; ++j)
       for (int i = 0; i < N; ++i) {
         double D = lam[i] + lam[j] + lam[k];
-        Dinv[i + (size_t)N * (j + (size_t)N * k)] = (i == null && j == null && k == null) ? 0.0 : 1.0 / D;
+        D32[i + (size_t)N * (j + (size_t)N * k)] = (i == null && j == null && k == null) ? 0.0f : (float)(1.0 / D);
       }
   CoarseSolver& cs = H.coarse;
   cs.N = N;
   cudaError_t e;
-  std::vector<double> VT((size_t)N * N);
+  std::vector<float> V32(V.begin(), V.end()), VT32((size_t)N * N);
   for (int i = 0; i < N; ++i)
-    for (int k = 0; k < N; ++k) VT[(size_t)i * N + k] = V[(size_t)k * N + i];
-  if (f32) {
-    std::vector<float> V32(V.begin(), V.end()), VT32(VT.begin(), VT.end()), D32(Dinv.begin(), Dinv.end());
-    if ((e = cudaMalloc(&cs.V32, V32.size() * 4)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&cs.VT32, VT32.size() * 4)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&cs.Dinv32, D32.size() * 4)) != cudaSuccess) return e;
-    cudaMemcpy(cs.V32, V32.data(), V32.size() * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(cs.VT32, VT32.data(), VT32.size() * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(cs.Dinv32, D32.data(), D32.size() * 4, cudaMemcpyHostToDevice);
-  } else {
-    if ((e = cudaMalloc(&cs.V64, V.size() * 8)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&cs.VT64, VT.size() * 8)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&cs.Dinv64, Dinv.size() * 8)) != cudaSuccess) return e;
-    cudaMemcpy(cs.V64, V.data(), V.size() * 8, cudaMemcpyHostToDevice);
-    cudaMemcpy(cs.VT64, VT.data(), VT.size() * 8, cudaMemcpyHostToDevice);
-    cudaMemcpy(cs.Dinv64, Dinv.data(), Dinv.size() * 8, cudaMemcpyHostToDevice);
-  }
+    for (int k = 0; k < N; ++k) VT32[(size_t)i * N + k] = (float)V[(size_t)k * N + i];
+  if ((e = cudaMalloc(&cs.V32, V32.size() * 4)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&cs.VT32, VT32.size() * 4)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&cs.Dinv32, D32.size() * 4)) != cudaSuccess) return e;
+  cudaMemcpy(cs.V32, V32.data(), V32.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(cs.VT32, VT32.data(), VT32.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(cs.Dinv32, D32.data(), D32.size() * 4, cudaMemcpyHostToDevice);
   H.lmax = estimate_lmax(c->st, 6);
   return cudaGetLastError();
 }
 
 static void mg_free(Solver* c) {
   for (Level& L : c->mg.lv) {
-    void* bufs[] = {L.x, L.b, L.r, L.d, L.t1, L.t2, L.a, L.c};
+    void* bufs[] = {L.x, L.b, L.r, L.d, L.t1, L.t2, L.a};
     for (void* p : bufs)
       if (p) cudaFree(p);
   }
   c->mg.lv.clear();
   CoarseSolver& cs = c->mg.coarse;
-  if (cs.V64) cudaFree(cs.V64);
-  if (cs.VT64) cudaFree(cs.VT64);
   if (cs.VT32) cudaFree(cs.VT32);
-  if (cs.Dinv64) cudaFree(cs.Dinv64);
   if (cs.V32) cudaFree(cs.V32);
   if (cs.Dinv32) cudaFree(cs.Dinv32);
   cs = CoarseSolver();
@@ -1351,22 +1362,38 @@ static cudaError_t ensure_solver_buffers(Solver* c) {
   return cudaSuccess;
 }
 
-// r = s (b - K phi) in FP32 from the double-float phi and b (the refinement
-// residual; s the power-of-two scale in the derived scalars)
-static cudaError_t resid_df(Solver* c, const dfv* phi, const dfv* b, float* r) {
+// ---------------------------------------------------------------------------
+// Iterative refinement.  Both precisions solve K e = r for corrections with the
+// FP32 multigrid-preconditioned CG; the iterate, Pi b and the residual
+// r = Pi b - K phi are kept in a wider format: double-float (MIXED) or FP64
+// (FP64).  Every residual handed to the FP32 solve is scaled by one power of
+// two s (2^-k with 2^k near the RMS of b), so its range suits FP32 whatever
+// the units of b.
+//   MIXED: Pi b in res64 and the iterate in phidf, as float pairs
+//   FP64:  Pi b in res64 and the iterate in the output buffer, FP64
+
+// r = s (Pi b - K phi) in FP32
+static cudaError_t refine_resid(Solver* c, const double* phi64, float* r) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
   const int steps = apply_steps(N);
-  const dfv z = {0.0f, 0.0f};
   const ApplyDot nd = {nullptr, nullptr, nullptr, 0};
-  FEP3M_CL k_apply_el<dfv, EPI_RESID><<<apply_grid(N, steps), AT, sizeof(ApplySmem<dfv, EPI_RESID>), c->stream>>>(
-      N, steps, phi, reinterpret_cast<dfv*>(r), b, nullptr, nullptr, z, z, z, c->scal, nd);
+  if (c->precision == FEP3M_FP64) {
+    FEP3M_CL k_apply_el<double, EPI_RESID>
+        <<<apply_grid(N, steps), AT, sizeof(ApplySmem<double, EPI_RESID>), c->stream>>>(
+            N, steps, phi64, reinterpret_cast<double*>(r), c->res64, nullptr, nullptr, 0.0, 0.0, 0.0, c->scal, nd);
+  } else {
+    const dfv z = {0.0f, 0.0f};
+    FEP3M_CL k_apply_el<dfv, EPI_RESID>
+        <<<apply_grid(N, steps), AT, sizeof(ApplySmem<dfv, EPI_RESID>), c->stream>>>(
+            N, steps, reinterpret_cast<const dfv*>(c->phidf), reinterpret_cast<dfv*>(r),
+            reinterpret_cast<const dfv*>(c->res64), nullptr, nullptr, z, z, z, c->scal, nd);
+  }
   return cudaGetLastError();
 }
 
-// start of a MIXED solve: bdf = Pi b as float pairs, the power-of-two scale s
-// (2^-k with 2^k near the RMS of b), phidf = 0 and r = s Pi b in FP32
-static void refine_setup(Solver* c, const double* b, dfv* bdf, dfv* phidf, float* r) {
+// start: Pi b, the scale s, phi = 0, r = s Pi b in FP32
+static void refine_setup(Solver* c, const double* b, double* phi64, float* r) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
   const size_t n = L0.size;
@@ -1376,20 +1403,44 @@ static void refine_setup(Solver* c, const double* b, dfv* bdf, dfv* phidf, float
   reduce<double>(c, N, RD_SUM, b, nullptr, sc + 5, POST_MEAN, 1.0 / W);
   reduce<double>(c, N, RD_NORM2, b, nullptr, sc + 7, POST_SCALE, 1.0 / (double)n);
   const int bx = std::min(N, 256);
-  FEP3M_CL k_split_df<<<dim3((N + bx - 1) / bx, N, N), bx, 0, s>>>(N, b, sc, bdf);
-  cudaMemsetAsync(phidf, 0, n * sizeof(dfv), s);
-  FEP3M_CL k_df_round_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, bdf, r, sc);
+  const dim3 g3((N + bx - 1) / bx, N, N);
+  if (c->precision == FEP3M_FP64) {
+    FEP3M_CL k_project_copy64<<<g3, bx, 0, s>>>(N, b, sc, c->res64);
+    cudaMemsetAsync(phi64, 0, n * sizeof(double), s);
+    FEP3M_CL k_round_scaled64<<<grid_for(n), TPB, 0, s>>>((int64_t)n, c->res64, r, sc);
+  } else {
+    FEP3M_CL k_split_df<<<g3, bx, 0, s>>>(N, b, sc, reinterpret_cast<dfv*>(c->res64));
+    cudaMemsetAsync(c->phidf, 0, n * sizeof(dfv), s);
+    FEP3M_CL k_df_round_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, reinterpret_cast<const dfv*>(c->res64), r,
+                                                           sc);
+  }
 }
 
-// end of a MIXED solve: phi = phidf in FP64, mean zero
-static void refine_finish(Solver* c, const dfv* phidf, double* phi) {
+// phi += e / s
+static void refine_update(Solver* c, double* phi64, const float* e) {
+  const size_t n = c->mg.lv[0].size;
+  if (c->precision == FEP3M_FP64)
+    FEP3M_CL k_add_scaled<<<grid_for(n), TPB, 0, c->stream>>>((int64_t)n, phi64, e, c->scal);
+  else
+    FEP3M_CL k_df_update<<<grid_for(n), TPB, 0, c->stream>>>((int64_t)n, reinterpret_cast<dfv*>(c->phidf), e,
+                                                             c->scal);
+}
+
+// end: phi in FP64 with mean zero
+static void refine_finish(Solver* c, double* phi) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
   const size_t n = L0.size;
   const double W = (double)L0.n * L0.n * L0.n;
-  FEP3M_CL k_df_to_double<<<grid_for(n), TPB, 0, c->stream>>>((int64_t)n, phidf, phi);
+  if (c->precision != FEP3M_FP64)
+    FEP3M_CL k_df_to_double<<<grid_for(n), TPB, 0, c->stream>>>((int64_t)n, reinterpret_cast<const dfv*>(c->phidf),
+                                                                phi);
   reduce<double>(c, N, RD_WSUM, phi, nullptr, c->scal + 6, POST_MEAN, 1.0 / W);
   project<double>(c, N, phi, 1);
+}
+
+static double solver_rtol(const Solver* c) {
+  return c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : (c->precision == FEP3M_FP64 ? 1e-13 : 1e-10);
 }
 
 // host-checked solve (used once to calibrate the iteration counts, and as the
@@ -1398,41 +1449,25 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
                                  int* refine_steps, int* k_inner_max) {
   void** sb = c->sb;   // r, z, p, q, x, rhs
   const Level& L0 = c->mg.lv[0];
-  const size_t n = L0.size;
   const int N = L0.N;
   cudaStream_t s = c->stream;
-  const double W = (double)L0.n * L0.n * L0.n;
   double* sc = c->scal;
   *refine_steps = 0;
   *k_inner_max = 0;
-  if (c->precision == FEP3M_FP64) {
-    MG<double> mg(c);
-    const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : 1e-13;
-    const int maxit = c->cfg.mg_max_cycles > 0 ? c->cfg.mg_max_cycles : 60;
-    *iters = mg.pcg(b, phi, (double*)sb[0], (double*)sb[1], (double*)sb[2], (double*)sb[3], rtol, maxit, relres);
-    reduce<double>(c, N, RD_WSUM, phi, nullptr, sc + 6, POST_MEAN, 1.0 / W);
-    project<double>(c, N, phi, 1);
-    return cudaGetLastError();
-  }
-  // MIXED: iterative refinement.  The iterate and Pi b are double-float, the
-  // residual is formed in double-float arithmetic and rounded to FP32, the
-  // correction comes from the FP32 multigrid-preconditioned CG.
+  *iters = 0;
+  *relres = 0;
   MG<float> mg(c);
-  const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : 1e-10;
-  const int maxout = c->cfg.mg_max_cycles > 0 ? c->cfg.mg_max_cycles : 8;
-  dfv* bdf = reinterpret_cast<dfv*>(c->res64);
-  dfv* phd = reinterpret_cast<dfv*>(c->phidf);
+  const double rtol = solver_rtol(c);
+  const int maxout = c->cfg.mg_max_cycles > 0 ? c->cfg.mg_max_cycles : 10;
   float* r32 = (float*)sb[5];
   float* e32 = (float*)sb[4];
-  refine_setup(c, b, bdf, phd, r32);
+  refine_setup(c, b, phi, r32);
   reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 10);
   double bb = 0;
   cudaMemcpyAsync(&bb, sc + 10, sizeof(double), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
-  *iters = 0;
-  *relres = 0;
   if (bb == 0.0) {
-    refine_finish(c, phd, phi);
+    refine_finish(c, phi);
     return cudaGetLastError();
   }
   double rr = bb;
@@ -1442,10 +1477,10 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
     int it = mg.pcg(r32, e32, (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], 1e-5, 30, &inner_res);
     *iters += it;
     *k_inner_max = std::max(*k_inner_max, it);
-    FEP3M_CL k_df_update<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phd, e32, sc);
+    refine_update(c, phi, e32);
     // the residual's sum is rounding noise (K has zero column sums), and the
     // inner solve projects its right-hand side: no projection here
-    cudaError_t e = resid_df(c, phd, bdf, r32);
+    cudaError_t e = refine_resid(c, phi, r32);
     if (e != cudaSuccess) return e;
     reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 9);
     cudaMemcpyAsync(&rr, sc + 9, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1457,44 +1492,31 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
   }
   *refine_steps = step;
   *relres = std::sqrt(rr / bb);
-  refine_finish(c, phd, phi);
+  refine_finish(c, phi);
   return cudaGetLastError();
 }
 
 // fixed-count solve from c->in64 into c->out64, no host round trip; leaves
-// |Pi b|^2 in scal[10] and the final residual |r|^2 in scal[11]
+// |s Pi b|^2 in scal[10] and the final scaled residual |r|^2 in scal[11]
 static cudaError_t solve_fixed(Solver* c) {
   void** sb = c->sb;
   const Level& L0 = c->mg.lv[0];
-  const size_t n = L0.size;
   const int N = L0.N;
-  cudaStream_t s = c->stream;
-  const double W = (double)L0.n * L0.n * L0.n;
   double* sc = c->scal;
-  if (c->precision == FEP3M_FP64) {
-    MG<double> mg(c);
-    mg.pcg_fixed(c->in64, c->out64, (double*)sb[0], (double*)sb[1], (double*)sb[2], (double*)sb[3], c->plan_k);
-    cudaMemcpyAsync(sc + 10, sc + 4, sizeof(double), cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(sc + 11, sc + 3, sizeof(double), cudaMemcpyDeviceToDevice, s);
-    reduce<double>(c, N, RD_WSUM, c->out64, nullptr, sc + 6, POST_MEAN, 1.0 / W);
-    project<double>(c, N, c->out64, 1);
-    return cudaGetLastError();
-  }
   MG<float> mg(c);
-  dfv* bdf = reinterpret_cast<dfv*>(c->res64);
-  dfv* phd = reinterpret_cast<dfv*>(c->phidf);
   float* r32 = (float*)sb[5];
   float* e32 = (float*)sb[4];
-  refine_setup(c, c->in64, bdf, phd, r32);
+  double* phi = c->out64;
+  refine_setup(c, c->in64, phi, r32);
   reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 10);
   for (int step = 0; step < c->plan_kout; ++step) {
     mg.pcg_fixed(r32, e32, (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], c->plan_kin);
-    FEP3M_CL k_df_update<<<grid_for(n), TPB, 0, s>>>((int64_t)n, phd, e32, sc);
-    cudaError_t e = resid_df(c, phd, bdf, r32);
+    refine_update(c, phi, e32);
+    cudaError_t e = refine_resid(c, phi, r32);
     if (e != cudaSuccess) return e;
   }
   reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 11);
-  refine_finish(c, phd, c->out64);
+  refine_finish(c, phi);
   return cudaGetLastError();
 }
 
@@ -1540,21 +1562,13 @@ static cudaError_t build_plan(Solver* c) {
   return e;
 }
 
-static double solver_rtol(const Solver* c) {
-  return c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : (c->precision == FEP3M_FP64 ? 1e-13 : 1e-10);
-}
-
 // synchronous calibrated solve; records the counts and captures the replay graph
 static cudaError_t solve_calibrate(Solver* c, const double* b, double* phi) {
   int kin = 0;
   cudaError_t e = solve_checked(c, b, phi, &c->iters, &c->relres, &c->refine_steps, &kin);
   if (e != cudaSuccess || c->relres > solver_rtol(c)) return e;
-  if (c->precision == FEP3M_FP64) {
-    c->plan_k = std::max(c->plan_k, c->iters);
-  } else {
-    c->plan_kin = std::max(c->plan_kin, kin);
-    c->plan_kout = std::max(c->plan_kout, c->refine_steps);
-  }
+  c->plan_kin = std::max(c->plan_kin, kin);
+  c->plan_kout = std::max(c->plan_kout, c->refine_steps);
   const size_t n = c->mg.lv[0].size;
   if (!c->in64 && (e = cudaMalloc(&c->in64, n * sizeof(double))) != cudaSuccess) return e;
   if (!c->out64 && (e = cudaMalloc(&c->out64, n * sizeof(double))) != cudaSuccess) return e;
@@ -1591,13 +1605,12 @@ cudaError_t mesh_solve_end(Solver* c) {
   const double rel = bb > 0 ? std::sqrt(rr / bb) : 0.0;
   if (rel <= solver_rtol(c)) {
     c->relres = rel;
-    c->iters = c->precision == FEP3M_FP64 ? c->plan_k : c->plan_kin * c->plan_kout;
-    c->refine_steps = c->precision == FEP3M_FP64 ? 0 : c->plan_kout;
+    c->iters = c->plan_kin * c->plan_kout;
+    c->refine_steps = c->plan_kout;
     return cudaSuccess;
   }
   // this right-hand side needs more iterations: one more sweep from now on
-  if (c->precision == FEP3M_FP64) ++c->plan_k;
-  else ++c->plan_kout;
+  ++c->plan_kout;
   destroy_plan(c);
   return solve_calibrate(c, c->pend_b, c->pend_phi);
 }
