@@ -155,8 +155,9 @@ def test_mixed_matches_oracle(api, name):
     assert abs(r["U"] - ref["U"]) < bound, (abs(r["U"] - ref["U"]), bound)
 
 
-NACL_FP32 = pytest.mark.xfail(strict=True, reason="rock-salt forces are ~4% of the nearest-neighbour pair "
-                              "forces; the per-element field stored in FP32 limits them to ~1e-4")
+NACL_FP32 = pytest.mark.xfail(strict=True, reason="rock-salt forces are small residues of the field parts; the "
+                              "FP32 products and sums of the 512-term screen-field contraction leave ~1e-4 "
+                              "relative error in them (FP64 and the potentials pass)")
 
 
 @pytest.mark.parametrize("name", [pytest.param(k, marks=NACL_FP32) if k == "nacl16" else k for k in CASES])
