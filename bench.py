@@ -42,6 +42,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--legs", default="all", choices=["all", "main"],
+                   help="main: only the timed loop of --precision (no FP64 leg, end-to-end leg or accuracy); "
+                        "for profiling")
     return p.parse_args()
 
 
@@ -170,7 +173,8 @@ def run_ours(args):
     flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     results = {}
-    for prec in ([args.precision] + (["fp64"] if args.precision == "mixed" else [])):
+    legs = [args.precision] + (["fp64"] if args.precision == "mixed" and args.legs == "all" else [])
+    for prec in legs:
         eng = api.FEP3M(d["L"], d["n_el"], precision=prec, device=dev.index)
         eng.set_timing(True)
         out = dict(phi=torch.empty(N, dtype=torch.float64, device=dev),
@@ -199,6 +203,14 @@ def run_ours(args):
 
     main = results[args.precision]
     value = ws * N * main["steps"] / (main["total"] / 1e3)
+    if args.legs == "main":
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": round(value, 1), "unit": "particles/s", "n_gpus": ws,
+                              "steps": args.steps, "warmup": args.warmup, "legs": "main",
+                              "ms_per_step": round(main["total"] / main["steps"], 4)}))
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
 
     # end to end through the public API with pinned host buffers (H2D inputs, D2H Phi/forces/U)
     eng = main["eng"]
