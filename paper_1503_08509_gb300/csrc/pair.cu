@@ -56,148 +56,6 @@ template <class T> struct Acc {
   __device__ __forceinline__ T get() const { return s - c; }
 };
 
-template <class T, int K>
-__device__ __forceinline__ void block_sum(T (&v)[K], T* sh /* K * (PT/32) */) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    T x = v[k];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) sh[k * (PT / 32) + wid] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      T s = T(0);
-      for (int w = 0; w < PT / 32; ++w) s += sh[k * (PT / 32) + w];
-      v[k] = s;
-    }
-  }
-  __syncthreads();
-}
-
-// screen + mesh field of target element e at its 64 nodes (reference units)
-template <class T>
-__device__ void element_field(int n, int n_sr, int ex, int ey, int ez, const T* __restrict__ C,
-                              const T* __restrict__ rv, const T* __restrict__ phi_mesh, const T* __restrict__ Hw,
-                              T* __restrict__ G /* smem 64 */, T* __restrict__ Gp /* smem 4*64 */) {
-  const int keep = n_sr + 1, noff = 2 * n_sr + 2, no3 = noff * noff * noff;
-  const int m = threadIdx.x & 63, q = threadIdx.x >> 6;
-  T acc = T(0);
-  for (int o = q; o < no3; o += PT / 64) {
-    const int ox = o % noff - keep, oy = (o / noff) % noff - keep, oz = o / (noff * noff) - keep;
-    const int vx = ex - ox, vy = ey - oy, vz = ez - oz;   // vertex
-    T A;
-    if (ox > -keep && ox < n_sr && oy > -keep && oy < n_sr && oz > -keep && oz < n_sr) {
-      A = rv[wrapn(vx, n) + (int64_t)n * (wrapn(vy, n) + (int64_t)n * wrapn(vz, n))];
-    } else {
-      A = T(0);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
-        // corner k of element v - k lies in the block iff o + k in [-n_sr, n_sr] per axis
-        if (ox + kx < -n_sr || ox + kx > n_sr || oy + ky < -n_sr || oy + ky > n_sr || oz + kz < -n_sr ||
-            oz + kz > n_sr)
-          continue;
-        const int64_t el = wrapn(vx - kx, n) + (int64_t)n * (wrapn(vy - ky, n) + (int64_t)n * wrapn(vz - kz, n));
-        A += C[el * 8 + k];
-      }
-    }
-    acc += A * Hw[(int64_t)o * 64 + m];
-  }
-  Gp[q * 64 + m] = acc;
-  __syncthreads();
-  if (threadIdx.x < 64) {
-    T s = T(0);
-    for (int k = 0; k < PT / 64; ++k) s += Gp[k * 64 + m];
-    const int N = 3 * n;
-    const int mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
-    const int gx = wrapn(3 * ex + mx, N), gy = wrapn(3 * ey + my, N), gz = wrapn(3 * ez + mz, N);
-    G[m] = phi_mesh[gx + (int64_t)N * (gy + (int64_t)N * gz)] - s;
-  }
-  __syncthreads();
-}
-
-template <class T, bool GRAD>
-__global__ void __launch_bounds__(PT) k_pair_fwd(int n, int n_sr, T h, T inv_h, const int* __restrict__ start,
-                                                 const int* __restrict__ count,
-                                                 const typename vec4<T>::type* __restrict__ part,
-                                                 const T* __restrict__ C, const T* __restrict__ rv,
-                                                 const T* __restrict__ phi_mesh, const T* __restrict__ Hw,
-                                                 const int* __restrict__ perm, double* __restrict__ phi_s,
-                                                 double* __restrict__ E_s, double* __restrict__ phi_out) {
-  const int64_t e = blockIdx.x;
-  const int cnt = count[e];
-  if (cnt == 0) return;
-  __shared__ T G[64];
-  __shared__ T Gp[PT];
-  __shared__ T red[8 * (PT / 32)];
-  const int ex = (int)(e % n), ey = (int)((e / n) % n), ez = (int)(e / ((int64_t)n * n));
-  element_field<T>(n, n_sr, ex, ey, ez, C, rv, phi_mesh, Hw, G, Gp);
-  const int nb = 2 * n_sr + 1, nb3 = nb * nb * nb;
-  const int s0 = start[e];
-  for (int k = 0; k < cnt; ++k) {
-    const int slot = s0 + k;
-    const typename vec4<T>::type pt = part[slot];
-    T v[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = T(0);
-    if (threadIdx.x < 64) {
-      const int m = threadIdx.x, mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
-      T ux[4], uy[4], uz[4];
-      q3_values<T>(pt.x, ux);
-      q3_values<T>(pt.y, uy);
-      q3_values<T>(pt.z, uz);
-      v[0] = G[m] * ux[mx] * uy[my] * uz[mz];
-      if (GRAD) {
-        T dx[4], dy[4], dz[4];
-        q3_derivs<T>(pt.x, dx);
-        q3_derivs<T>(pt.y, dy);
-        q3_derivs<T>(pt.z, dz);
-        v[1] = G[m] * dx[mx] * uy[my] * uz[mz];
-        v[2] = G[m] * ux[mx] * dy[my] * uz[mz];
-        v[3] = G[m] * ux[mx] * uy[my] * dz[mz];
-      }
-    }
-    Acc<T> ps, fx, fy, fz;
-    for (int d = threadIdx.x; d < nb3; d += PT) {
-      const int dx = d % nb - n_sr, dy = (d / nb) % nb - n_sr, dz = d / (nb * nb) - n_sr;
-      const int64_t s = wrapn(ex + dx, n) + (int64_t)n * (wrapn(ey + dy, n) + (int64_t)n * wrapn(ez + dz, n));
-      const int j0 = start[s], j1 = j0 + count[s];
-      for (int j = j0; j < j1; ++j) {
-        if (j == slot) continue;
-        const typename vec4<T>::type pj = part[j];
-        const T rx = (T(dx) + pj.x - pt.x) * h, ry = (T(dy) + pj.y - pt.y) * h, rz = (T(dz) + pj.z - pt.z) * h;
-        const T ir = rsq<T>(rx * rx + ry * ry + rz * rz);
-        ps.add(pj.w * ir);
-        if (GRAD) {
-          const T f = pj.w * ir * ir * ir;   // d/dx_t of Q_j / |x_j - x_t| = Q_j (x_j - x_t) / r^3
-          fx.add(f * rx);
-          fy.add(f * ry);
-          fz.add(f * rz);
-        }
-      }
-    }
-    v[4] = ps.get();
-    v[5] = fx.get();
-    v[6] = fy.get();
-    v[7] = fz.get();
-    block_sum<T, 8>(v, red);
-    if (threadIdx.x == 0) {
-      const double phi = (double)v[0] * (double)inv_h + (double)v[4];
-      phi_s[slot] = phi;
-      if (phi_out) phi_out[perm[slot]] = phi;
-      if (GRAD) {
-        const double ih2 = (double)inv_h * (double)inv_h;
-        E_s[3 * slot + 0] = (double)v[1] * ih2 + (double)v[5];
-        E_s[3 * slot + 1] = (double)v[2] * ih2 + (double)v[6];
-        E_s[3 * slot + 2] = (double)v[3] * ih2 + (double)v[7];
-      }
-    }
-  }
-}
-
 // ------------------------------------------------------------------- v2
 // One CTA per brick of BX x BY x BZ target elements.
 //  (1) stage the brick's vertex densities and the element coefficients of its
@@ -211,24 +69,6 @@ __global__ void __launch_bounds__(PT) k_pair_fwd(int n, int n_sr, T h, T inv_h, 
 constexpr int BX = 4, BY = 4, BZ = 4, BE = BX * BY * BZ;   // 64 elements per brick
 constexpr int OCH = 32;                                      // offsets per chunk
 constexpr int MAXRUN = 2 * 81;                               // rows of the block (n_sr <= 4), 2 runs each
-
-struct BrickGeom {
-  int n, n_sr, keep, noff;
-  int E0x, E0y, E0z;        // brick origin (element coords)
-  int VW;                   // vertex tile width: BX + 2 n_sr + 1
-  int CW;                   // element tile width: BX + 2 n_sr
-};
-
-template <class T>
-struct PairSmem {
-  // sizes in elements of T, laid out in one dynamic buffer
-  static size_t bytes(int n_sr) {
-    const int VW = BX + 2 * n_sr + 1, CW = BX + 2 * n_sr;
-    size_t t = (size_t)VW * VW * VW + (size_t)CW * CW * CW * 8 + 2 * (size_t)OCH * 64;   // r, C, A chunk, H chunk
-    size_t ints = (BE + 1) + 8 * 2 * MAXRUN + 8 * (MAXRUN + 1);
-    return t * sizeof(T) + ints * sizeof(int) + 64;
-  }
-};
 
 // source weights of the singular sum: the charge itself, or an adjoint weight array
 template <class T> struct WeightQ {
@@ -314,184 +154,6 @@ __device__ __forceinline__ void warp_singular(int n, int n_sr, T h, int ex, int 
   out[3] = fz.get();
   for (int i = 0; i < 4; ++i) warp_sum(out[i]);
   __syncwarp();
-}
-
-template <class T, bool GRAD>
-__global__ void __launch_bounds__(PT) k_pair_brick(int n, int n_sr, T h, T inv_h, const int* __restrict__ start,
-                                                   const int* __restrict__ count,
-                                                   const typename vec4<T>::type* __restrict__ part,
-                                                   const int* __restrict__ ecoord, const T* __restrict__ C,
-                                                   const T* __restrict__ rv, const T* __restrict__ phi_mesh,
-                                                   const T* __restrict__ Hw, const int* __restrict__ perm,
-                                                   double* __restrict__ phi_s, double* __restrict__ E_s,
-                                                   double* __restrict__ phi_out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nbx = (n + BX - 1) / BX, nby = (n + BY - 1) / BY;
-  const int E0x = (blockIdx.x % nbx) * BX, E0y = ((blockIdx.x / nbx) % nby) * BY, E0z = (blockIdx.x / (nbx * nby)) * BZ;
-  const int keep = n_sr + 1, noff = 2 * n_sr + 2, no3 = noff * noff * noff;
-  const int VW = BX + 2 * n_sr + 1, CW = BX + 2 * n_sr;
-  T* r_t = (T*)smem_raw;                              // VW^3 vertex densities, origin E0 - n_sr
-  T* C_t = r_t + VW * VW * VW;                        // CW^3 x 8 element coefficients, origin E0 - n_sr
-  T* A_c = C_t + CW * CW * CW * 8;                    // [OCH][64]
-  T* H_c = A_c + OCH * 64;                            // [OCH][64]
-  int* epre = (int*)(H_c + OCH * 64);                 // BE + 1 target prefix over brick elements
-  int* runs_all = epre + BE + 1;                      // 8 warps x 2*MAXRUN
-  int* pre_all = runs_all + 8 * 2 * MAXRUN;           // 8 warps x (MAXRUN+1)
-  const int tid = threadIdx.x;
-  // targets in the brick
-  if (tid == 0) {
-    int acc = 0;
-    for (int l = 0; l < BE; ++l) {
-      epre[l] = acc;
-      const int lx = E0x + (l % BX), ly = E0y + (l / BX) % BY, lz = E0z + l / (BX * BY);
-      if (lx < n && ly < n && lz < n) acc += count[lx + (int64_t)n * (ly + (int64_t)n * lz)];
-    }
-    epre[BE] = acc;
-  }
-  __syncthreads();
-  const int ntarget = epre[BE];
-  if (ntarget == 0) return;
-  // (1) stage vertex densities and element coefficients of the halo
-  for (int i = tid; i < VW * VW * VW; i += PT) {
-    const int vx = i % VW, vy = (i / VW) % VW, vz = i / (VW * VW);
-    r_t[i] = rv[wrapn(E0x - n_sr + vx, n) + (int64_t)n * (wrapn(E0y - n_sr + vy, n) + (int64_t)n * wrapn(E0z - n_sr + vz, n))];
-  }
-  for (int i = tid; i < CW * CW * CW * 8; i += PT) {
-    const int k = i & 7, el = i >> 3;
-    const int cx = el % CW, cy = (el / CW) % CW, cz = el / (CW * CW);
-    C_t[i] = C[(wrapn(E0x - n_sr + cx, n) + (int64_t)n * (wrapn(E0y - n_sr + cy, n) + (int64_t)n * wrapn(E0z - n_sr + cz, n))) * 8 + k];
-  }
-  // (2) screen field, 4 x 4 register tile: elements 4 eb .. 4 eb + 3, nodes 4 mb .. 4 mb + 3
-  const int eb = tid >> 4, mb = tid & 15;
-  // per-chunk partial sums are added into a separate total: rounding grows with
-  // the 32-term chunks instead of all 512 terms
-  T acc[4][4], tot[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) tot[i][j] = T(0);
-  for (int o0 = 0; o0 < no3; o0 += OCH) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-    __syncthreads();
-    for (int i = tid; i < OCH * 64; i += PT) {
-      const int oi = i >> 6, m = i & 63, o = o0 + oi;
-      H_c[i] = o < no3 ? Hw[(int64_t)o * 64 + m] : T(0);
-      // vertex amplitude A(e, o) for brick element l = m (64 elements)
-      T A = T(0);
-      if (o < no3) {
-        const int l = m;
-        const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
-        const int ox = o % noff - keep, oy = (o / noff) % noff - keep, oz = o / (noff * noff) - keep;
-        // vertex v = e - o in tile coords (tile origin E0 - n_sr)
-        const int tx = lx - ox + n_sr, ty = ly - oy + n_sr, tz = lz - oz + n_sr;
-        if (ox > -keep && ox < n_sr && oy > -keep && oy < n_sr && oz > -keep && oz < n_sr) {
-          A = r_t[tx + VW * (ty + VW * tz)];
-        } else {
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
-            if (ox + kx < -n_sr || ox + kx > n_sr || oy + ky < -n_sr || oy + ky > n_sr || oz + kz < -n_sr ||
-                oz + kz > n_sr)
-              continue;
-            A += C_t[((tx - kx) + CW * ((ty - ky) + CW * (tz - kz))) * 8 + k];
-          }
-        }
-      }
-      A_c[i] = A;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int oi = 0; oi < OCH; ++oi) {
-      T a[4], hh[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        a[i] = A_c[oi * 64 + 4 * eb + i];
-        hh[i] = H_c[oi * 64 + 4 * mb + i];
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * hh[j];
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j];
-  }
-  __syncthreads();
-  // G = mesh potential - screen field, into the A chunk buffer ([64 elements][64 nodes] = 2 chunks)
-  T* G = A_c;
-  {
-    const int N = 3 * n;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int l = 4 * eb + i;
-      const int ex = E0x + l % BX, ey = E0y + (l / BX) % BY, ez = E0z + l / (BX * BY);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int m = 4 * mb + j, mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
-        T val = T(0);
-        if (ex < n && ey < n && ez < n) {
-          const int gx = wrapn(3 * ex + mx, N), gy = wrapn(3 * ey + my, N), gz = wrapn(3 * ez + mz, N);
-          val = phi_mesh[gx + (int64_t)N * (gy + (int64_t)N * gz)] - tot[i][j];
-        }
-        G[l * 64 + m] = val;
-      }
-    }
-  }
-  __syncthreads();
-  // (3) one warp per target
-  const int warp = tid >> 5, lane = tid & 31;
-  int* runs = runs_all + warp * 2 * MAXRUN;
-  int* pre = pre_all + warp * (MAXRUN + 1);
-  for (int k = warp; k < ntarget; k += PT / 32) {
-    int l = 0;
-    while (epre[l + 1] <= k) ++l;
-    const int ex = E0x + l % BX, ey = E0y + (l / BX) % BY, ez = E0z + l / (BX * BY);
-    const int64_t e = ex + (int64_t)n * (ey + (int64_t)n * ez);
-    const int slot = start[e] + (k - epre[l]);
-    const typename vec4<T>::type pt = part[slot];
-    T ux[4], uy[4], uz[4], dx4[4], dy4[4], dz4[4];
-    q3_values<T>(pt.x, ux);
-    q3_values<T>(pt.y, uy);
-    q3_values<T>(pt.z, uz);
-    if (GRAD) {
-      q3_derivs<T>(pt.x, dx4);
-      q3_derivs<T>(pt.y, dy4);
-      q3_derivs<T>(pt.z, dz4);
-    }
-    T ev[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-    for (int h2 = 0; h2 < 2; ++h2) {
-      const int m = lane + 32 * h2, mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
-      const T g = G[l * 64 + m];
-      ev[0] += g * ux[mx] * uy[my] * uz[mz];
-      if (GRAD) {
-        ev[1] += g * dx4[mx] * uy[my] * uz[mz];
-        ev[2] += g * ux[mx] * dy4[my] * uz[mz];
-        ev[3] += g * ux[mx] * uy[my] * dz4[mz];
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) warp_sum(ev[i]);
-    T sg[4];
-    warp_singular<T, GRAD>(n, n_sr, h, ex, ey, ez, slot, pt, start, part, ecoord, runs, pre,
-                           WeightQ<T>(), sg);
-    if (lane == 0) {
-      const double phi = (double)ev[0] * (double)inv_h + (double)sg[0];
-      phi_s[slot] = phi;
-      if (phi_out) phi_out[perm[slot]] = phi;
-      if (GRAD) {
-        const double ih2 = (double)inv_h * (double)inv_h;
-        E_s[3 * slot + 0] = (double)ev[1] * ih2 + (double)sg[1];
-        E_s[3 * slot + 1] = (double)ev[2] * ih2 + (double)sg[2];
-        E_s[3 * slot + 2] = (double)ev[3] * ih2 + (double)sg[3];
-      }
-    }
-  }
 }
 
 // ------------------------------------------------------------------- v3
@@ -945,79 +607,6 @@ __global__ void k_node_assemble(int n, const T* __restrict__ W, double* __restri
         acc += (double)W[e * 64 + lo[0][a] + 4 * lo[1][b] + 16 * lo[2][c]];
       }
   g[i] = acc;
-}
-
-// A[s][k] = sum_{e in block(s)} sum_m W[e][m] H(e - (s + k), m): the screen
-// part of the adjoint potential seen by the corner-k screen basis of element s
-template <class T>
-__global__ void __launch_bounds__(PT) k_screen_adjoint(int n, int n_sr, const int* __restrict__ count,
-                                                       const T* __restrict__ W, const T* __restrict__ Hw,
-                                                       T* __restrict__ A) {
-  const int64_t s = blockIdx.x;
-  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (count[s] == 0) {
-    if (lane == 0) A[s * 8 + k] = T(0);
-    return;
-  }
-  const int sx = (int)(s % n), sy = (int)((s / n) % n), sz = (int)(s / ((int64_t)n * n));
-  const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
-  const int nb = 2 * n_sr + 1, nb3 = nb * nb * nb, keep = n_sr + 1, noff = 2 * n_sr + 2;
-  T acc = T(0);
-  for (int d = 0; d < nb3; ++d) {
-    const int dx = d % nb - n_sr, dy = (d / nb) % nb - n_sr, dz = d / (nb * nb) - n_sr;
-    const int64_t e = wrapn(sx + dx, n) + (int64_t)n * (wrapn(sy + dy, n) + (int64_t)n * wrapn(sz + dz, n));
-    if (count[e] == 0) continue;
-    const int o = (dx - kx + keep) + noff * ((dy - ky + keep) + noff * (dz - kz + keep));
-    acc += W[e * 64 + lane] * Hw[(int64_t)o * 64 + lane] + W[e * 64 + lane + 32] * Hw[(int64_t)o * 64 + lane + 32];
-  }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if (lane == 0) A[s * 8 + k] = acc;
-}
-
-// psi_t = sum_j w_j / |x_j - x_t| and its x_t-gradient over the block (singular adjoint potential)
-template <class T>
-__global__ void __launch_bounds__(PT) k_pair_adj(int n, int n_sr, T h, const int* __restrict__ start,
-                                                 const int* __restrict__ count,
-                                                 const typename vec4<T>::type* __restrict__ part,
-                                                 const double* __restrict__ w, double* __restrict__ psi,
-                                                 double* __restrict__ gpsi) {
-  const int64_t e = blockIdx.x;
-  const int cnt = count[e];
-  if (cnt == 0) return;
-  __shared__ T red[4 * (PT / 32)];
-  const int ex = (int)(e % n), ey = (int)((e / n) % n), ez = (int)(e / ((int64_t)n * n));
-  const int nb = 2 * n_sr + 1, nb3 = nb * nb * nb;
-  const int s0 = start[e];
-  for (int k = 0; k < cnt; ++k) {
-    const int slot = s0 + k;
-    const typename vec4<T>::type pt = part[slot];
-    Acc<T> ps, fx, fy, fz;
-    for (int d = threadIdx.x; d < nb3; d += PT) {
-      const int dx = d % nb - n_sr, dy = (d / nb) % nb - n_sr, dz = d / (nb * nb) - n_sr;
-      const int64_t s = wrapn(ex + dx, n) + (int64_t)n * (wrapn(ey + dy, n) + (int64_t)n * wrapn(ez + dz, n));
-      const int j0 = start[s], j1 = j0 + count[s];
-      for (int j = j0; j < j1; ++j) {
-        if (j == slot) continue;
-        const typename vec4<T>::type pj = part[j];
-        const T rx = (T(dx) + pj.x - pt.x) * h, ry = (T(dy) + pj.y - pt.y) * h, rz = (T(dz) + pj.z - pt.z) * h;
-        const T ir = rsq<T>(rx * rx + ry * ry + rz * rz);
-        const T wj = (T)w[j];
-        ps.add(wj * ir);
-        const T f = wj * ir * ir * ir;
-        fx.add(f * rx);
-        fy.add(f * ry);
-        fz.add(f * rz);
-      }
-    }
-    T v[4] = {ps.get(), fx.get(), fy.get(), fz.get()};
-    block_sum<T, 4>(v, red);
-    if (threadIdx.x == 0) {
-      psi[slot] = (double)v[0];
-      gpsi[3 * slot + 0] = (double)v[1];
-      gpsi[3 * slot + 1] = (double)v[2];
-      gpsi[3 * slot + 2] = (double)v[3];
-    }
-  }
 }
 
 // Screen part of the adjoint, as a GEMM and a gather (deterministic, no atomics):
