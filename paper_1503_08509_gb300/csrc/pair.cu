@@ -56,16 +56,19 @@ template <class T> struct Acc {
   __device__ __forceinline__ T get() const { return s - c; }
 };
 
-// ------------------------------------------------------------------- v2
-// One CTA per brick of BX x BY x BZ target elements.
-//  (1) stage the brick's vertex densities and the element coefficients of its
-//      short-range halo in shared memory;
-//  (2) accumulate the screen field of all brick elements at their 64 nodes,
-//      G[e][m] = sum_o A(e, o) H(o, m), as 512 rank-1 updates of a 64 x 64
-//      tile (4 x 4 register tile per thread), staging A and H in chunks of 32
-//      offsets; add the mesh potential;
-//  (3) one warp per target charge: evaluate sum_m G u_m and its gradient, and
-//      the singular sum over the 49 contiguous element rows of its block.
+// ------------------------------------------------------------ brick kernel
+// One CTA per brick of BX x BY x BZ target elements:
+//  (1) the brick's "extended vertex field" R in shared memory (below);
+//  (2) the screen field of all brick elements at their 64 nodes,
+//      G[e][m] = phi[node(e, m)] - sum_o A(e, o) H(o, m), as 512 rank-1
+//      updates of a 64 x 64 tile (4 x 4 register tile per thread), staging A
+//      and H in chunks of OCH offsets;
+//  (3) the charges of the brick's short-range halo, staged in shared memory
+//      in element order (when they fit) with each charge's halo x index;
+//  (4) four threads per target: the smooth-and-screen potential from G at 16
+//      of the 64 nodes each, and the singular sum over a quarter of the 49
+//      element rows of the target's block, each row one contiguous run of
+//      staged charges.
 constexpr int BX = 4, BY = 4, BZ = 4, BE = BX * BY * BZ;   // 64 elements per brick
 constexpr int OCH = 32;                                      // offsets per chunk
 constexpr int MAXRUN = 2 * 81;                               // rows of the block (n_sr <= 4), 2 runs each
@@ -156,35 +159,32 @@ __device__ __forceinline__ void warp_singular(int n, int n_sr, T h, int ex, int 
   __syncwarp();
 }
 
-// ------------------------------------------------------------------- v3
-// Same decomposition as k_pair_brick, with two changes:
-//  * the vertex amplitudes come from an "extended vertex field" R built once
-//    per brick: per axis SW = 3 BX + 2 n_sr - 1 slots, the first SF = BX + 2 n_sr - 1
-//    the full vertex densities of the vertices interior offsets reach, then BX
-//    slots of corner-1-only sums (offset -(n_sr+1), vertex e + n_sr + 1) and BX
-//    of corner-0-only sums (offset n_sr, vertex e - n_sr).  A(e, o) is then the
-//    single value R[beta(o) + lambda(e)];
-//  * the charges of the brick's halo elements are staged in shared memory
-//    (when they fit) and each target's singular sum walks its 343 elements
-//    there; otherwise the row-run walk over global memory is used.
+// Extended vertex field: per axis SW = 3 BX + 2 n_sr - 1 slots, the first
+// SF = BX + 2 n_sr - 1 the full vertex densities of the vertices interior
+// offsets reach, then BX slots of corner-1-only sums (offset -(n_sr+1),
+// vertex e + n_sr + 1) and BX of corner-0-only sums (offset n_sr, vertex
+// e - n_sr).  A(e, o) is then the single value R[beta(o) + lambda(e)].
+constexpr int STAGE_CAP = 1536;   // halo charges staged in shared memory (T = float)
+
 template <class T>
 struct Pair3Smem {
   __host__ __device__ static int SW(int n_sr) { return 3 * BX + 2 * n_sr - 1; }
   __host__ __device__ static int HW(int n_sr) { return BX + 2 * n_sr; }
+  // charges that can be staged: STAGE_CAP floats-worth of float4 (half as many double4)
+  __host__ __device__ static int cap() { return STAGE_CAP * 4 / (int)sizeof(T); }
+  // region 1 holds R first, then the staged charges
   __host__ __device__ static size_t region1(int n_sr) {
     const int sw = SW(n_sr);
     const size_t r = (size_t)sw * sw * sw * sizeof(T);
-    const size_t runs = (size_t)8 * (2 * MAXRUN + MAXRUN + 1) * sizeof(int);
-    return (((r > runs ? r : runs) + 15) / 16) * 16;
+    const size_t stg = (size_t)cap() * sizeof(typename vec4<T>::type);
+    return (((r > stg ? r : stg) + 31) / 32) * 32;
   }
-  // charges that can be staged: region 1 holds R first, then the charges
-  __host__ __device__ static int cap(int n_sr) { return (int)(region1(n_sr) / sizeof(typename vec4<T>::type)); }
   static size_t bytes(int n_sr) {
     const int hw = HW(n_sr);
     const int noff = 2 * n_sr + 2, nb = 2 * n_sr + 1, sw = SW(n_sr);
     const size_t ints = (size_t)hw * hw * hw + 1 + BE + 1 + 1 + PT / 32 + 1 + (size_t)noff * noff * noff +
-                        2 * (size_t)nb * nb * nb + 3 * sw + 3 * hw + 32;
-    return region1(n_sr) + 2 * (size_t)OCH * 64 * sizeof(T) + ints * sizeof(int);
+                        (size_t)nb * nb + 3 * sw + 3 * hw + 32;
+    return region1(n_sr) + 2 * (size_t)OCH * 64 * sizeof(T) + ints * sizeof(int) + (size_t)cap();
   }
 };
 
@@ -230,11 +230,10 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
   const int E0x = (blockIdx.x % nbx) * BX, E0y = ((blockIdx.x / nbx) % nby) * BY, E0z = (blockIdx.x / (nbx * nby)) * BZ;
   const int keep = n_sr + 1, noff = 2 * n_sr + 2, no3 = noff * noff * noff;
   const int SW = 3 * BX + 2 * n_sr - 1, SF = BX + 2 * n_sr - 1, HW = BX + 2 * n_sr;
-  const int nb = 2 * n_sr + 1, nb3 = nb * nb * nb;
+  const int nb = 2 * n_sr + 1, nrow = nb * nb;
   const size_t r1 = Pair3Smem<T>::region1(n_sr);
   T* R = (T*)smem_raw;                                    // region 1: R, later the staged charges
   V4* stg = (V4*)smem_raw;
-  int* runs_all = (int*)smem_raw;                         // (fallback) region 1 as run tables
   T* A_c = (T*)(smem_raw + r1);                           // [OCH][64], then G [64][64] with H_c
   T* H_c = A_c + OCH * 64;
   int* hs = (int*)(H_c + OCH * 64);                       // halo element prefix, HW^3 + 1
@@ -242,10 +241,10 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
   int* flag = epre + BE + 1;
   int* wsum = flag + 1;                                   // PT/32 + 1 scan scratch
   int* otab = wsum + PT / 32 + 1;                         // no3: R base index of each offset
-  int* dtab = otab + no3;                                 // nb3: halo offset of each block element
-  int* dpk = dtab + nb3;                                  // nb3: packed (dx, dy, dz) + n_sr
-  int* wv = dpk + nb3;                                    // 3 x SW wrapped vertex coords
+  int* rtab = otab + no3;                                 // nb^2: halo offset of each (dy, dz) row
+  int* wv = rtab + nrow;                                  // 3 x SW wrapped vertex coords
   int* we = wv + 3 * SW;                                  // 3 x HW wrapped halo element coords
+  unsigned char* sxb = (unsigned char*)(we + 3 * HW + 32);   // cap(): halo x index of each staged charge
   const int tid = threadIdx.x;
   int ntarget;
   {
@@ -267,11 +266,7 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
     const int bz = oz == -keep ? SF : (oz == n_sr ? SF + BX : n_sr - 1 - oz);
     otab[o] = bx + SW * (by + SW * bz);
   }
-  for (int d = tid; d < nb3; d += PT) {
-    const int dx = d % nb, dy = (d / nb) % nb, dz = d / (nb * nb);
-    dtab[d] = dx + HW * (dy + HW * dz);
-    dpk[d] = dx | (dy << 8) | (dz << 16);
-  }
+  for (int r = tid; r < nrow; r += PT) rtab[r] = HW * ((r % nb) + HW * (r / nb));
   {
     const int E0[3] = {E0x, E0y, E0z};
     for (int i = tid; i < 3 * SW; i += PT) {
@@ -350,12 +345,11 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
       for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 #pragma unroll 4
     for (int oi = 0; oi < OCH; ++oi) {
-      T a[4], hh[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        a[i] = A_c[oi * 64 + 4 * eb + i];
-        hh[i] = H_c[oi * 64 + 4 * mb + i];
-      }
+      // one vector load each (16 lanes share the A row: a broadcast; the H
+      // rows of the 16 mb are contiguous: conflict-free)
+      const V4 av = *reinterpret_cast<const V4*>(A_c + oi * 64 + 4 * eb);
+      const V4 hv = *reinterpret_cast<const V4*>(H_c + oi * 64 + 4 * mb);
+      const T a[4] = {av.x, av.y, av.z, av.w}, hh[4] = {hv.x, hv.y, hv.z, hv.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -407,7 +401,7 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
     }
     int total;
     int run = block_scan_excl(sum, wsum, &total);
-    const bool fits = total <= Pair3Smem<T>::cap(n_sr);
+    const bool fits = total <= Pair3Smem<T>::cap();
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const int i = i0 + k;
@@ -415,7 +409,11 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
         hs[i] = run;
         if (fits) {
           const int j0 = start[gid[k]];
-          for (int q = 0; q < cnt[k]; ++q) stg[run + q] = part[j0 + q];
+          const unsigned char hx = (unsigned char)(i % HW);
+          for (int q = 0; q < cnt[k]; ++q) {
+            stg[run + q] = part[j0 + q];
+            sxb[run + q] = hx;
+          }
         }
       }
       run += cnt[k];
@@ -427,10 +425,12 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
   }
   __syncthreads();
   const bool staged = flag[0] != 0;
-  // (4) four threads per target: each takes 16 of the 64 nodes and a quarter
-  // of the block's elements; a two-step shuffle combines the quarters
+  // (4) four threads per target: each takes 16 of the 64 nodes and the rows
+  // r = q, q + 4, ... of the target's block; a two-step shuffle combines them.
+  // A row (dy, dz) of the block is 2 n_sr + 1 consecutive halo elements, so
+  // its staged charges are one run; each row's terms are summed in FP32 and
+  // the row sums are added with compensation.
   const int q = tid & 3;
-  const int d0 = (q * nb3) / 4, d1 = ((q + 1) * nb3) / 4;
   for (int tb = 0; tb < ntarget; tb += PT / 4) {
     const int k = tb + (tid >> 2);
     const bool valid = k < ntarget;
@@ -462,10 +462,12 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
       }
       // nodes 16 q .. 16 q + 15: mz = q, (mx, my) over 4 x 4
 #pragma unroll
-      for (int my = 0; my < 4; ++my)
+      for (int my = 0; my < 4; ++my) {
+        const V4 gv = *reinterpret_cast<const V4*>(G + l * 64 + 16 * q + 4 * my);
+        const T g4[4] = {gv.x, gv.y, gv.z, gv.w};
 #pragma unroll
         for (int mx = 0; mx < 4; ++mx) {
-          const T g = G[l * 64 + 16 * q + 4 * my + mx];
+          const T g = g4[mx];
           const T wyz = uy[my] * uz[q];
           v8[0] += g * ux[mx] * wyz;
           if (GRAD) {
@@ -474,48 +476,69 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
             v8[3] += g * ux[mx] * uy[my] * dz4[q];
           }
         }
+      }
       const int base = lx + HW * (ly + HW * lz);          // halo index of block offset (-n_sr, -n_sr, -n_sr)
+      const int cx = lx + n_sr;                           // the target's halo x index
       Acc<T> ps, fx, fy, fz;
       if (staged) {
         const int self = hs[base + n_sr * (1 + HW + HW * HW)] + kk;
-        for (int d = d0; d < d1; ++d) {
-          const int hidx = base + dtab[d];
-          const int pk = dpk[d];
-          const T ddx = T((pk & 255) - n_sr), ddy = T(((pk >> 8) & 255) - n_sr), ddz = T((pk >> 16) - n_sr);
-          const int j1 = hs[hidx + 1];
-          for (int j = hs[hidx]; j < j1; ++j) {
-            if (j == self) continue;
+        for (int r = q; r < nrow; r += 4) {
+          const int h0 = base + rtab[r];
+          const int j0 = hs[h0], j1 = hs[h0 + nb];
+          const T ddy = T(r % nb - n_sr), ddz = T(r / nb - n_sr);
+          T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+          for (int j = j0; j < j1; ++j) {
             const V4 pj = stg[j];
+            const T ddx = T((int)sxb[j] - cx);
             const T rx = (ddx + (pj.x - pt.x)) * h, ry = (ddy + (pj.y - pt.y)) * h, rz = (ddz + (pj.z - pt.z)) * h;
-            const T ir = rsq<T>(rx * rx + ry * ry + rz * rz);
-            ps.add(pj.w * ir);
+            const T ir = j == self ? T(0) : rsq<T>(rx * rx + ry * ry + rz * rz);
+            const T qi = pj.w * ir;
+            s0 += qi;
             if (GRAD) {
-              const T f3 = pj.w * ir * ir * ir;
-              fx.add(f3 * rx);
-              fy.add(f3 * ry);
-              fz.add(f3 * rz);
+              const T f3 = qi * ir * ir;
+              s1 += f3 * rx;
+              s2 += f3 * ry;
+              s3 += f3 * rz;
             }
+          }
+          ps.add(s0);
+          if (GRAD) {
+            fx.add(s1);
+            fy.add(s2);
+            fz.add(s3);
           }
         }
       } else {
-        for (int d = d0; d < d1; ++d) {
-          const int pk = dpk[d];
-          const int ax = pk & 255, ay = (pk >> 8) & 255, az = pk >> 16;   // 0 .. 2 n_sr
-          const int64_t g = we[lx + ax] + (int64_t)n * (we[HW + ly + ay] + (int64_t)n * we[2 * HW + lz + az]);
-          const T ddx = T(ax - n_sr), ddy = T(ay - n_sr), ddz = T(az - n_sr);
-          const int j0 = start[g], j1 = j0 + count[g];
-          for (int j = j0; j < j1; ++j) {
-            if (j == slot) continue;
-            const V4 pj = part[j];
-            const T rx = (ddx + (pj.x - pt.x)) * h, ry = (ddy + (pj.y - pt.y)) * h, rz = (ddz + (pj.z - pt.z)) * h;
-            const T ir = rsq<T>(rx * rx + ry * ry + rz * rz);
-            ps.add(pj.w * ir);
-            if (GRAD) {
-              const T f3 = pj.w * ir * ir * ir;
-              fx.add(f3 * rx);
-              fy.add(f3 * ry);
-              fz.add(f3 * rz);
+        // charges not staged (dense halo): the same rows from global memory,
+        // element by element (a row may wrap around the periodic box)
+        for (int r = q; r < nrow; r += 4) {
+          const int ay = r % nb, az = r / nb;
+          const int64_t rowg = (int64_t)n * (we[HW + ly + ay] + (int64_t)n * we[2 * HW + lz + az]);
+          const T ddy = T(ay - n_sr), ddz = T(az - n_sr);
+          T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+          for (int ax = 0; ax < nb; ++ax) {
+            const int64_t g = rowg + we[lx + ax];
+            const T ddx = T(ax - n_sr);
+            const int j0 = start[g], j1 = j0 + count[g];
+            for (int j = j0; j < j1; ++j) {
+              const V4 pj = part[j];
+              const T rx = (ddx + (pj.x - pt.x)) * h, ry = (ddy + (pj.y - pt.y)) * h, rz = (ddz + (pj.z - pt.z)) * h;
+              const T ir = j == slot ? T(0) : rsq<T>(rx * rx + ry * ry + rz * rz);
+              const T qi = pj.w * ir;
+              s0 += qi;
+              if (GRAD) {
+                const T f3 = qi * ir * ir;
+                s1 += f3 * rx;
+                s2 += f3 * ry;
+                s3 += f3 * rz;
+              }
             }
+          }
+          ps.add(s0);
+          if (GRAD) {
+            fx.add(s1);
+            fy.add(s2);
+            fz.add(s3);
           }
         }
       }
