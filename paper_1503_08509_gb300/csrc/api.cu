@@ -216,7 +216,7 @@ const char* fep3m_strerror(int s) {
 void fep3m_destroy(fep3m_ctx* c) {
   if (!c) return;
   free_particles(c);
-  void* p[] = {c->Hw64, c->Hw32, c->count, c->start, c->fill, c->scan_tmp, c->C, c->rv, c->b64, c->phi64,
+  void* p[] = {c->Hw64, c->Hw32, c->count, c->start, c->fill, c->scan_tmp, c->C, c->rv, c->Cv, c->b64, c->phi64,
                c->res64, c->g64, c->lam64, c->scal, c->iflags, c->phi_mesh_T, c->W_el, c->A_el, c->mu_v,
                c->red_tmp, c->red_counter, c->D_adj};
   for (void* q : p) dfree(q);
@@ -281,6 +281,7 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
       (e = dalloc(&c->fill, ne)) != cudaSuccess ||
       (e = cudaMalloc(&c->scan_tmp, scan_tmp_bytes(ne))) != cudaSuccess ||
       (e = cudaMalloc(&c->C, ne * 8 * es)) != cudaSuccess || (e = cudaMalloc(&c->rv, ne * es)) != cudaSuccess ||
+      (e = cudaMalloc(&c->Cv, ne * 8 * es)) != cudaSuccess ||
       (e = dalloc(&c->b64, nodes)) != cudaSuccess || (e = dalloc(&c->phi64, nodes)) != cudaSuccess ||
       (e = dalloc(&c->res64, nodes)) != cudaSuccess || (e = dalloc(&c->g64, nodes)) != cudaSuccess ||
       (e = dalloc(&c->lam64, nodes)) != cudaSuccess || (e = dalloc(&c->scal, 64)) != cudaSuccess ||

@@ -142,6 +142,7 @@ struct fep3m_ctx {
   // element / vertex fields
   void* C = nullptr;             // n^3 * 8 (T)
   void* rv = nullptr;            // n^3 vertex density (T)
+  void* Cv = nullptr;            // n^3 * 8 (T): C regrouped by vertex, Cv[v][k] = C[v - k][k]
   // fine-level FP64 vectors
   double* b64 = nullptr;         // (3n)^3 load vector
   double* phi64 = nullptr;       // (3n)^3 mesh potential, reference units

@@ -114,8 +114,10 @@ __global__ void k_elem_coeff(int64_t ne, const int* __restrict__ start, const in
   for (int k = 0; k < 8; ++k) C[e * 8 + k] = acc[k];
 }
 
+// vertex density r_v = sum_k C[v - k][k], and the same eight terms stored by
+// vertex (Cv[v][k]) for the short-range kernel's partial (block-boundary) sums
 template <class T>
-__global__ void k_vertex_density(int n, const T* __restrict__ C, T* __restrict__ rv) {
+__global__ void k_vertex_density(int n, const T* __restrict__ C, T* __restrict__ rv, T* __restrict__ Cv) {
   int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t ne = (int64_t)n * n * n;
   if (v >= ne) return;
@@ -124,7 +126,9 @@ __global__ void k_vertex_density(int n, const T* __restrict__ C, T* __restrict__
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     int ex = wrapi(vx - (k & 1), n), ey = wrapi(vy - ((k >> 1) & 1), n), ez = wrapi(vz - (k >> 2), n);
-    acc += C[(ex + (int64_t)n * (ey + (int64_t)n * ez)) * 8 + k];
+    const T ck = C[(ex + (int64_t)n * (ey + (int64_t)n * ez)) * 8 + k];
+    Cv[v * 8 + k] = ck;
+    acc += ck;
   }
   rv[v] = acc;
 }
@@ -1678,11 +1682,13 @@ cudaError_t assemble_forward(fep3m_ctx* c) {
   const size_t nodes = (size_t)27 * ne;
   if (c->precision == FEP3M_MIXED) {
     FEP3M_CL k_elem_coeff<float><<<grid_for(ne), TPB, 0, s>>>(ne, c->start, c->count, (const float4*)c->part, (float*)c->C);
-    FEP3M_CL k_vertex_density<float><<<grid_for(ne), TPB, 0, s>>>(n, (const float*)c->C, (float*)c->rv);
+    FEP3M_CL k_vertex_density<float><<<grid_for(ne), TPB, 0, s>>>(n, (const float*)c->C, (float*)c->rv,
+                                                                   (float*)c->Cv);
     FEP3M_CL k_load_vector<float><<<grid_for(nodes), TPB, 0, s>>>(n, (const float*)c->rv, c->b64);
   } else {
     FEP3M_CL k_elem_coeff<double><<<grid_for(ne), TPB, 0, s>>>(ne, c->start, c->count, (const vec4<double>::type*)c->part, (double*)c->C);
-    FEP3M_CL k_vertex_density<double><<<grid_for(ne), TPB, 0, s>>>(n, (const double*)c->C, (double*)c->rv);
+    FEP3M_CL k_vertex_density<double><<<grid_for(ne), TPB, 0, s>>>(n, (const double*)c->C, (double*)c->rv,
+                                                                    (double*)c->Cv);
     FEP3M_CL k_load_vector<double><<<grid_for(nodes), TPB, 0, s>>>(n, (const double*)c->rv, c->b64);
   }
   return cudaGetLastError();

@@ -219,7 +219,7 @@ template <class T, bool GRAD>
 __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_h, const int* __restrict__ start,
                                                     const int* __restrict__ count,
                                                     const typename vec4<T>::type* __restrict__ part,
-                                                    const int* __restrict__ ecoord, const T* __restrict__ C,
+                                                    const int* __restrict__ ecoord, const T* __restrict__ Cv,
                                                     const T* __restrict__ rv, const T* __restrict__ phi_mesh,
                                                     const T* __restrict__ Hw, const int* __restrict__ perm,
                                                     double* __restrict__ phi_s, double* __restrict__ E_s,
@@ -291,16 +291,17 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
     const int tz = sz < SF ? 3 : (sz < SF + BX ? 2 : 1);
     const int vx = wv[sx], vy = wv[SW + sy], vz = wv[2 * SW + sz];
     T val = T(0);
+    const int64_t v = vx + (int64_t)n * (vy + (int64_t)n * vz);
     if ((tx & ty & tz) == 3) {
-      val = rv[vx + (int64_t)n * (vy + (int64_t)n * vz)];
+      val = rv[v];
     } else {
-      const int vxm = vx == 0 ? n - 1 : vx - 1, vym = vy == 0 ? n - 1 : vy - 1, vzm = vz == 0 ? n - 1 : vz - 1;
+      // the vertex's eight corner terms are contiguous: two vector loads
+      const V4 c03 = reinterpret_cast<const V4*>(Cv + 8 * v)[0], c47 = reinterpret_cast<const V4*>(Cv + 8 * v)[1];
+      const T c8[8] = {c03.x, c03.y, c03.z, c03.w, c47.x, c47.y, c47.z, c47.w};
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
-        if (!((tx >> kx) & 1) || !((ty >> ky) & 1) || !((tz >> kz) & 1)) continue;
-        const int ex = kx ? vxm : vx, ey = ky ? vym : vy, ez = kz ? vzm : vz;
-        val += C[(ex + (int64_t)n * (ey + (int64_t)n * ez)) * 8 + k];
+        if (((tx >> kx) & 1) && ((ty >> ky) & 1) && ((tz >> kz) & 1)) val += c8[k];
       }
     }
     R[i] = val;
@@ -862,7 +863,7 @@ static cudaError_t launch_pair_brick(fep3m_ctx* c, const T* phi_mesh, const T* H
   if (e != cudaSuccess) return e;
   FEP3M_CL kern<<<(unsigned)(nbx * nby * nbz), PT, smem, c->stream>>>(
       n, c->n_sr, (T)c->h, (T)c->inv_h, c->start, c->count, (const typename vec4<T>::type*)c->part, c->ecoord,
-      (const T*)c->C, (const T*)c->rv, phi_mesh, Hw, c->perm, c->phi_s, c->E_s, phi_out);
+      (const T*)c->Cv, (const T*)c->rv, phi_mesh, Hw, c->perm, c->phi_s, c->E_s, phi_out);
   return cudaGetLastError();
 }
 
