@@ -179,6 +179,7 @@ constexpr int CP_MAX = 64, CP_PEN = 32;
 template <class T>
 __global__ void __launch_bounds__(256) k_coarse_plane(int N, const T* __restrict__ A, const T* __restrict__ in,
                                                       T* __restrict__ out) {
+  PDL_PROLOGUE
   extern __shared__ __align__(16) unsigned char cpsm[];
   const int P = N + 1;   // padded row
   T* As = (T*)cpsm;      // A[r][k] at r P + k
@@ -218,6 +219,7 @@ template <class T>
 __global__ void __launch_bounds__(256) k_coarse_pencil(int N, const T* __restrict__ VT, const T* __restrict__ V,
                                                        const T* __restrict__ Dinv, const T* __restrict__ in,
                                                        T* __restrict__ out) {
+  PDL_PROLOGUE
   extern __shared__ __align__(16) unsigned char cpsm[];
   const int P = N + 1;
   T* VTs = (T*)cpsm;
@@ -483,6 +485,7 @@ template <class T, int EPI, bool DOT = false>
 __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
     k_apply_el(int N, int steps, const T* __restrict__ x, T* __restrict__ out, const T* __restrict__ b,
                T* __restrict__ d, T* __restrict__ xo, T c0, T c1, T c2, double* __restrict__ scal, ApplyDot dt) {
+  PDL_PROLOGUE
   static_assert(!DOT || EPI == EPI_Y || EPI == EPI_CHEB, "fused dots: EPI_Y and EPI_CHEB");
   extern __shared__ __align__(16) unsigned char apply_smem_raw[];
   ApplySmem<T, EPI, DOT>& S = *reinterpret_cast<ApplySmem<T, EPI, DOT>*>(apply_smem_raw);
@@ -699,6 +702,7 @@ static inline dim3 apply_grid(int N, int steps) {
 // when the smoothing degree is 1); grid (ceil(N / 128), N, N)
 template <class T>
 __global__ void k_cheb0(int N, const T* __restrict__ b, T* __restrict__ d, T* __restrict__ x, T inv_theta) {
+  PDL_PROLOGUE
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
   if (ix >= N) return;
   const int iy = blockIdx.y, iz = blockIdx.z;
@@ -715,6 +719,7 @@ __global__ void k_cheb0(int N, const T* __restrict__ b, T* __restrict__ d, T* __
 template <class T>
 __global__ void k_restrict_axis(int axis, int Nc, int e0, int e1, int e2, const T* __restrict__ in,
                                 T* __restrict__ out, T scale) {
+  PDL_PROLOGUE
   // the row of P depends on the lane: read it from shared memory, not from
   // the constant bank (which serialises lanes that read different addresses)
   __shared__ T Ps[6][4];
@@ -749,6 +754,7 @@ __global__ void k_restrict_axis(int axis, int Nc, int e0, int e1, int e2, const 
 template <class T, bool ADD>
 __global__ void k_prolong_axis(int axis, int Nc, int e0, int e1, int e2, const T* __restrict__ in,
                                T* __restrict__ out, const T* __restrict__ add) {
+  PDL_PROLOGUE
   __shared__ T Ps[6][4];
   if (threadIdx.x < 24) Ps[threadIdx.x / 4][threadIdx.x % 4] = Cst<T>::P(threadIdx.x / 4, threadIdx.x % 4);
   __syncthreads();
@@ -779,6 +785,7 @@ __global__ void k_prolong_axis(int axis, int Nc, int e0, int e1, int e2, const T
 template <class T>
 __global__ void k_dense_axis(int N, int axis, const T* __restrict__ V, bool transpose, const T* __restrict__ in,
                              T* __restrict__ out, const T* __restrict__ scale) {
+  PDL_PROLOGUE
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t NN = (int64_t)N * N;
   if (g >= NN * N) return;
@@ -815,6 +822,7 @@ template <class T, int MODE>
 __global__ void k_reduce(int N, const T* __restrict__ x, const T* __restrict__ y, double* __restrict__ partials,
                          unsigned int* __restrict__ counter, double* __restrict__ out, int post, double arg,
                          double* __restrict__ scal) {
+  PDL_PROLOGUE
   const int64_t NN = (int64_t)N * N, tot = NN * N;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
@@ -859,6 +867,7 @@ __device__ __forceinline__ T derived(const double* scal, int k) {
 // v -= m (mean zero, m = sum w3 v / W); grid (ceil(N / bx), N, N)
 template <class T>
 __global__ void k_project(int N, T* __restrict__ v, const double* __restrict__ scal, int mean_zero) {
+  PDL_PROLOGUE
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
   if (ix >= N) return;
   const int iy = blockIdx.y, iz = blockIdx.z;
@@ -877,6 +886,7 @@ __global__ void k_project(int N, T* __restrict__ v, const double* __restrict__ s
 template <class T>
 __global__ void k_cg_update(int64_t n, const double* __restrict__ scal, T* __restrict__ x, T* __restrict__ r,
                             const T* __restrict__ p, const T* __restrict__ q) {
+  PDL_PROLOGUE
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
   const T alpha = derived<T>(scal, SD_ALPHA);
@@ -886,6 +896,7 @@ __global__ void k_cg_update(int64_t n, const double* __restrict__ scal, T* __res
 //   p = z + beta p
 template <class T>
 __global__ void k_cg_dir(int64_t n, const double* __restrict__ scal, T* __restrict__ p, const T* __restrict__ z) {
+  PDL_PROLOGUE
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
   const T beta = derived<T>(scal, SD_BETA);
@@ -896,6 +907,7 @@ __global__ void k_cg_dir(int64_t n, const double* __restrict__ scal, T* __restri
 // bdf = b - m w3 as float pairs (m = sum b / W from the preceding reduction);
 // grid (ceil(N / bx), N, N)
 __global__ void k_split_df(int N, const double* __restrict__ b, const double* __restrict__ scal, dfv* __restrict__ bdf) {
+  PDL_PROLOGUE
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
   if (ix >= N) return;
   const int iy = blockIdx.y, iz = blockIdx.z;
@@ -909,6 +921,7 @@ __global__ void k_split_df(int N, const double* __restrict__ b, const double* __
 // r = s (h + l) rounded to FP32 (s the power-of-two scale)
 __global__ void k_df_round_scaled(int64_t n, const dfv* __restrict__ v, float* __restrict__ r,
                                   const double* __restrict__ scal) {
+  PDL_PROLOGUE
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
   const float s = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_SCALE];
@@ -919,6 +932,7 @@ __global__ void k_df_round_scaled(int64_t n, const dfv* __restrict__ v, float* _
 // phi += e / s (exact: s is a power of two), two-sum then renormalised
 __global__ void k_df_update(int64_t n, dfv* __restrict__ phi, const float* __restrict__ e,
                             const double* __restrict__ scal) {
+  PDL_PROLOGUE
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
   const float is = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_INVSCALE];
@@ -935,6 +949,7 @@ __global__ void k_df_update(int64_t n, dfv* __restrict__ phi, const float* __res
 // FP64 refinement: bp = b - m w3 (m = sum b / W); grid (ceil(N / bx), N, N)
 __global__ void k_project_copy64(int N, const double* __restrict__ b, const double* __restrict__ scal,
                                  double* __restrict__ bp) {
+  PDL_PROLOGUE
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
   if (ix >= N) return;
   const int iy = blockIdx.y, iz = blockIdx.z;
@@ -946,6 +961,7 @@ __global__ void k_project_copy64(int N, const double* __restrict__ b, const doub
 // r = s v rounded to FP32 (s the power-of-two scale)
 __global__ void k_round_scaled64(int64_t n, const double* __restrict__ v, float* __restrict__ r,
                                  const double* __restrict__ scal) {
+  PDL_PROLOGUE
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
   r[g] = (float)(v[g] * scal[SC_DERIVED + SD_SCALE]);
@@ -954,12 +970,14 @@ __global__ void k_round_scaled64(int64_t n, const double* __restrict__ v, float*
 // phi += e / s (FP64 accumulation of an FP32 correction)
 __global__ void k_add_scaled(int64_t n, double* __restrict__ phi, const float* __restrict__ e,
                              const double* __restrict__ scal) {
+  PDL_PROLOGUE
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
   phi[g] += scal[SC_DERIVED + SD_INVSCALE] * (double)e[g];
 }
 
 __global__ void k_df_to_double(int64_t n, const dfv* __restrict__ v, double* __restrict__ out) {
+  PDL_PROLOGUE
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
   const dfv x = v[g];
@@ -982,13 +1000,13 @@ static void reduce(Solver* c, int N, int mode, const T* x, const T* y, double* o
   double* tmp = (double*)c->red_tmp;
   cudaStream_t s = c->stream;
   if (mode == RD_DOT)
-    FEP3M_CL k_reduce<T, RD_DOT><<<nb, TPB, 0, s>>>(N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
+    launch_pdl(k_reduce<T, RD_DOT>, nb, TPB, 0, s, N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
   else if (mode == RD_SUM)
-    FEP3M_CL k_reduce<T, RD_SUM><<<nb, TPB, 0, s>>>(N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
+    launch_pdl(k_reduce<T, RD_SUM>, nb, TPB, 0, s, N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
   else if (mode == RD_WSUM)
-    FEP3M_CL k_reduce<T, RD_WSUM><<<nb, TPB, 0, s>>>(N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
+    launch_pdl(k_reduce<T, RD_WSUM>, nb, TPB, 0, s, N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
   else
-    FEP3M_CL k_reduce<T, RD_NORM2><<<nb, TPB, 0, s>>>(N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
+    launch_pdl(k_reduce<T, RD_NORM2>, nb, TPB, 0, s, N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
 }
 
 // remove the background load (mean_zero 0) or the mean (1) with the scalar
@@ -997,7 +1015,7 @@ template <class T>
 static void project(Solver* c, int N, T* v, int mean_zero) {
   const int bx = std::min(N, 256);
   const dim3 grid((N + bx - 1) / bx, N, N);
-  FEP3M_CL k_project<T><<<grid, bx, 0, c->stream>>>(N, v, c->scal, mean_zero);
+  launch_pdl(k_project<T>, grid, bx, 0, c->stream, N, v, c->scal, mean_zero);
 }
 
 template <class T>
@@ -1016,22 +1034,22 @@ struct MG {
     double* sc = c->scal;
     const ApplyDot nd = {nullptr, nullptr, nullptr, 0};
     if (epi == EPI_Y && dot)
-      FEP3M_CL k_apply_el<T, EPI_Y, true><<<grid, AT, sizeof(ApplySmem<T, EPI_Y, true>), s>>>(
+      launch_pdl(k_apply_el<T, EPI_Y, true>, grid, AT, sizeof(ApplySmem<T, EPI_Y, true>), s, 
           L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, *dot);
     else if (epi == EPI_Y)
-      FEP3M_CL k_apply_el<T, EPI_Y><<<grid, AT, sizeof(ApplySmem<T, EPI_Y>), s>>>(L.N, steps, x, out, b, d, xo,
+      launch_pdl(k_apply_el<T, EPI_Y>, grid, AT, sizeof(ApplySmem<T, EPI_Y>), s, L.N, steps, x, out, b, d, xo,
                                                                                   c0, c1, c2, sc, nd);
     else if (epi == EPI_RESID)
-      FEP3M_CL k_apply_el<T, EPI_RESID><<<grid, AT, sizeof(ApplySmem<T, EPI_RESID>), s>>>(
+      launch_pdl(k_apply_el<T, EPI_RESID>, grid, AT, sizeof(ApplySmem<T, EPI_RESID>), s, 
           L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, nd);
     else if (epi == EPI_CHEB && dot)
-      FEP3M_CL k_apply_el<T, EPI_CHEB, true><<<grid, AT, sizeof(ApplySmem<T, EPI_CHEB, true>), s>>>(
+      launch_pdl(k_apply_el<T, EPI_CHEB, true>, grid, AT, sizeof(ApplySmem<T, EPI_CHEB, true>), s, 
           L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, *dot);
     else if (epi == EPI_CHEB)
-      FEP3M_CL k_apply_el<T, EPI_CHEB><<<grid, AT, sizeof(ApplySmem<T, EPI_CHEB>), s>>>(
+      launch_pdl(k_apply_el<T, EPI_CHEB>, grid, AT, sizeof(ApplySmem<T, EPI_CHEB>), s, 
           L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, nd);
     else
-      FEP3M_CL k_apply_el<T, EPI_CHEB0><<<grid, AT, sizeof(ApplySmem<T, EPI_CHEB0>), s>>>(
+      launch_pdl(k_apply_el<T, EPI_CHEB0>, grid, AT, sizeof(ApplySmem<T, EPI_CHEB0>), s, 
           L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, nd);
   }
 
@@ -1052,7 +1070,7 @@ struct MG {
     T* oth = x;
     if (from_zero) {
       if (degree <= 1) {
-        FEP3M_CL k_cheb0<T><<<dim3((L.N + 127) / 128, L.N, L.N), 128, 0, c->stream>>>(L.N, b, (T*)L.d, x,
+        launch_pdl(k_cheb0<T>, dim3((L.N + 127) / 128, L.N, L.N), 128, 0, c->stream, L.N, b, (T*)L.d, x,
                                                                                       (T)(1.0 / theta));
         return;
       }
@@ -1092,18 +1110,18 @@ struct MG {
       const size_t smp = (size_t)3 * N * (N + 1) * sizeof(T);
       const size_t smq = ((size_t)2 * N * (N + 1) + (size_t)2 * CP_PEN * (N + 1)) * sizeof(T);
       const unsigned gq = (unsigned)(((int64_t)N * N + CP_PEN - 1) / CP_PEN);
-      FEP3M_CL k_coarse_plane<T><<<N, 256, smp, s>>>(N, VT, b, w1);
-      FEP3M_CL k_coarse_pencil<T><<<gq, 256, smq, s>>>(N, VT, V, Dinv, w1, w2);
-      FEP3M_CL k_coarse_plane<T><<<N, 256, smp, s>>>(N, V, w2, x);
+      launch_pdl(k_coarse_plane<T>, N, 256, smp, s, N, VT, b, w1);
+      launch_pdl(k_coarse_pencil<T>, gq, 256, smq, s, N, VT, V, Dinv, w1, w2);
+      launch_pdl(k_coarse_plane<T>, N, 256, smp, s, N, V, w2, x);
       return;
     }
     const int gsz = grid_for(L.size);
-    FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 0, V, true, b, w1, nullptr);
-    FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 1, V, true, w1, w2, nullptr);
-    FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 2, V, true, w2, w1, Dinv);
-    FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 0, V, false, w1, w2, nullptr);
-    FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 1, V, false, w2, w1, nullptr);
-    FEP3M_CL k_dense_axis<T><<<gsz, TPB, 0, s>>>(N, 2, V, false, w1, x, nullptr);
+    launch_pdl(k_dense_axis<T>, gsz, TPB, 0, s, N, 0, V, true, b, w1, nullptr);
+    launch_pdl(k_dense_axis<T>, gsz, TPB, 0, s, N, 1, V, true, w1, w2, nullptr);
+    launch_pdl(k_dense_axis<T>, gsz, TPB, 0, s, N, 2, V, true, w2, w1, Dinv);
+    launch_pdl(k_dense_axis<T>, gsz, TPB, 0, s, N, 0, V, false, w1, w2, nullptr);
+    launch_pdl(k_dense_axis<T>, gsz, TPB, 0, s, N, 1, V, false, w2, w1, nullptr);
+    launch_pdl(k_dense_axis<T>, gsz, TPB, 0, s, N, 2, V, false, w1, x, nullptr);
   }
 
   // approximately solve A_l x = b on level l (x overwritten)
@@ -1124,13 +1142,13 @@ struct MG {
     T* s1 = (T*)L.t1;
     T* s2 = (T*)L.t2;
     auto g3 = [](int e0, int e1, int e2) { return dim3((e0 + 127) / 128, e1, e2); };
-    FEP3M_CL k_restrict_axis<T><<<g3(Nc, Nf, Nf), 128, 0, s>>>(0, Nc, Nc, Nf, Nf, (T*)L.r, s1, T(1));
-    FEP3M_CL k_restrict_axis<T><<<g3(Nc, Nc, Nf), 128, 0, s>>>(1, Nc, Nc, Nc, Nf, s1, s2, T(1));
-    FEP3M_CL k_restrict_axis<T><<<g3(Nc, Nc, Nc), 128, 0, s>>>(2, Nc, Nc, Nc, Nc, s2, (T*)Cl.b, T(0.5));
+    launch_pdl(k_restrict_axis<T>, g3(Nc, Nf, Nf), 128, 0, s, 0, Nc, Nc, Nf, Nf, (T*)L.r, s1, T(1));
+    launch_pdl(k_restrict_axis<T>, g3(Nc, Nc, Nf), 128, 0, s, 1, Nc, Nc, Nc, Nf, s1, s2, T(1));
+    launch_pdl(k_restrict_axis<T>, g3(Nc, Nc, Nc), 128, 0, s, 2, Nc, Nc, Nc, Nc, s2, (T*)Cl.b, T(0.5));
     vcycle(l + 1, (T*)Cl.b, (T*)Cl.x);
-    FEP3M_CL k_prolong_axis<T, false><<<g3(Nc, Nc, Nf), 128, 0, s>>>(2, Nc, Nc, Nc, Nf, (T*)Cl.x, s1, nullptr);
-    FEP3M_CL k_prolong_axis<T, false><<<g3(Nc, Nf, Nf), 128, 0, s>>>(1, Nc, Nc, Nf, Nf, s1, s2, nullptr);
-    FEP3M_CL k_prolong_axis<T, true><<<g3(Nf, Nf, Nf), 128, 0, s>>>(0, Nc, Nf, Nf, Nf, s2, (T*)L.a, x);
+    launch_pdl(k_prolong_axis<T, false>, g3(Nc, Nc, Nf), 128, 0, s, 2, Nc, Nc, Nc, Nf, (T*)Cl.x, s1, nullptr);
+    launch_pdl(k_prolong_axis<T, false>, g3(Nc, Nf, Nf), 128, 0, s, 1, Nc, Nc, Nf, Nf, s1, s2, nullptr);
+    launch_pdl(k_prolong_axis<T, true>, g3(Nf, Nf, Nf), 128, 0, s, 0, Nc, Nf, Nf, Nf, s2, (T*)L.a, x);
     smooth(L, x, b, false, H.cheb_degree, dot);   // starts from L.a = x + P e
   }
 
@@ -1163,13 +1181,13 @@ struct MG {
     double rr = bb;
     for (it = 1; it <= maxit; ++it) {
       apply(L, p, EPI_Y, q, nullptr, nullptr, nullptr, T(0), T(0), T(0), &d_pq);
-      FEP3M_CL k_cg_update<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, x, r, p, q);
+      launch_pdl(k_cg_update<T>, grid_for(n), TPB, 0, s, (int64_t)n, sc, x, r, p, q);
       reduce<T>(c, N, RD_NORM2, r, nullptr, sc + 3);
       cudaMemcpyAsync(&rr, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s);
       cudaStreamSynchronize(s);
       if (rr <= rtol * rtol * bb) break;
       vcycle(0, r, z, &d_rz);
-      FEP3M_CL k_cg_dir<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, p, z);
+      launch_pdl(k_cg_dir<T>, grid_for(n), TPB, 0, s, (int64_t)n, sc, p, z);
     }
     *relres = std::sqrt(rr / bb);
     return std::min(it, maxit);
@@ -1194,13 +1212,13 @@ struct MG {
     cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
     for (int it = 1; it <= k; ++it) {
       apply(L, p, EPI_Y, q, nullptr, nullptr, nullptr, T(0), T(0), T(0), &d_pq);
-      FEP3M_CL k_cg_update<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, x, r, p, q);
+      launch_pdl(k_cg_update<T>, grid_for(n), TPB, 0, s, (int64_t)n, sc, x, r, p, q);
       if (it == k) {
         reduce<T>(c, N, RD_NORM2, r, nullptr, sc + 3);
         break;
       }
       vcycle(0, r, z, &d_rz);
-      FEP3M_CL k_cg_dir<T><<<grid_for(n), TPB, 0, s>>>((int64_t)n, sc, p, z);
+      launch_pdl(k_cg_dir<T>, grid_for(n), TPB, 0, s, (int64_t)n, sc, p, z);
     }
     if (k <= 0) reduce<T>(c, N, RD_NORM2, r, nullptr, sc + 3);
   }
@@ -1383,13 +1401,11 @@ static cudaError_t refine_resid(Solver* c, const double* phi64, float* r) {
   const int steps = apply_steps(N);
   const ApplyDot nd = {nullptr, nullptr, nullptr, 0};
   if (c->precision == FEP3M_FP64) {
-    FEP3M_CL k_apply_el<double, EPI_RESID>
-        <<<apply_grid(N, steps), AT, sizeof(ApplySmem<double, EPI_RESID>), c->stream>>>(
+    launch_pdl(k_apply_el<double, EPI_RESID>, apply_grid(N, steps), AT, sizeof(ApplySmem<double, EPI_RESID>), c->stream, 
             N, steps, phi64, reinterpret_cast<double*>(r), c->res64, nullptr, nullptr, 0.0, 0.0, 0.0, c->scal, nd);
   } else {
     const dfv z = {0.0f, 0.0f};
-    FEP3M_CL k_apply_el<dfv, EPI_RESID>
-        <<<apply_grid(N, steps), AT, sizeof(ApplySmem<dfv, EPI_RESID>), c->stream>>>(
+    launch_pdl(k_apply_el<dfv, EPI_RESID>, apply_grid(N, steps), AT, sizeof(ApplySmem<dfv, EPI_RESID>), c->stream, 
             N, steps, reinterpret_cast<const dfv*>(c->phidf), reinterpret_cast<dfv*>(r),
             reinterpret_cast<const dfv*>(c->res64), nullptr, nullptr, z, z, z, c->scal, nd);
   }
@@ -1409,13 +1425,13 @@ static void refine_setup(Solver* c, const double* b, double* phi64, float* r) {
   const int bx = std::min(N, 256);
   const dim3 g3((N + bx - 1) / bx, N, N);
   if (c->precision == FEP3M_FP64) {
-    FEP3M_CL k_project_copy64<<<g3, bx, 0, s>>>(N, b, sc, c->res64);
+    launch_pdl(k_project_copy64, g3, bx, 0, s, N, b, sc, c->res64);
     cudaMemsetAsync(phi64, 0, n * sizeof(double), s);
-    FEP3M_CL k_round_scaled64<<<grid_for(n), TPB, 0, s>>>((int64_t)n, c->res64, r, sc);
+    launch_pdl(k_round_scaled64, grid_for(n), TPB, 0, s, (int64_t)n, c->res64, r, sc);
   } else {
-    FEP3M_CL k_split_df<<<g3, bx, 0, s>>>(N, b, sc, reinterpret_cast<dfv*>(c->res64));
+    launch_pdl(k_split_df, g3, bx, 0, s, N, b, sc, reinterpret_cast<dfv*>(c->res64));
     cudaMemsetAsync(c->phidf, 0, n * sizeof(dfv), s);
-    FEP3M_CL k_df_round_scaled<<<grid_for(n), TPB, 0, s>>>((int64_t)n, reinterpret_cast<const dfv*>(c->res64), r,
+    launch_pdl(k_df_round_scaled, grid_for(n), TPB, 0, s, (int64_t)n, reinterpret_cast<const dfv*>(c->res64), r,
                                                            sc);
   }
 }
@@ -1424,9 +1440,9 @@ static void refine_setup(Solver* c, const double* b, double* phi64, float* r) {
 static void refine_update(Solver* c, double* phi64, const float* e) {
   const size_t n = c->mg.lv[0].size;
   if (c->precision == FEP3M_FP64)
-    FEP3M_CL k_add_scaled<<<grid_for(n), TPB, 0, c->stream>>>((int64_t)n, phi64, e, c->scal);
+    launch_pdl(k_add_scaled, grid_for(n), TPB, 0, c->stream, (int64_t)n, phi64, e, c->scal);
   else
-    FEP3M_CL k_df_update<<<grid_for(n), TPB, 0, c->stream>>>((int64_t)n, reinterpret_cast<dfv*>(c->phidf), e,
+    launch_pdl(k_df_update, grid_for(n), TPB, 0, c->stream, (int64_t)n, reinterpret_cast<dfv*>(c->phidf), e,
                                                              c->scal);
 }
 
@@ -1437,7 +1453,7 @@ static void refine_finish(Solver* c, double* phi) {
   const size_t n = L0.size;
   const double W = (double)L0.n * L0.n * L0.n;
   if (c->precision != FEP3M_FP64)
-    FEP3M_CL k_df_to_double<<<grid_for(n), TPB, 0, c->stream>>>((int64_t)n, reinterpret_cast<const dfv*>(c->phidf),
+    launch_pdl(k_df_to_double, grid_for(n), TPB, 0, c->stream, (int64_t)n, reinterpret_cast<const dfv*>(c->phidf),
                                                                 phi);
   reduce<double>(c, N, RD_WSUM, phi, nullptr, c->scal + 6, POST_MEAN, 1.0 / W);
   project<double>(c, N, phi, 1);
