@@ -172,10 +172,48 @@ __global__ void k_load_vector(int n, const T* __restrict__ rv, double* __restric
 //   k_coarse_plane   one CTA per z plane: the x and y transforms in shared memory
 //   k_coarse_pencil  CP_PEN z pencils per CTA: z transform, Dinv, inverse z transform
 //   k_coarse_plane   the inverse x and y transforms
-constexpr int CP_MAX = 64, CP_PEN = 32;
+// Each thread computes 3 x 3 outputs of a transform (six shared loads per nine
+// multiply-adds); the CTA's 256 threads cover a 48 x 48 tile per round.
+constexpr int CP_MAX = 64, CP_PEN = 48;
+
+// out[r][c] = sum_k L[r][k] R[k][c] for r < nr, c < nc, k < K (shared
+// memory, row strides ls, rs); 3 x 3 register tiles, rounds of 48 x 48
+template <class T, class Store>
+__device__ __forceinline__ void cp_matmul(int nr, int nc, int K, const T* L, int ls, const T* R, int rs, Store st) {
+  const int t3r = threadIdx.x >> 4, t3c = threadIdx.x & 15;
+  for (int r0 = 0; r0 < nr; r0 += 48)
+    for (int c0 = 0; c0 < nc; c0 += 48) {
+      const int r = r0 + 3 * t3r, c = c0 + 3 * t3c;
+      T acc[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) acc[i][j] = T(0);
+      // rows / columns past the edge read row or column 0 and are not stored
+      const int ri[3] = {r < nr ? r : 0, r + 1 < nr ? r + 1 : 0, r + 2 < nr ? r + 2 : 0};
+      const int ci[3] = {c < nc ? c : 0, c + 1 < nc ? c + 1 : 0, c + 2 < nc ? c + 2 : 0};
+      for (int k = 0; k < K; ++k) {
+        T l[3], rr[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          l[i] = L[ri[i] * ls + k];
+          rr[i] = R[k * rs + ci[i]];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) acc[i][j] += l[i] * rr[j];
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          if (r + i < nr && c + j < nc) st(r + i, c + j, acc[i][j]);
+    }
+}
 
 // out[z][r'][r] = sum_{j,k} A[r'][j] A[r][k] in[z][j][k] (A row r = output r);
-// dynamic shared memory (3 N (N + 1)) elements; grid N
+// dynamic shared memory 3 N (N + 1) elements; grid N, 256 threads
 template <class T>
 __global__ void __launch_bounds__(256) k_coarse_plane(int N, const T* __restrict__ A, const T* __restrict__ in,
                                                       T* __restrict__ out) {
@@ -192,40 +230,58 @@ __global__ void __launch_bounds__(256) k_coarse_plane(int N, const T* __restrict
     X[r * P + k] = in[base + i];
   }
   __syncthreads();
-  // x transform: Y[y][r] = sum_k A[r][k] X[y][k]
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-    const int y = i / N, r = i - y * N;
-    const T* a = As + r * P;
-    const T* xr = X + y * P;
-    T acc = T(0);
-    for (int k = 0; k < N; ++k) acc += a[k] * xr[k];
-    Y[y * P + r] = acc;
+  // x transform: Y[y][r] = sum_k X[y][k] A[r][k]  (L = X, R = A^T: R[k][r] = As[r P + k])
+  {
+    const int t3r = threadIdx.x >> 4, t3c = threadIdx.x & 15;
+    for (int r0 = 0; r0 < N; r0 += 48)
+      for (int c0 = 0; c0 < N; c0 += 48) {
+        const int y = r0 + 3 * t3r, rr0 = c0 + 3 * t3c;
+        T acc[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) acc[i][j] = T(0);
+        const int yi[3] = {y < N ? y : 0, y + 1 < N ? y + 1 : 0, y + 2 < N ? y + 2 : 0};
+        const int ri[3] = {rr0 < N ? rr0 : 0, rr0 + 1 < N ? rr0 + 1 : 0, rr0 + 2 < N ? rr0 + 2 : 0};
+        for (int k = 0; k < N; ++k) {
+          T xv[3], av[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            xv[i] = X[yi[i] * P + k];
+            av[i] = As[ri[i] * P + k];
+          }
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) acc[i][j] += xv[i] * av[j];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            if (y + i < N && rr0 + j < N) Y[(y + i) * P + rr0 + j] = acc[i][j];
+      }
   }
   __syncthreads();
   // y transform: out[r'][x] = sum_k A[r'][k] Y[k][x]
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-    const int rp = i / N, x = i - rp * N;
-    const T* a = As + rp * P;
-    T acc = T(0);
-    for (int k = 0; k < N; ++k) acc += a[k] * Y[k * P + x];
-    out[base + i] = acc;
-  }
+  cp_matmul<T>(N, N, N, As, P, Y, P,
+               [&](int rp, int x, T v) { out[base + (int64_t)rp * N + x] = v; });
 }
 
 // for the CP_PEN pencils q = x + N y starting at blockIdx.x CP_PEN:
 //   u[z'] = sum_z VT[z'][z] in[z][q];  u[z'] *= Dinv[z'][q];  out[z][q] = sum_z' V[z][z'] u[z']
-// dynamic shared memory (2 N (N + 1) + 2 CP_PEN (N + 1)) elements; grid ceil(N^2 / CP_PEN)
+// dynamic shared memory (2 N (N + 1) + 2 N (CP_PEN + 1)) elements; grid ceil(N^2 / CP_PEN)
 template <class T>
 __global__ void __launch_bounds__(256) k_coarse_pencil(int N, const T* __restrict__ VT, const T* __restrict__ V,
                                                        const T* __restrict__ Dinv, const T* __restrict__ in,
                                                        T* __restrict__ out) {
   PDL_PROLOGUE
   extern __shared__ __align__(16) unsigned char cpsm[];
-  const int P = N + 1;
+  const int P = N + 1, Q = CP_PEN + 1;
   T* VTs = (T*)cpsm;
   T* Vs = VTs + N * P;
-  T* U = Vs + N * P;          // [pencil][z]
-  T* W = U + CP_PEN * P;      // [pencil][z']
+  T* U = Vs + N * P;          // [z][pencil]
+  T* W = U + N * Q;           // [z'][pencil]
   const int64_t NN = (int64_t)N * N;
   const int64_t q0 = (int64_t)blockIdx.x * CP_PEN;
   const int np = (int)min((int64_t)CP_PEN, NN - q0);
@@ -236,27 +292,14 @@ __global__ void __launch_bounds__(256) k_coarse_pencil(int N, const T* __restric
   }
   for (int i = threadIdx.x; i < CP_PEN * N; i += blockDim.x) {
     const int z = i / CP_PEN, p = i - z * CP_PEN;
-    U[p * P + z] = p < np ? in[z * NN + q0 + p] : T(0);
+    U[z * Q + p] = p < np ? in[z * NN + q0 + p] : T(0);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < CP_PEN * N; i += blockDim.x) {
-    const int zp = i / CP_PEN, p = i - zp * CP_PEN;
-    const T* a = VTs + zp * P;
-    const T* u = U + p * P;
-    T acc = T(0);
-    for (int k = 0; k < N; ++k) acc += a[k] * u[k];
-    W[p * P + zp] = p < np ? acc * Dinv[zp * NN + q0 + p] : T(0);
-  }
+  // W[z'][p] = Dinv[z'][q0 + p] sum_z VT[z'][z] U[z][p]
+  cp_matmul<T>(N, np, N, VTs, P, U, Q, [&](int zp, int p, T v) { W[zp * Q + p] = v * Dinv[zp * NN + q0 + p]; });
   __syncthreads();
-  for (int i = threadIdx.x; i < CP_PEN * N; i += blockDim.x) {
-    const int z = i / CP_PEN, p = i - z * CP_PEN;
-    if (p >= np) continue;
-    const T* a = Vs + z * P;
-    const T* w = W + p * P;
-    T acc = T(0);
-    for (int k = 0; k < N; ++k) acc += a[k] * w[k];
-    out[z * NN + q0 + p] = acc;
-  }
+  // out[z][q0 + p] = sum_z' V[z][z'] W[z'][p]
+  cp_matmul<T>(N, np, N, Vs, P, W, Q, [&](int z, int p, T v) { out[z * NN + q0 + p] = v; });
 }
 
 // ------------------------------------------------------------ operator apply
@@ -678,7 +721,7 @@ static cudaError_t apply_set_smem() {
   if (e == cudaSuccess) e = apply_set_smem_one<dfv, EPI_RESID>();
   // coarsest-level kernels at N = CP_MAX
   const int smp = 3 * CP_MAX * (CP_MAX + 1) * (int)sizeof(float);
-  const int smq = (2 * CP_MAX * (CP_MAX + 1) + 2 * CP_PEN * (CP_MAX + 1)) * (int)sizeof(float);
+  const int smq = (2 * CP_MAX * (CP_MAX + 1) + 2 * CP_MAX * (CP_PEN + 1)) * (int)sizeof(float);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_coarse_plane<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smp);
   if (e == cudaSuccess)
@@ -1108,7 +1151,7 @@ struct MG {
     T* w2 = (T*)L.t2;
     if (N <= CP_MAX) {
       const size_t smp = (size_t)3 * N * (N + 1) * sizeof(T);
-      const size_t smq = ((size_t)2 * N * (N + 1) + (size_t)2 * CP_PEN * (N + 1)) * sizeof(T);
+      const size_t smq = ((size_t)2 * N * (N + 1) + (size_t)2 * N * (CP_PEN + 1)) * sizeof(T);
       const unsigned gq = (unsigned)(((int64_t)N * N + CP_PEN - 1) / CP_PEN);
       launch_pdl(k_coarse_plane<T>, N, 256, smp, s, N, VT, b, w1);
       launch_pdl(k_coarse_pencil<T>, gq, 256, smq, s, N, VT, V, Dinv, w1, w2);
