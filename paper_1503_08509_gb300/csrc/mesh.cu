@@ -757,11 +757,12 @@ __global__ void k_cheb0(int N, const T* __restrict__ b, T* __restrict__ d, T* __
 
 // ------------------------------------------------------- grid transfers
 // restriction along one axis (transpose of the 1-D prolongation): the input
-// has 2 Nc nodes along `axis`, the output Nc; output extents (e0, e1, e2) in
-// (x, y, z); grid (ceil(e0 / blockDim.x), e1, e2)
-template <class T>
-__global__ void k_restrict_axis(int axis, int Nc, int e0, int e1, int e2, const T* __restrict__ in,
-                                T* __restrict__ out, T scale) {
+// has 2 Nc nodes along `axis` (a template argument, so the index arrays stay
+// in registers), the output Nc; output extents (e0, e1, e2) in (x, y, z);
+// grid (ceil(e0 / blockDim.x), e1, e2)
+template <class T, int axis>
+__global__ void k_restrict_axis(int Nc, int e0, int e1, int e2, const T* __restrict__ in, T* __restrict__ out,
+                                T scale) {
   PDL_PROLOGUE
   // the row of P depends on the lane: read it from shared memory, not from
   // the constant bank (which serialises lanes that read different addresses)
@@ -794,9 +795,9 @@ __global__ void k_restrict_axis(int axis, int Nc, int e0, int e1, int e2, const 
 
 // prolongation along one axis: output has 2 Nc nodes along axis, extents
 // (e0, e1, e2); ADD: out = add + P in; grid (ceil(e0 / blockDim.x), e1, e2)
-template <class T, bool ADD>
-__global__ void k_prolong_axis(int axis, int Nc, int e0, int e1, int e2, const T* __restrict__ in,
-                               T* __restrict__ out, const T* __restrict__ add) {
+template <class T, int axis, bool ADD>
+__global__ void k_prolong_axis(int Nc, int e0, int e1, int e2, const T* __restrict__ in, T* __restrict__ out,
+                               const T* __restrict__ add) {
   PDL_PROLOGUE
   __shared__ T Ps[6][4];
   if (threadIdx.x < 24) Ps[threadIdx.x / 4][threadIdx.x % 4] = Cst<T>::P(threadIdx.x / 4, threadIdx.x % 4);
@@ -1185,13 +1186,13 @@ struct MG {
     T* s1 = (T*)L.t1;
     T* s2 = (T*)L.t2;
     auto g3 = [](int e0, int e1, int e2) { return dim3((e0 + 127) / 128, e1, e2); };
-    launch_pdl(k_restrict_axis<T>, g3(Nc, Nf, Nf), 128, 0, s, 0, Nc, Nc, Nf, Nf, (T*)L.r, s1, T(1));
-    launch_pdl(k_restrict_axis<T>, g3(Nc, Nc, Nf), 128, 0, s, 1, Nc, Nc, Nc, Nf, s1, s2, T(1));
-    launch_pdl(k_restrict_axis<T>, g3(Nc, Nc, Nc), 128, 0, s, 2, Nc, Nc, Nc, Nc, s2, (T*)Cl.b, T(0.5));
+    launch_pdl(k_restrict_axis<T, 0>, g3(Nc, Nf, Nf), 128, 0, s, Nc, Nc, Nf, Nf, (T*)L.r, s1, T(1));
+    launch_pdl(k_restrict_axis<T, 1>, g3(Nc, Nc, Nf), 128, 0, s, Nc, Nc, Nc, Nf, s1, s2, T(1));
+    launch_pdl(k_restrict_axis<T, 2>, g3(Nc, Nc, Nc), 128, 0, s, Nc, Nc, Nc, Nc, s2, (T*)Cl.b, T(0.5));
     vcycle(l + 1, (T*)Cl.b, (T*)Cl.x);
-    launch_pdl(k_prolong_axis<T, false>, g3(Nc, Nc, Nf), 128, 0, s, 2, Nc, Nc, Nc, Nf, (T*)Cl.x, s1, nullptr);
-    launch_pdl(k_prolong_axis<T, false>, g3(Nc, Nf, Nf), 128, 0, s, 1, Nc, Nc, Nf, Nf, s1, s2, nullptr);
-    launch_pdl(k_prolong_axis<T, true>, g3(Nf, Nf, Nf), 128, 0, s, 0, Nc, Nf, Nf, Nf, s2, (T*)L.a, x);
+    launch_pdl(k_prolong_axis<T, 2, false>, g3(Nc, Nc, Nf), 128, 0, s, Nc, Nc, Nc, Nf, (T*)Cl.x, s1, nullptr);
+    launch_pdl(k_prolong_axis<T, 1, false>, g3(Nc, Nf, Nf), 128, 0, s, Nc, Nc, Nf, Nf, s1, s2, nullptr);
+    launch_pdl(k_prolong_axis<T, 0, true>, g3(Nf, Nf, Nf), 128, 0, s, Nc, Nf, Nf, Nf, s2, (T*)L.a, x);
     smooth(L, x, b, false, H.cheb_degree, dot);   // starts from L.a = x + P e
   }
 
