@@ -256,23 +256,32 @@ def run_ours(args):
         acc["mixed_vs_fp64"] = dict(phi_rel_rms=rel_rms(results["mixed"]["phi"], results["fp64"]["phi"]),
                                     force_rel_rms=rel_rms(results["mixed"]["F"], results["fp64"]["F"]))
 
-    # roofline of the dominant hot-path kernel: the short-range pair kernel (FP32 FMA bound)
+    # roofline of the hot-path kernel the method is built around: the short-range pair kernel (FP32 issue bound).
+    # achieved = flops it executes (vertex-regrouped screen GEMM, field evaluation, singular pairs) / its
+    # CUDA-event time; SURVEY 8(d)'s element-to-point counts are reported beside it.
     st = main["stats"]
     ne_nonempty = st["nonempty_elements"]
     pairs = st["singular_pairs"]
     flops = ne_nonempty * 512 * 64 * 2 + N * 64 * 2 * 4 + pairs * 20
+    flops_elem = st["screen_element_pairs"] * 1024 + N * 128 + pairs * 20
+    flops_charge = st["screen_charge_pairs"] * 1024 + N * 128 + pairs * 20
     pair_ms = statistics.mean(main["pair"])
     achieved = flops / (pair_ms * 1e-3) / 1e12
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
-    roof = {"kernel": "k_pair_fwd (short-range pair + screen field + smooth evaluation)", "bound": "alu",
-            "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+    roof = {"kernel": "k_pair_brick3 (screen field GEMM + smooth/screen evaluation + singular pairs, with gradients)",
+            "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4), "traffic": None,
             "peak_note": "FP32 FMA peak derived: %d SMs x 128 lanes x 2 flops x %.0f MHz (max SM clock)"
                          % (props.multi_processor_count, sm_max),
-            "flops_per_launch": flops, "ms_per_launch": round(pair_ms, 4)}
+            "flops_per_launch": flops, "ms_per_launch": round(pair_ms, 4),
+            "element_to_point_count": {
+                "per_target_element": {"flops": flops_elem,
+                                       "frac": round(flops_elem / (pair_ms * 1e-3) / 1e12 / peak, 4)},
+                "per_target_charge": {"flops": flops_charge,
+                                      "frac": round(flops_charge / (pair_ms * 1e-3) / 1e12 / peak, 4)}}}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "particles/s", "n_gpus": ws, "steps": args.steps,

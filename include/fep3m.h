@@ -96,6 +96,11 @@ typedef struct {
                                covers the short-range pair kernel launch alone   */
   int64_t kernel_launches;  /* CUDA kernels launched by this library in this
                                process so far (all contexts)                     */
+  int64_t screen_element_pairs;  /* (non-empty element, non-empty element of its
+                               block) pairs: the units of the element-to-point
+                               screen sums of Sec. 3.1.2 per target element      */
+  int64_t screen_charge_pairs;   /* (charge, non-empty element of its block) pairs:
+                               the same per target charge                        */
 } fep3m_stats;
 
 /* Create a context: validates cfg, builds the FE basis-screen table (a

@@ -24,7 +24,8 @@ class Stats(ctypes.Structure):
                 ("singular_pairs", ctypes.c_int64), ("nonempty_elements", ctypes.c_int64),
                 ("max_per_element", ctypes.c_int), ("ms_bin", ctypes.c_double), ("ms_assemble", ctypes.c_double),
                 ("ms_solve", ctypes.c_double), ("ms_pair", ctypes.c_double), ("ms_adjoint", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("screen_element_pairs", ctypes.c_int64),
+                ("screen_charge_pairs", ctypes.c_int64)]
 
 
 P = ctypes.c_void_p

@@ -331,9 +331,9 @@ int fep3m_set_particles(fep3m_ctx* c, int64_t N, const double* pos, const double
   ev_record(c, 7);
   CK(pair_counts(c, (unsigned long long*)(c->scal + 48)));
   double sums[2];
-  unsigned long long cnt3[3];
+  unsigned long long cnt3[5];
   int flag = 0;
-  CK(cudaMemcpyAsync(cnt3, c->scal + 48, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(cnt3, c->scal + 48, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(sums, c->scal + 32, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(&flag, c->iflags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -342,6 +342,8 @@ int fep3m_set_particles(fep3m_ctx* c, int64_t N, const double* pos, const double
   c->stats.singular_pairs = (int64_t)cnt3[0];
   c->stats.nonempty_elements = (int64_t)cnt3[1];
   c->stats.max_per_element = (int)cnt3[2];
+  c->stats.screen_element_pairs = (int64_t)cnt3[3];
+  c->stats.screen_charge_pairs = (int64_t)cnt3[4];
   if (flag) return FEP3M_EINVAL;
   if (!(c->cfg.flags & FEP3M_NEUTRALIZE) && std::fabs(sums[0]) > 1e-12 * sums[1]) return FEP3M_ENOTNEUTRAL;
   c->have_particles = true;

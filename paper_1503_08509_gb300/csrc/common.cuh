@@ -231,7 +231,7 @@ cudaError_t mesh_solve_begin(Solver* s, const double* b, double* phi);
 cudaError_t mesh_solve_end(Solver* s);
 cudaError_t mesh_solve(Solver* s, const double* b, double* phi);
 cudaError_t pair_prepare(fep3m_ctx* c);
-cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev3);
+cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev5);
 cudaError_t pair_forward(fep3m_ctx* c, double* phi_out, int want_grad);
 // adjoint in three parts: weights and deposit (-> g64), the parts that need
 // lam (vertex adjoint, screen sweep, singular adjoint), and the per-charge assembly

@@ -830,26 +830,35 @@ cudaError_t pair_prepare(fep3m_ctx* c) {
 }
 
 // ordered singular pairs, non-empty elements and the largest element population
+// per non-empty element e with c0 charges and s charges in its block (nb
+// non-empty block elements): singular pairs c0 s - c0, one non-empty element,
+// the largest c0, nb (element pairs of the screen contraction) and c0 nb
+// (charge-element pairs)
 __global__ void k_pair_count(int n, int n_sr, const int* __restrict__ count, unsigned long long* __restrict__ out) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= (int64_t)n * n * n) return;
   const int c0 = count[e];
   if (c0 == 0) return;
   const int ex = (int)(e % n), ey = (int)((e / n) % n), ez = (int)(e / ((int64_t)n * n));
-  long long s = 0;
+  long long s = 0, nb = 0;
   for (int dz = -n_sr; dz <= n_sr; ++dz)
     for (int dy = -n_sr; dy <= n_sr; ++dy)
-      for (int dx = -n_sr; dx <= n_sr; ++dx)
-        s += count[wrapn(ex + dx, n) + (int64_t)n * (wrapn(ey + dy, n) + (int64_t)n * wrapn(ez + dz, n))];
+      for (int dx = -n_sr; dx <= n_sr; ++dx) {
+        const int cj = count[wrapn(ex + dx, n) + (int64_t)n * (wrapn(ey + dy, n) + (int64_t)n * wrapn(ez + dz, n))];
+        s += cj;
+        nb += cj > 0;
+      }
   atomicAdd(&out[0], (unsigned long long)((long long)c0 * s - c0));
   atomicAdd(&out[1], 1ull);
   atomicMax(&out[2], (unsigned long long)c0);
+  atomicAdd(&out[3], (unsigned long long)nb);
+  atomicAdd(&out[4], (unsigned long long)((long long)c0 * nb));
 }
 
-cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev3) {
+cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev5) {
   const int64_t ne = (int64_t)c->n * c->n * c->n;
-  cudaMemsetAsync(dev3, 0, 3 * sizeof(unsigned long long), c->stream);
-  FEP3M_CL k_pair_count<<<gsz(ne), PT, 0, c->stream>>>(c->n, c->n_sr, c->count, dev3);
+  cudaMemsetAsync(dev5, 0, 5 * sizeof(unsigned long long), c->stream);
+  FEP3M_CL k_pair_count<<<gsz(ne), PT, 0, c->stream>>>(c->n, c->n_sr, c->count, dev5);
   return cudaGetLastError();
 }
 
