@@ -824,6 +824,199 @@ __global__ void k_prolong_axis(int Nc, int e0, int e1, int e2, const T* __restri
   else out[g] = acc;
 }
 
+// ---------------------------------------------- fused grid transfers (3-D)
+// Restriction (transpose of the prolongation, scaled) and prolongation in one
+// launch each.  A CTA owns RX x RY coarse elements in x and y and marches one
+// coarse element (three coarse planes, six fine planes) at a time in z; the x
+// and y passes of each plane run in shared memory, the z weights in registers.
+// 1-D rules, coarse node 3E + j, fine node 6E + s (P the 1-D prolongation):
+//   restrict:  c[3E + j] = sum_{s=1..5} P[s][j] f[6E + s]  (j = 1, 2)
+//              c[3E]     = f[6E] + sum_{s=1..5} (P[s][0] f[6E + s] + P[s][3] f[6E - 6 + s])
+//   prolong:   f[6E + s] = sum_{j=0..3} P[s][j] c[3E + j]   (3E + 3 wraps)
+constexpr int RX = 4, RY = 4;                       // coarse elements per tile
+constexpr int RCX = 3 * RX, RCY = 3 * RY;           // coarse nodes per tile
+constexpr int RFX = 6 * RX + 5, RFY = 6 * RY + 5;   // fine halo tile of a restriction plane
+constexpr int RT = 160;                             // threads (>= RCX * RCY)
+constexpr int RNF = RFX * RFY, RPL = (RNF + RT - 1) / RT;
+static_assert(RCX * RCY <= RT, "one coarse column per thread");
+
+__device__ __forceinline__ int wrap_mod(int v, int n) { return ((v % n) + n) % n; }
+
+// grid (ceil(nc / RX), ceil(nc / RY), ceil(nc / steps)), RT threads; Nf = 2 Nc, Nc = 3 nc
+template <class T>
+__global__ void __launch_bounds__(RT) k_restrict3(int Nf, int steps, const T* __restrict__ in, T* __restrict__ out,
+                                                  T scale) {
+  PDL_PROLOGUE
+  __shared__ T F[RFY][RFX];      // one fine plane of the tile (halo 5 below)
+  __shared__ T Xt[RCX][RFY];     // after the x pass, coarse x major
+  __shared__ T Ps[6][4];
+  const int Nc = Nf / 2, nc = Nc / 3;
+  const int64_t NNf = (int64_t)Nf * Nf, NNc = (int64_t)Nc * Nc;
+  const int X0 = blockIdx.x * RX, Y0 = blockIdx.y * RY;
+  const int E0 = blockIdx.z * steps, E1 = min(nc, E0 + steps);
+  const int tid = threadIdx.x;
+  if (tid < 24) Ps[tid / 4][tid % 4] = Cst<T>::P(tid / 4, tid % 4);
+  int foff[RPL];
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    const int i = tid + k * RT;
+    const int row = i / RFX, col = i - row * RFX;
+    foff[k] = i < RNF ? wrap_mod(6 * Y0 - 5 + row, Nf) * Nf + wrap_mod(6 * X0 - 5 + col, Nf) : 0;
+  }
+  // this thread's coarse column
+  const int cy = tid / RCX, cx = tid - cy * RCX;
+  const bool col_on = tid < RCX * RCY && X0 + cx / 3 < nc && Y0 + cy / 3 < nc;
+  const int64_t gcol = (int64_t)(3 * Y0 + cy) * Nc + 3 * X0 + cx;
+  T acc_v = T(0), acc_1 = T(0), acc_2 = T(0), acc_n = T(0);
+  for (int f = 6 * E0 - 5; f < 6 * E1; ++f) {
+    const int fz = f < 0 ? f + Nf : (f >= Nf ? f - Nf : f);
+    const T* src = in + fz * NNf;
+    __syncthreads();   // the previous plane's x pass is done with F
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      const int i = tid + k * RT;
+      if (i < RNF) (&F[0][0])[i] = src[foff[k]];
+    }
+    __syncthreads();
+    // x pass: item w = (coarse x, fine row), rows fastest (conflict-free reads of F)
+    for (int w = tid; w < RCX * RFY; w += RT) {
+      const int c = w / RFY, row = w - c * RFY;
+      const int Ex = c / 3, j = c - 3 * Ex;
+      const T* fr = &F[row][6 * Ex + 5];
+      T a = T(0);
+#pragma unroll
+      for (int s = 1; s < 6; ++s) a += Ps[s][j] * fr[s];
+      if (j == 0) {
+        a += fr[0];
+#pragma unroll
+        for (int s = 1; s < 6; ++s) a += Ps[s][3] * fr[s - 6];
+      }
+      Xt[c][row] = a;
+    }
+    __syncthreads();
+    // y pass of this thread's column, then the z weights of fine plane f = 6 Ez + sz
+    if (tid < RCX * RCY) {
+      const int Ey = cy / 3, jy = cy - 3 * Ey;
+      const T* xr = &Xt[cx][6 * Ey + 5];
+      T v = T(0);
+#pragma unroll
+      for (int s = 1; s < 6; ++s) v += Ps[s][jy] * xr[s];
+      if (jy == 0) {
+        v += xr[0];
+#pragma unroll
+        for (int s = 1; s < 6; ++s) v += Ps[s][3] * xr[s - 6];
+      }
+      const int Ez = (f + 6) / 6 - 1, sz = f - 6 * Ez;   // f >= -5
+      if (Ez < E0) {
+        acc_v += Ps[sz][3] * v;                           // element E0 - 1: vertex of E0
+      } else if (sz == 0) {
+        acc_v += v;
+      } else {
+        acc_v += Ps[sz][0] * v;
+        acc_1 += Ps[sz][1] * v;
+        acc_2 += Ps[sz][2] * v;
+        acc_n += Ps[sz][3] * v;
+      }
+      if (sz == 5 && Ez >= E0) {                          // element Ez complete
+        if (col_on) {
+          out[(3 * Ez) * NNc + gcol] = scale * acc_v;
+          out[(3 * Ez + 1) * NNc + gcol] = scale * acc_1;
+          out[(3 * Ez + 2) * NNc + gcol] = scale * acc_2;
+        }
+        acc_v = acc_n;
+        acc_1 = acc_2 = acc_n = T(0);
+      }
+    }
+  }
+}
+
+// fine = add + P c.  grid (ceil(nc / RX), ceil(nc / RY), ceil(nc / steps)), PTH threads
+constexpr int PFX = 6 * RX, PFY = 6 * RY;           // fine nodes per tile
+constexpr int PCX = 3 * RX + 1, PCY = 3 * RY + 1;   // coarse nodes of a tile plane (with the next vertex)
+constexpr int PTH = 192;
+constexpr int PPT = (PFX * PFY + PTH - 1) / PTH;    // fine columns per thread
+template <class T>
+__global__ void __launch_bounds__(PTH) k_prolong3(int Nf, int steps, const T* __restrict__ in,
+                                                  T* __restrict__ out, const T* __restrict__ add) {
+  PDL_PROLOGUE
+  __shared__ T Cc[PCY][PCX];          // one coarse plane of the tile
+  __shared__ T Xp[PCY][PFX];          // after the x pass
+  __shared__ T Yp[4][PFY][PFX];       // prolonged coarse planes 3E .. 3E + 3 (ring)
+  __shared__ T Ps[6][4];
+  const int Nc = Nf / 2, nc = Nc / 3;
+  const int64_t NNf = (int64_t)Nf * Nf, NNc = (int64_t)Nc * Nc;
+  const int X0 = blockIdx.x * RX, Y0 = blockIdx.y * RY;
+  const int E0 = blockIdx.z * steps, E1 = min(nc, E0 + steps);
+  const int tid = threadIdx.x;
+  if (tid < 24) Ps[tid / 4][tid % 4] = Cst<T>::P(tid / 4, tid % 4);
+  // coarse tile offsets (x, y wrapped), one per thread
+  const int ci_r = tid / PCX, ci_c = tid - ci_r * PCX;
+  const bool ci_on = tid < PCX * PCY;
+  const int64_t coff = ci_on ? (int64_t)((3 * Y0 + ci_r) % Nc) * Nc + (3 * X0 + ci_c) % Nc : 0;
+  // this thread's fine columns
+  int64_t fo[PPT];
+  bool fon[PPT];
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int i = tid + k * PTH;
+    const int fy = i / PFX, fx = i - fy * PFX;
+    fon[k] = i < PFX * PFY && X0 + fx / 6 < nc && Y0 + fy / 6 < nc;
+    fo[k] = fon[k] ? (int64_t)(6 * Y0 + fy) * Nf + 6 * X0 + fx : 0;
+  }
+  // the x and y passes of coarse plane cz into ring slot r
+  auto plane2d = [&](int cz, int r) {
+    __syncthreads();   // Cc and Xp are free
+    if (ci_on) Cc[ci_r][ci_c] = in[(int64_t)cz * NNc + coff];
+    __syncthreads();
+    for (int w = tid; w < PCY * PFX; w += PTH) {
+      const int row = w / PFX, fx = w - row * PFX;
+      const int Ex = fx / 6, sx = fx - 6 * Ex;
+      T a = T(0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a += Ps[sx][j] * Cc[row][3 * Ex + j];
+      Xp[row][fx] = a;
+    }
+    __syncthreads();
+    for (int w = tid; w < PFY * PFX; w += PTH) {
+      const int fy = w / PFX, fx = w - fy * PFX;
+      const int Ey = fy / 6, sy = fy - 6 * Ey;
+      T a = T(0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a += Ps[sy][j] * Xp[3 * Ey + j][fx];
+      Yp[r][fy][fx] = a;
+    }
+  };
+  plane2d(3 * E0, 0);
+  for (int E = E0; E < E1; ++E) {
+    const int r0 = (3 * (E - E0)) & 3;   // ring slot of plane 3E
+    for (int j = 1; j < 4; ++j) {
+      int cz = 3 * E + j;
+      if (cz >= Nc) cz -= Nc;
+      plane2d(cz, (r0 + j) & 3);
+    }
+    __syncthreads();
+    for (int s = 0; s < 6; ++s) {
+      const int64_t zb = (int64_t)(6 * E + s) * NNf;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const int i = tid + k * PTH;
+        if (!fon[k]) continue;
+        const int fy = i / PFX, fx = i - fy * PFX;
+        T a = T(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a += Ps[s][j] * Yp[(r0 + j) & 3][fy][fx];
+        out[zb + fo[k]] = add[zb + fo[k]] + a;
+      }
+    }
+  }
+}
+
+// coarse elements per CTA in z for the fused transfers (nc coarse elements per axis)
+static inline int transfer_steps(int nc) {
+  const int64_t cols = (int64_t)((nc + RX - 1) / RX) * ((nc + RY - 1) / RY);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(8, cols * nc / (152 * 4)));
+}
+
 // dense 1-D transform along an axis: out[.. i ..] = sum_k A[i][k] in[.. k ..]
 // (A = V^T when transpose), optionally scaled elementwise by s after.
 template <class T>
@@ -1181,18 +1374,13 @@ struct MG {
     cudaStream_t s = c->stream;
     smooth(L, x, b, true, H.cheb_degree);
     apply(L, x, EPI_RESID, (T*)L.r, b, nullptr, nullptr, T(0), T(0));
-    // restrict r: x-axis, y-axis, z-axis (the last scales by 1/2: reference-unit Galerkin)
-    const int Nc = Cl.N, Nf = L.N;
-    T* s1 = (T*)L.t1;
-    T* s2 = (T*)L.t2;
-    auto g3 = [](int e0, int e1, int e2) { return dim3((e0 + 127) / 128, e1, e2); };
-    launch_pdl(k_restrict_axis<T, 0>, g3(Nc, Nf, Nf), 128, 0, s, Nc, Nc, Nf, Nf, (T*)L.r, s1, T(1));
-    launch_pdl(k_restrict_axis<T, 1>, g3(Nc, Nc, Nf), 128, 0, s, Nc, Nc, Nc, Nf, s1, s2, T(1));
-    launch_pdl(k_restrict_axis<T, 2>, g3(Nc, Nc, Nc), 128, 0, s, Nc, Nc, Nc, Nc, s2, (T*)Cl.b, T(0.5));
+    // restrict r (scaled by 1/2: reference-unit Galerkin), coarse cycle, prolong and add
+    const int Nf = L.N, nc = Cl.n;
+    const int ts = transfer_steps(nc);
+    const dim3 gt((nc + RX - 1) / RX, (nc + RY - 1) / RY, (nc + ts - 1) / ts);
+    launch_pdl(k_restrict3<T>, gt, RT, 0, s, Nf, ts, (const T*)L.r, (T*)Cl.b, T(0.5));
     vcycle(l + 1, (T*)Cl.b, (T*)Cl.x);
-    launch_pdl(k_prolong_axis<T, 2, false>, g3(Nc, Nc, Nf), 128, 0, s, Nc, Nc, Nc, Nf, (T*)Cl.x, s1, nullptr);
-    launch_pdl(k_prolong_axis<T, 1, false>, g3(Nc, Nf, Nf), 128, 0, s, Nc, Nc, Nf, Nf, s1, s2, nullptr);
-    launch_pdl(k_prolong_axis<T, 0, true>, g3(Nf, Nf, Nf), 128, 0, s, Nc, Nf, Nf, Nf, s2, (T*)L.a, x);
+    launch_pdl(k_prolong3<T>, gt, PTH, 0, s, Nf, ts, (const T*)Cl.x, (T*)L.a, (const T*)x);
     smooth(L, x, b, false, H.cheb_degree, dot);   // starts from L.a = x + P e
   }
 
