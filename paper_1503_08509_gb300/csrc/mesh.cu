@@ -836,7 +836,7 @@ __global__ void k_prolong_axis(int Nc, int e0, int e1, int e2, const T* __restri
 constexpr int RX = 4, RY = 4;                       // coarse elements per tile
 constexpr int RCX = 3 * RX, RCY = 3 * RY;           // coarse nodes per tile
 constexpr int RFX = 6 * RX + 5, RFY = 6 * RY + 5;   // fine halo tile of a restriction plane
-constexpr int RT = 160;                             // threads (>= RCX * RCY)
+constexpr int RT = 256;                             // threads (>= RCX * RCY)
 constexpr int RNF = RFX * RFY, RPL = (RNF + RT - 1) / RT;
 static_assert(RCX * RCY <= RT, "one coarse column per thread");
 
@@ -868,15 +868,23 @@ __global__ void __launch_bounds__(RT) k_restrict3(int Nf, int steps, const T* __
   const bool col_on = tid < RCX * RCY && X0 + cx / 3 < nc && Y0 + cy / 3 < nc;
   const int64_t gcol = (int64_t)(3 * Y0 + cy) * Nc + 3 * X0 + cx;
   T acc_v = T(0), acc_1 = T(0), acc_2 = T(0), acc_n = T(0);
-  for (int f = 6 * E0 - 5; f < 6 * E1; ++f) {
+  // the next fine plane is fetched into registers while the current one is reduced
+  T pf[RPL];
+  auto fetch = [&](int f) {
     const int fz = f < 0 ? f + Nf : (f >= Nf ? f - Nf : f);
     const T* src = in + fz * NNf;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) pf[k] = src[foff[k]];
+  };
+  fetch(6 * E0 - 5);
+  for (int f = 6 * E0 - 5; f < 6 * E1; ++f) {
     __syncthreads();   // the previous plane's x pass is done with F
 #pragma unroll
     for (int k = 0; k < RPL; ++k) {
       const int i = tid + k * RT;
-      if (i < RNF) (&F[0][0])[i] = src[foff[k]];
+      if (i < RNF) (&F[0][0])[i] = pf[k];
     }
+    if (f + 1 < 6 * E1) fetch(f + 1);
     __syncthreads();
     // x pass: item w = (coarse x, fine row), rows fastest (conflict-free reads of F)
     for (int w = tid; w < RCX * RFY; w += RT) {
