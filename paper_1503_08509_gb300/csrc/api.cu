@@ -63,8 +63,12 @@ __global__ void k_to_double(int64_t n, const A* in, double* out, double a) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) out[i] = (double)in[i] * a;
 }
-__global__ void k_charge_sums(int64_t N, const double* Q, double* out /* [0] sum, [1] sum |Q| */) {
+// sum Q and sum |Q| (the neutrality check): per-block partials, the last
+// block to finish adds them in block order (deterministic)
+__global__ void k_charge_sums(int64_t N, const double* __restrict__ Q, double* __restrict__ partials,
+                              unsigned int* __restrict__ counter, double* __restrict__ out) {
   __shared__ double s1[PT], s2[PT];
+  __shared__ bool last;
   double a = 0, b = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     a += Q[i];
@@ -81,8 +85,22 @@ __global__ void k_charge_sums(int64_t N, const double* Q, double* out /* [0] sum
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    out[0] = s1[0];
-    out[1] = s2[0];
+    partials[2 * blockIdx.x] = s1[0];
+    partials[2 * blockIdx.x + 1] = s2[0];
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double t1 = 0, t2 = 0;
+    for (unsigned k = 0; k < gridDim.x; ++k) {
+      t1 += ((volatile double*)partials)[2 * k];
+      t2 += ((volatile double*)partials)[2 * k + 1];
+    }
+    out[0] = t1;
+    out[1] = t2;
+    *counter = 0u;
   }
 }
 
@@ -327,7 +345,8 @@ int fep3m_set_particles(fep3m_ctx* c, int64_t N, const double* pos, const double
   CK(cudaMemsetAsync(c->iflags, 0, sizeof(int), c->stream));
   CK(bin_particles(c, dpos, dQ, c->precision == FEP3M_MIXED));
   CK(sorted_charges(c));
-  FEP3M_CL k_charge_sums<<<1, PT, 0, c->stream>>>(N, dQ, c->scal + 32);   // one block: writes the totals
+  FEP3M_CL k_charge_sums<<<(unsigned)std::min<int64_t>(std::max<int64_t>(gsz(N) / 4, 1), 256), PT, 0, c->stream>>>(
+      N, dQ, (double*)c->red_tmp, c->red_counter, c->scal + 32);
   ev_record(c, 7);
   CK(pair_counts(c, (unsigned long long*)(c->scal + 48)));
   double sums[2];

@@ -135,36 +135,39 @@ __global__ void k_vertex_density(int n, const T* __restrict__ C, T* __restrict__
 
 // one axis of the order-3 x order-1 mixed mass: global order-3 node g -> up to
 // three vertices with weights
-__device__ __forceinline__ int mpq_row(int g, int n, int vtx[3], double wgt[3]) {
+template <class T>
+__device__ __forceinline__ int mpq_row(int g, int n, int vtx[3], T wgt[3]) {
   const int e = g / 3, t = g - 3 * e;
   if (t == 0) {
-    vtx[0] = wrapi(e - 1, n); wgt[0] = cMpq64[3][0];
-    vtx[1] = e;               wgt[1] = cMpq64[0][0] + cMpq64[3][1];
-    vtx[2] = wrapi(e + 1, n); wgt[2] = cMpq64[0][1];
+    vtx[0] = wrapi(e - 1, n); wgt[0] = (T)cMpq64[3][0];
+    vtx[1] = e;               wgt[1] = (T)(cMpq64[0][0] + cMpq64[3][1]);
+    vtx[2] = wrapi(e + 1, n); wgt[2] = (T)cMpq64[0][1];
     return 3;
   }
-  vtx[0] = e;               wgt[0] = cMpq64[t][0];
-  vtx[1] = wrapi(e + 1, n); wgt[1] = cMpq64[t][1];
+  vtx[0] = e;               wgt[0] = (T)cMpq64[t][0];
+  vtx[1] = wrapi(e + 1, n); wgt[1] = (T)cMpq64[t][1];
   return 2;
 }
 
+// b = 4 pi (Mpq (x) Mpq (x) Mpq) r, accumulated in the vertex density's type;
+// grid (ceil(N / 128), N, N)
 template <class T>
 __global__ void k_load_vector(int n, const T* __restrict__ rv, double* __restrict__ b) {
   const int N = 3 * n;
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= (int64_t)N * N * N) return;
-  const int ix = (int)(g % N), iy = (int)((g / N) % N), iz = (int)(g / ((int64_t)N * N));
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= N) return;
+  const int iy = blockIdx.y, iz = blockIdx.z;
   int vx[3], vy[3], vz[3];
-  double wx[3], wy[3], wz[3];
-  const int nx = mpq_row(ix, n, vx, wx), ny = mpq_row(iy, n, vy, wy), nz = mpq_row(iz, n, vz, wz);
-  double acc = 0.0;
+  T wx[3], wy[3], wz[3];
+  const int nx = mpq_row<T>(ix, n, vx, wx), ny = mpq_row<T>(iy, n, vy, wy), nz = mpq_row<T>(iz, n, vz, wz);
+  T acc = T(0);
   for (int c = 0; c < nz; ++c)
     for (int bb = 0; bb < ny; ++bb) {
-      double wyz = wy[bb] * wz[c];
+      const T wyz = wy[bb] * wz[c];
       const int64_t row = (int64_t)n * (vy[bb] + (int64_t)n * vz[c]);
-      for (int a = 0; a < nx; ++a) acc += wx[a] * wyz * (double)rv[vx[a] + row];
+      for (int a = 0; a < nx; ++a) acc += wx[a] * wyz * rv[vx[a] + row];
     }
-  b[g] = 4.0 * M_PI * acc;
+  b[ix + (int64_t)N * (iy + (int64_t)N * iz)] = 4.0 * M_PI * (double)acc;
 }
 
 // Coarsest-level exact solve x = V (Dinv o (V^T b)) (V the 1-D generalized
@@ -1940,12 +1943,14 @@ cudaError_t assemble_forward(fep3m_ctx* c) {
     FEP3M_CL k_elem_coeff<float><<<grid_for(ne), TPB, 0, s>>>(ne, c->start, c->count, (const float4*)c->part, (float*)c->C);
     FEP3M_CL k_vertex_density<float><<<grid_for(ne), TPB, 0, s>>>(n, (const float*)c->C, (float*)c->rv,
                                                                    (float*)c->Cv);
-    FEP3M_CL k_load_vector<float><<<grid_for(nodes), TPB, 0, s>>>(n, (const float*)c->rv, c->b64);
+    FEP3M_CL k_load_vector<float><<<dim3((3 * n + 127) / 128, 3 * n, 3 * n), 128, 0, s>>>(n, (const float*)c->rv,
+                                                                                         c->b64);
   } else {
     FEP3M_CL k_elem_coeff<double><<<grid_for(ne), TPB, 0, s>>>(ne, c->start, c->count, (const vec4<double>::type*)c->part, (double*)c->C);
     FEP3M_CL k_vertex_density<double><<<grid_for(ne), TPB, 0, s>>>(n, (const double*)c->C, (double*)c->rv,
                                                                     (double*)c->Cv);
-    FEP3M_CL k_load_vector<double><<<grid_for(nodes), TPB, 0, s>>>(n, (const double*)c->rv, c->b64);
+    FEP3M_CL k_load_vector<double><<<dim3((3 * n + 127) / 128, 3 * n, 3 * n), 128, 0, s>>>(n, (const double*)c->rv,
+                                                                                          c->b64);
   }
   return cudaGetLastError();
 }

@@ -834,9 +834,8 @@ cudaError_t pair_prepare(fep3m_ctx* c) {
 // non-empty block elements): singular pairs c0 s - c0, one non-empty element,
 // the largest c0, nb (element pairs of the screen contraction) and c0 nb
 // (charge-element pairs)
-__global__ void k_pair_count(int n, int n_sr, const int* __restrict__ count, unsigned long long* __restrict__ out) {
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= (int64_t)n * n * n) return;
+__device__ __forceinline__ void pair_count_one(int n, int n_sr, const int* __restrict__ count, int64_t e,
+                                               unsigned long long v[5]) {
   const int c0 = count[e];
   if (c0 == 0) return;
   const int ex = (int)(e % n), ey = (int)((e / n) % n), ez = (int)(e / ((int64_t)n * n));
@@ -848,11 +847,34 @@ __global__ void k_pair_count(int n, int n_sr, const int* __restrict__ count, uns
         s += cj;
         nb += cj > 0;
       }
-  atomicAdd(&out[0], (unsigned long long)((long long)c0 * s - c0));
-  atomicAdd(&out[1], 1ull);
-  atomicMax(&out[2], (unsigned long long)c0);
-  atomicAdd(&out[3], (unsigned long long)nb);
-  atomicAdd(&out[4], (unsigned long long)((long long)c0 * nb));
+  v[0] = (unsigned long long)((long long)c0 * s - c0);
+  v[1] = 1ull;
+  v[2] = (unsigned long long)c0;
+  v[3] = (unsigned long long)nb;
+  v[4] = (unsigned long long)((long long)c0 * nb);
+}
+
+// warp sums (and max) first: one atomic per warp and counter
+__global__ void k_pair_count(int n, int n_sr, const int* __restrict__ count, unsigned long long* __restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned long long v[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
+  if (e < (int64_t)n * n * n) pair_count_one(n, n_sr, count, e, v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
+    v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
+    const unsigned long long m = __shfl_down_sync(0xffffffffu, v[2], o);
+    v[2] = m > v[2] ? m : v[2];
+    v[3] += __shfl_down_sync(0xffffffffu, v[3], o);
+    v[4] += __shfl_down_sync(0xffffffffu, v[4], o);
+  }
+  if ((threadIdx.x & 31) == 0 && v[1] != 0ull) {
+    atomicAdd(&out[0], v[0]);
+    atomicAdd(&out[1], v[1]);
+    atomicMax(&out[2], v[2]);
+    atomicAdd(&out[3], v[3]);
+    atomicAdd(&out[4], v[4]);
+  }
 }
 
 cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev5) {
