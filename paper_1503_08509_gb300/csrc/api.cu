@@ -181,9 +181,15 @@ int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev)
   fep3m::Solver* A = &c->solv[1];
   F->stream = c->stream;
   if (force_dev) {
+    // adjoint chain on aux (deposit, mesh solve, vertex adjoint) with its
+    // screen and singular sweeps forked onto a third stream
     CK(cudaEventRecord(c->ev_fork, c->stream));
     CK(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
     CK(adjoint_pre(c, 1.0, nullptr, c->aux_stream));
+    CK(cudaEventRecord(c->ev_fork2, c->aux_stream));
+    CK(cudaStreamWaitEvent(c->sweep_stream, c->ev_fork2, 0));
+    CK(adjoint_sweeps(c, c->sweep_stream));
+    CK(cudaEventRecord(c->ev_join2, c->sweep_stream));
     CK(mesh_solve_begin(A, c->g64, c->lam64));
   }
   ev_record(c, 0);
@@ -202,9 +208,10 @@ int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev)
     CK(mesh_solve_end(A));
     c->stats.adj_iterations = A->iters;
     c->stats.adj_rel_residual = A->relres;
-    CK(adjoint_mid(c, c->aux_stream));
+    CK(adjoint_vertex(c, c->aux_stream));
     CK(cudaEventRecord(c->ev_join, c->aux_stream));
     CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join2, 0));
     CK(adjoint_final(c, 1.0, force_dev, nullptr, -1.0, c->stream));
     ev_record(c, 4);
   }
@@ -241,8 +248,11 @@ void fep3m_destroy(fep3m_ctx* c) {
   fep3m::solver_destroy(&c->solv[0]);
   fep3m::solver_destroy(&c->solv[1]);
   if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  if (c->sweep_stream) cudaStreamDestroy(c->sweep_stream);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_fork2) cudaEventDestroy(c->ev_fork2);
+  if (c->ev_join2) cudaEventDestroy(c->ev_join2);
   if (c->ev_init)
     for (int k = 0; k < 8; ++k) cudaEventDestroy(c->ev[k]);
   delete c;
@@ -312,8 +322,11 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
   cudaMemset(c->red_counter, 0, sizeof(unsigned int));
   cudaMemset(c->iflags, 0, 16 * sizeof(int));
   if ((e = cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&c->sweep_stream, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+      (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming)) != cudaSuccess)
     return fail(from_cuda(e));
   if ((e = solver_init(&c->solv[0], c, c->stream)) != cudaSuccess) return fail(from_cuda(e));
   if ((e = solver_init(&c->solv[1], c, c->aux_stream)) != cudaSuccess) return fail(from_cuda(e));
@@ -420,12 +433,17 @@ int fep3m_vjp(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double*
   CK(cudaEventRecord(c->ev_fork, c->stream));
   CK(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
   CK(adjoint_pre(c, gU, g, c->aux_stream));
+  CK(cudaEventRecord(c->ev_fork2, c->aux_stream));
+  CK(cudaStreamWaitEvent(c->sweep_stream, c->ev_fork2, 0));
+  CK(adjoint_sweeps(c, c->sweep_stream));
+  CK(cudaEventRecord(c->ev_join2, c->sweep_stream));
   CK(mesh_solve(&c->solv[1], c->g64, c->lam64));
   c->stats.adj_iterations = c->solv[1].iters;
   c->stats.adj_rel_residual = c->solv[1].relres;
-  CK(adjoint_mid(c, c->aux_stream));
+  CK(adjoint_vertex(c, c->aux_stream));
   CK(cudaEventRecord(c->ev_join, c->aux_stream));
   CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_join2, 0));
   CK(adjoint_final(c, gU, dp, dq, 1.0, c->stream));
   if (dpos && !pdev) {
     int s = deliver(c, dpos, c->out_tmp + N, 3 * N * sizeof(double));

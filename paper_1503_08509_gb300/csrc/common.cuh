@@ -199,7 +199,8 @@ struct fep3m_ctx {
   double* out_tmp = nullptr;     // N*3 staging for host outputs
   fep3m::Solver solv[2];          // [0] forward mesh solve, [1] adjoint mesh solve
   cudaStream_t aux_stream = nullptr;   // adjoint chain, concurrent with the forward one
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t sweep_stream = nullptr; // adjoint screen and singular sweeps (need no mesh solution)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
   // stats
   fep3m_stats stats;
   bool timing = false;
@@ -236,7 +237,8 @@ cudaError_t pair_forward(fep3m_ctx* c, double* phi_out, int want_grad);
 // adjoint in three parts: weights and deposit (-> g64), the parts that need
 // lam (vertex adjoint, screen sweep, singular adjoint), and the per-charge assembly
 cudaError_t adjoint_pre(fep3m_ctx* c, double gU, const double* gphi, cudaStream_t s);
-cudaError_t adjoint_mid(fep3m_ctx* c, cudaStream_t s);
+cudaError_t adjoint_sweeps(fep3m_ctx* c, cudaStream_t s);
+cudaError_t adjoint_vertex(fep3m_ctx* c, cudaStream_t s);
 cudaError_t adjoint_final(fep3m_ctx* c, double gU, double* dpos, double* dQ, double sign, cudaStream_t s);
 cudaError_t energy(fep3m_ctx* c, double* U_dev);
 cudaError_t sorted_charges(fep3m_ctx* c);

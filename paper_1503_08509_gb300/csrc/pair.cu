@@ -969,15 +969,15 @@ cudaError_t adjoint_pre(fep3m_ctx* c, double gU, const double* gphi, cudaStream_
   return cudaGetLastError();
 }
 
-// the parts that need lam: vertex adjoint mu, screen sweep A, singular adjoint potential
-cudaError_t adjoint_mid(fep3m_ctx* c, cudaStream_t s) {
+// the screen sweep A and the singular adjoint potential: they need the
+// deposit of the weights (adjoint_pre) but not the adjoint mesh solution, so
+// they run concurrently with the mesh solves
+cudaError_t adjoint_sweeps(fep3m_ctx* c, cudaStream_t s) {
   const int n = c->n;
   const int64_t N = c->N;
-  const fep3m::Level& L0 = c->solv[1].mg.lv[0];
-  cudaError_t e = vertex_adjoint(c, c->lam64, c->mu_v, L0.t1, L0.t2, s);
-  if (e != cudaSuccess) return e;
   cudaStream_t keep = c->stream;
   c->stream = s;   // screen_adjoint issues on c->stream
+  cudaError_t e;
   if (c->precision == FEP3M_MIXED) {
     e = screen_adjoint<float>(c, (const float*)c->W_el, c->Hw32, (float*)c->A_el);
     if (e == cudaSuccess)
@@ -993,6 +993,12 @@ cudaError_t adjoint_mid(fep3m_ctx* c, cudaStream_t s) {
   c->stream = keep;
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+// the part that needs lam: the vertex adjoint mu = 4 pi (Mpq^T)^3 lam
+cudaError_t adjoint_vertex(fep3m_ctx* c, cudaStream_t s) {
+  const fep3m::Level& L0 = c->solv[1].mg.lv[0];
+  return vertex_adjoint(c, c->lam64, c->mu_v, L0.t1, L0.t2, s);
 }
 
 // per-charge dLf/dx (times sign) and dLf/dQ
