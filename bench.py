@@ -32,6 +32,9 @@ METRIC = "particles/sec for Phi_i+forces at stated RMS error vs Ewald; mixed vs 
 WORKLOAD = "nacl32"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "nacl32_sample.txt")
 L2_FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one pair-kernel launch on this workload, from the ncu
+# capture summarised in profiles/k_pair_brick3_nacl32.md (set to None whenever the kernel changes)
+PAIR_DRAM_BYTES = 5863680
 
 
 def parse():
@@ -273,7 +276,7 @@ def run_ours(args):
     peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
     roof = {"kernel": "k_pair_brick3 (screen field GEMM + smooth/screen evaluation + singular pairs, with gradients)",
             "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
+            "frac": round(achieved / peak, 4), "traffic": PAIR_DRAM_BYTES,
             "peak_note": "FP32 FMA peak derived: %d SMs x 128 lanes x 2 flops x %.0f MHz (max SM clock)"
                          % (props.multi_processor_count, sm_max),
             "flops_per_launch": flops, "ms_per_launch": round(pair_ms, 4),
