@@ -105,7 +105,7 @@ struct Hierarchy {
   std::vector<Level> lv;
   CoarseSolver coarse;
   double lmax = 0;            // estimate of lambda_max(D^-1 K)
-  int cheb_degree = 3;
+  int cheb_degree = 4;
 };
 
 // One multigrid solver instance (the context holds two, so that the forward
