@@ -32,9 +32,9 @@ METRIC = "particles/sec for Phi_i+forces at stated RMS error vs Ewald; mixed vs 
 WORKLOAD = "nacl32"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "nacl32_sample.txt")
 L2_FLUSH_BYTES = 256 << 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one pair-kernel launch on this workload, from the ncu
-# capture summarised in profiles/k_pair_brick3_nacl32.md (set to None whenever the kernel changes)
-PAIR_DRAM_BYTES = 5863680
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_pair_screen launch on this workload, from the ncu
+# capture summarised in profiles/ (None until one is taken of the current kernel)
+PAIR_DRAM_BYTES = None
 
 
 def parse():
@@ -135,7 +135,7 @@ def fp32_peak_tflops(n_sm, mhz):
 
 
 def time_engine(eng, pos, Q, out, steps, warmup, flush, torch, host=False):
-    """Run warmup + timed steps; returns (list of ms per step, list of pair-kernel ms, launches per step)."""
+    """Run warmup + timed steps; returns (list of ms per step, list of screen-kernel ms, launches per step)."""
     stream = eng.stream
     for _ in range(warmup):
         eng.set_particles(pos, Q)
@@ -153,7 +153,7 @@ def time_engine(eng, pos, Q, out, steps, warmup, flush, torch, host=False):
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
-        pair.append(eng.stats()["ms_pair"])
+        pair.append(eng.stats()["ms_pair_screen"])
     launches = (eng.stats()["kernel_launches"] - l0) / steps
     return ms, pair, launches, r
 
@@ -259,32 +259,35 @@ def run_ours(args):
         acc["mixed_vs_fp64"] = dict(phi_rel_rms=rel_rms(results["mixed"]["phi"], results["fp64"]["phi"]),
                                     force_rel_rms=rel_rms(results["mixed"]["F"], results["fp64"]["F"]))
 
-    # roofline of the hot-path kernel the method is built around: the short-range pair kernel (FP32 issue bound).
-    # achieved = flops it executes (vertex-regrouped screen GEMM, field evaluation, singular pairs) / its
-    # CUDA-event time; SURVEY 8(d)'s element-to-point counts are reported beside it.
+    # roofline of the hot-path kernel the method is built around: the short-range screen/singular kernel
+    # k_pair_screen (FP32 issue bound), timed with CUDA events on its own stream, where it runs concurrently
+    # with the forward and adjoint mesh solves.  achieved = SURVEY 8(d)'s algorithmic count for a build that
+    # collapses the screen sums per target element (1024 flops per non-empty target element and non-empty
+    # element of its block, 20 per singular pair with gradients; the 128 per target of the 64-node
+    # evaluation belong to k_pair_eval); the per-target-charge count and the flops the kernel executes
+    # (vertex-regrouped contraction: 512 x 64 x 2 per non-empty target element) are reported beside it.
     st = main["stats"]
     ne_nonempty = st["nonempty_elements"]
     pairs = st["singular_pairs"]
-    flops = ne_nonempty * 512 * 64 * 2 + N * 64 * 2 * 4 + pairs * 20
-    flops_elem = st["screen_element_pairs"] * 1024 + N * 128 + pairs * 20
-    flops_charge = st["screen_charge_pairs"] * 1024 + N * 128 + pairs * 20
+    flops_elem = st["screen_element_pairs"] * 1024 + pairs * 20
+    flops_charge = st["screen_charge_pairs"] * 1024 + pairs * 20
+    flops_exec = ne_nonempty * 512 * 64 * 2 + pairs * 20
     pair_ms = statistics.mean(main["pair"])
-    achieved = flops / (pair_ms * 1e-3) / 1e12
+    tf = lambda f: f / (pair_ms * 1e-3) / 1e12
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
-    roof = {"kernel": "k_pair_brick3 (screen field GEMM + smooth/screen evaluation + singular pairs, with gradients)",
-            "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": PAIR_DRAM_BYTES,
+    roof = {"kernel": "k_pair_screen (screen-field contraction + singular pairs with gradients, concurrent with "
+                      "the mesh solves)",
+            "bound": "alu", "achieved": round(tf(flops_elem), 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+            "frac": round(tf(flops_elem) / peak, 4), "traffic": PAIR_DRAM_BYTES,
             "peak_note": "FP32 FMA peak derived: %d SMs x 128 lanes x 2 flops x %.0f MHz (max SM clock)"
                          % (props.multi_processor_count, sm_max),
-            "flops_per_launch": flops, "ms_per_launch": round(pair_ms, 4),
-            "element_to_point_count": {
-                "per_target_element": {"flops": flops_elem,
-                                       "frac": round(flops_elem / (pair_ms * 1e-3) / 1e12 / peak, 4)},
-                "per_target_charge": {"flops": flops_charge,
-                                      "frac": round(flops_charge / (pair_ms * 1e-3) / 1e12 / peak, 4)}}}
+            "count": "per (non-empty target element, non-empty block element) pair x 1024 + singular pairs x 20",
+            "flops_per_launch": flops_elem, "ms_per_launch": round(pair_ms, 4),
+            "per_target_charge": {"flops": flops_charge, "frac": round(tf(flops_charge) / peak, 4)},
+            "executed": {"flops": flops_exec, "frac": round(tf(flops_exec) / peak, 4)}}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
@@ -300,7 +303,8 @@ def run_ours(args):
         "fp64": ({"value": round(ws * N * results["fp64"]["steps"] / (results["fp64"]["total"] / 1e3), 1),
                   "ms_per_step": round(results["fp64"]["total"] / results["fp64"]["steps"], 4)}
                  if "fp64" in results and args.precision == "mixed" else None),
-        "stages_ms": {k: round(st[k], 4) for k in ("ms_bin", "ms_assemble", "ms_solve", "ms_pair", "ms_adjoint")},
+        "stages_ms": {k: round(st[k], 4) for k in ("ms_bin", "ms_assemble", "ms_solve", "ms_pair_screen",
+                                                   "ms_pair_eval", "ms_adjoint")},
         "mg": {"levels": st["mg_levels"], "iterations": st["mg_iterations"], "refine_steps": st["refine_steps"],
                "rel_residual": st["mg_rel_residual"], "adj_iterations": st["adj_iterations"]},
         "roofline": roof,

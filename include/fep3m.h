@@ -93,7 +93,7 @@ typedef struct {
   int max_per_element;
   double ms_bin, ms_assemble, ms_solve, ms_pair, ms_adjoint;  /* last call, if
                                timing was enabled with fep3m_set_timing; ms_pair
-                               covers the short-range pair kernel launch alone   */
+                               = ms_pair_screen + ms_pair_eval (below)           */
   int64_t kernel_launches;  /* CUDA kernels launched by this library in this
                                process so far (all contexts)                     */
   int64_t screen_element_pairs;  /* (non-empty element, non-empty element of its
@@ -101,6 +101,11 @@ typedef struct {
                                screen sums of Sec. 3.1.2 per target element      */
   int64_t screen_charge_pairs;   /* (charge, non-empty element of its block) pairs:
                                the same per target charge                        */
+  double ms_pair_screen;    /* the screen-contraction and singular-sum launch,
+                               which runs on its own stream concurrently with
+                               the forward mesh solve                            */
+  double ms_pair_eval;      /* the evaluation of the mesh potential minus the
+                               screen field at the targets, after the solve      */
 } fep3m_stats;
 
 /* Create a context: validates cfg, builds the FE basis-screen table (a

@@ -25,7 +25,8 @@ class Stats(ctypes.Structure):
                 ("max_per_element", ctypes.c_int), ("ms_bin", ctypes.c_double), ("ms_assemble", ctypes.c_double),
                 ("ms_solve", ctypes.c_double), ("ms_pair", ctypes.c_double), ("ms_adjoint", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("screen_element_pairs", ctypes.c_int64),
-                ("screen_charge_pairs", ctypes.c_int64)]
+                ("screen_charge_pairs", ctypes.c_int64), ("ms_pair_screen", ctypes.c_double),
+                ("ms_pair_eval", ctypes.c_double)]
 
 
 P = ctypes.c_void_p

@@ -194,17 +194,20 @@ struct fep3m_ctx {
   void* D_adj = nullptr;         // adjoint table-field GEMM output, chunk of offsets x n^3 (T)
   size_t D_bytes = 0;
   void* mu_v = nullptr;          // n^3 vertex adjoint (T)
+  void* Gscr = nullptr;          // screen field at each brick element's 64 nodes, bricks * 4096 (T)
   double* red_tmp = nullptr;     // reduction partials (1024)
   unsigned int* red_counter = nullptr;
   double* out_tmp = nullptr;     // N*3 staging for host outputs
   fep3m::Solver solv[2];          // [0] forward mesh solve, [1] adjoint mesh solve
   cudaStream_t aux_stream = nullptr;   // adjoint chain, concurrent with the forward one
   cudaStream_t sweep_stream = nullptr; // adjoint screen and singular sweeps (need no mesh solution)
+  cudaStream_t pair_stream = nullptr;  // screen contraction and singular sums (need no mesh solution)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
+  cudaEvent_t ev_pfork = nullptr, ev_pjoin = nullptr;
   // stats
   fep3m_stats stats;
   bool timing = false;
-  cudaEvent_t ev[8];
+  cudaEvent_t ev[11];
   bool ev_init = false;
 };
 
@@ -230,10 +233,20 @@ cudaError_t vertex_adjoint(fep3m_ctx* c, const double* lam, void* mu, void* work
 // it, checks the residual and re-solves if needed.  Results in s->iters etc.
 cudaError_t mesh_solve_begin(Solver* s, const double* b, double* phi);
 cudaError_t mesh_solve_end(Solver* s);
+// after the caller has synchronised with the replayed solve (and its residual
+// copy): true if it met its tolerance; false drops the plan, so that the next
+// mesh_solve_begin re-calibrates with one more refinement sweep
+bool mesh_solve_check(Solver* s);
 cudaError_t mesh_solve(Solver* s, const double* b, double* phi);
 cudaError_t pair_prepare(fep3m_ctx* c);
 cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev5);
-cudaError_t pair_forward(fep3m_ctx* c, double* phi_out, int want_grad);
+// short-range part in two launches: the screen contraction and the singular
+// sums need only the binned charges and the vertex density, so they run on
+// their own stream while the mesh is solved; the evaluation of the mesh
+// potential minus the screen field at the targets follows the solve.
+size_t pair_screen_bytes(const fep3m_ctx* c);
+cudaError_t pair_screen(fep3m_ctx* c, int want_grad, cudaStream_t s);
+cudaError_t pair_eval(fep3m_ctx* c, double* phi_out, int want_grad);
 // adjoint in three parts: weights and deposit (-> g64), the parts that need
 // lam (vertex adjoint, screen sweep, singular adjoint), and the per-charge assembly
 cudaError_t adjoint_pre(fep3m_ctx* c, double gU, const double* gphi, cudaStream_t s);

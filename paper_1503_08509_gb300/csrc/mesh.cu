@@ -1859,22 +1859,29 @@ cudaError_t mesh_solve_begin(Solver* c, const double* b, double* phi) {
   return cudaGetLastError();
 }
 
-cudaError_t mesh_solve_end(Solver* c) {
-  if (!c->pending) return cudaSuccess;
+bool mesh_solve_check(Solver* c) {
+  if (!c->pending) return true;
   c->pending = false;
-  cudaError_t e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return e;
   const double bb = c->host_res[0], rr = c->host_res[1];
   const double rel = bb > 0 ? std::sqrt(rr / bb) : 0.0;
   if (rel <= solver_rtol(c)) {
     c->relres = rel;
     c->iters = c->plan_kin * c->plan_kout;
     c->refine_steps = c->plan_kout;
-    return cudaSuccess;
+    return true;
   }
-  // this right-hand side needs more iterations: one more sweep from now on
+  // this right-hand side needs more iterations: one more sweep from now on,
+  // and the next solve re-calibrates
   ++c->plan_kout;
   destroy_plan(c);
+  return false;
+}
+
+cudaError_t mesh_solve_end(Solver* c) {
+  if (!c->pending) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return e;
+  if (mesh_solve_check(c)) return cudaSuccess;
   return solve_calibrate(c, c->pend_b, c->pend_phi);
 }
 

@@ -215,15 +215,16 @@ __device__ __forceinline__ int block_scan_excl(int v, int* wsum /* PT/32 + 1 */,
   return res;
 }
 
+// One CTA per brick of BX x BY x BZ elements: the screen field of every brick
+// element at its 64 nodes (written to Gscr, brick-major) and the singular sums
+// of every target charge in the brick (written to phi_s and E_s).
 template <class T, bool GRAD>
-__global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_h, const int* __restrict__ start,
+__global__ void __launch_bounds__(PT) k_pair_screen(int n, int n_sr, T h, const int* __restrict__ start,
                                                     const int* __restrict__ count,
                                                     const typename vec4<T>::type* __restrict__ part,
-                                                    const int* __restrict__ ecoord, const T* __restrict__ Cv,
-                                                    const T* __restrict__ rv, const T* __restrict__ phi_mesh,
-                                                    const T* __restrict__ Hw, const int* __restrict__ perm,
-                                                    double* __restrict__ phi_s, double* __restrict__ E_s,
-                                                    double* __restrict__ phi_out) {
+                                                    const T* __restrict__ Cv, const T* __restrict__ rv,
+                                                    const T* __restrict__ Hw, T* __restrict__ Gscr,
+                                                    double* __restrict__ phi_s, double* __restrict__ E_s) {
   typedef typename vec4<T>::type V4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nbx = (n + BX - 1) / BX, nby = (n + BY - 1) / BY;
@@ -361,25 +362,20 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
 #pragma unroll
       for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j];
   }
-  __syncthreads();
-  T* G = A_c;
+  // the brick's screen fields: row l of the brick (64 nodes) per element, one
+  // vector store per (i); the 16 mb of a row are contiguous.  Region 1 (R) was
+  // last read before the loop's final barrier, so the staging below may
+  // overwrite it without another one.
   {
-    const int N = 3 * n;
+    T* gb = Gscr + (int64_t)blockIdx.x * (BE * 64);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int l = 4 * eb + i;
-      const int ex = E0x + l % BX, ey = E0y + (l / BX) % BY, ez = E0z + l / (BX * BY);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int m = 4 * mb + j, mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
-        T val = T(0);
-        if (ex < n && ey < n && ez < n) {
-          const int gx = 3 * ex + mx, gy = 3 * ey + my, gz = 3 * ez + mz;   // < 3n + 3
-          val = phi_mesh[(gx >= N ? gx - N : gx) + (int64_t)N * ((gy >= N ? gy - N : gy) + (int64_t)N * (gz >= N ? gz - N : gz))] -
-                tot[i][j];
-        }
-        G[l * 64 + m] = val;
-      }
+      V4 v;
+      v.x = tot[i][0];
+      v.y = tot[i][1];
+      v.z = tot[i][2];
+      v.w = tot[i][3];
+      *reinterpret_cast<V4*>(gb + (4 * eb + i) * 64 + 4 * mb) = v;
     }
   }
   // (3) stage the halo charges if they fit (region 1 is free now)
@@ -426,18 +422,16 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
   }
   __syncthreads();
   const bool staged = flag[0] != 0;
-  // (4) four threads per target: each takes 16 of the 64 nodes and the rows
-  // r = q, q + 4, ... of the target's block; a two-step shuffle combines them.
-  // A row (dy, dz) of the block is 2 n_sr + 1 consecutive halo elements, so
-  // its staged charges are one run; each row's terms are summed in FP32 and
-  // the row sums are added with compensation.
+  // (4) four threads per target, each summing the rows r = q, q + 4, ... of the
+  // target's block; a two-step shuffle combines them.  A row (dy, dz) of the
+  // block is 2 n_sr + 1 consecutive halo elements, so its staged charges are
+  // one run; each row's terms are summed in FP32 and the row sums are added
+  // with compensation.
   const int q = tid & 3;
   for (int tb = 0; tb < ntarget; tb += PT / 4) {
     const int k = tb + (tid >> 2);
     const bool valid = k < ntarget;
-    T v8[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v8[i] = T(0);
+    T v4[4] = {T(0), T(0), T(0), T(0)};
     int slot = 0;
     if (valid) {
       int lo = 0, hi2 = BE;                 // element of target k: epre[l] <= k < epre[l + 1]
@@ -452,32 +446,6 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
       const int kk = k - epre[l];
       slot = start[ex + (int64_t)n * (ey + (int64_t)n * ez)] + kk;
       const V4 pt = part[slot];
-      T ux[4], uy[4], uz[4], dx4[4], dy4[4], dz4[4];
-      q3_values<T>(pt.x, ux);
-      q3_values<T>(pt.y, uy);
-      q3_values<T>(pt.z, uz);
-      if (GRAD) {
-        q3_derivs<T>(pt.x, dx4);
-        q3_derivs<T>(pt.y, dy4);
-        q3_derivs<T>(pt.z, dz4);
-      }
-      // nodes 16 q .. 16 q + 15: mz = q, (mx, my) over 4 x 4
-#pragma unroll
-      for (int my = 0; my < 4; ++my) {
-        const V4 gv = *reinterpret_cast<const V4*>(G + l * 64 + 16 * q + 4 * my);
-        const T g4[4] = {gv.x, gv.y, gv.z, gv.w};
-#pragma unroll
-        for (int mx = 0; mx < 4; ++mx) {
-          const T g = g4[mx];
-          const T wyz = uy[my] * uz[q];
-          v8[0] += g * ux[mx] * wyz;
-          if (GRAD) {
-            v8[1] += g * dx4[mx] * wyz;
-            v8[2] += g * ux[mx] * dy4[my] * uz[q];
-            v8[3] += g * ux[mx] * uy[my] * dz4[q];
-          }
-        }
-      }
       const int base = lx + HW * (ly + HW * lz);          // halo index of block offset (-n_sr, -n_sr, -n_sr)
       const int cx = lx + n_sr;                           // the target's halo x index
       Acc<T> ps, fx, fy, fz;
@@ -543,25 +511,129 @@ __global__ void __launch_bounds__(PT) k_pair_brick3(int n, int n_sr, T h, T inv_
           }
         }
       }
-      v8[4] = ps.get();
-      v8[5] = fx.get();
-      v8[6] = fy.get();
-      v8[7] = fz.get();
+      v4[0] = ps.get();
+      v4[1] = fx.get();
+      v4[2] = fy.get();
+      v4[3] = fz.get();
     }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      v8[i] += __shfl_xor_sync(0xffffffffu, v8[i], 1);
-      v8[i] += __shfl_xor_sync(0xffffffffu, v8[i], 2);
+    for (int i = 0; i < 4; ++i) {
+      v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], 1);
+      v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], 2);
     }
     if (valid && q == 0) {
-      const double phi = (double)v8[0] * (double)inv_h + (double)v8[4];
+      phi_s[slot] = (double)v4[0];
+      if (GRAD) {
+        E_s[3 * slot + 0] = (double)v4[1];
+        E_s[3 * slot + 1] = (double)v4[2];
+        E_s[3 * slot + 2] = (double)v4[3];
+      }
+    }
+  }
+}
+
+// One CTA per brick, after the mesh solve: G = mesh potential - screen field
+// at the 64 nodes of each non-empty brick element (shared memory), then four
+// threads per target charge each contract 16 of the nodes with the order-3
+// shape functions (and their derivatives) at the charge; the mesh part is
+// added to the singular part the screen kernel left in phi_s / E_s.
+template <class T, bool GRAD>
+__global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __restrict__ start,
+                                                  const int* __restrict__ count,
+                                                  const typename vec4<T>::type* __restrict__ part,
+                                                  const T* __restrict__ phi_mesh, const T* __restrict__ Gscr,
+                                                  const int* __restrict__ perm, double* __restrict__ phi_s,
+                                                  double* __restrict__ E_s, double* __restrict__ phi_out) {
+  typedef typename vec4<T>::type V4;
+  __shared__ __align__(32) T G[BE * 64];
+  __shared__ int epre[BE + 1];
+  __shared__ int wsum[PT / 32 + 1];
+  const int nbx = (n + BX - 1) / BX, nby = (n + BY - 1) / BY;
+  const int E0x = (blockIdx.x % nbx) * BX, E0y = ((blockIdx.x / nbx) % nby) * BY, E0z = (blockIdx.x / (nbx * nby)) * BZ;
+  const int tid = threadIdx.x;
+  int ntarget;
+  {
+    int c0 = 0;
+    if (tid < BE) {
+      const int lx = E0x + (tid % BX), ly = E0y + (tid / BX) % BY, lz = E0z + tid / (BX * BY);
+      if (lx < n && ly < n && lz < n) c0 = count[lx + (int64_t)n * (ly + (int64_t)n * lz)];
+    }
+    const int pre = block_scan_excl(c0, wsum, &ntarget);
+    if (tid < BE) epre[tid] = pre;
+    if (tid == 0) epre[BE] = ntarget;
+  }
+  if (ntarget == 0) return;
+  __syncthreads();
+  {
+    const T* gb = Gscr + (int64_t)blockIdx.x * (BE * 64);
+    const int N = 3 * n;
+    for (int i = tid; i < BE * 64; i += PT) {
+      const int l = i >> 6, m = i & 63;
+      if (epre[l + 1] == epre[l]) continue;   // empty (or outside the mesh): never read
+      const int ex = E0x + l % BX, ey = E0y + (l / BX) % BY, ez = E0z + l / (BX * BY);
+      const int gx = 3 * ex + (m & 3), gy = 3 * ey + ((m >> 2) & 3), gz = 3 * ez + (m >> 4);   // < 3n + 3
+      G[i] = phi_mesh[(gx >= N ? gx - N : gx) + (int64_t)N * ((gy >= N ? gy - N : gy) + (int64_t)N * (gz >= N ? gz - N : gz))] -
+             gb[i];
+    }
+  }
+  __syncthreads();
+  const int q = tid & 3;   // nodes 16 q .. 16 q + 15: mz = q, (mx, my) over 4 x 4
+  for (int tb = 0; tb < ntarget; tb += PT / 4) {
+    const int k = tb + (tid >> 2);
+    const bool valid = k < ntarget;
+    T v4[4] = {T(0), T(0), T(0), T(0)};
+    int slot = 0;
+    if (valid) {
+      int lo = 0, hi2 = BE;
+      while (hi2 - lo > 1) {
+        const int mid = (lo + hi2) >> 1;
+        if (epre[mid] <= k) lo = mid;
+        else hi2 = mid;
+      }
+      const int l = lo;
+      const int ex = E0x + l % BX, ey = E0y + (l / BX) % BY, ez = E0z + l / (BX * BY);
+      slot = start[ex + (int64_t)n * (ey + (int64_t)n * ez)] + (k - epre[l]);
+      const V4 pt = part[slot];
+      T ux[4], uy[4], uz[4], dx4[4], dy4[4], dz4[4];
+      q3_values<T>(pt.x, ux);
+      q3_values<T>(pt.y, uy);
+      q3_values<T>(pt.z, uz);
+      if (GRAD) {
+        q3_derivs<T>(pt.x, dx4);
+        q3_derivs<T>(pt.y, dy4);
+        q3_derivs<T>(pt.z, dz4);
+      }
+#pragma unroll
+      for (int my = 0; my < 4; ++my) {
+        const V4 gv = *reinterpret_cast<const V4*>(G + l * 64 + 16 * q + 4 * my);
+        const T g4[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+        for (int mx = 0; mx < 4; ++mx) {
+          const T g = g4[mx];
+          const T wyz = uy[my] * uz[q];
+          v4[0] += g * ux[mx] * wyz;
+          if (GRAD) {
+            v4[1] += g * dx4[mx] * wyz;
+            v4[2] += g * ux[mx] * dy4[my] * uz[q];
+            v4[3] += g * ux[mx] * uy[my] * dz4[q];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], 1);
+      v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], 2);
+    }
+    if (valid && q == 0) {
+      const double phi = (double)v4[0] * (double)inv_h + phi_s[slot];
       phi_s[slot] = phi;
       if (phi_out) phi_out[perm[slot]] = phi;
       if (GRAD) {
         const double ih2 = (double)inv_h * (double)inv_h;
-        E_s[3 * slot + 0] = (double)v8[1] * ih2 + (double)v8[5];
-        E_s[3 * slot + 1] = (double)v8[2] * ih2 + (double)v8[6];
-        E_s[3 * slot + 2] = (double)v8[3] * ih2 + (double)v8[7];
+        E_s[3 * slot + 0] = (double)v4[1] * ih2 + E_s[3 * slot + 0];
+        E_s[3 * slot + 1] = (double)v4[2] * ih2 + E_s[3 * slot + 1];
+        E_s[3 * slot + 2] = (double)v4[3] * ih2 + E_s[3 * slot + 2];
       }
     }
   }
@@ -884,28 +956,48 @@ cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev5) {
   return cudaGetLastError();
 }
 
-template <class T, bool GRAD>
-static cudaError_t launch_pair_brick(fep3m_ctx* c, const T* phi_mesh, const T* Hw, double* phi_out) {
+static int pair_bricks(const fep3m_ctx* c) {
   const int n = c->n;
-  const int nbx = (n + BX - 1) / BX, nby = (n + BY - 1) / BY, nbz = (n + BZ - 1) / BZ;
+  return ((n + BX - 1) / BX) * ((n + BY - 1) / BY) * ((n + BZ - 1) / BZ);
+}
+
+size_t pair_screen_bytes(const fep3m_ctx* c) {
+  return (size_t)pair_bricks(c) * BE * 64 * (c->precision == FEP3M_MIXED ? sizeof(float) : sizeof(double));
+}
+
+template <class T, bool GRAD>
+static cudaError_t launch_pair_screen(fep3m_ctx* c, const T* Hw, cudaStream_t s) {
   const size_t smem = Pair3Smem<T>::bytes(c->n_sr);
-  auto kern = k_pair_brick3<T, GRAD>;
+  auto kern = k_pair_screen<T, GRAD>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  FEP3M_CL kern<<<(unsigned)(nbx * nby * nbz), PT, smem, c->stream>>>(
-      n, c->n_sr, (T)c->h, (T)c->inv_h, c->start, c->count, (const typename vec4<T>::type*)c->part, c->ecoord,
-      (const T*)c->Cv, (const T*)c->rv, phi_mesh, Hw, c->perm, c->phi_s, c->E_s, phi_out);
+  FEP3M_CL kern<<<(unsigned)pair_bricks(c), PT, smem, s>>>(
+      c->n, c->n_sr, (T)c->h, c->start, c->count, (const typename vec4<T>::type*)c->part, (const T*)c->Cv,
+      (const T*)c->rv, Hw, (T*)c->Gscr, c->phi_s, c->E_s);
   return cudaGetLastError();
 }
 
-cudaError_t pair_forward(fep3m_ctx* c, double* phi_out, int want_grad) {
+template <class T, bool GRAD>
+static cudaError_t launch_pair_eval(fep3m_ctx* c, const T* phi_mesh, double* phi_out) {
+  FEP3M_CL k_pair_eval<T, GRAD><<<(unsigned)pair_bricks(c), PT, 0, c->stream>>>(
+      c->n, (T)c->inv_h, c->start, c->count, (const typename vec4<T>::type*)c->part, phi_mesh, (const T*)c->Gscr,
+      c->perm, c->phi_s, c->E_s, phi_out);
+  return cudaGetLastError();
+}
+
+cudaError_t pair_screen(fep3m_ctx* c, int want_grad, cudaStream_t s) {
+  if (c->precision == FEP3M_MIXED)
+    return want_grad ? launch_pair_screen<float, true>(c, c->Hw32, s) : launch_pair_screen<float, false>(c, c->Hw32, s);
+  return want_grad ? launch_pair_screen<double, true>(c, c->Hw64, s) : launch_pair_screen<double, false>(c, c->Hw64, s);
+}
+
+cudaError_t pair_eval(fep3m_ctx* c, double* phi_out, int want_grad) {
   if (c->precision == FEP3M_MIXED) {
     const float* pm = (const float*)c->phi_mesh_T;
-    return want_grad ? launch_pair_brick<float, true>(c, pm, c->Hw32, phi_out)
-                     : launch_pair_brick<float, false>(c, pm, c->Hw32, phi_out);
+    return want_grad ? launch_pair_eval<float, true>(c, pm, phi_out) : launch_pair_eval<float, false>(c, pm, phi_out);
   }
-  return want_grad ? launch_pair_brick<double, true>(c, c->phi64, c->Hw64, phi_out)
-                   : launch_pair_brick<double, false>(c, c->phi64, c->Hw64, phi_out);
+  return want_grad ? launch_pair_eval<double, true>(c, c->phi64, phi_out)
+                   : launch_pair_eval<double, false>(c, c->phi64, phi_out);
 }
 
 cudaError_t sorted_charges(fep3m_ctx* c) {
