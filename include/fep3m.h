@@ -57,6 +57,8 @@ enum { FEP3M_FP64 = 0, FEP3M_MIXED = 1 };
 
 /* flags */
 #define FEP3M_NEUTRALIZE 1u    /* accept non-neutral input: uniform background */
+#define FEP3M_CUDA_CORE_SCREEN 2u  /* MIXED: screen-field contraction on the FP32
+                                      CUDA cores instead of the tensor cores    */
 
 typedef struct fep3m_ctx fep3m_ctx;
 
@@ -77,7 +79,7 @@ typedef struct {
   int mg_max_cycles;   /* cap on refinement sweeps; 0 -> 10                      */
   int table_pad;       /* Dirichlet box margin, elements, beyond the kept table;
                           0 -> 4                                                 */
-  unsigned flags;      /* FEP3M_NEUTRALIZE                                       */
+  unsigned flags;      /* FEP3M_NEUTRALIZE, FEP3M_CUDA_CORE_SCREEN               */
 } fep3m_config;
 
 typedef struct {

@@ -38,10 +38,12 @@ class FEP3M:
     """One FE-P3M context: mesh, screen tables and multigrid for a periodic cube.
 
     precision: 'fp64' or 'mixed' (FP32 pairs and multigrid, FP64 refinement).
+    tensor_cores: mixed precision only; False runs the screen-field contraction
+    on the FP32 CUDA cores instead of the split-precision bf16 tensor-core MMAs.
     """
 
     def __init__(self, L, n_el, n_sr=3, precision="fp64", mg_rtol=0.0, mg_max_cycles=0, neutralize=False,
-                 table_pad=0, device=None, stream=None):
+                 table_pad=0, device=None, stream=None, tensor_cores=True):
         lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.L, self.n_el, self.n_sr = float(L), int(n_el), int(n_sr)
@@ -49,7 +51,8 @@ class FEP3M:
         cfg = _lib.Config(L=self.L, n_el=self.n_el, q=1, n_sr=self.n_sr,
                           precision=_lib.FEP3M_MIXED if precision == "mixed" else _lib.FEP3M_FP64,
                           mg_rtol=mg_rtol, mg_max_cycles=mg_max_cycles, table_pad=table_pad,
-                          flags=_lib.FEP3M_NEUTRALIZE if neutralize else 0)
+                          flags=(_lib.FEP3M_NEUTRALIZE if neutralize else 0) |
+                          (0 if tensor_cores else _lib.FEP3M_CUDA_CORE_SCREEN))
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             h = ctypes.c_void_p()

@@ -184,6 +184,7 @@ int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev)
   fep3m::Solver* F = &c->solv[0];
   fep3m::Solver* A = &c->solv[1];
   F->stream = c->stream;
+  CK(cudaMemsetAsync(c->iflags + 2, 0, sizeof(int), c->stream));   // bounded-wait flag of the pair kernels
   if (force_dev) {
     CK(cudaEventRecord(c->ev_fork, c->stream));
     CK(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
@@ -270,11 +271,12 @@ void fep3m_destroy(fep3m_ctx* c) {
   if (!c) return;
   free_particles(c);
   void* p[] = {c->Hw64, c->Hw32, c->count, c->start, c->fill, c->scan_tmp, c->C, c->rv, c->Cv, c->b64, c->phi64,
-               c->res64, c->g64, c->lam64, c->scal, c->iflags, c->phi_mesh_T, c->W_el, c->A_el, c->mu_v, c->Gscr,
+               c->res64, c->g64, c->lam64, c->scal, c->iflags, c->phi_hl, c->W_el, c->A_el, c->mu_v, c->Gscr, c->Hb,
                c->red_tmp, c->red_counter, c->D_adj};
   for (void* q : p) dfree(q);
   fep3m::solver_destroy(&c->solv[0]);
   fep3m::solver_destroy(&c->solv[1]);
+  if (c->host_err) cudaFreeHost(c->host_err);
   if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
   if (c->sweep_stream) cudaStreamDestroy(c->sweep_stream);
   if (c->pair_stream) cudaStreamDestroy(c->pair_stream);
@@ -333,6 +335,15 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
   if ((st = from_cuda(dalloc(&c->Hw32, Hw.size()))) != FEP3M_OK) return fail(st);
   cudaMemcpy(c->Hw64, Hw.data(), Hw.size() * 8, cudaMemcpyHostToDevice);
   cudaMemcpy(c->Hw32, Hw32.data(), Hw32.size() * 4, cudaMemcpyHostToDevice);
+  if (c->precision == FEP3M_MIXED && !(cfg->flags & FEP3M_CUDA_CORE_SCREEN)) {
+    // bf16 pieces of the table for the tensor-core screen contraction
+    std::vector<uint16_t> hb(pair_tc_table_bytes(c->n_sr) / 2);
+    pair_tc_table(c->n_sr, Hw.data(), hb.data());
+    if ((st = from_cuda(cudaMalloc(&c->Hb, hb.size() * 2))) != FEP3M_OK) return fail(st);
+    cudaMemcpy(c->Hb, hb.data(), hb.size() * 2, cudaMemcpyHostToDevice);
+  }
+  if ((st = from_cuda(cudaMallocHost(&c->host_err, sizeof(int)))) != FEP3M_OK) return fail(st);
+  *c->host_err = 0;
   const int64_t ne = (int64_t)c->n * c->n * c->n, nodes = 27 * ne;
   const size_t es = c->precision == FEP3M_MIXED ? 4 : 8;
   cudaError_t e = cudaSuccess;
@@ -345,11 +356,12 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
       (e = dalloc(&c->res64, nodes)) != cudaSuccess || (e = dalloc(&c->g64, nodes)) != cudaSuccess ||
       (e = dalloc(&c->lam64, nodes)) != cudaSuccess || (e = dalloc(&c->scal, 64)) != cudaSuccess ||
       (e = dalloc(&c->iflags, 16)) != cudaSuccess || (e = cudaMalloc(&c->W_el, ne * 64 * es)) != cudaSuccess ||
-      (e = cudaMalloc(&c->A_el, ne * 8 * es)) != cudaSuccess || (e = cudaMalloc(&c->mu_v, ne * es)) != cudaSuccess ||
+      (e = cudaMalloc(&c->A_el, ne * 8 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&c->mu_v, ne * sizeof(double))) != cudaSuccess ||
       (e = dalloc(&c->red_tmp, 1024)) != cudaSuccess || (e = dalloc(&c->red_counter, 1)) != cudaSuccess ||
       (e = cudaMalloc(&c->Gscr, pair_screen_bytes(c))) != cudaSuccess)
     return fail(from_cuda(e));
-  if (c->precision == FEP3M_MIXED && (e = cudaMalloc(&c->phi_mesh_T, nodes * es)) != cudaSuccess)
+  if (c->precision == FEP3M_MIXED && (e = cudaMalloc(&c->phi_hl, nodes * 2 * sizeof(float))) != cudaSuccess)
     return fail(from_cuda(e));
   cudaMemset(c->red_counter, 0, sizeof(unsigned int));
   cudaMemset(c->iflags, 0, 16 * sizeof(int));
@@ -432,7 +444,9 @@ int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
       CK(energy(c, c->scal + 40));
       CK(cudaMemcpyAsync(U, c->scal + 40, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     }
+    CK(cudaMemcpyAsync(c->host_err, c->iflags + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (*c->host_err) return FEP3M_ETIMEOUT;
     if (!solves_missed(c, force != nullptr) || attempt == kMaxReruns) break;
   }
   const int st = solve_status(c, force != nullptr);
@@ -464,7 +478,9 @@ int fep3m_vjp(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double*
     for (int attempt = 0;; ++attempt) {
       int st = run_forward(c, nullptr, 1, nullptr);
       if (st != FEP3M_OK) return st;
+      CK(cudaMemcpyAsync(c->host_err, c->iflags + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
+      if (*c->host_err) return FEP3M_ETIMEOUT;
       if (!solves_missed(c, false) || attempt == kMaxReruns) break;
     }
     solve_status(c, false);

@@ -178,8 +178,8 @@ struct fep3m_ctx {
   double* g64 = nullptr;         // adjoint right-hand side
   double* lam64 = nullptr;       // adjoint mesh solution
   double* scal = nullptr;        // device scalars (dots, norms, flags), 64 doubles
+  void* phi_hl = nullptr;        // MIXED: mesh potential as hi + lo floats, (3n)^3 float2
   int* iflags = nullptr;         // device int flags: [0] input error, [1] converged, ...
-  void* phi_mesh_T = nullptr;    // mesh potential in working precision (for the pair kernel)
   void* lam_T = nullptr;
   // per-particle outputs, sorted order
   double* phi_s = nullptr;       // N
@@ -190,11 +190,13 @@ struct fep3m_ctx {
   double* Q_s = nullptr;         // N sorted charges (FP64)
   double* gphi_dev = nullptr;    // N staging for a host gphi
   void* W_el = nullptr;          // n^3 * 64 element deposits (T)
-  void* A_el = nullptr;          // n^3 * 8 screen adjoint (T)
+  void* A_el = nullptr;          // n^3 * 8 screen adjoint (FP64)
   void* D_adj = nullptr;         // adjoint table-field GEMM output, chunk of offsets x n^3 (T)
   size_t D_bytes = 0;
-  void* mu_v = nullptr;          // n^3 vertex adjoint (T)
+  void* mu_v = nullptr;          // n^3 vertex adjoint (FP64)
   void* Gscr = nullptr;          // screen field at each brick element's 64 nodes, bricks * 4096 (T)
+  void* Hb = nullptr;            // bf16 pieces of the table for the tensor-core contraction (MIXED)
+  int* host_err = nullptr;       // pinned: device-side error flags read after a step
   double* red_tmp = nullptr;     // reduction partials (1024)
   unsigned int* red_counter = nullptr;
   double* out_tmp = nullptr;     // N*3 staging for host outputs
@@ -238,14 +240,16 @@ cudaError_t mesh_solve_end(Solver* s);
 // mesh_solve_begin re-calibrates with one more refinement sweep
 bool mesh_solve_check(Solver* s);
 cudaError_t mesh_solve(Solver* s, const double* b, double* phi);
-cudaError_t pair_prepare(fep3m_ctx* c);
 cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev5);
 // short-range part in two launches: the screen contraction and the singular
 // sums need only the binned charges and the vertex density, so they run on
 // their own stream while the mesh is solved; the evaluation of the mesh
 // potential minus the screen field at the targets follows the solve.
 size_t pair_screen_bytes(const fep3m_ctx* c);
+size_t pair_tc_table_bytes(int n_sr);
+void pair_tc_table(int n_sr, const double* Hw, uint16_t* out);
 cudaError_t pair_screen(fep3m_ctx* c, int want_grad, cudaStream_t s);
+cudaError_t pair_prepare(fep3m_ctx* c);
 cudaError_t pair_eval(fep3m_ctx* c, double* phi_out, int want_grad);
 // adjoint in three parts: weights and deposit (-> g64), the parts that need
 // lam (vertex adjoint, screen sweep, singular adjoint), and the per-charge assembly

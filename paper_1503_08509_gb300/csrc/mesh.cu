@@ -1992,16 +1992,13 @@ __global__ void k_mpqT_axis(int axis, int n, int e0, int e1, int e2, const doubl
 }
 
 cudaError_t vertex_adjoint(fep3m_ctx* c, const double* lam, void* mu, void* work1, void* work2, cudaStream_t s) {
+  // FP64 in both precisions: mu meets the screen adjoint in a difference that
+  // cancels; the two partial passes (9 n^3 and 3 n^3 values) fit as doubles
+  // in work buffers of (3n)^3 floats
   const int n = c->n, N = 3 * n;
-  if (c->precision == FEP3M_MIXED) {
-    FEP3M_CL k_mpqT_axis<float><<<grid_for((size_t)n * N * N), TPB, 0, s>>>(0, n, n, N, N, lam, nullptr, (float*)work1, 1.0);
-    FEP3M_CL k_mpqT_axis<float><<<grid_for((size_t)n * n * N), TPB, 0, s>>>(1, n, n, n, N, nullptr, (float*)work1, (float*)work2, 1.0);
-    FEP3M_CL k_mpqT_axis<float><<<grid_for((size_t)n * n * n), TPB, 0, s>>>(2, n, n, n, n, nullptr, (float*)work2, (float*)mu, 4.0 * M_PI);
-  } else {
-    FEP3M_CL k_mpqT_axis<double><<<grid_for((size_t)n * N * N), TPB, 0, s>>>(0, n, n, N, N, lam, nullptr, (double*)work1, 1.0);
-    FEP3M_CL k_mpqT_axis<double><<<grid_for((size_t)n * n * N), TPB, 0, s>>>(1, n, n, n, N, nullptr, (double*)work1, (double*)work2, 1.0);
-    FEP3M_CL k_mpqT_axis<double><<<grid_for((size_t)n * n * n), TPB, 0, s>>>(2, n, n, n, n, nullptr, (double*)work2, (double*)mu, 4.0 * M_PI);
-  }
+  FEP3M_CL k_mpqT_axis<double><<<grid_for((size_t)n * N * N), TPB, 0, s>>>(0, n, n, N, N, lam, nullptr, (double*)work1, 1.0);
+  FEP3M_CL k_mpqT_axis<double><<<grid_for((size_t)n * n * N), TPB, 0, s>>>(1, n, n, n, N, nullptr, (double*)work1, (double*)work2, 1.0);
+  FEP3M_CL k_mpqT_axis<double><<<grid_for((size_t)n * n * n), TPB, 0, s>>>(2, n, n, n, n, nullptr, (double*)work2, (double*)mu, 4.0 * M_PI);
   return cudaGetLastError();
 }
 

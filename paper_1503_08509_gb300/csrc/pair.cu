@@ -18,6 +18,9 @@
 // o (element units) from the vertex.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+
+#include <cuda_bf16.h>
 
 #include "common.cuh"
 
@@ -26,6 +29,7 @@ namespace fep3m {
 namespace {
 
 constexpr int PT = 256;
+constexpr int PTC = 512;   // threads of the tensor-core screen kernel
 
 __device__ __forceinline__ int wrapn(int i, int n) {
   i %= n;
@@ -166,31 +170,43 @@ __device__ __forceinline__ void warp_singular(int n, int n_sr, T h, int ex, int 
 // e - n_sr).  A(e, o) is then the single value R[beta(o) + lambda(e)].
 constexpr int STAGE_CAP = 1536;   // halo charges staged in shared memory (T = float)
 
-template <class T>
+// CUDA-core layout (TC = false): region 1 holds R first, then the staged
+// charges; A and H chunks follow.  Tensor-core layout (TC = true): 48 KB of
+// operand tiles (1 KB aligned; the staged charges reuse them after the
+// contraction), then R.  Both end with the index tables.
+template <class T, bool TC = false>
 struct Pair3Smem {
+  static constexpr int NT = TC ? PTC : PT;
   __host__ __device__ static int SW(int n_sr) { return 3 * BX + 2 * n_sr - 1; }
   __host__ __device__ static int HW(int n_sr) { return BX + 2 * n_sr; }
   // charges that can be staged: STAGE_CAP floats-worth of float4 (half as many double4)
   __host__ __device__ static int cap() { return STAGE_CAP * 4 / (int)sizeof(T); }
-  // region 1 holds R first, then the staged charges
-  __host__ __device__ static size_t region1(int n_sr) {
+  __host__ __device__ static size_t rbytes(int n_sr) {
     const int sw = SW(n_sr);
-    const size_t r = (size_t)sw * sw * sw * sizeof(T);
-    const size_t stg = (size_t)cap() * sizeof(typename vec4<T>::type);
-    return (((r > stg ? r : stg) + 31) / 32) * 32;
+    return (((size_t)sw * sw * sw * sizeof(T)) + 31) / 32 * 32;
   }
-  static size_t bytes(int n_sr) {
+  __host__ __device__ static size_t region1(int n_sr) {
+    const size_t r = rbytes(n_sr);
+    const size_t stg = (size_t)cap() * sizeof(typename vec4<T>::type);
+    return r > stg ? r : stg;
+  }
+  __host__ __device__ static size_t ints(int n_sr) {
     const int hw = HW(n_sr);
     const int noff = 2 * n_sr + 2, nb = 2 * n_sr + 1, sw = SW(n_sr);
-    const size_t ints = (size_t)hw * hw * hw + 1 + BE + 1 + 1 + PT / 32 + 1 + (size_t)noff * noff * noff +
-                        (size_t)nb * nb + 3 * sw + 3 * hw + 32;
-    return region1(n_sr) + 2 * (size_t)OCH * 64 * sizeof(T) + ints * sizeof(int) + (size_t)cap();
+    return (size_t)hw * hw * hw + 1 + BE + 1 + 1 + NT / 32 + 1 + (size_t)noff * noff * noff + (size_t)nb * nb +
+           3 * sw + 3 * hw + 32;
+  }
+  static constexpr size_t TILES = 6 * 8192;   // three bf16 pieces of A (64 x 64) and of B (64 x 64)
+  static size_t bytes(int n_sr) {
+    if (TC) return 1024 + TILES + rbytes(n_sr) + ints(n_sr) * sizeof(int) + 16;
+    return region1(n_sr) + 2 * (size_t)OCH * 64 * sizeof(T) + ints(n_sr) * sizeof(int) + (size_t)cap();
   }
 };
 
-// exclusive scan of one int per thread over the block (PT threads); returns the
+// exclusive scan of one int per thread over the block (NT threads); returns the
 // thread's prefix and writes the total to *total
-__device__ __forceinline__ int block_scan_excl(int v, int* wsum /* PT/32 + 1 */, int* total) {
+template <int NT>
+__device__ __forceinline__ int block_scan_excl(int v, int* wsum /* NT/32 + 1 */, int* total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int x = v;
   for (int o = 1; o < 32; o <<= 1) {
@@ -201,51 +217,152 @@ __device__ __forceinline__ int block_scan_excl(int v, int* wsum /* PT/32 + 1 */,
   __syncthreads();
   if (threadIdx.x == 0) {
     int a = 0;
-    for (int w = 0; w < PT / 32; ++w) {
+    for (int w = 0; w < NT / 32; ++w) {
       const int t = wsum[w];
       wsum[w] = a;
       a += t;
     }
-    wsum[PT / 32] = a;
+    wsum[NT / 32] = a;
   }
   __syncthreads();
   const int res = wsum[wid] + x - v;
-  *total = wsum[PT / 32];
+  *total = wsum[NT / 32];
   __syncthreads();
   return res;
 }
 
+// ---------------------------------------------------- tensor-core helpers
+// The screen contraction of the tensor-core kernel runs as bf16 x bf16 -> f32
+// MMAs (tcgen05, kind::f16) on three-piece bf16 splits of both operands
+// (x = x0 + x1 + x2, each piece the bf16 rounding of what the previous ones
+// leave), keeping the six products of total order <= 2: every product of two
+// pieces is exact in FP32, the dropped ones are below 2^-24 of the result.
+// Operand tiles are K-major with the 128-byte swizzle: row r of a 64-wide
+// bf16 tile is 128 bytes, its 16-byte chunk c stored at chunk c ^ (r mod 8),
+// rows in 8-row atoms of 1 KB.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__host__ __device__ __forceinline__ uint32_t sw128_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 1 KB between 8-row atoms
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// instruction descriptor: bf16 A and B (K-major), f32 accumulator, M = 128, N = 64
+constexpr uint32_t UMMA_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                   tmem_d),
+               "l"(a), "l"(b), "r"(UMMA_IDESC), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(uint32_t mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// bounded wait for the phase with the given parity; false if it gave up
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(mbar), "r"(parity)
+                 : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void sts128(uint32_t addr, const uint32_t v[4]) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t v[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// three-piece bf16 split of two consecutive values, packed in pairs
+__device__ __forceinline__ void bf16_split2(float xa, float xb, uint32_t& p0, uint32_t& p1, uint32_t& p2) {
+  const __nv_bfloat16 a0 = __float2bfloat16_rn(xa), b0 = __float2bfloat16_rn(xb);
+  const float ra = xa - __bfloat162float(a0), rb = xb - __bfloat162float(b0);
+  const __nv_bfloat16 a1 = __float2bfloat16_rn(ra), b1 = __float2bfloat16_rn(rb);
+  const __nv_bfloat16 a2 = __float2bfloat16_rn(ra - __bfloat162float(a1)),
+                      b2 = __float2bfloat16_rn(rb - __bfloat162float(b1));
+  p0 = (uint32_t)__bfloat16_as_ushort(a0) | ((uint32_t)__bfloat16_as_ushort(b0) << 16);
+  p1 = (uint32_t)__bfloat16_as_ushort(a1) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+  p2 = (uint32_t)__bfloat16_as_ushort(a2) | ((uint32_t)__bfloat16_as_ushort(b2) << 16);
+}
+
 // One CTA per brick of BX x BY x BZ elements: the screen field of every brick
 // element at its 64 nodes (written to Gscr, brick-major) and the singular sums
-// of every target charge in the brick (written to phi_s and E_s).
-template <class T, bool GRAD>
-__global__ void __launch_bounds__(PT) k_pair_screen(int n, int n_sr, T h, const int* __restrict__ start,
-                                                    const int* __restrict__ count,
-                                                    const typename vec4<T>::type* __restrict__ part,
-                                                    const T* __restrict__ Cv, const T* __restrict__ rv,
-                                                    const T* __restrict__ Hw, T* __restrict__ Gscr,
-                                                    double* __restrict__ phi_s, double* __restrict__ E_s) {
+// of every target charge in the brick (written to phi_s and E_s).  TC: the
+// contraction on the tensor cores (FP32 only; Hb holds the table's bf16
+// pieces in the tiles' layout, err receives a bounded wait that gave up),
+// 512 threads and eight per target; otherwise CUDA cores, 256 threads and
+// four per target.
+template <class T, bool GRAD, bool TC>
+__global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, T h, const int* __restrict__ start,
+                                                             const int* __restrict__ count,
+                                                             const typename vec4<T>::type* __restrict__ part,
+                                                             const T* __restrict__ Cv, const T* __restrict__ rv,
+                                                             const T* __restrict__ Hw, const uint4* __restrict__ Hb,
+                                                             T* __restrict__ Gscr, double* __restrict__ phi_s,
+                                                             double* __restrict__ E_s, int* __restrict__ err) {
+  static_assert(!TC || sizeof(T) == 4, "the tensor-core contraction is the FP32 path's");
+  constexpr int NT = TC ? PTC : PT, TPT = TC ? 8 : 4;
   typedef typename vec4<T>::type V4;
+  typedef Pair3Smem<T, TC> SM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nbx = (n + BX - 1) / BX, nby = (n + BY - 1) / BY;
   const int E0x = (blockIdx.x % nbx) * BX, E0y = ((blockIdx.x / nbx) % nby) * BY, E0z = (blockIdx.x / (nbx * nby)) * BZ;
   const int keep = n_sr + 1, noff = 2 * n_sr + 2, no3 = noff * noff * noff;
   const int SW = 3 * BX + 2 * n_sr - 1, SF = BX + 2 * n_sr - 1, HW = BX + 2 * n_sr;
   const int nb = 2 * n_sr + 1, nrow = nb * nb;
-  const size_t r1 = Pair3Smem<T>::region1(n_sr);
-  T* R = (T*)smem_raw;                                    // region 1: R, later the staged charges
-  V4* stg = (V4*)smem_raw;
-  T* A_c = (T*)(smem_raw + r1);                           // [OCH][64], then G [64][64] with H_c
-  T* H_c = A_c + OCH * 64;
-  int* hs = (int*)(H_c + OCH * 64);                       // halo element prefix, HW^3 + 1
+  T *R, *A_c = nullptr, *H_c = nullptr;
+  V4* stg;
+  unsigned char* tiles = nullptr;
+  int* hs;                                                // halo element prefix, HW^3 + 1
+  if (TC) {
+    tiles = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // swizzle atoms on 1 KB
+    stg = (V4*)tiles;                                     // after the contraction
+    R = (T*)(tiles + SM::TILES);
+    hs = (int*)((unsigned char*)R + SM::rbytes(n_sr));
+  } else {
+    const size_t r1 = SM::region1(n_sr);
+    R = (T*)smem_raw;                                     // region 1: R, later the staged charges
+    stg = (V4*)smem_raw;
+    A_c = (T*)(smem_raw + r1);                            // [OCH][64] chunks of A and H
+    H_c = A_c + OCH * 64;
+    hs = (int*)(H_c + OCH * 64);
+  }
   int* epre = hs + HW * HW * HW + 1;                      // BE + 1
   int* flag = epre + BE + 1;
-  int* wsum = flag + 1;                                   // PT/32 + 1 scan scratch
-  int* otab = wsum + PT / 32 + 1;                         // no3: R base index of each offset
+  int* wsum = flag + 1;                                   // NT/32 + 1 scan scratch
+  int* otab = wsum + NT / 32 + 1;                         // no3: R base index of each offset
   int* rtab = otab + no3;                                 // nb^2: halo offset of each (dy, dz) row
   int* wv = rtab + nrow;                                  // 3 x SW wrapped vertex coords
   int* we = wv + 3 * SW;                                  // 3 x HW wrapped halo element coords
-  unsigned char* sxb = (unsigned char*)(we + 3 * HW + 32);   // cap(): halo x index of each staged charge
+  // cap(): halo x index of each staged charge
+  unsigned char* sxb = TC ? tiles + SM::cap() * sizeof(V4) : (unsigned char*)(we + 3 * HW + 32);
+  uint64_t* mbar = (uint64_t*)(((uintptr_t)(we + 3 * HW) + 7) & ~(uintptr_t)7);   // TC only
+  uint32_t* tslot = (uint32_t*)(mbar + 1);
   const int tid = threadIdx.x;
   int ntarget;
   {
@@ -254,23 +371,23 @@ __global__ void __launch_bounds__(PT) k_pair_screen(int n, int n_sr, T h, const 
       const int lx = E0x + (tid % BX), ly = E0y + (tid / BX) % BY, lz = E0z + tid / (BX * BY);
       if (lx < n && ly < n && lz < n) c0 = count[lx + (int64_t)n * (ly + (int64_t)n * lz)];
     }
-    const int pre = block_scan_excl(c0, wsum, &ntarget);
+    const int pre = block_scan_excl<NT>(c0, wsum, &ntarget);
     if (tid < BE) epre[tid] = pre;
     if (tid == 0) epre[BE] = ntarget;
   }
   if (ntarget == 0) return;
   // index tables (no divisions in the hot loops below)
-  for (int o = tid; o < no3; o += PT) {
+  for (int o = tid; o < no3; o += NT) {
     const int ox = o % noff - keep, oy = (o / noff) % noff - keep, oz = o / (noff * noff) - keep;
     const int bx = ox == -keep ? SF : (ox == n_sr ? SF + BX : n_sr - 1 - ox);
     const int by = oy == -keep ? SF : (oy == n_sr ? SF + BX : n_sr - 1 - oy);
     const int bz = oz == -keep ? SF : (oz == n_sr ? SF + BX : n_sr - 1 - oz);
     otab[o] = bx + SW * (by + SW * bz);
   }
-  for (int r = tid; r < nrow; r += PT) rtab[r] = HW * ((r % nb) + HW * (r / nb));
+  for (int r = tid; r < nrow; r += NT) rtab[r] = HW * ((r % nb) + HW * (r / nb));
   {
     const int E0[3] = {E0x, E0y, E0z};
-    for (int i = tid; i < 3 * SW; i += PT) {
+    for (int i = tid; i < 3 * SW; i += NT) {
       const int a = i / SW, sa = i % SW;
       int v;
       if (sa < SF) v = E0[a] + sa - (n_sr - 1);
@@ -278,14 +395,14 @@ __global__ void __launch_bounds__(PT) k_pair_screen(int n, int n_sr, T h, const 
       else v = E0[a] + (sa - SF - BX) - n_sr;
       wv[i] = wrapn(v, n);
     }
-    for (int i = tid; i < 3 * HW; i += PT) {
+    for (int i = tid; i < 3 * HW; i += NT) {
       const int a = i / HW, ha = i % HW;
       we[i] = wrapn(E0[a] - n_sr + ha, n);
     }
   }
   __syncthreads();
   // (1) extended vertex field
-  for (int i = tid; i < SW * SW * SW; i += PT) {
+  for (int i = tid; i < SW * SW * SW; i += NT) {
     const int sx = i % SW, sy = (i / SW) % SW, sz = i / (SW * SW);
     const int tx = sx < SF ? 3 : (sx < SF + BX ? 2 : 1);     // allowed corners (bit0: 0, bit1: 1)
     const int ty = sy < SF ? 3 : (sy < SF + BX ? 2 : 1);
@@ -307,7 +424,109 @@ __global__ void __launch_bounds__(PT) k_pair_screen(int n, int n_sr, T h, const 
     }
     R[i] = val;
   }
-  // (2) screen field: 4 x 4 register tile, per-chunk partial sums added into a total
+  // (2) screen field
+  if constexpr (TC) {
+    // tensor cores: for each chunk of 64 offsets, the three bf16 pieces of A
+    // (64 brick elements x 64 offsets, built from R) and of H (64 nodes x 64
+    // offsets, precomputed) in shared memory; one thread issues the six
+    // piece products per K step of 16 into two TMEM accumulators (hi: the
+    // product of the leading pieces, lo: the other five).  The hi accumulator
+    // holds one chunk at a time and is added into registers after each chunk,
+    // so that no accumulation inside the tensor core spans more than 64 terms
+    // of the leading product.  M = 128: rows 64 .. 127 of each A operand read
+    // the next tile and their results are unused.
+    const uint32_t tl = smem_u32(tiles);
+    if (tid < 32) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tslot)));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) mbar_init(smem_u32(mbar));
+    tc_fence_before();
+    __syncthreads();   // R complete; TMEM address and barrier visible
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const int l = tid & 63, g = tid >> 6;   // this thread's A unit: row l, chunk offsets 8 g .. 8 g + 7
+    const int lam = (l % BX) + SW * (((l / BX) % BY) + SW * (l / (BX * BY)));
+    const uint32_t aoff = sw128_off(l, 8 * g);
+    const int nch = (no3 + 63) / 64;
+    const int warp = tid >> 5, q4 = warp & 3, cg = warp >> 2;   // TMEM lanes 32 q4 .., columns 16 cg ..
+    const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 16 * cg;
+    float hsum[16];   // rows 32 q4 + lane, columns 16 cg .. (warps with q4 < 2)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) hsum[j] = 0.f;
+    bool failed = false;
+    for (int c = 0; c < nch; ++c) {
+      for (int i = tid; i < 1536; i += NT) cp_async16(tl + 24576 + 16 * i, Hb + (size_t)c * 1536 + i);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      uint32_t p0[4], p1[4], p2[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int o = 64 * c + 8 * g + 2 * j;
+        const float xa = o < no3 ? (float)R[otab[o] + lam] : 0.f;
+        const float xb = o + 1 < no3 ? (float)R[otab[o + 1] + lam] : 0.f;
+        bf16_split2(xa, xb, p0[j], p1[j], p2[j]);
+      }
+      sts128(tl + aoff, p0);
+      sts128(tl + 8192 + aoff, p1);
+      sts128(tl + 16384 + aoff, p2);
+      cp_async_wait_all();
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t a = tl + 32 * kk, b = tl + 24576 + 32 * kk;
+          const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+          umma_bf16(tmem, umma_desc(a), umma_desc(b), kk > 0 ? 1u : 0u);         // a0 b0
+          umma_bf16(tmem + 64, umma_desc(a), umma_desc(b + 8192), acc);          // a0 b1
+          umma_bf16(tmem + 64, umma_desc(a + 8192), umma_desc(b), 1u);           // a1 b0
+          umma_bf16(tmem + 64, umma_desc(a), umma_desc(b + 16384), 1u);          // a0 b2
+          umma_bf16(tmem + 64, umma_desc(a + 8192), umma_desc(b + 8192), 1u);   // a1 b1
+          umma_bf16(tmem + 64, umma_desc(a + 16384), umma_desc(b), 1u);          // a2 b0
+        }
+        umma_commit(smem_u32(mbar));
+      }
+      const bool done = mbar_wait(smem_u32(mbar), (uint32_t)(c & 1));
+      if (__syncthreads_or(!done)) {
+        failed = true;
+        break;
+      }
+      tc_fence_after();
+      if (q4 < 2) {
+        uint32_t vh[16];
+        tmem_ld16(ta, vh);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) hsum[j] += __uint_as_float(vh[j]);
+      }
+      tc_fence_before();   // the next chunk's MMAs overwrite hi after the next barrier
+    }
+    if (failed) {
+      if (tid == 0) atomicExch(err, 1);
+      // a last bounded wait on both phases for MMAs still in flight
+      (void)mbar_wait(smem_u32(mbar), 0u);
+      (void)mbar_wait(smem_u32(mbar), 1u);
+    }
+    tc_fence_after();
+    if (!failed && q4 < 2) {
+      uint32_t vl[16];
+      tmem_ld16(ta + 64, vl);
+      tmem_wait_ld();
+      float* drow = (float*)Gscr + (int64_t)blockIdx.x * (BE * 64) + (32 * q4 + (tid & 31)) * 64 + 16 * cg;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        reinterpret_cast<float4*>(drow)[i] = make_float4(hsum[4 * i] + __uint_as_float(vl[4 * i]),
+                                                         hsum[4 * i + 1] + __uint_as_float(vl[4 * i + 1]),
+                                                         hsum[4 * i + 2] + __uint_as_float(vl[4 * i + 2]),
+                                                         hsum[4 * i + 3] + __uint_as_float(vl[4 * i + 3]));
+    }
+    tc_fence_before();
+    __syncthreads();   // every TMEM read done; the tiles are free for the staged charges
+    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+    if (failed) return;
+  } else {
+  // CUDA cores: 4 x 4 register tile, per-chunk partial sums added into a total
   const int eb = tid >> 4, mb = tid & 15;
   T acc[4][4], tot[4][4];
 #pragma unroll
@@ -378,10 +597,11 @@ __global__ void __launch_bounds__(PT) k_pair_screen(int n, int n_sr, T h, const 
       *reinterpret_cast<V4*>(gb + (4 * eb + i) * 64 + 4 * mb) = v;
     }
   }
+  }
   // (3) stage the halo charges if they fit (region 1 is free now)
   const int nh = HW * HW * HW;
   {
-    const int per = (nh + PT - 1) / PT, i0 = tid * per;
+    const int per = (nh + NT - 1) / NT, i0 = tid * per;
     int cnt[8], gid[8];   // per <= 8 for n_sr <= 4 (nh <= 1728)
     int sum = 0;
 #pragma unroll
@@ -397,8 +617,8 @@ __global__ void __launch_bounds__(PT) k_pair_screen(int n, int n_sr, T h, const 
       sum += cnt[k];
     }
     int total;
-    int run = block_scan_excl(sum, wsum, &total);
-    const bool fits = total <= Pair3Smem<T>::cap();
+    int run = block_scan_excl<NT>(sum, wsum, &total);
+    const bool fits = total <= SM::cap();
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const int i = i0 + k;
@@ -422,14 +642,14 @@ __global__ void __launch_bounds__(PT) k_pair_screen(int n, int n_sr, T h, const 
   }
   __syncthreads();
   const bool staged = flag[0] != 0;
-  // (4) four threads per target, each summing the rows r = q, q + 4, ... of the
-  // target's block; a two-step shuffle combines them.  A row (dy, dz) of the
+  // (4) TPT threads per target, each summing the rows r = q, q + TPT, ... of
+  // the target's block; a shuffle tree combines them.  A row (dy, dz) of the
   // block is 2 n_sr + 1 consecutive halo elements, so its staged charges are
   // one run; each row's terms are summed in FP32 and the row sums are added
   // with compensation.
-  const int q = tid & 3;
-  for (int tb = 0; tb < ntarget; tb += PT / 4) {
-    const int k = tb + (tid >> 2);
+  const int q = tid & (TPT - 1);
+  for (int tb = 0; tb < ntarget; tb += NT / TPT) {
+    const int k = tb + tid / TPT;
     const bool valid = k < ntarget;
     T v4[4] = {T(0), T(0), T(0), T(0)};
     int slot = 0;
@@ -451,7 +671,7 @@ __global__ void __launch_bounds__(PT) k_pair_screen(int n, int n_sr, T h, const 
       Acc<T> ps, fx, fy, fz;
       if (staged) {
         const int self = hs[base + n_sr * (1 + HW + HW * HW)] + kk;
-        for (int r = q; r < nrow; r += 4) {
+        for (int r = q; r < nrow; r += TPT) {
           const int h0 = base + rtab[r];
           const int j0 = hs[h0], j1 = hs[h0 + nb];
           const T ddy = T(r % nb - n_sr), ddz = T(r / nb - n_sr);
@@ -480,7 +700,7 @@ __global__ void __launch_bounds__(PT) k_pair_screen(int n, int n_sr, T h, const 
       } else {
         // charges not staged (dense halo): the same rows from global memory,
         // element by element (a row may wrap around the periodic box)
-        for (int r = q; r < nrow; r += 4) {
+        for (int r = q; r < nrow; r += TPT) {
           const int ay = r % nb, az = r / nb;
           const int64_t rowg = (int64_t)n * (we[HW + ly + ay] + (int64_t)n * we[2 * HW + lz + az]);
           const T ddy = T(ay - n_sr), ddz = T(az - n_sr);
@@ -517,10 +737,9 @@ __global__ void __launch_bounds__(PT) k_pair_screen(int n, int n_sr, T h, const 
       v4[3] = fz.get();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], 1);
-      v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], 2);
-    }
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int o = 1; o < TPT; o <<= 1) v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], o);
     if (valid && q == 0) {
       phi_s[slot] = (double)v4[0];
       if (GRAD) {
@@ -533,19 +752,26 @@ __global__ void __launch_bounds__(PT) k_pair_screen(int n, int n_sr, T h, const 
 }
 
 // One CTA per brick, after the mesh solve: G = mesh potential - screen field
-// at the 64 nodes of each non-empty brick element (shared memory), then four
-// threads per target charge each contract 16 of the nodes with the order-3
-// shape functions (and their derivatives) at the charge; the mesh part is
-// added to the singular part the screen kernel left in phi_s / E_s.
+// at the 64 nodes of each non-empty brick element, held in T in shared memory
+// relative to its value G0 at the element's first node (FP64): the shape
+// functions sum to one and their gradients to zero, so G0 enters the
+// potential alone and the rounding to T acts on the variation of G only.  The
+// FP32 path reads the mesh potential as a hi + lo pair of floats (phi_hl) and
+// forms the variation in FP32; the FP64 path reads it in FP64 (phi64).  Then
+// four threads per target charge each contract 16 of the nodes with the
+// order-3 shape functions (and their derivatives) at the charge, and the mesh
+// part is added to the singular part the screen kernel left in phi_s / E_s.
 template <class T, bool GRAD>
 __global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __restrict__ start,
                                                   const int* __restrict__ count,
                                                   const typename vec4<T>::type* __restrict__ part,
-                                                  const T* __restrict__ phi_mesh, const T* __restrict__ Gscr,
+                                                  const double* __restrict__ phi64, const float2* __restrict__ phi_hl,
+                                                  const T* __restrict__ Gscr,
                                                   const int* __restrict__ perm, double* __restrict__ phi_s,
                                                   double* __restrict__ E_s, double* __restrict__ phi_out) {
   typedef typename vec4<T>::type V4;
   __shared__ __align__(32) T G[BE * 64];
+  __shared__ double G0[BE];
   __shared__ int epre[BE + 1];
   __shared__ int wsum[PT / 32 + 1];
   const int nbx = (n + BX - 1) / BX, nby = (n + BY - 1) / BY;
@@ -558,22 +784,37 @@ __global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __r
       const int lx = E0x + (tid % BX), ly = E0y + (tid / BX) % BY, lz = E0z + tid / (BX * BY);
       if (lx < n && ly < n && lz < n) c0 = count[lx + (int64_t)n * (ly + (int64_t)n * lz)];
     }
-    const int pre = block_scan_excl(c0, wsum, &ntarget);
+    const int pre = block_scan_excl<PT>(c0, wsum, &ntarget);
     if (tid < BE) epre[tid] = pre;
     if (tid == 0) epre[BE] = ntarget;
   }
   if (ntarget == 0) return;
   __syncthreads();
-  {
-    const T* gb = Gscr + (int64_t)blockIdx.x * (BE * 64);
-    const int N = 3 * n;
-    for (int i = tid; i < BE * 64; i += PT) {
-      const int l = i >> 6, m = i & 63;
-      if (epre[l + 1] == epre[l]) continue;   // empty (or outside the mesh): never read
-      const int ex = E0x + l % BX, ey = E0y + (l / BX) % BY, ez = E0z + l / (BX * BY);
-      const int gx = 3 * ex + (m & 3), gy = 3 * ey + ((m >> 2) & 3), gz = 3 * ez + (m >> 4);   // < 3n + 3
-      G[i] = phi_mesh[(gx >= N ? gx - N : gx) + (int64_t)N * ((gy >= N ? gy - N : gy) + (int64_t)N * (gz >= N ? gz - N : gz))] -
-             gb[i];
+  const T* gb = Gscr + (int64_t)blockIdx.x * (BE * 64);
+  const int N = 3 * n;
+  // mesh node of node m of brick element l
+  auto node = [&](int l, int m) -> int64_t {
+    const int ex = E0x + l % BX, ey = E0y + (l / BX) % BY, ez = E0z + l / (BX * BY);
+    const int gx = 3 * ex + (m & 3), gy = 3 * ey + ((m >> 2) & 3), gz = 3 * ez + (m >> 4);   // < 3n + 3
+    return (gx >= N ? gx - N : gx) + (int64_t)N * ((gy >= N ? gy - N : gy) + (int64_t)N * (gz >= N ? gz - N : gz));
+  };
+  if (tid < BE && epre[tid + 1] != epre[tid]) {
+    if constexpr (sizeof(T) == 4) {
+      const float2 p0 = phi_hl[node(tid, 0)];
+      G0[tid] = ((double)p0.x + (double)p0.y) - (double)gb[tid * 64];
+    } else {
+      G0[tid] = phi64[node(tid, 0)] - gb[tid * 64];
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < BE * 64; i += PT) {
+    const int l = i >> 6, m = i & 63;
+    if (epre[l + 1] == epre[l]) continue;   // empty (or outside the mesh): never read
+    if constexpr (sizeof(T) == 4) {
+      const float2 p = phi_hl[node(l, m)], p0 = phi_hl[node(l, 0)];
+      G[i] = ((p.x - p0.x) + (p.y - p0.y)) - (gb[i] - gb[l * 64]);
+    } else {
+      G[i] = (phi64[node(l, m)] - gb[i]) - G0[l];
     }
   }
   __syncthreads();
@@ -582,7 +823,7 @@ __global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __r
     const int k = tb + (tid >> 2);
     const bool valid = k < ntarget;
     T v4[4] = {T(0), T(0), T(0), T(0)};
-    int slot = 0;
+    int slot = 0, l = 0;
     if (valid) {
       int lo = 0, hi2 = BE;
       while (hi2 - lo > 1) {
@@ -590,7 +831,7 @@ __global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __r
         if (epre[mid] <= k) lo = mid;
         else hi2 = mid;
       }
-      const int l = lo;
+      l = lo;
       const int ex = E0x + l % BX, ey = E0y + (l / BX) % BY, ez = E0z + l / (BX * BY);
       slot = start[ex + (int64_t)n * (ey + (int64_t)n * ez)] + (k - epre[l]);
       const V4 pt = part[slot];
@@ -626,7 +867,7 @@ __global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __r
       v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], 2);
     }
     if (valid && q == 0) {
-      const double phi = (double)v4[0] * (double)inv_h + phi_s[slot];
+      const double phi = ((double)v4[0] + G0[l]) * (double)inv_h + phi_s[slot];
       phi_s[slot] = phi;
       if (phi_out) phi_out[perm[slot]] = phi;
       if (GRAD) {
@@ -763,13 +1004,14 @@ __global__ void __launch_bounds__(PT) k_adj_gemm(int64_t ne, int o0, int no, con
 // terms are added in increasing o, as the offsets are stored.
 template <class T>
 __global__ void k_adj_gather(int n, int n_sr, int o0, int no, int first, const int* __restrict__ count,
-                             const T* __restrict__ D, T* __restrict__ A) {
+                             const T* __restrict__ D, double* __restrict__ A) {
   const int64_t ne = (int64_t)n * n * n;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= 8 * ne) return;
   const int k = (int)(gid / ne);
   const int64_t s = gid - k * ne;
-  T acc = first ? T(0) : A[s * 8 + k];
+  Acc<T> acc;   // compensated in FP32: the block's terms cancel to a small remainder
+  const double prev = first ? 0.0 : A[s * 8 + k];
   if (count[s] != 0) {
     const int keep = n_sr + 1, noff = 2 * n_sr + 2;
     const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
@@ -784,13 +1026,13 @@ __global__ void k_adj_gather(int n, int n_sr, int o0, int no, int first, const i
         int ex = ex0;
         for (int ux = -n_sr; ux <= n_sr; ++ux) {
           const int oi = oyz + ux;
-          if ((unsigned)oi < (unsigned)no) acc += D[(int64_t)oi * ne + row + ex];
+          if ((unsigned)oi < (unsigned)no) acc.add(D[(int64_t)oi * ne + row + ex]);
           if (++ex == n) ex = 0;
         }
       }
     }
   }
-  A[s * 8 + k] = acc;
+  A[s * 8 + k] = prev + ((double)acc.s - (double)acc.c);
 }
 
 // singular adjoint potential, one warp per charge
@@ -824,8 +1066,8 @@ __global__ void k_final(int64_t N, int n, double inv_h, double gU, double sign,
                         const typename vec4<T>::type* __restrict__ part,
                         const int* __restrict__ perm, const int* __restrict__ cell, const double* __restrict__ w,
                         const double* __restrict__ phi_s, const double* __restrict__ E_s,
-                        const double* __restrict__ psi, const double* __restrict__ gpsi, const T* __restrict__ mu,
-                        const T* __restrict__ A, double* __restrict__ dpos, double* __restrict__ dQ) {
+                        const double* __restrict__ psi, const double* __restrict__ gpsi, const double* __restrict__ mu,
+                        const double* __restrict__ A, double* __restrict__ dpos, double* __restrict__ dQ) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= N) return;
   const int i = perm[t];
@@ -839,7 +1081,7 @@ __global__ void k_final(int64_t N, int n, double inv_h, double gU, double sign,
   for (int k = 0; k < 8; ++k) {
     const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
     const int64_t v = wrapn(ex + kx, n) + (int64_t)n * (wrapn(ey + ky, n) + (int64_t)n * wrapn(ez + kz, n));
-    const double coef = ((double)mu[v] - (double)A[(int64_t)e * 8 + k]) * inv_h;
+    const double coef = (mu[v] - A[(int64_t)e * 8 + k]) * inv_h;
     sQ += wx[kx] * wy[ky] * wz[kz] * coef;
     gx += sg[kx] * wy[ky] * wz[kz] * coef;
     gy += wx[kx] * sg[ky] * wz[kz] * coef;
@@ -892,14 +1134,6 @@ __global__ void k_cast(int64_t n, const A* __restrict__ in, B* __restrict__ out,
 inline int gsz(int64_t n, int t = PT) { return (int)((n + t - 1) / t); }
 
 }  // namespace
-
-// the mesh potential in the working precision of the pair kernel
-cudaError_t pair_prepare(fep3m_ctx* c) {
-  const int64_t nodes = (int64_t)27 * c->n * c->n * c->n;
-  if (c->precision == FEP3M_MIXED)
-    FEP3M_CL k_cast<double, float><<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->phi64, (float*)c->phi_mesh_T, 1.0);
-  return cudaGetLastError();
-}
 
 // ordered singular pairs, non-empty elements and the largest element population
 // per non-empty element e with c0 charges and s charges in its block (nb
@@ -965,39 +1199,94 @@ size_t pair_screen_bytes(const fep3m_ctx* c) {
   return (size_t)pair_bricks(c) * BE * 64 * (c->precision == FEP3M_MIXED ? sizeof(float) : sizeof(double));
 }
 
-template <class T, bool GRAD>
+template <class T, bool GRAD, bool TC>
 static cudaError_t launch_pair_screen(fep3m_ctx* c, const T* Hw, cudaStream_t s) {
-  const size_t smem = Pair3Smem<T>::bytes(c->n_sr);
-  auto kern = k_pair_screen<T, GRAD>;
+  const size_t smem = Pair3Smem<T, TC>::bytes(c->n_sr);
+  auto kern = k_pair_screen<T, GRAD, TC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  FEP3M_CL kern<<<(unsigned)pair_bricks(c), PT, smem, s>>>(
+  FEP3M_CL kern<<<(unsigned)pair_bricks(c), TC ? PTC : PT, smem, s>>>(
       c->n, c->n_sr, (T)c->h, c->start, c->count, (const typename vec4<T>::type*)c->part, (const T*)c->Cv,
-      (const T*)c->rv, Hw, (T*)c->Gscr, c->phi_s, c->E_s);
+      (const T*)c->rv, Hw, (const uint4*)c->Hb, (T*)c->Gscr, c->phi_s, c->E_s, c->iflags + 2);
   return cudaGetLastError();
 }
 
 template <class T, bool GRAD>
-static cudaError_t launch_pair_eval(fep3m_ctx* c, const T* phi_mesh, double* phi_out) {
+static cudaError_t launch_pair_eval(fep3m_ctx* c, double* phi_out) {
   FEP3M_CL k_pair_eval<T, GRAD><<<(unsigned)pair_bricks(c), PT, 0, c->stream>>>(
-      c->n, (T)c->inv_h, c->start, c->count, (const typename vec4<T>::type*)c->part, phi_mesh, (const T*)c->Gscr,
-      c->perm, c->phi_s, c->E_s, phi_out);
+      c->n, (T)c->inv_h, c->start, c->count, (const typename vec4<T>::type*)c->part, c->phi64,
+      (const float2*)c->phi_hl, (const T*)c->Gscr, c->perm, c->phi_s, c->E_s, phi_out);
   return cudaGetLastError();
 }
 
 cudaError_t pair_screen(fep3m_ctx* c, int want_grad, cudaStream_t s) {
-  if (c->precision == FEP3M_MIXED)
-    return want_grad ? launch_pair_screen<float, true>(c, c->Hw32, s) : launch_pair_screen<float, false>(c, c->Hw32, s);
-  return want_grad ? launch_pair_screen<double, true>(c, c->Hw64, s) : launch_pair_screen<double, false>(c, c->Hw64, s);
+  if (c->precision == FEP3M_MIXED) {
+    if (c->Hb)
+      return want_grad ? launch_pair_screen<float, true, true>(c, c->Hw32, s)
+                       : launch_pair_screen<float, false, true>(c, c->Hw32, s);
+    return want_grad ? launch_pair_screen<float, true, false>(c, c->Hw32, s)
+                     : launch_pair_screen<float, false, false>(c, c->Hw32, s);
+  }
+  return want_grad ? launch_pair_screen<double, true, false>(c, c->Hw64, s)
+                   : launch_pair_screen<double, false, false>(c, c->Hw64, s);
+}
+
+// the table's three bf16 pieces per chunk of 64 offsets, in the swizzled
+// K-major layout of the tensor-core tiles: [chunk][piece][node row][offset]
+size_t pair_tc_table_bytes(int n_sr) {
+  const int noff = 2 * n_sr + 2, no3 = noff * noff * noff;
+  return (size_t)((no3 + 63) / 64) * 3 * 8192;
+}
+void pair_tc_table(int n_sr, const double* Hw, uint16_t* out) {
+  const int noff = 2 * n_sr + 2, no3 = noff * noff * noff, nch = (no3 + 63) / 64;
+  auto bits = [](double v) -> uint16_t {   // round to nearest even bf16 (finite v)
+    const float f = (float)v;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+  };
+  auto val = [](uint16_t b) -> double {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return (double)f;
+  };
+  std::memset(out, 0, pair_tc_table_bytes(n_sr));
+  for (int ch = 0; ch < nch; ++ch)
+    for (int m = 0; m < 64; ++m)
+      for (int k = 0; k < 64; ++k) {
+        const int o = 64 * ch + k;
+        double r = o < no3 ? Hw[(size_t)o * 64 + m] : 0.0;
+        for (int p = 0; p < 3; ++p) {
+          const uint16_t b = bits(r);
+          r -= val(b);
+          out[((size_t)(ch * 3 + p) * 8192 + sw128_off(m, k)) / 2] = b;
+        }
+      }
+}
+
+// the FP32 path's mesh potential as hi + lo floats
+__global__ void k_phi_hilo(int64_t n, const double* __restrict__ phi, float2* __restrict__ out) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const double v = phi[g];
+  const float hi = (float)v;
+  out[g] = make_float2(hi, (float)(v - (double)hi));
+}
+
+cudaError_t pair_prepare(fep3m_ctx* c) {
+  if (c->precision == FEP3M_MIXED) {
+    const int64_t nodes = (int64_t)27 * c->n * c->n * c->n;
+    FEP3M_CL k_phi_hilo<<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->phi64, (float2*)c->phi_hl);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t pair_eval(fep3m_ctx* c, double* phi_out, int want_grad) {
-  if (c->precision == FEP3M_MIXED) {
-    const float* pm = (const float*)c->phi_mesh_T;
-    return want_grad ? launch_pair_eval<float, true>(c, pm, phi_out) : launch_pair_eval<float, false>(c, pm, phi_out);
-  }
-  return want_grad ? launch_pair_eval<double, true>(c, c->phi64, phi_out)
-                   : launch_pair_eval<double, false>(c, c->phi64, phi_out);
+  if (c->precision == FEP3M_MIXED)
+    return want_grad ? launch_pair_eval<float, true>(c, phi_out) : launch_pair_eval<float, false>(c, phi_out);
+  return want_grad ? launch_pair_eval<double, true>(c, phi_out) : launch_pair_eval<double, false>(c, phi_out);
 }
 
 cudaError_t sorted_charges(fep3m_ctx* c) {
@@ -1018,7 +1307,7 @@ cudaError_t energy(fep3m_ctx* c, double* U_dev) {
 
 // D-GEMM + gather over offset chunks sized so D stays within a memory budget
 template <class T>
-static cudaError_t screen_adjoint(fep3m_ctx* c, const T* W, const T* Hw, T* A) {
+static cudaError_t screen_adjoint(fep3m_ctx* c, const T* W, const T* Hw, double* A) {
   const int n = c->n;
   const int64_t ne = (int64_t)n * n * n;
   const int no3 = c->noff * c->noff * c->noff;
@@ -1071,7 +1360,7 @@ cudaError_t adjoint_sweeps(fep3m_ctx* c, cudaStream_t s) {
   c->stream = s;   // screen_adjoint issues on c->stream
   cudaError_t e;
   if (c->precision == FEP3M_MIXED) {
-    e = screen_adjoint<float>(c, (const float*)c->W_el, c->Hw32, (float*)c->A_el);
+    e = screen_adjoint<float>(c, (const float*)c->W_el, c->Hw32, (double*)c->A_el);
     if (e == cudaSuccess)
       FEP3M_CL k_pair_adj_warp<float><<<(unsigned)((N + 7) / 8), PT, 0, s>>>(N, n, c->n_sr, (float)c->h, c->start,
                                                          (const float4*)c->part, c->ecoord, c->w_s, c->psi_s, c->gpsi_s);
@@ -1098,8 +1387,8 @@ cudaError_t adjoint_final(fep3m_ctx* c, double gU, double* dpos, double* dQ, dou
   const int64_t N = c->N;
   if (c->precision == FEP3M_MIXED)
     FEP3M_CL k_final<float><<<gsz(N), PT, 0, s>>>(N, c->n, c->inv_h, gU, sign, (const float4*)c->part, c->perm, c->cell,
-                                         c->w_s, c->phi_s, c->E_s, c->psi_s, c->gpsi_s, (const float*)c->mu_v,
-                                         (const float*)c->A_el, dpos, dQ);
+                                         c->w_s, c->phi_s, c->E_s, c->psi_s, c->gpsi_s, (const double*)c->mu_v,
+                                         (const double*)c->A_el, dpos, dQ);
   else
     FEP3M_CL k_final<double><<<gsz(N), PT, 0, s>>>(N, c->n, c->inv_h, gU, sign, (const vec4<double>::type*)c->part, c->perm,
                                           c->cell, c->w_s, c->phi_s, c->E_s, c->psi_s, c->gpsi_s,
