@@ -191,7 +191,7 @@ int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev)
     CK(adjoint_pre(c, 1.0, nullptr, c->aux_stream));
     CK(cudaEventRecord(c->ev_fork2, c->aux_stream));
     CK(cudaStreamWaitEvent(c->sweep_stream, c->ev_fork2, 0));
-    CK(adjoint_sweeps(c, c->sweep_stream));
+    CK(adjoint_sweeps(c, c->sweep_stream, false));   // singular part: from the screen kernel
     CK(cudaEventRecord(c->ev_join2, c->sweep_stream));
     CK(mesh_solve_begin(A, c->g64, c->lam64));
   }
@@ -201,7 +201,7 @@ int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev)
   CK(cudaEventRecord(c->ev_pfork, c->stream));
   CK(cudaStreamWaitEvent(c->pair_stream, c->ev_pfork, 0));
   ev_record(c, 8, c->pair_stream);
-  CK(pair_screen(c, want_grad, c->pair_stream));
+  CK(pair_screen(c, want_grad, c->pair_stream, force_dev != nullptr));
   ev_record(c, 9, c->pair_stream);
   CK(cudaEventRecord(c->ev_pjoin, c->pair_stream));
   CK(mesh_solve_begin(F, c->b64, c->phi64));
@@ -498,7 +498,7 @@ int fep3m_vjp(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double*
   CK(adjoint_pre(c, gU, g, c->aux_stream));
   CK(cudaEventRecord(c->ev_fork2, c->aux_stream));
   CK(cudaStreamWaitEvent(c->sweep_stream, c->ev_fork2, 0));
-  CK(adjoint_sweeps(c, c->sweep_stream));
+  CK(adjoint_sweeps(c, c->sweep_stream, true));
   CK(cudaEventRecord(c->ev_join2, c->sweep_stream));
   CK(mesh_solve(&c->solv[1], c->g64, c->lam64));
   c->stats.adj_iterations = c->solv[1].iters;

@@ -248,13 +248,15 @@ cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev5);
 size_t pair_screen_bytes(const fep3m_ctx* c);
 size_t pair_tc_table_bytes(int n_sr);
 void pair_tc_table(int n_sr, const double* Hw, uint16_t* out);
-cudaError_t pair_screen(fep3m_ctx* c, int want_grad, cudaStream_t s);
+// energy_adjoint: also leave half the singular sums in psi_s / gpsi_s (the
+// singular adjoint of the energy's weights Q / 2)
+cudaError_t pair_screen(fep3m_ctx* c, int want_grad, cudaStream_t s, bool energy_adjoint);
 cudaError_t pair_prepare(fep3m_ctx* c);
 cudaError_t pair_eval(fep3m_ctx* c, double* phi_out, int want_grad);
 // adjoint in three parts: weights and deposit (-> g64), the parts that need
 // lam (vertex adjoint, screen sweep, singular adjoint), and the per-charge assembly
 cudaError_t adjoint_pre(fep3m_ctx* c, double gU, const double* gphi, cudaStream_t s);
-cudaError_t adjoint_sweeps(fep3m_ctx* c, cudaStream_t s);
+cudaError_t adjoint_sweeps(fep3m_ctx* c, cudaStream_t s, bool singular);
 cudaError_t adjoint_vertex(fep3m_ctx* c, cudaStream_t s);
 cudaError_t adjoint_final(fep3m_ctx* c, double gU, double* dpos, double* dQ, double sign, cudaStream_t s);
 cudaError_t energy(fep3m_ctx* c, double* U_dev);

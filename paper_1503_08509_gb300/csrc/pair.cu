@@ -312,7 +312,9 @@ __device__ __forceinline__ void bf16_split2(float xa, float xb, uint32_t& p0, ui
 
 // One CTA per brick of BX x BY x BZ elements: the screen field of every brick
 // element at its 64 nodes (written to Gscr, brick-major) and the singular sums
-// of every target charge in the brick (written to phi_s and E_s).  TC: the
+// of every target charge in the brick (written to phi_s and E_s; with psi,
+// half of them to psi and gpsi as well: the singular adjoint for the weights
+// Q / 2 of the energy, whose kernel 1/r is symmetric).  TC: the
 // contraction on the tensor cores (FP32 only; Hb holds the table's bf16
 // pieces in the tiles' layout, err receives a bounded wait that gave up),
 // 512 threads and eight per target; otherwise CUDA cores, 256 threads and
@@ -324,7 +326,8 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
                                                              const T* __restrict__ Cv, const T* __restrict__ rv,
                                                              const T* __restrict__ Hw, const uint4* __restrict__ Hb,
                                                              T* __restrict__ Gscr, double* __restrict__ phi_s,
-                                                             double* __restrict__ E_s, int* __restrict__ err) {
+                                                             double* __restrict__ E_s, double* __restrict__ psi,
+                                                             double* __restrict__ gpsi, int* __restrict__ err) {
   static_assert(!TC || sizeof(T) == 4, "the tensor-core contraction is the FP32 path's");
   constexpr int NT = TC ? PTC : PT, TPT = TC ? 8 : 4;
   typedef typename vec4<T>::type V4;
@@ -742,10 +745,13 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
       for (int o = 1; o < TPT; o <<= 1) v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], o);
     if (valid && q == 0) {
       phi_s[slot] = (double)v4[0];
+      if (psi) psi[slot] = 0.5 * (double)v4[0];
       if (GRAD) {
-        E_s[3 * slot + 0] = (double)v4[1];
-        E_s[3 * slot + 1] = (double)v4[2];
-        E_s[3 * slot + 2] = (double)v4[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          E_s[3 * slot + a] = (double)v4[1 + a];
+          if (gpsi) gpsi[3 * slot + a] = 0.5 * (double)v4[1 + a];
+        }
       }
     }
   }
@@ -1200,14 +1206,15 @@ size_t pair_screen_bytes(const fep3m_ctx* c) {
 }
 
 template <class T, bool GRAD, bool TC>
-static cudaError_t launch_pair_screen(fep3m_ctx* c, const T* Hw, cudaStream_t s) {
+static cudaError_t launch_pair_screen(fep3m_ctx* c, const T* Hw, cudaStream_t s, bool half) {
   const size_t smem = Pair3Smem<T, TC>::bytes(c->n_sr);
   auto kern = k_pair_screen<T, GRAD, TC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   FEP3M_CL kern<<<(unsigned)pair_bricks(c), TC ? PTC : PT, smem, s>>>(
       c->n, c->n_sr, (T)c->h, c->start, c->count, (const typename vec4<T>::type*)c->part, (const T*)c->Cv,
-      (const T*)c->rv, Hw, (const uint4*)c->Hb, (T*)c->Gscr, c->phi_s, c->E_s, c->iflags + 2);
+      (const T*)c->rv, Hw, (const uint4*)c->Hb, (T*)c->Gscr, c->phi_s, c->E_s, half ? c->psi_s : nullptr,
+      half ? c->gpsi_s : nullptr, c->iflags + 2);
   return cudaGetLastError();
 }
 
@@ -1219,16 +1226,17 @@ static cudaError_t launch_pair_eval(fep3m_ctx* c, double* phi_out) {
   return cudaGetLastError();
 }
 
-cudaError_t pair_screen(fep3m_ctx* c, int want_grad, cudaStream_t s) {
+cudaError_t pair_screen(fep3m_ctx* c, int want_grad, cudaStream_t s, bool energy_adjoint) {
+  const bool half = energy_adjoint && want_grad;
   if (c->precision == FEP3M_MIXED) {
     if (c->Hb)
-      return want_grad ? launch_pair_screen<float, true, true>(c, c->Hw32, s)
-                       : launch_pair_screen<float, false, true>(c, c->Hw32, s);
-    return want_grad ? launch_pair_screen<float, true, false>(c, c->Hw32, s)
-                     : launch_pair_screen<float, false, false>(c, c->Hw32, s);
+      return want_grad ? launch_pair_screen<float, true, true>(c, c->Hw32, s, half)
+                       : launch_pair_screen<float, false, true>(c, c->Hw32, s, half);
+    return want_grad ? launch_pair_screen<float, true, false>(c, c->Hw32, s, half)
+                     : launch_pair_screen<float, false, false>(c, c->Hw32, s, half);
   }
-  return want_grad ? launch_pair_screen<double, true, false>(c, c->Hw64, s)
-                   : launch_pair_screen<double, false, false>(c, c->Hw64, s);
+  return want_grad ? launch_pair_screen<double, true, false>(c, c->Hw64, s, half)
+                   : launch_pair_screen<double, false, false>(c, c->Hw64, s, half);
 }
 
 // the table's three bf16 pieces per chunk of 64 offsets, in the swizzled
@@ -1350,10 +1358,10 @@ cudaError_t adjoint_pre(fep3m_ctx* c, double gU, const double* gphi, cudaStream_
   return cudaGetLastError();
 }
 
-// the screen sweep A and the singular adjoint potential: they need the
-// deposit of the weights (adjoint_pre) but not the adjoint mesh solution, so
-// they run concurrently with the mesh solves
-cudaError_t adjoint_sweeps(fep3m_ctx* c, cudaStream_t s) {
+// the screen sweep A and (with singular) the singular adjoint potential: they
+// need the deposit of the weights (adjoint_pre) but not the adjoint mesh
+// solution, so they run concurrently with the mesh solves
+cudaError_t adjoint_sweeps(fep3m_ctx* c, cudaStream_t s, bool singular) {
   const int n = c->n;
   const int64_t N = c->N;
   cudaStream_t keep = c->stream;
@@ -1361,12 +1369,12 @@ cudaError_t adjoint_sweeps(fep3m_ctx* c, cudaStream_t s) {
   cudaError_t e;
   if (c->precision == FEP3M_MIXED) {
     e = screen_adjoint<float>(c, (const float*)c->W_el, c->Hw32, (double*)c->A_el);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && singular)
       FEP3M_CL k_pair_adj_warp<float><<<(unsigned)((N + 7) / 8), PT, 0, s>>>(N, n, c->n_sr, (float)c->h, c->start,
                                                          (const float4*)c->part, c->ecoord, c->w_s, c->psi_s, c->gpsi_s);
   } else {
     e = screen_adjoint<double>(c, (const double*)c->W_el, c->Hw64, (double*)c->A_el);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && singular)
       FEP3M_CL k_pair_adj_warp<double><<<(unsigned)((N + 7) / 8), PT, 0, s>>>(N, n, c->n_sr, c->h, c->start,
                                                           (const vec4<double>::type*)c->part, c->ecoord, c->w_s,
                                                           c->psi_s, c->gpsi_s);
