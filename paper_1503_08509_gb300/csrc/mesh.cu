@@ -758,75 +758,6 @@ __global__ void k_cheb0(int N, const T* __restrict__ b, T* __restrict__ d, T* __
   x[g] = v;
 }
 
-// ------------------------------------------------------- grid transfers
-// restriction along one axis (transpose of the 1-D prolongation): the input
-// has 2 Nc nodes along `axis` (a template argument, so the index arrays stay
-// in registers), the output Nc; output extents (e0, e1, e2) in (x, y, z);
-// grid (ceil(e0 / blockDim.x), e1, e2)
-template <class T, int axis>
-__global__ void k_restrict_axis(int Nc, int e0, int e1, int e2, const T* __restrict__ in, T* __restrict__ out,
-                                T scale) {
-  PDL_PROLOGUE
-  // the row of P depends on the lane: read it from shared memory, not from
-  // the constant bank (which serialises lanes that read different addresses)
-  __shared__ T Ps[6][4];
-  if (threadIdx.x < 24) Ps[threadIdx.x / 4][threadIdx.x % 4] = Cst<T>::P(threadIdx.x / 4, threadIdx.x % 4);
-  __syncthreads();
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ix >= e0) return;
-  int i[3] = {ix, (int)blockIdx.y, (int)blockIdx.z};
-  int ein[3] = {e0, e1, e2};
-  const int Nf = 2 * Nc;
-  ein[axis] = Nf;
-  const int64_t st[3] = {1, ein[0], (int64_t)ein[0] * ein[1]};
-  const int64_t g = ix + (int64_t)e0 * (i[1] + (int64_t)e1 * i[2]);
-  const int gc = i[axis];
-  i[axis] = 0;
-  const int64_t base = i[0] * st[0] + i[1] * st[1] + i[2] * st[2];
-  const int E = gc / 3, j = gc - 3 * E;
-  T acc = T(0);
-#pragma unroll
-  for (int s = 1; s < 6; ++s) acc += Ps[s][j] * in[base + (6 * E + s) * st[axis]];
-  if (j == 0) {
-    acc += in[base + (6 * E) * st[axis]];   // P[0][0] = 1
-    const int El = E == 0 ? Nc / 3 - 1 : E - 1;
-#pragma unroll
-    for (int s = 1; s < 6; ++s) acc += Ps[s][3] * in[base + (6 * El + s) * st[axis]];
-  }
-  out[g] = scale * acc;
-}
-
-// prolongation along one axis: output has 2 Nc nodes along axis, extents
-// (e0, e1, e2); ADD: out = add + P in; grid (ceil(e0 / blockDim.x), e1, e2)
-template <class T, int axis, bool ADD>
-__global__ void k_prolong_axis(int Nc, int e0, int e1, int e2, const T* __restrict__ in, T* __restrict__ out,
-                               const T* __restrict__ add) {
-  PDL_PROLOGUE
-  __shared__ T Ps[6][4];
-  if (threadIdx.x < 24) Ps[threadIdx.x / 4][threadIdx.x % 4] = Cst<T>::P(threadIdx.x / 4, threadIdx.x % 4);
-  __syncthreads();
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ix >= e0) return;
-  int i[3] = {ix, (int)blockIdx.y, (int)blockIdx.z};
-  int ein[3] = {e0, e1, e2};
-  ein[axis] = Nc;
-  const int64_t st[3] = {1, ein[0], (int64_t)ein[0] * ein[1]};
-  const int64_t g = ix + (int64_t)e0 * (i[1] + (int64_t)e1 * i[2]);
-  const int f = i[axis];
-  i[axis] = 0;
-  const int64_t base = i[0] * st[0] + i[1] * st[1] + i[2] * st[2];
-  const int E = f / 6, s = f - 6 * E;
-  T acc = T(0);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    int gc = 3 * E + j;
-    if (gc >= Nc) gc -= Nc;
-    acc += Ps[s][j] * in[base + gc * st[axis]];
-  }
-  if (ADD) out[g] = add[g] + acc;
-  else out[g] = acc;
-}
-
 // ---------------------------------------------- fused grid transfers (3-D)
 // Restriction (transpose of the prolongation, scaled) and prolongation in one
 // launch each.  A CTA owns RX x RY coarse elements in x and y and marches one
