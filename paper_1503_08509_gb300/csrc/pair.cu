@@ -1016,7 +1016,7 @@ __global__ void k_adj_gather(int n, int n_sr, int o0, int no, int first, const i
   if (gid >= 8 * ne) return;
   const int k = (int)(gid / ne);
   const int64_t s = gid - k * ne;
-  Acc<T> acc;   // compensated in FP32: the block's terms cancel to a small remainder
+  Acc<T> acc;   // compensated over the block's rows: the terms cancel to a small remainder
   const double prev = first ? 0.0 : A[s * 8 + k];
   if (count[s] != 0) {
     const int keep = n_sr + 1, noff = 2 * n_sr + 2;
@@ -1030,11 +1030,13 @@ __global__ void k_adj_gather(int n, int n_sr, int o0, int no, int first, const i
         const int64_t row = (int64_t)n * (wrapn(sy + uy, n) + (int64_t)n * ez);
         const int oyz = noff * ((uy - ky + keep) + noff * oz) - kx + keep - o0;   // o - o0 at ux = 0
         int ex = ex0;
+        T rs = T(0);   // one row of the block in plain FP32, the rows compensated
         for (int ux = -n_sr; ux <= n_sr; ++ux) {
           const int oi = oyz + ux;
-          if ((unsigned)oi < (unsigned)no) acc.add(D[(int64_t)oi * ne + row + ex]);
+          if ((unsigned)oi < (unsigned)no) rs += D[(int64_t)oi * ne + row + ex];
           if (++ex == n) ex = 0;
         }
+        acc.add(rs);
       }
     }
   }
