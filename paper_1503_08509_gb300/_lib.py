@@ -10,6 +10,7 @@ FEP3M_OK, FEP3M_EINVAL, FEP3M_ENOTNEUTRAL, FEP3M_ENOMEM, FEP3M_ECUDA, FEP3M_ENOC
 FEP3M_FP64, FEP3M_MIXED = 0, 1
 FEP3M_NEUTRALIZE = 1
 FEP3M_CUDA_CORE_SCREEN = 2
+FEP3M_MULTIGRID = 4
 
 
 class Config(ctypes.Structure):

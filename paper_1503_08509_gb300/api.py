@@ -40,10 +40,13 @@ class FEP3M:
     precision: 'fp64' or 'mixed' (FP32 pairs and multigrid, FP64 refinement).
     tensor_cores: mixed precision only; False runs the screen-field contraction
     on the FP32 CUDA cores instead of the split-precision bf16 tensor-core MMAs.
+    solver: the FP32 inner solve of the mesh system's iterative refinement,
+    'fdm' (exact, by fast diagonalisation) or 'multigrid' (multigrid-
+    preconditioned CG).
     """
 
     def __init__(self, L, n_el, n_sr=3, precision="fp64", mg_rtol=0.0, mg_max_cycles=0, neutralize=False,
-                 table_pad=0, device=None, stream=None, tensor_cores=True):
+                 table_pad=0, device=None, stream=None, tensor_cores=True, solver="fdm"):
         lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.L, self.n_el, self.n_sr = float(L), int(n_el), int(n_sr)
@@ -52,7 +55,8 @@ class FEP3M:
                           precision=_lib.FEP3M_MIXED if precision == "mixed" else _lib.FEP3M_FP64,
                           mg_rtol=mg_rtol, mg_max_cycles=mg_max_cycles, table_pad=table_pad,
                           flags=(_lib.FEP3M_NEUTRALIZE if neutralize else 0) |
-                          (0 if tensor_cores else _lib.FEP3M_CUDA_CORE_SCREEN))
+                          (0 if tensor_cores else _lib.FEP3M_CUDA_CORE_SCREEN) |
+                          (_lib.FEP3M_MULTIGRID if solver == "multigrid" else 0))
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             h = ctypes.c_void_p()

@@ -100,10 +100,23 @@ struct CoarseSolver {
   float* VT32 = nullptr;      // V^T (row k mode): the forward transform
 };
 
+// Exact FP32 solve of the fine-level system by fast diagonalisation: the
+// periodic Q3 operator is K1 (x) M1 (x) M1 + M1 (x) K1 (x) M1 + M1 (x) M1 (x) K1,
+// so with V^T K1 V = Lambda, V^T M1 V = I its pseudo-inverse is
+// (V (x) V (x) V) (Lambda_i + Lambda_j + Lambda_k)^+ (V (x) V (x) V)^T.
+struct FineFDM {
+  int N = 0;                  // nodes per axis (3 n)
+  float* V32 = nullptr;       // N x N, V[node][mode]
+  float* VT32 = nullptr;      // V^T
+  float* lam32 = nullptr;     // N generalized eigenvalues
+  int null_mode = -1;         // the constant mode (eigenvalue 0)
+};
+
 struct Hierarchy {
   int elem_size = 0;          // 4: the multigrid runs in FP32
   std::vector<Level> lv;
   CoarseSolver coarse;
+  FineFDM fdm;                // set when the fine level is solved by fast diagonalisation
   double lmax = 0;            // estimate of lambda_max(D^-1 K)
   int cheb_degree = 4;
 };
@@ -219,6 +232,7 @@ void element_matrices_q3(double Me[4][4], double Ke[4][4], double Mpq[4][2]);
 void make_stencils(Stencils& st);
 void generalized_eigen(int n, const std::vector<double>& A, const std::vector<double>& B,
                        std::vector<double>& lam, std::vector<double>& V);
+void periodic_eigen(int n, const Stencils& st, std::vector<double>& lam, std::vector<double>& V);
 void build_table(int n_sr, int pad, std::vector<double>& kept);
 double estimate_lmax(const Stencils& st, int n);
 

@@ -959,6 +959,77 @@ static inline int transfer_steps(int nc) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(8, cols * nc / (152 * 4)));
 }
 
+// One pass of the fine-level fast-diagonalisation solve: a dense 1-D transform
+// along the fastest axis of an N^3 array with the axes rotated on output,
+//   out[i R + r] = s(r, i) sum_a in[r N + a] W[a N + i],   R = N^2 rows r,
+// so that three passes contract x, y and z in turn and return to the input's
+// axis order.  SCALE (the third analysis pass): s = 1 / (lam_i + lam_{r mod N}
+// + lam_{r / N}), 0 for the constant mode.  Tiled GEMM: FM rows x FN columns
+// per CTA, FK-deep chunks of the contraction in shared memory, 8 x 4 outputs
+// per thread (rows tr + 16 m, columns 4 tc + c: the stores of a half-warp are
+// 16 consecutive rows of one output column).
+constexpr int FM = 128, FN = 64, FK = 32;
+
+template <bool SCALE>
+__global__ void __launch_bounds__(256) k_fdm_axis(int N, const float* __restrict__ in, const float* __restrict__ W,
+                                                  const float* __restrict__ lam, int null_mode, float* __restrict__ out) {
+  PDL_PROLOGUE
+  __shared__ float As[FK][FM + 1];                  // [k][row]
+  __shared__ __align__(16) float Ws[FK][FN];        // [k][column]
+  const int64_t R = (int64_t)N * N;
+  const int64_t r0 = (int64_t)blockIdx.x * FM;
+  const int i0 = blockIdx.y * FN;
+  const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
+  float acc[8][4];
+#pragma unroll
+  for (int m = 0; m < 8; ++m)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[m][c] = 0.f;
+  for (int k0 = 0; k0 < N; k0 += FK) {
+    for (int e = tid; e < FM * FK; e += 256) {   // lanes along the contraction: coalesced rows
+      const int rr = e / FK, kk = e % FK;
+      const int64_t r = r0 + rr;
+      const int a = k0 + kk;
+      As[kk][rr] = (r < R && a < N) ? in[r * N + a] : 0.f;
+    }
+    for (int e = tid; e < FK * FN; e += 256) {
+      const int kk = e / FN, cc = e % FN;
+      const int a = k0 + kk, i = i0 + cc;
+      Ws[kk][cc] = (a < N && i < N) ? W[(int64_t)a * N + i] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < FK; ++kk) {
+      const float4 w = *reinterpret_cast<const float4*>(&Ws[kk][4 * tc]);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const float a = As[kk][tr + 16 * m];
+        acc[m][0] = fmaf(a, w.x, acc[m][0]);
+        acc[m][1] = fmaf(a, w.y, acc[m][1]);
+        acc[m][2] = fmaf(a, w.z, acc[m][2]);
+        acc[m][3] = fmaf(a, w.w, acc[m][3]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int64_t r = r0 + tr + 16 * m;
+    if (r >= R) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = i0 + 4 * tc + c;
+      if (i >= N) continue;
+      float v = acc[m][c];
+      if (SCALE) {
+        const int j = (int)(r % N), k = (int)(r / N);
+        v = (i == null_mode && j == null_mode && k == null_mode) ? 0.f : v / (lam[i] + lam[j] + lam[k]);
+      }
+      out[(int64_t)i * R + r] = v;
+    }
+  }
+}
+
 // dense 1-D transform along an axis: out[.. i ..] = sum_k A[i][k] in[.. k ..]
 // (A = V^T when transpose), optionally scaled elementwise by s after.
 template <class T>
@@ -1303,6 +1374,23 @@ struct MG {
     launch_pdl(k_dense_axis<T>, gsz, TPB, 0, s, N, 2, V, false, w1, x, nullptr);
   }
 
+  // exact FP32 solve of the fine level, x = K^+ b, by fast diagonalisation:
+  // three analysis passes (the third scaled by the inverse eigenvalue sums)
+  // and three synthesis passes; w1, w2 are N^3 scratch
+  void fdm_solve(const T* b, T* x, T* w1, T* w2) {
+    static_assert(std::is_same<T, float>::value, "the inner solve runs in FP32");
+    const FineFDM& f = H.fdm;
+    const int N = f.N;
+    cudaStream_t s = c->stream;
+    const dim3 g((unsigned)(((int64_t)N * N + FM - 1) / FM), (unsigned)((N + FN - 1) / FN));
+    launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, b, f.V32, f.lam32, f.null_mode, w1);
+    launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, (const T*)w1, f.V32, f.lam32, f.null_mode, w2);
+    launch_pdl(k_fdm_axis<true>, g, 256, 0, s, N, (const T*)w2, f.V32, f.lam32, f.null_mode, w1);
+    launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, (const T*)w1, f.VT32, f.lam32, f.null_mode, w2);
+    launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, (const T*)w2, f.VT32, f.lam32, f.null_mode, w1);
+    launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, (const T*)w1, f.VT32, f.lam32, f.null_mode, x);
+  }
+
   // approximately solve A_l x = b on level l (x overwritten)
   // dot: accumulate b.x of the result (fused into the last smoothing step)
   void vcycle(int l, const T* b, T* x, const ApplyDot* dot = nullptr) {
@@ -1515,6 +1603,26 @@ static cudaError_t mg_setup(Solver* c) {
   cudaMemcpy(cs.VT32, VT32.data(), VT32.size() * 4, cudaMemcpyHostToDevice);
   cudaMemcpy(cs.Dinv32, D32.data(), D32.size() * 4, cudaMemcpyHostToDevice);
   H.lmax = estimate_lmax(c->st, 6);
+  if (!(c->cfg.flags & FEP3M_MULTIGRID)) {
+    // fine level by fast diagonalisation (block-Fourier eigenbasis, O(N^2) on the host)
+    FineFDM& f = H.fdm;
+    const int Nf = 3 * c->n;
+    std::vector<double> lamf, Vf;
+    periodic_eigen(c->n, c->st, lamf, Vf);
+    f.null_mode = 0;
+    for (int i = 1; i < Nf; ++i)
+      if (std::fabs(lamf[i]) < std::fabs(lamf[f.null_mode])) f.null_mode = i;
+    std::vector<float> Vf32(Vf.begin(), Vf.end()), VTf32((size_t)Nf * Nf), lf32(lamf.begin(), lamf.end());
+    for (int i = 0; i < Nf; ++i)
+      for (int k = 0; k < Nf; ++k) VTf32[(size_t)k * Nf + i] = (float)Vf[(size_t)i * Nf + k];
+    if ((e = cudaMalloc(&f.V32, Vf32.size() * 4)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.VT32, VTf32.size() * 4)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.lam32, lf32.size() * 4)) != cudaSuccess) return e;
+    cudaMemcpy(f.V32, Vf32.data(), Vf32.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(f.VT32, VTf32.data(), VTf32.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(f.lam32, lf32.data(), lf32.size() * 4, cudaMemcpyHostToDevice);
+    f.N = Nf;
+  }
   return cudaGetLastError();
 }
 
@@ -1525,6 +1633,11 @@ static void mg_free(Solver* c) {
       if (p) cudaFree(p);
   }
   c->mg.lv.clear();
+  FineFDM& f = c->mg.fdm;
+  if (f.V32) cudaFree(f.V32);
+  if (f.VT32) cudaFree(f.VT32);
+  if (f.lam32) cudaFree(f.lam32);
+  f = FineFDM();
   CoarseSolver& cs = c->mg.coarse;
   if (cs.VT32) cudaFree(cs.VT32);
   if (cs.V32) cudaFree(cs.V32);
@@ -1666,9 +1779,12 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
   }
   double rr = bb;
   int step = 0;
+  const bool fdm = c->mg.fdm.N > 0;
   for (step = 0; step < maxout; ++step) {
     double inner_res = 0;
-    int it = mg.pcg(r32, e32, (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], 1e-5, 30, &inner_res);
+    int it = 1;
+    if (fdm) mg.fdm_solve(r32, e32, (float*)sb[0], (float*)sb[1]);
+    else it = mg.pcg(r32, e32, (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], 1e-5, 30, &inner_res);
     *iters += it;
     *k_inner_max = std::max(*k_inner_max, it);
     refine_update(c, phi, e32);
@@ -1704,7 +1820,8 @@ static cudaError_t solve_fixed(Solver* c) {
   refine_setup(c, c->in64, phi, r32);
   reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 10);
   for (int step = 0; step < c->plan_kout; ++step) {
-    mg.pcg_fixed(r32, e32, (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], c->plan_kin);
+    if (c->mg.fdm.N > 0) mg.fdm_solve(r32, e32, (float*)sb[0], (float*)sb[1]);
+    else mg.pcg_fixed(r32, e32, (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], c->plan_kin);
     refine_update(c, phi, e32);
     cudaError_t e = refine_resid(c, phi, r32);
     if (e != cudaSuccess) return e;

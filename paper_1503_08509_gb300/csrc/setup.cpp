@@ -186,6 +186,75 @@ void generalized_eigen(int n, const std::vector<double>& A, const std::vector<do
     }
 }
 
+// Generalized eigenpairs K1 v = lam M1 v of the periodic 1-D order-3 matrices
+// on n elements (N = 3 n nodes), V M1-orthonormal (V^T M1 V = I), V[g][mode].
+// Both matrices are block circulant (3 x 3 blocks B_d, d = -1, 0, 1, one per
+// element), so the span of {cos(theta e) w, sin(theta e) w : w in R^3},
+// theta = 2 pi k / n, is invariant under both: per wavenumber k the problem
+// reduces to a 6 x 6 one (3 x 3 for k = 0 and k = n / 2) in the coefficients
+// (c, s) of u_e = c cos(theta e) + s sin(theta e), with the matrices
+//   (n / 2) [[Sc, Ss], [-Ss, Sc]],  Sc = sum_d B_d cos(theta d),
+//   Ss = sum_d B_d sin(theta d)  (Sc symmetric, Ss antisymmetric),
+// and (n) Sc for the real modes.  O(N^2) work in all, against O(N^3) for a
+// dense eigensolver of the N x N pencil.
+void periodic_eigen(int n, const Stencils& st, std::vector<double>& lam, std::vector<double>& V) {
+  const int N = 3 * n;
+  double BK[3][3][3] = {}, BM[3][3][3] = {};   // [d + 1][tau][tau']
+  for (int tau = 0; tau < 3; ++tau)
+    for (int j = -3; j <= 3; ++j) {
+      const int t = tau + j;
+      const int d = t < 0 ? -1 : (t >= 3 ? 1 : 0);
+      const int tp = t - 3 * d;
+      BK[d + 1][tau][tp] += st.K[tau][j + 3];
+      BM[d + 1][tau][tp] += st.M[tau][j + 3];
+    }
+  lam.clear();
+  V.assign((size_t)N * N, 0.0);
+  int mode = 0;
+  for (int k = 0; 2 * k <= n; ++k) {
+    const double th = 2.0 * M_PI * k / n;
+    const bool real = k == 0 || 2 * k == n;
+    const int m = real ? 3 : 6;
+    std::vector<double> A((size_t)m * m, 0.0), B((size_t)m * m, 0.0);
+    double Kc[3][3] = {}, Ks[3][3] = {}, Mc[3][3] = {}, Ms[3][3] = {};
+    for (int d = -1; d <= 1; ++d)
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          Kc[a][b] += BK[d + 1][a][b] * std::cos(th * d);
+          Ks[a][b] += BK[d + 1][a][b] * std::sin(th * d);
+          Mc[a][b] += BM[d + 1][a][b] * std::cos(th * d);
+          Ms[a][b] += BM[d + 1][a][b] * std::sin(th * d);
+        }
+    const double w = real ? (double)n : 0.5 * n;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        A[(size_t)a * m + b] = w * Kc[a][b];
+        B[(size_t)a * m + b] = w * Mc[a][b];
+        if (!real) {
+          A[(size_t)a * m + 3 + b] = w * Ks[a][b];
+          A[(size_t)(3 + a) * m + b] = -w * Ks[a][b];
+          A[(size_t)(3 + a) * m + 3 + b] = w * Kc[a][b];
+          B[(size_t)a * m + 3 + b] = w * Ms[a][b];
+          B[(size_t)(3 + a) * m + b] = -w * Ms[a][b];
+          B[(size_t)(3 + a) * m + 3 + b] = w * Mc[a][b];
+        }
+      }
+    std::vector<double> l6, v6;
+    generalized_eigen(m, A, B, l6, v6);
+    for (int q = 0; q < m; ++q, ++mode) {
+      lam.push_back(l6[q]);
+      for (int e = 0; e < n; ++e) {
+        const double ce = std::cos(th * e), se = std::sin(th * e);
+        for (int tau = 0; tau < 3; ++tau) {
+          double v = v6[(size_t)tau * m + q] * ce;
+          if (!real) v += v6[(size_t)(3 + tau) * m + q] * se;
+          V[(size_t)(3 * e + tau) * N + mode] = v;
+        }
+      }
+    }
+  }
+}
+
 namespace {
 
 // y = A x along one axis of an N^3 array (index ix + N iy + N^2 iz), A dense N x N.
