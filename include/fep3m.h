@@ -57,8 +57,10 @@ enum { FEP3M_FP64 = 0, FEP3M_MIXED = 1 };
 
 /* flags */
 #define FEP3M_NEUTRALIZE 1u    /* accept non-neutral input: uniform background */
-#define FEP3M_CUDA_CORE_SCREEN 2u  /* MIXED: screen-field contraction on the FP32
-                                      CUDA cores instead of the tensor cores    */
+#define FEP3M_CUDA_CORES 2u    /* the split-precision contractions (screen field
+                                  of the MIXED pair kernel, transforms of the
+                                  fast-diagonalisation solve) on the FP32 CUDA
+                                  cores instead of the tensor cores             */
 #define FEP3M_MULTIGRID 4u     /* inner mesh solver: multigrid-preconditioned CG
                                   instead of the exact fast-diagonalisation
                                   solve (both inside the same refinement)       */
@@ -82,7 +84,7 @@ typedef struct {
   int mg_max_cycles;   /* cap on refinement sweeps; 0 -> 10                      */
   int table_pad;       /* Dirichlet box margin, elements, beyond the kept table;
                           0 -> 4                                                 */
-  unsigned flags;      /* FEP3M_NEUTRALIZE, FEP3M_CUDA_CORE_SCREEN,
+  unsigned flags;      /* FEP3M_NEUTRALIZE, FEP3M_CUDA_CORES,
                           FEP3M_MULTIGRID                                        */
 } fep3m_config;
 

@@ -9,7 +9,7 @@ FEP3M_OK, FEP3M_EINVAL, FEP3M_ENOTNEUTRAL, FEP3M_ENOMEM, FEP3M_ECUDA, FEP3M_ENOC
     0, -1, -2, -3, -4, -5, -6, -7
 FEP3M_FP64, FEP3M_MIXED = 0, 1
 FEP3M_NEUTRALIZE = 1
-FEP3M_CUDA_CORE_SCREEN = 2
+FEP3M_CUDA_CORES = 2
 FEP3M_MULTIGRID = 4
 
 

@@ -38,8 +38,9 @@ class FEP3M:
     """One FE-P3M context: mesh, screen tables and multigrid for a periodic cube.
 
     precision: 'fp64' or 'mixed' (FP32 pairs and multigrid, FP64 refinement).
-    tensor_cores: mixed precision only; False runs the screen-field contraction
-    on the FP32 CUDA cores instead of the split-precision bf16 tensor-core MMAs.
+    tensor_cores: False runs the split-precision contractions (the mixed pair
+    kernel's screen field, the fast-diagonalisation transforms) on the FP32
+    CUDA cores instead of as bf16 tensor-core MMAs.
     solver: the FP32 inner solve of the mesh system's iterative refinement,
     'fdm' (exact, by fast diagonalisation) or 'multigrid' (multigrid-
     preconditioned CG).
@@ -55,7 +56,7 @@ class FEP3M:
                           precision=_lib.FEP3M_MIXED if precision == "mixed" else _lib.FEP3M_FP64,
                           mg_rtol=mg_rtol, mg_max_cycles=mg_max_cycles, table_pad=table_pad,
                           flags=(_lib.FEP3M_NEUTRALIZE if neutralize else 0) |
-                          (0 if tensor_cores else _lib.FEP3M_CUDA_CORE_SCREEN) |
+                          (0 if tensor_cores else _lib.FEP3M_CUDA_CORES) |
                           (_lib.FEP3M_MULTIGRID if solver == "multigrid" else 0))
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -33,7 +33,7 @@ def flags():
 def _compile(src):
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     srcp = os.path.join(CSRC, src)
-    deps = [srcp, os.path.join(CSRC, "common.cuh"), os.path.join(ROOT, "include", "fep3m.h")]
+    deps = [srcp, os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "tc.cuh"), os.path.join(ROOT, "include", "fep3m.h")]
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj, ""
     lang = ["-x", "cu"] if src.endswith(".cu") else ["-x", "c++"]

@@ -335,7 +335,7 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
   if ((st = from_cuda(dalloc(&c->Hw32, Hw.size()))) != FEP3M_OK) return fail(st);
   cudaMemcpy(c->Hw64, Hw.data(), Hw.size() * 8, cudaMemcpyHostToDevice);
   cudaMemcpy(c->Hw32, Hw32.data(), Hw32.size() * 4, cudaMemcpyHostToDevice);
-  if (c->precision == FEP3M_MIXED && !(cfg->flags & FEP3M_CUDA_CORE_SCREEN)) {
+  if (c->precision == FEP3M_MIXED && !(cfg->flags & FEP3M_CUDA_CORES)) {
     // bf16 pieces of the table for the tensor-core screen contraction
     std::vector<uint16_t> hb(pair_tc_table_bytes(c->n_sr) / 2);
     pair_tc_table(c->n_sr, Hw.data(), hb.data());

@@ -110,6 +110,12 @@ struct FineFDM {
   float* VT32 = nullptr;      // V^T
   float* lam32 = nullptr;     // N generalized eigenvalues
   int null_mode = -1;         // the constant mode (eigenvalue 0)
+  // tensor-core transforms: bf16 pieces of V^T (analysis) and V (synthesis)
+  // per column tile of nt modes and chunk of 64 nodes (unset: CUDA cores)
+  void* BpF = nullptr;
+  void* BpI = nullptr;
+  int nt = 0, ntile = 0;
+  int* err = nullptr;         // device flag: a bounded wait gave up
 };
 
 struct Hierarchy {

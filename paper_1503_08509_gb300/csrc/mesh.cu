@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace fep3m {
 
@@ -1030,6 +1031,129 @@ __global__ void __launch_bounds__(256) k_fdm_axis(int N, const float* __restrict
   }
 }
 
+// The same pass on the tensor cores: per CTA 128 rows r and the nt columns i
+// of one column tile, the contraction over a in chunks of 64 as tcgen05
+// bf16 MMAs (M = 128, N = nt) on three-piece splits of both operands (six
+// piece products, two TMEM accumulators: the leading product, the other
+// five).  A (the input rows) is split in the kernel into 128-byte-swizzled
+// K-major tiles; B = W^T, B[i][a] = W[a][i], comes split and laid out in
+// advance (Bp: [column tile][chunk][piece][nt rows][64], zero outside N).
+// The epilogue reads one row per thread from TMEM, so a warp's stores of one
+// column are 32 consecutive rows.  err: a bounded wait that gave up.
+constexpr int FT_THREADS = 256;
+
+template <bool SCALE>
+__global__ void __launch_bounds__(FT_THREADS) k_fdm_tc(int N, int nt, const float* __restrict__ in,
+                                                        const uint4* __restrict__ Bp, const float* __restrict__ lam,
+                                                        int null_mode, float* __restrict__ out, int* __restrict__ err) {
+  PDL_PROLOGUE
+  using namespace tc;
+  extern __shared__ __align__(16) unsigned char fsm[];
+  unsigned char* tiles = fsm + ((1024u - (smem_u32(fsm) & 1023u)) & 1023u);
+  const uint32_t tl = smem_u32(tiles), tb = tl + 3 * 16384;   // A pieces (128 x 64 each), then B pieces (nt x 64)
+  const uint32_t bpiece = (uint32_t)nt * 128;
+  uint64_t* mbar = (uint64_t*)(tiles + 3 * 16384 + 3 * bpiece);
+  uint32_t* tslot = (uint32_t*)(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t R = (int64_t)N * N;
+  const int64_t r0 = (int64_t)blockIdx.x * 128;
+  const int n0 = blockIdx.y * nt;
+  const int kc = (N + 63) / 64;
+  uint32_t ncols = 32;
+  while (ncols < 2u * (uint32_t)nt) ncols <<= 1;
+  const uint32_t lo_off = ncols / 2, idesc = umma_idesc((uint32_t)nt);
+  if (warp == 0) tmem_alloc(smem_u32(tslot), ncols);
+  if (tid == 0) mbar_init(smem_u32(mbar));
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint4* bsrc = Bp + (size_t)blockIdx.y * kc * 3 * (bpiece / 16);
+  bool failed = false;
+  for (int c = 0; c < kc; ++c) {
+    for (int i = tid; i < 3 * (int)(bpiece / 16); i += FT_THREADS) cp_async16(tb + 16 * i, bsrc + (size_t)c * 3 * (bpiece / 16) + i);
+    cp_async_commit();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {   // 128 rows x 8 groups of 8: four per thread, eight threads per row
+      const int u = tid + FT_THREADS * j, row = u >> 3, g = u & 7;
+      const int64_t r = r0 + row;
+      const int a0 = 64 * c + 8 * g;
+      float x[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) x[t] = (r < R && a0 + t < N) ? in[r * N + a0 + t] : 0.f;
+      uint32_t p0[4], p1[4], p2[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) bf16_split2(x[2 * t], x[2 * t + 1], p0[t], p1[t], p2[t]);
+      const uint32_t off = sw128_off(row, 8 * g);
+      sts128(tl + off, p0);
+      sts128(tl + 16384 + off, p1);
+      sts128(tl + 32768 + off, p2);
+    }
+    cp_async_wait_all();
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t a = tl + 32 * kk, b = tb + 32 * kk;
+        const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+        umma_bf16(tmem, umma_desc(a), umma_desc(b), idesc, acc);                                 // a0 b0
+        umma_bf16(tmem + lo_off, umma_desc(a), umma_desc(b + bpiece), idesc, acc);               // a0 b1
+        umma_bf16(tmem + lo_off, umma_desc(a + 16384), umma_desc(b), idesc, 1u);                 // a1 b0
+        umma_bf16(tmem + lo_off, umma_desc(a), umma_desc(b + 2 * bpiece), idesc, 1u);            // a0 b2
+        umma_bf16(tmem + lo_off, umma_desc(a + 16384), umma_desc(b + bpiece), idesc, 1u);        // a1 b1
+        umma_bf16(tmem + lo_off, umma_desc(a + 32768), umma_desc(b), idesc, 1u);                 // a2 b0
+      }
+      umma_commit(smem_u32(mbar));
+    }
+    const bool done = mbar_wait(smem_u32(mbar), (uint32_t)(c & 1));
+    if (__syncthreads_or(!done)) {
+      failed = true;
+      break;
+    }
+  }
+  if (failed) {
+    if (tid == 0) atomicExch(err, 1);
+    (void)mbar_wait(smem_u32(mbar), 0u);
+    (void)mbar_wait(smem_u32(mbar), 1u);
+  }
+  tc_fence_after();
+  if (!failed) {
+    const int q4 = warp & 3;
+    const int64_t r = r0 + 32 * q4 + (tid & 31);
+    float djk = 0.f;
+    bool jk_null = false;
+    if (SCALE && r < R) {
+      const int j = (int)(r % N), k = (int)(r / N);
+      djk = lam[j] + lam[k];
+      jk_null = j == null_mode && k == null_mode;
+    }
+    for (int grp = warp >> 2; 16 * grp < nt; grp += 2) {
+      uint32_t vh[16], vl[16];
+      const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 16 * grp;
+      tmem_ld16(ta, vh);
+      tmem_ld16(ta + lo_off, vl);
+      tmem_wait_ld();
+      if (r < R) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int i = n0 + 16 * grp + t;
+          if (i >= N || 16 * grp + t >= nt) continue;
+          float v = __uint_as_float(vh[t]) + __uint_as_float(vl[t]);
+          if (SCALE) v = (jk_null && i == null_mode) ? 0.f : v * __frcp_rn(lam[i] + djk);
+          out[(int64_t)i * R + r] = v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+static size_t fdm_tc_smem(int nt) { return 1024 + 3 * 16384 + (size_t)3 * nt * 128 + 16; }
+
 // dense 1-D transform along an axis: out[.. i ..] = sum_k A[i][k] in[.. k ..]
 // (A = V^T when transpose), optionally scaled elementwise by s after.
 template <class T>
@@ -1382,6 +1506,19 @@ struct MG {
     const FineFDM& f = H.fdm;
     const int N = f.N;
     cudaStream_t s = c->stream;
+    if (f.BpF) {
+      const dim3 g((unsigned)(((int64_t)N * N + 127) / 128), (unsigned)f.ntile);
+      const size_t sm = fdm_tc_smem(f.nt);
+      const uint4* F = (const uint4*)f.BpF;
+      const uint4* I = (const uint4*)f.BpI;
+      launch_pdl(k_fdm_tc<false>, g, FT_THREADS, sm, s, N, f.nt, b, F, f.lam32, f.null_mode, w1, f.err);
+      launch_pdl(k_fdm_tc<false>, g, FT_THREADS, sm, s, N, f.nt, (const T*)w1, F, f.lam32, f.null_mode, w2, f.err);
+      launch_pdl(k_fdm_tc<true>, g, FT_THREADS, sm, s, N, f.nt, (const T*)w2, F, f.lam32, f.null_mode, w1, f.err);
+      launch_pdl(k_fdm_tc<false>, g, FT_THREADS, sm, s, N, f.nt, (const T*)w1, I, f.lam32, f.null_mode, w2, f.err);
+      launch_pdl(k_fdm_tc<false>, g, FT_THREADS, sm, s, N, f.nt, (const T*)w2, I, f.lam32, f.null_mode, w1, f.err);
+      launch_pdl(k_fdm_tc<false>, g, FT_THREADS, sm, s, N, f.nt, (const T*)w1, I, f.lam32, f.null_mode, x, f.err);
+      return;
+    }
     const dim3 g((unsigned)(((int64_t)N * N + FM - 1) / FM), (unsigned)((N + FN - 1) / FN));
     launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, b, f.V32, f.lam32, f.null_mode, w1);
     launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, (const T*)w1, f.V32, f.lam32, f.null_mode, w2);
@@ -1622,6 +1759,45 @@ static cudaError_t mg_setup(Solver* c) {
     cudaMemcpy(f.VT32, VTf32.data(), VTf32.size() * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(f.lam32, lf32.data(), lf32.size() * 4, cudaMemcpyHostToDevice);
     f.N = Nf;
+    if (!(c->cfg.flags & FEP3M_CUDA_CORES)) {
+      // column tiles of nt modes (a multiple of 16, <= 128), enough CTAs to cover the SMs
+      const int64_t rt = ((int64_t)Nf * Nf + 127) / 128;
+      int ntile = std::max<int>((Nf + 127) / 128, (int)((148 + rt - 1) / rt));
+      const int nt = ((Nf + ntile - 1) / ntile + 15) / 16 * 16;
+      ntile = (Nf + nt - 1) / nt;
+      const int kc = (Nf + 63) / 64;
+      const size_t per = (size_t)3 * nt * 64;   // bf16 values per (tile, chunk)
+      std::vector<uint16_t> bf((size_t)ntile * kc * per), bi((size_t)ntile * kc * per);
+      for (int t = 0; t < ntile; ++t)
+        for (int ch = 0; ch < kc; ++ch)
+          for (int ii = 0; ii < nt; ++ii)
+            for (int k = 0; k < 64; ++k) {
+              const int i = t * nt + ii, a = 64 * ch + k;
+              const bool in = i < Nf && a < Nf;
+              uint16_t pf[3] = {0, 0, 0}, pi[3] = {0, 0, 0};
+              if (in) {
+                tc::bf16_pieces(Vf[(size_t)a * Nf + i], pf);   // analysis: B[i][a] = V[a][i]
+                tc::bf16_pieces(Vf[(size_t)i * Nf + a], pi);   // synthesis: B[i][a] = V[i][a]
+              }
+              for (int p = 0; p < 3; ++p) {
+                const size_t o = ((size_t)(t * kc + ch) * 3 + p) * nt * 64 + tc::sw128_off(ii, k) / 2;
+                bf[o] = pf[p];
+                bi[o] = pi[p];
+              }
+            }
+      if ((e = cudaMalloc(&f.BpF, bf.size() * 2)) != cudaSuccess) return e;
+      if ((e = cudaMalloc(&f.BpI, bi.size() * 2)) != cudaSuccess) return e;
+      cudaMemcpy(f.BpF, bf.data(), bf.size() * 2, cudaMemcpyHostToDevice);
+      cudaMemcpy(f.BpI, bi.data(), bi.size() * 2, cudaMemcpyHostToDevice);
+      f.nt = nt;
+      f.ntile = ntile;
+      const int sm = (int)fdm_tc_smem(nt);
+      if ((e = cudaFuncSetAttribute(k_fdm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess ||
+          (e = cudaFuncSetAttribute(k_fdm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
+        return e;
+      if ((e = cudaMalloc(&f.err, sizeof(int))) != cudaSuccess) return e;
+      cudaMemset(f.err, 0, sizeof(int));
+    }
   }
   return cudaGetLastError();
 }
@@ -1634,6 +1810,9 @@ static void mg_free(Solver* c) {
   }
   c->mg.lv.clear();
   FineFDM& f = c->mg.fdm;
+  if (f.BpF) cudaFree(f.BpF);
+  if (f.BpI) cudaFree(f.BpI);
+  if (f.err) cudaFree(f.err);
   if (f.V32) cudaFree(f.V32);
   if (f.VT32) cudaFree(f.VT32);
   if (f.lam32) cudaFree(f.lam32);
