@@ -271,7 +271,7 @@ void fep3m_destroy(fep3m_ctx* c) {
   if (!c) return;
   free_particles(c);
   void* p[] = {c->Hw64, c->Hw32, c->count, c->start, c->fill, c->scan_tmp, c->C, c->rv, c->Cv, c->b64, c->phi64,
-               c->res64, c->g64, c->lam64, c->scal, c->iflags, c->phi_hl, c->W_el, c->A_el, c->mu_v, c->Gscr, c->Hb,
+               c->res64, c->g64, c->lam64, c->scal, c->iflags, c->phi_hl, c->W_el, c->A_el, c->mu_v, c->Gscr, c->Hb, c->HbA,
                c->red_tmp, c->red_counter, c->D_adj};
   for (void* q : p) dfree(q);
   fep3m::solver_destroy(&c->solv[0]);
@@ -341,6 +341,11 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
     pair_tc_table(c->n_sr, Hw.data(), hb.data());
     if ((st = from_cuda(cudaMalloc(&c->Hb, hb.size() * 2))) != FEP3M_OK) return fail(st);
     cudaMemcpy(c->Hb, hb.data(), hb.size() * 2, cudaMemcpyHostToDevice);
+    std::vector<uint16_t> ha(pair_adj_table_bytes(c->n_sr) / 2);
+    pair_adj_table(c->n_sr, Hw.data(), ha.data());
+    if ((st = from_cuda(cudaMalloc(&c->HbA, ha.size() * 2))) != FEP3M_OK) return fail(st);
+    cudaMemcpy(c->HbA, ha.data(), ha.size() * 2, cudaMemcpyHostToDevice);
+    if ((st = from_cuda(tc_rows_prepare(128))) != FEP3M_OK) return fail(st);
   }
   if ((st = from_cuda(cudaMallocHost(&c->host_err, sizeof(int)))) != FEP3M_OK) return fail(st);
   *c->host_err = 0;

@@ -215,6 +215,7 @@ struct fep3m_ctx {
   void* mu_v = nullptr;          // n^3 vertex adjoint (FP64)
   void* Gscr = nullptr;          // screen field at each brick element's 64 nodes, bricks * 4096 (T)
   void* Hb = nullptr;            // bf16 pieces of the table for the tensor-core contraction (MIXED)
+  void* HbA = nullptr;           // the same for the screen adjoint's contraction (MIXED)
   int* host_err = nullptr;       // pinned: device-side error flags read after a step
   double* red_tmp = nullptr;     // reduction partials (1024)
   unsigned int* red_counter = nullptr;
@@ -268,10 +269,17 @@ cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev5);
 size_t pair_screen_bytes(const fep3m_ctx* c);
 size_t pair_tc_table_bytes(int n_sr);
 void pair_tc_table(int n_sr, const double* Hw, uint16_t* out);
+size_t pair_adj_table_bytes(int n_sr);
+void pair_adj_table(int n_sr, const double* Hw, uint16_t* out);
 // energy_adjoint: also leave half the singular sums in psi_s / gpsi_s (the
 // singular adjoint of the energy's weights Q / 2)
 cudaError_t pair_screen(fep3m_ctx* c, int want_grad, cudaStream_t s, bool energy_adjoint);
 cudaError_t pair_prepare(fep3m_ctx* c);
+// tensor-core row GEMM with transposed output (mesh.cu): out[(i - tile0 nt) R + r]
+// = sum_{a < K} in[r K + a] B[i][a]; B in split bf16 pieces per column tile of nt
+cudaError_t tc_rows_prepare(int nt);
+cudaError_t tc_rows_gemm(int64_t R, int K, int NC, int nt, int tile0, int ntiles, const float* in, const void* Bp,
+                         float* out, int* err, cudaStream_t s);
 cudaError_t pair_eval(fep3m_ctx* c, double* phi_out, int want_grad);
 // adjoint in three parts: weights and deposit (-> g64), the parts that need
 // lam (vertex adjoint, screen sweep, singular adjoint), and the per-charge assembly

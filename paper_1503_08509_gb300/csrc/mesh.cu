@@ -1031,21 +1031,28 @@ __global__ void __launch_bounds__(256) k_fdm_axis(int N, const float* __restrict
   }
 }
 
-// The same pass on the tensor cores: per CTA 128 rows r and the nt columns i
-// of one column tile, the contraction over a in chunks of 64 as tcgen05
-// bf16 MMAs (M = 128, N = nt) on three-piece splits of both operands (six
-// piece products, two TMEM accumulators: the leading product, the other
-// five).  A (the input rows) is split in the kernel into 128-byte-swizzled
-// K-major tiles; B = W^T, B[i][a] = W[a][i], comes split and laid out in
-// advance (Bp: [column tile][chunk][piece][nt rows][64], zero outside N).
-// The epilogue reads one row per thread from TMEM, so a warp's stores of one
-// column are 32 consecutive rows.  err: a bounded wait that gave up.
+// The same pass on the tensor cores, as a general row GEMM with the output
+// transposed: out[(i - c0) R + r] = s(r, i) sum_{a < K} in[r K + a] B[i][a]
+// for R rows r and columns i in [c0, min(NC, c0 + gridDim.y nt)), c0 =
+// tile0 nt.  Per CTA 128 rows and the nt columns of one column tile; the
+// contraction in chunks of 64 as tcgen05 bf16 MMAs (M = 128, N = nt) on
+// three-piece splits of both operands (six piece products, two TMEM
+// accumulators: the leading product, the other five).  A (the input rows) is
+// split in the kernel into 128-byte-swizzled K-major tiles; B comes split and
+// laid out in advance (Bp: [column tile][chunk][piece][nt rows][64], zero
+// outside NC x K).  The epilogue reads one row per thread from TMEM, so a
+// warp's stores of one column are 32 consecutive rows.  Used for the
+// fast-diagonalisation passes (R = N^2, K = NC = N, B = W^T; SCALE: the
+// inverse eigenvalue sums, rows r = j + N k) and for the screen adjoint's
+// contraction (R elements, K = 64 nodes, NC offsets).  err: a bounded wait
+// that gave up.
 constexpr int FT_THREADS = 256;
 
 template <bool SCALE>
-__global__ void __launch_bounds__(FT_THREADS) k_fdm_tc(int N, int nt, const float* __restrict__ in,
-                                                        const uint4* __restrict__ Bp, const float* __restrict__ lam,
-                                                        int null_mode, float* __restrict__ out, int* __restrict__ err) {
+__global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int NC, int nt, int tile0,
+                                                         const float* __restrict__ in, const uint4* __restrict__ Bp,
+                                                         const float* __restrict__ lam, int null_mode, int N,
+                                                         float* __restrict__ out, int* __restrict__ err) {
   PDL_PROLOGUE
   using namespace tc;
   extern __shared__ __align__(16) unsigned char fsm[];
@@ -1055,10 +1062,9 @@ __global__ void __launch_bounds__(FT_THREADS) k_fdm_tc(int N, int nt, const floa
   uint64_t* mbar = (uint64_t*)(tiles + 3 * 16384 + 3 * bpiece);
   uint32_t* tslot = (uint32_t*)(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int64_t R = (int64_t)N * N;
   const int64_t r0 = (int64_t)blockIdx.x * 128;
-  const int n0 = blockIdx.y * nt;
-  const int kc = (N + 63) / 64;
+  const int tile = tile0 + (int)blockIdx.y, c0 = tile0 * nt, n0 = tile * nt;
+  const int kc = (K + 63) / 64;
   uint32_t ncols = 32;
   while (ncols < 2u * (uint32_t)nt) ncols <<= 1;
   const uint32_t lo_off = ncols / 2, idesc = umma_idesc((uint32_t)nt);
@@ -1068,7 +1074,7 @@ __global__ void __launch_bounds__(FT_THREADS) k_fdm_tc(int N, int nt, const floa
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint4* bsrc = Bp + (size_t)blockIdx.y * kc * 3 * (bpiece / 16);
+  const uint4* bsrc = Bp + (size_t)tile * kc * 3 * (bpiece / 16);
   bool failed = false;
   for (int c = 0; c < kc; ++c) {
     for (int i = tid; i < 3 * (int)(bpiece / 16); i += FT_THREADS) cp_async16(tb + 16 * i, bsrc + (size_t)c * 3 * (bpiece / 16) + i);
@@ -1080,7 +1086,7 @@ __global__ void __launch_bounds__(FT_THREADS) k_fdm_tc(int N, int nt, const floa
       const int a0 = 64 * c + 8 * g;
       float x[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) x[t] = (r < R && a0 + t < N) ? in[r * N + a0 + t] : 0.f;
+      for (int t = 0; t < 8; ++t) x[t] = (r < R && a0 + t < K) ? in[r * K + a0 + t] : 0.f;
       uint32_t p0[4], p1[4], p2[4];
 #pragma unroll
       for (int t = 0; t < 4; ++t) bf16_split2(x[2 * t], x[2 * t + 1], p0[t], p1[t], p2[t]);
@@ -1139,10 +1145,10 @@ __global__ void __launch_bounds__(FT_THREADS) k_fdm_tc(int N, int nt, const floa
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
           const int i = n0 + 16 * grp + t;
-          if (i >= N || 16 * grp + t >= nt) continue;
+          if (i >= NC || 16 * grp + t >= nt) continue;
           float v = __uint_as_float(vh[t]) + __uint_as_float(vl[t]);
           if (SCALE) v = (jk_null && i == null_mode) ? 0.f : v * __frcp_rn(lam[i] + djk);
-          out[(int64_t)i * R + r] = v;
+          out[(int64_t)(i - c0) * R + r] = v;
         }
       }
     }
@@ -1152,7 +1158,8 @@ __global__ void __launch_bounds__(FT_THREADS) k_fdm_tc(int N, int nt, const floa
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
-static size_t fdm_tc_smem(int nt) { return 1024 + 3 * 16384 + (size_t)3 * nt * 128 + 16; }
+static size_t tc_rows_smem(int nt) { return 1024 + 3 * 16384 + (size_t)3 * nt * 128 + 16; }
+
 
 // dense 1-D transform along an axis: out[.. i ..] = sum_k A[i][k] in[.. k ..]
 // (A = V^T when transpose), optionally scaled elementwise by s after.
@@ -1360,6 +1367,25 @@ __global__ void k_df_to_double(int64_t n, const dfv* __restrict__ v, double* __r
 
 }  // namespace
 
+// allow the row GEMM the dynamic shared memory of its largest column tile
+// (nt <= 128), whatever nt a caller uses
+cudaError_t tc_rows_prepare(int nt) {
+  if (nt > 128) return cudaErrorInvalidValue;
+  const int sm = (int)tc_rows_smem(128);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
+}
+
+// out[(i - tile0 nt) R + r] = sum_{a < K} in[r K + a] B[i][a] for the column tiles tile0 .. tile0 + ntiles - 1
+cudaError_t tc_rows_gemm(int64_t R, int K, int NC, int nt, int tile0, int ntiles, const float* in, const void* Bp,
+                         float* out, int* err, cudaStream_t s) {
+  const dim3 g((unsigned)((R + 127) / 128), (unsigned)ntiles);
+  FEP3M_CL k_tc_rows<false><<<g, FT_THREADS, tc_rows_smem(nt), s>>>(R, K, NC, nt, tile0, in, (const uint4*)Bp,
+                                                                    nullptr, -1, 0, out, err);
+  return cudaGetLastError();
+}
+
 // ======================================================================
 // host side
 // ======================================================================
@@ -1508,15 +1534,18 @@ struct MG {
     cudaStream_t s = c->stream;
     if (f.BpF) {
       const dim3 g((unsigned)(((int64_t)N * N + 127) / 128), (unsigned)f.ntile);
-      const size_t sm = fdm_tc_smem(f.nt);
+      const size_t sm = tc_rows_smem(f.nt);
       const uint4* F = (const uint4*)f.BpF;
       const uint4* I = (const uint4*)f.BpI;
-      launch_pdl(k_fdm_tc<false>, g, FT_THREADS, sm, s, N, f.nt, b, F, f.lam32, f.null_mode, w1, f.err);
-      launch_pdl(k_fdm_tc<false>, g, FT_THREADS, sm, s, N, f.nt, (const T*)w1, F, f.lam32, f.null_mode, w2, f.err);
-      launch_pdl(k_fdm_tc<true>, g, FT_THREADS, sm, s, N, f.nt, (const T*)w2, F, f.lam32, f.null_mode, w1, f.err);
-      launch_pdl(k_fdm_tc<false>, g, FT_THREADS, sm, s, N, f.nt, (const T*)w1, I, f.lam32, f.null_mode, w2, f.err);
-      launch_pdl(k_fdm_tc<false>, g, FT_THREADS, sm, s, N, f.nt, (const T*)w2, I, f.lam32, f.null_mode, w1, f.err);
-      launch_pdl(k_fdm_tc<false>, g, FT_THREADS, sm, s, N, f.nt, (const T*)w1, I, f.lam32, f.null_mode, x, f.err);
+      const int64_t R = (int64_t)N * N;
+      const float* lm = f.lam32;
+      const int nm = f.null_mode, nt = f.nt;
+      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, N, nt, 0, b, F, lm, nm, N, w1, f.err);
+      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, N, nt, 0, (const T*)w1, F, lm, nm, N, w2, f.err);
+      launch_pdl(k_tc_rows<true>, g, FT_THREADS, sm, s, R, N, N, nt, 0, (const T*)w2, F, lm, nm, N, w1, f.err);
+      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, N, nt, 0, (const T*)w1, I, lm, nm, N, w2, f.err);
+      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, N, nt, 0, (const T*)w2, I, lm, nm, N, w1, f.err);
+      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, N, nt, 0, (const T*)w1, I, lm, nm, N, x, f.err);
       return;
     }
     const dim3 g((unsigned)(((int64_t)N * N + FM - 1) / FM), (unsigned)((N + FN - 1) / FN));
@@ -1791,10 +1820,7 @@ static cudaError_t mg_setup(Solver* c) {
       cudaMemcpy(f.BpI, bi.data(), bi.size() * 2, cudaMemcpyHostToDevice);
       f.nt = nt;
       f.ntile = ntile;
-      const int sm = (int)fdm_tc_smem(nt);
-      if ((e = cudaFuncSetAttribute(k_fdm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess ||
-          (e = cudaFuncSetAttribute(k_fdm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
-        return e;
+      if ((e = tc_rows_prepare(nt)) != cudaSuccess) return e;
       if ((e = cudaMalloc(&f.err, sizeof(int))) != cudaSuccess) return e;
       cudaMemset(f.err, 0, sizeof(int));
     }

@@ -880,6 +880,7 @@ __global__ void k_node_assemble(int n, const T* __restrict__ W, double* __restri
 //   A[s][k] = sum_{o : o + k in block} D[o][s + k + o]
 // D[o][e] is the table field of element e's deposit seen from the vertex e - o.
 constexpr int GT = 64;   // GEMM tile: 64 elements x 64 offsets, K = 64 nodes
+constexpr int ADJ_NT = 128;   // tensor-core column tile: offsets per tile
 
 template <class T>
 __global__ void __launch_bounds__(PT) k_adj_gemm(int64_t ne, int o0, int no, const T* __restrict__ W,
@@ -928,45 +929,57 @@ __global__ void __launch_bounds__(PT) k_adj_gemm(int64_t ne, int o0, int no, con
 }
 
 // A[s][k] (+)= sum over offsets o in [o0, o0 + no) with o + k inside the block of D[o][s + k + o].
-// Written as a loop over the block element u = k + o (each axis in [-n_sr, n_sr], so o is
-// always a stored offset), with the wrapped element index advanced incrementally; the
-// terms are added in increasing o, as the offsets are stored.
+// One thread per source element s, all eight corners k: the eight readers of a
+// value D[o][e] are the neighbouring elements e - o - k + (n_sr + 1), so they
+// run in neighbouring threads and the repeated reads hit the caches.  Written
+// as a loop over the block element u = k + o (each axis in [-n_sr, n_sr], so o
+// is always a stored offset), with the wrapped element index advanced
+// incrementally; per (s, k) the terms of one block row are added in FP32 and
+// the rows with compensation, in increasing o.
 template <class T>
 __global__ void k_adj_gather(int n, int n_sr, int o0, int no, int first, const int* __restrict__ count,
                              const T* __restrict__ D, double* __restrict__ A) {
   const int64_t ne = (int64_t)n * n * n;
-  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= 8 * ne) return;
-  const int k = (int)(gid / ne);
-  const int64_t s = gid - k * ne;
-  Acc<T> acc;   // compensated over the block's rows: the terms cancel to a small remainder
-  const double prev = first ? 0.0 : A[s * 8 + k];
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= ne) return;
+  Acc<T> acc[8];   // compensated over the block's rows: the terms cancel to a small remainder
   if (count[s] != 0) {
     const int keep = n_sr + 1, noff = 2 * n_sr + 2;
-    const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
     const int sx = (int)(s % n), sy = (int)((s / n) % n), sz = (int)(s / ((int64_t)n * n));
     const int ex0 = wrapn(sx - n_sr, n);
     for (int uz = -n_sr; uz <= n_sr; ++uz) {
       const int64_t ez = wrapn(sz + uz, n);
-      const int oz = uz - kz + keep;
       for (int uy = -n_sr; uy <= n_sr; ++uy) {
         const int64_t row = (int64_t)n * (wrapn(sy + uy, n) + (int64_t)n * ez);
-        const int oyz = noff * ((uy - ky + keep) + noff * oz) - kx + keep - o0;   // o - o0 at ux = 0
+        int oyz[8];   // o - o0 at ux = 0, per corner
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          oyz[k] = noff * ((uy - ((k >> 1) & 1) + keep) + noff * (uz - (k >> 2) + keep)) - (k & 1) + keep - o0;
+        T rs[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) rs[k] = T(0);
         int ex = ex0;
-        T rs = T(0);   // one row of the block in plain FP32, the rows compensated
         for (int ux = -n_sr; ux <= n_sr; ++ux) {
-          const int oi = oyz + ux;
-          if ((unsigned)oi < (unsigned)no) rs += D[(int64_t)oi * ne + row + ex];
+          const int64_t e = row + ex;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int oi = oyz[k] + ux;
+            if ((unsigned)oi < (unsigned)no) rs[k] += D[(int64_t)oi * ne + e];
+          }
           if (++ex == n) ex = 0;
         }
-        acc.add(rs);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k].add(rs[k]);
       }
     }
   }
-  A[s * 8 + k] = prev + ((double)acc.s - (double)acc.c);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const double prev = first ? 0.0 : A[s * 8 + k];
+    A[s * 8 + k] = prev + ((double)acc[k].s - (double)acc[k].c);
+  }
 }
 
-// singular adjoint potential, one warp per charge
 template <class T>
 __global__ void __launch_bounds__(PT) k_pair_adj_warp(int64_t N, int n, int n_sr, T h, const int* __restrict__ start,
                                                       const typename vec4<T>::type* __restrict__ part,
@@ -1164,6 +1177,28 @@ cudaError_t pair_screen(fep3m_ctx* c, int want_grad, cudaStream_t s, bool energy
                    : launch_pair_screen<double, false, false>(c, c->Hw64, s, half);
 }
 
+// the table's three bf16 pieces for the screen adjoint's contraction
+// D[o][e] = sum_m W[e][m] H(o, m) on the tensor cores: B[o][m] = H(o, m) in
+// column tiles of ADJ_NT offsets, one chunk of the 64 nodes
+size_t pair_adj_table_bytes(int n_sr) {
+  const int noff = 2 * n_sr + 2, no3 = noff * noff * noff;
+  return (size_t)((no3 + ADJ_NT - 1) / ADJ_NT) * 3 * ADJ_NT * 64 * 2;
+}
+void pair_adj_table(int n_sr, const double* Hw, uint16_t* out) {
+  const int noff = 2 * n_sr + 2, no3 = noff * noff * noff, ntile = (no3 + ADJ_NT - 1) / ADJ_NT;
+  std::memset(out, 0, pair_adj_table_bytes(n_sr));
+  for (int t = 0; t < ntile; ++t)
+    for (int ii = 0; ii < ADJ_NT; ++ii) {
+      const int o = t * ADJ_NT + ii;
+      if (o >= no3) continue;
+      for (int m = 0; m < 64; ++m) {
+        uint16_t pc[3];
+        bf16_pieces(Hw[(size_t)o * 64 + m], pc);
+        for (int p = 0; p < 3; ++p) out[((size_t)t * 3 + p) * ADJ_NT * 64 + sw128_off(ii, m) / 2] = pc[p];
+      }
+    }
+}
+
 // the table's three bf16 pieces per chunk of 64 offsets, in the swizzled
 // K-major layout of the tensor-core tiles: [chunk][piece][node row][offset]
 size_t pair_tc_table_bytes(int n_sr) {
@@ -1245,7 +1280,10 @@ static cudaError_t screen_adjoint(fep3m_ctx* c, const T* W, const T* Hw, double*
   const int64_t ne = (int64_t)n * n * n;
   const int no3 = c->noff * c->noff * c->noff;
   const size_t budget = (size_t)1 << 31;   // bytes of D held at once
-  int chunk = (int)std::min<int64_t>(no3, std::max<int64_t>(GT, (int64_t)(budget / (ne * sizeof(T))) / GT * GT));
+  // tensor cores (FP32 path, table pieces prepared): column tiles of ADJ_NT offsets
+  const bool tcore = sizeof(T) == 4 && c->HbA != nullptr;
+  const int q = tcore ? ADJ_NT : GT;
+  int chunk = (int)std::min<int64_t>(no3, std::max<int64_t>(q, (int64_t)(budget / (ne * sizeof(T))) / q * q));
   const size_t need = (size_t)chunk * ne * sizeof(T);
   if (c->D_bytes < need) {
     if (c->D_adj) cudaFree(c->D_adj);
@@ -1258,9 +1296,15 @@ static cudaError_t screen_adjoint(fep3m_ctx* c, const T* W, const T* Hw, double*
   cudaStream_t s = c->stream;
   for (int o0 = 0; o0 < no3; o0 += chunk) {
     const int no = std::min(chunk, no3 - o0);
-    dim3 grid((unsigned)((ne + GT - 1) / GT), (unsigned)((no + GT - 1) / GT));
-    FEP3M_CL k_adj_gemm<T><<<grid, PT, 0, s>>>(ne, o0, no, W, Hw, (T*)c->D_adj);
-    FEP3M_CL k_adj_gather<T><<<gsz(8 * ne), PT, 0, s>>>(n, c->n_sr, o0, no, o0 == 0, c->count, (const T*)c->D_adj, A);
+    if (tcore) {
+      cudaError_t e = tc_rows_gemm(ne, 64, no3, ADJ_NT, o0 / ADJ_NT, (no + ADJ_NT - 1) / ADJ_NT, (const float*)W,
+                                   c->HbA, (float*)c->D_adj, c->iflags + 2, s);
+      if (e != cudaSuccess) return e;
+    } else {
+      dim3 grid((unsigned)((ne + GT - 1) / GT), (unsigned)((no + GT - 1) / GT));
+      FEP3M_CL k_adj_gemm<T><<<grid, PT, 0, s>>>(ne, o0, no, W, Hw, (T*)c->D_adj);
+    }
+    FEP3M_CL k_adj_gather<T><<<gsz(ne), PT, 0, s>>>(n, c->n_sr, o0, no, o0 == 0, c->count, (const T*)c->D_adj, A);
   }
   return cudaGetLastError();
 }
