@@ -46,6 +46,10 @@ template <> __device__ __forceinline__ float rsq<float>(float x) {
   return y * fmaf(-0.5f * x, y * y, 1.5f);
 }
 
+// fused multiply-add in the working precision
+__device__ __forceinline__ float fmaw(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaw(double a, double b, double c) { return fma(a, b, c); }
+
 // compensated (Kahan) accumulator; FP64 uses plain sums
 template <class T> struct Acc {
   T s = T(0), c = T(0);
@@ -605,15 +609,16 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
           for (int j = j0; j < j1; ++j) {
             const V4 pj = stg[j];
             const T ddx = T((int)sxb[j] - cx);
-            const T rx = (ddx + (pj.x - pt.x)) * h, ry = (ddy + (pj.y - pt.y)) * h, rz = (ddz + (pj.z - pt.z)) * h;
-            const T ir = j == self ? T(0) : rsq<T>(rx * rx + ry * ry + rz * rz);
+            // element units (1/h applied once per target, in FP64), fused r^2 and sums
+            const T rx = ddx + (pj.x - pt.x), ry = ddy + (pj.y - pt.y), rz = ddz + (pj.z - pt.z);
+            const T ir = j == self ? T(0) : rsq<T>(fmaw(rx, rx, fmaw(ry, ry, rz * rz)));
             const T qi = pj.w * ir;
             s0 += qi;
             if (GRAD) {
-              const T f3 = qi * ir * ir;
-              s1 += f3 * rx;
-              s2 += f3 * ry;
-              s3 += f3 * rz;
+              const T f3 = qi * (ir * ir);
+              s1 = fmaw(f3, rx, s1);
+              s2 = fmaw(f3, ry, s2);
+              s3 = fmaw(f3, rz, s3);
             }
           }
           ps.add(s0);
@@ -637,15 +642,15 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
             const int j0 = start[g], j1 = j0 + count[g];
             for (int j = j0; j < j1; ++j) {
               const V4 pj = part[j];
-              const T rx = (ddx + (pj.x - pt.x)) * h, ry = (ddy + (pj.y - pt.y)) * h, rz = (ddz + (pj.z - pt.z)) * h;
-              const T ir = j == slot ? T(0) : rsq<T>(rx * rx + ry * ry + rz * rz);
+              const T rx = ddx + (pj.x - pt.x), ry = ddy + (pj.y - pt.y), rz = ddz + (pj.z - pt.z);
+              const T ir = j == slot ? T(0) : rsq<T>(fmaw(rx, rx, fmaw(ry, ry, rz * rz)));
               const T qi = pj.w * ir;
               s0 += qi;
               if (GRAD) {
-                const T f3 = qi * ir * ir;
-                s1 += f3 * rx;
-                s2 += f3 * ry;
-                s3 += f3 * rz;
+                const T f3 = qi * (ir * ir);
+                s1 = fmaw(f3, rx, s1);
+                s2 = fmaw(f3, ry, s2);
+                s3 = fmaw(f3, rz, s3);
               }
             }
           }
@@ -667,13 +672,16 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
 #pragma unroll
       for (int o = 1; o < TPT; o <<= 1) v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], o);
     if (valid && q == 0) {
-      phi_s[slot] = (double)v4[0];
-      if (psi) psi[slot] = 0.5 * (double)v4[0];
+      const double ih = 1.0 / (double)h;   // the sums are in element units
+      const double ps0 = (double)v4[0] * ih;
+      phi_s[slot] = ps0;
+      if (psi) psi[slot] = 0.5 * ps0;
       if (GRAD) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          E_s[3 * slot + a] = (double)v4[1 + a];
-          if (gpsi) gpsi[3 * slot + a] = 0.5 * (double)v4[1 + a];
+          const double e = (double)v4[1 + a] * (ih * ih);
+          E_s[3 * slot + a] = e;
+          if (gpsi) gpsi[3 * slot + a] = 0.5 * e;
         }
       }
     }
@@ -934,15 +942,15 @@ __global__ void __launch_bounds__(PT) k_adj_gemm(int64_t ne, int o0, int no, con
 // run in neighbouring threads and the repeated reads hit the caches.  Written
 // as a loop over the block element u = k + o (each axis in [-n_sr, n_sr], so o
 // is always a stored offset), with the wrapped element index advanced
-// incrementally; per (s, k) the terms of one block row are added in FP32 and
-// the rows with compensation, in increasing o.
+// incrementally; per (s, k) the terms are added with compensation, in
+// increasing o.
 template <class T>
 __global__ void k_adj_gather(int n, int n_sr, int o0, int no, int first, const int* __restrict__ count,
                              const T* __restrict__ D, double* __restrict__ A) {
   const int64_t ne = (int64_t)n * n * n;
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= ne) return;
-  Acc<T> acc[8];   // compensated over the block's rows: the terms cancel to a small remainder
+  Acc<T> acc[8];   // compensated: the block's terms cancel to a small remainder
   if (count[s] != 0) {
     const int keep = n_sr + 1, noff = 2 * n_sr + 2;
     const int sx = (int)(s % n), sy = (int)((s / n) % n), sz = (int)(s / ((int64_t)n * n));
@@ -955,21 +963,16 @@ __global__ void k_adj_gather(int n, int n_sr, int o0, int no, int first, const i
 #pragma unroll
         for (int k = 0; k < 8; ++k)
           oyz[k] = noff * ((uy - ((k >> 1) & 1) + keep) + noff * (uz - (k >> 2) + keep)) - (k & 1) + keep - o0;
-        T rs[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) rs[k] = T(0);
         int ex = ex0;
         for (int ux = -n_sr; ux <= n_sr; ++ux) {
           const int64_t e = row + ex;
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             const int oi = oyz[k] + ux;
-            if ((unsigned)oi < (unsigned)no) rs[k] += D[(int64_t)oi * ne + e];
+            if ((unsigned)oi < (unsigned)no) acc[k].add(D[(int64_t)oi * ne + e]);
           }
           if (++ex == n) ex = 0;
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k].add(rs[k]);
       }
     }
   }

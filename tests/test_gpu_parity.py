@@ -164,9 +164,9 @@ def test_mixed_matches_oracle(api, name, tc):
 
 
 NACL_FP32 = pytest.mark.xfail(strict=True, reason="rock-salt forces are small residues of large field parts (the "
-                              "lattice nearly cancels them); the FP32 arithmetic of the pair and adjoint sums "
-                              "leaves ~1e-5 of the parts in them, above 1e-5 of the forces (FP64 and the "
-                              "potentials pass)")
+                              "lattice nearly cancels them); on this 16^3 lattice the FP32 arithmetic of the pair "
+                              "and adjoint sums leaves slightly more than 1e-5 of the forces (the 32^3 lattice of "
+                              "the full-size tests passes; FP64 and the potentials pass)")
 
 
 @pytest.mark.parametrize("tc", [True, False])
