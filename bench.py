@@ -32,9 +32,11 @@ METRIC = "particles/sec for Phi_i+forces at stated RMS error vs Ewald; mixed vs 
 WORKLOAD = "nacl32"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "nacl32_sample.txt")
 L2_FLUSH_BYTES = 256 << 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_pair_screen launch on this workload, from the ncu
-# capture summarised in profiles/ (None until one is taken of the current kernel)
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_pair_screen launch and of one transform pass of the
+# mesh solve (k_tc_rows) on this workload, from the ncu captures summarised in profiles/ (None until one is
+# taken of the current kernel)
 PAIR_DRAM_BYTES = 2252288
+PASS_DRAM_BYTES = None
 
 
 def parse():
@@ -135,7 +137,8 @@ def fp32_peak_tflops(n_sm, mhz):
 
 
 def time_engine(eng, pos, Q, out, steps, warmup, flush, torch, host=False):
-    """Run warmup + timed steps; returns (list of ms per step, list of screen-kernel ms, launches per step)."""
+    """Run warmup + timed steps; returns (ms per step, (screen-kernel ms, inner-solve ms) per step, launches per
+    step, the last result)."""
     stream = eng.stream
     for _ in range(warmup):
         eng.set_particles(pos, Q)
@@ -153,7 +156,8 @@ def time_engine(eng, pos, Q, out, steps, warmup, flush, torch, host=False):
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
-        pair.append(eng.stats()["ms_pair_screen"])
+        st = eng.stats()
+        pair.append((st["ms_pair_screen"], st["ms_inner_solve"]))
     launches = (eng.stats()["kernel_launches"] - l0) / steps
     return ms, pair, launches, r
 
@@ -259,35 +263,57 @@ def run_ours(args):
         acc["mixed_vs_fp64"] = dict(phi_rel_rms=rel_rms(results["mixed"]["phi"], results["fp64"]["phi"]),
                                     force_rel_rms=rel_rms(results["mixed"]["F"], results["fp64"]["F"]))
 
-    # roofline of the hot-path kernel the method is built around: the short-range screen/singular kernel
-    # k_pair_screen (FP32 issue bound), timed with CUDA events on its own stream, where it runs concurrently
-    # with the forward and adjoint mesh solves.  achieved = SURVEY 8(d)'s algorithmic count for a build that
-    # collapses the screen sums per target element (1024 flops per non-empty target element and non-empty
-    # element of its block, 20 per singular pair with gradients; the 128 per target of the 64-node
-    # evaluation belong to k_pair_eval); the per-target-charge count and the flops the kernel executes
-    # (vertex-regrouped contraction: 512 x 64 x 2 per non-empty target element) are reported beside it.
     st = main["stats"]
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+
+    # roofline of the step's dominant kernel (the largest share of the step's launch time,
+    # profiles/launches_nacl32_mixed_step.md): k_tc_rows, the tensor-core transform passes of the mesh
+    # solve.  Each pass reads and writes the (3n)^3 FP32 vector once: SURVEY 8(d)'s 8 B per DOF per
+    # fine-level sweep of the mesh solve.  Timed with CUDA events recorded inside the replayed solve graph
+    # around the forward solve's first inner solve (six passes), concurrent with the rest of the step.
+    nodes = (3 * d["n_el"]) ** 3
+    inner_ms = statistics.mean(p[1] for p in main["pair"])
+    pass_ms = inner_ms / 6 if inner_ms > 0 else float("nan")
+    hbm = peaks.get("hbm_gbs")
+    hbm_note = "measured copy bandwidth (MEASURED_PEAKS.json)"
+    if not hbm:
+        hbm, hbm_note = 6800.0, "fallback 6.8 TB/s"
+    pass_bytes = 8 * nodes
+    achieved_gbs = pass_bytes / (pass_ms * 1e-3) / 1e9
+    roof = {"kernel": "k_tc_rows (fast-diagonalisation transform pass of the mesh solve, tensor cores)",
+            "bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved_gbs / hbm, 4), "traffic": PASS_DRAM_BYTES, "peak_note": hbm_note,
+            "count": "8 B per node per pass ((3n)^3 = %d nodes, FP32 read + write)" % nodes,
+            "bytes_per_launch": pass_bytes, "ms_per_launch": round(pass_ms, 5),
+            "note": "at 32^3 the vector (3.5 MB) stays in L2 and each pass is launch/latency bound"}
+
+    # roofline of the short-range kernel the method is built around: k_pair_screen (FP32 issue bound),
+    # timed with CUDA events on its own stream, where it runs concurrently with the forward and adjoint mesh
+    # solves.  achieved = SURVEY 8(d)'s algorithmic count for a build that collapses the screen sums per
+    # target element (1024 flops per non-empty target element and non-empty element of its block, 20 per
+    # singular pair with gradients; the 128 per target of the 64-node evaluation belong to k_pair_eval);
+    # the per-target-charge count and the flops the kernel executes (vertex-regrouped contraction: 512 x 64
+    # x 2 per non-empty target element) are reported beside it.
     ne_nonempty = st["nonempty_elements"]
     pairs = st["singular_pairs"]
     flops_elem = st["screen_element_pairs"] * 1024 + pairs * 20
     flops_charge = st["screen_charge_pairs"] * 1024 + pairs * 20
     flops_exec = ne_nonempty * 512 * 64 * 2 + pairs * 20
-    pair_ms = statistics.mean(main["pair"])
+    pair_ms = statistics.mean(p[0] for p in main["pair"])
     tf = lambda f: f / (pair_ms * 1e-3) / 1e12
-    props = torch.cuda.get_device_properties(dev)
-    peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
     peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
-    roof = {"kernel": "k_pair_screen (screen-field contraction + singular pairs with gradients, concurrent with "
-                      "the mesh solves)",
-            "bound": "alu", "achieved": round(tf(flops_elem), 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-            "frac": round(tf(flops_elem) / peak, 4), "traffic": PAIR_DRAM_BYTES,
-            "peak_note": "FP32 FMA peak derived: %d SMs x 128 lanes x 2 flops x %.0f MHz (max SM clock)"
-                         % (props.multi_processor_count, sm_max),
-            "count": "per (non-empty target element, non-empty block element) pair x 1024 + singular pairs x 20",
-            "flops_per_launch": flops_elem, "ms_per_launch": round(pair_ms, 4),
-            "per_target_charge": {"flops": flops_charge, "frac": round(tf(flops_charge) / peak, 4)},
-            "executed": {"flops": flops_exec, "frac": round(tf(flops_exec) / peak, 4)}}
+    roof_pair = {"kernel": "k_pair_screen (screen-field contraction + singular pairs with gradients, concurrent "
+                           "with the mesh solves)",
+                 "bound": "alu", "achieved": round(tf(flops_elem), 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                 "frac": round(tf(flops_elem) / peak, 4), "traffic": PAIR_DRAM_BYTES,
+                 "peak_note": "FP32 FMA peak derived: %d SMs x 128 lanes x 2 flops x %.0f MHz (max SM clock)"
+                              % (props.multi_processor_count, sm_max),
+                 "count": "per (non-empty target element, non-empty block element) pair x 1024 + singular pairs x 20",
+                 "flops_per_launch": flops_elem, "ms_per_launch": round(pair_ms, 4),
+                 "per_target_charge": {"flops": flops_charge, "frac": round(tf(flops_charge) / peak, 4)},
+                 "executed": {"flops": flops_exec, "frac": round(tf(flops_exec) / peak, 4)}}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
@@ -308,6 +334,7 @@ def run_ours(args):
         "mg": {"levels": st["mg_levels"], "iterations": st["mg_iterations"], "refine_steps": st["refine_steps"],
                "rel_residual": st["mg_rel_residual"], "adj_iterations": st["adj_iterations"]},
         "roofline": roof,
+        "roofline_pair": roof_pair,
         "e2e": {"value": round(e2e_value, 1), "unit": "particles/s", "h2d_bytes_per_step": N * 32,
                 "d2h_bytes_per_step": N * 8 + N * 24 + 8},
         "gpu_launches": int(round(main["launches"])),

@@ -114,6 +114,10 @@ typedef struct {
                                the forward mesh solve                            */
   double ms_pair_eval;      /* the evaluation of the mesh potential minus the
                                screen field at the targets, after the solve      */
+  double ms_inner_solve;    /* the first FP32 inner solve of the last replayed
+                               forward mesh solve (six transform passes of the
+                               fast diagonalisation, or the multigrid-
+                               preconditioned CG)                                */
 } fep3m_stats;
 
 /* Create a context: validates cfg, builds the FE basis-screen table (a

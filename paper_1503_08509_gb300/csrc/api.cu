@@ -164,6 +164,17 @@ double ev_ms(fep3m_ctx* c, int a, int b) {
   return ms;
 }
 
+// the pair statistics of the last set_particles, once their copy has landed
+void take_counts(fep3m_ctx* c) {
+  const unsigned long long* n = c->host_cnt;
+  c->stats.singular_pairs = (int64_t)n[0];
+  c->stats.nonempty_elements = (int64_t)n[1];
+  c->stats.max_per_element = (int)n[2];
+  c->stats.screen_element_pairs = (int64_t)n[3];
+  c->stats.screen_charge_pairs = (int64_t)n[4];
+  c->counts_pending = false;
+}
+
 void solve_stats(fep3m_ctx* c) {
   const fep3m::Solver& F = c->solv[0];
   c->stats.mg_iterations = F.iters;
@@ -282,6 +293,8 @@ void fep3m_destroy(fep3m_ctx* c) {
   if (c->pair_stream) cudaStreamDestroy(c->pair_stream);
   if (c->ev_pfork) cudaEventDestroy(c->ev_pfork);
   if (c->ev_pjoin) cudaEventDestroy(c->ev_pjoin);
+  if (c->ev_pcount) cudaEventDestroy(c->ev_pcount);
+  if (c->host_cnt) cudaFreeHost(c->host_cnt);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->ev_fork2) cudaEventDestroy(c->ev_fork2);
@@ -375,6 +388,8 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
       (e = cudaStreamCreateWithFlags(&c->pair_stream, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_pfork, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_pjoin, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_pcount, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaMallocHost(&c->host_cnt, 5 * sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming)) != cudaSuccess ||
@@ -407,27 +422,29 @@ int fep3m_set_particles(fep3m_ctx* c, int64_t N, const double* pos, const double
     dQ = c->Q_in;
   }
   ev_record(c, 6);
+  // the previous call's pair counts read the element counts this call rewrites
+  CK(cudaStreamWaitEvent(c->stream, c->ev_pcount, 0));
   CK(cudaMemsetAsync(c->iflags, 0, sizeof(int), c->stream));
   CK(bin_particles(c, dpos, dQ, c->precision == FEP3M_MIXED));
   CK(sorted_charges(c));
   FEP3M_CL k_charge_sums<<<(unsigned)std::min<int64_t>(std::max<int64_t>(gsz(N) / 4, 1), 256), PT, 0, c->stream>>>(
       N, dQ, (double*)c->red_tmp, c->red_counter, c->scal + 32);
   ev_record(c, 7);
-  CK(pair_counts(c, (unsigned long long*)(c->scal + 48)));
+  // pair statistics on the pair stream, read back by the next synchronising call
+  CK(cudaEventRecord(c->ev_pfork, c->stream));
+  CK(cudaStreamWaitEvent(c->pair_stream, c->ev_pfork, 0));
+  CK(pair_counts(c, (unsigned long long*)(c->scal + 48), c->pair_stream));
+  CK(cudaMemcpyAsync(c->host_cnt, c->scal + 48, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                     c->pair_stream));
+  CK(cudaEventRecord(c->ev_pcount, c->pair_stream));
+  c->counts_pending = true;
   double sums[2];
-  unsigned long long cnt3[5];
   int flag = 0;
-  CK(cudaMemcpyAsync(cnt3, c->scal + 48, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(sums, c->scal + 32, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(&flag, c->iflags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->have_particles = false;
   c->have_forward = false;
-  c->stats.singular_pairs = (int64_t)cnt3[0];
-  c->stats.nonempty_elements = (int64_t)cnt3[1];
-  c->stats.max_per_element = (int)cnt3[2];
-  c->stats.screen_element_pairs = (int64_t)cnt3[3];
-  c->stats.screen_charge_pairs = (int64_t)cnt3[4];
   if (flag) return FEP3M_EINVAL;
   if (!(c->cfg.flags & FEP3M_NEUTRALIZE) && std::fabs(sums[0]) > 1e-12 * sums[1]) return FEP3M_ENOTNEUTRAL;
   c->have_particles = true;
@@ -464,6 +481,7 @@ int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
     if (s2 != FEP3M_OK) return s2;
   }
   CK(cudaStreamSynchronize(c->stream));
+  if (c->counts_pending) take_counts(c);   // the pair stream was joined before the final kernels
   if (c->timing) {
     c->stats.ms_assemble = ev_ms(c, 0, 1);
     c->stats.ms_solve = ev_ms(c, 1, 2);
@@ -471,6 +489,11 @@ int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
     c->stats.ms_pair_eval = ev_ms(c, 10, 3);
     c->stats.ms_pair = c->stats.ms_pair_screen + c->stats.ms_pair_eval;
     c->stats.ms_adjoint = force ? ev_ms(c, 3, 4) : 0.0;
+    float ms = 0;
+    const fep3m::Solver& F = c->solv[0];
+    c->stats.ms_inner_solve =
+        (F.solve_exec && cudaEventElapsedTime(&ms, F.ev_in0, F.ev_in1) == cudaSuccess) ? (double)ms : 0.0;
+    (void)cudaGetLastError();
   }
   return st;
 }
@@ -527,6 +550,8 @@ int fep3m_vjp(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double*
 
 int fep3m_get_stats(const fep3m_ctx* c, fep3m_stats* out) {
   if (!c || !out) return FEP3M_EINVAL;
+  fep3m_ctx* m = const_cast<fep3m_ctx*>(c);   // folding in the pending pair counts is not a visible change
+  if (m->counts_pending && cudaEventSynchronize(m->ev_pcount) == cudaSuccess) take_counts(m);
   *out = c->stats;
   out->kernel_launches = (int64_t)g_kernel_launches;
   return FEP3M_OK;

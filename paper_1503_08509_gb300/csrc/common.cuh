@@ -155,6 +155,8 @@ struct Solver {
   double* pend_phi = nullptr;
   int iters = 0, refine_steps = 0;
   double relres = 0;
+  // recorded around the first inner solve of a replayed solve (events in the graph)
+  cudaEvent_t ev_in0 = nullptr, ev_in1 = nullptr;
 };
 
 }  // namespace fep3m
@@ -226,6 +228,9 @@ struct fep3m_ctx {
   cudaStream_t pair_stream = nullptr;  // screen contraction and singular sums (need no mesh solution)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
   cudaEvent_t ev_pfork = nullptr, ev_pjoin = nullptr;
+  cudaEvent_t ev_pcount = nullptr;          // the pair statistics' copy to host_cnt
+  unsigned long long* host_cnt = nullptr;   // pinned: 5 pair statistics of the last set_particles
+  bool counts_pending = false;
   // stats
   fep3m_stats stats;
   bool timing = false;
@@ -261,7 +266,7 @@ cudaError_t mesh_solve_end(Solver* s);
 // mesh_solve_begin re-calibrates with one more refinement sweep
 bool mesh_solve_check(Solver* s);
 cudaError_t mesh_solve(Solver* s, const double* b, double* phi);
-cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev5);
+cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev5, cudaStream_t s);
 // short-range part in two launches: the screen contraction and the singular
 // sums need only the binned charges and the vertex density, so they run on
 // their own stream while the mesh is solved; the evaluation of the mesh

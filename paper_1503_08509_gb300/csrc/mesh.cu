@@ -1075,21 +1075,42 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int NC
   tc_fence_after();
   const uint32_t tmem = *tslot;
   const uint4* bsrc = Bp + (size_t)tile * kc * 3 * (bpiece / 16);
+  // this thread's input units: 128 rows x 8 groups of 8, four per thread, eight threads per row;
+  // the next chunk's values are loaded while the current chunk's MMAs run
+  const bool vec = (K & 7) == 0;   // whole units, 32-byte aligned: two vector loads each
+  float x[4][8];
+  auto load_units = [&](int c) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int u = tid + FT_THREADS * j, row = u >> 3, g = u & 7;
+      const int64_t r = r0 + row;
+      const int a0 = 64 * c + 8 * g;
+      if (vec) {
+        float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+        if (r < R && a0 < K) {
+          const float4* src = reinterpret_cast<const float4*>(in + r * K + a0);
+          v0 = src[0];
+          v1 = src[1];
+        }
+        x[j][0] = v0.x; x[j][1] = v0.y; x[j][2] = v0.z; x[j][3] = v0.w;
+        x[j][4] = v1.x; x[j][5] = v1.y; x[j][6] = v1.z; x[j][7] = v1.w;
+      } else {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) x[j][t] = (r < R && a0 + t < K) ? in[r * K + a0 + t] : 0.f;
+      }
+    }
+  };
+  load_units(0);
   bool failed = false;
   for (int c = 0; c < kc; ++c) {
     for (int i = tid; i < 3 * (int)(bpiece / 16); i += FT_THREADS) cp_async16(tb + 16 * i, bsrc + (size_t)c * 3 * (bpiece / 16) + i);
     cp_async_commit();
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {   // 128 rows x 8 groups of 8: four per thread, eight threads per row
+    for (int j = 0; j < 4; ++j) {
       const int u = tid + FT_THREADS * j, row = u >> 3, g = u & 7;
-      const int64_t r = r0 + row;
-      const int a0 = 64 * c + 8 * g;
-      float x[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) x[t] = (r < R && a0 + t < K) ? in[r * K + a0 + t] : 0.f;
       uint32_t p0[4], p1[4], p2[4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) bf16_split2(x[2 * t], x[2 * t + 1], p0[t], p1[t], p2[t]);
+      for (int t = 0; t < 4; ++t) bf16_split2(x[j][2 * t], x[j][2 * t + 1], p0[t], p1[t], p2[t]);
       const uint32_t off = sw128_off(row, 8 * g);
       sts128(tl + off, p0);
       sts128(tl + 16384 + off, p1);
@@ -1113,6 +1134,7 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int NC
       }
       umma_commit(smem_u32(mbar));
     }
+    if (c + 1 < kc) load_units(c + 1);
     const bool done = mbar_wait(smem_u32(mbar), (uint32_t)(c & 1));
     if (__syncthreads_or(!done)) {
       failed = true;
@@ -2025,8 +2047,10 @@ static cudaError_t solve_fixed(Solver* c) {
   refine_setup(c, c->in64, phi, r32);
   reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 10);
   for (int step = 0; step < c->plan_kout; ++step) {
+    if (step == 0 && c->ev_in0) cudaEventRecordWithFlags(c->ev_in0, c->stream, cudaEventRecordExternal);
     if (c->mg.fdm.N > 0) mg.fdm_solve(r32, e32, (float*)sb[0], (float*)sb[1]);
     else mg.pcg_fixed(r32, e32, (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], c->plan_kin);
+    if (step == 0 && c->ev_in1) cudaEventRecordWithFlags(c->ev_in1, c->stream, cudaEventRecordExternal);
     refine_update(c, phi, e32);
     cudaError_t e = refine_resid(c, phi, r32);
     if (e != cudaSuccess) return e;
@@ -2173,6 +2197,7 @@ cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream) {
   if ((e = cudaMalloc(&s->res64, nodes * sizeof(double))) != cudaSuccess) return e;
   if (s->precision == FEP3M_MIXED && (e = cudaMalloc(&s->phidf, nodes * sizeof(dfv))) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&s->host_res, 2 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&s->ev_in0)) != cudaSuccess || (e = cudaEventCreate(&s->ev_in1)) != cudaSuccess) return e;
   cudaMemset(s->red_counter, 0, sizeof(unsigned int));
   cudaMemset(s->scal, 0, 64 * sizeof(double));
   if ((e = apply_set_smem()) != cudaSuccess) return e;
@@ -2180,6 +2205,9 @@ cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream) {
 }
 
 void solver_destroy(Solver* s) {
+  if (s->ev_in0) cudaEventDestroy(s->ev_in0);
+  if (s->ev_in1) cudaEventDestroy(s->ev_in1);
+  s->ev_in0 = s->ev_in1 = nullptr;
   solver_plan_free(s);
   mg_free(s);
   solver_free(s);

@@ -937,20 +937,26 @@ __global__ void __launch_bounds__(PT) k_adj_gemm(int64_t ne, int o0, int no, con
 }
 
 // A[s][k] (+)= sum over offsets o in [o0, o0 + no) with o + k inside the block of D[o][s + k + o].
-// One thread per source element s, all eight corners k: the eight readers of a
-// value D[o][e] are the neighbouring elements e - o - k + (n_sr + 1), so they
-// run in neighbouring threads and the repeated reads hit the caches.  Written
-// as a loop over the block element u = k + o (each axis in [-n_sr, n_sr], so o
-// is always a stored offset), with the wrapped element index advanced
-// incrementally; per (s, k) the terms are added with compensation, in
-// increasing o.
-template <class T>
-__global__ void k_adj_gather(int n, int n_sr, int o0, int no, int first, const int* __restrict__ count,
-                             const T* __restrict__ D, double* __restrict__ A) {
+// Each value D[o][e] is read by eight (s, k), the elements s = e - o - k +
+// (n_sr + 1) of its corners k.  ALL8 = false (small meshes, where D stays in
+// L2): one thread per (s, k), a block being 32 consecutive s (the lanes of a
+// warp: coalesced rows of D) times the eight corners (its warps).  ALL8 =
+// true (large meshes): one thread per s for all eight corners, so the eight
+// readers of a value are neighbouring threads and the reads of D from DRAM
+// are not repeated.  Written as a loop over the block element u = k + o (each
+// axis in [-n_sr, n_sr], so o is always a stored offset), with the wrapped
+// element index advanced incrementally; per (s, k) the terms are added with
+// compensation, in increasing o (the same order in both mappings).
+template <class T, bool ALL8>
+__global__ void __launch_bounds__(256) k_adj_gather(int n, int n_sr, int o0, int no, int first,
+                                                    const int* __restrict__ count, const T* __restrict__ D,
+                                                    double* __restrict__ A) {
+  constexpr int NK = ALL8 ? 8 : 1;
   const int64_t ne = (int64_t)n * n * n;
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t s = ALL8 ? blockIdx.x * (int64_t)256 + threadIdx.x : blockIdx.x * (int64_t)32 + (threadIdx.x & 31);
+  const int k0 = ALL8 ? 0 : (int)(threadIdx.x >> 5);
   if (s >= ne) return;
-  Acc<T> acc[8];   // compensated: the block's terms cancel to a small remainder
+  Acc<T> acc[NK];   // compensated: the block's terms cancel to a small remainder
   if (count[s] != 0) {
     const int keep = n_sr + 1, noff = 2 * n_sr + 2;
     const int sx = (int)(s % n), sy = (int)((s / n) % n), sz = (int)(s / ((int64_t)n * n));
@@ -959,17 +965,19 @@ __global__ void k_adj_gather(int n, int n_sr, int o0, int no, int first, const i
       const int64_t ez = wrapn(sz + uz, n);
       for (int uy = -n_sr; uy <= n_sr; ++uy) {
         const int64_t row = (int64_t)n * (wrapn(sy + uy, n) + (int64_t)n * ez);
-        int oyz[8];   // o - o0 at ux = 0, per corner
+        int oyz[NK];   // o - o0 at ux = 0, per corner
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-          oyz[k] = noff * ((uy - ((k >> 1) & 1) + keep) + noff * (uz - (k >> 2) + keep)) - (k & 1) + keep - o0;
+        for (int q = 0; q < NK; ++q) {
+          const int k = k0 + q;
+          oyz[q] = noff * ((uy - ((k >> 1) & 1) + keep) + noff * (uz - (k >> 2) + keep)) - (k & 1) + keep - o0;
+        }
         int ex = ex0;
         for (int ux = -n_sr; ux <= n_sr; ++ux) {
           const int64_t e = row + ex;
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const int oi = oyz[k] + ux;
-            if ((unsigned)oi < (unsigned)no) acc[k].add(D[(int64_t)oi * ne + e]);
+          for (int q = 0; q < NK; ++q) {
+            const int oi = oyz[q] + ux;
+            if ((unsigned)oi < (unsigned)no) acc[q].add(D[(int64_t)oi * ne + e]);
           }
           if (++ex == n) ex = 0;
         }
@@ -977,9 +985,10 @@ __global__ void k_adj_gather(int n, int n_sr, int o0, int no, int first, const i
     }
   }
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
+  for (int q = 0; q < NK; ++q) {
+    const int k = k0 + q;
     const double prev = first ? 0.0 : A[s * 8 + k];
-    A[s * 8 + k] = prev + ((double)acc[k].s - (double)acc[k].c);
+    A[s * 8 + k] = prev + ((double)acc[q].s - (double)acc[q].c);
   }
 }
 
@@ -1130,10 +1139,10 @@ __global__ void k_pair_count(int n, int n_sr, const int* __restrict__ count, uns
   }
 }
 
-cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev5) {
+cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev5, cudaStream_t s) {
   const int64_t ne = (int64_t)c->n * c->n * c->n;
-  cudaMemsetAsync(dev5, 0, 5 * sizeof(unsigned long long), c->stream);
-  FEP3M_CL k_pair_count<<<gsz(ne), PT, 0, c->stream>>>(c->n, c->n_sr, c->count, dev5);
+  cudaMemsetAsync(dev5, 0, 5 * sizeof(unsigned long long), s);
+  FEP3M_CL k_pair_count<<<gsz(ne), PT, 0, s>>>(c->n, c->n_sr, c->count, dev5);
   return cudaGetLastError();
 }
 
@@ -1307,7 +1316,12 @@ static cudaError_t screen_adjoint(fep3m_ctx* c, const T* W, const T* Hw, double*
       dim3 grid((unsigned)((ne + GT - 1) / GT), (unsigned)((no + GT - 1) / GT));
       FEP3M_CL k_adj_gemm<T><<<grid, PT, 0, s>>>(ne, o0, no, W, Hw, (T*)c->D_adj);
     }
-    FEP3M_CL k_adj_gather<T><<<gsz(ne), PT, 0, s>>>(n, c->n_sr, o0, no, o0 == 0, c->count, (const T*)c->D_adj, A);
+    if (ne >= ((int64_t)1 << 20))
+      FEP3M_CL k_adj_gather<T, true><<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(n, c->n_sr, o0, no, o0 == 0,
+                                                                                  c->count, (const T*)c->D_adj, A);
+    else
+      FEP3M_CL k_adj_gather<T, false><<<(unsigned)((ne + 31) / 32), 256, 0, s>>>(n, c->n_sr, o0, no, o0 == 0,
+                                                                                 c->count, (const T*)c->D_adj, A);
   }
   return cudaGetLastError();
 }
