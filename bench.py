@@ -36,7 +36,7 @@ L2_FLUSH_BYTES = 256 << 20
 # mesh solve (k_tc_rows) on this workload, from the ncu captures summarised in profiles/ (None until one is
 # taken of the current kernel)
 PAIR_DRAM_BYTES = 2252288
-PASS_DRAM_BYTES = None
+PASS_DRAM_BYTES = 3647744
 
 
 def parse():
