@@ -53,6 +53,18 @@ def parse():
     return p.parse_args()
 
 
+def replica_throughput(total_ms, units, steps, ws, device):
+    """Whole-job throughput of ws independent replicas that each processed `units` per step for `steps`
+    steps: the job's time is the slowest rank's (MAX over ranks).  Returns (job ms, units per second)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as tdist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, ws * units * steps / (total_ms / 1e3)
+
+
 def dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -199,17 +211,13 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.barrier()
         ck = clocks.stop() if main else None
-        total = sum(ms)
-        if ws > 1:
-            t = torch.tensor([total], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
+        total, _ = replica_throughput(sum(ms), N, steps, ws, dev)
         st = eng.stats()
         results[prec] = dict(ms=ms, total=total, steps=steps, pair=pair, launches=launches, stats=st, clocks=ck,
                              phi=out["phi"].cpu().numpy(), F=out["forces"].cpu().numpy(), U=r["U"], eng=eng)
 
     main = results[args.precision]
-    value = ws * N * main["steps"] / (main["total"] / 1e3)
+    value = ws * N * main["steps"] / (main["total"] / 1e3)   # total: already the slowest rank's
     if args.legs == "main":
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": round(value, 1), "unit": "particles/s", "n_gpus": ws,
@@ -237,12 +245,7 @@ def run_ours(args):
         eng.set_particles(pos_h, Q_h)
         eng.compute(forces=True, out=dict(phi=phi_h, forces=F_h))
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_total = sum(e2e_ms)
-    if ws > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = ws * N * args.steps / (e2e_total / 1e3)
+    e2e_total, e2e_value = replica_throughput(sum(e2e_ms), N, args.steps, ws, dev)
 
     if rank != 0:
         if ws > 1:
