@@ -1040,7 +1040,8 @@ __global__ void __launch_bounds__(256) k_fdm_axis(int N, const float* __restrict
 // accumulators: the leading product, the other five).  A (the input rows) is
 // split in the kernel into 128-byte-swizzled K-major tiles; B comes split and
 // laid out in advance (Bp: [column tile][chunk][piece][nt rows][64], zero
-// outside NC x K).  The epilogue reads one row per thread from TMEM, so a
+// outside NC x K).  nt <= 256: the two accumulators take up to all 512 TMEM
+// columns.  The epilogue reads one row per thread from TMEM, so a
 // warp's stores of one column are 32 consecutive rows.  Used for the
 // fast-diagonalisation passes (R = N^2, K = NC = N, B = W^T; SCALE: the
 // inverse eigenvalue sums, rows r = j + N k) and for the screen adjoint's
@@ -1121,7 +1122,6 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int NC
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-#pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const uint32_t a = tl + 32 * kk, b = tb + 32 * kk;
         const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
@@ -1390,10 +1390,10 @@ __global__ void k_df_to_double(int64_t n, const dfv* __restrict__ v, double* __r
 }  // namespace
 
 // allow the row GEMM the dynamic shared memory of its largest column tile
-// (nt <= 128), whatever nt a caller uses
+// (nt <= 256), whatever nt a caller uses
 cudaError_t tc_rows_prepare(int nt) {
-  if (nt > 128) return cudaErrorInvalidValue;
-  const int sm = (int)tc_rows_smem(128);
+  if (nt > 256 || nt % 16 != 0) return cudaErrorInvalidValue;
+  const int sm = (int)tc_rows_smem(256);
   cudaError_t e = cudaFuncSetAttribute(k_tc_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   return e;
@@ -1811,7 +1811,9 @@ static cudaError_t mg_setup(Solver* c) {
     cudaMemcpy(f.lam32, lf32.data(), lf32.size() * 4, cudaMemcpyHostToDevice);
     f.N = Nf;
     if (!(c->cfg.flags & FEP3M_CUDA_CORES)) {
-      // column tiles of nt modes (a multiple of 16, <= 128), enough CTAs to cover the SMs
+      // column tiles of nt modes (a multiple of 16, <= 128: two CTAs per SM), enough tiles to give every
+      // SM a CTA (measured: tiles of 192 or 256 modes, one CTA per SM, read the input fewer times but were
+      // no faster at 128^3)
       const int64_t rt = ((int64_t)Nf * Nf + 127) / 128;
       int ntile = std::max<int>((Nf + 127) / 128, (int)((148 + rt - 1) / rt));
       const int nt = ((Nf + ntile - 1) / ntile + 15) / 16 * 16;

@@ -249,3 +249,24 @@ def test_autograd_function(api):
     U.backward()
     assert maxrel(pos.grad.cpu().numpy(), dx) < 1e-10
     assert abs(U.item() - ref["U"]) < 1e-11 * abs(ref["U"])
+
+
+@pytest.mark.parametrize("n", [72, 96])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_larger_meshes_match_multigrid(api, n, precision):
+    """The fast-diagonalisation solve on 216^3 and 288^3 nodes (two and three column tiles of 112 and 96
+    modes) against the independent multigrid inner solver (pinned to the oracle at the smaller sizes
+    above) and the solver's own FP64 residual."""
+    rng = np.random.default_rng(n)
+    b = rng.normal(size=(3 * n) ** 3)
+    b -= b.mean()
+    phi = {}
+    for solver in ("fdm", "multigrid"):
+        eng = api.FEP3M(1.3, n, precision=precision, solver=solver)
+        for _ in range(2):   # calibrate, then replay the captured solve
+            phi[solver] = eng.solve_mesh(b)
+        st = eng.stats()
+        assert st["mg_rel_residual"] <= (1e-12 if precision == "fp64" else 1e-9), st
+        del eng
+    tol = 1e-11 if precision == "fp64" else 1e-7
+    assert maxrel(phi["fdm"], phi["multigrid"]) < tol, maxrel(phi["fdm"], phi["multigrid"])
