@@ -150,7 +150,9 @@ int fep3m_compute(fep3m_ctx* ctx, double* phi, double* U, double* force);
  * part uses the same multigrid on the adjoint right-hand side.             */
 int fep3m_vjp(fep3m_ctx* ctx, double gU, const double* gphi, double* dpos, double* dQ);
 
-/* Counters of the last calls (see fep3m_stats).                              */
+/* Counters of the last calls (see fep3m_stats).  The pair statistics
+ * (singular_pairs ... screen_charge_pairs) are counted on the first request
+ * after fep3m_set_particles, which then synchronises with the device.       */
 int fep3m_get_stats(const fep3m_ctx* ctx, fep3m_stats* out);
 
 /* Enable (1) / disable (0) per-stage CUDA-event timing in fep3m_stats.      */

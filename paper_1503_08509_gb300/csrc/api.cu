@@ -172,7 +172,7 @@ void take_counts(fep3m_ctx* c) {
   c->stats.max_per_element = (int)n[2];
   c->stats.screen_element_pairs = (int64_t)n[3];
   c->stats.screen_charge_pairs = (int64_t)n[4];
-  c->counts_pending = false;
+  c->counts_stale = false;
 }
 
 void solve_stats(fep3m_ctx* c) {
@@ -430,14 +430,7 @@ int fep3m_set_particles(fep3m_ctx* c, int64_t N, const double* pos, const double
   FEP3M_CL k_charge_sums<<<(unsigned)std::min<int64_t>(std::max<int64_t>(gsz(N) / 4, 1), 256), PT, 0, c->stream>>>(
       N, dQ, (double*)c->red_tmp, c->red_counter, c->scal + 32);
   ev_record(c, 7);
-  // pair statistics on the pair stream, read back by the next synchronising call
-  CK(cudaEventRecord(c->ev_pfork, c->stream));
-  CK(cudaStreamWaitEvent(c->pair_stream, c->ev_pfork, 0));
-  CK(pair_counts(c, (unsigned long long*)(c->scal + 48), c->pair_stream));
-  CK(cudaMemcpyAsync(c->host_cnt, c->scal + 48, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                     c->pair_stream));
-  CK(cudaEventRecord(c->ev_pcount, c->pair_stream));
-  c->counts_pending = true;
+  c->counts_stale = true;   // pair statistics: counted when fep3m_get_stats asks for them
   double sums[2];
   int flag = 0;
   CK(cudaMemcpyAsync(sums, c->scal + 32, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -481,7 +474,6 @@ int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
     if (s2 != FEP3M_OK) return s2;
   }
   CK(cudaStreamSynchronize(c->stream));
-  if (c->counts_pending) take_counts(c);   // the pair stream was joined before the final kernels
   if (c->timing) {
     c->stats.ms_assemble = ev_ms(c, 0, 1);
     c->stats.ms_solve = ev_ms(c, 1, 2);
@@ -550,8 +542,21 @@ int fep3m_vjp(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double*
 
 int fep3m_get_stats(const fep3m_ctx* c, fep3m_stats* out) {
   if (!c || !out) return FEP3M_EINVAL;
-  fep3m_ctx* m = const_cast<fep3m_ctx*>(c);   // folding in the pending pair counts is not a visible change
-  if (m->counts_pending && cudaEventSynchronize(m->ev_pcount) == cudaSuccess) take_counts(m);
+  // the pair statistics of the particles last set, counted on first request (on the pair stream, ordered
+  // after the binning); filling them in is not a visible change of the context
+  fep3m_ctx* m = const_cast<fep3m_ctx*>(c);
+  if (m->counts_stale && m->have_particles) {
+    if (cudaEventRecord(m->ev_pfork, m->stream) == cudaSuccess &&
+        cudaStreamWaitEvent(m->pair_stream, m->ev_pfork, 0) == cudaSuccess &&
+        pair_counts(m, (unsigned long long*)(m->scal + 48), m->pair_stream) == cudaSuccess &&
+        cudaMemcpyAsync(m->host_cnt, m->scal + 48, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        m->pair_stream) == cudaSuccess &&
+        cudaEventRecord(m->ev_pcount, m->pair_stream) == cudaSuccess &&
+        cudaEventSynchronize(m->ev_pcount) == cudaSuccess)
+      take_counts(m);
+    else
+      (void)cudaGetLastError();
+  }
   *out = c->stats;
   out->kernel_launches = (int64_t)g_kernel_launches;
   return FEP3M_OK;

@@ -230,7 +230,7 @@ struct fep3m_ctx {
   cudaEvent_t ev_pfork = nullptr, ev_pjoin = nullptr;
   cudaEvent_t ev_pcount = nullptr;          // the pair statistics' copy to host_cnt
   unsigned long long* host_cnt = nullptr;   // pinned: 5 pair statistics of the last set_particles
-  bool counts_pending = false;
+  bool counts_stale = false;               // the pair statistics predate the particles last set
   // stats
   fep3m_stats stats;
   bool timing = false;

@@ -1309,6 +1309,58 @@ __global__ void k_cg_dir(int64_t n, const double* __restrict__ scal, T* __restri
 // ------------------------------------------- double-float refinement helpers
 // bdf = b - m w3 as float pairs (m = sum b / W from the preceding reduction);
 // grid (ceil(N / bx), N, N)
+// r = s v rounded to FP32 (v the projected right-hand side as float pairs or
+// FP64, s the power-of-two scale) and |r|^2 into *out (grid of the reductions)
+template <class S>
+__global__ void k_round_scaled_norm(int64_t n, const S* __restrict__ v, float* __restrict__ r,
+                                    double* __restrict__ partials, unsigned int* __restrict__ counter,
+                                    double* __restrict__ out, double* __restrict__ scal) {
+  PDL_PROLOGUE
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
+    float x;
+    if constexpr (std::is_same<S, dfv>::value) {
+      const float sc = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_SCALE];
+      const dfv y = v[g];
+      x = (y.h + y.l) * sc;
+    } else {
+      x = (float)(v[g] * scal[SC_DERIVED + SD_SCALE]);
+    }
+    r[g] = x;
+    acc += (double)x * (double)x;
+  }
+  block_sum_finish(acc, blockIdx.x, gridDim.x, partials, counter, out, POST_NONE, 0.0, scal);
+}
+
+// phi = h + l in FP64 and its integral (sum of the order-3 node weights times
+// phi, rows per warp as in k_reduce) into *out with the mean derived (POST_MEAN, arg = 1 / n^3)
+__global__ void k_df_to_double_wsum(int N, const dfv* __restrict__ v, double* __restrict__ phi,
+                                    double* __restrict__ partials, unsigned int* __restrict__ counter,
+                                    double* __restrict__ out, double arg, double* __restrict__ scal) {
+  PDL_PROLOGUE
+  const int64_t rows = (int64_t)N * N, stride = (int64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nwarps = stride >> 5;
+  double acc = 0.0;
+  for (int64_t row = warp; row < rows; row += nwarps) {
+    const int iz = (int)(row / N), iy = (int)(row - (int64_t)iz * N);
+    const double wyz = (iy % 3 ? 0.375 : 0.25) * (iz % 3 ? 0.375 : 0.25);
+    const dfv* vr = v + row * N;
+    double* pr = phi + row * N;
+    double s0 = 0.0, s1 = 0.0;   // vertex / interior columns
+    for (int ix = lane; ix < N; ix += 32) {
+      const dfv y = vr[ix];
+      const double x = (double)y.h + (double)y.l;
+      pr[ix] = x;
+      if (ix % 3 == 0) s0 += x;
+      else s1 += x;
+    }
+    acc += wyz * (0.25 * s0 + 0.375 * s1);
+  }
+  block_sum_finish(acc, blockIdx.x, gridDim.x, partials, counter, out, POST_MEAN, arg, scal);
+}
+
 __global__ void k_split_df(int N, const double* __restrict__ b, const double* __restrict__ scal, dfv* __restrict__ bdf) {
   PDL_PROLOGUE
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1319,17 +1371,6 @@ __global__ void k_split_df(int N, const double* __restrict__ b, const double* __
   const double v = b[g] - scal[SC_DERIVED + SD_MEAN] * w;
   const float h = (float)v;
   bdf[g] = {h, (float)(v - (double)h)};
-}
-
-// r = s (h + l) rounded to FP32 (s the power-of-two scale)
-__global__ void k_df_round_scaled(int64_t n, const dfv* __restrict__ v, float* __restrict__ r,
-                                  const double* __restrict__ scal) {
-  PDL_PROLOGUE
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  const float s = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_SCALE];
-  const dfv x = v[g];
-  r[g] = (x.h + x.l) * s;
 }
 
 // phi += e / s (exact: s is a power of two), two-sum then renormalised
@@ -1361,15 +1402,6 @@ __global__ void k_project_copy64(int N, const double* __restrict__ b, const doub
   bp[g] = b[g] - scal[SC_DERIVED + SD_MEAN] * w;
 }
 
-// r = s v rounded to FP32 (s the power-of-two scale)
-__global__ void k_round_scaled64(int64_t n, const double* __restrict__ v, float* __restrict__ r,
-                                 const double* __restrict__ scal) {
-  PDL_PROLOGUE
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  r[g] = (float)(v[g] * scal[SC_DERIVED + SD_SCALE]);
-}
-
 // phi += e / s (FP64 accumulation of an FP32 correction)
 __global__ void k_add_scaled(int64_t n, double* __restrict__ phi, const float* __restrict__ e,
                              const double* __restrict__ scal) {
@@ -1377,14 +1409,6 @@ __global__ void k_add_scaled(int64_t n, double* __restrict__ phi, const float* _
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
   phi[g] += scal[SC_DERIVED + SD_INVSCALE] * (double)e[g];
-}
-
-__global__ void k_df_to_double(int64_t n, const dfv* __restrict__ v, double* __restrict__ out) {
-  PDL_PROLOGUE
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  const dfv x = v[g];
-  out[g] = (double)x.h + (double)x.l;
 }
 
 }  // namespace
@@ -1928,7 +1952,7 @@ static cudaError_t refine_resid(Solver* c, const double* phi64, float* r) {
   return cudaGetLastError();
 }
 
-// start: Pi b, the scale s, phi = 0, r = s Pi b in FP32
+// start: Pi b, the scale s, phi = 0, r = s Pi b in FP32 and |r|^2 into scal[10]
 static void refine_setup(Solver* c, const double* b, double* phi64, float* r) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
@@ -1943,12 +1967,13 @@ static void refine_setup(Solver* c, const double* b, double* phi64, float* r) {
   if (c->precision == FEP3M_FP64) {
     launch_pdl(k_project_copy64, g3, bx, 0, s, N, b, sc, c->res64);
     cudaMemsetAsync(phi64, 0, n * sizeof(double), s);
-    launch_pdl(k_round_scaled64, grid_for(n), TPB, 0, s, (int64_t)n, c->res64, r, sc);
+    launch_pdl(k_round_scaled_norm<double>, (int)reduce_blocks(n), TPB, 0, s, (int64_t)n, (const double*)c->res64,
+               r, (double*)c->red_tmp, c->red_counter, sc + 10, sc);
   } else {
     launch_pdl(k_split_df, g3, bx, 0, s, N, b, sc, reinterpret_cast<dfv*>(c->res64));
     cudaMemsetAsync(c->phidf, 0, n * sizeof(dfv), s);
-    launch_pdl(k_df_round_scaled, grid_for(n), TPB, 0, s, (int64_t)n, reinterpret_cast<const dfv*>(c->res64), r,
-                                                           sc);
+    launch_pdl(k_round_scaled_norm<dfv>, (int)reduce_blocks(n), TPB, 0, s, (int64_t)n,
+               reinterpret_cast<const dfv*>(c->res64), r, (double*)c->red_tmp, c->red_counter, sc + 10, sc);
   }
 }
 
@@ -1969,9 +1994,11 @@ static void refine_finish(Solver* c, double* phi) {
   const size_t n = L0.size;
   const double W = (double)L0.n * L0.n * L0.n;
   if (c->precision != FEP3M_FP64)
-    launch_pdl(k_df_to_double, grid_for(n), TPB, 0, c->stream, (int64_t)n, reinterpret_cast<const dfv*>(c->phidf),
-                                                                phi);
-  reduce<double>(c, N, RD_WSUM, phi, nullptr, c->scal + 6, POST_MEAN, 1.0 / W);
+    launch_pdl(k_df_to_double_wsum, (int)reduce_blocks(n), TPB, 0, c->stream, N,
+               reinterpret_cast<const dfv*>(c->phidf), phi, (double*)c->red_tmp, c->red_counter, c->scal + 6,
+               1.0 / W, c->scal);
+  else
+    reduce<double>(c, N, RD_WSUM, phi, nullptr, c->scal + 6, POST_MEAN, 1.0 / W);
   project<double>(c, N, phi, 1);
 }
 
@@ -1997,8 +2024,7 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
   const int maxout = c->cfg.mg_max_cycles > 0 ? c->cfg.mg_max_cycles : 10;
   float* r32 = (float*)sb[5];
   float* e32 = (float*)sb[4];
-  refine_setup(c, b, phi, r32);
-  reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 10);
+  refine_setup(c, b, phi, r32);   // |r|^2 into sc[10]
   double bb = 0;
   cudaMemcpyAsync(&bb, sc + 10, sizeof(double), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
@@ -2046,8 +2072,7 @@ static cudaError_t solve_fixed(Solver* c) {
   float* r32 = (float*)sb[5];
   float* e32 = (float*)sb[4];
   double* phi = c->out64;
-  refine_setup(c, c->in64, phi, r32);
-  reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 10);
+  refine_setup(c, c->in64, phi, r32);   // |r|^2 into sc[10]
   for (int step = 0; step < c->plan_kout; ++step) {
     if (step == 0 && c->ev_in0) cudaEventRecordWithFlags(c->ev_in0, c->stream, cudaEventRecordExternal);
     if (c->mg.fdm.N > 0) mg.fdm_solve(r32, e32, (float*)sb[0], (float*)sb[1]);
