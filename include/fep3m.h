@@ -187,6 +187,13 @@ int fep3m_solve_mesh(fep3m_ctx* ctx, const double* b, double* phi);
  * s = 6 n_sr + 7.                                                            */
 int fep3m_get_table(const fep3m_ctx* ctx, double* table);
 
+/* The 1-D eigenbasis of the fast-diagonalisation mesh solve (host only, no
+ * context or GPU): the generalized eigenpairs K1 v = lam M1 v of the periodic
+ * order-3 stiffness and mass matrices on n_el elements of unit length
+ * (N = 3 n_el nodes), M1-orthonormal.  lam: N values; V: N x N host array,
+ * V[node * N + mode].  Returns FEP3M_EINVAL for n_el < 1 or n_el > 4096.    */
+int fep3m_mesh_eigenbasis(int n_el, double* lam, double* V);
+
 /* Load vector without any allocation (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory: work issued while a
  * stream is being captured into a CUDA graph, applications whose memory

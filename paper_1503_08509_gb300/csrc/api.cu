@@ -626,6 +626,17 @@ int fep3m_solve_mesh(fep3m_ctx* c, const double* b, double* phi) {
   return rel <= 10 * rtol ? FEP3M_OK : FEP3M_ENOCONV;
 }
 
+int fep3m_mesh_eigenbasis(int n_el, double* lam, double* V) {
+  if (n_el < 1 || n_el > 4096 || !lam || !V) return FEP3M_EINVAL;
+  fep3m::Stencils st;
+  fep3m::make_stencils(st);
+  std::vector<double> l, v;
+  fep3m::periodic_eigen(n_el, st, l, v);
+  std::memcpy(lam, l.data(), l.size() * sizeof(double));
+  std::memcpy(V, v.data(), v.size() * sizeof(double));
+  return FEP3M_OK;
+}
+
 int fep3m_get_table(const fep3m_ctx* c, double* table) {
   if (!c || !table) return FEP3M_EINVAL;
   if (is_device_ptr(table)) {
