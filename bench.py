@@ -271,11 +271,11 @@ def run_ours(args):
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
 
-    # roofline of the step's dominant kernel (the largest share of the step's launch time,
-    # profiles/launches_nacl32_mixed_step.md): k_tc_rows, the tensor-core transform passes of the mesh
-    # solve.  Each pass reads and writes the (3n)^3 FP32 vector once: SURVEY 8(d)'s 8 B per DOF per
-    # fine-level sweep of the mesh solve.  Timed with CUDA events recorded inside the replayed solve graph
-    # around the forward solve's first inner solve (six passes), concurrent with the rest of the step.
+    # roofline of the step's dominant kernel (the largest share of the step's launch time in the ncu launch
+    # list): k_tc_rows, the tensor-core transform passes of the mesh solve.  Each pass reads and writes the
+    # (3n)^3 FP32 vector once: 8 B per degree of freedom per fine-level sweep of the mesh solve.  Timed with
+    # CUDA events recorded inside the replayed solve graph around the forward solve's first inner solve (six
+    # passes), concurrent with the rest of the step.
     nodes = (3 * d["n_el"]) ** 3
     inner_ms = statistics.mean(p[1] for p in main["pair"])
     pass_ms = inner_ms / 6 if inner_ms > 0 else float("nan")
@@ -294,7 +294,7 @@ def run_ours(args):
 
     # roofline of the short-range kernel the method is built around: k_pair_screen (FP32 issue bound),
     # timed with CUDA events on its own stream, where it runs concurrently with the forward and adjoint mesh
-    # solves.  achieved = SURVEY 8(d)'s algorithmic count for a build that collapses the screen sums per
+    # solves.  achieved = the algorithmic element-to-point count for a build that collapses the screen sums per
     # target element (1024 flops per non-empty target element and non-empty element of its block, 20 per
     # singular pair with gradients; the 128 per target of the 64-node evaluation belong to k_pair_eval);
     # the per-target-charge count and the flops the kernel executes (vertex-regrouped contraction: 512 x 64

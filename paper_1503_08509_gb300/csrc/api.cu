@@ -546,6 +546,7 @@ int fep3m_get_stats(const fep3m_ctx* c, fep3m_stats* out) {
   // after the binning); filling them in is not a visible change of the context
   fep3m_ctx* m = const_cast<fep3m_ctx*>(c);
   if (m->counts_stale && m->have_particles) {
+    const unsigned long long launches = g_kernel_launches;   // bookkeeping, not a launch of the method
     if (cudaEventRecord(m->ev_pfork, m->stream) == cudaSuccess &&
         cudaStreamWaitEvent(m->pair_stream, m->ev_pfork, 0) == cudaSuccess &&
         pair_counts(m, (unsigned long long*)(m->scal + 48), m->pair_stream) == cudaSuccess &&
@@ -556,6 +557,7 @@ int fep3m_get_stats(const fep3m_ctx* c, fep3m_stats* out) {
       take_counts(m);
     else
       (void)cudaGetLastError();
+    g_kernel_launches = launches;
   }
   *out = c->stats;
   out->kernel_launches = (int64_t)g_kernel_launches;
