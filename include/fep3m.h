@@ -8,7 +8,8 @@
  * and the energy U = 1/2 sum_i Q_i Phi_i (Eq. potentialenergy), split as
  * Phi = Phi^sr + Phi^sm (Eq. phisplit): a polynomial screen of order q = 1
  * (Sec. 2.1, Eq. moment1d) turns the long-range part into a periodic order
- * p = 3 finite-element Poisson problem (Sec. 2.2) solved here by multigrid,
+ * p = 3 finite-element Poisson problem (Sec. 2.2) solved here by iterative
+ * refinement around an exact FP32 fast-diagonalisation solve (or multigrid),
  * evaluated at the charges by Eq. evalsmooth (Sec. 2.3); the short-range
  * part (Sec. 2.4, Eq. sc, self term Sec. 2.5) is a sum over the
  * (2 n_sr + 1)^3 elements around each charge's element using FE basis-screen
@@ -74,11 +75,15 @@ typedef struct {
   int n_sr;            /* short-range block half-width in elements, 1..4 (3 in
                           the paper's tests, Sec. 4: a 7 x 7 x 7 block)         */
   int precision;       /* FEP3M_FP64 or FEP3M_MIXED.  Both solve the mesh
-                          system by iterative refinement around an FP32
-                          multigrid-preconditioned CG; the iterate and residual
-                          are FP64 (FP64) or double-float pairs (MIXED).  Pair
-                          and screen sums run in FP64 (FP64) or FP32 (MIXED);
-                          projections and the energy reduction in FP64.         */
+                          system by iterative refinement around an FP32 inner
+                          solve (fast diagonalisation on the tensor cores, or
+                          with FEP3M_MULTIGRID a multigrid-preconditioned CG);
+                          the iterate and residual are FP64 (FP64) or
+                          double-float pairs (MIXED).  Pair and screen sums run
+                          in FP64 (FP64) or FP32 (MIXED; the screen
+                          contractions as split-precision bf16 tensor-core
+                          MMAs unless FEP3M_CUDA_CORES); projections and the
+                          energy reduction in FP64.                              */
   double mg_rtol;      /* relative FE residual target; 0 -> 1e-13 (FP64) or
                           1e-10 (MIXED)                                          */
   int mg_max_cycles;   /* cap on refinement sweeps; 0 -> 10                      */
@@ -122,8 +127,8 @@ typedef struct {
 
 /* Create a context: validates cfg, builds the FE basis-screen table (a
  * Dirichlet order-3 FE solve around one vertex hat, Remark of Sec. 4), the
- * multigrid hierarchy for the periodic mesh and the screen constants
- * (Eq. moment1d).  cuda_stream is a cudaStream_t (NULL = legacy default).
+ * mesh solver (the 1-D eigenbasis of the fast-diagonalisation solve and the
+ * multigrid hierarchy) and the screen constants (Eq. moment1d).  cuda_stream is a cudaStream_t (NULL = legacy default).
  * On success *out owns everything and must be released by fep3m_destroy.  */
 int fep3m_create(const fep3m_config* cfg, void* cuda_stream, fep3m_ctx** out);
 
@@ -147,7 +152,7 @@ int fep3m_compute(fep3m_ctx* ctx, double* phi, double* U, double* force);
  * writes dLf/dx (N x 3) into dpos and dLf/dQ (N) into dQ (host or device;
  * either may be NULL).  gphi may be NULL (zero).  The derivative is that of
  * the discrete method (element and block membership held fixed); the mesh
- * part uses the same multigrid on the adjoint right-hand side.             */
+ * part uses the same mesh solver on the adjoint right-hand side.           */
 int fep3m_vjp(fep3m_ctx* ctx, double gU, const double* gphi, double* dpos, double* dQ);
 
 /* Counters of the last calls (see fep3m_stats).  The pair statistics
@@ -178,7 +183,7 @@ int fep3m_get_mesh(const fep3m_ctx* ctx, double* C, double* b, double* phi_mesh)
 
 /* Solve the periodic FE system K phi = b - (sum b) w / sum w, int phi = 0,
  * for a caller right-hand side b ((3n)^3, host or device) with the context's
- * multigrid (precision as configured); writes phi (physical units).  Used
+ * mesh solver (precision as configured); writes phi (physical units).  Used
  * to test the solver alone.                                                 */
 int fep3m_solve_mesh(fep3m_ctx* ctx, const double* b, double* phi);
 

@@ -35,9 +35,9 @@ def _f64(x, shape):
 
 
 class FEP3M:
-    """One FE-P3M context: mesh, screen tables and multigrid for a periodic cube.
+    """One FE-P3M context: mesh, screen tables and mesh solver for a periodic cube.
 
-    precision: 'fp64' or 'mixed' (FP32 pairs and multigrid, FP64 refinement).
+    precision: 'fp64' or 'mixed' (FP32 pair sums and inner mesh solve, FP64 refinement).
     tensor_cores: False runs the split-precision contractions (the mixed pair
     kernel's screen field, the fast-diagonalisation transforms) on the FP32
     CUDA cores instead of as bf16 tensor-core MMAs.

@@ -13,7 +13,7 @@ namespace fep3m {
 extern unsigned long long g_kernel_launches;
 #define FEP3M_CL (void)++::fep3m::g_kernel_launches,
 
-// Programmatic dependent launch (the multigrid solve: hundreds of short
+// Programmatic dependent launch (the mesh solve: chains of short
 // dependent kernels).  A kernel launched by launch_pdl may be set up while the
 // kernel before it on the stream finishes; its first statement must be
 // pdl_wait(), which returns once the preceding grid has completed and its
@@ -127,7 +127,7 @@ struct Hierarchy {
   int cheb_degree = 4;
 };
 
-// One multigrid solver instance (the context holds two, so that the forward
+// One mesh solver instance (the context holds two, so that the forward
 // and adjoint mesh solves can run concurrently on different streams).
 struct Solver {
   fep3m_config cfg;

@@ -8,13 +8,18 @@
 // Everything on the mesh is in reference units (element size 1): the
 // physical mesh potential is phi / h.  K is the Kronecker sum of 1-D periodic
 // order-3 stiffness and mass matrices, applied matrix-free by sum
-// factorisation (three 7-tap passes).  The solver is a conjugate gradient
-// preconditioned by one multigrid V-cycle: h-coarsening with the same order-3
-// operator on every level (the coarse spaces are nested, so the Galerkin
-// coarse operator is the coarse-mesh operator), Chebyshev-Jacobi smoothing
-// and an exact coarsest solve by fast diagonalisation.  FEP3M_MIXED runs the
-// cycle and the CG in FP32 inside an FP64 iterative-refinement loop whose
-// residual, projections and update are FP64.
+// factorisation (three 7-tap passes).  Both precisions solve by iterative
+// refinement (residual and iterate in FP64, or in double-float pairs for
+// FEP3M_MIXED) around an FP32 inner solve:
+//   - by default the exact one by fast diagonalisation: with the 1-D
+//     generalized eigenpairs K1 V = M1 V Lambda, V^T M1 V = I, the
+//     pseudo-inverse of K is (V x V x V) diag(1 / (l_i + l_j + l_k)) (V x V x V)^T,
+//     six dense transform passes on the tensor cores;
+//   - or (FEP3M_MULTIGRID) a conjugate gradient preconditioned by one
+//     multigrid V-cycle: h-coarsening with the same order-3 operator on every
+//     level (the coarse spaces are nested, so the Galerkin coarse operator is
+//     the coarse-mesh operator), Chebyshev-Jacobi smoothing and an exact
+//     coarsest solve by fast diagonalisation.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
