@@ -1,6 +1,5 @@
-// Short-range evaluation (Sec. 2.4-2.5) fused with the smooth-potential
-// evaluation (Sec. 2.3, Eq. evalsmooth), and the reverse sweeps of the
-// adjoint.
+// Short-range evaluation (Sec. 2.4-2.5) and the smooth-potential evaluation
+// (Sec. 2.3, Eq. evalsmooth), and the reverse sweeps of the adjoint.
 //
 // For a target charge t in element e (local coordinate tau_t in [0,1]^3):
 //   Phi_t = (1/h) sum_m G_e[m] u_m(tau_t) + sum_{j in block(e), j != t} Q_j / |x_j - x_t|
@@ -16,6 +15,11 @@
 // which equal the full vertex density r_v inside the block and partial sums on
 // its boundary.  H(o, m) is the table value at node m of an element at offset
 // o (element units) from the vertex.
+//
+// Two launches per evaluation: k_pair_screen (the screen field sum_o A_e(o)
+// H(o, m) and the singular sums; it needs no mesh solution and runs while the
+// mesh is solved) and k_pair_eval (G_e and the contraction with u_m(tau_t)
+// after the solve).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -66,19 +70,19 @@ template <class T> struct Acc {
   __device__ __forceinline__ T get() const { return s - c; }
 };
 
-// ------------------------------------------------------------ brick kernel
-// One CTA per brick of BX x BY x BZ target elements:
+// ----------------------------------------------------------- brick kernels
+// k_pair_screen: one CTA per brick of BX x BY x BZ target elements:
 //  (1) the brick's "extended vertex field" R in shared memory (below);
 //  (2) the screen field of all brick elements at their 64 nodes,
-//      G[e][m] = phi[node(e, m)] - sum_o A(e, o) H(o, m), as 512 rank-1
-//      updates of a 64 x 64 tile (4 x 4 register tile per thread), staging A
-//      and H in chunks of OCH offsets;
+//      sum_o A(e, o) H(o, m): on the tensor cores (split bf16 MMAs) or as 512
+//      rank-1 updates of a 64 x 64 tile on the CUDA cores (4 x 4 register
+//      tile per thread, A and H staged in chunks of OCH offsets);
 //  (3) the charges of the brick's short-range halo, staged in shared memory
 //      in element order (when they fit) with each charge's halo x index;
-//  (4) four threads per target: the smooth-and-screen potential from G at 16
-//      of the 64 nodes each, and the singular sum over a quarter of the 49
-//      element rows of the target's block, each row one contiguous run of
-//      staged charges.
+//  (4) a few threads per target, each summing some of the 49 element rows of
+//      the target's block (one contiguous run of staged charges per row).
+// k_pair_eval: one CTA per brick after the solve: G = phi - screen field at
+// the nodes, contracted with the shape functions at each target.
 constexpr int BX = 4, BY = 4, BZ = 4, BE = BX * BY * BZ;   // 64 elements per brick
 constexpr int OCH = 32;                                      // offsets per chunk
 constexpr int MAXRUN = 2 * 81;                               // rows of the block (n_sr <= 4), 2 runs each
