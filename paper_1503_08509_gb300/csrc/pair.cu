@@ -43,7 +43,19 @@ __device__ __forceinline__ int wrapn(int i, int n) {
 }
 
 template <class T> __device__ __forceinline__ T rsq(T x);
-template <> __device__ __forceinline__ double rsq<double>(double x) { return 1.0 / sqrt(x); }
+// 1 / sqrt(x) in FP64 by Newton-Raphson on f(y) = 1 / y^2 - x, y <- y (3 - x y^2) / 2,
+// from the FP32 hardware estimate (relative error ~2^-23): the error squares at
+// each step (~2^-46, then below FP64 rounding), for a fraction of the cost of an
+// FP64 square root and division.  Outside the FP32 range of the estimate
+// (including x = 0, coincident charges) the FP64 division is used.
+template <> __device__ __forceinline__ double rsq<double>(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+  const double hx = 0.5 * x;
+  y = y * fma(-hx * y, y, 1.5);
+  y = y * fma(-hx * y, y, 1.5);
+  return y;
+}
 // the hardware reciprocal square root refined by one Newton step, y (3 - x y^2) / 2
 template <> __device__ __forceinline__ float rsq<float>(float x) {
   const float y = rsqrtf(x);
