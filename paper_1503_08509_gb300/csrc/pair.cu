@@ -472,13 +472,15 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
     if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
     if (failed) return;
   } else {
-  // CUDA cores: 4 x 4 register tile, per-chunk partial sums added into a total
+  // CUDA cores: 4 x 4 register tile, per-chunk partial sums added into a
+  // total.  FP64: the chunk sums run in double-float arithmetic on the FP32
+  // pipes (FP64 issues at a small fraction of the FP32 rate here): A and H are
+  // staged as hi + lo float pairs, each product keeps its exact leading part
+  // (fused two-product) and the two cross terms, and the products are summed
+  // by two-sum into a hi + lo accumulator; each chunk's sum goes into an FP64
+  // total, which keeps the relative error near 2^-48 of the chunk's sum of
+  // |A H| instead of growing over all offsets.
   const int eb = tid >> 4, mb = tid & 15;
-  T acc[4][4], tot[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) tot[i][j] = T(0);
   // this thread stages entries i = tid + k PT: element l = i & 63 is fixed per thread
   const int lst = tid & 63;
   const int lam = (lst % BX) + SW * (((lst / BX) % BY) + SW * (lst / (BX * BY)));
@@ -489,50 +491,121 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
     const int i = tid + k * PT, o = i >> 6;
     hpf[k] = o < no3 ? Hw[(int64_t)o * 64 + (i & 63)] : T(0);
   }
-  for (int o0 = 0; o0 < no3; o0 += OCH) {
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < SPT; ++k) {
-      const int i = tid + k * PT;
-      const int o = o0 + (i >> 6);
-      H_c[i] = hpf[k];
-      A_c[i] = o < no3 ? R[otab[o] + lam] : T(0);
-    }
-    __syncthreads();
-    if (o0 + OCH < no3) {
-#pragma unroll
-      for (int k = 0; k < SPT; ++k) {
-        const int i = tid + k * PT, o = o0 + OCH + (i >> 6);
-        hpf[k] = o < no3 ? Hw[(int64_t)o * 64 + (i & 63)] : T(0);
-      }
-    }
+  T* gb = Gscr + (int64_t)blockIdx.x * (BE * 64);
+  if constexpr (sizeof(T) == 8) {
+    float sh[4][4], sl[4][4];
+    double tot[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-#pragma unroll 4
-    for (int oi = 0; oi < OCH; ++oi) {
-      // one vector load each (16 lanes share the A row: a broadcast; the H
-      // rows of the 16 mb are contiguous: conflict-free)
-      const V4 av = *reinterpret_cast<const V4*>(A_c + oi * 64 + 4 * eb);
-      const V4 hv = *reinterpret_cast<const V4*>(H_c + oi * 64 + 4 * mb);
-      const T a[4] = {av.x, av.y, av.z, av.w}, hh[4] = {hv.x, hv.y, hv.z, hv.w};
+      for (int j = 0; j < 4; ++j) tot[i][j] = 0.0;
+    float2* A2 = reinterpret_cast<float2*>(A_c);
+    float2* H2 = reinterpret_cast<float2*>(H_c);
+    auto split = [](double v) {
+      const float hi = (float)v;
+      return make_float2(hi, (float)(v - (double)hi));
+    };
+    for (int o0 = 0; o0 < no3; o0 += OCH) {
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < SPT; ++k) {
+        const int i = tid + k * PT;
+        const int o = o0 + (i >> 6);
+        H2[i] = split((double)hpf[k]);
+        A2[i] = split(o < no3 ? (double)R[otab[o] + lam] : 0.0);
+      }
+      __syncthreads();
+      if (o0 + OCH < no3) {
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+          const int i = tid + k * PT, o = o0 + OCH + (i >> 6);
+          hpf[k] = o < no3 ? Hw[(int64_t)o * 64 + (i & 63)] : T(0);
+        }
+      }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * hh[j];
+        for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
+#pragma unroll 2
+      for (int oi = 0; oi < OCH; ++oi) {
+        const float4* ap = reinterpret_cast<const float4*>(A2 + oi * 64 + 4 * eb);
+        const float4* hp = reinterpret_cast<const float4*>(H2 + oi * 64 + 4 * mb);
+        const float4 a01 = ap[0], a23 = ap[1], h01 = hp[0], h23 = hp[1];
+        const float ah[4] = {a01.x, a01.z, a23.x, a23.z}, al[4] = {a01.y, a01.w, a23.y, a23.w};
+        const float hh[4] = {h01.x, h01.z, h23.x, h23.z}, hl[4] = {h01.y, h01.w, h23.y, h23.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float p = ah[i] * hh[j];
+            float e = fmaf(ah[i], hh[j], -p);
+            e = fmaf(ah[i], hl[j], e);
+            e = fmaf(al[i], hh[j], e);
+            const float t = sh[i][j] + p, z = t - sh[i][j];
+            sl[i][j] += ((sh[i][j] - (t - z)) + (p - z)) + e;
+            sh[i][j] = t;
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tot[i][j] += (double)sh[i][j] + (double)sl[i][j];
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      V4 v;
+      v.x = tot[i][0];
+      v.y = tot[i][1];
+      v.z = tot[i][2];
+      v.w = tot[i][3];
+      *reinterpret_cast<V4*>(gb + (4 * eb + i) * 64 + 4 * mb) = v;
+    }
+  } else {
+    T acc[4][4], tot[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j];
-  }
-  // the brick's screen fields: row l of the brick (64 nodes) per element, one
-  // vector store per (i); the 16 mb of a row are contiguous.  Region 1 (R) was
-  // last read before the loop's final barrier, so the staging below may
-  // overwrite it without another one.
-  {
-    T* gb = Gscr + (int64_t)blockIdx.x * (BE * 64);
+      for (int j = 0; j < 4; ++j) tot[i][j] = T(0);
+    for (int o0 = 0; o0 < no3; o0 += OCH) {
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < SPT; ++k) {
+        const int i = tid + k * PT;
+        const int o = o0 + (i >> 6);
+        H_c[i] = hpf[k];
+        A_c[i] = o < no3 ? R[otab[o] + lam] : T(0);
+      }
+      __syncthreads();
+      if (o0 + OCH < no3) {
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+          const int i = tid + k * PT, o = o0 + OCH + (i >> 6);
+          hpf[k] = o < no3 ? Hw[(int64_t)o * 64 + (i & 63)] : T(0);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+#pragma unroll 4
+      for (int oi = 0; oi < OCH; ++oi) {
+        // one vector load each (16 lanes share the A row: a broadcast; the H
+        // rows of the 16 mb are contiguous: conflict-free)
+        const V4 av = *reinterpret_cast<const V4*>(A_c + oi * 64 + 4 * eb);
+        const V4 hv = *reinterpret_cast<const V4*>(H_c + oi * 64 + 4 * mb);
+        const T a[4] = {av.x, av.y, av.z, av.w}, hh[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * hh[j];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j];
+    }
+    // the brick's screen fields: row l of the brick (64 nodes) per element, one
+    // vector store per (i); the 16 mb of a row are contiguous
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       V4 v;
@@ -543,6 +616,8 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
       *reinterpret_cast<V4*>(gb + (4 * eb + i) * 64 + 4 * mb) = v;
     }
   }
+  // Region 1 (R) was last read before the chunk loop's final barrier, so the
+  // staging below may overwrite it without another one.
   }
   // (3) stage the halo charges if they fit (region 1 is free now)
   const int nh = HW * HW * HW;
@@ -906,19 +981,34 @@ __global__ void k_node_assemble(int n, const T* __restrict__ W, double* __restri
 constexpr int GT = 64;   // GEMM tile: 64 elements x 64 offsets, K = 64 nodes
 constexpr int ADJ_NT = 128;   // tensor-core column tile: offsets per tile
 
+// FP64: the products are summed in double-float arithmetic on the FP32 pipes,
+// as in the screen contraction (hi + lo float pairs in shared memory, fused
+// two-product with the cross terms, two-sum accumulation), in two halves of
+// 32 nodes whose sums are added in FP64.
 template <class T>
 __global__ void __launch_bounds__(PT) k_adj_gemm(int64_t ne, int o0, int no, const T* __restrict__ W,
                                                  const T* __restrict__ Hw, T* __restrict__ D) {
   __shared__ T Ws[64][GT + 1];   // [m][element]
   __shared__ T Hs[64][GT + 1];   // [m][offset]
+  constexpr bool DF = sizeof(T) == 8;
+  float2(*Ws2)[GT + 1] = reinterpret_cast<float2(*)[GT + 1]>(Ws);
+  float2(*Hs2)[GT + 1] = reinterpret_cast<float2(*)[GT + 1]>(Hs);
   const int64_t e0 = (int64_t)blockIdx.x * GT;
   const int oo0 = o0 + blockIdx.y * GT;
   for (int i = threadIdx.x; i < GT * 64; i += PT) {
     const int r = i >> 6, m = i & 63;
     const int64_t e = e0 + r;
-    Ws[m][r] = e < ne ? W[e * 64 + m] : T(0);
     const int o = oo0 + r;
-    Hs[m][r] = (o < o0 + no) ? Hw[(int64_t)o * 64 + m] : T(0);
+    const T w = e < ne ? W[e * 64 + m] : T(0);
+    const T hv = (o < o0 + no) ? Hw[(int64_t)o * 64 + m] : T(0);
+    if constexpr (DF) {
+      const float wh = (float)w, hh = (float)hv;
+      Ws2[m][r] = make_float2(wh, (float)((double)w - (double)wh));
+      Hs2[m][r] = make_float2(hh, (float)((double)hv - (double)hh));
+    } else {
+      Ws[m][r] = w;
+      Hs[m][r] = hv;
+    }
   }
   __syncthreads();
   const int te = threadIdx.x & 15, to = threadIdx.x >> 4;   // 4 elements x 4 offsets per thread
@@ -927,18 +1017,54 @@ __global__ void __launch_bounds__(PT) k_adj_gemm(int64_t ne, int o0, int no, con
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-#pragma unroll 8
-  for (int m = 0; m < 64; ++m) {
-    T a[4], b[4];
+  if constexpr (DF) {
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+      float sh[4][4], sl[4][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      a[i] = Ws[m][te + 16 * i];
-      b[i] = Hs[m][to + 16 * i];
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
+#pragma unroll 4
+      for (int m = 32 * half; m < 32 * half + 32; ++m) {
+        float2 a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          a[i] = Ws2[m][te + 16 * i];
+          b[i] = Hs2[m][to + 16 * i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float p = a[i].x * b[j].x;
+            float e = fmaf(a[i].x, b[j].x, -p);
+            e = fmaf(a[i].x, b[j].y, e);
+            e = fmaf(a[i].y, b[j].x, e);
+            const float t = sh[i][j] + p, z = t - sh[i][j];
+            sl[i][j] += ((sh[i][j] - (t - z)) + (p - z)) + e;
+            sh[i][j] = t;
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += (double)sh[i][j] + (double)sl[i][j];
     }
+  } else {
+#pragma unroll 8
+    for (int m = 0; m < 64; ++m) {
+      T a[4], b[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 4; ++i) {
+        a[i] = Ws[m][te + 16 * i];
+        b[i] = Hs[m][to + 16 * i];
+      }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
