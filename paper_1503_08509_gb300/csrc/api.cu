@@ -283,7 +283,7 @@ void fep3m_destroy(fep3m_ctx* c) {
   free_particles(c);
   void* p[] = {c->Hw64, c->Hw32, c->count, c->start, c->fill, c->scan_tmp, c->C, c->rv, c->Cv, c->b64, c->phi64,
                c->res64, c->g64, c->lam64, c->scal, c->iflags, c->phi_hl, c->W_el, c->A_el, c->mu_v, c->Gscr, c->Hb, c->HbA,
-               c->red_tmp, c->red_counter, c->D_adj};
+               c->Hdf, c->red_tmp, c->red_counter, c->D_adj};
   for (void* q : p) dfree(q);
   fep3m::solver_destroy(&c->solv[0]);
   fep3m::solver_destroy(&c->solv[1]);
@@ -348,6 +348,17 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
   if ((st = from_cuda(dalloc(&c->Hw32, Hw.size()))) != FEP3M_OK) return fail(st);
   cudaMemcpy(c->Hw64, Hw.data(), Hw.size() * 8, cudaMemcpyHostToDevice);
   cudaMemcpy(c->Hw32, Hw32.data(), Hw32.size() * 4, cudaMemcpyHostToDevice);
+  if (c->precision == FEP3M_FP64) {
+    // hi = fl32(H), lo = fl32(H - hi): the operand pairs of the FP64 path's
+    // double-float screen contraction
+    std::vector<float> hdf(2 * Hw.size());
+    for (size_t i = 0; i < Hw.size(); ++i) {
+      hdf[2 * i] = (float)Hw[i];
+      hdf[2 * i + 1] = (float)(Hw[i] - (double)hdf[2 * i]);
+    }
+    if ((st = from_cuda(cudaMalloc(&c->Hdf, hdf.size() * 4))) != FEP3M_OK) return fail(st);
+    cudaMemcpy(c->Hdf, hdf.data(), hdf.size() * 4, cudaMemcpyHostToDevice);
+  }
   if (c->precision == FEP3M_MIXED && !(cfg->flags & FEP3M_CUDA_CORES)) {
     // bf16 pieces of the table for the tensor-core screen contraction
     std::vector<uint16_t> hb(pair_tc_table_bytes(c->n_sr) / 2);

@@ -218,6 +218,7 @@ struct fep3m_ctx {
   void* Gscr = nullptr;          // screen field at each brick element's 64 nodes, bricks * 4096 (T)
   void* Hb = nullptr;            // bf16 pieces of the table for the tensor-core contraction (MIXED)
   void* HbA = nullptr;           // the same for the screen adjoint's contraction (MIXED)
+  void* Hdf = nullptr;           // hi + lo float pairs of the table, the double-float screen contraction (FP64)
   int* host_err = nullptr;       // pinned: device-side error flags read after a step
   double* red_tmp = nullptr;     // reduction partials (1024)
   unsigned int* red_counter = nullptr;

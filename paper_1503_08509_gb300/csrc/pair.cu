@@ -43,18 +43,19 @@ __device__ __forceinline__ int wrapn(int i, int n) {
 }
 
 template <class T> __device__ __forceinline__ T rsq(T x);
-// 1 / sqrt(x) in FP64 by Newton-Raphson on f(y) = 1 / y^2 - x, y <- y (3 - x y^2) / 2,
-// from the FP32 hardware estimate (relative error ~2^-23): the error squares at
-// each step (~2^-46, then below FP64 rounding), for a fraction of the cost of an
-// FP64 square root and division.  Outside the FP32 range of the estimate
-// (including x = 0, coincident charges) the FP64 division is used.
+// 1 / sqrt(x) in FP64 from the FP32 hardware estimate y (relative error
+// ~2^-22), refined by one third-order (Householder) step: with e = 1 - x y^2,
+// 1 / sqrt(x) = y (1 - e)^(-1/2) = y (1 + e/2 + 3 e^2 / 8 + O(e^3)), and the
+// dropped term is below 2^-64 (emulated worst case 0.9 ulp).  Outside
+// [2^-100, 2^100), where the FP32 estimate could under- or overflow
+// (including x = 0, coincident charges, and negative or NaN x), the FP64
+// division is used; the range test reads the exponent bits on the integer pipe.
 template <> __device__ __forceinline__ double rsq<double>(double x) {
-  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
-  double y = (double)rsqrtf((float)x);
-  const double hx = 0.5 * x;
-  y = y * fma(-hx * y, y, 1.5);
-  y = y * fma(-hx * y, y, 1.5);
-  return y;
+  const int bexp = __double2hiint(x) >> 20;   // sign and biased exponent
+  if ((unsigned)(bexp - 923) >= 200u) return 1.0 / sqrt(x);
+  const double y = (double)rsqrtf((float)x);
+  const double e = fma(-x * y, y, 1.0);
+  return fma(y * e, fma(0.375, e, 0.5), y);
 }
 // the hardware reciprocal square root refined by one Newton step, y (3 - x y^2) / 2
 template <> __device__ __forceinline__ float rsq<float>(float x) {
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
                                                              const typename vec4<T>::type* __restrict__ part,
                                                              const T* __restrict__ Cv, const T* __restrict__ rv,
                                                              const T* __restrict__ Hw, const uint4* __restrict__ Hb,
-                                                             T* __restrict__ Gscr, double* __restrict__ phi_s,
+                                                             const float2* __restrict__ Hdf, T* __restrict__ Gscr, double* __restrict__ phi_s,
                                                              double* __restrict__ E_s, double* __restrict__ psi,
                                                              double* __restrict__ gpsi, int* __restrict__ err) {
   static_assert(!TC || sizeof(T) == 4, "the tensor-core contraction is the FP32 path's");
@@ -368,7 +369,14 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
         if (((tx >> kx) & 1) && ((ty >> ky) & 1) && ((tz >> kz) & 1)) val += c8[k];
       }
     }
-    R[i] = val;
+    if constexpr (sizeof(T) == 8) {
+      // FP64: split once here into the hi + lo floats of the double-float
+      // contraction (each R value is read by several offsets)
+      const float vh = (float)val;
+      reinterpret_cast<float2*>(R)[i] = make_float2(vh, (float)((double)val - (double)vh));
+    } else {
+      R[i] = val;
+    }
   }
   // (2) screen field
   if constexpr (TC) {
@@ -485,14 +493,16 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
   const int lst = tid & 63;
   const int lam = (lst % BX) + SW * (((lst / BX) % BY) + SW * (lst / (BX * BY)));
   constexpr int SPT = OCH * 64 / PT;   // staged entries per thread per chunk
-  T hpf[SPT];                          // next chunk's table values, fetched during this chunk
-#pragma unroll
-  for (int k = 0; k < SPT; ++k) {
-    const int i = tid + k * PT, o = i >> 6;
-    hpf[k] = o < no3 ? Hw[(int64_t)o * 64 + (i & 63)] : T(0);
-  }
   T* gb = Gscr + (int64_t)blockIdx.x * (BE * 64);
   if constexpr (sizeof(T) == 8) {
+    // the table's hi + lo floats come precomputed (Hdf); R was split in (1)
+    float2 hpf[SPT];                   // next chunk's table values, fetched during this chunk
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+      const int i = tid + k * PT, o = i >> 6;
+      hpf[k] = o < no3 ? Hdf[(int64_t)o * 64 + (i & 63)] : make_float2(0.f, 0.f);
+    }
+    const float2* R2 = reinterpret_cast<const float2*>(R);
     float sh[4][4], sl[4][4];
     double tot[4][4];
 #pragma unroll
@@ -501,25 +511,21 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
       for (int j = 0; j < 4; ++j) tot[i][j] = 0.0;
     float2* A2 = reinterpret_cast<float2*>(A_c);
     float2* H2 = reinterpret_cast<float2*>(H_c);
-    auto split = [](double v) {
-      const float hi = (float)v;
-      return make_float2(hi, (float)(v - (double)hi));
-    };
     for (int o0 = 0; o0 < no3; o0 += OCH) {
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < SPT; ++k) {
         const int i = tid + k * PT;
         const int o = o0 + (i >> 6);
-        H2[i] = split((double)hpf[k]);
-        A2[i] = split(o < no3 ? (double)R[otab[o] + lam] : 0.0);
+        H2[i] = hpf[k];
+        A2[i] = o < no3 ? R2[otab[o] + lam] : make_float2(0.f, 0.f);
       }
       __syncthreads();
       if (o0 + OCH < no3) {
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
           const int i = tid + k * PT, o = o0 + OCH + (i >> 6);
-          hpf[k] = o < no3 ? Hw[(int64_t)o * 64 + (i & 63)] : T(0);
+          hpf[k] = o < no3 ? Hdf[(int64_t)o * 64 + (i & 63)] : make_float2(0.f, 0.f);
         }
       }
 #pragma unroll
@@ -561,6 +567,12 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
       *reinterpret_cast<V4*>(gb + (4 * eb + i) * 64 + 4 * mb) = v;
     }
   } else {
+    T hpf[SPT];                        // next chunk's table values, fetched during this chunk
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+      const int i = tid + k * PT, o = i >> 6;
+      hpf[k] = o < no3 ? Hw[(int64_t)o * 64 + (i & 63)] : T(0);
+    }
     T acc[4][4], tot[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -1305,7 +1317,7 @@ static cudaError_t launch_pair_screen(fep3m_ctx* c, const T* Hw, cudaStream_t s,
   if (e != cudaSuccess) return e;
   FEP3M_CL kern<<<(unsigned)pair_bricks(c), TC ? PTC : PT, smem, s>>>(
       c->n, c->n_sr, (T)c->h, c->start, c->count, (const typename vec4<T>::type*)c->part, (const T*)c->Cv,
-      (const T*)c->rv, Hw, (const uint4*)c->Hb, (T*)c->Gscr, c->phi_s, c->E_s, half ? c->psi_s : nullptr,
+      (const T*)c->rv, Hw, (const uint4*)c->Hb, (const float2*)c->Hdf, (T*)c->Gscr, c->phi_s, c->E_s, half ? c->psi_s : nullptr,
       half ? c->gpsi_s : nullptr, c->iflags + 2);
   return cudaGetLastError();
 }
