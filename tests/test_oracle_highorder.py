@@ -1,0 +1,150 @@
+"""Pins for the order-q screen oracle (oracle.highorder): screens of order q >= 2 with the
+order p = q + 2 mesh (Sec. 2.1, Sec. 2.4, the Remark of Sec. 4, Fig. decayavg, Fig. compareerr)."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import ewald, fe1d, fep3m, highorder, screens, tables
+from paper_1503_08509_gb300 import workloads
+
+
+def test_q1_table_is_the_hat_table():
+    # for q = 1 the only basis-screen type is the vertex hat of oracle.tables
+    H, _ = tables.basis_screen_table(3, 8, 8)
+    H1, _ = highorder.type_table(3, 1, (0, 0, 0), 8, 8)
+    assert np.abs(H - H1).max() < 1e-14 * np.abs(H).max()
+
+
+def test_q1_reduces_to_the_q1_oracle():
+    pos, Q = workloads.uniform_pm(60, seed=6)
+    a = fep3m.forward(pos, Q, 1.0, 8)
+    b = highorder.forward(pos, Q, 1.0, 8, 1, half_width=8, ngl=8)
+    assert np.abs(a['phi'] - b['phi']).max() < 1e-13 * np.abs(a['phi']).max()
+
+
+@pytest.mark.parametrize("q", [2, 3])
+def test_type_tables_symmetries(q):
+    # every box is symmetric about its screen's support: type 0 is even about its
+    # vertex, interior type i is the mirror image of type q - i about the element
+    # centre, and permuting the axes permutes the types
+    p, hw = q + 2, 3
+    T = {t3: highorder.type_table(p, q, t3, hw, 6)[0] for t3 in itertools.product(range(q), repeat=3)}
+    scale = max(np.abs(H).max() for H in T.values())
+    for t3, H in T.items():
+        for perm in itertools.permutations(range(3)):
+            tp = tuple(t3[a] for a in perm)
+            assert np.abs(T[tp] - H.transpose(perm)).max() < 1e-12 * scale, (t3, perm)
+        for a in range(3):
+            tm = list(t3)
+            tm[a] = (q - t3[a]) % q
+            assert np.abs(T[tuple(tm)] - np.flip(H, axis=a)).max() < 1e-12 * scale, (t3, a)
+
+
+def independent_mixed_column(p, q, node, lo, nel):
+    """int phi^p_k psi dx with psi the order-q nodal function of the centred element's
+    local node `node` (oracle.screens.omega_pieces, element [-1/2, 1/2]), shifted so its
+    anchor vertex sits at 0, by Gauss-Legendre quadrature of the product on each element."""
+    pieces = screens.omega_pieces(q, 1.0)[node]
+    shift = 0.5 - (1.0 if node == q else 0.0)
+    t, w = fe1d.gauss_legendre01(p + q + 2)
+    m1 = np.zeros(p * nel + 1)
+    for e in range(nel):
+        x = lo + e + t
+        psi = np.zeros_like(x)
+        for (a, b, f) in pieces:
+            inside = (x - shift >= a) & (x - shift <= b)
+            psi = np.where(inside, f(np.clip(x - shift, a, b)), psi)
+        m1[p * e:p * e + p + 1] += np.einsum('g,g,gk->k', w, psi, fe1d.lagrange_values(p, t))
+    return m1
+
+
+@pytest.mark.parametrize("q, t3", [(2, (0, 0, 0)), (2, (1, 0, 1)), (3, (2, 0, 1)), (3, (0, 1, 2))])
+def test_type_table_solves_dirichlet_problem(q, t3):
+    p, hw = q + 2, 3
+    H, x1 = highorder.type_table(p, q, t3, hw, 6)
+    ext = [highorder.box_extent(t, hw) for t in t3]
+    nel = [hi - lo for lo, hi in ext]
+    Me, Ke = fe1d.element_matrices(p, 1.0)
+    M1 = [fe1d.assemble_open(Me, ne, p) for ne in nel]
+    K1 = [fe1d.assemble_open(Ke, ne, p) for ne in nel]
+    m1 = [independent_mixed_column(p, q, t, lo, ne) for t, (lo, _), ne in zip(t3, ext, nel)]
+    rhs = 4 * np.pi * m1[0][:, None, None] * m1[1][None, :, None] * m1[2][None, None, :]
+    KH = (tables.kron_apply(K1[0], M1[1], M1[2], H) + tables.kron_apply(M1[0], K1[1], M1[2], H)
+          + tables.kron_apply(M1[0], M1[1], K1[2], H))
+    assert np.abs((KH - rhs)[1:-1, 1:-1, 1:-1]).max() < 1e-12 * np.abs(rhs).max()
+    # boundary rows: the continuum potential, here with a finer quadrature
+    pts = np.array([[x1[0][0], x1[1][3], x1[2][7]], [x1[0][-1], x1[1][-1], x1[2][9]]])
+    ref = highorder.basis_potential_continuum(q, t3, pts, ngl=16)
+    assert np.allclose([H[0, 3, 7], H[-1, -1, 9]], ref, rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("q", [2, 3])
+def test_nodal_density_carries_charge_and_dipole(q):
+    # Eq. moment1d with l = 0, 1: the screens hold each charge's total and its first
+    # moments, so the order-q nodal density integrates to sum Q and sum Q x
+    n, L = 5, 1.0
+    pos, Q = workloads.uniform_pm(40, seed=4)
+    pos = pos * 0.6 + 0.2                             # away from the periodic seam
+    b = fep3m.bin_particles(pos, L, n)
+    r = highorder.nodal_density(highorder.element_coefficients(b, Q, n, q), n, q)
+    w = fe1d.node_integrals_periodic(q, n, L / n)
+    assert abs(np.einsum('ijk,i,j,k->', r, w, w, w) - Q.sum()) < 1e-12 * np.abs(Q).sum()
+    # first moment along x: nodes of the order-q mesh at i h / q, integrated with
+    # x * psi_i (the density's support crosses no periodic seam here)
+    t, wg = fe1d.gauss_legendre01(q + 2)
+    h = L / n
+    wx = np.zeros(q * n)
+    for e in range(n):
+        x = (e + t) * h
+        lv = fe1d.lagrange_values(q, t)
+        for i in range(q + 1):
+            wx[(q * e + i) % (q * n)] += h * np.sum(wg * x * lv[:, i])
+    mx = np.einsum('ijk,i,j,k->', r, wx, w, w)
+    assert abs(mx - np.dot(Q, pos[:, 0])) < 1e-12 * np.abs(Q).sum()
+
+
+@pytest.mark.parametrize("q", [2, 3])
+def test_screened_potential_decays_like_r_minus_q_plus_2(q):
+    # Fig. decayavg: the charge-plus-screen potential of order q decays like R^-(q+2);
+    # the screen is built from the type/anchor map the tables use (local node i of
+    # the element [-1/2, 1/2]: anchor -1/2 + [i = q], type i mod q)
+    delta = np.array([0.23, -0.11, 0.37])
+    c = screens.screen_coefficients(q, 1.0, delta[None, :])[0]
+    rng = np.random.default_rng(1)
+    dirs = rng.normal(size=(16, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    vals = {}
+    for R in (4.0, 8.0):
+        x = delta + R * dirs
+        phi_sc = np.zeros(len(x))
+        for kap in range((q + 1) ** 3):
+            loc = highorder.local_node(kap, q)
+            anchor = -0.5 + (loc == q)
+            t3 = tuple(int(v) for v in loc % q)
+            phi_sc += c[kap] * highorder.basis_potential_continuum(q, t3, x - anchor, ngl=12)
+        vals[R] = np.sqrt(np.mean((1.0 / R - phi_sc) ** 2))
+    slope = np.log(vals[8.0] / vals[4.0]) / np.log(2.0)
+    assert -(q + 2) - 0.35 < slope < -(q + 2) + 0.35, slope
+
+
+def test_whole_element_shift_is_exact_q2():
+    pos, Q = workloads.uniform_pm(50, seed=12)
+    n = 7
+    a = highorder.forward(pos, Q, 1.0, n, 2, n_sr=2)
+    b = highorder.forward(pos + np.array([1, -2, 3]) / n, Q, 1.0, n, 2, n_sr=2)
+    assert np.abs(a['phi'] - b['phi']).max() < 1e-11 * np.abs(a['phi']).max()
+
+
+def test_error_against_ewald_falls_with_q():
+    # Fig. compareerr: the error against a converged Ewald sum falls fast with q
+    # (measured here: 8.0e-3, 1.6e-3, 3.5e-4 for q = 1, 2, 3 at n = 8, n_sr = 2)
+    pos, Q = workloads.uniform_pm(100, seed=9)
+    pe = ewald.ewald(pos, Q, 1.0)
+    err = {}
+    for q in (1, 2, 3):
+        d = highorder.forward(pos, Q, 1.0, 8, q, n_sr=2)['phi'] - pe
+        d -= d.mean()                                   # potentials agree up to a constant (Sec. 4)
+        err[q] = np.linalg.norm(d) / np.linalg.norm(pe)
+    assert err[1] < 2e-2, err
+    assert err[2] < err[1] / 3 and err[3] < err[2] / 3, err
