@@ -123,13 +123,14 @@ def type_table(p, q, t3, half_width=6, ngl=6):
     return H, tuple(x1)
 
 
-def kept_tables(p, q, keep, half_width=None, ngl=6):
-    """Nodal values of every type's table on [-keep, keep]^3 about its anchor:
-    dict t3 -> array ((2 keep p + 1),)*3."""
+def kept_tables(p, q, keep, half_width=None, ngl=6, interior_only=False):
+    """Nodal values of each type's table on [-keep, keep]^3 about its anchor:
+    dict t3 -> array ((2 keep p + 1),)*3; interior_only: the types with no vertex
+    factor (all that one-element screens use)."""
     if half_width is None:
         half_width = keep + 2
     out = {}
-    for t3 in itertools.product(range(q), repeat=3):
+    for t3 in itertools.product(range(1 if interior_only else 0, q), repeat=3):
         H, _ = type_table(p, q, t3, half_width, ngl)
         s = p * (half_width - keep)
         e = p * (half_width + keep) + 1
@@ -143,9 +144,34 @@ def local_node(kappa, q):
     return np.array([kappa % q1, (kappa // q1) % q1, kappa // (q1 * q1)])
 
 
-def element_coefficients(bins, Q, n, q):
-    """C[e, kappa] = sum_{j in e} Q_j c_kappa(delta_j), shape (n^3, (q+1)^3), units charge/h^3."""
-    c = screens.screen_coefficients(q, bins['h'], bins['delta'])
+def one_element_coefficients(q, h, delta3):
+    """Screens confined to the charge's element (one-element screens, Sec. 5.3): only the
+    (q-1)^3 interior nodes carry weight.  Per axis the q - 1 interior weights solve the
+    moment system of Eq. moment1d for l = 0 .. q-2 (the interior functions vanish outside
+    the element, so their moments are the rows l < q - 1, columns 1 .. q-1 of the
+    patch moment matrix).  Returns (..., (q+1)^3), zero on the element's face nodes."""
+    assert q >= 2, "a one-element screen needs an interior node"
+    delta3 = np.asarray(delta3, dtype=np.float64)
+    Om = screens.moment_matrix_1d(q, h)[:q - 1, 1:q]
+    w = []
+    for a in range(3):
+        rhs = np.stack([delta3[..., a] ** l for l in range(q - 1)], axis=-1)
+        wi = np.linalg.solve(Om, rhs[..., None])[..., 0]
+        full = np.zeros(delta3.shape[:-1] + (q + 1,))
+        full[..., 1:q] = wi
+        w.append(full)
+    c = w[2][..., :, None, None] * w[1][..., None, :, None] * w[0][..., None, None, :]
+    return c.reshape(delta3.shape[:-1] + ((q + 1) ** 3,))
+
+
+def element_coefficients(bins, Q, n, q, support='patch'):
+    """C[e, kappa] = sum_{j in e} Q_j c_kappa(delta_j), shape (n^3, (q+1)^3), units charge/h^3.
+    support='patch': the screens of Eq. moment1d on the element's (q+1)^3 nodes;
+    support='element': one-element screens on its interior nodes."""
+    if support == 'element':
+        c = one_element_coefficients(q, bins['h'], bins['delta'])
+    else:
+        c = screens.screen_coefficients(q, bins['h'], bins['delta'])
     C = np.zeros((n ** 3, c.shape[1]))
     np.add.at(C, bins['cell'], np.asarray(Q)[:, None] * c)
     return C
@@ -181,6 +207,8 @@ def screen_window_matrix(n_sr, p, q, kept):
         loc = local_node(kap, q)
         s = (loc == q).astype(int)
         t3 = tuple(int(x) for x in loc % q)
+        if t3 not in kept:
+            continue                              # a node no screen uses (one-element screens)
         Hk = kept[t3]
         for k, d in enumerate(offs):
             base = p * (-d - s + keep)
@@ -188,16 +216,17 @@ def screen_window_matrix(n_sr, p, q, kept):
     return W.reshape(len(offs) * q1 ** 3, p1 ** 3)
 
 
-def forward(pos, Q, L, n, q, n_sr=3, neutralise=True, chunk=1024, half_width=None, ngl=6):
+def forward(pos, Q, L, n, q, n_sr=3, neutralise=True, chunk=1024, half_width=None, ngl=6, support='patch'):
     """Phi_i and U for charges Q at pos (N x 3) with order-q screens and the order p = q + 2
-    mesh (Sec. 2: p = q + 2), with the intermediates."""
+    mesh (Sec. 2: p = q + 2), with the intermediates.  support='element' uses one-element
+    screens (Sec. 5.3), still with p = q + 2."""
     pos = np.asarray(pos, dtype=np.float64)
     Q = np.asarray(Q, dtype=np.float64)
     assert n >= 2 * n_sr + 1, "the short-range block must not wrap onto itself"
     p = q + 2
     bins = bin_particles(pos, L, n)
     h = bins['h']
-    C = element_coefficients(bins, Q, n, q)
+    C = element_coefficients(bins, Q, n, q, support)
     r = nodal_density(C, n, q)
     ops = MeshOperators(L, n, p, q)
     b = ops.load_vector(r)
@@ -208,7 +237,7 @@ def forward(pos, Q, L, n, q, n_sr=3, neutralise=True, chunk=1024, half_width=Non
     ix, iy, iz = element_node_index(bins['c3'], n, p)
     phi_sm = np.einsum('nm,nm->n', phi_mesh[ix, iy, iz], U3)
     phi_sing, _ = singular_sums(bins, Q, n, n_sr)
-    kept = kept_tables(p, q, n_sr + 1, half_width, ngl)
+    kept = kept_tables(p, q, n_sr + 1, half_width, ngl, interior_only=support == 'element')
     Wmat = screen_window_matrix(n_sr, p, q, kept)
     offs = block_offsets(n_sr)
     phi_scr = np.zeros(len(Q))

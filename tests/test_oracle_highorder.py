@@ -148,3 +148,66 @@ def test_error_against_ewald_falls_with_q():
         err[q] = np.linalg.norm(d) / np.linalg.norm(pe)
     assert err[1] < 2e-2, err
     assert err[2] < err[1] / 3 and err[3] < err[2] / 3, err
+
+
+# ------------------------------------------------- one-element screens (Sec. 5.3)
+def one_element_screened_rms(q, Rs):
+    delta = np.array([0.21, -0.1, 0.33])
+    c = highorder.one_element_coefficients(q, 1.0, delta[None, :])[0]
+    rng = np.random.default_rng(1)
+    dirs = rng.normal(size=(16, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    out = {}
+    for R in Rs:
+        x = delta + R * dirs
+        phi = np.zeros(len(x))
+        for kap in np.flatnonzero(c):
+            loc = highorder.local_node(kap, q)
+            assert np.all((loc > 0) & (loc < q))             # interior nodes only
+            phi += c[kap] * highorder.basis_potential_continuum(q, tuple(int(v) for v in loc), x + 0.5, ngl=12)
+        out[R] = np.sqrt(np.mean((1.0 / R - phi) ** 2))
+    return out
+
+
+@pytest.mark.parametrize("q", [2, 3, 4])
+def test_one_element_screens_decay_like_r_minus_q(q):
+    # Sec. 5.3: confining the screen to the charge's element loses two powers of decay
+    # (q = 3 gives R^-3 instead of R^-5), but the asymptotic rate starts near R^ = 1
+    # instead of 3: the slope is already -q between 2 and 4 element widths
+    v = one_element_screened_rms(q, (2.0, 4.0, 8.0))
+    far = np.log(v[8.0] / v[4.0]) / np.log(2.0)
+    near = np.log(v[4.0] / v[2.0]) / np.log(2.0)
+    assert abs(far + q) < 0.15 and abs(near + q) < 0.2, (far, near)
+
+
+def test_one_element_density_stays_in_the_element_and_keeps_charge_and_dipole():
+    q, n, L = 3, 5, 1.0
+    pos, Q = workloads.uniform_pm(40, seed=4)
+    pos = pos * 0.6 + 0.2
+    b = fep3m.bin_particles(pos, L, n)
+    r = highorder.nodal_density(highorder.element_coefficients(b, Q, n, q, 'element'), n, q)
+    idx = np.arange(q * n)
+    face = (idx % q) == 0
+    assert np.all(r[face, :, :] == 0) and np.all(r[:, face, :] == 0) and np.all(r[:, :, face] == 0)
+    w = fe1d.node_integrals_periodic(q, n, L / n)
+    assert abs(np.einsum('ijk,i,j,k->', r, w, w, w) - Q.sum()) < 1e-12 * np.abs(Q).sum()
+    h = L / n
+    t, wg = fe1d.gauss_legendre01(q + 2)
+    wx = np.zeros(q * n)
+    for e in range(n):
+        lv = fe1d.lagrange_values(q, t)
+        for i in range(q + 1):
+            wx[(q * e + i) % (q * n)] += h * np.sum(wg * (e + t) * h * lv[:, i])
+    assert abs(np.einsum('ijk,i,j,k->', r, w, wx, w) - np.dot(Q, pos[:, 1])) < 1e-12 * np.abs(Q).sum()
+
+
+def test_one_element_screens_against_ewald():
+    # measured: 7.4e-3 (q = 3) and 3.9e-4 (q = 4) at n = 8, n_sr = 2
+    pos, Q = workloads.uniform_pm(100, seed=9)
+    pe = ewald.ewald(pos, Q, 1.0)
+    err = {}
+    for q in (3, 4):
+        d = highorder.forward(pos, Q, 1.0, 8, q, n_sr=2, support='element')['phi'] - pe
+        d -= d.mean()
+        err[q] = np.linalg.norm(d) / np.linalg.norm(pe)
+    assert err[3] < 2e-2 and err[4] < err[3] / 5, err
