@@ -199,6 +199,31 @@ int fep3m_get_table(const fep3m_ctx* ctx, double* table);
  * V[node * N + mode].  Returns FEP3M_EINVAL for n_el < 1 or n_el > 4096.    */
 int fep3m_mesh_eigenbasis(int n_el, double* lam, double* V);
 
+/* Host-only building blocks for screens of order q >= 2 and the order
+ * p = q + 2 mesh (Sec. 2: p = q + 2); no context or GPU is involved.
+ *
+ * fep3m_mesh_eigenbasis_order: as fep3m_mesh_eigenbasis for the periodic
+ * order-p matrices (equispaced Lagrange nodes, N = p n_el nodes): lam: N
+ * values, V: N x N host array, V[node * N + mode], M1-orthonormal.
+ * FEP3M_EINVAL unless 1 <= p <= 8, n_el >= 1 and p n_el <= 8192.
+ *
+ * fep3m_screen_type_table: the FE table (Remark of Sec. 4) of one basis
+ * screen of order q (1 <= q <= 4).  The order-q nodal functions of the screen
+ * mesh come in q types per axis: type 0, the function of a vertex (support
+ * the two elements next to it), and type t = 1 .. q-1, the interior function
+ * of an element with its node at t/q.  (tx, ty, tz) picks the product
+ * screen; the table is the order-(q+2) Galerkin solution of
+ * -Lap H = 4 pi psi (h = 1) on a box reaching n_sr + 1 + pad elements
+ * beyond the screen's anchor vertex (the left vertex of the element holding
+ * its node) on each side, one element more on the right along interior-type
+ * axes, with the continuum potential of psi as Dirichlet data.  kept: host
+ * array of K^3 values, K = 2 (n_sr + 1)(q + 2) + 1, the nodal values on
+ * [-(n_sr+1), n_sr+1]^3 about the anchor in steps of 1/(q+2), index
+ * ix + K iy + K^2 iz.  For q = 1 this is the table of fep3m_get_table.
+ * FEP3M_EINVAL for q, n_sr (1..4), pad (1..8) or a type out of range.       */
+int fep3m_mesh_eigenbasis_order(int p, int n_el, double* lam, double* V);
+int fep3m_screen_type_table(int q, int tx, int ty, int tz, int n_sr, int pad, double* kept);
+
 /* Load vector without any allocation (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory: work issued while a
  * stream is being captured into a CUDA graph, applications whose memory

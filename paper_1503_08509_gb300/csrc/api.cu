@@ -54,10 +54,6 @@ void dfree(void* p) {
   if (p) cudaFree(p);
 }
 
-__global__ void k_scale(int64_t n, double* x, double a) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) x[i] *= a;
-}
 template <class A>
 __global__ void k_to_double(int64_t n, const A* in, double* out, double a) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

@@ -243,6 +243,7 @@ namespace fep3m {
 // host setup (setup.cpp)
 void element_matrices_q3(double Me[4][4], double Ke[4][4], double Mpq[4][2]);
 void make_stencils(Stencils& st);
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
 void generalized_eigen(int n, const std::vector<double>& A, const std::vector<double>& B,
                        std::vector<double>& lam, std::vector<double>& V);
 void periodic_eigen(int n, const Stencils& st, std::vector<double>& lam, std::vector<double>& V);

@@ -1,0 +1,298 @@
+// Create-time host computations for screens of any order q and the order
+// p = q + 2 mesh: equispaced Lagrange element matrices, the 1-D eigenbasis of
+// the periodic order-p mesh (block-Fourier reduction), and the FE tables of the
+// q^3 basis-screen types (Remark of Sec. 4).  Host code only; nothing here runs
+// per evaluation.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fep3m {
+
+namespace {
+
+// Equispaced order-p Lagrange basis on [0, 1] at t, and its derivative
+// (product rule, one factor at a time).
+void lagrange(int p, double t, double* v, double* d) {
+  for (int k = 0; k <= p; ++k) {
+    const double xk = (double)k / p;
+    double val = 1.0, der = 0.0;
+    for (int j = 0; j <= p; ++j) {
+      if (j == k) continue;
+      const double xj = (double)j / p, den = xk - xj;
+      der = der * (t - xj) / den + val / den;
+      val *= (t - xj) / den;
+    }
+    v[k] = val;
+    if (d) d[k] = der;
+  }
+}
+
+// Element matrices on [0, 1] (h = 1): mass Me and stiffness Ke of the order-p
+// basis ((p+1) x (p+1)), mixed mass Mpq = int l^p_i l^q_j ((p+1) x (q+1)).
+struct ElementPQ {
+  int p, q;
+  std::vector<double> Me, Ke, Mpq;
+  ElementPQ(int p_, int q_) : p(p_), q(q_), Me((p_ + 1) * (p_ + 1)), Ke((p_ + 1) * (p_ + 1)), Mpq((p_ + 1) * (q_ + 1)) {
+    std::vector<double> x, w;
+    gauss_legendre01(p + 2, x, w);   // exact for degree 2 p + 3
+    std::vector<double> v(p + 1), d(p + 1), vq(q + 1);
+    for (size_t g = 0; g < x.size(); ++g) {
+      lagrange(p, x[g], v.data(), d.data());
+      lagrange(q, x[g], vq.data(), nullptr);
+      for (int i = 0; i <= p; ++i) {
+        for (int j = 0; j <= p; ++j) {
+          Me[i * (p + 1) + j] += w[g] * v[i] * v[j];
+          Ke[i * (p + 1) + j] += w[g] * d[i] * d[j];
+        }
+        for (int j = 0; j <= q; ++j) Mpq[i * (q + 1) + j] += w[g] * v[i] * vq[j];
+      }
+    }
+  }
+};
+
+// y = A x along one axis of an n0 x n1 x n2 array (index i0 + n0 (i1 + n1 i2)),
+// A dense na x na (row major), na = the axis length.
+void axis_apply(const int dims[3], const std::vector<double>& A, const std::vector<double>& x, std::vector<double>& y,
+                int axis, bool transpose) {
+  y.assign(x.size(), 0.0);
+  const size_t s[3] = {1, (size_t)dims[0], (size_t)dims[0] * dims[1]};
+  const int na = dims[axis], o1 = (axis + 1) % 3, o2 = (axis + 2) % 3;
+  for (int j1 = 0; j1 < dims[o1]; ++j1)
+    for (int j2 = 0; j2 < dims[o2]; ++j2) {
+      const size_t base = j1 * s[o1] + j2 * s[o2];
+      for (int i = 0; i < na; ++i) {
+        double acc = 0;
+        for (int k = 0; k < na; ++k)
+          acc += (transpose ? A[(size_t)k * na + i] : A[(size_t)i * na + k]) * x[base + k * s[axis]];
+        y[base + i * s[axis]] = acc;
+      }
+    }
+}
+
+// Quadrature of the 1-D type-t order-q nodal function (anchor at 0, element
+// units): points and weights times the function, ngl Gauss points per
+// polynomial piece.  Type 0: the vertex function on [-1, 0] (local node q of
+// the left element) and [0, 1] (local node 0 of the right one); type t >= 1:
+// local node t of the element [0, 1].
+void type_quadrature(int q, int t, int ngl, std::vector<double>& px, std::vector<double>& pw) {
+  std::vector<double> x, w, vq(q + 1);
+  gauss_legendre01(ngl, x, w);
+  px.clear();
+  pw.clear();
+  auto piece = [&](double lo, int node) {
+    for (int g = 0; g < ngl; ++g) {
+      lagrange(q, x[g], vq.data(), nullptr);
+      px.push_back(lo + x[g]);
+      pw.push_back(w[g] * vq[node]);
+    }
+  };
+  if (t == 0) {
+    piece(-1.0, q);
+    piece(0.0, 0);
+  } else {
+    piece(0.0, t);
+  }
+}
+
+}  // namespace
+
+// Generalized eigenpairs K1 v = lam M1 v of the periodic 1-D order-p matrices on
+// n elements (N = p n nodes), V M1-orthonormal, V[node * N + mode].  The
+// matrices are block circulant with p x p blocks B_d (d = -1, 0, 1): element
+// e's local node l is node l mod p of element e + [l = p].  Per wavenumber
+// k (theta = 2 pi k / n) the span of {cos(theta e) w, sin(theta e) w} is
+// invariant, so each k is a 2p x 2p problem (p x p for k = 0 and k = n / 2)
+// with the matrices (n/2) [[Sc, Ss], [-Ss, Sc]], Sc = sum_d B_d cos(theta d),
+// Ss = sum_d B_d sin(theta d), and n Sc for the real modes.
+void periodic_eigen_order(int p, int n, std::vector<double>& lam, std::vector<double>& V) {
+  const ElementPQ E(p, 1);
+  const int N = p * n, pp = p * p;
+  std::vector<double> BK(3 * pp, 0.0), BM(3 * pp, 0.0);   // [d + 1][tau][tau']
+  for (int l = 0; l <= p; ++l)
+    for (int l2 = 0; l2 <= p; ++l2) {
+      const int d = (l2 == p) - (l == p);
+      const size_t at = (size_t)(d + 1) * pp + (l % p) * p + (l2 % p);
+      BK[at] += E.Ke[l * (p + 1) + l2];
+      BM[at] += E.Me[l * (p + 1) + l2];
+    }
+  lam.clear();
+  V.assign((size_t)N * N, 0.0);
+  int mode = 0;
+  for (int k = 0; 2 * k <= n; ++k) {
+    const double th = 2.0 * M_PI * k / n;
+    const bool real = k == 0 || 2 * k == n;
+    const int m = real ? p : 2 * p;
+    std::vector<double> Kc(pp, 0.0), Ks(pp, 0.0), Mc(pp, 0.0), Ms(pp, 0.0);
+    for (int d = -1; d <= 1; ++d)
+      for (int i = 0; i < pp; ++i) {
+        Kc[i] += BK[(d + 1) * pp + i] * std::cos(th * d);
+        Ks[i] += BK[(d + 1) * pp + i] * std::sin(th * d);
+        Mc[i] += BM[(d + 1) * pp + i] * std::cos(th * d);
+        Ms[i] += BM[(d + 1) * pp + i] * std::sin(th * d);
+      }
+    const double w = real ? (double)n : 0.5 * n;
+    std::vector<double> A((size_t)m * m, 0.0), B((size_t)m * m, 0.0);
+    for (int a = 0; a < p; ++a)
+      for (int b = 0; b < p; ++b) {
+        A[(size_t)a * m + b] = w * Kc[a * p + b];
+        B[(size_t)a * m + b] = w * Mc[a * p + b];
+        if (!real) {
+          A[(size_t)a * m + p + b] = w * Ks[a * p + b];
+          A[(size_t)(p + a) * m + b] = -w * Ks[a * p + b];
+          A[(size_t)(p + a) * m + p + b] = w * Kc[a * p + b];
+          B[(size_t)a * m + p + b] = w * Ms[a * p + b];
+          B[(size_t)(p + a) * m + b] = -w * Ms[a * p + b];
+          B[(size_t)(p + a) * m + p + b] = w * Mc[a * p + b];
+        }
+      }
+    std::vector<double> lk, vk;
+    generalized_eigen(m, A, B, lk, vk);
+    for (int j = 0; j < m; ++j, ++mode) {
+      lam.push_back(lk[j]);
+      for (int e = 0; e < n; ++e) {
+        const double ce = std::cos(th * e), se = std::sin(th * e);
+        for (int tau = 0; tau < p; ++tau) {
+          double v = vk[(size_t)tau * m + j] * ce;
+          if (!real) v += vk[(size_t)(p + tau) * m + j] * se;
+          V[(size_t)(p * e + tau) * N + mode] = v;
+        }
+      }
+    }
+  }
+}
+
+// FE table of the basis screen of type (t0, t1, t2) (order q, order-p mesh,
+// h = 1; Remark of Sec. 4): the Galerkin solution H of -Lap H = 4 pi psi on a
+// box extending B = keep + pad elements beyond the screen's anchor vertex on
+// each side, and one element more on the right along interior-type axes (so
+// the box is symmetric about the screen's support), with the continuum
+// potential of psi (Eq. screenintegral, tensor Gauss-Legendre, ngl points per
+// piece) as Dirichlet data, solved exactly by fast diagonalisation of the 1-D
+// Dirichlet pencils.  Returns the nodal values on [-keep, keep]^3 about the
+// anchor, K = 2 keep p + 1 per axis, index ix + K (iy + K iz).
+void screen_type_table(int p, int q, const int t3[3], int keep, int pad, int ngl, std::vector<double>& kept) {
+  const ElementPQ E(p, q);
+  const int B = keep + pad;
+  int nel[3], dims[3], dI[3];
+  std::vector<double> M1[3], K1[3], m1[3], qx[3], qw[3];
+  for (int a = 0; a < 3; ++a) {
+    nel[a] = 2 * B + (t3[a] ? 1 : 0);
+    const int N = p * nel[a] + 1;
+    dims[a] = N;
+    dI[a] = N - 2;
+    M1[a].assign((size_t)N * N, 0.0);
+    K1[a].assign((size_t)N * N, 0.0);
+    for (int e = 0; e < nel[a]; ++e)
+      for (int i = 0; i <= p; ++i)
+        for (int j = 0; j <= p; ++j) {
+          M1[a][(size_t)(p * e + i) * N + p * e + j] += E.Me[i * (p + 1) + j];
+          K1[a][(size_t)(p * e + i) * N + p * e + j] += E.Ke[i * (p + 1) + j];
+        }
+    // int phi^p_k psi_t: the anchor is the left end of element B
+    m1[a].assign(N, 0.0);
+    for (int k = 0; k <= p; ++k) {
+      if (t3[a] == 0) {
+        m1[a][p * (B - 1) + k] += E.Mpq[k * (q + 1) + q];
+        m1[a][p * B + k] += E.Mpq[k * (q + 1) + 0];
+      } else {
+        m1[a][p * B + k] += E.Mpq[k * (q + 1) + t3[a]];
+      }
+    }
+    type_quadrature(q, t3[a], ngl, qx[a], qw[a]);
+  }
+  const size_t NN = (size_t)dims[0] * dims[1] * dims[2];
+  std::vector<double> H(NN, 0.0);
+  auto idx = [&](int i, int j, int k) { return i + (size_t)dims[0] * (j + (size_t)dims[1] * k); };
+  auto pos = [&](int k) { return -B + (double)k / p; };
+  for (int k = 0; k < dims[2]; ++k)
+    for (int j = 0; j < dims[1]; ++j)
+      for (int i = 0; i < dims[0]; ++i) {
+        if (!(i == 0 || j == 0 || k == 0 || i == dims[0] - 1 || j == dims[1] - 1 || k == dims[2] - 1)) continue;
+        const double x = pos(i), y = pos(j), z = pos(k);
+        double acc = 0;
+        for (size_t c = 0; c < qx[2].size(); ++c) {
+          const double dz = z - qx[2][c];
+          for (size_t b = 0; b < qx[1].size(); ++b) {
+            const double dy = y - qx[1][b], wyz = qw[1][b] * qw[2][c];
+            for (size_t g = 0; g < qx[0].size(); ++g) {
+              const double dx = x - qx[0][g];
+              acc += qw[0][g] * wyz / std::sqrt(dx * dx + dy * dy + dz * dz);
+            }
+          }
+        }
+        H[idx(i, j, k)] = acc;
+      }
+  // interior residual rhs - K Hb, K = K1 (x) M1 (x) M1 + M1 (x) K1 (x) M1 + M1 (x) M1 (x) K1
+  std::vector<double> tA, tB, tC, acc(NN, 0.0);
+  for (int term = 0; term < 3; ++term) {
+    axis_apply(dims, term == 0 ? K1[0] : M1[0], H, tA, 0, false);
+    axis_apply(dims, term == 1 ? K1[1] : M1[1], tA, tB, 1, false);
+    axis_apply(dims, term == 2 ? K1[2] : M1[2], tB, tC, 2, false);
+    for (size_t i = 0; i < NN; ++i) acc[i] += tC[i];
+  }
+  const size_t NI = (size_t)dI[0] * dI[1] * dI[2];
+  std::vector<double> r(NI);
+  for (int k = 0; k < dI[2]; ++k)
+    for (int j = 0; j < dI[1]; ++j)
+      for (int i = 0; i < dI[0]; ++i)
+        r[i + (size_t)dI[0] * (j + (size_t)dI[1] * k)] =
+            4.0 * M_PI * m1[0][i + 1] * m1[1][j + 1] * m1[2][k + 1] - acc[idx(i + 1, j + 1, k + 1)];
+  std::vector<double> lam[3], Vv[3];
+  for (int a = 0; a < 3; ++a) {
+    const int n = dI[a], N = dims[a];
+    std::vector<double> KI((size_t)n * n), MI((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        KI[(size_t)i * n + j] = K1[a][(size_t)(i + 1) * N + j + 1];
+        MI[(size_t)i * n + j] = M1[a][(size_t)(i + 1) * N + j + 1];
+      }
+    generalized_eigen(n, KI, MI, lam[a], Vv[a]);
+  }
+  std::vector<double> s1, s2;
+  axis_apply(dI, Vv[0], r, s1, 0, true);
+  axis_apply(dI, Vv[1], s1, s2, 1, true);
+  axis_apply(dI, Vv[2], s2, s1, 2, true);
+  for (int k = 0; k < dI[2]; ++k)
+    for (int j = 0; j < dI[1]; ++j)
+      for (int i = 0; i < dI[0]; ++i) s1[i + (size_t)dI[0] * (j + (size_t)dI[1] * k)] /= lam[0][i] + lam[1][j] + lam[2][k];
+  axis_apply(dI, Vv[0], s1, s2, 0, false);
+  axis_apply(dI, Vv[1], s2, s1, 1, false);
+  axis_apply(dI, Vv[2], s1, s2, 2, false);
+  for (int k = 0; k < dI[2]; ++k)
+    for (int j = 0; j < dI[1]; ++j)
+      for (int i = 0; i < dI[0]; ++i) H[idx(i + 1, j + 1, k + 1)] = s2[i + (size_t)dI[0] * (j + (size_t)dI[1] * k)];
+  const int K = 2 * keep * p + 1, o = p * (B - keep);
+  kept.assign((size_t)K * K * K, 0.0);
+  for (int k = 0; k < K; ++k)
+    for (int j = 0; j < K; ++j)
+      for (int i = 0; i < K; ++i) kept[i + (size_t)K * (j + (size_t)K * k)] = H[idx(i + o, j + o, k + o)];
+}
+
+}  // namespace fep3m
+
+extern "C" {
+
+int fep3m_mesh_eigenbasis_order(int p, int n_el, double* lam, double* V) {
+  if (p < 1 || p > 8 || n_el < 1 || (long long)p * n_el > 8192 || !lam || !V) return FEP3M_EINVAL;
+  std::vector<double> l, v;
+  fep3m::periodic_eigen_order(p, n_el, l, v);
+  std::memcpy(lam, l.data(), l.size() * sizeof(double));
+  std::memcpy(V, v.data(), v.size() * sizeof(double));
+  return FEP3M_OK;
+}
+
+int fep3m_screen_type_table(int q, int tx, int ty, int tz, int n_sr, int pad, double* kept) {
+  if (q < 1 || q > 4 || n_sr < 1 || n_sr > 4 || pad < 1 || pad > 8 || !kept) return FEP3M_EINVAL;
+  const int t3[3] = {tx, ty, tz};
+  for (int a = 0; a < 3; ++a)
+    if (t3[a] < 0 || t3[a] >= q) return FEP3M_EINVAL;
+  std::vector<double> out;
+  fep3m::screen_type_table(q + 2, q, t3, n_sr + 1, pad, 8, out);
+  std::memcpy(kept, out.data(), out.size() * sizeof(double));
+  return FEP3M_OK;
+}
+
+}  // extern "C"

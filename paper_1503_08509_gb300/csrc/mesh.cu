@@ -2258,7 +2258,6 @@ cudaError_t assemble_forward(fep3m_ctx* c) {
   const int n = c->n;
   const int64_t ne = (int64_t)n * n * n;
   cudaStream_t s = c->stream;
-  const size_t nodes = (size_t)27 * ne;
   if (c->precision == FEP3M_MIXED) {
     FEP3M_CL k_elem_coeff<float><<<grid_for(ne), TPB, 0, s>>>(ne, c->start, c->count, (const float4*)c->part, (float*)c->C);
     FEP3M_CL k_vertex_density<float><<<grid_for(ne), TPB, 0, s>>>(n, (const float*)c->C, (float*)c->rv,

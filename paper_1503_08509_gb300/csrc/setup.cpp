@@ -13,8 +13,6 @@
 
 namespace fep3m {
 
-namespace {
-
 // n-point Gauss-Legendre rule on [0, 1] by Newton iteration on P_n.
 void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
   x.assign(n, 0.0);
@@ -39,8 +37,6 @@ void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
     w[i] = 1.0 / ((1.0 - z * z) * dp * dp);   // 2/((1-z^2) P'^2) mapped by 1/2
   }
 }
-
-}  // namespace
 
 void element_matrices_q3(double Me[4][4], double Ke[4][4], double Mpq[4][2]) {
   std::vector<double> x, w;

@@ -1,0 +1,78 @@
+"""Host-only building blocks for screens of order q >= 2 (C ABI, no GPU): the periodic
+order-p eigenbasis against a dense generalized eigensolver on the oracle's matrices, and
+the basis-screen type tables against the oracle's (oracle.highorder)."""
+import ctypes
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+from oracle import fe1d, highorder, tables
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1503_08509_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("n", [1, 2, 3, 8])
+def test_order_p_eigenbasis_matches_dense_solver(lib, p, n):
+    N = p * n
+    lam, V = np.empty(N), np.empty((N, N))
+    assert lib.fep3m_mesh_eigenbasis_order(p, n, ptr(lam), ptr(V)) == 0
+    M1, K1, _ = fe1d.periodic_matrices(p, n, 1.0, 1)
+    ref = sl.eigh(K1, M1, eigvals_only=True)
+    scale = max(np.abs(ref).max(), 1.0)                  # p = n = 1: the single eigenvalue is 0
+    assert np.abs(np.sort(lam) - ref).max() < 1e-11 * scale
+    assert np.abs(V.T @ M1 @ V - np.eye(N)).max() < 1e-11
+    assert np.abs(V.T @ K1 @ V - np.diag(lam)).max() < 1e-11 * scale
+
+
+def test_order_3_eigenbasis_is_the_mesh_solver_basis(lib):
+    n = 7
+    a, Va, b, Vb = np.empty(21), np.empty((21, 21)), np.empty(21), np.empty((21, 21))
+    assert lib.fep3m_mesh_eigenbasis_order(3, n, ptr(a), ptr(Va)) == 0
+    assert lib.fep3m_mesh_eigenbasis(n, ptr(b), ptr(Vb)) == 0
+    assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+
+
+def type_table(lib, q, t3, n_sr, pad):
+    K = 2 * (n_sr + 1) * (q + 2) + 1
+    out = np.empty(K ** 3)
+    assert lib.fep3m_screen_type_table(q, t3[0], t3[1], t3[2], n_sr, pad, ptr(out)) == 0
+    return out.reshape(K, K, K).transpose(2, 1, 0)        # [ix, iy, iz]
+
+
+def test_q1_type_table_is_the_hat_table(lib):
+    n_sr, pad = 1, 2
+    ref = tables.kept_table(3, half_width=n_sr + 1 + pad, ngl=8, keep=n_sr + 1)
+    assert np.abs(type_table(lib, 1, (0, 0, 0), n_sr, pad) - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("q, t3", [(2, (0, 0, 0)), (2, (1, 0, 0)), (2, (0, 1, 1)), (3, (2, 1, 0)), (3, (1, 1, 1))])
+def test_type_tables_match_the_oracle(lib, q, t3):
+    n_sr, pad = 1, 1
+    keep = n_sr + 1
+    H, _ = highorder.type_table(q + 2, q, t3, keep + pad, 8)
+    s = (q + 2) * pad
+    ref = H[s:H.shape[0] - s - (q + 2) * (t3[0] > 0), s:H.shape[1] - s - (q + 2) * (t3[1] > 0),
+            s:H.shape[2] - s - (q + 2) * (t3[2] > 0)]
+    got = type_table(lib, q, t3, n_sr, pad)
+    assert got.shape == ref.shape
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_bad_arguments_are_rejected(lib):
+    out = np.empty(1)
+    assert lib.fep3m_mesh_eigenbasis_order(0, 4, ptr(out), ptr(out)) != 0
+    assert lib.fep3m_mesh_eigenbasis_order(9, 4, ptr(out), ptr(out)) != 0
+    assert lib.fep3m_screen_type_table(2, 2, 0, 0, 1, 1, ptr(out)) != 0     # type out of range
+    assert lib.fep3m_screen_type_table(5, 0, 0, 0, 1, 1, ptr(out)) != 0     # q out of range
+    assert lib.fep3m_screen_type_table(2, 0, 0, 0, 0, 1, ptr(out)) != 0     # n_sr out of range
