@@ -209,9 +209,11 @@ int fep3m_mesh_eigenbasis(int n_el, double* lam, double* V);
  *
  * fep3m_screen_type_table: the FE table (Remark of Sec. 4) of one basis
  * screen of order q (1 <= q <= 4).  The order-q nodal functions of the screen
- * mesh come in q types per axis: type 0, the function of a vertex (support
- * the two elements next to it), and type t = 1 .. q-1, the interior function
- * of an element with its node at t/q.  (tx, ty, tz) picks the product
+ * mesh (Lagrange functions on Gauss-Lobatto-Legendre nodes, which are the
+ * equispaced ones for q <= 2) come in q types per axis: type 0, the function
+ * of a vertex (support the two elements next to it), and type t = 1 .. q-1,
+ * the interior function of an element with its t-th interior node.
+ * (tx, ty, tz) picks the product
  * screen; the table is the order-(q+2) Galerkin solution of
  * -Lap H = 4 pi psi (h = 1) on a box reaching n_sr + 1 + pad elements
  * beyond the screen's anchor vertex (the left vertex of the element holding

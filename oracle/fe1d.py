@@ -16,9 +16,27 @@ def gauss_legendre01(n):
     return 0.5 * (x + 1.0), 0.5 * w
 
 
-def lagrange_values(p, t):
-    """Equispaced order-p Lagrange basis on [0,1] at points t: shape t.shape+(p+1,)."""
-    nodes = np.linspace(0.0, 1.0, p + 1)
+def gll_nodes01(p):
+    """Gauss-Lobatto-Legendre nodes on [0, 1]: the end points and the roots of P_p'."""
+    if p == 1:
+        return np.array([0.0, 1.0])
+    x = np.sort(np.real(np.polynomial.legendre.Legendre.basis(p).deriv().roots()))
+    return np.concatenate([[0.0], 0.5 * (x + 1.0), [1.0]])
+
+
+def node_set(p, nodes=None):
+    """The order-p nodes on [0, 1]: equispaced (None or 'equispaced') or 'gll'."""
+    if nodes is None or nodes == 'equispaced':
+        return np.linspace(0.0, 1.0, p + 1)
+    if nodes == 'gll':
+        return gll_nodes01(p)
+    raise ValueError(nodes)
+
+
+def lagrange_values(p, t, nodes=None):
+    """Order-p Lagrange basis on [0,1] at points t: shape t.shape+(p+1,); equispaced nodes
+    unless nodes = 'gll'."""
+    nodes = node_set(p, nodes)
     t = np.asarray(t, dtype=np.float64)
     out = np.ones(t.shape + (p + 1,))
     for k in range(p + 1):
@@ -45,9 +63,10 @@ def lagrange_derivs(p, t):
     return out
 
 
-def element_matrices(p, h, q=None):
+def element_matrices(p, h, q=None, qnodes=None):
     """Element mass h*int(l_i l_j), stiffness (1/h)*int(l_i' l_j') on [0,1];
-    with q given, also the mixed mass h*int(l^p_i l^q_j) (order-p rows, order-q columns)."""
+    with q given, also the mixed mass h*int(l^p_i l^q_j) (order-p rows, order-q columns,
+    the order-q basis on the node set qnodes)."""
     t, w = gauss_legendre01(p + 2)
     L = lagrange_values(p, t)
     D = lagrange_derivs(p, t)
@@ -55,7 +74,7 @@ def element_matrices(p, h, q=None):
     Ke = (1.0 / h) * np.einsum('g,gi,gj->ij', w, D, D)
     if q is None:
         return Me, Ke
-    Lq = lagrange_values(q, t)
+    Lq = lagrange_values(q, t, qnodes)
     Mpq = h * np.einsum('g,gi,gj->ij', w, L, Lq)
     return Me, Ke, Mpq
 
@@ -86,9 +105,9 @@ def assemble_open(Ae, n, p):
     return A
 
 
-def periodic_matrices(p, n, h, q=1):
+def periodic_matrices(p, n, h, q=1, qnodes=None):
     """1-D periodic order-p mass M1, stiffness K1 (p*n square) and mixed mass Mpq (p*n x q*n)."""
-    Me, Ke, Mpq_e = element_matrices(p, h, q)
+    Me, Ke, Mpq_e = element_matrices(p, h, q, qnodes)
     M1 = assemble_periodic(Me, n, p)
     K1 = assemble_periodic(Ke, n, p)
     Mpq = assemble_periodic(Mpq_e, n, p, q)

@@ -87,9 +87,9 @@ def vertex_density(C, n):
 class MeshOperators:
     """1-D periodic order-p matrices for the mesh solve and its exact inverse."""
 
-    def __init__(self, L, n, p=P_ORDER, q=Q_ORDER):
+    def __init__(self, L, n, p=P_ORDER, q=Q_ORDER, qnodes=None):
         self.L, self.n, self.p, self.h = L, n, p, L / n
-        self.M1, self.K1, self.Mpq = fe1d.periodic_matrices(p, n, self.h, q)
+        self.M1, self.K1, self.Mpq = fe1d.periodic_matrices(p, n, self.h, q, qnodes)
         self.w1 = fe1d.node_integrals_periodic(p, n, self.h)
         lam, V = scipy.linalg.eigh(self.K1, self.M1)
         self.lam, self.V = lam, V

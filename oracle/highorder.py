@@ -17,6 +17,8 @@ The same steps as oracle.fep3m (Algorithm 1), written for a general screen order
   7. Phi = Phi^sm + Phi^sr and U = 1/2 sum Q Phi (Eq. potentialenergy).
 
 Readings beyond those of oracle.fep3m (the paper leaves them open):
+  * the order-q screen basis uses Gauss-Lobatto-Legendre nodes (NODES below); the
+    equispaced set stays available (nodes='equispaced');
   * the 1-D order-q nodal functions of the screen mesh come in q types: type 0, the
     vertex function (support the two elements next to its vertex), and types
     i = 1 .. q-1, the interior functions of one element (node at i/q of it).  A 3-D
@@ -43,40 +45,47 @@ from . import fe1d, screens, tables
 from .fep3m import MeshOperators, bin_particles, block_offsets, element_node_index, gather_block_coefficients, \
     q3_basis, singular_sums
 
+# Node set of the order-q screen basis (the order-p mesh space does not depend on one).
+# Gauss-Lobatto-Legendre: with it the error against Ewald on the paper's two-cube
+# workload (Sec. 4) falls faster at each step of q through q = 4, as Fig. compareerr
+# shows; with equispaced nodes the q = 4 screens are larger than the q = 3 ones at the
+# block's edge and q = 4 loses to q = 3.  The two sets coincide for q <= 2.
+NODES = 'gll'
 
-def basis_pieces_1d(q, t):
+
+def basis_pieces_1d(q, t, nodes=NODES):
     """Polynomial pieces (a, b, f) of the 1-D type-t order-q nodal function, element
     units, anchor at 0: type 0 on [-1, 0] and [0, 1], type t >= 1 on [0, 1]."""
     if t == 0:
-        return [(-1.0, 0.0, lambda x: fe1d.lagrange_values(q, x + 1.0)[..., q]),
-                (0.0, 1.0, lambda x: fe1d.lagrange_values(q, x)[..., 0])]
-    return [(0.0, 1.0, lambda x, t=t: fe1d.lagrange_values(q, x)[..., t])]
+        return [(-1.0, 0.0, lambda x: fe1d.lagrange_values(q, x + 1.0, nodes)[..., q]),
+                (0.0, 1.0, lambda x: fe1d.lagrange_values(q, x, nodes)[..., 0])]
+    return [(0.0, 1.0, lambda x, t=t: fe1d.lagrange_values(q, x, nodes)[..., t])]
 
 
-def quadrature_1d(q, t, ngl):
+def quadrature_1d(q, t, ngl, nodes=NODES):
     """Points and weights times the type-t nodal function, per polynomial piece."""
     tq, wq = fe1d.gauss_legendre01(ngl)
     xs, ws = [], []
-    for (a, b, f) in basis_pieces_1d(q, t):
+    for (a, b, f) in basis_pieces_1d(q, t, nodes):
         x = a + (b - a) * tq
         xs.append(x)
         ws.append((b - a) * wq * f(x))
     return np.concatenate(xs), np.concatenate(ws)
 
 
-def basis_potential_continuum(q, t3, points, ngl=8):
+def basis_potential_continuum(q, t3, points, ngl=8, nodes=NODES):
     """int psi_t(xi) / |x - xi| dxi for the 3-D basis screen of type t3 = (tx, ty, tz),
     anchor at the origin, h = 1 (Eq. screenintegral), points well outside its support."""
-    q1 = [quadrature_1d(q, t, ngl) for t in t3]
+    q1 = [quadrature_1d(q, t, ngl, nodes) for t in t3]
     X, Y, Z = np.meshgrid(q1[0][0], q1[1][0], q1[2][0], indexing='ij')
     W = q1[0][1][:, None, None] * q1[1][1][None, :, None] * q1[2][1][None, None, :]
     return tables.coulomb_quadrature(points, np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1), W.ravel())
 
 
-def mixed_mass_column(p, q, t, lo, nel):
+def mixed_mass_column(p, q, t, lo, nel, nodes=NODES):
     """int phi^p_k(x) psi_t(x) dx for the order-p nodes k of the open mesh of nel elements
     starting at x = lo (element units), psi_t anchored at 0."""
-    _, _, Mpq_e = fe1d.element_matrices(p, 1.0, q)
+    _, _, Mpq_e = fe1d.element_matrices(p, 1.0, q, nodes)
     m1 = np.zeros(p * nel + 1)
     c = -lo                                     # the anchor is the left end of element c
     if t == 0:
@@ -93,7 +102,7 @@ def box_extent(t, half_width):
 
 
 @functools.lru_cache(maxsize=256)
-def type_table(p, q, t3, half_width=6, ngl=6):
+def type_table(p, q, t3, half_width=6, ngl=6, nodes=NODES):
     """FE potential of the basis screen of type t3 on its box (h = 1): H[ix, iy, iz] at
     x = lo_a + k / p along each axis a.  Galerkin: K_II H_I = 4 pi (Mpq psi)_I - K_IB H_B,
     solved exactly by fast diagonalisation of the 1-D Dirichlet pencils."""
@@ -102,7 +111,7 @@ def type_table(p, q, t3, half_width=6, ngl=6):
     Me, Ke = fe1d.element_matrices(p, 1.0)
     M1 = [fe1d.assemble_open(Me, ne, p) for ne in nel]
     K1 = [fe1d.assemble_open(Ke, ne, p) for ne in nel]
-    m1 = [mixed_mass_column(p, q, t, lo, ne) for t, (lo, _), ne in zip(t3, ext, nel)]
+    m1 = [mixed_mass_column(p, q, t, lo, ne, nodes) for t, (lo, _), ne in zip(t3, ext, nel)]
     rhs = 4.0 * np.pi * m1[0][:, None, None] * m1[1][None, :, None] * m1[2][None, None, :]
     x1 = [lo + np.arange(p * ne + 1) / p for (lo, _), ne in zip(ext, nel)]
     N = [len(x) for x in x1]
@@ -110,7 +119,7 @@ def type_table(p, q, t3, half_width=6, ngl=6):
     onb = (I == 0) | (I == N[0] - 1) | (J == 0) | (J == N[1] - 1) | (K == 0) | (K == N[2] - 1)
     Hb = np.zeros(tuple(N))
     pts = np.stack([x1[0][I[onb]], x1[1][J[onb]], x1[2][K[onb]]], axis=1)
-    Hb[onb] = basis_potential_continuum(q, t3, pts, ngl)
+    Hb[onb] = basis_potential_continuum(q, t3, pts, ngl, nodes)
     r = rhs - (tables.kron_apply(K1[0], M1[1], M1[2], Hb) + tables.kron_apply(M1[0], K1[1], M1[2], Hb)
                + tables.kron_apply(M1[0], M1[1], K1[2], Hb))
     r = r[1:-1, 1:-1, 1:-1]
@@ -123,7 +132,7 @@ def type_table(p, q, t3, half_width=6, ngl=6):
     return H, tuple(x1)
 
 
-def kept_tables(p, q, keep, half_width=None, ngl=6, interior_only=False):
+def kept_tables(p, q, keep, half_width=None, ngl=6, interior_only=False, nodes=NODES):
     """Nodal values of each type's table on [-keep, keep]^3 about its anchor:
     dict t3 -> array ((2 keep p + 1),)*3; interior_only: the types with no vertex
     factor (all that one-element screens use)."""
@@ -131,7 +140,7 @@ def kept_tables(p, q, keep, half_width=None, ngl=6, interior_only=False):
         half_width = keep + 2
     out = {}
     for t3 in itertools.product(range(1 if interior_only else 0, q), repeat=3):
-        H, _ = type_table(p, q, t3, half_width, ngl)
+        H, _ = type_table(p, q, t3, half_width, ngl, nodes)
         s = p * (half_width - keep)
         e = p * (half_width + keep) + 1
         out[t3] = H[s:e, s:e, s:e]
@@ -144,7 +153,7 @@ def local_node(kappa, q):
     return np.array([kappa % q1, (kappa // q1) % q1, kappa // (q1 * q1)])
 
 
-def one_element_coefficients(q, h, delta3):
+def one_element_coefficients(q, h, delta3, nodes=NODES):
     """Screens confined to the charge's element (one-element screens, Sec. 5.3): only the
     (q-1)^3 interior nodes carry weight.  Per axis the q - 1 interior weights solve the
     moment system of Eq. moment1d for l = 0 .. q-2 (the interior functions vanish outside
@@ -152,7 +161,7 @@ def one_element_coefficients(q, h, delta3):
     patch moment matrix).  Returns (..., (q+1)^3), zero on the element's face nodes."""
     assert q >= 2, "a one-element screen needs an interior node"
     delta3 = np.asarray(delta3, dtype=np.float64)
-    Om = screens.moment_matrix_1d(q, h)[:q - 1, 1:q]
+    Om = screens.moment_matrix_1d(q, h, nodes)[:q - 1, 1:q]
     w = []
     for a in range(3):
         rhs = np.stack([delta3[..., a] ** l for l in range(q - 1)], axis=-1)
@@ -164,14 +173,14 @@ def one_element_coefficients(q, h, delta3):
     return c.reshape(delta3.shape[:-1] + ((q + 1) ** 3,))
 
 
-def element_coefficients(bins, Q, n, q, support='patch'):
+def element_coefficients(bins, Q, n, q, support='patch', nodes=NODES):
     """C[e, kappa] = sum_{j in e} Q_j c_kappa(delta_j), shape (n^3, (q+1)^3), units charge/h^3.
     support='patch': the screens of Eq. moment1d on the element's (q+1)^3 nodes;
     support='element': one-element screens on its interior nodes."""
     if support == 'element':
-        c = one_element_coefficients(q, bins['h'], bins['delta'])
+        c = one_element_coefficients(q, bins['h'], bins['delta'], nodes)
     else:
-        c = screens.screen_coefficients(q, bins['h'], bins['delta'])
+        c = screens.screen_coefficients(q, bins['h'], bins['delta'], nodes)
     C = np.zeros((n ** 3, c.shape[1]))
     np.add.at(C, bins['cell'], np.asarray(Q)[:, None] * c)
     return C
@@ -216,19 +225,21 @@ def screen_window_matrix(n_sr, p, q, kept):
     return W.reshape(len(offs) * q1 ** 3, p1 ** 3)
 
 
-def forward(pos, Q, L, n, q, n_sr=3, neutralise=True, chunk=1024, half_width=None, ngl=6, support='patch'):
+def forward(pos, Q, L, n, q, n_sr=3, neutralise=True, chunk=1024, half_width=None, ngl=6, support='patch',
+            nodes=NODES):
     """Phi_i and U for charges Q at pos (N x 3) with order-q screens and the order p = q + 2
     mesh (Sec. 2: p = q + 2), with the intermediates.  support='element' uses one-element
-    screens (Sec. 5.3), still with p = q + 2."""
+    screens (Sec. 5.3), still with p = q + 2.  nodes: the node set of the order-q screen
+    basis ('gll' or 'equispaced'); the order-p mesh space does not depend on it."""
     pos = np.asarray(pos, dtype=np.float64)
     Q = np.asarray(Q, dtype=np.float64)
     assert n >= 2 * n_sr + 1, "the short-range block must not wrap onto itself"
     p = q + 2
     bins = bin_particles(pos, L, n)
     h = bins['h']
-    C = element_coefficients(bins, Q, n, q, support)
+    C = element_coefficients(bins, Q, n, q, support, nodes)
     r = nodal_density(C, n, q)
-    ops = MeshOperators(L, n, p, q)
+    ops = MeshOperators(L, n, p, q, nodes)
     b = ops.load_vector(r)
     if neutralise:
         b = ops.neutralise(b)
@@ -237,7 +248,7 @@ def forward(pos, Q, L, n, q, n_sr=3, neutralise=True, chunk=1024, half_width=Non
     ix, iy, iz = element_node_index(bins['c3'], n, p)
     phi_sm = np.einsum('nm,nm->n', phi_mesh[ix, iy, iz], U3)
     phi_sing, _ = singular_sums(bins, Q, n, n_sr)
-    kept = kept_tables(p, q, n_sr + 1, half_width, ngl, interior_only=support == 'element')
+    kept = kept_tables(p, q, n_sr + 1, half_width, ngl, interior_only=support == 'element', nodes=nodes)
     Wmat = screen_window_matrix(n_sr, p, q, kept)
     offs = block_offsets(n_sr)
     phi_scr = np.zeros(len(Q))

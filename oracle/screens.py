@@ -15,7 +15,7 @@ import numpy as np
 from .fe1d import gauss_legendre01, lagrange_values
 
 
-def omega_pieces(q, h):
+def omega_pieces(q, h, nodes=None):
     """Global C0 order-q nodal functions of the centre element's q+1 nodes.
 
     Returns, for node i, a list of (a, b, f) pieces: on [a, b], omega_i = f(x).
@@ -23,20 +23,20 @@ def omega_pieces(q, h):
     vertex of [-3h/2, -h/2], its right vertex (i = q) the left vertex of [h/2, 3h/2]."""
     out = []
     for i in range(q + 1):
-        pieces = [(-0.5 * h, 0.5 * h, (lambda x, i=i: lagrange_values(q, (x + 0.5 * h) / h)[..., i]))]
+        pieces = [(-0.5 * h, 0.5 * h, (lambda x, i=i: lagrange_values(q, (x + 0.5 * h) / h, nodes)[..., i]))]
         if i == 0:
-            pieces.append((-1.5 * h, -0.5 * h, lambda x: lagrange_values(q, (x + 1.5 * h) / h)[..., q]))
+            pieces.append((-1.5 * h, -0.5 * h, lambda x: lagrange_values(q, (x + 1.5 * h) / h, nodes)[..., q]))
         if i == q:
-            pieces.append((0.5 * h, 1.5 * h, lambda x: lagrange_values(q, (x - 0.5 * h) / h)[..., 0]))
+            pieces.append((0.5 * h, 1.5 * h, lambda x: lagrange_values(q, (x - 0.5 * h) / h, nodes)[..., 0]))
         out.append(pieces)
     return out
 
 
-def moment_matrix_1d(q, h):
+def moment_matrix_1d(q, h, nodes=None):
     """Omega[l, i] = bar-omega_i^(l), the centred 1-D moments (Eq. cmomentsbasis)."""
     t, w = gauss_legendre01(q + 2)
     Om = np.zeros((q + 1, q + 1))
-    for i, pieces in enumerate(omega_pieces(q, h)):
+    for i, pieces in enumerate(omega_pieces(q, h, nodes)):
         for (a, b, f) in pieces:
             x = a + (b - a) * t
             fx = f(x)
@@ -45,24 +45,24 @@ def moment_matrix_1d(q, h):
     return Om
 
 
-def screen_weights_1d(q, h, delta):
+def screen_weights_1d(q, h, delta, nodes=None):
     """w_i(delta), i = 0..q, for offsets delta (any shape): solves Eq. moment1d.
 
     Output shape delta.shape + (q+1,), units 1/h."""
     delta = np.asarray(delta, dtype=np.float64)
-    Om = moment_matrix_1d(q, h)
+    Om = moment_matrix_1d(q, h, nodes)
     rhs = np.stack([delta ** l for l in range(q + 1)], axis=-1)
     return np.linalg.solve(Om, rhs[..., None])[..., 0]
 
 
-def screen_coefficients(q, h, delta3):
+def screen_coefficients(q, h, delta3, nodes=None):
     """c_kappa(delta) = w^x_i w^y_j w^z_k with kappa = i + (q+1) j + (q+1)^2 k (Eq. oned).
 
     delta3: (..., 3) offsets from the element centre.  Returns (..., (q+1)^3), units 1/h^3."""
     delta3 = np.asarray(delta3, dtype=np.float64)
-    wx = screen_weights_1d(q, h, delta3[..., 0])
-    wy = screen_weights_1d(q, h, delta3[..., 1])
-    wz = screen_weights_1d(q, h, delta3[..., 2])
+    wx = screen_weights_1d(q, h, delta3[..., 0], nodes)
+    wy = screen_weights_1d(q, h, delta3[..., 1], nodes)
+    wz = screen_weights_1d(q, h, delta3[..., 2], nodes)
     c = wz[..., :, None, None] * wy[..., None, :, None] * wx[..., None, None, :]
     return c.reshape(delta3.shape[:-1] + ((q + 1) ** 3,))
 

@@ -1,5 +1,6 @@
 // Create-time host computations for screens of any order q and the order
-// p = q + 2 mesh: equispaced Lagrange element matrices, the 1-D eigenbasis of
+// p = q + 2 mesh: Lagrange element matrices (equispaced order-p mesh basis,
+// Gauss-Lobatto order-q screen basis), the 1-D eigenbasis of
 // the periodic order-p mesh (block-Fourier reduction), and the FE tables of the
 // q^3 basis-screen types (Remark of Sec. 4).  Host code only; nothing here runs
 // per evaluation.
@@ -13,15 +14,34 @@ namespace fep3m {
 
 namespace {
 
-// Equispaced order-p Lagrange basis on [0, 1] at t, and its derivative
-// (product rule, one factor at a time).
-void lagrange(int p, double t, double* v, double* d) {
+// Nodes on [0, 1] of the order-p Lagrange basis: equispaced (the order-p mesh
+// space, which does not depend on them) or Gauss-Lobatto-Legendre (the order-q
+// screen basis: the ends and the roots of P_q', closed forms for q <= 4; the two
+// sets coincide for q <= 2).
+void node_set(int p, bool gll, double* x) {
+  for (int k = 0; k <= p; ++k) x[k] = (double)k / p;
+  if (!gll || p <= 2) return;
+  if (p == 3) {
+    const double r = 1.0 / std::sqrt(5.0);
+    x[1] = 0.5 * (1.0 - r);
+    x[2] = 0.5 * (1.0 + r);
+  } else if (p == 4) {
+    const double r = std::sqrt(3.0 / 7.0);
+    x[1] = 0.5 * (1.0 - r);
+    x[2] = 0.5;
+    x[3] = 0.5 * (1.0 + r);
+  }
+}
+
+// Order-p Lagrange basis on the nodes x at t, and its derivative (product
+// rule, one factor at a time).
+void lagrange(int p, const double* x, double t, double* v, double* d) {
   for (int k = 0; k <= p; ++k) {
-    const double xk = (double)k / p;
+    const double xk = x[k];
     double val = 1.0, der = 0.0;
     for (int j = 0; j <= p; ++j) {
       if (j == k) continue;
-      const double xj = (double)j / p, den = xk - xj;
+      const double xj = x[j], den = xk - xj;
       der = der * (t - xj) / den + val / den;
       val *= (t - xj) / den;
     }
@@ -31,17 +51,20 @@ void lagrange(int p, double t, double* v, double* d) {
 }
 
 // Element matrices on [0, 1] (h = 1): mass Me and stiffness Ke of the order-p
-// basis ((p+1) x (p+1)), mixed mass Mpq = int l^p_i l^q_j ((p+1) x (q+1)).
+// basis ((p+1) x (p+1), equispaced nodes), mixed mass Mpq = int l^p_i l^q_j
+// ((p+1) x (q+1), the order-q screen basis on Gauss-Lobatto nodes).
 struct ElementPQ {
   int p, q;
   std::vector<double> Me, Ke, Mpq;
   ElementPQ(int p_, int q_) : p(p_), q(q_), Me((p_ + 1) * (p_ + 1)), Ke((p_ + 1) * (p_ + 1)), Mpq((p_ + 1) * (q_ + 1)) {
     std::vector<double> x, w;
     gauss_legendre01(p + 2, x, w);   // exact for degree 2 p + 3
-    std::vector<double> v(p + 1), d(p + 1), vq(q + 1);
+    std::vector<double> v(p + 1), d(p + 1), vq(q + 1), np_(p + 1), nq(q + 1);
+    node_set(p, false, np_.data());
+    node_set(q, true, nq.data());
     for (size_t g = 0; g < x.size(); ++g) {
-      lagrange(p, x[g], v.data(), d.data());
-      lagrange(q, x[g], vq.data(), nullptr);
+      lagrange(p, np_.data(), x[g], v.data(), d.data());
+      lagrange(q, nq.data(), x[g], vq.data(), nullptr);
       for (int i = 0; i <= p; ++i) {
         for (int j = 0; j <= p; ++j) {
           Me[i * (p + 1) + j] += w[g] * v[i] * v[j];
@@ -72,19 +95,20 @@ void axis_apply(const int dims[3], const std::vector<double>& A, const std::vect
     }
 }
 
-// Quadrature of the 1-D type-t order-q nodal function (anchor at 0, element
+// Quadrature of the 1-D type-t order-q nodal function (Gauss-Lobatto nodes; anchor at 0, element
 // units): points and weights times the function, ngl Gauss points per
 // polynomial piece.  Type 0: the vertex function on [-1, 0] (local node q of
 // the left element) and [0, 1] (local node 0 of the right one); type t >= 1:
 // local node t of the element [0, 1].
 void type_quadrature(int q, int t, int ngl, std::vector<double>& px, std::vector<double>& pw) {
-  std::vector<double> x, w, vq(q + 1);
+  std::vector<double> x, w, vq(q + 1), nq(q + 1);
   gauss_legendre01(ngl, x, w);
+  node_set(q, true, nq.data());
   px.clear();
   pw.clear();
   auto piece = [&](double lo, int node) {
     for (int g = 0; g < ngl; ++g) {
-      lagrange(q, x[g], vq.data(), nullptr);
+      lagrange(q, nq.data(), x[g], vq.data(), nullptr);
       px.push_back(lo + x[g]);
       pw.push_back(w[g] * vq[node]);
     }

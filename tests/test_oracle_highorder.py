@@ -45,7 +45,7 @@ def independent_mixed_column(p, q, node, lo, nel):
     """int phi^p_k psi dx with psi the order-q nodal function of the centred element's
     local node `node` (oracle.screens.omega_pieces, element [-1/2, 1/2]), shifted so its
     anchor vertex sits at 0, by Gauss-Legendre quadrature of the product on each element."""
-    pieces = screens.omega_pieces(q, 1.0)[node]
+    pieces = screens.omega_pieces(q, 1.0, highorder.NODES)[node]
     shift = 0.5 - (1.0 if node == q else 0.0)
     t, w = fe1d.gauss_legendre01(p + q + 2)
     m1 = np.zeros(p * nel + 1)
@@ -79,6 +79,17 @@ def test_type_table_solves_dirichlet_problem(q, t3):
     assert np.allclose([H[0, 3, 7], H[-1, -1, 9]], ref, rtol=1e-11, atol=0)
 
 
+def screen_node_integrals(q, n, h):
+    """Integrals of the periodic order-q screen basis functions (the oracle's node set)."""
+    t, wg = fe1d.gauss_legendre01(q + 2)
+    we = h * np.einsum('g,gi->i', wg, fe1d.lagrange_values(q, t, highorder.NODES))
+    out = np.zeros(q * n)
+    for e in range(n):
+        for i in range(q + 1):
+            out[(q * e + i) % (q * n)] += we[i]
+    return out
+
+
 @pytest.mark.parametrize("q", [2, 3])
 def test_nodal_density_carries_charge_and_dipole(q):
     # Eq. moment1d with l = 0, 1: the screens hold each charge's total and its first
@@ -88,7 +99,7 @@ def test_nodal_density_carries_charge_and_dipole(q):
     pos = pos * 0.6 + 0.2                             # away from the periodic seam
     b = fep3m.bin_particles(pos, L, n)
     r = highorder.nodal_density(highorder.element_coefficients(b, Q, n, q), n, q)
-    w = fe1d.node_integrals_periodic(q, n, L / n)
+    w = screen_node_integrals(q, n, L / n)
     assert abs(np.einsum('ijk,i,j,k->', r, w, w, w) - Q.sum()) < 1e-12 * np.abs(Q).sum()
     # first moment along x: nodes of the order-q mesh at i h / q, integrated with
     # x * psi_i (the density's support crosses no periodic seam here)
@@ -97,7 +108,7 @@ def test_nodal_density_carries_charge_and_dipole(q):
     wx = np.zeros(q * n)
     for e in range(n):
         x = (e + t) * h
-        lv = fe1d.lagrange_values(q, t)
+        lv = fe1d.lagrange_values(q, t, highorder.NODES)
         for i in range(q + 1):
             wx[(q * e + i) % (q * n)] += h * np.sum(wg * x * lv[:, i])
     mx = np.einsum('ijk,i,j,k->', r, wx, w, w)
@@ -110,7 +121,7 @@ def test_screened_potential_decays_like_r_minus_q_plus_2(q):
     # the screen is built from the type/anchor map the tables use (local node i of
     # the element [-1/2, 1/2]: anchor -1/2 + [i = q], type i mod q)
     delta = np.array([0.23, -0.11, 0.37])
-    c = screens.screen_coefficients(q, 1.0, delta[None, :])[0]
+    c = screens.screen_coefficients(q, 1.0, delta[None, :], highorder.NODES)[0]
     rng = np.random.default_rng(1)
     dirs = rng.normal(size=(16, 3))
     dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
@@ -138,7 +149,7 @@ def test_whole_element_shift_is_exact_q2():
 
 def test_error_against_ewald_falls_with_q():
     # Fig. compareerr: the error against a converged Ewald sum falls fast with q
-    # (measured here: 8.0e-3, 1.6e-3, 3.5e-4 for q = 1, 2, 3 at n = 8, n_sr = 2)
+    # (measured here: 8.0e-3, 1.6e-3, 2.1e-4 for q = 1, 2, 3 at n = 8, n_sr = 2)
     pos, Q = workloads.uniform_pm(100, seed=9)
     pe = ewald.ewald(pos, Q, 1.0)
     err = {}
@@ -189,13 +200,13 @@ def test_one_element_density_stays_in_the_element_and_keeps_charge_and_dipole():
     idx = np.arange(q * n)
     face = (idx % q) == 0
     assert np.all(r[face, :, :] == 0) and np.all(r[:, face, :] == 0) and np.all(r[:, :, face] == 0)
-    w = fe1d.node_integrals_periodic(q, n, L / n)
+    w = screen_node_integrals(q, n, L / n)
     assert abs(np.einsum('ijk,i,j,k->', r, w, w, w) - Q.sum()) < 1e-12 * np.abs(Q).sum()
     h = L / n
     t, wg = fe1d.gauss_legendre01(q + 2)
     wx = np.zeros(q * n)
     for e in range(n):
-        lv = fe1d.lagrange_values(q, t)
+        lv = fe1d.lagrange_values(q, t, highorder.NODES)
         for i in range(q + 1):
             wx[(q * e + i) % (q * n)] += h * np.sum(wg * (e + t) * h * lv[:, i])
     assert abs(np.einsum('ijk,i,j,k->', r, w, wx, w) - np.dot(Q, pos[:, 1])) < 1e-12 * np.abs(Q).sum()
@@ -211,3 +222,31 @@ def test_one_element_screens_against_ewald():
         d -= d.mean()
         err[q] = np.linalg.norm(d) / np.linalg.norm(pe)
     assert err[3] < 2e-2 and err[4] < err[3] / 5, err
+
+
+# ------------------------------------------------------ node set of the screen basis
+@pytest.mark.parametrize("q", [1, 2, 3, 4, 5])
+def test_gauss_lobatto_nodes(q):
+    # the Gauss-Lobatto rule on these nodes (weights = integrals of the Lagrange basis)
+    # integrates polynomials of degree 2q - 1 exactly; q <= 2 gives the equispaced set
+    x = fe1d.gll_nodes01(q)
+    t, wg = fe1d.gauss_legendre01(q + 2)
+    w = np.einsum('g,gi->i', wg, fe1d.lagrange_values(q, t, 'gll'))
+    for k in range(2 * q):
+        assert abs(np.dot(w, x ** k) - 1.0 / (k + 1)) < 1e-14, k
+    if q <= 2:
+        assert np.array_equal(x, np.linspace(0.0, 1.0, q + 1))
+
+
+def test_error_on_the_paper_workload_falls_faster_with_each_q():
+    # Sec. 4 / Fig. compareerr: two biased cubes, h = 1/15, 7^3 block, q = 1 .. 4;
+    # measured 2.9e-3, 3.2e-4, 2.3e-5, 1.5e-6: each step of q gains more than the last
+    pos, Q = workloads.two_biased_cubes(120)
+    pe = ewald.ewald(pos, Q, 1.0)
+    err = []
+    for q in (1, 2, 3, 4):
+        d = highorder.forward(pos, Q, 1.0, 15, q, n_sr=3)['phi'] - pe
+        d -= d.mean()
+        err.append(np.linalg.norm(d) / np.linalg.norm(pe))
+    gain = [err[i] / err[i + 1] for i in range(3)]
+    assert err[0] < 5e-3 and gain[0] > 5 and gain[1] > gain[0] and gain[2] > gain[1], (err, gain)
