@@ -226,6 +226,19 @@ int fep3m_mesh_eigenbasis(int n_el, double* lam, double* V);
 int fep3m_mesh_eigenbasis_order(int p, int n_el, double* lam, double* V);
 int fep3m_screen_type_table(int q, int tx, int ty, int tz, int n_sr, int pad, double* kept);
 
+/* Host only: the table operand of the node-regrouped screen contraction of
+ * order q (Sec. 2.4, Eq. sc with the tables of the Remark of Sec. 4), p = q + 2.
+ * The screens of a target element's block are the sum over the order-q screen
+ * nodes u of the block (U = (2 n_sr + 1) q + 1 per axis, u = -q n_sr ..
+ * q (n_sr + 1) in steps of 1/q element from the target element's origin) of
+ * the node's weight times the table of its type (u mod q) anchored at
+ * floor(u / q).  H: host array of U^3 (q + 3)^3 values, H[o (q+3)^3 + m],
+ * o = ox + U (oy + U oz) with o_a = q (n_sr + 1) - u_a, m = mx + (q+3) (my +
+ * (q+3) mz) the target element's order-p nodes; the values are those of the
+ * type tables (h = 1).  For q = 1 this is the vertex-offset table of the
+ * order-1 screen contraction.  FEP3M_EINVAL as fep3m_screen_type_table.     */
+int fep3m_screen_node_table(int q, int n_sr, int pad, double* H);
+
 /* Load vector without any allocation (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory: work issued while a
  * stream is being captured into a CUDA graph, applications whose memory

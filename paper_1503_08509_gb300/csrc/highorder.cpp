@@ -295,6 +295,46 @@ void screen_type_table(int p, int q, const int t3[3], int keep, int pad, int ngl
       for (int i = 0; i < K; ++i) kept[i + (size_t)K * (j + (size_t)K * k)] = H[idx(i + o, j + o, k + o)];
 }
 
+// The table operand of the node-regrouped screen contraction for order q
+// (Sec. 2.4, Eq. sc with the Remark's tables): the screens of a target
+// element's block are sums over the order-q screen nodes u of the block
+// (U = (2 n_sr + 1) q + 1 per axis, u = -q n_sr .. q (n_sr + 1) in steps of
+// 1 / q element from the target element's origin), each node's weight times
+// the table of its type (u mod q) anchored at floor(u / q).  Row o (per axis
+// o = q (n_sr + 1) - u, so that q = 1 gives the vertex-offset order of the
+// order-1 contraction) holds that table at the (p+1)^3 nodes m of the target
+// element: table index p ceil(o / q) + m along each axis.  H[o * (p+1)^3 + m],
+// o = ox + U (oy + U oz), m = mx + (p+1) (my + (p+1) mz).
+void screen_node_table(int q, int n_sr, int pad, int ngl, std::vector<double>& H) {
+  const int p = q + 2, keep = n_sr + 1, U = (2 * n_sr + 1) * q + 1, P1 = p + 1, K = 2 * keep * p + 1;
+  std::vector<std::vector<double>> T((size_t)q * q * q);
+  for (int tz = 0; tz < q; ++tz)
+    for (int ty = 0; ty < q; ++ty)
+      for (int tx = 0; tx < q; ++tx) {
+        const int t3[3] = {tx, ty, tz};
+        screen_type_table(p, q, t3, keep, pad, ngl, T[tx + q * (ty + q * tz)]);
+      }
+  const int M = P1 * P1 * P1;
+  H.assign((size_t)U * U * U * M, 0.0);
+  for (int oz = 0; oz < U; ++oz)
+    for (int oy = 0; oy < U; ++oy)
+      for (int ox = 0; ox < U; ++ox) {
+        const int o[3] = {ox, oy, oz};
+        int type[3], base[3];
+        for (int a = 0; a < 3; ++a) {
+          type[a] = (q - o[a] % q) % q;            // (u mod q) with u = q keep - o
+          base[a] = p * ((o[a] + q - 1) / q);      // p ceil(o / q)
+        }
+        const std::vector<double>& Tt = T[type[0] + q * (type[1] + q * type[2])];
+        double* row = H.data() + ((size_t)ox + (size_t)U * (oy + (size_t)U * oz)) * M;
+        for (int mz = 0; mz < P1; ++mz)
+          for (int my = 0; my < P1; ++my)
+            for (int mx = 0; mx < P1; ++mx)
+              row[mx + P1 * (my + P1 * mz)] =
+                  Tt[(base[0] + mx) + (size_t)K * ((base[1] + my) + (size_t)K * (base[2] + mz))];
+      }
+}
+
 }  // namespace fep3m
 
 extern "C" {
@@ -305,6 +345,14 @@ int fep3m_mesh_eigenbasis_order(int p, int n_el, double* lam, double* V) {
   fep3m::periodic_eigen_order(p, n_el, l, v);
   std::memcpy(lam, l.data(), l.size() * sizeof(double));
   std::memcpy(V, v.data(), v.size() * sizeof(double));
+  return FEP3M_OK;
+}
+
+int fep3m_screen_node_table(int q, int n_sr, int pad, double* H) {
+  if (q < 1 || q > 4 || n_sr < 1 || n_sr > 4 || pad < 1 || pad > 8 || !H) return FEP3M_EINVAL;
+  std::vector<double> out;
+  fep3m::screen_node_table(q, n_sr, pad, 8, out);
+  std::memcpy(H, out.data(), out.size() * sizeof(double));
   return FEP3M_OK;
 }
 

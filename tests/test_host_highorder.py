@@ -76,3 +76,40 @@ def test_bad_arguments_are_rejected(lib):
     assert lib.fep3m_screen_type_table(2, 2, 0, 0, 1, 1, ptr(out)) != 0     # type out of range
     assert lib.fep3m_screen_type_table(5, 0, 0, 0, 1, 1, ptr(out)) != 0     # q out of range
     assert lib.fep3m_screen_type_table(2, 0, 0, 0, 0, 1, ptr(out)) != 0     # n_sr out of range
+
+
+@pytest.mark.parametrize("q, n_sr", [(1, 2), (2, 1), (3, 1)])
+def test_node_table_regroups_the_window_contraction(lib, q, n_sr):
+    # the block's screens at a target element's nodes, regrouped by screen node u,
+    # equal the oracle's per-source-element window contraction
+    from oracle import fep3m
+    p, keep, pad = q + 2, n_sr + 1, 1
+    U, M = (2 * n_sr + 1) * q + 1, (p + 1) ** 3
+    H = np.empty(U ** 3 * M)
+    assert lib.fep3m_screen_node_table(q, n_sr, pad, ptr(H)) == 0
+    H = H.reshape(U ** 3, M)
+    n = 2 * n_sr + 3
+    rng = np.random.default_rng(q)
+    C = rng.normal(size=(n ** 3, (q + 1) ** 3))
+    c3 = rng.integers(0, n, size=(6, 3))
+    offs = fep3m.block_offsets(n_sr)
+    kept = highorder.kept_tables(p, q, keep, half_width=keep + pad, ngl=8)
+    ref = fep3m.gather_block_coefficients(C, c3, n, offs) @ highorder.screen_window_matrix(n_sr, p, q, kept)
+    A = np.zeros((len(c3), U ** 3))
+    for t, e in enumerate(c3):
+        for d in offs:
+            s = (e + d) % n
+            for kap in range((q + 1) ** 3):
+                o = q * keep - (q * d + highorder.local_node(kap, q))
+                A[t, o[0] + U * (o[1] + U * o[2])] += C[s[0] + n * s[1] + n * n * s[2], kap]
+    got = A @ H
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+    if q == 1:
+        # the order-1 vertex-offset layout: row o reads the hat table at 3 o + m
+        K = 6 * keep + 1
+        T = np.empty(K ** 3)
+        assert lib.fep3m_screen_type_table(1, 0, 0, 0, n_sr, pad, ptr(T)) == 0
+        T = T.reshape(K, K, K)                           # [z][y][x]
+        o, m = (1, 4, 2), (3, 0, 2)
+        row = o[0] + U * (o[1] + U * o[2])
+        assert H[row, m[0] + 4 * (m[1] + 4 * m[2])] == T[3 * o[2] + m[2], 3 * o[1] + m[1], 3 * o[0] + m[0]]
