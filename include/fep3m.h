@@ -239,6 +239,16 @@ int fep3m_screen_type_table(int q, int tx, int ty, int tz, int n_sr, int pad, do
  * order-1 screen contraction.  FEP3M_EINVAL as fep3m_screen_type_table.     */
 int fep3m_screen_node_table(int q, int n_sr, int pad, double* H);
 
+/* Host only: the screen weights of Eq. moment1d as polynomials.  Per axis the
+ * weight of local node i (0..q) of the charge's element, offset delta from
+ * the element's centre, is w_i = sum_l W[i (q+1) + l] (delta / h)^l / h, with
+ * W the inverse of the centred moment matrix of the order-q nodal functions
+ * (Gauss-Lobatto nodes; the vertex functions reach into the neighbouring
+ * elements).  one_element != 0: the one-element screens (Sec. 5.3), interior
+ * nodes only and moments l < q - 1 (needs q >= 2); other entries are zero.
+ * W: host array of (q+1)^2 values.  FEP3M_EINVAL for q outside 1..4.        */
+int fep3m_screen_weight_poly(int q, int one_element, double* W);
+
 /* Load vector without any allocation (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory: work issued while a
  * stream is being captured into a CUDA graph, applications whose memory

@@ -6,6 +6,7 @@
 // per evaluation.
 #include <cmath>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -335,9 +336,74 @@ void screen_node_table(int q, int n_sr, int pad, int ngl, std::vector<double>& H
       }
 }
 
+// Screen weights as polynomials in delta / h (Eq. moment1d): per axis the
+// weights w_i(delta) of the order-q nodal functions of the charge's element
+// solve sum_i Omega[l][i] w_i = delta^l, Omega[l][i] = int x^l omega_i(x) dx
+// (centred element [-1/2, 1/2], h = 1; the vertex functions reach into the
+// neighbouring elements), so w = Omega^-1 (1, delta, delta^2, ...) and
+// W = Omega^-1 holds the coefficients: w_i = sum_l W[i][l] (delta / h)^l / h.
+// One-element screens (Sec. 5.3) use the interior functions only, with the
+// moments l < q - 1; their rows and columns sit at i = 1 .. q-1, l = 0 .. q-2,
+// the rest zero.  Gauss-Lobatto nodes, as the type tables.  Returns false if
+// the moment matrix is singular.
+bool screen_weight_poly(int q, bool one_element, std::vector<double>& W) {
+  std::vector<double> x, w, vq(q + 1), nq(q + 1);
+  gauss_legendre01(q + 2, x, w);
+  node_set(q, true, nq.data());
+  std::vector<double> Om((size_t)(q + 1) * (q + 1), 0.0);   // [l][i]
+  auto add_piece = [&](double lo, int local, int node) {   // piece [lo, lo + 1], local basis index
+    for (size_t g = 0; g < x.size(); ++g) {
+      lagrange(q, nq.data(), x[g], vq.data(), nullptr);
+      const double xs = lo + x[g];
+      double xl = 1.0;
+      for (int l = 0; l <= q; ++l, xl *= xs) Om[(size_t)l * (q + 1) + node] += w[g] * xl * vq[local];
+    }
+  };
+  for (int i = 0; i <= q; ++i) add_piece(-0.5, i, i);
+  add_piece(-1.5, q, 0);    // node 0 is the right vertex of the left neighbour
+  add_piece(0.5, 0, q);     // node q is the left vertex of the right neighbour
+  const int i0 = one_element ? 1 : 0, m = one_element ? q - 1 : q + 1;
+  if (m < 1) return false;
+  // Gauss-Jordan inverse of the m x m block Om[l][i0 + i], l < m, partial pivoting
+  std::vector<double> A((size_t)m * 2 * m, 0.0);
+  for (int l = 0; l < m; ++l) {
+    for (int i = 0; i < m; ++i) A[(size_t)l * 2 * m + i] = Om[(size_t)l * (q + 1) + i0 + i];
+    A[(size_t)l * 2 * m + m + l] = 1.0;
+  }
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (std::fabs(A[(size_t)r * 2 * m + c]) > std::fabs(A[(size_t)piv * 2 * m + c])) piv = r;
+    if (std::fabs(A[(size_t)piv * 2 * m + c]) < 1e-300) return false;
+    if (piv != c)
+      for (int k = 0; k < 2 * m; ++k) std::swap(A[(size_t)c * 2 * m + k], A[(size_t)piv * 2 * m + k]);
+    const double d = A[(size_t)c * 2 * m + c];
+    for (int k = 0; k < 2 * m; ++k) A[(size_t)c * 2 * m + k] /= d;
+    for (int r = 0; r < m; ++r) {
+      if (r == c) continue;
+      const double f = A[(size_t)r * 2 * m + c];
+      if (f != 0.0)
+        for (int k = 0; k < 2 * m; ++k) A[(size_t)r * 2 * m + k] -= f * A[(size_t)c * 2 * m + k];
+    }
+  }
+  // A's right half is Om_block^-1: rows = nodes i, columns = moments l
+  W.assign((size_t)(q + 1) * (q + 1), 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int l = 0; l < m; ++l) W[(size_t)(i0 + i) * (q + 1) + l] = A[(size_t)i * 2 * m + m + l];
+  return true;
+}
+
 }  // namespace fep3m
 
 extern "C" {
+
+int fep3m_screen_weight_poly(int q, int one_element, double* W) {
+  if (q < 1 || q > 4 || !W || (one_element && q < 2)) return FEP3M_EINVAL;
+  std::vector<double> out;
+  if (!fep3m::screen_weight_poly(q, one_element != 0, out)) return FEP3M_EINVAL;
+  std::memcpy(W, out.data(), out.size() * sizeof(double));
+  return FEP3M_OK;
+}
 
 int fep3m_mesh_eigenbasis_order(int p, int n_el, double* lam, double* V) {
   if (p < 1 || p > 8 || n_el < 1 || (long long)p * n_el > 8192 || !lam || !V) return FEP3M_EINVAL;

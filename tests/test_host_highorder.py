@@ -113,3 +113,27 @@ def test_node_table_regroups_the_window_contraction(lib, q, n_sr):
         o, m = (1, 4, 2), (3, 0, 2)
         row = o[0] + U * (o[1] + U * o[2])
         assert H[row, m[0] + 4 * (m[1] + 4 * m[2])] == T[3 * o[2] + m[2], 3 * o[1] + m[1], 3 * o[0] + m[0]]
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4])
+@pytest.mark.parametrize("one_element", [False, True])
+def test_screen_weight_polynomials_match_the_oracle(lib, q, one_element):
+    if one_element and q < 2:
+        return
+    W = np.empty((q + 1) ** 2)
+    assert lib.fep3m_screen_weight_poly(q, int(one_element), ptr(W)) == 0
+    W = W.reshape(q + 1, q + 1)                        # [node i][power l]
+    h = 0.37
+    delta = np.linspace(-0.5, 0.5, 7) * h
+    got = np.stack([np.polyval(W[i][::-1], delta / h) / h for i in range(q + 1)], axis=-1)
+    from oracle import screens
+    if one_element:
+        # the oracle's one-element system: interior functions, moments l < q - 1
+        Om = screens.moment_matrix_1d(q, h, highorder.NODES)[:q - 1, 1:q]
+        rhs = np.stack([delta ** l for l in range(q - 1)], axis=0)
+        ref = np.linalg.solve(Om, rhs).T
+        assert np.allclose(got[:, 1:q], ref, rtol=1e-11, atol=1e-11 / h)
+        assert np.all(got[:, 0] == 0) and np.all(got[:, q] == 0)
+    else:
+        ref = screens.screen_weights_1d(q, h, delta, highorder.NODES)
+        assert np.allclose(got, ref, rtol=1e-11, atol=1e-11 / h)
