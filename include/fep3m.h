@@ -249,6 +249,15 @@ int fep3m_screen_node_table(int q, int n_sr, int pad, double* H);
  * W: host array of (q+1)^2 values.  FEP3M_EINVAL for q outside 1..4.        */
 int fep3m_screen_weight_poly(int q, int one_element, double* W);
 
+/* Host only: the 1-D eigenbasis of the order-p mesh on a box of n_el
+ * elements of unit length (Sec. "Alternate boundary conditions"), for the
+ * fast-diagonalisation solve of a box.  dirichlet != 0: the interior nodes,
+ * N = p n_el - 1; else (Neumann data) all nodes, N = p n_el + 1, with one
+ * zero eigenvalue (the constant).  lam: N values (ascending); V: N x N host
+ * array, V[node * N + mode], M1-orthonormal.  FEP3M_EINVAL unless
+ * 1 <= p <= 8, n_el >= 1 and p n_el <= 1024.                                */
+int fep3m_box_eigenbasis(int p, int n_el, int dirichlet, double* lam, double* V);
+
 /* Load vector without any allocation (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory: work issued while a
  * stream is being captured into a CUDA graph, applications whose memory

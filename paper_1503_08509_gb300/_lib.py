@@ -48,6 +48,7 @@ SIGNATURES = {
     "fep3m_screen_type_table": (ctypes.c_int, [ctypes.c_int] * 6 + [P]),
     "fep3m_screen_node_table": (ctypes.c_int, [ctypes.c_int] * 3 + [P]),
     "fep3m_screen_weight_poly": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P]),
+    "fep3m_box_eigenbasis": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]),
     "fep3m_load_vector_static": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, ctypes.c_int64, P, P, P, P]),
     "fep3m_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "fep3m_destroy": (None, [P]),

@@ -4,6 +4,7 @@
 // the periodic order-p mesh (block-Fourier reduction), and the FE tables of the
 // q^3 basis-screen types (Remark of Sec. 4).  Host code only; nothing here runs
 // per evaluation.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <utility>
@@ -393,9 +394,50 @@ bool screen_weight_poly(int q, bool one_element, std::vector<double>& W) {
   return true;
 }
 
+// Generalized eigenpairs K1 v = lam M1 v of the order-p mesh on a box of n
+// elements (open mesh, p n + 1 nodes, h = 1): Dirichlet data fixes the two end
+// nodes, so the pencil is the interior block (p n - 1 nodes); Neumann data
+// leaves every node free (p n + 1 nodes; one eigenvalue is 0, the constant).
+// The boxes' fast-diagonalisation solves (Sec. "Alternate boundary
+// conditions") transform with V, V^T M1 V = I, V[node * N + mode].
+void box_eigen(int p, int n, bool dirichlet, std::vector<double>& lam, std::vector<double>& V) {
+  const ElementPQ E(p, 1);
+  const int Nall = p * n + 1, o = dirichlet ? 1 : 0, N = dirichlet ? Nall - 2 : Nall;
+  std::vector<double> M((size_t)N * N, 0.0), K((size_t)N * N, 0.0);
+  for (int e = 0; e < n; ++e)
+    for (int i = 0; i <= p; ++i)
+      for (int j = 0; j <= p; ++j) {
+        const int r = p * e + i - o, c = p * e + j - o;
+        if (r < 0 || c < 0 || r >= N || c >= N) continue;
+        M[(size_t)r * N + c] += E.Me[i * (p + 1) + j];
+        K[(size_t)r * N + c] += E.Ke[i * (p + 1) + j];
+      }
+  std::vector<double> l0, V0;
+  generalized_eigen(N, K, M, l0, V0);
+  std::vector<int> ord(N);
+  for (int i = 0; i < N; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return l0[a] < l0[b]; });
+  lam.resize(N);
+  V.assign((size_t)N * N, 0.0);
+  for (int k = 0; k < N; ++k) {
+    lam[k] = l0[ord[k]];
+    for (int i = 0; i < N; ++i) V[(size_t)i * N + k] = V0[(size_t)i * N + ord[k]];
+  }
+}
+
 }  // namespace fep3m
 
 extern "C" {
+
+int fep3m_box_eigenbasis(int p, int n_el, int dirichlet, double* lam, double* V) {
+  if (p < 1 || p > 8 || n_el < 1 || (long long)p * n_el > 1024 || !lam || !V) return FEP3M_EINVAL;
+  if (dirichlet && p * n_el < 2) return FEP3M_EINVAL;
+  std::vector<double> l, v;
+  fep3m::box_eigen(p, n_el, dirichlet != 0, l, v);
+  std::memcpy(lam, l.data(), l.size() * sizeof(double));
+  std::memcpy(V, v.data(), v.size() * sizeof(double));
+  return FEP3M_OK;
+}
 
 int fep3m_screen_weight_poly(int q, int one_element, double* W) {
   if (q < 1 || q > 4 || !W || (one_element && q < 2)) return FEP3M_EINVAL;

@@ -137,3 +137,26 @@ def test_screen_weight_polynomials_match_the_oracle(lib, q, one_element):
     else:
         ref = screens.screen_weights_1d(q, h, delta, highorder.NODES)
         assert np.allclose(got, ref, rtol=1e-11, atol=1e-11 / h)
+
+
+@pytest.mark.parametrize("p", [1, 3, 5])
+@pytest.mark.parametrize("n", [1, 4, 9])
+@pytest.mark.parametrize("dirichlet", [True, False])
+def test_box_eigenbasis_matches_dense_solver(lib, p, n, dirichlet):
+    if dirichlet and p * n < 2:
+        return
+    Me, Ke = fe1d.element_matrices(p, 1.0)
+    M1, K1 = fe1d.assemble_open(Me, n, p), fe1d.assemble_open(Ke, n, p)
+    if dirichlet:
+        M1, K1 = M1[1:-1, 1:-1], K1[1:-1, 1:-1]
+    N = len(M1)
+    lam, V = np.empty(N), np.empty((N, N))
+    assert lib.fep3m_box_eigenbasis(p, n, int(dirichlet), ptr(lam), ptr(V)) == 0
+    ref = sl.eigh(K1, M1, eigvals_only=True)
+    scale = max(np.abs(ref).max(), 1.0)
+    assert np.all(np.diff(lam) >= 0)
+    assert np.abs(lam - ref).max() < 1e-10 * scale
+    assert np.abs(V.T @ M1 @ V - np.eye(N)).max() < 1e-10
+    assert np.abs(V.T @ K1 @ V - np.diag(lam)).max() < 1e-10 * scale
+    if not dirichlet:
+        assert abs(lam[0]) < 1e-10 * scale                # the constant mode
