@@ -79,11 +79,16 @@ typedef struct {
                           solve (fast diagonalisation on the tensor cores, or
                           with FEP3M_MULTIGRID a multigrid-preconditioned CG);
                           the iterate and residual are FP64 (FP64) or
-                          double-float pairs (MIXED).  Pair and screen sums run
-                          in FP64 (FP64) or FP32 (MIXED; the screen
-                          contractions as split-precision bf16 tensor-core
-                          MMAs unless FEP3M_CUDA_CORES); projections and the
-                          energy reduction in FP64.                              */
+                          double-float pairs (MIXED).  Pair sums run in FP64
+                          (FP64) or FP32 (MIXED); the screen contractions in
+                          double-float arithmetic on the FP32 pipes (FP64) or
+                          as split-precision bf16 tensor-core MMAs (MIXED,
+                          unless FEP3M_CUDA_CORES); projections and the energy
+                          reduction in FP64.  Both paths hold charges and
+                          screen weights in FP32 ranges somewhere (the FP64
+                          path's double-float contractions, whose low words
+                          sit 2^-24 below the charges): keep |Q| within
+                          about 1e-30 .. 1e30 for full accuracy.               */
   double mg_rtol;      /* relative FE residual target; 0 -> 1e-13 (FP64) or
                           1e-10 (MIXED)                                          */
   int mg_max_cycles;   /* cap on refinement sweeps; 0 -> 10                      */
