@@ -33,6 +33,13 @@
  *   - Streams: all device work is issued on the stream given to
  *     fep3m_create, in order; calls returning host values synchronise it.
  *   - A context is not thread-safe; use one per host thread.
+ *   - Reproducibility: fep3m_compute and fep3m_vjp are bitwise reproducible
+ *     for the same inputs, configuration and GPU model: their only atomics
+ *     are on integers (bin counts, pair counts, last-block counters), and
+ *     every floating-point sum has a fixed order (the sorted charge order of
+ *     fep3m_set_particles is stable by index).  fep3m_load_vector_static
+ *     accumulates the vertex density with FP64 atomics and is reproducible
+ *     to rounding only.
  */
 #ifndef FEP3M_H
 #define FEP3M_H
