@@ -132,6 +132,68 @@ def type_table(p, q, t3, half_width=6, ngl=6, nodes=NODES):
     return H, tuple(x1)
 
 
+@functools.lru_cache(maxsize=64)
+def fine_type_table(p, q, t3, half_width, refine, ngl=6, nodes=NODES):
+    """The potential of the type-t3 basis screen on its box (as type_table) from an
+    order-p Galerkin solve on a mesh refine times finer (element size 1 / refine):
+    the stand-in for the continuum potential of Eq. sc (FE error ~ refine^-(p+1) of
+    the table's).  H[ix, iy, iz] at x = lo + k / (p refine)."""
+    ext = [box_extent(t, half_width) for t in t3]
+    nel = [refine * (hi - lo) for (lo, hi) in ext]
+    hf = 1.0 / refine
+    Me, Ke = fe1d.element_matrices(p, hf)
+    M1 = [fe1d.assemble_open(Me, ne, p) for ne in nel]
+    K1 = [fe1d.assemble_open(Ke, ne, p) for ne in nel]
+    tq, wq = fe1d.gauss_legendre01(p + q + 2)
+    m1 = []
+    for t, (lo, _), ne in zip(t3, ext, nel):
+        col = np.zeros(p * ne + 1)
+        for e in range(ne):
+            x = lo + (e + tq) * hf
+            psi = np.zeros_like(x)
+            for (a, b, f) in basis_pieces_1d(q, t, nodes):
+                inside = (x >= a) & (x <= b)
+                psi = np.where(inside, f(np.clip(x, a, b)), psi)
+            col[p * e:p * e + p + 1] += hf * np.einsum('g,g,gk->k', wq, psi, fe1d.lagrange_values(p, tq))
+        m1.append(col)
+    rhs = 4.0 * np.pi * m1[0][:, None, None] * m1[1][None, :, None] * m1[2][None, None, :]
+    x1 = [lo + np.arange(p * ne + 1) * (hf / p) for (lo, _), ne in zip(ext, nel)]
+    N = [len(x) for x in x1]
+    I, J, K = np.meshgrid(np.arange(N[0]), np.arange(N[1]), np.arange(N[2]), indexing='ij')
+    onb = (I == 0) | (I == N[0] - 1) | (J == 0) | (J == N[1] - 1) | (K == 0) | (K == N[2] - 1)
+    Hb = np.zeros(tuple(N))
+    pts = np.stack([x1[0][I[onb]], x1[1][J[onb]], x1[2][K[onb]]], axis=1)
+    Hb[onb] = basis_potential_continuum(q, t3, pts, ngl, nodes)
+    r = rhs - (tables.kron_apply(K1[0], M1[1], M1[2], Hb) + tables.kron_apply(M1[0], K1[1], M1[2], Hb)
+               + tables.kron_apply(M1[0], M1[1], K1[2], Hb))
+    r = r[1:-1, 1:-1, 1:-1]
+    eig = [scipy.linalg.eigh(K1[a][1:-1, 1:-1], M1[a][1:-1, 1:-1]) for a in range(3)]
+    (l0, V0), (l1, V1), (l2, V2) = eig
+    rh = tables.kron_apply(V0.T, V1.T, V2.T, r)
+    rh /= l0[:, None, None] + l1[None, :, None] + l2[None, None, :]
+    H = Hb.copy()
+    H[1:-1, 1:-1, 1:-1] = tables.kron_apply(V0, V1, V2, rh)
+    return H, tuple(x1)
+
+
+def evaluate_fine_table(H, x1, p, refine, pts):
+    """The fine table at points (M, 3) (anchor-relative, element units) with the order-p
+    basis of the fine element holding each point."""
+    lo = np.array([x[0] for x in x1])
+    u = (pts - lo) * refine                                  # fine-element units
+    nfe = np.array([(len(x) - 1) // p for x in x1])
+    e = np.clip(np.floor(u).astype(np.int64), 0, nfe - 1)
+    t = u - e
+    lv = [fe1d.lagrange_values(p, t[:, a]) for a in range(3)]
+    out = np.zeros(len(pts))
+    for mx in range(p + 1):
+        for my in range(p + 1):
+            for mz in range(p + 1):
+                out += (H[p * e[:, 0] + mx, p * e[:, 1] + my, p * e[:, 2] + mz]
+                        * lv[0][:, mx] * lv[1][:, my] * lv[2][:, mz])
+    return out
+
+
 def kept_tables(p, q, keep, half_width=None, ngl=6, interior_only=False, nodes=NODES):
     """Nodal values of each type's table on [-keep, keep]^3 about its anchor:
     dict t3 -> array ((2 keep p + 1),)*3; interior_only: the types with no vertex
@@ -226,11 +288,15 @@ def screen_window_matrix(n_sr, p, q, kept):
 
 
 def forward(pos, Q, L, n, q, n_sr=3, neutralise=True, chunk=1024, half_width=None, ngl=6, support='patch',
-            nodes=NODES):
+            nodes=NODES, screen_tables='fe', refine=3):
     """Phi_i and U for charges Q at pos (N x 3) with order-q screens and the order p = q + 2
     mesh (Sec. 2: p = q + 2), with the intermediates.  support='element' uses one-element
     screens (Sec. 5.3), still with p = q + 2.  nodes: the node set of the order-q screen
-    basis ('gll' or 'equispaced'); the order-p mesh space does not depend on it."""
+    basis ('gll' or 'equispaced'); the order-p mesh space does not depend on it.
+    screen_tables='fe': the screen potentials through the FE tables, evaluated with the
+    target element's order-p basis (the Remark of Sec. 4); 'continuum': through the
+    tables of a refine-times finer mesh evaluated at the charge itself, standing in for
+    the continuum tables of Eq. sc."""
     pos = np.asarray(pos, dtype=np.float64)
     Q = np.asarray(Q, dtype=np.float64)
     assert n >= 2 * n_sr + 1, "the short-range block must not wrap onto itself"
@@ -256,6 +322,32 @@ def forward(pos, Q, L, n, q, n_sr=3, neutralise=True, chunk=1024, half_width=Non
         sl = slice(s0, s0 + chunk)
         Cblk = gather_block_coefficients(C, bins['c3'][sl], n, offs)
         phi_scr[sl] = np.einsum('nm,nm->n', (h * h) * (Cblk @ Wmat), U3[sl])
+    if screen_tables == 'continuum':
+        phi_scr = continuum_screen_part(bins, C, n, q, p, n_sr, half_width, refine, ngl, nodes)
     phi = phi_sm + phi_sing - phi_scr
     return dict(phi=phi, U=0.5 * np.dot(Q, phi), phi_sm=phi_sm, phi_sing=phi_sing, phi_scr=phi_scr,
                 phi_mesh=phi_mesh, r=r, b=b, C=C, bins=bins, ops=ops, Wmat=Wmat, p=p, q=q)
+
+
+def continuum_screen_part(bins, C, n, q, p, n_sr, half_width, refine, ngl, nodes):
+    """Screen potentials of the block's charges at each charge from the fine tables,
+    evaluated at the charge's own position (Eq. sc form)."""
+    keep = n_sr + 1
+    hw = keep + 2 if half_width is None else half_width
+    h = bins['h']
+    c3, delta = bins['c3'], bins['delta']
+    tables_f = {t3: fine_type_table(p, q, t3, hw, refine, ngl, nodes) for t3 in itertools.product(range(q), repeat=3)}
+    x_loc = delta / h + 0.5                                   # target position in its element, element units
+    out = np.zeros(len(c3))
+    for d in block_offsets(n_sr):
+        src = (c3 + d) % n
+        s = src[:, 0] + n * src[:, 1] + n * n * src[:, 2]
+        for kap in range((q + 1) ** 3):
+            w = C[s, kap]
+            if not np.any(w):
+                continue
+            loc = local_node(kap, q)
+            anchor = d + (loc == q)                           # anchor vertex, target element units
+            H, x1 = tables_f[tuple(int(v) for v in loc % q)]
+            out += (h * h) * w * evaluate_fine_table(H, x1, p, refine, x_loc - anchor)
+    return out
