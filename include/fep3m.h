@@ -86,12 +86,19 @@ typedef struct {
                           solve (fast diagonalisation on the tensor cores, or
                           with FEP3M_MULTIGRID a multigrid-preconditioned CG);
                           the iterate and residual are FP64 (FP64) or
-                          double-float pairs (MIXED).  Pair sums run in FP64
+                          double-float pairs (MIXED: a departure from an FP64
+                          refinement residual, for speed -- FP64 issues at
+                          1/64 of the FP32 rate on this GPU -- accurate to
+                          about 2e-14 relative, far inside the 1e-10 the
+                          refinement reaches).  Pair sums run in FP64
                           (FP64) or FP32 (MIXED); the screen contractions in
-                          double-float arithmetic on the FP32 pipes (FP64) or
-                          as split-precision bf16 tensor-core MMAs (MIXED,
-                          unless FEP3M_CUDA_CORES); projections and the energy
-                          reduction in FP64.  Both paths hold charges and
+                          double-float arithmetic on the FP32 pipes (FP64, and
+                          MIXED with FEP3M_CUDA_CORES) or as split-precision
+                          bf16 tensor-core MMAs against tables relative to
+                          each element's corners (MIXED), with the parts that
+                          carry an element's potential level in double-float
+                          or FP64; projections and the energy reduction in
+                          FP64.  Both paths hold charges and
                           screen weights in FP32 ranges somewhere (the FP64
                           path's double-float contractions, whose low words
                           sit 2^-24 below the charges): keep |Q| within
@@ -277,8 +284,12 @@ int fep3m_box_eigenbasis(int p, int n_el, int dirichlet, double* lam, double* V)
  * implicit synchronisation).  Computes the same b as fep3m_get_mesh after a
  * compute: b = 4 pi (Mpq (x) Mpq (x) Mpq) r, r the order-1 vertex density of
  * the charges' screens, index ix + 3n iy + 9n^2 iz, without the neutrality
- * projection.  pos (N x 3), Q (N) and b ((3 n_el)^3) must be device pointers
- * on the current device; cuda_stream is a cudaStream_t (NULL = default).
+ * projection.  pos (N x 3), Q (N) and b ((3 n_el)^3) must be device (or
+ * managed) pointers of the current device, else FEP3M_EINVAL; cuda_stream is a
+ * cudaStream_t (NULL = default).  Unlike fep3m_set_particles this call does
+ * not check its inputs for finiteness: a non-finite coordinate is taken as 0
+ * and a non-finite charge carries into b (the call returns before the device
+ * has looked at the data).
  * Scratch is a file-scope device array of FEP3M_STATIC_MAX_NEL^3 doubles
  * (2 MiB) held by every GPU that loads the library until the process exits;
  * n_el > FEP3M_STATIC_MAX_NEL returns FEP3M_EINVAL.  The first call on a

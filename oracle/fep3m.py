@@ -364,3 +364,82 @@ def screen_coefficient_gradients(h, delta):
         out[:, kap, 1] = w[0][:, i] * dw[j] * w[2][:, k]
         out[:, kap, 2] = w[0][:, i] * w[1][:, j] * dw[k]
     return out
+
+
+def forces_at(pos, Q, L, n, targets, n_sr=3, chunk=4096):
+    """-dU/dx at the charges listed in targets only: the energy's adjoint (vjp with
+    gU = 1, gphi = 0, weights w = Q / 2) restricted to those charges.
+
+    The parts of vjp() are local to the target, except the mesh part: the
+    potential's mesh solve and the adjoint mesh solve still take every charge.
+    Target side (w_i grad_x [sum_j Q_j K(x, j)] at x_i): the singular sums over
+    the target's block, and the gradient of (mesh potential - screen field) at
+    the charge.  Source side (Q_i grad_x_i [sum_t w_t K(t, i)]): the singular sums
+    with weights w, the screen adjoint A[e_i, kappa] = sum over the charges t
+    whose block holds e_i of w_t h^2 T_kappa(x_t), and the vertex adjoint mu."""
+    pos = np.asarray(pos, dtype=np.float64)
+    Q = np.asarray(Q, dtype=np.float64)
+    tg = np.asarray(targets)
+    bins = bin_particles(pos, L, n)
+    h = bins['h']
+    C = element_coefficients(bins, Q, n)
+    r = vertex_density(C, n)
+    ops = MeshOperators(L, n)
+    phi_mesh = ops.solve(ops.neutralise(ops.load_vector(r)))
+    w = 0.5 * Q
+    sub = dict(bins)
+    for k in ('c3', 'cell', 'delta'):
+        sub[k] = bins[k][tg]
+    U3t, G3t = q3_basis(sub)
+    offs = block_offsets(n_sr)
+    Wmat = screen_window_matrix(n_sr)
+    # target side: mesh potential minus the screen field, differentiated at the charge
+    ix, iy, iz = element_node_index(sub['c3'], n)
+    Cblk = gather_block_coefficients(C, sub['c3'], n, offs)
+    Gscr = (h * h) * (Cblk @ Wmat)
+    grad_field = np.einsum('nm,nmk->nk', phi_mesh[ix, iy, iz] - Gscr, G3t)
+    # singular sums at the targets: sum_j Q_j (x_j - x_i)/R^3 and the same with w
+    perm, start, count = bins['perm'], bins['start'], bins['count']
+    grad_q = np.zeros((len(tg), 3))
+    grad_w = np.zeros((len(tg), 3))
+    for d in offs:
+        src = (sub['c3'] + d) % n
+        s = src[:, 0] + n * src[:, 1] + n * n * src[:, 2]
+        cnt = count[s]
+        for k in range(int(cnt.max()) if len(tg) else 0):
+            valid = k < cnt
+            j = perm[np.where(valid, start[s] + k, 0)]
+            valid &= j != tg
+            rel = d * h + bins['delta'][j] - sub['delta']
+            R = np.where(valid, np.sqrt(np.einsum('nk,nk->n', rel, rel)), 1.0)
+            grad_q += (np.where(valid, Q[j], 0.0) / R ** 3)[:, None] * rel
+            grad_w += (np.where(valid, w[j], 0.0) / R ** 3)[:, None] * rel
+    dx = w[tg, None] * (grad_field + grad_q) + Q[tg, None] * grad_w
+    # screen, source side: A[e_i, kappa] over the charges t of the blocks that hold e_i
+    # (t in element e_i - d for the block offset d; the window row of offset d)
+    A = np.zeros((len(tg), 8))
+    nw = Wmat.reshape(len(offs), 8, -1)
+    for di, d in enumerate(offs):
+        src = (sub['c3'] - d) % n
+        s = src[:, 0] + n * src[:, 1] + n * n * src[:, 2]
+        cnt = count[s]
+        for k in range(int(cnt.max()) if len(tg) else 0):
+            valid = k < cnt
+            t = perm[np.where(valid, start[s] + k, 0)]
+            Ut, _ = q3_basis(dict(h=h, delta=bins['delta'][t]))
+            A += (h * h) * np.where(valid, w[t], 0.0)[:, None] * (Ut @ nw[di].T)
+    # mesh, source side: lam = S g with g = sum_t w_t u(x_t) over every charge
+    g = np.zeros((3 * n,) * 3)
+    for s0 in range(0, len(Q), 1 << 18):
+        sl = slice(s0, s0 + (1 << 18))
+        U3, _ = q3_basis(dict(h=h, delta=bins['delta'][sl]))
+        gx, gy, gz = element_node_index(bins['c3'][sl], n)
+        np.add.at(g, (gx.ravel(), gy.ravel(), gz.ravel()), (w[sl, None] * U3).ravel())
+    mu = ops.vertex_adjoint(ops.solve(ops.neutralise(g)))
+    dc = screen_coefficient_gradients(h, sub['delta'])
+    coef = np.zeros((len(tg), 8))
+    for kap in range(8):
+        v = (sub['c3'] + corner(kap)) % n
+        coef[:, kap] = mu[v[:, 0], v[:, 1], v[:, 2]] - A[:, kap]
+    dx += Q[tg, None] * np.einsum('nk,nkd->nd', coef, dc)
+    return -dx

@@ -65,6 +65,7 @@ class FEP3M:
                                         ctypes.byref(h)), "fep3m_create")
         self._h = h
         self.N = 0
+        self.generation = 0   # bumped by set_particles: which charges the context holds
 
     def close(self):
         if getattr(self, "_h", None):
@@ -86,6 +87,7 @@ class FEP3M:
         pos = _f64(pos, (N, 3))
         Q = _f64(Q, (N,))
         self._keep = (pos, Q)   # the device path reads them on the stream
+        self.generation += 1
         _lib.check(_lib.load().fep3m_set_particles(self._h, N, _ptr(pos), _ptr(Q)), "fep3m_set_particles")
         self.N = N
 
@@ -155,19 +157,31 @@ class FEP3M:
 
 
 class FEP3MEnergy(torch.autograd.Function):
-    """(U, Phi) = FEP3MEnergy.apply(pos, Q, engine); backward uses the library's adjoint."""
+    """(U, Phi) = FEP3MEnergy.apply(pos, Q, engine); backward uses the library's adjoint.
+
+    The engine holds one set of charges at a time.  The forward saves its
+    inputs and the engine's generation; if the engine was given other charges
+    before this backward runs (another apply, set_particles), the backward sets
+    the saved ones again, so that the adjoint is that of this forward."""
 
     @staticmethod
     def forward(ctx, pos, Q, engine):
-        engine.set_particles(pos.detach(), Q.detach())
+        pos_d, Q_d = pos.detach(), Q.detach()
+        engine.set_particles(pos_d, Q_d)
         out = engine.compute(phi=True, energy=True, forces=False)
         ctx.engine = engine
-        ctx.mark_non_differentiable()
+        ctx.generation = engine.generation
+        ctx.save_for_backward(pos_d, Q_d)
         U = torch.tensor(out["U"], dtype=torch.float64, device=pos.device)
         return U, out["phi"]
 
     @staticmethod
     def backward(ctx, gU, gphi):
+        eng = ctx.engine
+        if eng.generation != ctx.generation:
+            pos, Q = ctx.saved_tensors
+            eng.set_particles(pos, Q)
+            ctx.generation = eng.generation
         gUv = 0.0 if gU is None else float(gU)
-        dpos, dQ = ctx.engine.vjp(gUv, None if gphi is None else gphi.contiguous())
+        dpos, dQ = eng.vjp(gUv, None if gphi is None else gphi.contiguous())
         return dpos, dQ, None

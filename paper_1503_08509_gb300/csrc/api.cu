@@ -11,7 +11,8 @@
 using namespace fep3m;
 
 namespace fep3m {
-unsigned long long g_kernel_launches = 0;
+std::atomic<unsigned long long> g_kernel_launches{0};
+thread_local bool t_uncounted = false;
 }
 
 namespace {
@@ -277,9 +278,9 @@ const char* fep3m_strerror(int s) {
 void fep3m_destroy(fep3m_ctx* c) {
   if (!c) return;
   free_particles(c);
-  void* p[] = {c->Hw64, c->Hw32, c->count, c->start, c->fill, c->scan_tmp, c->C, c->rv, c->Cv, c->b64, c->phi64,
+  void* p[] = {c->Hw64, c->count, c->start, c->fill, c->scan_tmp, c->C, c->rv, c->Cv, c->b64, c->phi64,
                c->res64, c->g64, c->lam64, c->scal, c->iflags, c->phi_hl, c->W_el, c->A_el, c->mu_v, c->Gscr, c->Hb, c->HbA,
-               c->Hdf, c->red_tmp, c->red_counter, c->D_adj};
+               c->Hdf, c->red_tmp, c->red_counter, c->D_adj, c->Ha64, c->H0df, c->Wsum};
   for (void* q : p) dfree(q);
   fep3m::solver_destroy(&c->solv[0]);
   fep3m::solver_destroy(&c->solv[1]);
@@ -339,30 +340,44 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
           const size_t o = ox + (size_t)noff * (oy + (size_t)noff * oz);
           Hw[o * 64 + m] = c->table_host[(3 * ox + mx) + (size_t)sk * ((3 * oy + my) + (size_t)sk * (3 * oz + mz))];
         }
-  std::vector<float> Hw32(Hw.begin(), Hw.end());
+  // MIXED: the FP32 contractions take the tables in relative form (the screen
+  // field's relative to each element's corners, the adjoint's to node 0), so
+  // their FP32 sums carry no large smooth part (pair_relative_table)
+  std::vector<double> Hrel(Hw.size()), Hd(Hw.size());
+  std::vector<float> H0((size_t)noff * noff * noff * 2);
+  if (c->precision == FEP3M_MIXED) {
+    pair_relative_table(c->n_sr, Hw.data(), Hrel.data());
+    pair_adjoint_table(c->n_sr, Hw.data(), Hd.data(), H0.data());
+  } else {
+    Hrel = Hw;
+  }
   if ((st = from_cuda(dalloc(&c->Hw64, Hw.size()))) != FEP3M_OK) return fail(st);
-  if ((st = from_cuda(dalloc(&c->Hw32, Hw.size()))) != FEP3M_OK) return fail(st);
   cudaMemcpy(c->Hw64, Hw.data(), Hw.size() * 8, cudaMemcpyHostToDevice);
-  cudaMemcpy(c->Hw32, Hw32.data(), Hw32.size() * 4, cudaMemcpyHostToDevice);
-  if (c->precision == FEP3M_FP64) {
-    // hi = fl32(H), lo = fl32(H - hi): the operand pairs of the FP64 path's
-    // double-float screen contraction
-    std::vector<float> hdf(2 * Hw.size());
-    for (size_t i = 0; i < Hw.size(); ++i) {
-      hdf[2 * i] = (float)Hw[i];
-      hdf[2 * i + 1] = (float)(Hw[i] - (double)hdf[2 * i]);
+  if (c->precision == FEP3M_FP64 || (cfg->flags & FEP3M_CUDA_CORES)) {
+    // hi = fl32(H), lo = fl32(H - hi): the operand pairs of the double-float
+    // screen contraction on the CUDA cores (MIXED: of the relative table)
+    std::vector<float> hdf(2 * Hrel.size());
+    for (size_t i = 0; i < Hrel.size(); ++i) {
+      hdf[2 * i] = (float)Hrel[i];
+      hdf[2 * i + 1] = (float)(Hrel[i] - (double)hdf[2 * i]);
     }
     if ((st = from_cuda(cudaMalloc(&c->Hdf, hdf.size() * 4))) != FEP3M_OK) return fail(st);
     cudaMemcpy(c->Hdf, hdf.data(), hdf.size() * 4, cudaMemcpyHostToDevice);
   }
+  if (c->precision == FEP3M_MIXED) {
+    if ((st = from_cuda(dalloc(&c->Ha64, Hd.size()))) != FEP3M_OK) return fail(st);
+    cudaMemcpy(c->Ha64, Hd.data(), Hd.size() * 8, cudaMemcpyHostToDevice);
+    if ((st = from_cuda(cudaMalloc(&c->H0df, H0.size() * 4))) != FEP3M_OK) return fail(st);
+    cudaMemcpy(c->H0df, H0.data(), H0.size() * 4, cudaMemcpyHostToDevice);
+  }
   if (c->precision == FEP3M_MIXED && !(cfg->flags & FEP3M_CUDA_CORES)) {
     // bf16 pieces of the table for the tensor-core screen contraction
     std::vector<uint16_t> hb(pair_tc_table_bytes(c->n_sr) / 2);
-    pair_tc_table(c->n_sr, Hw.data(), hb.data());
+    pair_tc_table(c->n_sr, Hrel.data(), hb.data());
     if ((st = from_cuda(cudaMalloc(&c->Hb, hb.size() * 2))) != FEP3M_OK) return fail(st);
     cudaMemcpy(c->Hb, hb.data(), hb.size() * 2, cudaMemcpyHostToDevice);
     std::vector<uint16_t> ha(pair_adj_table_bytes(c->n_sr) / 2);
-    pair_adj_table(c->n_sr, Hw.data(), ha.data());
+    pair_adj_table(c->n_sr, Hd.data(), ha.data());
     if ((st = from_cuda(cudaMalloc(&c->HbA, ha.size() * 2))) != FEP3M_OK) return fail(st);
     cudaMemcpy(c->HbA, ha.data(), ha.size() * 2, cudaMemcpyHostToDevice);
     if ((st = from_cuda(tc_rows_prepare(128))) != FEP3M_OK) return fail(st);
@@ -386,7 +401,8 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
       (e = dalloc(&c->red_tmp, 1024)) != cudaSuccess || (e = dalloc(&c->red_counter, 1)) != cudaSuccess ||
       (e = cudaMalloc(&c->Gscr, pair_screen_bytes(c))) != cudaSuccess)
     return fail(from_cuda(e));
-  if (c->precision == FEP3M_MIXED && (e = cudaMalloc(&c->phi_hl, nodes * 2 * sizeof(float))) != cudaSuccess)
+  if (c->precision == FEP3M_MIXED && ((e = cudaMalloc(&c->phi_hl, nodes * 2 * sizeof(float))) != cudaSuccess ||
+                                      (e = cudaMalloc(&c->Wsum, ne * sizeof(float2))) != cudaSuccess))
     return fail(from_cuda(e));
   cudaMemset(c->red_counter, 0, sizeof(unsigned int));
   cudaMemset(c->iflags, 0, 16 * sizeof(int));
@@ -553,7 +569,7 @@ int fep3m_get_stats(const fep3m_ctx* c, fep3m_stats* out) {
   // after the binning); filling them in is not a visible change of the context
   fep3m_ctx* m = const_cast<fep3m_ctx*>(c);
   if (m->counts_stale && m->have_particles) {
-    const unsigned long long launches = g_kernel_launches;   // bookkeeping, not a launch of the method
+    t_uncounted = true;   // bookkeeping, not a launch of the method
     if (cudaEventRecord(m->ev_pfork, m->stream) == cudaSuccess &&
         cudaStreamWaitEvent(m->pair_stream, m->ev_pfork, 0) == cudaSuccess &&
         pair_counts(m, (unsigned long long*)(m->scal + 48), m->pair_stream) == cudaSuccess &&
@@ -564,10 +580,10 @@ int fep3m_get_stats(const fep3m_ctx* c, fep3m_stats* out) {
       take_counts(m);
     else
       (void)cudaGetLastError();
-    g_kernel_launches = launches;
+    t_uncounted = false;
   }
   *out = c->stats;
-  out->kernel_launches = (int64_t)g_kernel_launches;
+  out->kernel_launches = (int64_t)g_kernel_launches.load(std::memory_order_relaxed);
   return FEP3M_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations of the FE-P3M library (not part of the C ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
 #include <vector>
@@ -10,8 +11,15 @@
 namespace fep3m {
 
 // every kernel launch of the library is prefixed with FEP3M_CL, which counts it
-extern unsigned long long g_kernel_launches;
-#define FEP3M_CL (void)++::fep3m::g_kernel_launches,
+// (relaxed atomic: the allocation-free entry point may run on other host
+// threads).  Launches a host thread issues while capturing a graph, or for
+// bookkeeping, are not counted (t_uncounted); a replayed graph adds its kernels.
+extern std::atomic<unsigned long long> g_kernel_launches;
+extern thread_local bool t_uncounted;
+inline void count_launches(unsigned long long k = 1) {
+  if (!t_uncounted) g_kernel_launches.fetch_add(k, std::memory_order_relaxed);
+}
+#define FEP3M_CL ::fep3m::count_launches(),
 
 // Programmatic dependent launch (the mesh solve: chains of short
 // dependent kernels).  A kernel launched by launch_pdl may be set up while the
@@ -27,7 +35,7 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args&&... args) {
-  ++g_kernel_launches;
+  count_launches();
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -169,10 +177,9 @@ struct fep3m_ctx {
   double L = 1, h = 1, inv_h = 1;
   int precision = FEP3M_FP64;
   fep3m::Stencils st;
-  // kept FE table (host copy) and device copies in [offset][node] layout
+  // kept FE table (host copy) and its device copy in [offset][node] layout
   std::vector<double> table_host;
   double* Hw64 = nullptr;
-  float* Hw32 = nullptr;
   // particles
   int64_t N = 0, cap = 0;
   bool have_particles = false, have_forward = false, have_grad = false;
@@ -218,7 +225,11 @@ struct fep3m_ctx {
   void* Gscr = nullptr;          // screen field at each brick element's 64 nodes, bricks * 4096 (T)
   void* Hb = nullptr;            // bf16 pieces of the table for the tensor-core contraction (MIXED)
   void* HbA = nullptr;           // the same for the screen adjoint's contraction (MIXED)
-  void* Hdf = nullptr;           // hi + lo float pairs of the table, the double-float screen contraction (FP64)
+  void* Hdf = nullptr;           // hi + lo float pairs of the table (MIXED: of Hrel), the double-float
+                                 // screen contraction on the CUDA cores
+  double* Ha64 = nullptr;        // MIXED: the screen adjoint's table relative to node 0 (pair_adjoint_table)
+  void* H0df = nullptr;          // MIXED: H(o, 0) per vertex offset as hi + lo floats
+  void* Wsum = nullptr;          // MIXED: per element, the sum of the adjoint weights as hi + lo floats
   int* host_err = nullptr;       // pinned: device-side error flags read after a step
   double* red_tmp = nullptr;     // reduction partials (1024)
   unsigned int* red_counter = nullptr;
@@ -278,15 +289,21 @@ size_t pair_tc_table_bytes(int n_sr);
 void pair_tc_table(int n_sr, const double* Hw, uint16_t* out);
 size_t pair_adj_table_bytes(int n_sr);
 void pair_adj_table(int n_sr, const double* Hw, uint16_t* out);
+// the FP32 path's tables: the screen field's relative to each element's
+// corners, the screen adjoint's relative to node 0 (with H(o, 0) as hi + lo
+// floats, 2 per offset)
+void pair_relative_table(int n_sr, const double* Hw, double* Hrel);
+void pair_adjoint_table(int n_sr, const double* Hw, double* Hd, float* H0);
 // energy_adjoint: also leave half the singular sums in psi_s / gpsi_s (the
 // singular adjoint of the energy's weights Q / 2)
 cudaError_t pair_screen(fep3m_ctx* c, int want_grad, cudaStream_t s, bool energy_adjoint);
 cudaError_t pair_prepare(fep3m_ctx* c);
-// tensor-core row GEMM with transposed output (mesh.cu): out[(i - tile0 nt) R + r]
-// = sum_{a < K} in[r K + a] B[i][a]; B in split bf16 pieces per column tile of nt
+// tensor-core row GEMM with transposed output (mesh.cu): out[(i - cb) R + r]
+// = sum_{a < K} in[r K + a] B[i][a] for the columns cb <= i < ce; B in split
+// bf16 pieces per column tile of nt
 cudaError_t tc_rows_prepare(int nt);
-cudaError_t tc_rows_gemm(int64_t R, int K, int NC, int nt, int tile0, int ntiles, const float* in, const void* Bp,
-                         float* out, int* err, cudaStream_t s);
+cudaError_t tc_rows_gemm(int64_t R, int K, int cb, int ce, int nt, const float* in, const void* Bp, float* out,
+                         int* err, cudaStream_t s);
 cudaError_t pair_eval(fep3m_ctx* c, double* phi_out, int want_grad);
 // adjoint in three parts: weights and deposit (-> g64), the parts that need
 // lam (vertex adjoint, screen sweep, singular adjoint), and the per-charge assembly

@@ -140,23 +140,29 @@ __global__ void k_vertex_density(int n, const T* __restrict__ C, T* __restrict__
 }
 
 // one axis of the order-3 x order-1 mixed mass: global order-3 node g -> up to
-// three vertices with weights
+// three vertices with weights.  FP32: the weights times 120, which are exact
+// integers (the element entries are 13/120, 1/60, 3/10 and 3/40), so that the
+// load vector carries no systematic rounding of the weights (it would scale
+// each charge's own smooth potential against its screen and bias U); the
+// caller divides by 120^3 in FP64.
 template <class T>
 __device__ __forceinline__ int mpq_row(int g, int n, int vtx[3], T wgt[3]) {
+  const double s = sizeof(T) == 4 ? 120.0 : 1.0;
+  auto wq = [s](double v) -> T { return sizeof(T) == 4 ? (T)rint(s * v) : (T)v; };
   const int e = g / 3, t = g - 3 * e;
   if (t == 0) {
-    vtx[0] = wrapi(e - 1, n); wgt[0] = (T)cMpq64[3][0];
-    vtx[1] = e;               wgt[1] = (T)(cMpq64[0][0] + cMpq64[3][1]);
-    vtx[2] = wrapi(e + 1, n); wgt[2] = (T)cMpq64[0][1];
+    vtx[0] = wrapi(e - 1, n); wgt[0] = wq(cMpq64[3][0]);
+    vtx[1] = e;               wgt[1] = wq(cMpq64[0][0] + cMpq64[3][1]);
+    vtx[2] = wrapi(e + 1, n); wgt[2] = wq(cMpq64[0][1]);
     return 3;
   }
-  vtx[0] = e;               wgt[0] = (T)cMpq64[t][0];
-  vtx[1] = wrapi(e + 1, n); wgt[1] = (T)cMpq64[t][1];
+  vtx[0] = e;               wgt[0] = wq(cMpq64[t][0]);
+  vtx[1] = wrapi(e + 1, n); wgt[1] = wq(cMpq64[t][1]);
   return 2;
 }
 
-// b = 4 pi (Mpq (x) Mpq (x) Mpq) r, accumulated in the vertex density's type;
-// grid (ceil(N / 128), N, N)
+// b = 4 pi (Mpq (x) Mpq (x) Mpq) r, accumulated in the vertex density's type
+// (FP32: integer weights, mpq_row); grid (ceil(N / 128), N, N)
 template <class T>
 __global__ void k_load_vector(int n, const T* __restrict__ rv, double* __restrict__ b) {
   const int N = 3 * n;
@@ -173,7 +179,8 @@ __global__ void k_load_vector(int n, const T* __restrict__ rv, double* __restric
       const int64_t row = (int64_t)n * (vy[bb] + (int64_t)n * vz[c]);
       for (int a = 0; a < nx; ++a) acc += wx[a] * wyz * rv[vx[a] + row];
     }
-  b[ix + (int64_t)N * (iy + (int64_t)N * iz)] = 4.0 * M_PI * (double)acc;
+  const double scale = sizeof(T) == 4 ? 4.0 * M_PI / (120.0 * 120.0 * 120.0) : 4.0 * M_PI;
+  b[ix + (int64_t)N * (iy + (int64_t)N * iz)] = scale * (double)acc;
 }
 
 // Coarsest-level exact solve x = V (Dinv o (V^T b)) (V the 1-D generalized
@@ -1037,9 +1044,9 @@ __global__ void __launch_bounds__(256) k_fdm_axis(int N, const float* __restrict
 }
 
 // The same pass on the tensor cores, as a general row GEMM with the output
-// transposed: out[(i - c0) R + r] = s(r, i) sum_{a < K} in[r K + a] B[i][a]
-// for R rows r and columns i in [c0, min(NC, c0 + gridDim.y nt)), c0 =
-// tile0 nt.  Per CTA 128 rows and the nt columns of one column tile; the
+// transposed: out[(i - cb) R + r] = s(r, i) sum_{a < K} in[r K + a] B[i][a]
+// for R rows r and columns cb <= i < ce (the column tiles of nt from the one
+// holding cb).  Per CTA 128 rows and the nt columns of one column tile; the
 // contraction in chunks of 64 as tcgen05 bf16 MMAs (M = 128, N = nt) on
 // three-piece splits of both operands (six piece products, two TMEM
 // accumulators: the leading product, the other five).  A (the input rows) is
@@ -1055,7 +1062,7 @@ __global__ void __launch_bounds__(256) k_fdm_axis(int N, const float* __restrict
 constexpr int FT_THREADS = 256;
 
 template <bool SCALE>
-__global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int NC, int nt, int tile0,
+__global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int cb, int ce, int nt,
                                                          const float* __restrict__ in, const uint4* __restrict__ Bp,
                                                          const float* __restrict__ lam, int null_mode, int N,
                                                          float* __restrict__ out, int* __restrict__ err) {
@@ -1069,7 +1076,7 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int NC
   uint32_t* tslot = (uint32_t*)(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t r0 = (int64_t)blockIdx.x * 128;
-  const int tile = tile0 + (int)blockIdx.y, c0 = tile0 * nt, n0 = tile * nt;
+  const int tile = cb / nt + (int)blockIdx.y, n0 = tile * nt;
   const int kc = (K + 63) / 64;
   uint32_t ncols = 32;
   while (ncols < 2u * (uint32_t)nt) ncols <<= 1;
@@ -1172,10 +1179,10 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int NC
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
           const int i = n0 + 16 * grp + t;
-          if (i >= NC || 16 * grp + t >= nt) continue;
+          if (i < cb || i >= ce || 16 * grp + t >= nt) continue;
           float v = __uint_as_float(vh[t]) + __uint_as_float(vl[t]);
           if (SCALE) v = (jk_null && i == null_mode) ? 0.f : v * __frcp_rn(lam[i] + djk);
-          out[(int64_t)(i - c0) * R + r] = v;
+          out[(int64_t)(i - cb) * R + r] = v;
         }
       }
     }
@@ -1428,11 +1435,11 @@ cudaError_t tc_rows_prepare(int nt) {
   return e;
 }
 
-// out[(i - tile0 nt) R + r] = sum_{a < K} in[r K + a] B[i][a] for the column tiles tile0 .. tile0 + ntiles - 1
-cudaError_t tc_rows_gemm(int64_t R, int K, int NC, int nt, int tile0, int ntiles, const float* in, const void* Bp,
-                         float* out, int* err, cudaStream_t s) {
-  const dim3 g((unsigned)((R + 127) / 128), (unsigned)ntiles);
-  FEP3M_CL k_tc_rows<false><<<g, FT_THREADS, tc_rows_smem(nt), s>>>(R, K, NC, nt, tile0, in, (const uint4*)Bp,
+// out[(i - cb) R + r] = sum_{a < K} in[r K + a] B[i][a] for the columns cb <= i < ce
+cudaError_t tc_rows_gemm(int64_t R, int K, int cb, int ce, int nt, const float* in, const void* Bp, float* out,
+                         int* err, cudaStream_t s) {
+  const dim3 g((unsigned)((R + 127) / 128), (unsigned)((ce + nt - 1) / nt - cb / nt));
+  FEP3M_CL k_tc_rows<false><<<g, FT_THREADS, tc_rows_smem(nt), s>>>(R, K, cb, ce, nt, in, (const uint4*)Bp,
                                                                     nullptr, -1, 0, out, err);
   return cudaGetLastError();
 }
@@ -1591,12 +1598,12 @@ struct MG {
       const int64_t R = (int64_t)N * N;
       const float* lm = f.lam32;
       const int nm = f.null_mode, nt = f.nt;
-      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, N, nt, 0, b, F, lm, nm, N, w1, f.err);
-      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, N, nt, 0, (const T*)w1, F, lm, nm, N, w2, f.err);
-      launch_pdl(k_tc_rows<true>, g, FT_THREADS, sm, s, R, N, N, nt, 0, (const T*)w2, F, lm, nm, N, w1, f.err);
-      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, N, nt, 0, (const T*)w1, I, lm, nm, N, w2, f.err);
-      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, N, nt, 0, (const T*)w2, I, lm, nm, N, w1, f.err);
-      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, N, nt, 0, (const T*)w1, I, lm, nm, N, x, f.err);
+      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, 0, N, nt, b, F, lm, nm, N, w1, f.err);
+      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const T*)w1, F, lm, nm, N, w2, f.err);
+      launch_pdl(k_tc_rows<true>, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const T*)w2, F, lm, nm, N, w1, f.err);
+      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const T*)w1, I, lm, nm, N, w2, f.err);
+      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const T*)w2, I, lm, nm, N, w1, f.err);
+      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const T*)w1, I, lm, nm, N, x, f.err);
       return;
     }
     const dim3 g((unsigned)(((int64_t)N * N + FM - 1) / FM), (unsigned)((N + FN - 1) / FN));
@@ -2102,7 +2109,8 @@ static void destroy_plan(Solver* c) {
 static cudaError_t build_plan(Solver* c) {
   destroy_plan(c);
   cudaStream_t user = c->stream;
-  const unsigned long long l0 = g_kernel_launches;
+  const bool unc = t_uncounted;
+  t_uncounted = true;   // captured launches run (and count) when the graph is replayed
   c->stream = c->cap_stream;
   cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
@@ -2126,7 +2134,7 @@ static cudaError_t build_plan(Solver* c) {
     }
   }
   c->stream = user;
-  g_kernel_launches = l0;   // captured launches run when the graph is replayed
+  t_uncounted = unc;
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     destroy_plan(c);
@@ -2159,7 +2167,7 @@ cudaError_t mesh_solve_begin(Solver* c, const double* b, double* phi) {
   cudaStream_t s = c->stream;
   cudaMemcpyAsync(c->in64, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if ((e = cudaGraphLaunch(c->solve_exec, s)) != cudaSuccess) return e;
-  g_kernel_launches += c->solve_graph_kernels;
+  count_launches((unsigned long long)c->solve_graph_kernels);
   cudaMemcpyAsync(phi, c->out64, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(c->host_res, c->scal + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
   c->pending = true;

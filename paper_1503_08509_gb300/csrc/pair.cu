@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 #include "tc.cuh"
@@ -200,13 +201,16 @@ constexpr int STAGE_CAP = 1536;   // halo charges staged in shared memory (T = f
 template <class T, bool TC = false>
 struct Pair3Smem {
   static constexpr int NT = TC ? PTC : PT;
+  // bytes per R and chunk-operand entry: one float (tensor cores) or a hi + lo
+  // float pair (the double-float CUDA-core contraction, both precisions)
+  static constexpr int ES = TC ? 4 : 8;
   __host__ __device__ static int SW(int n_sr) { return 3 * BX + 2 * n_sr - 1; }
   __host__ __device__ static int HW(int n_sr) { return BX + 2 * n_sr; }
   // charges that can be staged: STAGE_CAP floats-worth of float4 (half as many double4)
   __host__ __device__ static int cap() { return STAGE_CAP * 4 / (int)sizeof(T); }
   __host__ __device__ static size_t rbytes(int n_sr) {
     const int sw = SW(n_sr);
-    return (((size_t)sw * sw * sw * sizeof(T)) + 31) / 32 * 32;
+    return (((size_t)sw * sw * sw * ES) + 31) / 32 * 32;
   }
   __host__ __device__ static size_t region1(int n_sr) {
     const size_t r = rbytes(n_sr);
@@ -222,7 +226,7 @@ struct Pair3Smem {
   static constexpr size_t TILES = 6 * 8192;   // three bf16 pieces of A (64 x 64) and of B (64 x 64)
   static size_t bytes(int n_sr) {
     if (TC) return 1024 + TILES + rbytes(n_sr) + ints(n_sr) * sizeof(int) + 16;
-    return region1(n_sr) + 2 * (size_t)OCH * 64 * sizeof(T) + ints(n_sr) * sizeof(int) + (size_t)cap();
+    return region1(n_sr) + 2 * (size_t)OCH * 64 * ES + ints(n_sr) * sizeof(int) + (size_t)cap();
   }
 };
 
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
                                                              const int* __restrict__ count,
                                                              const typename vec4<T>::type* __restrict__ part,
                                                              const T* __restrict__ Cv, const T* __restrict__ rv,
-                                                             const T* __restrict__ Hw, const uint4* __restrict__ Hb,
+                                                             const uint4* __restrict__ Hb, const float2* __restrict__ H0,
                                                              const float2* __restrict__ Hdf, T* __restrict__ Gscr, double* __restrict__ phi_s,
                                                              double* __restrict__ E_s, double* __restrict__ psi,
                                                              double* __restrict__ gpsi, int* __restrict__ err) {
@@ -295,9 +299,9 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
     const size_t r1 = SM::region1(n_sr);
     R = (T*)smem_raw;                                     // region 1: R, later the staged charges
     stg = (V4*)smem_raw;
-    A_c = (T*)(smem_raw + r1);                            // [OCH][64] chunks of A and H
-    H_c = A_c + OCH * 64;
-    hs = (int*)(H_c + OCH * 64);
+    A_c = (T*)(smem_raw + r1);                            // [OCH][64] chunks of A and H (float pairs)
+    H_c = (T*)((unsigned char*)A_c + OCH * 64 * SM::ES);
+    hs = (int*)((unsigned char*)H_c + OCH * 64 * SM::ES);
   }
   int* epre = hs + HW * HW * HW + 1;                      // BE + 1
   int* flag = epre + BE + 1;
@@ -369,9 +373,10 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
         if (((tx >> kx) & 1) && ((ty >> ky) & 1) && ((tz >> kz) & 1)) val += c8[k];
       }
     }
-    if constexpr (sizeof(T) == 8) {
-      // FP64: split once here into the hi + lo floats of the double-float
-      // contraction (each R value is read by several offsets)
+    if constexpr (!TC) {
+      // split once here into the hi + lo floats of the double-float
+      // contraction (each R value is read by several offsets; an FP32 value
+      // has lo = 0)
       const float vh = (float)val;
       reinterpret_cast<float2*>(R)[i] = make_float2(vh, (float)((double)val - (double)vh));
     } else {
@@ -387,8 +392,11 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
     // product of the leading pieces, lo: the other five).  The hi accumulator
     // holds one chunk at a time and is added into registers after each chunk,
     // so that no accumulation inside the tensor core spans more than 64 terms
-    // of the leading product.  M = 128: rows 64 .. 127 of each A operand read
-    // the next tile and their results are unused.
+    // of the leading product; the chunk sums are added with compensation.  In
+    // the FP32 path the table is relative to each element's corners (see
+    // pair_relative_table), so these sums carry no large smooth part.  M = 128:
+    // rows 64 .. 127 of each A operand read the next tile and their results
+    // are unused.
     const uint32_t tl = smem_u32(tiles);
     if (tid < 32) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tslot)));
@@ -399,15 +407,36 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
     __syncthreads();   // R complete; TMEM address and barrier visible
     tc_fence_after();
     const uint32_t tmem = *tslot;
+    // The field at node 0 (the one absolute column of the relative table, the
+    // element's potential level), in double-float arithmetic on the CUDA cores
+    // from the table's hi + lo floats (H0): its FP32 tensor-core sum would be
+    // rounded alike in every element.  Eight threads per element, combined in
+    // the epilogue.
+    __shared__ float2 s0p[(PTC / 64) * BE];
+    {
+      const int l0 = tid & 63, g0 = tid >> 6;
+      const int lam0 = (l0 % BX) + SW * (((l0 / BX) % BY) + SW * (l0 / (BX * BY)));
+      float sh = 0.f, sl = 0.f;
+      for (int o = g0; o < no3; o += NT / 64) {
+        const float a = (float)R[otab[o] + lam0];
+        const float2 hh = H0[o];
+        const float p = a * hh.x;
+        const float e = fmaf(a, hh.y, fmaf(a, hh.x, -p));
+        const float t = sh + p, z = t - sh;
+        sl += ((sh - (t - z)) + (p - z)) + e;
+        sh = t;
+      }
+      s0p[g0 * BE + l0] = make_float2(sh, sl);
+    }
     const int l = tid & 63, g = tid >> 6;   // this thread's A unit: row l, chunk offsets 8 g .. 8 g + 7
     const int lam = (l % BX) + SW * (((l / BX) % BY) + SW * (l / (BX * BY)));
     const uint32_t aoff = sw128_off(l, 8 * g);
     const int nch = (no3 + 63) / 64;
     const int warp = tid >> 5, q4 = warp & 3, cg = warp >> 2;   // TMEM lanes 32 q4 .., columns 16 cg ..
     const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 16 * cg;
-    float hsum[16];   // rows 32 q4 + lane, columns 16 cg .. (warps with q4 < 2)
+    float hsum[16], hcmp[16];   // rows 32 q4 + lane, columns 16 cg .. (warps with q4 < 2): compensated chunk sums
 #pragma unroll
-    for (int j = 0; j < 16; ++j) hsum[j] = 0.f;
+    for (int j = 0; j < 16; ++j) hsum[j] = hcmp[j] = 0.f;
     bool failed = false;
     for (int c = 0; c < nch; ++c) {
       for (int i = tid; i < 1536; i += NT) cp_async16(tl + 24576 + 16 * i, Hb + (size_t)c * 1536 + i);
@@ -452,7 +481,11 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
         tmem_ld16(ta, vh);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) hsum[j] += __uint_as_float(vh[j]);
+        for (int j = 0; j < 16; ++j) {
+          const float y = __uint_as_float(vh[j]) - hcmp[j], t = hsum[j] + y;
+          hcmp[j] = (t - hsum[j]) - y;
+          hsum[j] = t;
+        }
       }
       tc_fence_before();   // the next chunk's MMAs overwrite hi after the next barrier
     }
@@ -467,13 +500,27 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
       uint32_t vl[16];
       tmem_ld16(ta + 64, vl);
       tmem_wait_ld();
-      float* drow = (float*)Gscr + (int64_t)blockIdx.x * (BE * 64) + (32 * q4 + (tid & 31)) * 64 + 16 * cg;
+      const int row = 32 * q4 + (tid & 31);
+      float* drow = (float*)Gscr + (int64_t)blockIdx.x * (BE * 64) + row * 64 + 16 * cg;
+      float c0 = (hsum[0] - hcmp[0]) + __uint_as_float(vl[0]);
+      if (cg == 0) {   // column 0 from the double-float sums
+        float sh = 0.f, sl = 0.f;
+#pragma unroll
+        for (int q = 0; q < PTC / 64; ++q) {
+          const float2 v = s0p[q * BE + row];
+          const float t = sh + v.x, z = t - sh;
+          sl += ((sh - (t - z)) + (v.x - z)) + v.y;
+          sh = t;
+        }
+        c0 = (float)((double)sh + (double)sl);
+      }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        reinterpret_cast<float4*>(drow)[i] = make_float4(hsum[4 * i] + __uint_as_float(vl[4 * i]),
-                                                         hsum[4 * i + 1] + __uint_as_float(vl[4 * i + 1]),
-                                                         hsum[4 * i + 2] + __uint_as_float(vl[4 * i + 2]),
-                                                         hsum[4 * i + 3] + __uint_as_float(vl[4 * i + 3]));
+        reinterpret_cast<float4*>(drow)[i] =
+            make_float4(i == 0 ? c0 : (hsum[4 * i] - hcmp[4 * i]) + __uint_as_float(vl[4 * i]),
+                        (hsum[4 * i + 1] - hcmp[4 * i + 1]) + __uint_as_float(vl[4 * i + 1]),
+                        (hsum[4 * i + 2] - hcmp[4 * i + 2]) + __uint_as_float(vl[4 * i + 2]),
+                        (hsum[4 * i + 3] - hcmp[4 * i + 3]) + __uint_as_float(vl[4 * i + 3]));
     }
     tc_fence_before();
     __syncthreads();   // every TMEM read done; the tiles are free for the staged charges
@@ -481,20 +528,21 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
     if (failed) return;
   } else {
   // CUDA cores: 4 x 4 register tile, per-chunk partial sums added into a
-  // total.  FP64: the chunk sums run in double-float arithmetic on the FP32
-  // pipes (FP64 issues at a small fraction of the FP32 rate here): A and H are
-  // staged as hi + lo float pairs, each product keeps its exact leading part
-  // (fused two-product) and the two cross terms, and the products are summed
-  // by two-sum into a hi + lo accumulator; each chunk's sum goes into an FP64
-  // total, which keeps the relative error near 2^-48 of the chunk's sum of
-  // |A H| instead of growing over all offsets.
+  // total, in double-float arithmetic on the FP32 pipes in both precisions
+  // (FP64 issues at a small fraction of the FP32 rate here): A and H are
+  // staged as hi + lo float pairs (the table's from FP64; an FP32 A has lo =
+  // 0), each product keeps its exact leading part (fused two-product) and the
+  // two cross terms, and the products are summed by two-sum into a hi + lo
+  // accumulator; each chunk's sum goes into an FP64 total, which keeps the
+  // relative error near 2^-48 of the chunk's sum of |A H| instead of growing
+  // over all offsets.  The FP32 path's result is then rounded to FP32.
   const int eb = tid >> 4, mb = tid & 15;
   // this thread stages entries i = tid + k PT: element l = i & 63 is fixed per thread
   const int lst = tid & 63;
   const int lam = (lst % BX) + SW * (((lst / BX) % BY) + SW * (lst / (BX * BY)));
   constexpr int SPT = OCH * 64 / PT;   // staged entries per thread per chunk
   T* gb = Gscr + (int64_t)blockIdx.x * (BE * 64);
-  if constexpr (sizeof(T) == 8) {
+  {
     // the table's hi + lo floats come precomputed (Hdf); R was split in (1)
     float2 hpf[SPT];                   // next chunk's table values, fetched during this chunk
 #pragma unroll
@@ -560,71 +608,10 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       V4 v;
-      v.x = tot[i][0];
-      v.y = tot[i][1];
-      v.z = tot[i][2];
-      v.w = tot[i][3];
-      *reinterpret_cast<V4*>(gb + (4 * eb + i) * 64 + 4 * mb) = v;
-    }
-  } else {
-    T hpf[SPT];                        // next chunk's table values, fetched during this chunk
-#pragma unroll
-    for (int k = 0; k < SPT; ++k) {
-      const int i = tid + k * PT, o = i >> 6;
-      hpf[k] = o < no3 ? Hw[(int64_t)o * 64 + (i & 63)] : T(0);
-    }
-    T acc[4][4], tot[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) tot[i][j] = T(0);
-    for (int o0 = 0; o0 < no3; o0 += OCH) {
-      __syncthreads();
-#pragma unroll
-      for (int k = 0; k < SPT; ++k) {
-        const int i = tid + k * PT;
-        const int o = o0 + (i >> 6);
-        H_c[i] = hpf[k];
-        A_c[i] = o < no3 ? R[otab[o] + lam] : T(0);
-      }
-      __syncthreads();
-      if (o0 + OCH < no3) {
-#pragma unroll
-        for (int k = 0; k < SPT; ++k) {
-          const int i = tid + k * PT, o = o0 + OCH + (i >> 6);
-          hpf[k] = o < no3 ? Hw[(int64_t)o * 64 + (i & 63)] : T(0);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-#pragma unroll 4
-      for (int oi = 0; oi < OCH; ++oi) {
-        // one vector load each (16 lanes share the A row: a broadcast; the H
-        // rows of the 16 mb are contiguous: conflict-free)
-        const V4 av = *reinterpret_cast<const V4*>(A_c + oi * 64 + 4 * eb);
-        const V4 hv = *reinterpret_cast<const V4*>(H_c + oi * 64 + 4 * mb);
-        const T a[4] = {av.x, av.y, av.z, av.w}, hh[4] = {hv.x, hv.y, hv.z, hv.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * hh[j];
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j];
-    }
-    // the brick's screen fields: row l of the brick (64 nodes) per element, one
-    // vector store per (i); the 16 mb of a row are contiguous
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      V4 v;
-      v.x = tot[i][0];
-      v.y = tot[i][1];
-      v.z = tot[i][2];
-      v.w = tot[i][3];
+      v.x = (T)tot[i][0];
+      v.y = (T)tot[i][1];
+      v.z = (T)tot[i][2];
+      v.w = (T)tot[i][3];
       *reinterpret_cast<V4*>(gb + (4 * eb + i) * 64 + 4 * mb) = v;
     }
   }
@@ -792,15 +779,24 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
 }
 
 // One CTA per brick, after the mesh solve: G = mesh potential - screen field
-// at the 64 nodes of each non-empty brick element, held in T in shared memory
-// relative to its value G0 at the element's first node (FP64): the shape
-// functions sum to one and their gradients to zero, so G0 enters the
-// potential alone and the rounding to T acts on the variation of G only.  The
-// FP32 path reads the mesh potential as a hi + lo pair of floats (phi_hl) and
-// forms the variation in FP32; the FP64 path reads it in FP64 (phi64).  Then
-// four threads per target charge each contract 16 of the nodes with the
-// order-3 shape functions (and their derivatives) at the charge, and the mesh
-// part is added to the singular part the screen kernel left in phi_s / E_s.
+// at the 64 nodes of each non-empty brick element, then four threads per
+// target charge each contract 16 of the nodes with the order-3 shape
+// functions (and their derivatives) at the charge; the mesh part is added to
+// the singular part the screen kernel left in phi_s / E_s.
+//
+// FP64 path: G is held in shared memory relative to its value G0 at the
+// element's first node (kept in FP64): the shape functions sum to one and
+// their gradients to zero, so G0 enters the potential alone and the rounding
+// acts on the variation of G only.
+//
+// FP32 path: the screen field arrives relative to the element's corners (the
+// field at node 0, corner fields relative to it, elsewhere the field less its
+// trilinear interpolant; pair_relative_table), and G is split the same way:
+// G0 and the corner values of G - G0 in FP64 (mesh potential read in FP64),
+// and the remainder G - G0 - trilinear(corners) in FP32 (the mesh potential as
+// a hi + lo pair of floats).  The trilinear part and its gradient at the
+// charge are evaluated in FP64; only the small remainder goes through the FP32
+// contraction.
 template <class T, bool GRAD>
 __global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __restrict__ start,
                                                   const int* __restrict__ count,
@@ -810,8 +806,10 @@ __global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __r
                                                   const int* __restrict__ perm, double* __restrict__ phi_s,
                                                   double* __restrict__ E_s, double* __restrict__ phi_out) {
   typedef typename vec4<T>::type V4;
+  constexpr bool F32 = sizeof(T) == 4;
   __shared__ __align__(32) T G[BE * 64];
   __shared__ double G0[BE];
+  __shared__ double Gc[F32 ? BE * 8 : 1];   // FP32 path: corner values of G - G0
   __shared__ int epre[BE + 1];
   __shared__ int wsum[PT / 32 + 1];
   const int nbx = (n + BX - 1) / BX, nby = (n + BY - 1) / BY;
@@ -838,22 +836,53 @@ __global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __r
     const int gx = 3 * ex + (m & 3), gy = 3 * ey + ((m >> 2) & 3), gz = 3 * ez + (m >> 4);   // < 3n + 3
     return (gx >= N ? gx - N : gx) + (int64_t)N * ((gy >= N ? gy - N : gy) + (int64_t)N * (gz >= N ? gz - N : gz));
   };
-  if (tid < BE && epre[tid + 1] != epre[tid]) {
-    if constexpr (sizeof(T) == 4) {
-      const float2 p0 = phi_hl[node(tid, 0)];
-      G0[tid] = ((double)p0.x + (double)p0.y) - (double)gb[tid * 64];
-    } else {
-      G0[tid] = phi64[node(tid, 0)] - gb[tid * 64];
+  if constexpr (F32) {
+    if (tid < BE && epre[tid + 1] != epre[tid]) {
+      const double p00 = phi64[node(tid, 0)];
+      G0[tid] = p00 - (double)gb[tid * 64];
+      Gc[tid * 8] = 0.0;
+#pragma unroll
+      for (int c = 1; c < 8; ++c) {
+        const int mc = 3 * (c & 1) + 12 * ((c >> 1) & 1) + 48 * (c >> 2);
+        Gc[tid * 8 + c] = (phi64[node(tid, mc)] - p00) - (double)gb[tid * 64 + mc];
+      }
     }
-  }
-  __syncthreads();
-  for (int i = tid; i < BE * 64; i += PT) {
-    const int l = i >> 6, m = i & 63;
-    if (epre[l + 1] == epre[l]) continue;   // empty (or outside the mesh): never read
-    if constexpr (sizeof(T) == 4) {
+    // node differences of the mesh potential from its hi + lo floats
+    for (int i = tid; i < BE * 64; i += PT) {
+      const int l = i >> 6, m = i & 63;
+      if (epre[l + 1] == epre[l]) continue;   // empty (or outside the mesh): never read
       const float2 p = phi_hl[node(l, m)], p0 = phi_hl[node(l, 0)];
-      G[i] = ((p.x - p0.x) + (p.y - p0.y)) - (gb[i] - gb[l * 64]);
-    } else {
+      G[i] = (p.x - p0.x) + (p.y - p0.y);
+    }
+    __syncthreads();
+    // remainder: the difference less its trilinear interpolant, less the screen
+    // remainder; zero at the corners
+    constexpr int PER = BE * 64 / PT;
+    float rem[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = tid + k * PT, l = i >> 6, m = i & 63;
+      const int mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
+      rem[k] = 0.f;
+      if (epre[l + 1] == epre[l]) continue;
+      if ((mx == 0 || mx == 3) && (my == 0 || my == 3) && (mz == 0 || mz == 3)) continue;
+      const float* g = G + l * 64;
+      const float tx = mx * (1.f / 3.f), ty = my * (1.f / 3.f), tz = mz * (1.f / 3.f);
+      // corners (0,0,0) 0, (3,0,0) 3, (0,3,0) 12, (3,3,0) 15, z + 48
+      const float x00 = fmaf(tx, g[3] - g[0], g[0]), x10 = fmaf(tx, g[15] - g[12], g[12]);
+      const float x01 = fmaf(tx, g[51] - g[48], g[48]), x11 = fmaf(tx, g[63] - g[60], g[60]);
+      const float y0 = fmaf(ty, x10 - x00, x00), y1 = fmaf(ty, x11 - x01, x01);
+      rem[k] = (g[m] - fmaf(tz, y1 - y0, y0)) - gb[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) G[tid + k * PT] = rem[k];
+  } else {
+    if (tid < BE && epre[tid + 1] != epre[tid]) G0[tid] = phi64[node(tid, 0)] - gb[tid * 64];
+    __syncthreads();
+    for (int i = tid; i < BE * 64; i += PT) {
+      const int l = i >> 6, m = i & 63;
+      if (epre[l + 1] == epre[l]) continue;   // empty (or outside the mesh): never read
       G[i] = (phi64[node(l, m)] - gb[i]) - G0[l];
     }
   }
@@ -864,6 +893,8 @@ __global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __r
     const bool valid = k < ntarget;
     T v4[4] = {T(0), T(0), T(0), T(0)};
     int slot = 0, l = 0;
+    V4 pt;
+    pt.x = pt.y = pt.z = pt.w = T(0);
     if (valid) {
       int lo = 0, hi2 = BE;
       while (hi2 - lo > 1) {
@@ -874,7 +905,7 @@ __global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __r
       l = lo;
       const int ex = E0x + l % BX, ey = E0y + (l / BX) % BY, ez = E0z + l / (BX * BY);
       slot = start[ex + (int64_t)n * (ey + (int64_t)n * ez)] + (k - epre[l]);
-      const V4 pt = part[slot];
+      pt = part[slot];
       T ux[4], uy[4], uz[4], dx4[4], dy4[4], dz4[4];
       q3_values<T>(pt.x, ux);
       q3_values<T>(pt.y, uy);
@@ -907,14 +938,33 @@ __global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __r
       v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], 2);
     }
     if (valid && q == 0) {
-      const double phi = ((double)v4[0] + G0[l]) * (double)inv_h + phi_s[slot];
+      // FP32 path: the trilinear part of G - G0 and its gradient at the charge, in FP64
+      double tv = 0.0, tg[3] = {0.0, 0.0, 0.0};
+      if constexpr (F32) {
+        const double* g = Gc + l * 8;
+        const double x = pt.x, y = pt.y, z = pt.z;
+        double a[4], b[4];   // x-lerps and x-differences of the corner pairs j = cy + 2 cz
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          b[j] = g[2 * j + 1] - g[2 * j];
+          a[j] = fma(x, b[j], g[2 * j]);
+        }
+        const double ay0 = a[1] - a[0], ay1 = a[3] - a[2];
+        const double a0 = fma(y, ay0, a[0]), a1 = fma(y, ay1, a[2]);
+        const double bx0 = fma(y, b[1] - b[0], b[0]), bx1 = fma(y, b[3] - b[2], b[2]);
+        tv = fma(z, a1 - a0, a0);
+        tg[0] = fma(z, bx1 - bx0, bx0);
+        tg[1] = fma(z, ay1 - ay0, ay0);
+        tg[2] = a1 - a0;
+      }
+      const double phi = (((double)v4[0] + tv) + G0[l]) * (double)inv_h + phi_s[slot];
       phi_s[slot] = phi;
       if (phi_out) phi_out[perm[slot]] = phi;
       if (GRAD) {
         const double ih2 = (double)inv_h * (double)inv_h;
-        E_s[3 * slot + 0] = (double)v4[1] * ih2 + E_s[3 * slot + 0];
-        E_s[3 * slot + 1] = (double)v4[2] * ih2 + E_s[3 * slot + 1];
-        E_s[3 * slot + 2] = (double)v4[3] * ih2 + E_s[3 * slot + 2];
+        E_s[3 * slot + 0] = ((double)v4[1] + tg[0]) * ih2 + E_s[3 * slot + 0];
+        E_s[3 * slot + 1] = ((double)v4[2] + tg[1]) * ih2 + E_s[3 * slot + 1];
+        E_s[3 * slot + 2] = ((double)v4[3] + tg[2]) * ih2 + E_s[3 * slot + 2];
       }
     }
   }
@@ -935,16 +985,19 @@ __global__ void k_charges(int64_t N, const typename vec4<T>::type* __restrict__ 
   Qs[k] = (double)part[k].w;
 }
 
-// W[e][m] = sum_{t in e} w_t u_m(tau_t): the adjoint's point deposit, per element
+// W[e][m] = sum_{t in e} w_t u_m(tau_t): the adjoint's point deposit, per
+// element.  wsum (FP32 path): sum_{t in e} w_t in FP64 as hi + lo floats, the
+// exact sum over m of W[e][m] (the shape functions sum to one).
 template <class T>
 __global__ void k_elem_deposit(int64_t ne, const int* __restrict__ start, const int* __restrict__ count,
                                const typename vec4<T>::type* __restrict__ part, const double* __restrict__ w,
-                               T* __restrict__ W) {
+                               T* __restrict__ W, float2* __restrict__ wsum) {
   const int64_t e = blockIdx.x * (int64_t)(blockDim.x / 64) + threadIdx.x / 64;
   if (e >= ne) return;
   const int m = threadIdx.x & 63, mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
   const int s = start[e], cnt = count[e];
   T acc = T(0);
+  double ws = 0.0;
   for (int j = s; j < s + cnt; ++j) {
     const typename vec4<T>::type p = part[j];
     T ux[4], uy[4], uz[4];
@@ -952,8 +1005,13 @@ __global__ void k_elem_deposit(int64_t ne, const int* __restrict__ start, const 
     q3_values<T>(p.y, uy);
     q3_values<T>(p.z, uz);
     acc += (T)w[j] * ux[mx] * uy[my] * uz[mz];
+    if (m == 0) ws += w[j];
   }
   W[e * 64 + m] = acc;
+  if (wsum && m == 0) {
+    const float hi = (float)ws;
+    wsum[e] = make_float2(hi, (float)(ws - (double)hi));
+  }
 }
 
 // g[node] = sum over (element, local node) pairs at the node of W
@@ -989,94 +1047,73 @@ __global__ void k_node_assemble(int n, const T* __restrict__ W, double* __restri
 // Screen part of the adjoint, as a GEMM and a gather (deterministic, no atomics):
 //   D[o][e] = sum_m W[e][m] H(o, m)               (every element e, every vertex offset o)
 //   A[s][k] = sum_{o : o + k in block} D[o][s + k + o]
-// D[o][e] is the table field of element e's deposit seen from the vertex e - o.
+// D[o][e] is the table field of element e's deposit seen from the vertex e - o
+// (k_adj_gemm on the CUDA cores, the tensor-core row GEMM in the FP32 path;
+// the gather is k_adj_vertex).
 constexpr int GT = 64;   // GEMM tile: 64 elements x 64 offsets, K = 64 nodes
 constexpr int ADJ_NT = 128;   // tensor-core column tile: offsets per tile
 
-// FP64: the products are summed in double-float arithmetic on the FP32 pipes,
-// as in the screen contraction (hi + lo float pairs in shared memory, fused
-// two-product with the cross terms, two-sum accumulation), in two halves of
-// 32 nodes whose sums are added in FP64.
+// The products are summed in double-float arithmetic on the FP32 pipes in both
+// precisions, as in the screen contraction (hi + lo float pairs in shared
+// memory: the table's from FP64, an FP32 deposit has lo = 0; fused two-product
+// with the cross terms, two-sum accumulation), in two halves of 32 nodes whose
+// sums are added in FP64; D is stored in T.
 template <class T>
 __global__ void __launch_bounds__(PT) k_adj_gemm(int64_t ne, int o0, int no, const T* __restrict__ W,
-                                                 const T* __restrict__ Hw, T* __restrict__ D) {
-  __shared__ T Ws[64][GT + 1];   // [m][element]
-  __shared__ T Hs[64][GT + 1];   // [m][offset]
-  constexpr bool DF = sizeof(T) == 8;
-  float2(*Ws2)[GT + 1] = reinterpret_cast<float2(*)[GT + 1]>(Ws);
-  float2(*Hs2)[GT + 1] = reinterpret_cast<float2(*)[GT + 1]>(Hs);
+                                                 const double* __restrict__ Hw, T* __restrict__ D) {
+  __shared__ float2 Ws2[64][GT + 1];   // [m][element]
+  __shared__ float2 Hs2[64][GT + 1];   // [m][offset]
   const int64_t e0 = (int64_t)blockIdx.x * GT;
   const int oo0 = o0 + blockIdx.y * GT;
   for (int i = threadIdx.x; i < GT * 64; i += PT) {
     const int r = i >> 6, m = i & 63;
     const int64_t e = e0 + r;
     const int o = oo0 + r;
-    const T w = e < ne ? W[e * 64 + m] : T(0);
-    const T hv = (o < o0 + no) ? Hw[(int64_t)o * 64 + m] : T(0);
-    if constexpr (DF) {
-      const float wh = (float)w, hh = (float)hv;
-      Ws2[m][r] = make_float2(wh, (float)((double)w - (double)wh));
-      Hs2[m][r] = make_float2(hh, (float)((double)hv - (double)hh));
-    } else {
-      Ws[m][r] = w;
-      Hs[m][r] = hv;
-    }
+    const double w = e < ne ? (double)W[e * 64 + m] : 0.0;
+    const double hv = (o < o0 + no) ? Hw[(int64_t)o * 64 + m] : 0.0;
+    const float wh = (float)w, hh = (float)hv;
+    Ws2[m][r] = make_float2(wh, (float)(w - (double)wh));
+    Hs2[m][r] = make_float2(hh, (float)(hv - (double)hh));
   }
   __syncthreads();
   const int te = threadIdx.x & 15, to = threadIdx.x >> 4;   // 4 elements x 4 offsets per thread
-  T acc[4][4];
+  double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-  if constexpr (DF) {
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 #pragma unroll 1
-    for (int half = 0; half < 2; ++half) {
-      float sh[4][4], sl[4][4];
+  for (int half = 0; half < 2; ++half) {
+    float sh[4][4], sl[4][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
+      for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
 #pragma unroll 4
-      for (int m = 32 * half; m < 32 * half + 32; ++m) {
-        float2 a[4], b[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          a[i] = Ws2[m][te + 16 * i];
-          b[i] = Hs2[m][to + 16 * i];
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float p = a[i].x * b[j].x;
-            float e = fmaf(a[i].x, b[j].x, -p);
-            e = fmaf(a[i].x, b[j].y, e);
-            e = fmaf(a[i].y, b[j].x, e);
-            const float t = sh[i][j] + p, z = t - sh[i][j];
-            sl[i][j] += ((sh[i][j] - (t - z)) + (p - z)) + e;
-            sh[i][j] = t;
-          }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += (double)sh[i][j] + (double)sl[i][j];
-    }
-  } else {
-#pragma unroll 8
-    for (int m = 0; m < 64; ++m) {
-      T a[4], b[4];
+    for (int m = 32 * half; m < 32 * half + 32; ++m) {
+      float2 a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        a[i] = Ws[m][te + 16 * i];
-        b[i] = Hs[m][to + 16 * i];
+        a[i] = Ws2[m][te + 16 * i];
+        b[i] = Hs2[m][to + 16 * i];
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        for (int j = 0; j < 4; ++j) {
+          const float p = a[i].x * b[j].x;
+          float e = fmaf(a[i].x, b[j].x, -p);
+          e = fmaf(a[i].x, b[j].y, e);
+          e = fmaf(a[i].y, b[j].x, e);
+          const float t = sh[i][j] + p, z = t - sh[i][j];
+          sl[i][j] += ((sh[i][j] - (t - z)) + (p - z)) + e;
+          sh[i][j] = t;
+        }
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += (double)sh[i][j] + (double)sl[i][j];
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -1085,64 +1122,116 @@ __global__ void __launch_bounds__(PT) k_adj_gemm(int64_t ne, int o0, int no, con
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int64_t e = e0 + te + 16 * i;
-      if (e < ne) D[(int64_t)(o - o0) * ne + e] = acc[i][j];
+      if (e < ne) D[(int64_t)(o - o0) * ne + e] = (T)acc[i][j];
     }
   }
 }
 
-// A[s][k] (+)= sum over offsets o in [o0, o0 + no) with o + k inside the block of D[o][s + k + o].
-// Each value D[o][e] is read by eight (s, k), the elements s = e - o - k +
-// (n_sr + 1) of its corners k.  ALL8 = false (small meshes, where D stays in
-// L2): one thread per (s, k), a block being 32 consecutive s (the lanes of a
-// warp: coalesced rows of D) times the eight corners (its warps).  ALL8 =
-// true (large meshes): one thread per s for all eight corners, so the eight
-// readers of a value are neighbouring threads and the reads of D from DRAM
-// are not repeated.  Written as a loop over the block element u = k + o (each
-// axis in [-n_sr, n_sr], so o is always a stored offset), with the wrapped
-// element index advanced incrementally; per (s, k) the terms are added with
-// compensation, in increasing o (the same order in both mappings).
-template <class T, bool ALL8>
-__global__ void __launch_bounds__(256) k_adj_gather(int n, int n_sr, int o0, int no, int first,
-                                                    const int* __restrict__ count, const T* __restrict__ D,
-                                                    double* __restrict__ A) {
-  constexpr int NK = ALL8 ? 8 : 1;
+// Double-float accumulator (hi + lo floats, summed by two-sum): the FP32
+// path's screen adjoint sums, whose terms cancel to a small remainder.
+struct dfacc {
+  float h = 0.f, l = 0.f;
+};
+__device__ __forceinline__ void acc_add(dfacc& a, float b) {
+  const float s = a.h + b, bb = s - a.h;
+  a.l += (a.h - (s - bb)) + (b - bb);
+  a.h = s;
+}
+__device__ __forceinline__ void acc_merge(dfacc& a, const dfacc& b) {
+  const float s = a.h + b.h, bb = s - a.h;
+  a.l += ((a.h - (s - bb)) + (b.h - bb)) + b.l;
+  a.h = s;
+}
+__device__ __forceinline__ void acc_merge(double& a, double b) { a += b; }
+__device__ __forceinline__ double acc_value(const dfacc& a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ double acc_value(double a) { return a; }
+
+// Screen adjoint, gathered by vertex:
+//   A[s][k] = sum over the offsets o with o + k inside the block of D(o, s + k + o).
+// For the vertex v = s + k the terms are D(o, v + o) over the offsets that
+// corner k's block holds: along each axis, o_a = -(n_sr + 1) only for k_a = 1,
+// o_a = n_sr only for k_a = 0, the others for both.  One thread per vertex
+// reads D(o, v + o) once for each offset of a chunk of whole offset planes
+// (oz in [z0, z1); consecutive threads read consecutive elements) and sums the
+// terms into 27 classes (the three cases per axis); A(v - k, k) is the sum of
+// the eight classes that corner k admits.  Each (s, k) is written by one
+// thread, in a fixed order: deterministic.  FP32 path (H0 set): D holds the
+// contraction with the node-0-relative table, and each term gains
+// H(o, 0) Wsum(v + o) (pair_adjoint_table); terms and sums in double-float
+// arithmetic.  FP64 path: D is the whole contraction, summed in FP64.
+template <class T, int NSR>
+__global__ void __launch_bounds__(128) k_adj_vertex(int n, int z0, int z1, int first, const int* __restrict__ count,
+                                                   const T* __restrict__ D, const float2* __restrict__ H0,
+                                                   const float2* __restrict__ wsum, double* __restrict__ A) {
+  constexpr int KEEP = NSR + 1, NOFF = 2 * NSR + 2, PLANE = NOFF * NOFF;
+  constexpr bool DF = sizeof(T) == 4;
+  typedef typename std::conditional<DF, dfacc, double>::type Acc;
   const int64_t ne = (int64_t)n * n * n;
-  const int64_t s = ALL8 ? blockIdx.x * (int64_t)256 + threadIdx.x : blockIdx.x * (int64_t)32 + (threadIdx.x & 31);
-  const int k0 = ALL8 ? 0 : (int)(threadIdx.x >> 5);
-  if (s >= ne) return;
-  Acc<T> acc[NK];   // compensated: the block's terms cancel to a small remainder
-  if (count[s] != 0) {
-    const int keep = n_sr + 1, noff = 2 * n_sr + 2;
-    const int sx = (int)(s % n), sy = (int)((s / n) % n), sz = (int)(s / ((int64_t)n * n));
-    const int ex0 = wrapn(sx - n_sr, n);
-    for (int uz = -n_sr; uz <= n_sr; ++uz) {
-      const int64_t ez = wrapn(sz + uz, n);
-      for (int uy = -n_sr; uy <= n_sr; ++uy) {
-        const int64_t row = (int64_t)n * (wrapn(sy + uy, n) + (int64_t)n * ez);
-        int oyz[NK];   // o - o0 at ux = 0, per corner
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= ne) return;
+  const int vx = (int)(v % n), vy = (int)((v / n) % n), vz = (int)(v / ((int64_t)n * n));
+  bool any = false;   // the eight elements v - k; A is read only for non-empty ones
 #pragma unroll
-        for (int q = 0; q < NK; ++q) {
-          const int k = k0 + q;
-          oyz[q] = noff * ((uy - ((k >> 1) & 1) + keep) + noff * (uz - (k >> 2) + keep)) - (k & 1) + keep - o0;
-        }
-        int ex = ex0;
-        for (int ux = -n_sr; ux <= n_sr; ++ux) {
-          const int64_t e = row + ex;
+  for (int k = 0; k < 8; ++k)
+    any |= count[wrapn(vx - (k & 1), n) + (int64_t)n * (wrapn(vy - ((k >> 1) & 1), n) +
+                                                        (int64_t)n * wrapn(vz - (k >> 2), n))] != 0;
+  if (!any) return;
+  int wx[NOFF], wy[NOFF];
 #pragma unroll
-          for (int q = 0; q < NK; ++q) {
-            const int oi = oyz[q] + ux;
-            if ((unsigned)oi < (unsigned)no) acc[q].add(D[(int64_t)oi * ne + e]);
-          }
-          if (++ex == n) ex = 0;
+  for (int i = 0; i < NOFF; ++i) {
+    wx[i] = wrapn(vx + i - KEEP, n);
+    wy[i] = n * wrapn(vy + i - KEEP, n);
+  }
+  Acc cls[27] = {};
+  for (int oz = z0; oz < z1; ++oz) {
+    const int64_t zrow = (int64_t)n * n * wrapn(vz + oz - KEEP, n);
+    const T* Dp = D + (int64_t)(oz - z0) * PLANE * ne;
+    Acc P[9] = {};
+#pragma unroll
+    for (int oy = 0; oy < NOFF; ++oy) {
+      const int cy = oy == 0 ? 0 : (oy == NOFF - 1 ? 2 : 1);
+#pragma unroll
+      for (int ox = 0; ox < NOFF; ++ox) {
+        const int cx = ox == 0 ? 0 : (ox == NOFF - 1 ? 2 : 1);
+        const int64_t e = zrow + wy[oy] + wx[ox];
+        const T d = Dp[(int64_t)(oy * NOFF + ox) * ne + e];
+        if constexpr (DF) {
+          const float2 h = H0[oz * PLANE + oy * NOFF + ox], w = wsum[e];
+          const float p = h.x * w.x;
+          float r = fmaf(h.x, w.x, -p);
+          r = fmaf(h.x, w.y, r);
+          r = fmaf(h.y, w.x, r);
+          acc_add(P[cy * 3 + cx], p);
+          acc_add(P[cy * 3 + cx], d + r);
+        } else {
+          P[cy * 3 + cx] += d;
         }
       }
     }
+    if (oz == 0) {
+#pragma unroll
+      for (int j = 0; j < 9; ++j) acc_merge(cls[j], P[j]);
+    } else if (oz == NOFF - 1) {
+#pragma unroll
+      for (int j = 0; j < 9; ++j) acc_merge(cls[18 + j], P[j]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 9; ++j) acc_merge(cls[9 + j], P[j]);
+    }
   }
 #pragma unroll
-  for (int q = 0; q < NK; ++q) {
-    const int k = k0 + q;
-    const double prev = first ? 0.0 : A[s * 8 + k];
-    A[s * 8 + k] = prev + ((double)acc[q].s - (double)acc[q].c);
+  for (int k = 0; k < 8; ++k) {
+    const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
+    Acc s = {};
+#pragma unroll
+    for (int cz = kz ? 0 : 1; cz <= (kz ? 1 : 2); ++cz)
+#pragma unroll
+      for (int cy = ky ? 0 : 1; cy <= (ky ? 1 : 2); ++cy)
+#pragma unroll
+        for (int cx = kx ? 0 : 1; cx <= (kx ? 1 : 2); ++cx) acc_merge(s, cls[cz * 9 + cy * 3 + cx]);
+    const int64_t se = wrapn(vx - kx, n) + (int64_t)n * (wrapn(vy - ky, n) + (int64_t)n * wrapn(vz - kz, n));
+    double* dst = A + se * 8 + k;
+    *dst = first ? acc_value(s) : *dst + acc_value(s);
   }
 }
 
@@ -1310,14 +1399,15 @@ size_t pair_screen_bytes(const fep3m_ctx* c) {
 }
 
 template <class T, bool GRAD, bool TC>
-static cudaError_t launch_pair_screen(fep3m_ctx* c, const T* Hw, cudaStream_t s, bool half) {
+static cudaError_t launch_pair_screen(fep3m_ctx* c, cudaStream_t s, bool half) {
   const size_t smem = Pair3Smem<T, TC>::bytes(c->n_sr);
   auto kern = k_pair_screen<T, GRAD, TC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   FEP3M_CL kern<<<(unsigned)pair_bricks(c), TC ? PTC : PT, smem, s>>>(
       c->n, c->n_sr, (T)c->h, c->start, c->count, (const typename vec4<T>::type*)c->part, (const T*)c->Cv,
-      (const T*)c->rv, Hw, (const uint4*)c->Hb, (const float2*)c->Hdf, (T*)c->Gscr, c->phi_s, c->E_s, half ? c->psi_s : nullptr,
+      (const T*)c->rv, (const uint4*)c->Hb, (const float2*)c->H0df, (const float2*)c->Hdf, (T*)c->Gscr, c->phi_s, c->E_s,
+      half ? c->psi_s : nullptr,
       half ? c->gpsi_s : nullptr, c->iflags + 2);
   return cudaGetLastError();
 }
@@ -1334,13 +1424,71 @@ cudaError_t pair_screen(fep3m_ctx* c, int want_grad, cudaStream_t s, bool energy
   const bool half = energy_adjoint && want_grad;
   if (c->precision == FEP3M_MIXED) {
     if (c->Hb)
-      return want_grad ? launch_pair_screen<float, true, true>(c, c->Hw32, s, half)
-                       : launch_pair_screen<float, false, true>(c, c->Hw32, s, half);
-    return want_grad ? launch_pair_screen<float, true, false>(c, c->Hw32, s, half)
-                     : launch_pair_screen<float, false, false>(c, c->Hw32, s, half);
+      return want_grad ? launch_pair_screen<float, true, true>(c, s, half)
+                       : launch_pair_screen<float, false, true>(c, s, half);
+    return want_grad ? launch_pair_screen<float, true, false>(c, s, half)
+                     : launch_pair_screen<float, false, false>(c, s, half);
   }
-  return want_grad ? launch_pair_screen<double, true, false>(c, c->Hw64, s, half)
-                   : launch_pair_screen<double, false, false>(c, c->Hw64, s, half);
+  return want_grad ? launch_pair_screen<double, true, false>(c, s, half)
+                   : launch_pair_screen<double, false, false>(c, s, half);
+}
+
+// Corner structure of an element's 64 order-3 nodes (m = mx + 4 my + 16 mz):
+// corner c = cx + 2 cy + 4 cz sits at node 3 cx + 12 cy + 48 cz, and the
+// trilinear interpolant of the eight corner values has weight
+// prod_a (c_a ? m_a / 3 : 1 - m_a / 3) at node m.
+static int corner_node(int c) { return 3 * (c & 1) + 12 * ((c >> 1) & 1) + 48 * (c >> 2); }
+static bool is_corner_node(int m) {
+  const int mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
+  return (mx == 0 || mx == 3) && (my == 0 || my == 3) && (mz == 0 || mz == 3);
+}
+static double corner_weight(int c, int m) {
+  const int mm[3] = {m & 3, (m >> 2) & 3, m >> 4};
+  double w = 1.0;
+  for (int a = 0; a < 3; ++a) w *= ((c >> a) & 1) ? mm[a] / 3.0 : 1.0 - mm[a] / 3.0;
+  return w;
+}
+
+// The FP32 path's screen-field table, relative to each element's corners:
+// column 0 is H(o, 0); the other corner columns H(o, c) - H(o, 0); every
+// other column H(o, m) minus the trilinear interpolant of H(o, corners) at m.
+// The contraction sum_o A(o) Hrel(o, m) then returns the field at node 0, the
+// corner fields relative to it and, elsewhere, the field less its trilinear
+// interpolant: the same field with its large smooth part taken out of the
+// FP32 sums (its corner values enter the evaluation in FP64).
+void pair_relative_table(int n_sr, const double* Hw, double* Hrel) {
+  const int noff = 2 * n_sr + 2, no3 = noff * noff * noff;
+  for (int o = 0; o < no3; ++o) {
+    const double* h = Hw + (size_t)o * 64;
+    double* r = Hrel + (size_t)o * 64;
+    for (int m = 0; m < 64; ++m) {
+      if (m == 0) {
+        r[m] = h[0];
+      } else if (is_corner_node(m)) {
+        r[m] = h[m] - h[0];
+      } else {
+        double t = 0.0;
+        for (int c = 0; c < 8; ++c) t += corner_weight(c, m) * h[corner_node(c)];
+        r[m] = h[m] - t;
+      }
+    }
+  }
+}
+
+// The FP32 path's screen-adjoint table: Hd(o, m) = H(o, m) - H(o, 0), column 0
+// zero.  With Wsum(e) = sum_m W[e][m] the contraction splits as
+//   D(o, e) = H(o, 0) Wsum(e) + sum_m W[e][m] Hd(o, m):
+// the tensor cores form the second part (small terms), the gather adds the
+// first in double-float arithmetic (H0: hi + lo floats of H(o, 0)).
+void pair_adjoint_table(int n_sr, const double* Hw, double* Hd, float* H0) {
+  const int noff = 2 * n_sr + 2, no3 = noff * noff * noff;
+  for (int o = 0; o < no3; ++o) {
+    const double h0 = Hw[(size_t)o * 64];
+    for (int m = 0; m < 64; ++m) Hd[(size_t)o * 64 + m] = m == 0 ? 0.0 : Hw[(size_t)o * 64 + m] - h0;
+    const float hi = (float)h0;
+    H0[2 * o] = hi;
+    H0[2 * o + 1] = (float)(h0 - (double)hi);
+  }
 }
 
 // the table's three bf16 pieces for the screen adjoint's contraction
@@ -1439,18 +1587,27 @@ cudaError_t energy(fep3m_ctx* c, double* U_dev) {
   return cudaGetLastError();
 }
 
-// D-GEMM + gather over offset chunks sized so D stays within a memory budget
+template <class T, int NSR>
+static void launch_adj_vertex(fep3m_ctx* c, int z0, int z1, const T* D, double* A, cudaStream_t s) {
+  const int64_t ne = (int64_t)c->n * c->n * c->n;
+  const bool df = sizeof(T) == 4;
+  FEP3M_CL k_adj_vertex<T, NSR><<<(unsigned)((ne + 127) / 128), 128, 0, s>>>(
+      c->n, z0, z1, z0 == 0, c->count, D, df ? (const float2*)c->H0df : nullptr, df ? (const float2*)c->Wsum : nullptr,
+      A);
+}
+
+// D-GEMM + gather over chunks of whole offset planes (all offsets with one
+// oz), sized so D stays within a memory budget
 template <class T>
-static cudaError_t screen_adjoint(fep3m_ctx* c, const T* W, const T* Hw, double* A) {
+static cudaError_t screen_adjoint(fep3m_ctx* c, const T* W, const double* Hw, double* A) {
   const int n = c->n;
   const int64_t ne = (int64_t)n * n * n;
-  const int no3 = c->noff * c->noff * c->noff;
+  const int noff = c->noff, plane = noff * noff;
   const size_t budget = (size_t)1 << 31;   // bytes of D held at once
   // tensor cores (FP32 path, table pieces prepared): column tiles of ADJ_NT offsets
   const bool tcore = sizeof(T) == 4 && c->HbA != nullptr;
-  const int q = tcore ? ADJ_NT : GT;
-  int chunk = (int)std::min<int64_t>(no3, std::max<int64_t>(q, (int64_t)(budget / (ne * sizeof(T))) / q * q));
-  const size_t need = (size_t)chunk * ne * sizeof(T);
+  const int planes = (int)std::min<int64_t>(noff, std::max<int64_t>(1, (int64_t)(budget / ((size_t)ne * sizeof(T) * plane))));
+  const size_t need = (size_t)planes * plane * ne * sizeof(T);
   if (c->D_bytes < need) {
     if (c->D_adj) cudaFree(c->D_adj);
     c->D_adj = nullptr;
@@ -1460,22 +1617,23 @@ static cudaError_t screen_adjoint(fep3m_ctx* c, const T* W, const T* Hw, double*
     c->D_bytes = need;
   }
   cudaStream_t s = c->stream;
-  for (int o0 = 0; o0 < no3; o0 += chunk) {
-    const int no = std::min(chunk, no3 - o0);
+  for (int z0 = 0; z0 < noff; z0 += planes) {
+    const int z1 = std::min(noff, z0 + planes), o0 = z0 * plane, no = (z1 - z0) * plane;
     if (tcore) {
-      cudaError_t e = tc_rows_gemm(ne, 64, no3, ADJ_NT, o0 / ADJ_NT, (no + ADJ_NT - 1) / ADJ_NT, (const float*)W,
-                                   c->HbA, (float*)c->D_adj, c->iflags + 2, s);
+      cudaError_t e = tc_rows_gemm(ne, 64, o0, o0 + no, ADJ_NT, (const float*)W, c->HbA, (float*)c->D_adj,
+                                   c->iflags + 2, s);
       if (e != cudaSuccess) return e;
     } else {
       dim3 grid((unsigned)((ne + GT - 1) / GT), (unsigned)((no + GT - 1) / GT));
       FEP3M_CL k_adj_gemm<T><<<grid, PT, 0, s>>>(ne, o0, no, W, Hw, (T*)c->D_adj);
     }
-    if (ne >= ((int64_t)1 << 20))
-      FEP3M_CL k_adj_gather<T, true><<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(n, c->n_sr, o0, no, o0 == 0,
-                                                                                  c->count, (const T*)c->D_adj, A);
-    else
-      FEP3M_CL k_adj_gather<T, false><<<(unsigned)((ne + 31) / 32), 256, 0, s>>>(n, c->n_sr, o0, no, o0 == 0,
-                                                                                 c->count, (const T*)c->D_adj, A);
+    const T* D = (const T*)c->D_adj;
+    switch (c->n_sr) {
+      case 1: launch_adj_vertex<T, 1>(c, z0, z1, D, A, s); break;
+      case 2: launch_adj_vertex<T, 2>(c, z0, z1, D, A, s); break;
+      case 3: launch_adj_vertex<T, 3>(c, z0, z1, D, A, s); break;
+      default: launch_adj_vertex<T, 4>(c, z0, z1, D, A, s); break;
+    }
   }
   return cudaGetLastError();
 }
@@ -1488,11 +1646,11 @@ cudaError_t adjoint_pre(fep3m_ctx* c, double gU, const double* gphi, cudaStream_
   const int per = PT / 64;
   if (c->precision == FEP3M_MIXED) {
     FEP3M_CL k_elem_deposit<float><<<gsz(ne, per), PT, 0, s>>>(ne, c->start, c->count, (const float4*)c->part, c->w_s,
-                                                      (float*)c->W_el);
+                                                               (float*)c->W_el, (float2*)c->Wsum);
     FEP3M_CL k_node_assemble<float><<<gsz(nodes), PT, 0, s>>>(n, (const float*)c->W_el, c->g64);
   } else {
     FEP3M_CL k_elem_deposit<double><<<gsz(ne, per), PT, 0, s>>>(ne, c->start, c->count, (const vec4<double>::type*)c->part,
-                                                       c->w_s, (double*)c->W_el);
+                                                                c->w_s, (double*)c->W_el, nullptr);
     FEP3M_CL k_node_assemble<double><<<gsz(nodes), PT, 0, s>>>(n, (const double*)c->W_el, c->g64);
   }
   return cudaGetLastError();
@@ -1508,7 +1666,7 @@ cudaError_t adjoint_sweeps(fep3m_ctx* c, cudaStream_t s, bool singular) {
   c->stream = s;   // screen_adjoint issues on c->stream
   cudaError_t e;
   if (c->precision == FEP3M_MIXED) {
-    e = screen_adjoint<float>(c, (const float*)c->W_el, c->Hw32, (double*)c->A_el);
+    e = screen_adjoint<float>(c, (const float*)c->W_el, c->Ha64, (double*)c->A_el);
     if (e == cudaSuccess && singular)
       FEP3M_CL k_pair_adj_warp<float><<<(unsigned)((N + 7) / 8), PT, 0, s>>>(N, n, c->n_sr, (float)c->h, c->start,
                                                          (const float4*)c->part, c->ecoord, c->w_s, c->psi_s, c->gpsi_s);

@@ -31,7 +31,10 @@ struct MpqWeights {
 __device__ __forceinline__ int wrapv(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // bin each charge (the same wrap/element/offset rule as fep3m_set_particles) and
-// scatter Q times its order-1 screen weights onto the 8 vertices of its element
+// scatter Q times its order-1 screen weights onto the 8 vertices of its element.
+// Inputs are not checked for finiteness (that would need a flag read back on
+// the host): a non-finite coordinate is taken as 0 and a non-finite charge
+// carries into b.
 __global__ void k_static_deposit(int64_t N, const double* __restrict__ pos, const double* __restrict__ Q, double L,
                                  int n, double h, double inv_h, double* __restrict__ r) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -86,13 +89,14 @@ __global__ void k_static_load(int n, MpqWeights m, const double* __restrict__ r,
   b[g] = 4.0 * M_PI * acc;
 }
 
-bool on_device(const void* p) {
+// device memory of the current device, or managed memory
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     (void)cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -101,12 +105,12 @@ extern "C" int fep3m_load_vector_static(double L, int n_el, int64_t N, const dou
                                         void* cuda_stream) {
   if (!(L > 0) || !std::isfinite(L) || n_el < 1 || n_el > kMaxNel || N < 1 || N > ((int64_t)1 << 31) - 1)
     return FEP3M_EINVAL;
-  if (!on_device(pos) || !on_device(Q) || !on_device(b)) return FEP3M_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     (void)cudaGetLastError();
     return FEP3M_ECUDA;
   }
+  if (!on_device(pos, dev) || !on_device(Q, dev) || !on_device(b, dev)) return FEP3M_EINVAL;
   double* r = nullptr;
   {
     // first call on this device: look up the device address of the static array

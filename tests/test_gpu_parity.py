@@ -23,6 +23,14 @@ def api():
     return a
 
 
+# mixed path: relative error of U = Q.Phi / 2 against the oracle's.  U adds the
+# potentials' errors coherently where they follow the charges (each charge's
+# own screen and smooth potential); measured 1e-8 .. 6e-7 on these cases and
+# 1.1e-6 on 4e6 clustered charges (the tensor cores' FP32 accumulation of the
+# screen field), hence 2e-6
+U_TOL = 2e-6
+
+
 def maxrel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
@@ -157,20 +165,12 @@ def test_mixed_matches_oracle(api, name, tc):
     d, ref, dx = oracle(name)
     r = run(api, d, "mixed", forces=False, tc=tc)
     assert normrel(r["phi"], ref["phi"]) < 1e-6, normrel(r["phi"], ref["phi"])
-    # U = Q.Phi / 2, so the Phi tolerance bounds U's error by Cauchy-Schwarz:
-    # |dU| <= |Q| |dPhi| / 2 <= 1e-6 |Q| |Phi| / 2
-    bound = 0.5 * np.linalg.norm(d["Q"]) * 1e-6 * np.linalg.norm(ref["phi"])
-    assert abs(r["U"] - ref["U"]) < bound, (abs(r["U"] - ref["U"]), bound)
-
-
-NACL_FP32 = pytest.mark.xfail(strict=True, reason="rock-salt forces are small residues of large field parts (the "
-                              "lattice nearly cancels them); on this 16^3 lattice the FP32 arithmetic of the pair "
-                              "and adjoint sums leaves slightly more than 1e-5 of the forces (the 32^3 lattice of "
-                              "the full-size tests passes; FP64 and the potentials pass)")
+    # the energy directly against the oracle's, relative to |U|
+    assert abs(r["U"] - ref["U"]) < U_TOL * abs(ref["U"]), abs(r["U"] - ref["U"]) / abs(ref["U"])
 
 
 @pytest.mark.parametrize("tc", [True, False])
-@pytest.mark.parametrize("name", [pytest.param(k, marks=NACL_FP32) if k == "nacl16" else k for k in CASES])
+@pytest.mark.parametrize("name", list(CASES))
 def test_mixed_forces_match_oracle(api, name, tc):
     d, ref, dx = oracle(name)
     r = run(api, d, "mixed", tc=tc)
@@ -249,6 +249,27 @@ def test_autograd_function(api):
     U.backward()
     assert maxrel(pos.grad.cpu().numpy(), dx) < 1e-10
     assert abs(U.item() - ref["U"]) < 1e-11 * abs(ref["U"])
+
+
+def test_autograd_two_applies_on_one_engine(api):
+    """Two configurations through one engine, summed into one loss: each backward
+    must differentiate its own forward (the engine holds one set of charges)."""
+    import torch
+    d, ref, dx = oracle("uniform1k")
+    pos2, Q2 = workloads.uniform_pm(400, seed=21)
+    ref2 = ofe.forward(pos2, Q2, d["L"], d["n_el"], want_grad=True)
+    dx2, _, _ = ofe.vjp(ref2, Q2)
+    eng = api.FEP3M(d["L"], d["n_el"])
+    p1 = torch.tensor(d["pos"], device="cuda", requires_grad=True)
+    q1 = torch.tensor(d["Q"], device="cuda", requires_grad=True)
+    p2 = torch.tensor(pos2, device="cuda", requires_grad=True)
+    q2 = torch.tensor(Q2, device="cuda", requires_grad=True)
+    U1, _ = api.FEP3MEnergy.apply(p1, q1, eng)
+    U2, _ = api.FEP3MEnergy.apply(p2, q2, eng)
+    (U1 + 2.0 * U2).backward()
+    assert maxrel(p1.grad.cpu().numpy(), dx) < 1e-10
+    assert maxrel(p2.grad.cpu().numpy(), 2.0 * dx2) < 1e-10
+    assert abs(U1.item() - ref["U"]) < 1e-11 * abs(ref["U"])
 
 
 @pytest.mark.parametrize("n", [72, 96])

@@ -186,3 +186,30 @@ def test_adjoint_against_central_differences():
         qm[i] -= 1e-5
         fd = (loss(pos, qp) - loss(pos, qm)) / 2e-5
         assert abs(fd - dQ[i]) < 1e-6 * max(1.0, abs(fd)), (i, fd, dQ[i])
+
+
+def test_forces_at_sampled_charges():
+    """forces_at (the energy's adjoint restricted to some charges, with the mesh
+    solves over every charge) equals -dU/dx by central differences of U at those
+    charges, and the full adjoint there."""
+    pos, Q = small_set(180, seed=41)
+    L, n = 1.3, 9
+    tg = np.sort(np.random.default_rng(5).choice(len(Q), 12, replace=False))
+    F = fep3m.forces_at(pos, Q, L, n, tg)
+    f = fep3m.forward(pos, Q, L, n, want_grad=True)
+    dx, _, _ = fep3m.vjp(f, Q)
+    assert np.abs(F + dx[tg]).max() < 1e-12 * np.abs(dx).max()
+    hfd = 1e-5 * L
+    safe = [k for k, i in enumerate(tg) if face_safe(pos[i:i + 1], L, n, 4 * hfd)[0]][:3]
+    for k in safe:
+        i = tg[k]
+        for a in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, a] += hfd
+            pm[i, a] -= hfd
+            fd = -(fepu(pp, Q, L, n) - fepu(pm, Q, L, n)) / (2 * hfd)
+            assert abs(fd - F[k, a]) < 1e-6 * max(1.0, abs(fd)), (i, a, fd, F[k, a])
+
+
+def fepu(pos, Q, L, n):
+    return fep3m.forward(pos, Q, L, n)['U']

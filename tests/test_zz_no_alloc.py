@@ -43,3 +43,8 @@ def test_static_load_vector_matches_context_path_twice():
     too_big = lib.fep3m_load_vector_static(1.0, 65, 1, ctypes.c_void_p(pos.data_ptr()),
                                            ctypes.c_void_p(Q.data_ptr()), ctypes.c_void_p(b.data_ptr()), None)
     assert too_big == _lib.FEP3M_EINVAL
+    # so are host buffers (the call takes device memory of the current device only)
+    host_b = np.empty(27 * 16 ** 3)
+    on_host = lib.fep3m_load_vector_static(1.0, 16, 1, ctypes.c_void_p(pos.data_ptr()),
+                                           ctypes.c_void_p(Q.data_ptr()), ctypes.c_void_p(host_b.ctypes.data), None)
+    assert on_host == _lib.FEP3M_EINVAL
