@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--large", type=int, default=1,
+                   help="1: also time the water (999 999 atoms, 128^3) and clustered (4e6, 256^3) workloads")
     p.add_argument("--legs", default="all", choices=["all", "main"],
                    help="main: only the timed loop of --precision (no FP64 leg, end-to-end leg or accuracy); "
                         "for profiling")
@@ -150,7 +152,7 @@ def fp32_peak_tflops(n_sm, mhz):
 
 def time_engine(eng, pos, Q, out, steps, warmup, flush, torch, host=False):
     """Run warmup + timed steps; returns (ms per step, (screen-kernel ms, inner-solve ms) per step, launches per
-    step, the last result)."""
+    step, the last result).  With timing enabled on eng, the stage times of each step are kept in eng.step_stats."""
     stream = eng.stream
     for _ in range(warmup):
         eng.set_particles(pos, Q)
@@ -170,8 +172,64 @@ def time_engine(eng, pos, Q, out, steps, warmup, flush, torch, host=False):
         ms.append(e0.elapsed_time(e1))
         st = eng.stats()
         pair.append((st["ms_pair_screen"], st["ms_inner_solve"]))
+        eng.step_stats.append(st)
     launches = (eng.stats()["kernel_launches"] - l0) / steps
     return ms, pair, launches, r
+
+
+STAGES = ("ms_bin", "ms_assemble", "ms_solve", "ms_inner_solve", "ms_pair_screen", "ms_pair_eval", "ms_adjoint")
+
+
+def large_workload(name, steps, warmup, flush, dev, torch, peaks):
+    """One of the full-size workloads (mixed, forces), timed like the headline: particles/s, per-step
+    stage times (CUDA events on their streams; the stages overlap across the four streams) and the
+    roofline of the two largest kernels: the transform pass of the mesh solve (tensor pipe: 2 N flops per
+    node and mode column, six split-bf16 products) and the short-range screen kernel (FP32, SURVEY 8(d)
+    count)."""
+    from paper_1503_08509_gb300 import api, workloads
+    d = workloads.workload(name)
+    N = len(d["Q"])
+    pos = torch.tensor(d["pos"], device=dev)
+    Q = torch.tensor(d["Q"], device=dev)
+    eng = api.FEP3M(d["L"], d["n_el"], precision="mixed", device=dev.index)
+    eng.set_timing(True)
+    eng.step_stats = []
+    out = dict(phi=torch.empty(N, dtype=torch.float64, device=dev),
+               forces=torch.empty((N, 3), dtype=torch.float64, device=dev))
+    ms, pair, launches, r = time_engine(eng, pos, Q, out, steps, warmup, flush, torch)
+    st = eng.stats()
+    stages = {k: round(statistics.mean(x[k] for x in eng.step_stats), 3) for k in STAGES}
+    Nn = 3 * d["n_el"]
+    pass_ms = stages["ms_inner_solve"] / 6
+    pass_flops = 2.0 * Nn ** 4 * 6          # six split products per pass
+    bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+    props = torch.cuda.get_device_properties(dev)
+    fp32 = fp32_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
+    flops_elem = st["screen_element_pairs"] * 1024 + st["singular_pairs"] * 20
+    pair_ms = stages["ms_pair_screen"]
+    res = {"workload": name, "n": N, "n_el": d["n_el"], "steps": steps, "warmup": warmup,
+           "value": round(N * steps / (sum(ms) / 1e3), 1), "unit": "particles/s",
+           "ms_per_step": round(sum(ms) / steps, 3), "stages_ms": stages,
+           "gpu_launches": int(round(launches)),
+           "mg": {"refine_steps": st["refine_steps"], "rel_residual": st["mg_rel_residual"],
+                  "adj_rel_residual": st["adj_rel_residual"]},
+           "pairs": {"singular": st["singular_pairs"], "screen_element_pairs": st["screen_element_pairs"],
+                     "nonempty_elements": st["nonempty_elements"], "max_per_element": st["max_per_element"]},
+           "roofline_transform": {"kernel": "k_tc_rows (transform pass of the mesh solve)", "bound": "tensor",
+                                  "achieved": round(pass_flops / (pass_ms * 1e-3) / 1e12, 1),
+                                  "peak": bf16, "unit": "TFLOP/s",
+                                  "frac": round(pass_flops / (pass_ms * 1e-3) / 1e12 / bf16, 4),
+                                  "count": "2 N^4 x 6 split-bf16 products per pass, N = %d" % Nn,
+                                  "ms_per_launch": round(pass_ms, 4),
+                                  "peak_note": "measured sustained bf16 (MEASURED_PEAKS.json)"},
+           "roofline_pair": {"kernel": "k_pair_screen", "bound": "alu",
+                             "achieved": round(flops_elem / (pair_ms * 1e-3) / 1e12, 2), "peak": round(fp32, 2),
+                             "unit": "TFLOP/s", "frac": round(flops_elem / (pair_ms * 1e-3) / 1e12 / fp32, 4),
+                             "ms_per_launch": pair_ms}}
+    eng.close()
+    del pos, Q, out
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_ours(args):
@@ -196,6 +254,7 @@ def run_ours(args):
     for prec in legs:
         eng = api.FEP3M(d["L"], d["n_el"], precision=prec, device=dev.index)
         eng.set_timing(True)
+        eng.step_stats = []
         out = dict(phi=torch.empty(N, dtype=torch.float64, device=dev),
                    forces=torch.empty((N, 3), dtype=torch.float64, device=dev))
         main = prec == args.precision
@@ -343,6 +402,10 @@ def run_ours(args):
         "gpu_launches": int(round(main["launches"])),
         "clocks": main["clocks"],
     }
+    if args.large and ws == 1:
+        # the full-size workloads of the other configurations, mixed with forces (not the headline)
+        line["workloads"] = {nm: large_workload(nm, st_, 3, flush, dev, torch, peaks)
+                             for nm, st_ in (("water1m", 20), ("blobs4m", 10))}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -357,8 +420,12 @@ def oracle_step(d):
     return f["U"], dx
 
 
+ONE_THREAD = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
 def cpu_baseline():
-    """The CPU oracle, as it stands, on the full workload (one step: Phi, U and forces)."""
+    """The CPU oracle, as it stands, on the full workload (one step: Phi, U and forces), on all host cores,
+    and again in a child process whose BLAS and OpenMP pools are limited to one thread."""
     from oracle import tables
     from paper_1503_08509_gb300 import workloads
     d = workloads.workload(WORKLOAD)
@@ -366,9 +433,23 @@ def cpu_baseline():
     t0 = time.perf_counter()
     oracle_step(d)
     dt = time.perf_counter() - t0
-    return {"value": round(len(d["Q"]) / dt, 1), "unit": "particles/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "full workload, one step (numpy/scipy FP64; BLAS threads = all cores)",
-            "seconds": round(dt, 2)}
+    res = {"value": round(len(d["Q"]) / dt, 1), "unit": "particles/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "full workload, one step (numpy/scipy FP64; BLAS threads = all cores)",
+           "seconds": round(dt, 2)}
+    env = dict(os.environ, **{k: "1" for k in ONE_THREAD})
+    code = ("import sys, time; sys.path.insert(0, %r); import bench; from oracle import tables; "
+            "from paper_1503_08509_gb300 import workloads; d = workloads.workload(bench.WORKLOAD); "
+            "tables.kept_table(); t0 = time.perf_counter(); bench.oracle_step(d); "
+            "print(time.perf_counter() - t0)" % ROOT)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        dt1 = float(r.stdout.strip().splitlines()[-1])
+        res["one_thread"] = {"value": round(len(d["Q"]) / dt1, 1), "unit": "particles/s", "cores": 1,
+                             "seconds": round(dt1, 2),
+                             "sample": "the same step in a child process with %s = 1" % "/".join(ONE_THREAD)}
+    except Exception as exc:   # reported, not fatal: the all-core figure stands
+        res["one_thread"] = {"error": str(exc)[:200]}
+    return res
 
 
 def run_reference(args):

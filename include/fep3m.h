@@ -71,14 +71,24 @@ enum { FEP3M_FP64 = 0, FEP3M_MIXED = 1 };
                                   cores instead of the tensor cores             */
 #define FEP3M_MULTIGRID 4u     /* inner mesh solver: multigrid-preconditioned CG
                                   instead of the exact fast-diagonalisation
-                                  solve (both inside the same refinement)       */
+                                  solve (both inside the same refinement; q = 1) */
+#define FEP3M_ONE_ELEMENT 8u   /* one-element screens (Sec. 5.3): weights on the
+                                  interior nodes of the charge's element only,
+                                  the moments l < q - 1; needs q >= 2           */
 
 typedef struct fep3m_ctx fep3m_ctx;
 
 typedef struct {
   double L;            /* periodic cube edge, > 0                              */
   int n_el;            /* elements per axis; >= 2 n_sr + 1; h = L / n_el        */
-  int q;               /* screen order; this build supports q = 1 (p = 3)       */
+  int q;               /* screen order 1..4 (Sec. 2.1), mesh order p = q + 2.
+                          q = 1: potentials, energy, forces and the VJP, in
+                          both precisions as described below.  q >= 2: the
+                          screen basis on Gauss-Lobatto nodes, potentials and
+                          energy only (fep3m_compute with force = NULL;
+                          fep3m_vjp returns FEP3M_EINVAL), the screen
+                          contraction in FP64 in both precisions; p n_el <=
+                          1024                                                  */
   int n_sr;            /* short-range block half-width in elements, 1..4 (3 in
                           the paper's tests, Sec. 4: a 7 x 7 x 7 block)         */
   int precision;       /* FEP3M_FP64 or FEP3M_MIXED.  Both solve the mesh
@@ -107,7 +117,7 @@ typedef struct {
                           1e-10 (MIXED)                                          */
   int mg_max_cycles;   /* cap on refinement sweeps; 0 -> 10                      */
   int table_pad;       /* Dirichlet box margin, elements, beyond the kept table;
-                          0 -> 4                                                 */
+                          0 -> 4 (q = 1) or 2 (q >= 2); at most 8               */
   unsigned flags;      /* FEP3M_NEUTRALIZE, FEP3M_CUDA_CORES,
                           FEP3M_MULTIGRID                                        */
 } fep3m_config;
@@ -162,7 +172,8 @@ int fep3m_set_particles(fep3m_ctx* ctx, int64_t N, const double* pos, const doub
 
 /* Phi_i (N, host or device; may be NULL) and U (host scalar; may be NULL) for
  * the charges last set.  force (N x 3, host or device, or NULL) receives
- * -dU/dx_i; computing it runs the adjoint (one more mesh solve).
+ * -dU/dx_i; computing it runs the adjoint (one more mesh solve; q = 1 only,
+ * FEP3M_EINVAL for q >= 2).
  * Synchronises the stream when U, force-on-host or phi-on-host is asked.   */
 int fep3m_compute(fep3m_ctx* ctx, double* phi, double* U, double* force);
 
@@ -197,18 +208,21 @@ int fep3m_get_binning(const fep3m_ctx* ctx, int32_t* perm, int32_t* count,
  *                     Eq. oned, k = i + 2 j + 4 k' the corner
  *   b      [(3n)^3]   FE load vector 4 pi int rho u_m (index ix + 3n iy + 9n^2 iz)
  *   phi_mesh [(3n)^3] mesh potential nodal values (physical units, mean zero)
- *   Phi^sm / Phi^sing / Phi^scr parts are not kept separately.             */
+ *   Phi^sm / Phi^sing / Phi^scr parts are not kept separately.
+ * For q >= 2: C [n^3 x (q+1)^3] (screen node i + (q+1)(j + (q+1) k)), b and
+ * phi_mesh [(p n)^3] on the order-p mesh (index ix + pn iy + (pn)^2 iz).     */
 int fep3m_get_mesh(const fep3m_ctx* ctx, double* C, double* b, double* phi_mesh);
 
 /* Solve the periodic FE system K phi = b - (sum b) w / sum w, int phi = 0,
- * for a caller right-hand side b ((3n)^3, host or device) with the context's
+ * for a caller right-hand side b ((p n)^3, host or device) with the context's
  * mesh solver (precision as configured); writes phi (physical units).  Used
  * to test the solver alone.                                                 */
 int fep3m_solve_mesh(fep3m_ctx* ctx, const double* b, double* phi);
 
 /* The kept FE basis-screen table (h = 1): nodal values on [-(n_sr+1), n_sr+1]^3
  * in steps of 1/3, (6 n_sr + 7)^3 values, index ix + s iy + s^2 iz with
- * s = 6 n_sr + 7.                                                            */
+ * s = 6 n_sr + 7.  q = 1 only (FEP3M_EINVAL otherwise; the order-q tables
+ * come from fep3m_screen_type_table).                                        */
 int fep3m_get_table(const fep3m_ctx* ctx, double* table);
 
 /* The 1-D eigenbasis of the fast-diagonalisation mesh solve (host only, no

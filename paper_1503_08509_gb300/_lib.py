@@ -11,6 +11,7 @@ FEP3M_FP64, FEP3M_MIXED = 0, 1
 FEP3M_NEUTRALIZE = 1
 FEP3M_CUDA_CORES = 2
 FEP3M_MULTIGRID = 4
+FEP3M_ONE_ELEMENT = 8
 
 
 class Config(ctypes.Structure):

@@ -43,21 +43,24 @@ class FEP3M:
     CUDA cores instead of as bf16 tensor-core MMAs.
     solver: the FP32 inner solve of the mesh system's iterative refinement,
     'fdm' (exact, by fast diagonalisation) or 'multigrid' (multigrid-
-    preconditioned CG).
+    preconditioned CG; q = 1).
+    q: screen order 1..4 (mesh order q + 2); q >= 2 computes potentials and
+    energy (no forces).  one_element: one-element screens (q >= 2).
     """
 
     def __init__(self, L, n_el, n_sr=3, precision="fp64", mg_rtol=0.0, mg_max_cycles=0, neutralize=False,
-                 table_pad=0, device=None, stream=None, tensor_cores=True, solver="fdm"):
+                 table_pad=0, device=None, stream=None, tensor_cores=True, solver="fdm", q=1, one_element=False):
         lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
-        self.L, self.n_el, self.n_sr = float(L), int(n_el), int(n_sr)
+        self.L, self.n_el, self.n_sr, self.q = float(L), int(n_el), int(n_sr), int(q)
         self.precision = precision
-        cfg = _lib.Config(L=self.L, n_el=self.n_el, q=1, n_sr=self.n_sr,
+        cfg = _lib.Config(L=self.L, n_el=self.n_el, q=self.q, n_sr=self.n_sr,
                           precision=_lib.FEP3M_MIXED if precision == "mixed" else _lib.FEP3M_FP64,
                           mg_rtol=mg_rtol, mg_max_cycles=mg_max_cycles, table_pad=table_pad,
                           flags=(_lib.FEP3M_NEUTRALIZE if neutralize else 0) |
                           (0 if tensor_cores else _lib.FEP3M_CUDA_CORES) |
-                          (_lib.FEP3M_MULTIGRID if solver == "multigrid" else 0))
+                          (_lib.FEP3M_MULTIGRID if solver == "multigrid" else 0) |
+                          (_lib.FEP3M_ONE_ELEMENT if one_element else 0))
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             h = ctypes.c_void_p()
@@ -80,7 +83,7 @@ class FEP3M:
 
     @property
     def nodes(self):
-        return (3 * self.n_el) ** 3
+        return ((self.q + 2) * self.n_el) ** 3
 
     def set_particles(self, pos, Q):
         N = int(pos.shape[0])
@@ -129,7 +132,7 @@ class FEP3M:
 
     def mesh(self):
         ne = self.n_el ** 3
-        d = dict(C=np.empty((ne, 8)), b=np.empty(self.nodes), phi_mesh=np.empty(self.nodes))
+        d = dict(C=np.empty((ne, (self.q + 1) ** 3)), b=np.empty(self.nodes), phi_mesh=np.empty(self.nodes))
         _lib.check(_lib.load().fep3m_get_mesh(self._h, _ptr(d["C"]), _ptr(d["b"]), _ptr(d["phi_mesh"])),
                    "fep3m_get_mesh")
         return d

@@ -255,6 +255,29 @@ int solve_status(fep3m_ctx* c, bool adjoint) {
   return ok ? FEP3M_OK : FEP3M_ENOCONV;
 }
 
+// order q >= 2: potentials and energy (no forces in this build)
+int compute_orderq(fep3m_ctx* c, double* phi, double* U) {
+  const int64_t N = c->N;
+  const bool phi_dev = is_device_ptr(phi);
+  double* pd = phi_dev ? phi : (phi ? c->out_tmp : nullptr);
+  ev_record(c, 0);
+  const int st = orderq_compute(c, pd, U ? c->scal + 40 : nullptr);
+  ev_record(c, 3);
+  if (st != FEP3M_OK && st != FEP3M_ENOCONV) return st;
+  if (U) CK(cudaMemcpyAsync(U, c->scal + 40, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->have_forward = true;
+  c->have_grad = false;
+  c->stats.refine_steps = c->oq->sweeps;
+  c->stats.mg_rel_residual = c->oq->relres;
+  if (phi && !phi_dev) {
+    int s2 = deliver(c, phi, c->out_tmp, N * sizeof(double));
+    if (s2 != FEP3M_OK) return s2;
+  }
+  if (c->timing) c->stats.ms_solve = ev_ms(c, 0, 3);
+  return st;
+}
+
 constexpr int kMaxReruns = 3;
 
 }  // namespace
@@ -284,6 +307,7 @@ void fep3m_destroy(fep3m_ctx* c) {
   for (void* q : p) dfree(q);
   fep3m::solver_destroy(&c->solv[0]);
   fep3m::solver_destroy(&c->solv[1]);
+  fep3m::orderq_destroy(c);
   if (c->host_err) cudaFreeHost(c->host_err);
   if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
   if (c->sweep_stream) cudaStreamDestroy(c->sweep_stream);
@@ -304,9 +328,11 @@ void fep3m_destroy(fep3m_ctx* c) {
 int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
   if (!cfg || !out) return FEP3M_EINVAL;
   *out = nullptr;
-  if (!(cfg->L > 0) || !std::isfinite(cfg->L) || cfg->q != 1 || cfg->n_sr < 1 || cfg->n_sr > 4 ||
+  if (!(cfg->L > 0) || !std::isfinite(cfg->L) || cfg->q < 1 || cfg->q > 4 || cfg->n_sr < 1 || cfg->n_sr > 4 ||
       cfg->n_el < 2 * cfg->n_sr + 1 || cfg->n_el > 400 ||
-      (cfg->precision != FEP3M_FP64 && cfg->precision != FEP3M_MIXED) || cfg->mg_rtol < 0 || cfg->table_pad < 0)
+      (cfg->precision != FEP3M_FP64 && cfg->precision != FEP3M_MIXED) || cfg->mg_rtol < 0 || cfg->table_pad < 0 ||
+      cfg->table_pad > 8 || ((cfg->flags & FEP3M_ONE_ELEMENT) && cfg->q < 2) ||
+      ((cfg->flags & FEP3M_MULTIGRID) && cfg->q > 1) || (long long)(cfg->q + 2) * cfg->n_el > 1024)
     return FEP3M_EINVAL;
   fep3m_ctx* c = new (std::nothrow) fep3m_ctx();
   if (!c) return FEP3M_ENOMEM;
@@ -328,6 +354,31 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
     return s;
   };
   make_stencils(c->st);
+  if (cfg->q >= 2) {
+    // screens of order q >= 2: the binning and bookkeeping buffers here, the
+    // rest in orderq_create
+    const int64_t ne = (int64_t)c->n * c->n * c->n;
+    cudaError_t e = cudaSuccess;
+    if ((e = dalloc(&c->count, ne)) != cudaSuccess || (e = dalloc(&c->start, ne + 1)) != cudaSuccess ||
+        (e = dalloc(&c->fill, ne)) != cudaSuccess || (e = cudaMalloc(&c->scan_tmp, scan_tmp_bytes(ne))) != cudaSuccess ||
+        (e = dalloc(&c->scal, 64)) != cudaSuccess || (e = dalloc(&c->iflags, 16)) != cudaSuccess ||
+        (e = dalloc(&c->red_tmp, 1024)) != cudaSuccess || (e = dalloc(&c->red_counter, 1)) != cudaSuccess ||
+        (e = cudaMallocHost(&c->host_err, sizeof(int))) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&c->pair_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_pfork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_pcount, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaMallocHost(&c->host_cnt, 5 * sizeof(unsigned long long))) != cudaSuccess)
+      return fail(from_cuda(e));
+    cudaMemset(c->red_counter, 0, sizeof(unsigned int));
+    cudaMemset(c->iflags, 0, 16 * sizeof(int));
+    *c->host_err = 0;
+    if ((st = orderq_create(c)) != FEP3M_OK) return fail(st);
+    for (int k = 0; k < 11; ++k) cudaEventCreate(&c->ev[k]);
+    c->ev_init = true;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(from_cuda(e));
+    *out = c;
+    return FEP3M_OK;
+  }
   // FE basis-screen table and its [vertex offset][node] layout for the kernels
   build_table(c->n_sr, cfg->table_pad > 0 ? cfg->table_pad : 4, c->table_host);
   const int keep = c->keep, noff = c->noff, sk = 6 * keep + 1;
@@ -468,9 +519,11 @@ int fep3m_set_particles(fep3m_ctx* c, int64_t N, const double* pos, const double
   return FEP3M_OK;
 }
 
+
 int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
   if (!c) return FEP3M_EINVAL;
   if (!c->have_particles) return FEP3M_ESTATE;
+  if (c->oq) return force ? FEP3M_EINVAL : compute_orderq(c, phi, U);
   const int64_t N = c->N;
   const bool phi_dev = is_device_ptr(phi);
   const bool fdev = force && is_device_ptr(force);
@@ -514,7 +567,7 @@ int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
 }
 
 int fep3m_vjp(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double* dQ) {
-  if (!c || !std::isfinite(gU)) return FEP3M_EINVAL;
+  if (!c || !std::isfinite(gU) || c->oq) return FEP3M_EINVAL;
   if (!c->have_particles) return FEP3M_ESTATE;
   const int64_t N = c->N;
   if (!c->have_forward || !c->have_grad) {
@@ -611,6 +664,20 @@ int fep3m_get_mesh(const fep3m_ctx* cc, double* C, double* b, double* phi_mesh) 
   fep3m_ctx* c = const_cast<fep3m_ctx*>(cc);
   if (!c) return FEP3M_EINVAL;
   if (!c->have_forward) return FEP3M_ESTATE;
+  if (c->oq) {
+    const fep3m::OrderQ* o = c->oq;
+    const int64_t ne = (int64_t)c->n * c->n * c->n, np3 = (int64_t)o->Np * o->Np * o->Np;
+    const int Q1 = o->q + 1;
+    int s;
+    if ((s = deliver(c, C, o->C, ne * Q1 * Q1 * Q1 * 8)) != FEP3M_OK) return s;
+    if ((s = deliver(c, b, o->b, np3 * 8)) != FEP3M_OK) return s;
+    if (phi_mesh) {
+      FEP3M_CL k_to_double<double><<<gsz(np3), PT, 0, c->stream>>>(np3, o->phi, o->t[0], c->inv_h);
+      if ((s = deliver(c, phi_mesh, o->t[0], np3 * 8)) != FEP3M_OK) return s;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return FEP3M_OK;
+  }
   const int64_t ne = (int64_t)c->n * c->n * c->n, nodes = 27 * ne;
   // staging through res64 (FP64, nodes >= 8 ne since 27 > 8)
   if (C) {
@@ -636,6 +703,21 @@ int fep3m_get_mesh(const fep3m_ctx* cc, double* C, double* b, double* phi_mesh) 
 
 int fep3m_solve_mesh(fep3m_ctx* c, const double* b, double* phi) {
   if (!c || !b || !phi) return FEP3M_EINVAL;
+  if (c->oq) {
+    fep3m::OrderQ* o = c->oq;
+    const int64_t np3 = (int64_t)o->Np * o->Np * o->Np;
+    CK(cudaMemcpyAsync(o->t[2], b, np3 * 8, is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->stream));
+    const int st = orderq_solve(c, o->t[2], o->t[3]);
+    if (st != FEP3M_OK && st != FEP3M_ENOCONV) return st;
+    c->stats.refine_steps = o->sweeps;
+    c->stats.mg_rel_residual = o->relres;
+    FEP3M_CL k_to_double<double><<<gsz(np3), PT, 0, c->stream>>>(np3, o->t[3], o->t[0], c->inv_h);
+    int s = deliver(c, phi, o->t[0], np3 * 8);
+    if (s != FEP3M_OK) return s;
+    CK(cudaStreamSynchronize(c->stream));
+    return st;
+  }
   const int64_t nodes = (int64_t)27 * c->n * c->n * c->n;
   CK(cudaMemcpyAsync(c->g64, b, nodes * 8, is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      c->stream));
@@ -663,7 +745,7 @@ int fep3m_mesh_eigenbasis(int n_el, double* lam, double* V) {
 }
 
 int fep3m_get_table(const fep3m_ctx* c, double* table) {
-  if (!c || !table) return FEP3M_EINVAL;
+  if (!c || !table || c->oq) return FEP3M_EINVAL;
   if (is_device_ptr(table)) {
     CK(cudaMemcpy(table, c->table_host.data(), c->table_host.size() * 8, cudaMemcpyHostToDevice));
   } else {

@@ -123,6 +123,7 @@ struct FineFDM {
   void* BpF = nullptr;
   void* BpI = nullptr;
   int nt = 0, ntile = 0;
+  bool lite = false;          // three of the six piece products (large N; see fdm_setup)
   int* err = nullptr;         // device flag: a bounded wait gave up
 };
 
@@ -165,6 +166,48 @@ struct Solver {
   double relres = 0;
   // recorded around the first inner solve of a replayed solve (events in the graph)
   cudaEvent_t ev_in0 = nullptr, ev_in1 = nullptr;
+};
+
+// Screens of order q >= 2 on the order p = q + 2 mesh (orderq.cu).  Per-order
+// constants passed to the kernels by value (q <= 4, p <= 6).
+struct OQParams {
+  int q, p;
+  double W[25];         // screen weight polynomials: w_i = sum_l W[i (q+1) + l] (delta / h)^l (times h)
+  double Mpq[35];       // element mixed mass int l^p_i l^q_j, (p+1) x (q+1), h = 1
+  double bM[6][13];     // 1-D periodic order-p mass row of node type t = g mod p: tap o -> node g + o - p
+  double bK[6][13];     // the same for the stiffness
+  double wn[6];         // node integrals by type
+};
+
+// host-side data of the order-q path (highorder.cpp)
+struct OrderQHost {
+  int q = 0, p = 0;
+  std::vector<double> Me, Ke, Mpq, W, H, lam, V;
+};
+bool orderq_host(int q, int n, int n_sr, int pad, bool one_element, OrderQHost& h);
+
+struct OrderQ {
+  int q = 0, p = 0, Nq = 0, Np = 0, U = 0;
+  bool one_element = false;
+  OQParams prm;
+  double* C = nullptr;        // n^3 (q+1)^3 element-to-point lists (dimensionless)
+  double* r = nullptr;        // (q n)^3 nodal screen density
+  double* b = nullptr;        // (p n)^3 load vector (element units)
+  double* pb = nullptr;       // the load vector less its neutralising background
+  double* phi = nullptr;      // (p n)^3 mesh potential (element units)
+  double* res = nullptr;      // refinement residual
+  double* t[4] = {};          // scratch of the stiffness apply
+  float* r32 = nullptr;       // FP32 inner solve: right-hand side, solution, scratch
+  float* x32 = nullptr;
+  float* w1 = nullptr;
+  float* w2 = nullptr;
+  double* S = nullptr;        // n^3 (p+1)^3 screen field at each element's order-p nodes
+  double* H = nullptr;        // U^3 (p+1)^3 node-regrouped tables
+  double* red = nullptr;      // reduction partials
+  double* host_red = nullptr; // pinned: one reduction result
+  FineFDM fdm;
+  int sweeps = 0;
+  double relres = 0;
 };
 
 }  // namespace fep3m
@@ -243,6 +286,7 @@ struct fep3m_ctx {
   cudaEvent_t ev_pcount = nullptr;          // the pair statistics' copy to host_cnt
   unsigned long long* host_cnt = nullptr;   // pinned: 5 pair statistics of the last set_particles
   bool counts_stale = false;               // the pair statistics predate the particles last set
+  fep3m::OrderQ* oq = nullptr;   // screens of order q >= 2 (orderq.cu)
   // stats
   fep3m_stats stats;
   bool timing = false;
@@ -265,6 +309,13 @@ double estimate_lmax(const Stencils& st, int n);
 cudaError_t bin_particles(fep3m_ctx* c, const double* pos, const double* Q, int use_fp32);
 cudaError_t assemble_forward(fep3m_ctx* c);
 cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream);
+// fast-diagonalisation solve of a periodic N^3 mesh from its 1-D eigenpairs
+// (mesh.cu): device data, x = K^+ b in FP32 (six transform passes; w1, w2 N^3
+// scratch), release
+cudaError_t fdm_setup(FineFDM& f, int N, const std::vector<double>& lam, const std::vector<double>& V,
+                      bool tensor_cores);
+cudaError_t fdm_apply(const FineFDM& f, const float* b, float* x, float* w1, float* w2, cudaStream_t s);
+void fdm_free(FineFDM& f);
 void solver_destroy(Solver* s);
 size_t scan_tmp_bytes(int64_t n);
 // mu = 4 pi (Mpq^T)^(x)3 lam on the vertex grid (working precision); work1/2 sized n*(3n)^2
@@ -312,5 +363,13 @@ cudaError_t adjoint_sweeps(fep3m_ctx* c, cudaStream_t s, bool singular);
 cudaError_t adjoint_vertex(fep3m_ctx* c, cudaStream_t s);
 cudaError_t adjoint_final(fep3m_ctx* c, double gU, double* dpos, double* dQ, double sign, cudaStream_t s);
 cudaError_t energy(fep3m_ctx* c, double* U_dev);
+// sum_j w_j / r and sum_j w_j (x_j - x_t) / r^3 over each target's block, j != t
+// (sorted order; physical units)
+cudaError_t singular_sums(fep3m_ctx* c, const double* w, double* psi, double* gpsi, cudaStream_t s);
+// the order-q path (orderq.cu)
+int orderq_create(fep3m_ctx* c);
+void orderq_destroy(fep3m_ctx* c);
+int orderq_compute(fep3m_ctx* c, double* phi_dev, double* U_dev);
+int orderq_solve(fep3m_ctx* c, const double* b_dev, double* phi_dev);
 cudaError_t sorted_charges(fep3m_ctx* c);
 }  // namespace fep3m

@@ -425,6 +425,25 @@ void box_eigen(int p, int n, bool dirichlet, std::vector<double>& lam, std::vect
   }
 }
 
+// Create-time data of the order-q path: the order-p element matrices (h = 1),
+// the mixed mass against the order-q screen basis, the screen weight
+// polynomials (patch or one-element screens), the node-regrouped table of the
+// screen contraction and the periodic order-p eigenbasis.  False if the weight
+// system is singular.
+bool orderq_host(int q, int n, int n_sr, int pad, bool one_element, OrderQHost& h) {
+  const int p = q + 2;
+  const ElementPQ E(p, q);
+  h.q = q;
+  h.p = p;
+  h.Me = E.Me;
+  h.Ke = E.Ke;
+  h.Mpq = E.Mpq;
+  if (!screen_weight_poly(q, one_element, h.W)) return false;
+  screen_node_table(q, n_sr, pad, 8, h.H);
+  periodic_eigen_order(p, n, h.lam, h.V);
+  return true;
+}
+
 }  // namespace fep3m
 
 extern "C" {

@@ -1061,7 +1061,7 @@ __global__ void __launch_bounds__(256) k_fdm_axis(int N, const float* __restrict
 // that gave up.
 constexpr int FT_THREADS = 256;
 
-template <bool SCALE>
+template <bool SCALE, bool LITE = false>
 __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int cb, int ce, int nt,
                                                          const float* __restrict__ in, const uint4* __restrict__ Bp,
                                                          const float* __restrict__ lam, int null_mode, int N,
@@ -1116,7 +1116,8 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int cb
   load_units(0);
   bool failed = false;
   for (int c = 0; c < kc; ++c) {
-    for (int i = tid; i < 3 * (int)(bpiece / 16); i += FT_THREADS) cp_async16(tb + 16 * i, bsrc + (size_t)c * 3 * (bpiece / 16) + i);
+    for (int i = tid; i < (LITE ? 2 : 3) * (int)(bpiece / 16); i += FT_THREADS)
+      cp_async16(tb + 16 * i, bsrc + (size_t)c * 3 * (bpiece / 16) + i);
     cp_async_commit();
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1127,7 +1128,7 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int cb
       const uint32_t off = sw128_off(row, 8 * g);
       sts128(tl + off, p0);
       sts128(tl + 16384 + off, p1);
-      sts128(tl + 32768 + off, p2);
+      if (!LITE) sts128(tl + 32768 + off, p2);
     }
     cp_async_wait_all();
     fence_async_smem();
@@ -1140,9 +1141,11 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int cb
         umma_bf16(tmem, umma_desc(a), umma_desc(b), idesc, acc);                                 // a0 b0
         umma_bf16(tmem + lo_off, umma_desc(a), umma_desc(b + bpiece), idesc, acc);               // a0 b1
         umma_bf16(tmem + lo_off, umma_desc(a + 16384), umma_desc(b), idesc, 1u);                 // a1 b0
-        umma_bf16(tmem + lo_off, umma_desc(a), umma_desc(b + 2 * bpiece), idesc, 1u);            // a0 b2
-        umma_bf16(tmem + lo_off, umma_desc(a + 16384), umma_desc(b + bpiece), idesc, 1u);        // a1 b1
-        umma_bf16(tmem + lo_off, umma_desc(a + 32768), umma_desc(b), idesc, 1u);                 // a2 b0
+        if (!LITE) {
+          umma_bf16(tmem + lo_off, umma_desc(a), umma_desc(b + 2 * bpiece), idesc, 1u);          // a0 b2
+          umma_bf16(tmem + lo_off, umma_desc(a + 16384), umma_desc(b + bpiece), idesc, 1u);      // a1 b1
+          umma_bf16(tmem + lo_off, umma_desc(a + 32768), umma_desc(b), idesc, 1u);               // a2 b0
+        }
       }
       umma_commit(smem_u32(mbar));
     }
@@ -1432,6 +1435,8 @@ cudaError_t tc_rows_prepare(int nt) {
   const int sm = (int)tc_rows_smem(256);
   cudaError_t e = cudaFuncSetAttribute(k_tc_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_rows<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_rows<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   return e;
 }
 
@@ -1591,19 +1596,7 @@ struct MG {
     const int N = f.N;
     cudaStream_t s = c->stream;
     if (f.BpF) {
-      const dim3 g((unsigned)(((int64_t)N * N + 127) / 128), (unsigned)f.ntile);
-      const size_t sm = tc_rows_smem(f.nt);
-      const uint4* F = (const uint4*)f.BpF;
-      const uint4* I = (const uint4*)f.BpI;
-      const int64_t R = (int64_t)N * N;
-      const float* lm = f.lam32;
-      const int nm = f.null_mode, nt = f.nt;
-      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, 0, N, nt, b, F, lm, nm, N, w1, f.err);
-      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const T*)w1, F, lm, nm, N, w2, f.err);
-      launch_pdl(k_tc_rows<true>, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const T*)w2, F, lm, nm, N, w1, f.err);
-      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const T*)w1, I, lm, nm, N, w2, f.err);
-      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const T*)w2, I, lm, nm, N, w1, f.err);
-      launch_pdl(k_tc_rows<false>, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const T*)w1, I, lm, nm, N, x, f.err);
+      fdm_apply(f, b, x, w1, w2, s);
       return;
     }
     const dim3 g((unsigned)(((int64_t)N * N + FM - 1) / FM), (unsigned)((N + FN - 1) / FN));
@@ -1829,61 +1822,10 @@ static cudaError_t mg_setup(Solver* c) {
   H.lmax = estimate_lmax(c->st, 6);
   if (!(c->cfg.flags & FEP3M_MULTIGRID)) {
     // fine level by fast diagonalisation (block-Fourier eigenbasis, O(N^2) on the host)
-    FineFDM& f = H.fdm;
     const int Nf = 3 * c->n;
     std::vector<double> lamf, Vf;
     periodic_eigen(c->n, c->st, lamf, Vf);
-    f.null_mode = 0;
-    for (int i = 1; i < Nf; ++i)
-      if (std::fabs(lamf[i]) < std::fabs(lamf[f.null_mode])) f.null_mode = i;
-    std::vector<float> Vf32(Vf.begin(), Vf.end()), VTf32((size_t)Nf * Nf), lf32(lamf.begin(), lamf.end());
-    for (int i = 0; i < Nf; ++i)
-      for (int k = 0; k < Nf; ++k) VTf32[(size_t)k * Nf + i] = (float)Vf[(size_t)i * Nf + k];
-    if ((e = cudaMalloc(&f.V32, Vf32.size() * 4)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.VT32, VTf32.size() * 4)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.lam32, lf32.size() * 4)) != cudaSuccess) return e;
-    cudaMemcpy(f.V32, Vf32.data(), Vf32.size() * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(f.VT32, VTf32.data(), VTf32.size() * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(f.lam32, lf32.data(), lf32.size() * 4, cudaMemcpyHostToDevice);
-    f.N = Nf;
-    if (!(c->cfg.flags & FEP3M_CUDA_CORES)) {
-      // column tiles of nt modes (a multiple of 16, <= 128: two CTAs per SM), enough tiles to give every
-      // SM a CTA (measured: tiles of 192 or 256 modes, one CTA per SM, read the input fewer times but were
-      // no faster at 128^3)
-      const int64_t rt = ((int64_t)Nf * Nf + 127) / 128;
-      int ntile = std::max<int>((Nf + 127) / 128, (int)((148 + rt - 1) / rt));
-      const int nt = ((Nf + ntile - 1) / ntile + 15) / 16 * 16;
-      ntile = (Nf + nt - 1) / nt;
-      const int kc = (Nf + 63) / 64;
-      const size_t per = (size_t)3 * nt * 64;   // bf16 values per (tile, chunk)
-      std::vector<uint16_t> bf((size_t)ntile * kc * per), bi((size_t)ntile * kc * per);
-      for (int t = 0; t < ntile; ++t)
-        for (int ch = 0; ch < kc; ++ch)
-          for (int ii = 0; ii < nt; ++ii)
-            for (int k = 0; k < 64; ++k) {
-              const int i = t * nt + ii, a = 64 * ch + k;
-              const bool in = i < Nf && a < Nf;
-              uint16_t pf[3] = {0, 0, 0}, pi[3] = {0, 0, 0};
-              if (in) {
-                tc::bf16_pieces(Vf[(size_t)a * Nf + i], pf);   // analysis: B[i][a] = V[a][i]
-                tc::bf16_pieces(Vf[(size_t)i * Nf + a], pi);   // synthesis: B[i][a] = V[i][a]
-              }
-              for (int p = 0; p < 3; ++p) {
-                const size_t o = ((size_t)(t * kc + ch) * 3 + p) * nt * 64 + tc::sw128_off(ii, k) / 2;
-                bf[o] = pf[p];
-                bi[o] = pi[p];
-              }
-            }
-      if ((e = cudaMalloc(&f.BpF, bf.size() * 2)) != cudaSuccess) return e;
-      if ((e = cudaMalloc(&f.BpI, bi.size() * 2)) != cudaSuccess) return e;
-      cudaMemcpy(f.BpF, bf.data(), bf.size() * 2, cudaMemcpyHostToDevice);
-      cudaMemcpy(f.BpI, bi.data(), bi.size() * 2, cudaMemcpyHostToDevice);
-      f.nt = nt;
-      f.ntile = ntile;
-      if ((e = tc_rows_prepare(nt)) != cudaSuccess) return e;
-      if ((e = cudaMalloc(&f.err, sizeof(int))) != cudaSuccess) return e;
-      cudaMemset(f.err, 0, sizeof(int));
-    }
+    if ((e = fdm_setup(H.fdm, Nf, lamf, Vf, !(c->cfg.flags & FEP3M_CUDA_CORES))) != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
@@ -1895,14 +1837,7 @@ static void mg_free(Solver* c) {
       if (p) cudaFree(p);
   }
   c->mg.lv.clear();
-  FineFDM& f = c->mg.fdm;
-  if (f.BpF) cudaFree(f.BpF);
-  if (f.BpI) cudaFree(f.BpI);
-  if (f.err) cudaFree(f.err);
-  if (f.V32) cudaFree(f.V32);
-  if (f.VT32) cudaFree(f.VT32);
-  if (f.lam32) cudaFree(f.lam32);
-  f = FineFDM();
+  fdm_free(c->mg.fdm);
   CoarseSolver& cs = c->mg.coarse;
   if (cs.VT32) cudaFree(cs.VT32);
   if (cs.V32) cudaFree(cs.V32);
@@ -2215,6 +2150,118 @@ static void solver_plan_free(Solver* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->in64 = c->out64 = nullptr;
   c->cap_stream = nullptr;
+}
+
+// Device data of a fast-diagonalisation solve on an N^3 periodic mesh from the
+// 1-D generalized eigenpairs (lamf, Vf[node * N + mode], M-orthonormal): the
+// FP32 eigenbasis for the CUDA-core passes and, with tensor_cores, its bf16
+// pieces in the layout of the tensor-core row GEMM (column tiles of nt modes,
+// chunks of 64 nodes).  Used by the order-3 fine level and the order-p mesh.
+// From N = kFdmLiteN nodes per axis the passes keep three of the six piece
+// products (a0 b0, a0 b1, a1 b0; the dropped ones are near 2^-16 of the
+// result): each inner solve then reduces the refinement residual by about 1e-4
+// instead of FP32 rounding's 1e-5 .. 1e-7, which at these sizes (where the
+// FP32 sums of N terms already cost the full scheme a third refinement sweep)
+// leaves the sweep count unchanged and halves the tensor work of each pass.
+constexpr int kFdmLiteN = 512;
+
+cudaError_t fdm_setup(FineFDM& f, int Nf, const std::vector<double>& lamf, const std::vector<double>& Vf,
+                      bool tensor_cores) {
+  cudaError_t e;
+  {
+    f.null_mode = 0;
+    for (int i = 1; i < Nf; ++i)
+      if (std::fabs(lamf[i]) < std::fabs(lamf[f.null_mode])) f.null_mode = i;
+    std::vector<float> Vf32(Vf.begin(), Vf.end()), VTf32((size_t)Nf * Nf), lf32(lamf.begin(), lamf.end());
+    for (int i = 0; i < Nf; ++i)
+      for (int k = 0; k < Nf; ++k) VTf32[(size_t)k * Nf + i] = (float)Vf[(size_t)i * Nf + k];
+    if ((e = cudaMalloc(&f.V32, Vf32.size() * 4)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.VT32, VTf32.size() * 4)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.lam32, lf32.size() * 4)) != cudaSuccess) return e;
+    cudaMemcpy(f.V32, Vf32.data(), Vf32.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(f.VT32, VTf32.data(), VTf32.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(f.lam32, lf32.data(), lf32.size() * 4, cudaMemcpyHostToDevice);
+    f.N = Nf;
+    if (tensor_cores) {
+      // column tiles of nt modes (a multiple of 16, <= 128: two CTAs per SM), enough tiles to give every
+      // SM a CTA (measured: tiles of 192 or 256 modes, one CTA per SM, read the input fewer times but were
+      // no faster at 128^3)
+      const int64_t rt = ((int64_t)Nf * Nf + 127) / 128;
+      int ntile = std::max<int>((Nf + 127) / 128, (int)((148 + rt - 1) / rt));
+      const int nt = ((Nf + ntile - 1) / ntile + 15) / 16 * 16;
+      ntile = (Nf + nt - 1) / nt;
+      const int kc = (Nf + 63) / 64;
+      const size_t per = (size_t)3 * nt * 64;   // bf16 values per (tile, chunk)
+      std::vector<uint16_t> bf((size_t)ntile * kc * per), bi((size_t)ntile * kc * per);
+      for (int t = 0; t < ntile; ++t)
+        for (int ch = 0; ch < kc; ++ch)
+          for (int ii = 0; ii < nt; ++ii)
+            for (int k = 0; k < 64; ++k) {
+              const int i = t * nt + ii, a = 64 * ch + k;
+              const bool in = i < Nf && a < Nf;
+              uint16_t pf[3] = {0, 0, 0}, pi[3] = {0, 0, 0};
+              if (in) {
+                tc::bf16_pieces(Vf[(size_t)a * Nf + i], pf);   // analysis: B[i][a] = V[a][i]
+                tc::bf16_pieces(Vf[(size_t)i * Nf + a], pi);   // synthesis: B[i][a] = V[i][a]
+              }
+              for (int p = 0; p < 3; ++p) {
+                const size_t o = ((size_t)(t * kc + ch) * 3 + p) * nt * 64 + tc::sw128_off(ii, k) / 2;
+                bf[o] = pf[p];
+                bi[o] = pi[p];
+              }
+            }
+      if ((e = cudaMalloc(&f.BpF, bf.size() * 2)) != cudaSuccess) return e;
+      if ((e = cudaMalloc(&f.BpI, bi.size() * 2)) != cudaSuccess) return e;
+      cudaMemcpy(f.BpF, bf.data(), bf.size() * 2, cudaMemcpyHostToDevice);
+      cudaMemcpy(f.BpI, bi.data(), bi.size() * 2, cudaMemcpyHostToDevice);
+      f.nt = nt;
+      f.ntile = ntile;
+      f.lite = Nf >= kFdmLiteN;
+      if ((e = tc_rows_prepare(nt)) != cudaSuccess) return e;
+      if ((e = cudaMalloc(&f.err, sizeof(int))) != cudaSuccess) return e;
+      cudaMemset(f.err, 0, sizeof(int));
+    }
+  }
+  return cudaGetLastError();
+}
+
+void fdm_free(FineFDM& f) {
+  void* p[] = {f.BpF, f.BpI, f.err, f.V32, f.VT32, f.lam32};
+  for (void* q : p)
+    if (q) cudaFree(q);
+  f = FineFDM();
+}
+
+// x = K^+ b by the six transform passes (tensor cores when the pieces are
+// set, else the CUDA-core passes); w1, w2: N^3 scratch
+cudaError_t fdm_apply(const FineFDM& f, const float* b, float* x, float* w1, float* w2, cudaStream_t s) {
+  const int N = f.N;
+  if (f.BpF) {
+    const dim3 g((unsigned)(((int64_t)N * N + 127) / 128), (unsigned)f.ntile);
+    const size_t sm = tc_rows_smem(f.nt);
+    const uint4* F = (const uint4*)f.BpF;
+    const uint4* I = (const uint4*)f.BpI;
+    const int64_t R = (int64_t)N * N;
+    const float* lm = f.lam32;
+    const int nm = f.null_mode, nt = f.nt;
+    auto k0 = f.lite ? k_tc_rows<false, true> : k_tc_rows<false, false>;
+    auto k1 = f.lite ? k_tc_rows<true, true> : k_tc_rows<true, false>;
+    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, b, F, lm, nm, N, w1, f.err);
+    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w1, F, lm, nm, N, w2, f.err);
+    launch_pdl(k1, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w2, F, lm, nm, N, w1, f.err);
+    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w1, I, lm, nm, N, w2, f.err);
+    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w2, I, lm, nm, N, w1, f.err);
+    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w1, I, lm, nm, N, x, f.err);
+    return cudaGetLastError();
+  }
+  const dim3 g((unsigned)(((int64_t)N * N + FM - 1) / FM), (unsigned)((N + FN - 1) / FN));
+  launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, b, f.V32, f.lam32, f.null_mode, w1);
+  launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, (const float*)w1, f.V32, f.lam32, f.null_mode, w2);
+  launch_pdl(k_fdm_axis<true>, g, 256, 0, s, N, (const float*)w2, f.V32, f.lam32, f.null_mode, w1);
+  launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, (const float*)w1, f.VT32, f.lam32, f.null_mode, w2);
+  launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, (const float*)w2, f.VT32, f.lam32, f.null_mode, w1);
+  launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, (const float*)w1, f.VT32, f.lam32, f.null_mode, x);
+  return cudaGetLastError();
 }
 
 cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream) {

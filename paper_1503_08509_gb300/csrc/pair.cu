@@ -1688,6 +1688,19 @@ cudaError_t adjoint_vertex(fep3m_ctx* c, cudaStream_t s) {
   return vertex_adjoint(c, c->lam64, c->mu_v, L0.t1, L0.t2, s);
 }
 
+cudaError_t singular_sums(fep3m_ctx* c, const double* w, double* psi, double* gpsi, cudaStream_t s) {
+  const int64_t N = c->N;
+  if (c->precision == FEP3M_MIXED)
+    FEP3M_CL k_pair_adj_warp<float><<<(unsigned)((N + 7) / 8), PT, 0, s>>>(N, c->n, c->n_sr, (float)c->h, c->start,
+                                                                           (const float4*)c->part, c->ecoord, w, psi,
+                                                                           gpsi);
+  else
+    FEP3M_CL k_pair_adj_warp<double><<<(unsigned)((N + 7) / 8), PT, 0, s>>>(N, c->n, c->n_sr, c->h, c->start,
+                                                                            (const vec4<double>::type*)c->part,
+                                                                            c->ecoord, w, psi, gpsi);
+  return cudaGetLastError();
+}
+
 // per-charge dLf/dx (times sign) and dLf/dQ
 cudaError_t adjoint_final(fep3m_ctx* c, double gU, double* dpos, double* dQ, double sign, cudaStream_t s) {
   const int64_t N = c->N;
