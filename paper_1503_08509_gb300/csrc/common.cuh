@@ -123,7 +123,6 @@ struct FineFDM {
   void* BpF = nullptr;
   void* BpI = nullptr;
   int nt = 0, ntile = 0;
-  bool lite = false;          // three of the six piece products (large N; see fdm_setup)
   int* err = nullptr;         // device flag: a bounded wait gave up
 };
 

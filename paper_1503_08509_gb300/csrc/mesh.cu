@@ -144,7 +144,7 @@ __global__ void k_vertex_density(int n, const T* __restrict__ C, T* __restrict__
 // integers (the element entries are 13/120, 1/60, 3/10 and 3/40), so that the
 // load vector carries no systematic rounding of the weights (it would scale
 // each charge's own smooth potential against its screen and bias U); the
-// caller divides by 120^3 in FP64.
+// last pass divides by 120^3 in FP64.
 template <class T>
 __device__ __forceinline__ int mpq_row(int g, int n, int vtx[3], T wgt[3]) {
   const double s = sizeof(T) == 4 ? 120.0 : 1.0;
@@ -161,26 +161,28 @@ __device__ __forceinline__ int mpq_row(int g, int n, int vtx[3], T wgt[3]) {
   return 2;
 }
 
-// b = 4 pi (Mpq (x) Mpq (x) Mpq) r, accumulated in the vertex density's type
-// (FP32: integer weights, mpq_row); grid (ceil(N / 128), N, N)
-template <class T>
-__global__ void k_load_vector(int n, const T* __restrict__ rv, double* __restrict__ b) {
-  const int N = 3 * n;
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ix >= N) return;
-  const int iy = blockIdx.y, iz = blockIdx.z;
-  int vx[3], vy[3], vz[3];
-  T wx[3], wy[3], wz[3];
-  const int nx = mpq_row<T>(ix, n, vx, wx), ny = mpq_row<T>(iy, n, vy, wy), nz = mpq_row<T>(iz, n, vz, wz);
-  T acc = T(0);
-  for (int c = 0; c < nz; ++c)
-    for (int bb = 0; bb < ny; ++bb) {
-      const T wyz = wy[bb] * wz[c];
-      const int64_t row = (int64_t)n * (vy[bb] + (int64_t)n * vz[c]);
-      for (int a = 0; a < nx; ++a) acc += wx[a] * wyz * rv[vx[a] + row];
-    }
-  const double scale = sizeof(T) == 4 ? 4.0 * M_PI / (120.0 * 120.0 * 120.0) : 4.0 * M_PI;
-  b[ix + (int64_t)N * (iy + (int64_t)N * iz)] = scale * (double)acc;
+// One axis of b = 4 pi (Mpq (x) Mpq (x) Mpq) r, three separable passes (x, y,
+// then z): out[.., g, ..] = scale sum_k w_k in[.., v_k, ..], vertices v_k of
+// order-3 node g along `axis` (mpq_row; FP32: integer weights, the caller's
+// scale divides by 120^3 at the last pass).  d[3]: the output's extents (3n
+// along the axes done, n along the others).
+template <class Tin, class Tout>
+__global__ void k_load_axis(int n, int axis, int d0, int d1, int d2, const Tin* __restrict__ in,
+                            Tout* __restrict__ out, double scale) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= (int64_t)d0 * d1 * d2) return;
+  int idx[3] = {(int)(g % d0), (int)((g / d0) % d1), (int)(g / ((int64_t)d0 * d1))};
+  int din[3] = {d0, d1, d2};
+  din[axis] = n;
+  const int64_t st[3] = {1, din[0], (int64_t)din[0] * din[1]};
+  int vtx[3];
+  Tin w[3];
+  const int k = mpq_row<Tin>(idx[axis], n, vtx, w);
+  idx[axis] = 0;
+  const int64_t base = idx[0] * st[0] + idx[1] * st[1] + idx[2] * st[2];
+  Tin acc = Tin(0);
+  for (int j = 0; j < k; ++j) acc += w[j] * in[base + vtx[j] * st[axis]];
+  out[g] = (Tout)(scale * (double)acc);
 }
 
 // Coarsest-level exact solve x = V (Dinv o (V^T b)) (V the 1-D generalized
@@ -1061,7 +1063,7 @@ __global__ void __launch_bounds__(256) k_fdm_axis(int N, const float* __restrict
 // that gave up.
 constexpr int FT_THREADS = 256;
 
-template <bool SCALE, bool LITE = false>
+template <bool SCALE>
 __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int cb, int ce, int nt,
                                                          const float* __restrict__ in, const uint4* __restrict__ Bp,
                                                          const float* __restrict__ lam, int null_mode, int N,
@@ -1075,8 +1077,11 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int cb
   uint64_t* mbar = (uint64_t*)(tiles + 3 * 16384 + 3 * bpiece);
   uint32_t* tslot = (uint32_t*)(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int64_t r0 = (int64_t)blockIdx.x * 128;
-  const int tile = cb / nt + (int)blockIdx.y, n0 = tile * nt;
+  // one-dimensional grid, column tile fastest: the CTAs that read the same 128
+  // rows run together, so each row tile comes from DRAM once and from L2 after
+  const int ntl = (ce + nt - 1) / nt - cb / nt;
+  const int64_t r0 = (int64_t)(blockIdx.x / ntl) * 128;
+  const int tile = cb / nt + (int)(blockIdx.x % ntl), n0 = tile * nt;
   const int kc = (K + 63) / 64;
   uint32_t ncols = 32;
   while (ncols < 2u * (uint32_t)nt) ncols <<= 1;
@@ -1116,8 +1121,7 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int cb
   load_units(0);
   bool failed = false;
   for (int c = 0; c < kc; ++c) {
-    for (int i = tid; i < (LITE ? 2 : 3) * (int)(bpiece / 16); i += FT_THREADS)
-      cp_async16(tb + 16 * i, bsrc + (size_t)c * 3 * (bpiece / 16) + i);
+    for (int i = tid; i < 3 * (int)(bpiece / 16); i += FT_THREADS) cp_async16(tb + 16 * i, bsrc + (size_t)c * 3 * (bpiece / 16) + i);
     cp_async_commit();
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1128,7 +1132,7 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int cb
       const uint32_t off = sw128_off(row, 8 * g);
       sts128(tl + off, p0);
       sts128(tl + 16384 + off, p1);
-      if (!LITE) sts128(tl + 32768 + off, p2);
+      sts128(tl + 32768 + off, p2);
     }
     cp_async_wait_all();
     fence_async_smem();
@@ -1141,11 +1145,9 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int cb
         umma_bf16(tmem, umma_desc(a), umma_desc(b), idesc, acc);                                 // a0 b0
         umma_bf16(tmem + lo_off, umma_desc(a), umma_desc(b + bpiece), idesc, acc);               // a0 b1
         umma_bf16(tmem + lo_off, umma_desc(a + 16384), umma_desc(b), idesc, 1u);                 // a1 b0
-        if (!LITE) {
-          umma_bf16(tmem + lo_off, umma_desc(a), umma_desc(b + 2 * bpiece), idesc, 1u);          // a0 b2
-          umma_bf16(tmem + lo_off, umma_desc(a + 16384), umma_desc(b + bpiece), idesc, 1u);      // a1 b1
-          umma_bf16(tmem + lo_off, umma_desc(a + 32768), umma_desc(b), idesc, 1u);               // a2 b0
-        }
+        umma_bf16(tmem + lo_off, umma_desc(a), umma_desc(b + 2 * bpiece), idesc, 1u);            // a0 b2
+        umma_bf16(tmem + lo_off, umma_desc(a + 16384), umma_desc(b + bpiece), idesc, 1u);        // a1 b1
+        umma_bf16(tmem + lo_off, umma_desc(a + 32768), umma_desc(b), idesc, 1u);                 // a2 b0
       }
       umma_commit(smem_u32(mbar));
     }
@@ -1435,15 +1437,13 @@ cudaError_t tc_rows_prepare(int nt) {
   const int sm = (int)tc_rows_smem(256);
   cudaError_t e = cudaFuncSetAttribute(k_tc_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_rows<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_rows<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   return e;
 }
 
 // out[(i - cb) R + r] = sum_{a < K} in[r K + a] B[i][a] for the columns cb <= i < ce
 cudaError_t tc_rows_gemm(int64_t R, int K, int cb, int ce, int nt, const float* in, const void* Bp, float* out,
                          int* err, cudaStream_t s) {
-  const dim3 g((unsigned)((R + 127) / 128), (unsigned)((ce + nt - 1) / nt - cb / nt));
+  const dim3 g((unsigned)((R + 127) / 128 * ((ce + nt - 1) / nt - cb / nt)));
   FEP3M_CL k_tc_rows<false><<<g, FT_THREADS, tc_rows_smem(nt), s>>>(R, K, cb, ce, nt, in, (const uint4*)Bp,
                                                                     nullptr, -1, 0, out, err);
   return cudaGetLastError();
@@ -2157,14 +2157,6 @@ static void solver_plan_free(Solver* c) {
 // FP32 eigenbasis for the CUDA-core passes and, with tensor_cores, its bf16
 // pieces in the layout of the tensor-core row GEMM (column tiles of nt modes,
 // chunks of 64 nodes).  Used by the order-3 fine level and the order-p mesh.
-// From N = kFdmLiteN nodes per axis the passes keep three of the six piece
-// products (a0 b0, a0 b1, a1 b0; the dropped ones are near 2^-16 of the
-// result): each inner solve then reduces the refinement residual by about 1e-4
-// instead of FP32 rounding's 1e-5 .. 1e-7, which at these sizes (where the
-// FP32 sums of N terms already cost the full scheme a third refinement sweep)
-// leaves the sweep count unchanged and halves the tensor work of each pass.
-constexpr int kFdmLiteN = 512;
-
 cudaError_t fdm_setup(FineFDM& f, int Nf, const std::vector<double>& lamf, const std::vector<double>& Vf,
                       bool tensor_cores) {
   cudaError_t e;
@@ -2216,7 +2208,6 @@ cudaError_t fdm_setup(FineFDM& f, int Nf, const std::vector<double>& lamf, const
       cudaMemcpy(f.BpI, bi.data(), bi.size() * 2, cudaMemcpyHostToDevice);
       f.nt = nt;
       f.ntile = ntile;
-      f.lite = Nf >= kFdmLiteN;
       if ((e = tc_rows_prepare(nt)) != cudaSuccess) return e;
       if ((e = cudaMalloc(&f.err, sizeof(int))) != cudaSuccess) return e;
       cudaMemset(f.err, 0, sizeof(int));
@@ -2237,15 +2228,15 @@ void fdm_free(FineFDM& f) {
 cudaError_t fdm_apply(const FineFDM& f, const float* b, float* x, float* w1, float* w2, cudaStream_t s) {
   const int N = f.N;
   if (f.BpF) {
-    const dim3 g((unsigned)(((int64_t)N * N + 127) / 128), (unsigned)f.ntile);
+    const dim3 g((unsigned)(((int64_t)N * N + 127) / 128 * f.ntile));
     const size_t sm = tc_rows_smem(f.nt);
     const uint4* F = (const uint4*)f.BpF;
     const uint4* I = (const uint4*)f.BpI;
     const int64_t R = (int64_t)N * N;
     const float* lm = f.lam32;
     const int nm = f.null_mode, nt = f.nt;
-    auto k0 = f.lite ? k_tc_rows<false, true> : k_tc_rows<false, false>;
-    auto k1 = f.lite ? k_tc_rows<true, true> : k_tc_rows<true, false>;
+    auto k0 = k_tc_rows<false>;
+    auto k1 = k_tc_rows<true>;
     launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, b, F, lm, nm, N, w1, f.err);
     launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w1, F, lm, nm, N, w2, f.err);
     launch_pdl(k1, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w2, F, lm, nm, N, w1, f.err);
@@ -2317,14 +2308,29 @@ cudaError_t assemble_forward(fep3m_ctx* c) {
     FEP3M_CL k_elem_coeff<float><<<grid_for(ne), TPB, 0, s>>>(ne, c->start, c->count, (const float4*)c->part, (float*)c->C);
     FEP3M_CL k_vertex_density<float><<<grid_for(ne), TPB, 0, s>>>(n, (const float*)c->C, (float*)c->rv,
                                                                    (float*)c->Cv);
-    FEP3M_CL k_load_vector<float><<<dim3((3 * n + 127) / 128, 3 * n, 3 * n), 128, 0, s>>>(n, (const float*)c->rv,
-                                                                                         c->b64);
   } else {
     FEP3M_CL k_elem_coeff<double><<<grid_for(ne), TPB, 0, s>>>(ne, c->start, c->count, (const vec4<double>::type*)c->part, (double*)c->C);
     FEP3M_CL k_vertex_density<double><<<grid_for(ne), TPB, 0, s>>>(n, (const double*)c->C, (double*)c->rv,
                                                                     (double*)c->Cv);
-    FEP3M_CL k_load_vector<double><<<dim3((3 * n + 127) / 128, 3 * n, 3 * n), 128, 0, s>>>(n, (const double*)c->rv,
-                                                                                          c->b64);
+  }
+  // the load vector in three separable passes through the forward solver's
+  // fine-level scratch (free until its solve, which follows on this stream)
+  const Level& L0 = c->solv[0].mg.lv[0];
+  const int N3 = 3 * n;
+  if (c->precision == FEP3M_MIXED) {
+    float *t1 = (float*)L0.t1, *t2 = (float*)L0.t2;
+    FEP3M_CL k_load_axis<float, float><<<grid_for((int64_t)N3 * n * n), TPB, 0, s>>>(n, 0, N3, n, n, (const float*)c->rv,
+                                                                                    t1, 1.0);
+    FEP3M_CL k_load_axis<float, float><<<grid_for((int64_t)N3 * N3 * n), TPB, 0, s>>>(n, 1, N3, N3, n, t1, t2, 1.0);
+    FEP3M_CL k_load_axis<float, double><<<grid_for((int64_t)N3 * N3 * N3), TPB, 0, s>>>(
+        n, 2, N3, N3, N3, t2, c->b64, 4.0 * M_PI / (120.0 * 120.0 * 120.0));
+  } else {
+    double *t1 = (double*)L0.t1, *t2 = (double*)L0.t2;
+    FEP3M_CL k_load_axis<double, double><<<grid_for((int64_t)N3 * n * n), TPB, 0, s>>>(n, 0, N3, n, n,
+                                                                                      (const double*)c->rv, t1, 1.0);
+    FEP3M_CL k_load_axis<double, double><<<grid_for((int64_t)N3 * N3 * n), TPB, 0, s>>>(n, 1, N3, N3, n, t1, t2, 1.0);
+    FEP3M_CL k_load_axis<double, double><<<grid_for((int64_t)N3 * N3 * N3), TPB, 0, s>>>(n, 2, N3, N3, N3, t2, c->b64,
+                                                                                        4.0 * M_PI);
   }
   return cudaGetLastError();
 }
