@@ -35,8 +35,8 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_pair_screen launch and of one transform pass of the
 # mesh solve (k_tc_rows) on this workload, from the ncu captures summarised in profiles/ (None until one is
 # taken of the current kernel)
-PAIR_DRAM_BYTES = 2247680
-PASS_DRAM_BYTES = 3647744
+PAIR_DRAM_BYTES = None
+PASS_DRAM_BYTES = None
 
 
 def parse():

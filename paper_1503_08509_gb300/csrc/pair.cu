@@ -352,7 +352,8 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
     }
   }
   __syncthreads();
-  // (1) extended vertex field
+  // (1) extended vertex field (unrolled: the gathers of several entries in flight)
+#pragma unroll 4
   for (int i = tid; i < SW * SW * SW; i += NT) {
     const int sx = i % SW, sy = (i / SW) % SW, sz = i / (SW * SW);
     const int tx = sx < SF ? 3 : (sx < SF + BX ? 2 : 1);     // allowed corners (bit0: 0, bit1: 1)
@@ -408,26 +409,13 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
     tc_fence_after();
     const uint32_t tmem = *tslot;
     // The field at node 0 (the one absolute column of the relative table, the
-    // element's potential level), in double-float arithmetic on the CUDA cores
-    // from the table's hi + lo floats (H0): its FP32 tensor-core sum would be
-    // rounded alike in every element.  Eight threads per element, combined in
-    // the epilogue.
+    // element's potential level) is summed on the CUDA cores from the A values
+    // each thread splits anyway, with the table's hi + lo floats (H0) in two
+    // FP32 sums rounded to nearest (the tensor cores' accumulation would round
+    // it alike in every element, and U adds that up); eight partial sums per
+    // element, combined in the epilogue.
     __shared__ float2 s0p[(PTC / 64) * BE];
-    {
-      const int l0 = tid & 63, g0 = tid >> 6;
-      const int lam0 = (l0 % BX) + SW * (((l0 / BX) % BY) + SW * (l0 / (BX * BY)));
-      float sh = 0.f, sl = 0.f;
-      for (int o = g0; o < no3; o += NT / 64) {
-        const float a = (float)R[otab[o] + lam0];
-        const float2 hh = H0[o];
-        const float p = a * hh.x;
-        const float e = fmaf(a, hh.y, fmaf(a, hh.x, -p));
-        const float t = sh + p, z = t - sh;
-        sl += ((sh - (t - z)) + (p - z)) + e;
-        sh = t;
-      }
-      s0p[g0 * BE + l0] = make_float2(sh, sl);
-    }
+    float s0h = 0.f, s0l = 0.f;
     const int l = tid & 63, g = tid >> 6;   // this thread's A unit: row l, chunk offsets 8 g .. 8 g + 7
     const int lam = (l % BX) + SW * (((l / BX) % BY) + SW * (l / (BX * BY)));
     const uint32_t aoff = sw128_off(l, 8 * g);
@@ -448,6 +436,11 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
         const float xa = o < no3 ? (float)R[otab[o] + lam] : 0.f;
         const float xb = o + 1 < no3 ? (float)R[otab[o + 1] + lam] : 0.f;
         bf16_split2(xa, xb, p0[j], p1[j], p2[j]);
+        if (o + 1 < no3) {
+          const float4 h2 = *reinterpret_cast<const float4*>(H0 + o);   // H0[o], H0[o + 1]
+          s0h = fmaf(xa, h2.x, fmaf(xb, h2.z, s0h));
+          s0l = fmaf(xa, h2.y, fmaf(xb, h2.w, s0l));
+        }
       }
       sts128(tl + aoff, p0);
       sts128(tl + 8192 + aoff, p1);
@@ -495,6 +488,8 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
       (void)mbar_wait(smem_u32(mbar), 0u);
       (void)mbar_wait(smem_u32(mbar), 1u);
     }
+    s0p[g * BE + l] = make_float2(s0h, s0l);
+    __syncthreads();
     tc_fence_after();
     if (!failed && q4 < 2) {
       uint32_t vl[16];
@@ -503,16 +498,14 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
       const int row = 32 * q4 + (tid & 31);
       float* drow = (float*)Gscr + (int64_t)blockIdx.x * (BE * 64) + row * 64 + 16 * cg;
       float c0 = (hsum[0] - hcmp[0]) + __uint_as_float(vl[0]);
-      if (cg == 0) {   // column 0 from the double-float sums
-        float sh = 0.f, sl = 0.f;
+      if (cg == 0) {   // column 0 from the CUDA-core sums
+        double sum = 0.0;
 #pragma unroll
         for (int q = 0; q < PTC / 64; ++q) {
           const float2 v = s0p[q * BE + row];
-          const float t = sh + v.x, z = t - sh;
-          sl += ((sh - (t - z)) + (v.x - z)) + v.y;
-          sh = t;
+          sum += (double)v.x + (double)v.y;
         }
-        c0 = (float)((double)sh + (double)sl);
+        c0 = (float)sum;
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
@@ -696,6 +689,7 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
           const int j0 = hs[h0], j1 = hs[h0 + nb];
           const T ddy = T(r % nb - n_sr), ddz = T(r / nb - n_sr);
           T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+#pragma unroll 4
           for (int j = j0; j < j1; ++j) {
             const V4 pj = stg[j];
             const T ddx = T((int)sxb[j] - cx);
