@@ -75,6 +75,17 @@ enum { FEP3M_FP64 = 0, FEP3M_MIXED = 1 };
 #define FEP3M_ONE_ELEMENT 8u   /* one-element screens (Sec. 5.3): weights on the
                                   interior nodes of the charge's element only,
                                   the moments l < q - 1; needs q >= 2           */
+#define FEP3M_DIRICHLET 16u    /* the box [0, L]^3 with Dirichlet data Phi = g on
+                                  its boundary (Sec. "Alternate boundary
+                                  conditions", Eq. bcadjust) instead of the
+                                  periodic cube: charges must lie in the box,
+                                  need not be neutral, and each short-range
+                                  block is cut off at the box faces (no
+                                  images).  g is set by fep3m_set_boundary
+                                  (default 0, a grounded box).  q = 1 only, no
+                                  FEP3M_MULTIGRID; potentials and energy
+                                  (fep3m_compute with force = NULL; fep3m_vjp
+                                  returns FEP3M_EINVAL)                        */
 
 typedef struct fep3m_ctx fep3m_ctx;
 
@@ -119,7 +130,7 @@ typedef struct {
   int table_pad;       /* Dirichlet box margin, elements, beyond the kept table;
                           0 -> 4 (q = 1) or 2 (q >= 2); at most 8               */
   unsigned flags;      /* FEP3M_NEUTRALIZE, FEP3M_CUDA_CORES,
-                          FEP3M_MULTIGRID                                        */
+                          FEP3M_MULTIGRID, FEP3M_ONE_ELEMENT, FEP3M_DIRICHLET   */
 } fep3m_config;
 
 typedef struct {
@@ -162,11 +173,14 @@ typedef struct {
 int fep3m_create(const fep3m_config* cfg, void* cuda_stream, fep3m_ctx** out);
 
 /* Charge positions (N x 3, host or device, any real values: they are wrapped
- * into [0, L)) and charges (N, host or device).  Bins the charges into
+ * into [0, L); in a FEP3M_DIRICHLET box they must lie in [0, L]^3, a charge
+ * on the faces x = L belonging to the last element) and charges (N, host or
+ * device).  Bins the charges into
  * elements (stable counting sort) and stores the sorted SoA copy; grows the
  * context's scratch when N exceeds earlier calls.  N >= 1.  Returns
- * FEP3M_EINVAL for non-finite input and FEP3M_ENOTNEUTRAL for a net charge
- * (unless FEP3M_NEUTRALIZE); either leaves no particles set.  Synchronises
+ * FEP3M_EINVAL for non-finite input (or, in a box, a charge outside it) and
+ * FEP3M_ENOTNEUTRAL for a net charge (periodic cube, unless
+ * FEP3M_NEUTRALIZE); either leaves no particles set.  Synchronises
  * the stream.                                                                */
 int fep3m_set_particles(fep3m_ctx* ctx, int64_t N, const double* pos, const double* Q);
 
@@ -210,14 +224,33 @@ int fep3m_get_binning(const fep3m_ctx* ctx, int32_t* perm, int32_t* count,
  *   phi_mesh [(3n)^3] mesh potential nodal values (physical units, mean zero)
  *   Phi^sm / Phi^sing / Phi^scr parts are not kept separately.
  * For q >= 2: C [n^3 x (q+1)^3] (screen node i + (q+1)(j + (q+1) k)), b and
- * phi_mesh [(p n)^3] on the order-p mesh (index ix + pn iy + (pn)^2 iz).     */
+ * phi_mesh [(p n)^3] on the order-p mesh (index ix + pn iy + (pn)^2 iz).
+ * FEP3M_DIRICHLET box: b and phi_mesh on the (3n + 1)^3 nodes of the box,
+ * index ix + (3n+1) iy + (3n+1)^2 iz, node (ix, iy, iz) at (ix, iy, iz) h / 3;
+ * b is the box integral (the part of a screen outside the box is not a load);
+ * phi_mesh holds the adjusted boundary values g - Phi^sr on the boundary
+ * nodes (Eq. bcadjust) and is not shifted.                                   */
 int fep3m_get_mesh(const fep3m_ctx* ctx, double* C, double* b, double* phi_mesh);
 
 /* Solve the periodic FE system K phi = b - (sum b) w / sum w, int phi = 0,
  * for a caller right-hand side b ((p n)^3, host or device) with the context's
  * mesh solver (precision as configured); writes phi (physical units).  Used
- * to test the solver alone.                                                 */
+ * to test the solver alone.  FEP3M_DIRICHLET box: b and phi on the (3n+1)^3
+ * box nodes (as fep3m_get_mesh); solves K phi = b at the interior nodes with
+ * phi = g (fep3m_set_boundary, no adjustment: no charges enter) on the
+ * boundary nodes.                                                           */
 int fep3m_solve_mesh(fep3m_ctx* ctx, const double* b, double* phi);
+
+/* Dirichlet data of a FEP3M_DIRICHLET box: g at the (3n + 1)^3 nodes of the
+ * order-3 box mesh (host or device, float64, index ix + (3n+1) iy +
+ * (3n+1)^2 iz, node (ix, iy, iz) at (ix, iy, iz) h / 3); only the boundary
+ * nodes (an index 0 or 3n) are read, and the FE solution takes their values
+ * interpolated by the order-3 basis on each face (Sec. "Alternate boundary
+ * conditions": the mesh problem's boundary values are g less the short-range
+ * potential there, Eq. bcadjust, so that Phi = g at the boundary nodes).
+ * Copied; kept until the next call.  FEP3M_EINVAL for a periodic context or
+ * non-finite data (the previous data are then kept).                       */
+int fep3m_set_boundary(fep3m_ctx* ctx, const double* g);
 
 /* The kept FE basis-screen table (h = 1): nodal values on [-(n_sr+1), n_sr+1]^3
  * in steps of 1/3, (6 n_sr + 7)^3 values, index ix + s iy + s^2 iz with

@@ -121,6 +121,20 @@ def boundary_nodes(n, h):
     return onb, idx * (h / P), el, idx / P - el
 
 
+def solve_interior(b, phiB, M1, K1):
+    """The Galerkin Dirichlet problem: K phi = b at the interior nodes with phi = phiB on
+    the boundary nodes (phiB's interior entries zero), K = K1 (x) M1 (x) M1 + M1 (x) K1
+    (x) M1 + M1 (x) M1 (x) K1; exact, by fast diagonalisation of the interior block."""
+    rhs = b - (tables.kron_apply(K1, M1, M1, phiB) + tables.kron_apply(M1, K1, M1, phiB)
+               + tables.kron_apply(M1, M1, K1, phiB))
+    lam, V = scipy.linalg.eigh(K1[1:-1, 1:-1], M1[1:-1, 1:-1])
+    rh = tables.kron_apply(V.T, V.T, V.T, rhs[1:-1, 1:-1, 1:-1])
+    rh /= lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
+    phi_mesh = phiB.copy()
+    phi_mesh[1:-1, 1:-1, 1:-1] = tables.kron_apply(V, V, V, rh)
+    return phi_mesh
+
+
 def forward(pos, Q, L, n, g, n_sr=3, adjust=True):
     """Phi_i at the charges for Dirichlet data g (a function of (M, 3) points), with the
     intermediates.  adjust=False sets Phi^sm = g on the boundary instead of Eq. bcadjust."""
@@ -138,13 +152,7 @@ def forward(pos, Q, L, n, g, n_sr=3, adjust=True):
         gb = gb - short_range(bpts, bel, bloc, bins, Q, n, n_sr)
     phiB = np.zeros(onb.shape)
     phiB[onb] = gb
-    rhs = b - (tables.kron_apply(K1, M1, M1, phiB) + tables.kron_apply(M1, K1, M1, phiB)
-               + tables.kron_apply(M1, M1, K1, phiB))
-    lam, V = scipy.linalg.eigh(K1[1:-1, 1:-1], M1[1:-1, 1:-1])
-    rh = tables.kron_apply(V.T, V.T, V.T, rhs[1:-1, 1:-1, 1:-1])
-    rh /= lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
-    phi_mesh = phiB.copy()
-    phi_mesh[1:-1, 1:-1, 1:-1] = tables.kron_apply(V, V, V, rh)
+    phi_mesh = solve_interior(b, phiB, M1, K1)
     # evaluation at the charges
     t = bins['delta'] / h + 0.5
     lv = [fe1d.lagrange_values(P, t[:, a]) for a in range(3)]

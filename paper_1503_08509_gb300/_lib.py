@@ -12,6 +12,7 @@ FEP3M_NEUTRALIZE = 1
 FEP3M_CUDA_CORES = 2
 FEP3M_MULTIGRID = 4
 FEP3M_ONE_ELEMENT = 8
+FEP3M_DIRICHLET = 16
 
 
 class Config(ctypes.Structure):
@@ -44,6 +45,7 @@ SIGNATURES = {
     "fep3m_get_mesh": (ctypes.c_int, [P, P, P, P]),
     "fep3m_solve_mesh": (ctypes.c_int, [P, P, P]),
     "fep3m_get_table": (ctypes.c_int, [P, P]),
+    "fep3m_set_boundary": (ctypes.c_int, [P, P]),
     "fep3m_mesh_eigenbasis": (ctypes.c_int, [ctypes.c_int, P, P]),
     "fep3m_mesh_eigenbasis_order": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, P]),
     "fep3m_screen_type_table": (ctypes.c_int, [ctypes.c_int] * 6 + [P]),

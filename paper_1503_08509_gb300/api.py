@@ -46,21 +46,26 @@ class FEP3M:
     preconditioned CG; q = 1).
     q: screen order 1..4 (mesh order q + 2); q >= 2 computes potentials and
     energy (no forces).  one_element: one-element screens (q >= 2).
+    dirichlet: the box [0, L]^3 with Dirichlet data (set_boundary; default 0)
+    instead of the periodic cube; q = 1, potentials and energy.
     """
 
     def __init__(self, L, n_el, n_sr=3, precision="fp64", mg_rtol=0.0, mg_max_cycles=0, neutralize=False,
-                 table_pad=0, device=None, stream=None, tensor_cores=True, solver="fdm", q=1, one_element=False):
+                 table_pad=0, device=None, stream=None, tensor_cores=True, solver="fdm", q=1, one_element=False,
+                 dirichlet=False):
         lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.L, self.n_el, self.n_sr, self.q = float(L), int(n_el), int(n_sr), int(q)
         self.precision = precision
+        self.dirichlet = bool(dirichlet)
         cfg = _lib.Config(L=self.L, n_el=self.n_el, q=self.q, n_sr=self.n_sr,
                           precision=_lib.FEP3M_MIXED if precision == "mixed" else _lib.FEP3M_FP64,
                           mg_rtol=mg_rtol, mg_max_cycles=mg_max_cycles, table_pad=table_pad,
                           flags=(_lib.FEP3M_NEUTRALIZE if neutralize else 0) |
                           (0 if tensor_cores else _lib.FEP3M_CUDA_CORES) |
                           (_lib.FEP3M_MULTIGRID if solver == "multigrid" else 0) |
-                          (_lib.FEP3M_ONE_ELEMENT if one_element else 0))
+                          (_lib.FEP3M_ONE_ELEMENT if one_element else 0) |
+                          (_lib.FEP3M_DIRICHLET if dirichlet else 0))
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             h = ctypes.c_void_p()
@@ -83,7 +88,21 @@ class FEP3M:
 
     @property
     def nodes(self):
+        if self.dirichlet:
+            return (3 * self.n_el + 1) ** 3
         return ((self.q + 2) * self.n_el) ** 3
+
+    def node_points(self):
+        """Coordinates (nodes x 3) of the box mesh's nodes, index ix + (3n+1) iy + (3n+1)^2 iz."""
+        m = 3 * self.n_el + 1
+        t = np.arange(m) * (self.L / (3 * self.n_el))
+        z, y, x = np.meshgrid(t, t, t, indexing="ij")
+        return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+
+    def set_boundary(self, g):
+        """Dirichlet data at the box mesh's nodes (only the boundary nodes are read)."""
+        g = _f64(g, (self.nodes,))
+        _lib.check(_lib.load().fep3m_set_boundary(self._h, _ptr(g)), "fep3m_set_boundary")
 
     def set_particles(self, pos, Q):
         N = int(pos.shape[0])

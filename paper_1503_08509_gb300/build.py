@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfep3m.so")
-SOURCES = ["bin.cu", "mesh.cu", "pair.cu", "orderq.cu", "api.cu", "static_noalloc.cu", "setup.cpp", "highorder.cpp"]
+SOURCES = ["bin.cu", "mesh.cu", "pair.cu", "orderq.cu", "box.cu", "api.cu", "static_noalloc.cu", "setup.cpp", "highorder.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -60,6 +60,11 @@ __global__ void k_to_double(int64_t n, const A* in, double* out, double a) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) out[i] = (double)in[i] * a;
 }
+// flag (1) when any of the n values is not finite
+__global__ void k_check_finite(int64_t n, const double* __restrict__ v, int* __restrict__ flag) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && !isfinite(v[i])) atomicOr(flag, 1);
+}
 // sum Q and sum |Q| (the neutrality check): per-block partials, the last
 // block to finish adds them in block order (deterministic)
 __global__ void k_charge_sums(int64_t N, const double* __restrict__ Q, double* __restrict__ partials,
@@ -278,6 +283,31 @@ int compute_orderq(fep3m_ctx* c, double* phi, double* U) {
   return st;
 }
 
+// the Dirichlet box: potentials and energy
+int compute_box(fep3m_ctx* c, double* phi, double* U) {
+  const int64_t N = c->N;
+  const bool phi_dev = is_device_ptr(phi);
+  double* pd = phi_dev ? phi : (phi ? c->out_tmp : nullptr);
+  ev_record(c, 0);
+  const int st = box_compute(c, pd, U ? c->scal + 40 : nullptr);
+  ev_record(c, 3);
+  if (st != FEP3M_OK && st != FEP3M_ENOCONV) return st;
+  if (U) CK(cudaMemcpyAsync(U, c->scal + 40, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->host_err, c->iflags + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (*c->host_err) return FEP3M_ETIMEOUT;
+  c->have_forward = true;
+  c->have_grad = false;
+  c->stats.refine_steps = c->box->sweeps;
+  c->stats.mg_rel_residual = c->box->relres;
+  if (phi && !phi_dev) {
+    int s2 = deliver(c, phi, c->out_tmp, N * sizeof(double));
+    if (s2 != FEP3M_OK) return s2;
+  }
+  if (c->timing) c->stats.ms_solve = ev_ms(c, 0, 3);
+  return st;
+}
+
 constexpr int kMaxReruns = 3;
 
 }  // namespace
@@ -308,6 +338,7 @@ void fep3m_destroy(fep3m_ctx* c) {
   fep3m::solver_destroy(&c->solv[0]);
   fep3m::solver_destroy(&c->solv[1]);
   fep3m::orderq_destroy(c);
+  fep3m::box_destroy(c);
   if (c->host_err) cudaFreeHost(c->host_err);
   if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
   if (c->sweep_stream) cudaStreamDestroy(c->sweep_stream);
@@ -332,7 +363,9 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
       cfg->n_el < 2 * cfg->n_sr + 1 || cfg->n_el > 400 ||
       (cfg->precision != FEP3M_FP64 && cfg->precision != FEP3M_MIXED) || cfg->mg_rtol < 0 || cfg->table_pad < 0 ||
       cfg->table_pad > 8 || ((cfg->flags & FEP3M_ONE_ELEMENT) && cfg->q < 2) ||
-      ((cfg->flags & FEP3M_MULTIGRID) && cfg->q > 1) || (long long)(cfg->q + 2) * cfg->n_el > 1024)
+      ((cfg->flags & FEP3M_MULTIGRID) && cfg->q > 1) || (long long)(cfg->q + 2) * cfg->n_el > 1024 ||
+      ((cfg->flags & FEP3M_DIRICHLET) &&
+       (cfg->q != 1 || (cfg->flags & (FEP3M_MULTIGRID | FEP3M_NEUTRALIZE)) != 0)))
     return FEP3M_EINVAL;
   fep3m_ctx* c = new (std::nothrow) fep3m_ctx();
   if (!c) return FEP3M_ENOMEM;
@@ -378,6 +411,13 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(from_cuda(e));
     *out = c;
     return FEP3M_OK;
+  }
+  // Dirichlet box: the order-1 kernels run on a periodic grid of n_el + n_sr
+  // elements per axis (period L (n_el + n_sr) / n_el), the box in its first n_el
+  const bool box = (cfg->flags & FEP3M_DIRICHLET) != 0;
+  if (box) {
+    c->n = cfg->n_el + cfg->n_sr;
+    c->L = c->n * c->h;
   }
   // FE basis-screen table and its [vertex offset][node] layout for the kernels
   build_table(c->n_sr, cfg->table_pad > 0 ? cfg->table_pad : 4, c->table_host);
@@ -469,9 +509,13 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
       (e = cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming)) != cudaSuccess)
     return fail(from_cuda(e));
-  if ((e = solver_init(&c->solv[0], c, c->stream)) != cudaSuccess) return fail(from_cuda(e));
-  if ((e = solver_init(&c->solv[1], c, c->aux_stream)) != cudaSuccess) return fail(from_cuda(e));
-  c->stats.mg_levels = (int)c->solv[0].mg.lv.size();
+  if (box) {
+    if ((st = box_create(c, cfg->n_el)) != FEP3M_OK) return fail(st);
+  } else {
+    if ((e = solver_init(&c->solv[0], c, c->stream)) != cudaSuccess) return fail(from_cuda(e));
+    if ((e = solver_init(&c->solv[1], c, c->aux_stream)) != cudaSuccess) return fail(from_cuda(e));
+    c->stats.mg_levels = (int)c->solv[0].mg.lv.size();
+  }
   for (int k = 0; k < 11; ++k) cudaEventCreate(&c->ev[k]);
   c->ev_init = true;
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(from_cuda(e));
@@ -513,7 +557,8 @@ int fep3m_set_particles(fep3m_ctx* c, int64_t N, const double* pos, const double
   c->have_particles = false;
   c->have_forward = false;
   if (flag) return FEP3M_EINVAL;
-  if (!(c->cfg.flags & FEP3M_NEUTRALIZE) && std::fabs(sums[0]) > 1e-12 * sums[1]) return FEP3M_ENOTNEUTRAL;
+  if (!c->box && !(c->cfg.flags & FEP3M_NEUTRALIZE) && std::fabs(sums[0]) > 1e-12 * sums[1])
+    return FEP3M_ENOTNEUTRAL;
   c->have_particles = true;
   if (c->timing) c->stats.ms_bin = ev_ms(c, 6, 7);
   return FEP3M_OK;
@@ -524,6 +569,7 @@ int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
   if (!c) return FEP3M_EINVAL;
   if (!c->have_particles) return FEP3M_ESTATE;
   if (c->oq) return force ? FEP3M_EINVAL : compute_orderq(c, phi, U);
+  if (c->box) return force ? FEP3M_EINVAL : compute_box(c, phi, U);
   const int64_t N = c->N;
   const bool phi_dev = is_device_ptr(phi);
   const bool fdev = force && is_device_ptr(force);
@@ -567,7 +613,7 @@ int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
 }
 
 int fep3m_vjp(fep3m_ctx* c, double gU, const double* gphi, double* dpos, double* dQ) {
-  if (!c || !std::isfinite(gU) || c->oq) return FEP3M_EINVAL;
+  if (!c || !std::isfinite(gU) || c->oq || c->box) return FEP3M_EINVAL;
   if (!c->have_particles) return FEP3M_ESTATE;
   const int64_t N = c->N;
   if (!c->have_forward || !c->have_grad) {
@@ -653,8 +699,18 @@ int fep3m_get_binning(const fep3m_ctx* cc, int32_t* perm, int32_t* count, int32_
   const int64_t N = c->N, ne = (int64_t)c->n * c->n * c->n;
   int s;
   if ((s = deliver(c, perm, c->perm, N * 4)) != FEP3M_OK) return s;
-  if ((s = deliver(c, count, c->count, ne * 4)) != FEP3M_OK) return s;
-  if ((s = deliver(c, cell, c->cell, N * 4)) != FEP3M_OK) return s;
+  if (c->box) {
+    // the box's elements out of the padded grid: counts via the box scratch, ids via out_tmp
+    const int64_t nb3 = (int64_t)c->box->nb * c->box->nb * c->box->nb;
+    int* cnt = (int*)c->box->t[0];
+    int* cel = (int*)c->out_tmp;
+    CK(box_binning(c, count ? cnt : nullptr, cell ? cel : nullptr));
+    if ((s = deliver(c, count, cnt, nb3 * 4)) != FEP3M_OK) return s;
+    if ((s = deliver(c, cell, cel, N * 4)) != FEP3M_OK) return s;
+  } else {
+    if ((s = deliver(c, count, c->count, ne * 4)) != FEP3M_OK) return s;
+    if ((s = deliver(c, cell, c->cell, N * 4)) != FEP3M_OK) return s;
+  }
   if ((s = deliver(c, delta, c->delta, 3 * N * 8)) != FEP3M_OK) return s;
   CK(cudaStreamSynchronize(c->stream));
   return FEP3M_OK;
@@ -674,6 +730,22 @@ int fep3m_get_mesh(const fep3m_ctx* cc, double* C, double* b, double* phi_mesh) 
     if (phi_mesh) {
       FEP3M_CL k_to_double<double><<<gsz(np3), PT, 0, c->stream>>>(np3, o->phi, o->t[0], c->inv_h);
       if ((s = deliver(c, phi_mesh, o->t[0], np3 * 8)) != FEP3M_OK) return s;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return FEP3M_OK;
+  }
+  if (c->box) {
+    const fep3m::Box* B = c->box;
+    const int64_t nn3 = (int64_t)B->Nn * B->Nn * B->Nn, nb3 = (int64_t)B->nb * B->nb * B->nb;
+    int s;
+    if (C) {
+      CK(box_coeffs(c, B->t[0]));   // 8 nb^3 <= Nn^3
+      if ((s = deliver(c, C, B->t[0], 8 * nb3 * 8)) != FEP3M_OK) return s;
+    }
+    if ((s = deliver(c, b, B->b, nn3 * 8)) != FEP3M_OK) return s;
+    if (phi_mesh) {
+      FEP3M_CL k_to_double<double><<<gsz(nn3), PT, 0, c->stream>>>(nn3, c->phi64, B->t[1], c->inv_h);
+      if ((s = deliver(c, phi_mesh, B->t[1], nn3 * 8)) != FEP3M_OK) return s;
     }
     CK(cudaStreamSynchronize(c->stream));
     return FEP3M_OK;
@@ -718,6 +790,22 @@ int fep3m_solve_mesh(fep3m_ctx* c, const double* b, double* phi) {
     CK(cudaStreamSynchronize(c->stream));
     return st;
   }
+  if (c->box) {
+    // right-hand side in g64, solution in lam64 (both (3n)^3 >= (3 nb + 1)^3 of the padded grid)
+    const fep3m::Box* B = c->box;
+    const int64_t nn3 = (int64_t)B->Nn * B->Nn * B->Nn;
+    CK(cudaMemcpyAsync(c->g64, b, nn3 * 8, is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->stream));
+    const int st = box_solve(c, c->g64, c->lam64);
+    if (st != FEP3M_OK && st != FEP3M_ENOCONV) return st;
+    c->stats.refine_steps = B->sweeps;
+    c->stats.mg_rel_residual = B->relres;
+    FEP3M_CL k_to_double<double><<<gsz(nn3), PT, 0, c->stream>>>(nn3, c->lam64, c->res64, c->inv_h);
+    int s = deliver(c, phi, c->res64, nn3 * 8);
+    if (s != FEP3M_OK) return s;
+    CK(cudaStreamSynchronize(c->stream));
+    return st;
+  }
   const int64_t nodes = (int64_t)27 * c->n * c->n * c->n;
   CK(cudaMemcpyAsync(c->g64, b, nodes * 8, is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      c->stream));
@@ -742,6 +830,24 @@ int fep3m_mesh_eigenbasis(int n_el, double* lam, double* V) {
   std::memcpy(lam, l.data(), l.size() * sizeof(double));
   std::memcpy(V, v.data(), v.size() * sizeof(double));
   return FEP3M_OK;
+}
+
+int fep3m_set_boundary(fep3m_ctx* c, const double* g) {
+  if (!c || !g || !c->box) return FEP3M_EINVAL;
+  const fep3m::Box* B = c->box;
+  const int64_t nn3 = (int64_t)B->Nn * B->Nn * B->Nn;
+  // staged in res64 and checked for finite values before it replaces the data
+  CK(cudaMemcpyAsync(c->res64, g, nn3 * 8, is_device_ptr(g) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     c->stream));
+  CK(cudaMemsetAsync(c->iflags + 3, 0, sizeof(int), c->stream));
+  FEP3M_CL k_check_finite<<<gsz(nn3), PT, 0, c->stream>>>(nn3, c->res64, c->iflags + 3);
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, c->iflags + 3, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (flag) return FEP3M_EINVAL;
+  const int st = box_set_boundary(c, c->res64);
+  c->have_forward = false;
+  return st;
 }
 
 int fep3m_get_table(const fep3m_ctx* c, double* table) {

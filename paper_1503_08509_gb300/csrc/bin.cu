@@ -17,17 +17,21 @@ constexpr int kScanTile = kScanThreads * kScanPer;
 
 // x -> element and offset, written with explicit round-to-nearest intrinsics
 // so that no multiply-add is fused: the result is bit-identical to the same
-// expression evaluated one IEEE operation at a time.
+// expression evaluated one IEEE operation at a time.  Periodic cube (box_L =
+// 0): x wrapped into [0, L), element index at most n - 1.  Box [0, box_L]^3
+// (box_L > 0, L the longer padded period, which wraps nothing in the box): a
+// coordinate outside the box is an input error, the element index at most
+// cmax (a charge on the far face belongs to the last box element).
 __global__ void k_bin(const double* __restrict__ pos, const double* __restrict__ Q, int64_t N, double L,
-                      int n, double h, double inv_h, int* __restrict__ cell, double* __restrict__ delta,
-                      int* __restrict__ count, int* __restrict__ err) {
+                      int n, double h, double inv_h, double box_L, int cmax, int* __restrict__ cell,
+                      double* __restrict__ delta, int* __restrict__ count, int* __restrict__ err) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   int c3[3];
   bool bad = !isfinite(Q[i]);
   for (int a = 0; a < 3; ++a) {
     double x = pos[3 * i + a];
-    if (!isfinite(x)) {
+    if (!isfinite(x) || (box_L > 0.0 && !(x >= 0.0 && x <= box_L))) {
       bad = true;
       x = 0.0;
     }
@@ -35,7 +39,7 @@ __global__ void k_bin(const double* __restrict__ pos, const double* __restrict__
     double xw = __dsub_rn(x, __dmul_rn(L, fl));
     if (xw >= L) xw = 0.0;
     double cf = floor(__dmul_rn(xw, inv_h));
-    int c = (int)fmax(0.0, fmin(cf, (double)(n - 1)));
+    int c = (int)fmax(0.0, fmin(cf, (double)cmax));
     c3[a] = c;
     delta[3 * i + a] = __dsub_rn(xw, __dmul_rn((double)c + 0.5, h));
   }
@@ -187,7 +191,10 @@ cudaError_t bin_particles(fep3m_ctx* c, const double* pos, const double* Q, int 
   cudaMemsetAsync(c->fill, 0, sizeof(int) * ne, s);
   const int T = 256;
   const int gN = (int)((c->N + T - 1) / T), gE = (int)((ne + T - 1) / T);
-  FEP3M_CL k_bin<<<gN, T, 0, s>>>(pos, Q, c->N, c->L, c->n, c->h, c->inv_h, c->cell, c->delta, c->count, c->iflags);
+  const double box_L = c->box ? c->cfg.L : 0.0;
+  const int cmax = c->box ? c->box->nb - 1 : c->n - 1;
+  FEP3M_CL k_bin<<<gN, T, 0, s>>>(pos, Q, c->N, c->L, c->n, c->h, c->inv_h, box_L, cmax, c->cell, c->delta, c->count,
+                                  c->iflags);
   cudaError_t e = exclusive_scan(c->count, ne, c->start, (int*)c->scan_tmp, s);
   if (e != cudaSuccess) return e;
   FEP3M_CL k_scatter<<<gN, T, 0, s>>>(c->cell, c->N, c->start, c->fill, c->perm);

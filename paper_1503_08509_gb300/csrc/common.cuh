@@ -209,6 +209,34 @@ struct OrderQ {
   double relres = 0;
 };
 
+// The box [0, L]^3 with Dirichlet data (box.cu): order-3 mesh of nb elements
+// per axis, Nn = 3 nb + 1 nodes, the NI = 3 nb - 1 interior ones solved for.
+struct BoxBand {
+  double bM[3][7];      // 1-D order-3 mass row of node type t = g mod 3: tap o -> node g + o - 3
+  double bK[3][7];      // the same for the stiffness (interior rows of the open matrices)
+  double Mpq[4][2];     // element mixed mass int l^3_i l^1_j (h = 1)
+};
+struct Box {
+  int nb = 0, Nn = 0, NI = 0;
+  BoxBand band;
+  double* g = nullptr;        // Nn^3 Dirichlet data (physical units; boundary nodes read)
+  double* b = nullptr;        // Nn^3 load vector (element units)
+  double* phi = nullptr;      // Nn^3 mesh potential (element units: h Phi^sm)
+  double* res = nullptr;      // Nn^3 residual b - K phi (interior rows)
+  double* t[4] = {};          // Nn^3 scratch of the stiffness apply and the load passes
+  float* r32 = nullptr;       // NI^3 FP32 inner solve: right-hand side, correction, scratch
+  float* x32 = nullptr;
+  float* w1 = nullptr;
+  float* w2 = nullptr;
+  int* bel = nullptr;         // boundary elements (ids in the padded grid)
+  int nbel = 0;
+  double* red = nullptr;      // reduction partials
+  double* host_red = nullptr; // pinned: one reduction result
+  FineFDM fdm;                // Dirichlet eigenbasis of the interior nodes (no null mode)
+  int sweeps = 0;
+  double relres = 0;
+};
+
 }  // namespace fep3m
 
 struct fep3m_ctx {
@@ -286,6 +314,8 @@ struct fep3m_ctx {
   unsigned long long* host_cnt = nullptr;   // pinned: 5 pair statistics of the last set_particles
   bool counts_stale = false;               // the pair statistics predate the particles last set
   fep3m::OrderQ* oq = nullptr;   // screens of order q >= 2 (orderq.cu)
+  fep3m::Box* box = nullptr;     // FEP3M_DIRICHLET (box.cu): n is then nb + n_sr, the box
+                                 // elements first on a periodic grid padded with empty ones
   // stats
   fep3m_stats stats;
   bool timing = false;
@@ -306,13 +336,15 @@ double estimate_lmax(const Stencils& st, int n);
 
 // device launches (return cudaGetLastError-style codes)
 cudaError_t bin_particles(fep3m_ctx* c, const double* pos, const double* Q, int use_fp32);
+// screen lists C and the vertex density (and its by-vertex copy Cv) of the binned charges
+cudaError_t element_lists(fep3m_ctx* c);
 cudaError_t assemble_forward(fep3m_ctx* c);
 cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream);
 // fast-diagonalisation solve of a periodic N^3 mesh from its 1-D eigenpairs
 // (mesh.cu): device data, x = K^+ b in FP32 (six transform passes; w1, w2 N^3
 // scratch), release
 cudaError_t fdm_setup(FineFDM& f, int N, const std::vector<double>& lam, const std::vector<double>& V,
-                      bool tensor_cores);
+                      bool tensor_cores, bool null_mode = true);
 cudaError_t fdm_apply(const FineFDM& f, const float* b, float* x, float* w1, float* w2, cudaStream_t s);
 void fdm_free(FineFDM& f);
 void solver_destroy(Solver* s);
@@ -371,4 +403,12 @@ void orderq_destroy(fep3m_ctx* c);
 int orderq_compute(fep3m_ctx* c, double* phi_dev, double* U_dev);
 int orderq_solve(fep3m_ctx* c, const double* b_dev, double* phi_dev);
 cudaError_t sorted_charges(fep3m_ctx* c);
+// the Dirichlet box (box.cu); n is the padded grid's, nb the box's elements per axis
+int box_create(fep3m_ctx* c, int nb);
+void box_destroy(fep3m_ctx* c);
+int box_set_boundary(fep3m_ctx* c, const double* g_dev);
+int box_compute(fep3m_ctx* c, double* phi_dev, double* U_dev);
+int box_solve(fep3m_ctx* c, const double* rhs_dev, double* phi_dev);
+cudaError_t box_binning(fep3m_ctx* c, int* count_out, int* cell_out);
+cudaError_t box_coeffs(fep3m_ctx* c, double* out);
 }  // namespace fep3m

@@ -2158,12 +2158,15 @@ static void solver_plan_free(Solver* c) {
 // pieces in the layout of the tensor-core row GEMM (column tiles of nt modes,
 // chunks of 64 nodes).  Used by the order-3 fine level and the order-p mesh.
 cudaError_t fdm_setup(FineFDM& f, int Nf, const std::vector<double>& lamf, const std::vector<double>& Vf,
-                      bool tensor_cores) {
+                      bool tensor_cores, bool null_mode) {
   cudaError_t e;
   {
-    f.null_mode = 0;
-    for (int i = 1; i < Nf; ++i)
-      if (std::fabs(lamf[i]) < std::fabs(lamf[f.null_mode])) f.null_mode = i;
+    // the constant mode of a periodic (or fully Neumann) mesh: the eigenvalue
+    // nearest 0, dropped from the solve; none for Dirichlet data
+    f.null_mode = null_mode ? 0 : -1;
+    if (null_mode)
+      for (int i = 1; i < Nf; ++i)
+        if (std::fabs(lamf[i]) < std::fabs(lamf[f.null_mode])) f.null_mode = i;
     std::vector<float> Vf32(Vf.begin(), Vf.end()), VTf32((size_t)Nf * Nf), lf32(lamf.begin(), lamf.end());
     for (int i = 0; i < Nf; ++i)
       for (int k = 0; k < Nf; ++k) VTf32[(size_t)k * Nf + i] = (float)Vf[(size_t)i * Nf + k];
@@ -2300,7 +2303,7 @@ void solver_destroy(Solver* s) {
   s->red_counter = nullptr;
 }
 
-cudaError_t assemble_forward(fep3m_ctx* c) {
+cudaError_t element_lists(fep3m_ctx* c) {
   const int n = c->n;
   const int64_t ne = (int64_t)n * n * n;
   cudaStream_t s = c->stream;
@@ -2313,6 +2316,14 @@ cudaError_t assemble_forward(fep3m_ctx* c) {
     FEP3M_CL k_vertex_density<double><<<grid_for(ne), TPB, 0, s>>>(n, (const double*)c->C, (double*)c->rv,
                                                                     (double*)c->Cv);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t assemble_forward(fep3m_ctx* c) {
+  const int n = c->n;
+  cudaStream_t s = c->stream;
+  cudaError_t e = element_lists(c);
+  if (e != cudaSuccess) return e;
   // the load vector in three separable passes through the forward solver's
   // fine-level scratch (free until its solve, which follows on this stream)
   const Level& L0 = c->solv[0].mg.lv[0];

@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
 // charge are evaluated in FP64; only the small remainder goes through the FP32
 // contraction.
 template <class T, bool GRAD>
-__global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __restrict__ start,
+__global__ void __launch_bounds__(PT) k_pair_eval(int n, int Nm, T inv_h, const int* __restrict__ start,
                                                   const int* __restrict__ count,
                                                   const typename vec4<T>::type* __restrict__ part,
                                                   const double* __restrict__ phi64, const float2* __restrict__ phi_hl,
@@ -823,8 +823,10 @@ __global__ void __launch_bounds__(PT) k_pair_eval(int n, T inv_h, const int* __r
   if (ntarget == 0) return;
   __syncthreads();
   const T* gb = Gscr + (int64_t)blockIdx.x * (BE * 64);
-  const int N = 3 * n;
-  // mesh node of node m of brick element l
+  const int N = Nm;
+  // mesh node of node m of brick element l: on the periodic mesh (Nm = 3n
+  // nodes per axis) wrapped, on a box's (Nm = 3 nb + 1, targets in the first
+  // nb elements) never past the last node
   auto node = [&](int l, int m) -> int64_t {
     const int ex = E0x + l % BX, ey = E0y + (l / BX) % BY, ez = E0z + l / (BX * BY);
     const int gx = 3 * ex + (m & 3), gy = 3 * ey + ((m >> 2) & 3), gz = 3 * ez + (m >> 4);   // < 3n + 3
@@ -1406,10 +1408,14 @@ static cudaError_t launch_pair_screen(fep3m_ctx* c, cudaStream_t s, bool half) {
   return cudaGetLastError();
 }
 
+// nodes per axis of the mesh the evaluation reads: the periodic order-3 mesh,
+// or a box's
+static int mesh_nodes_per_axis(const fep3m_ctx* c) { return c->box ? c->box->Nn : 3 * c->n; }
+
 template <class T, bool GRAD>
 static cudaError_t launch_pair_eval(fep3m_ctx* c, double* phi_out) {
   FEP3M_CL k_pair_eval<T, GRAD><<<(unsigned)pair_bricks(c), PT, 0, c->stream>>>(
-      c->n, (T)c->inv_h, c->start, c->count, (const typename vec4<T>::type*)c->part, c->phi64,
+      c->n, mesh_nodes_per_axis(c), (T)c->inv_h, c->start, c->count, (const typename vec4<T>::type*)c->part, c->phi64,
       (const float2*)c->phi_hl, (const T*)c->Gscr, c->perm, c->phi_s, c->E_s, phi_out);
   return cudaGetLastError();
 }
@@ -1553,7 +1559,7 @@ __global__ void k_phi_hilo(int64_t n, const double* __restrict__ phi, float2* __
 
 cudaError_t pair_prepare(fep3m_ctx* c) {
   if (c->precision == FEP3M_MIXED) {
-    const int64_t nodes = (int64_t)27 * c->n * c->n * c->n;
+    const int64_t na = mesh_nodes_per_axis(c), nodes = na * na * na;
     FEP3M_CL k_phi_hilo<<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->phi64, (float2*)c->phi_hl);
   }
   return cudaGetLastError();

@@ -95,6 +95,18 @@ def two_biased_cubes(N, seed=6):
 
 
 # Named workloads: (generator, mesh elements per axis, description)
+def box_charges(N, L=1.0, seed=7, on_faces=6):
+    """N charges in the closed box [0, L]^3 for the Dirichlet problem: uniform positions,
+    charges +1 / -1 drawn independently (not neutral), and the first on_faces charges moved
+    onto the faces, one per face in turn (coordinate 0 or exactly L)."""
+    rng = np.random.default_rng(seed)
+    pos = rng.random((N, 3)) * L
+    Q = rng.choice([-1.0, 1.0], size=N)
+    for k in range(min(on_faces, N)):
+        pos[k, k % 3] = 0.0 if (k // 3) % 2 == 0 else L
+    return pos, Q
+
+
 def workload(name):
     """Return dict(pos, Q, L, n_el, label) for a named workload."""
     if name == 'uniform1k':

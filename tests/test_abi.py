@@ -45,7 +45,11 @@ def test_create_rejects_bad_config_before_touching_the_gpu(lib):
     for kw in (dict(L=-1.0, n_el=16), dict(L=1.0, n_el=6), dict(L=1.0, n_el=16, q=5), dict(L=1.0, n_el=16, q=0),
                dict(L=1.0, n_el=16, q=1, flags=_lib.FEP3M_ONE_ELEMENT),
                dict(L=1.0, n_el=16, q=2, flags=_lib.FEP3M_MULTIGRID), dict(L=1.0, n_el=300, q=2),
-               dict(L=1.0, n_el=16, precision=5), dict(L=float("nan"), n_el=16)):
+               dict(L=1.0, n_el=16, precision=5), dict(L=float("nan"), n_el=16),
+               dict(L=1.0, n_el=16, q=2, flags=_lib.FEP3M_DIRICHLET),
+               dict(L=1.0, n_el=16, flags=_lib.FEP3M_DIRICHLET | _lib.FEP3M_MULTIGRID),
+               dict(L=1.0, n_el=16, flags=_lib.FEP3M_DIRICHLET | _lib.FEP3M_NEUTRALIZE),
+               dict(L=1.0, n_el=6, flags=_lib.FEP3M_DIRICHLET)):
         base = dict(L=1.0, n_el=16, q=1, n_sr=3, precision=0)
         base.update(kw)
         cfg = _lib.Config(**base)
