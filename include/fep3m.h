@@ -86,6 +86,18 @@ enum { FEP3M_FP64 = 0, FEP3M_MIXED = 1 };
                                   FEP3M_MULTIGRID; potentials and energy
                                   (fep3m_compute with force = NULL; fep3m_vjp
                                   returns FEP3M_EINVAL)                        */
+#define FEP3M_NEUMANN 32u      /* the box [0, L]^3 with Neumann data dPhi/dn = g
+                                  (outward normal) on its boundary: as
+                                  FEP3M_DIRICHLET, with the adjusted flux
+                                  g - dPhi^sr/dn entering the mesh problem as a
+                                  boundary load (Eq. bcadjust for Neumann
+                                  data).  The data fix Phi up to a constant:
+                                  the load is made compatible by removing its
+                                  component along the node integrals and the
+                                  mesh solution has int phi = 0, so Phi and U
+                                  carry that convention                         */
+#define FEP3M_NEUMANN_NGL 8    /* Gauss-Legendre points per axis of a face
+                                  element in the Neumann face integrals        */
 
 typedef struct fep3m_ctx fep3m_ctx;
 
@@ -129,8 +141,8 @@ typedef struct {
   int mg_max_cycles;   /* cap on refinement sweeps; 0 -> 10                      */
   int table_pad;       /* Dirichlet box margin, elements, beyond the kept table;
                           0 -> 4 (q = 1) or 2 (q >= 2); at most 8               */
-  unsigned flags;      /* FEP3M_NEUTRALIZE, FEP3M_CUDA_CORES,
-                          FEP3M_MULTIGRID, FEP3M_ONE_ELEMENT, FEP3M_DIRICHLET   */
+  unsigned flags;      /* FEP3M_NEUTRALIZE, FEP3M_CUDA_CORES, FEP3M_MULTIGRID,
+                          FEP3M_ONE_ELEMENT, FEP3M_DIRICHLET or FEP3M_NEUMANN   */
 } fep3m_config;
 
 typedef struct {
@@ -173,7 +185,7 @@ typedef struct {
 int fep3m_create(const fep3m_config* cfg, void* cuda_stream, fep3m_ctx** out);
 
 /* Charge positions (N x 3, host or device, any real values: they are wrapped
- * into [0, L); in a FEP3M_DIRICHLET box they must lie in [0, L]^3, a charge
+ * into [0, L); in a box (FEP3M_DIRICHLET, FEP3M_NEUMANN) they must lie in [0, L]^3, a charge
  * on the faces x = L belonging to the last element) and charges (N, host or
  * device).  Bins the charges into
  * elements (stable counting sort) and stores the sorted SoA copy; grows the
@@ -225,31 +237,43 @@ int fep3m_get_binning(const fep3m_ctx* ctx, int32_t* perm, int32_t* count,
  *   Phi^sm / Phi^sing / Phi^scr parts are not kept separately.
  * For q >= 2: C [n^3 x (q+1)^3] (screen node i + (q+1)(j + (q+1) k)), b and
  * phi_mesh [(p n)^3] on the order-p mesh (index ix + pn iy + (pn)^2 iz).
- * FEP3M_DIRICHLET box: b and phi_mesh on the (3n + 1)^3 nodes of the box,
- * index ix + (3n+1) iy + (3n+1)^2 iz, node (ix, iy, iz) at (ix, iy, iz) h / 3;
- * b is the box integral (the part of a screen outside the box is not a load);
- * phi_mesh holds the adjusted boundary values g - Phi^sr on the boundary
- * nodes (Eq. bcadjust) and is not shifted.                                   */
+ * Box (FEP3M_DIRICHLET, FEP3M_NEUMANN): b and phi_mesh on the (3n + 1)^3
+ * nodes of the box, index ix + (3n+1) iy + (3n+1)^2 iz, node (ix, iy, iz) at
+ * (ix, iy, iz) h / 3; b is the box integral of the screens (the part of a
+ * screen outside the box is not a load; the Neumann face load is not
+ * included); with Dirichlet data phi_mesh holds the adjusted boundary values
+ * g - Phi^sr on the boundary nodes (Eq. bcadjust) and is not shifted, with
+ * Neumann data it has int phi = 0.                                           */
 int fep3m_get_mesh(const fep3m_ctx* ctx, double* C, double* b, double* phi_mesh);
 
 /* Solve the periodic FE system K phi = b - (sum b) w / sum w, int phi = 0,
  * for a caller right-hand side b ((p n)^3, host or device) with the context's
  * mesh solver (precision as configured); writes phi (physical units).  Used
- * to test the solver alone.  FEP3M_DIRICHLET box: b and phi on the (3n+1)^3
- * box nodes (as fep3m_get_mesh); solves K phi = b at the interior nodes with
- * phi = g (fep3m_set_boundary, no adjustment: no charges enter) on the
- * boundary nodes.                                                           */
+ * to test the solver alone.  Box: b and phi on the (3n+1)^3 box nodes (as
+ * fep3m_get_mesh); FEP3M_DIRICHLET solves K phi = b at the interior nodes
+ * with phi = g (fep3m_set_boundary, no adjustment: no charges enter) on the
+ * boundary nodes, FEP3M_NEUMANN solves K phi = b - (sum b) w / sum w on all
+ * nodes with int phi = 0 (the data of fep3m_set_boundary do not enter).      */
 int fep3m_solve_mesh(fep3m_ctx* ctx, const double* b, double* phi);
 
-/* Dirichlet data of a FEP3M_DIRICHLET box: g at the (3n + 1)^3 nodes of the
- * order-3 box mesh (host or device, float64, index ix + (3n+1) iy +
- * (3n+1)^2 iz, node (ix, iy, iz) at (ix, iy, iz) h / 3); only the boundary
- * nodes (an index 0 or 3n) are read, and the FE solution takes their values
- * interpolated by the order-3 basis on each face (Sec. "Alternate boundary
- * conditions": the mesh problem's boundary values are g less the short-range
- * potential there, Eq. bcadjust, so that Phi = g at the boundary nodes).
- * Copied; kept until the next call.  FEP3M_EINVAL for a periodic context or
- * non-finite data (the previous data are then kept).                       */
+/* Boundary data of a box (host or device, float64; copied, kept until the
+ * next call; initially 0).
+ * FEP3M_DIRICHLET: g at the (3n + 1)^3 nodes of the order-3 box mesh (index
+ * ix + (3n+1) iy + (3n+1)^2 iz, node (ix, iy, iz) at (ix, iy, iz) h / 3);
+ * only the boundary nodes (an index 0 or 3n) are read, and the FE solution
+ * takes their values interpolated by the order-3 basis on each face (Sec.
+ * "Alternate boundary conditions": the mesh problem's boundary values are g
+ * less the short-range potential there, Eq. bcadjust, so that Phi = g at the
+ * boundary nodes).
+ * FEP3M_NEUMANN: the outward normal derivative g at the face quadrature
+ * points, 6 n^2 NGL^2 values (NGL = FEP3M_NEUMANN_NGL) in the order [face]
+ * [e1][e2][i][j]: face = 2 a + s for the face x_a = s L (s = 0, 1; outward
+ * normal (2 s - 1) along a), e1 and e2 the face element's indices along the
+ * axes a + 1 and a + 2 (mod 3), (i, j) the Gauss-Legendre points t_i, t_j of
+ * [0, 1] along those axes: point x_a = s L, x_{a+1} = (e1 + t_i) h,
+ * x_{a+2} = (e2 + t_j) h.
+ * FEP3M_EINVAL for a periodic context or non-finite data (the previous data
+ * are then kept).                                                           */
 int fep3m_set_boundary(fep3m_ctx* ctx, const double* g);
 
 /* The kept FE basis-screen table (h = 1): nodal values on [-(n_sr+1), n_sr+1]^3

@@ -113,6 +113,22 @@ def boundary_load(n, h, L, integrand, ngl):
     return s
 
 
+def solve_compatible(rhs, M1, K1):
+    """The fully Neumann Galerkin problem K phi = rhs on all nodes, K = K1 (x) M1 (x) M1 +
+    M1 (x) K1 (x) M1 + M1 (x) M1 (x) K1 (constant null space): the load less its component
+    along the node integrals, the constant mode dropped (int phi = 0); exact, by fast
+    diagonalisation."""
+    w1 = M1.sum(axis=1)
+    w3 = w1[:, None, None] * w1[None, :, None] * w1[None, None, :]
+    rhs = rhs - rhs.sum() * w3 / w3.sum()                              # compatible load
+    lam, V = scipy.linalg.eigh(K1, M1)
+    rh = tables.kron_apply(V.T, V.T, V.T, rhs)
+    D = lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
+    z = int(np.argmin(np.abs(lam)))
+    D[z, z, z] = np.inf                                                 # the constant mode
+    return tables.kron_apply(V, V, V, rh / D)
+
+
 def forward(pos, Q, L, n, gn, n_sr=3, adjust=True, ngl=8):
     """Phi_i at the charges (up to a constant) for Neumann data gn(points, normals), with
     the intermediates.  adjust=False takes dPhi^sm/dn = g instead."""
@@ -132,16 +148,7 @@ def forward(pos, Q, L, n, gn, n_sr=3, adjust=True, ngl=8):
         return f
 
     s = boundary_load(n, h, L, integrand, ngl)
-    rhs = b + s
-    w1 = M1.sum(axis=1)
-    w3 = w1[:, None, None] * w1[None, :, None] * w1[None, None, :]
-    rhs = rhs - rhs.sum() * w3 / w3.sum()                              # compatible load
-    lam, V = scipy.linalg.eigh(K1, M1)
-    rh = tables.kron_apply(V.T, V.T, V.T, rhs)
-    D = lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
-    z = int(np.argmin(np.abs(lam)))
-    D[z, z, z] = np.inf                                                 # the constant mode
-    phi_mesh = tables.kron_apply(V, V, V, rh / D)
+    phi_mesh = solve_compatible(b + s, M1, K1)
     phi_sm = evaluate_mesh(phi_mesh, bins['pos'], L, n)
     t = bins['delta'] / h + 0.5
     phi_sr = short_range(bins['pos'], bins['c3'], t, bins, Q, n, n_sr, exclude=np.arange(len(Q)))

@@ -13,6 +13,8 @@ FEP3M_CUDA_CORES = 2
 FEP3M_MULTIGRID = 4
 FEP3M_ONE_ELEMENT = 8
 FEP3M_DIRICHLET = 16
+FEP3M_NEUMANN = 32
+FEP3M_NEUMANN_NGL = 8
 
 
 class Config(ctypes.Structure):

@@ -46,18 +46,20 @@ class FEP3M:
     preconditioned CG; q = 1).
     q: screen order 1..4 (mesh order q + 2); q >= 2 computes potentials and
     energy (no forces).  one_element: one-element screens (q >= 2).
-    dirichlet: the box [0, L]^3 with Dirichlet data (set_boundary; default 0)
-    instead of the periodic cube; q = 1, potentials and energy.
+    dirichlet / neumann: the box [0, L]^3 with Dirichlet data at the mesh's
+    nodes (node_points) or Neumann data at the face quadrature points
+    (face_points), given by set_boundary (default 0), instead of the periodic
+    cube; q = 1, potentials and energy.
     """
 
     def __init__(self, L, n_el, n_sr=3, precision="fp64", mg_rtol=0.0, mg_max_cycles=0, neutralize=False,
                  table_pad=0, device=None, stream=None, tensor_cores=True, solver="fdm", q=1, one_element=False,
-                 dirichlet=False):
+                 dirichlet=False, neumann=False):
         lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.L, self.n_el, self.n_sr, self.q = float(L), int(n_el), int(n_sr), int(q)
         self.precision = precision
-        self.dirichlet = bool(dirichlet)
+        self.dirichlet, self.neumann = bool(dirichlet), bool(neumann)
         cfg = _lib.Config(L=self.L, n_el=self.n_el, q=self.q, n_sr=self.n_sr,
                           precision=_lib.FEP3M_MIXED if precision == "mixed" else _lib.FEP3M_FP64,
                           mg_rtol=mg_rtol, mg_max_cycles=mg_max_cycles, table_pad=table_pad,
@@ -65,7 +67,8 @@ class FEP3M:
                           (0 if tensor_cores else _lib.FEP3M_CUDA_CORES) |
                           (_lib.FEP3M_MULTIGRID if solver == "multigrid" else 0) |
                           (_lib.FEP3M_ONE_ELEMENT if one_element else 0) |
-                          (_lib.FEP3M_DIRICHLET if dirichlet else 0))
+                          (_lib.FEP3M_DIRICHLET if dirichlet else 0) |
+                          (_lib.FEP3M_NEUMANN if neumann else 0))
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             h = ctypes.c_void_p()
@@ -88,9 +91,29 @@ class FEP3M:
 
     @property
     def nodes(self):
-        if self.dirichlet:
+        if self.dirichlet or self.neumann:
             return (3 * self.n_el + 1) ** 3
         return ((self.q + 2) * self.n_el) ** 3
+
+    def face_points(self):
+        """Points and outward normals (each (6 n^2 NGL^2) x 3) of the Neumann data, in the order of
+        fep3m_set_boundary: [face = 2 axis + side][e1][e2][i][j]."""
+        n, h, G = self.n_el, self.L / self.n_el, _lib.FEP3M_NEUMANN_NGL
+        t = 0.5 * (np.polynomial.legendre.leggauss(G)[0] + 1.0)
+        pts, nrm = [], []
+        for ax in range(3):
+            a1, a2 = (ax + 1) % 3, (ax + 2) % 3
+            for side in (0, 1):
+                e1, e2, i, j = np.meshgrid(np.arange(n), np.arange(n), np.arange(G), np.arange(G), indexing="ij")
+                p = np.zeros(e1.shape + (3,))
+                p[..., ax] = side * self.L
+                p[..., a1] = (e1 + t[i]) * h
+                p[..., a2] = (e2 + t[j]) * h
+                v = np.zeros(3)
+                v[ax] = 1.0 if side else -1.0
+                pts.append(p.reshape(-1, 3))
+                nrm.append(np.tile(v, (p.size // 3, 1)))
+        return np.concatenate(pts), np.concatenate(nrm)
 
     def node_points(self):
         """Coordinates (nodes x 3) of the box mesh's nodes, index ix + (3n+1) iy + (3n+1)^2 iz."""
@@ -100,8 +123,10 @@ class FEP3M:
         return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
 
     def set_boundary(self, g):
-        """Dirichlet data at the box mesh's nodes (only the boundary nodes are read)."""
-        g = _f64(g, (self.nodes,))
+        """Dirichlet data at the box mesh's nodes (only the boundary nodes are read), or Neumann
+        data at the face quadrature points (face_points)."""
+        size = 6 * self.n_el ** 2 * _lib.FEP3M_NEUMANN_NGL ** 2 if self.neumann else self.nodes
+        g = _f64(g, (size,))
         _lib.check(_lib.load().fep3m_set_boundary(self._h, _ptr(g)), "fep3m_set_boundary")
 
     def set_particles(self, pos, Q):

@@ -364,8 +364,9 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
       (cfg->precision != FEP3M_FP64 && cfg->precision != FEP3M_MIXED) || cfg->mg_rtol < 0 || cfg->table_pad < 0 ||
       cfg->table_pad > 8 || ((cfg->flags & FEP3M_ONE_ELEMENT) && cfg->q < 2) ||
       ((cfg->flags & FEP3M_MULTIGRID) && cfg->q > 1) || (long long)(cfg->q + 2) * cfg->n_el > 1024 ||
-      ((cfg->flags & FEP3M_DIRICHLET) &&
-       (cfg->q != 1 || (cfg->flags & (FEP3M_MULTIGRID | FEP3M_NEUTRALIZE)) != 0)))
+      ((cfg->flags & (FEP3M_DIRICHLET | FEP3M_NEUMANN)) &&
+       (cfg->q != 1 || (cfg->flags & (FEP3M_MULTIGRID | FEP3M_NEUTRALIZE)) != 0)) ||
+      ((cfg->flags & FEP3M_DIRICHLET) && (cfg->flags & FEP3M_NEUMANN)))
     return FEP3M_EINVAL;
   fep3m_ctx* c = new (std::nothrow) fep3m_ctx();
   if (!c) return FEP3M_ENOMEM;
@@ -412,9 +413,10 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
     *out = c;
     return FEP3M_OK;
   }
-  // Dirichlet box: the order-1 kernels run on a periodic grid of n_el + n_sr
-  // elements per axis (period L (n_el + n_sr) / n_el), the box in its first n_el
-  const bool box = (cfg->flags & FEP3M_DIRICHLET) != 0;
+  // box (Dirichlet or Neumann data): the order-1 kernels run on a periodic grid
+  // of n_el + n_sr elements per axis (period L (n_el + n_sr) / n_el), the box
+  // in its first n_el
+  const bool box = (cfg->flags & (FEP3M_DIRICHLET | FEP3M_NEUMANN)) != 0;
   if (box) {
     c->n = cfg->n_el + cfg->n_sr;
     c->L = c->n * c->h;
@@ -510,7 +512,7 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
       (e = cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming)) != cudaSuccess)
     return fail(from_cuda(e));
   if (box) {
-    if ((st = box_create(c, cfg->n_el)) != FEP3M_OK) return fail(st);
+    if ((st = box_create(c, cfg->n_el, (cfg->flags & FEP3M_NEUMANN) != 0)) != FEP3M_OK) return fail(st);
   } else {
     if ((e = solver_init(&c->solv[0], c, c->stream)) != cudaSuccess) return fail(from_cuda(e));
     if ((e = solver_init(&c->solv[1], c, c->aux_stream)) != cudaSuccess) return fail(from_cuda(e));
@@ -834,18 +836,18 @@ int fep3m_mesh_eigenbasis(int n_el, double* lam, double* V) {
 
 int fep3m_set_boundary(fep3m_ctx* c, const double* g) {
   if (!c || !g || !c->box) return FEP3M_EINVAL;
-  const fep3m::Box* B = c->box;
-  const int64_t nn3 = (int64_t)B->Nn * B->Nn * B->Nn;
-  // staged in res64 and checked for finite values before it replaces the data
-  CK(cudaMemcpyAsync(c->res64, g, nn3 * 8, is_device_ptr(g) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+  const int64_t len = box_data_size(c);
+  // staged and checked for finite values before it replaces the data
+  double* stage = c->box->gstage;
+  CK(cudaMemcpyAsync(stage, g, len * 8, is_device_ptr(g) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      c->stream));
   CK(cudaMemsetAsync(c->iflags + 3, 0, sizeof(int), c->stream));
-  FEP3M_CL k_check_finite<<<gsz(nn3), PT, 0, c->stream>>>(nn3, c->res64, c->iflags + 3);
+  FEP3M_CL k_check_finite<<<gsz(len), PT, 0, c->stream>>>(len, stage, c->iflags + 3);
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, c->iflags + 3, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (flag) return FEP3M_EINVAL;
-  const int st = box_set_boundary(c, c->res64);
+  const int st = box_set_boundary(c, stage);
   c->have_forward = false;
   return st;
 }

@@ -214,17 +214,32 @@ struct OrderQ {
 struct BoxBand {
   double bM[3][7];      // 1-D order-3 mass row of node type t = g mod 3: tap o -> node g + o - 3
   double bK[3][7];      // the same for the stiffness (interior rows of the open matrices)
+  double dM[2], dK[2];  // diagonals of the open matrices' first and last rows (one element each)
   double Mpq[4][2];     // element mixed mass int l^3_i l^1_j (h = 1)
+  double wn[3];         // node integrals by node type t (t = 0: a vertex shared by two elements)
+  double wend;          // the node integral of the first and last node
+};
+// Gauss-Legendre rule on [0, 1] of the Neumann face integrals
+constexpr int BOX_NGL = 8;
+struct BoxQuad {
+  double t[BOX_NGL], w[BOX_NGL];
 };
 struct Box {
   int nb = 0, Nn = 0, NI = 0;
+  bool neumann = false;       // Neumann data (flux) instead of Dirichlet data
+  int Ns = 0, off = 0;        // solved nodes per axis and their first index: NI, 1 (Dirichlet) or Nn, 0
   BoxBand band;
-  double* g = nullptr;        // Nn^3 Dirichlet data (physical units; boundary nodes read)
+  BoxQuad quad;
+  double* sface = nullptr;    // Neumann: per face element its 16 face-node loads (6 nb^2 x 16)
+  double* g = nullptr;        // Dirichlet: Nn^3 data at the nodes (physical units; boundary nodes read);
+                              // Neumann: 6 nb^2 BOX_NGL^2 fluxes at the face quadrature points
+  double* gstage = nullptr;   // the same size: new data, checked before they replace g
   double* b = nullptr;        // Nn^3 load vector (element units)
+  double* rhs = nullptr;      // Nn^3 Neumann right-hand side: b + s, made compatible
   double* phi = nullptr;      // Nn^3 mesh potential (element units: h Phi^sm)
   double* res = nullptr;      // Nn^3 residual b - K phi (interior rows)
   double* t[4] = {};          // Nn^3 scratch of the stiffness apply and the load passes
-  float* r32 = nullptr;       // NI^3 FP32 inner solve: right-hand side, correction, scratch
+  float* r32 = nullptr;       // Ns^3 FP32 inner solve: right-hand side, correction, scratch
   float* x32 = nullptr;
   float* w1 = nullptr;
   float* w2 = nullptr;
@@ -232,7 +247,7 @@ struct Box {
   int nbel = 0;
   double* red = nullptr;      // reduction partials
   double* host_red = nullptr; // pinned: one reduction result
-  FineFDM fdm;                // Dirichlet eigenbasis of the interior nodes (no null mode)
+  FineFDM fdm;                // box eigenbasis of the solved nodes (Dirichlet: no null mode)
   int sweeps = 0;
   double relres = 0;
 };
@@ -314,8 +329,8 @@ struct fep3m_ctx {
   unsigned long long* host_cnt = nullptr;   // pinned: 5 pair statistics of the last set_particles
   bool counts_stale = false;               // the pair statistics predate the particles last set
   fep3m::OrderQ* oq = nullptr;   // screens of order q >= 2 (orderq.cu)
-  fep3m::Box* box = nullptr;     // FEP3M_DIRICHLET (box.cu): n is then nb + n_sr, the box
-                                 // elements first on a periodic grid padded with empty ones
+  fep3m::Box* box = nullptr;     // FEP3M_DIRICHLET / FEP3M_NEUMANN (box.cu): n is then nb + n_sr,
+                                 // the box elements first on a periodic grid padded with empty ones
   // stats
   fep3m_stats stats;
   bool timing = false;
@@ -403,12 +418,13 @@ void orderq_destroy(fep3m_ctx* c);
 int orderq_compute(fep3m_ctx* c, double* phi_dev, double* U_dev);
 int orderq_solve(fep3m_ctx* c, const double* b_dev, double* phi_dev);
 cudaError_t sorted_charges(fep3m_ctx* c);
-// the Dirichlet box (box.cu); n is the padded grid's, nb the box's elements per axis
-int box_create(fep3m_ctx* c, int nb);
+// the box (box.cu); n is the padded grid's, nb the box's elements per axis
+int box_create(fep3m_ctx* c, int nb, bool neumann);
+int64_t box_data_size(const fep3m_ctx* c);
 void box_destroy(fep3m_ctx* c);
 int box_set_boundary(fep3m_ctx* c, const double* g_dev);
 int box_compute(fep3m_ctx* c, double* phi_dev, double* U_dev);
-int box_solve(fep3m_ctx* c, const double* rhs_dev, double* phi_dev);
+int box_solve(fep3m_ctx* c, double* rhs_dev, double* phi_dev);   // rhs_dev may be overwritten
 cudaError_t box_binning(fep3m_ctx* c, int* count_out, int* cell_out);
 cudaError_t box_coeffs(fep3m_ctx* c, double* out);
 }  // namespace fep3m
