@@ -232,6 +232,47 @@ def large_workload(name, steps, warmup, flush, dev, torch, peaks):
     return res
 
 
+def box_workload(kind, steps, warmup, flush, dev, torch):
+    """The box with Dirichlet or Neumann data (Sec. "Alternate boundary conditions"), mixed, Phi and U:
+    the rock-salt ions of the headline workload moved to the element centres (offset h/2, so that the
+    jitter keeps every ion inside the box [0, L]^3), 32^3 box elements, grounded (g = 0) or zero-flux
+    data.  particles/s of set_particles + compute(Phi, U)."""
+    from paper_1503_08509_gb300 import api, workloads
+    pos_np, Q_np = workloads.rock_salt(32, L=1.0, jitter=1e-3, seed=2, offset=0.5)
+    N = len(Q_np)
+    pos = torch.tensor(pos_np, device=dev)
+    Q = torch.tensor(Q_np, device=dev)
+    eng = api.FEP3M(1.0, 32, precision="mixed", device=dev.index, dirichlet=kind == "dirichlet",
+                    neumann=kind == "neumann")
+    out = dict(phi=torch.empty(N, dtype=torch.float64, device=dev))
+    l0 = None
+    ms = []
+    for k in range(warmup + steps):
+        if k == warmup:
+            torch.cuda.synchronize()
+            l0 = eng.stats()["kernel_launches"]
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(eng.stream)
+        eng.set_particles(pos, Q)
+        r = eng.compute(phi=True, energy=True, forces=False, out=out)
+        e1.record(eng.stream)
+        e1.synchronize()
+        if k >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    st = eng.stats()
+    res = {"workload": "rock salt 32^3 ions at the element centres (jitter 1e-3 L) in a box of 32^3 elements, "
+                       "%s data (%s)" % (kind, "g = 0" if kind == "dirichlet" else "zero flux"),
+           "n": N, "steps": steps, "warmup": warmup, "value": round(N * steps / (sum(ms) / 1e3), 1),
+           "unit": "particles/s", "ms_per_step": round(sum(ms) / steps, 3),
+           "gpu_launches": int(round((st["kernel_launches"] - l0) / steps)),
+           "mg": {"refine_steps": st["refine_steps"], "rel_residual": st["mg_rel_residual"]},
+           "U": r["U"]}
+    eng.close()
+    return res
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist()
@@ -406,6 +447,8 @@ def run_ours(args):
         # the full-size workloads of the other configurations, mixed with forces (not the headline)
         line["workloads"] = {nm: large_workload(nm, st_, 3, flush, dev, torch, peaks)
                              for nm, st_ in (("water1m", 20), ("blobs4m", 10))}
+        for kind in ("dirichlet", "neumann"):
+            line["workloads"]["box_%s_nacl32" % kind] = box_workload(kind, 10, 3, flush, dev, torch)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -1152,7 +1152,8 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int cb
       umma_commit(smem_u32(mbar));
     }
     if (c + 1 < kc) load_units(c + 1);
-    const bool done = mbar_wait(smem_u32(mbar), (uint32_t)(c & 1));
+    // one warp polls the barrier; the others wait at the CTA barrier
+    const bool done = tid < 32 ? mbar_wait(smem_u32(mbar), (uint32_t)(c & 1)) : true;
     if (__syncthreads_or(!done)) {
       failed = true;
       break;

@@ -44,23 +44,32 @@ __device__ __forceinline__ int wrapn(int i, int n) {
 }
 
 template <class T> __device__ __forceinline__ T rsq(T x);
-// 1 / sqrt(x) in FP64 from the FP32 hardware estimate y (relative error
-// ~2^-22), refined by one third-order (Householder) step: with e = 1 - x y^2,
-// 1 / sqrt(x) = y (1 - e)^(-1/2) = y (1 + e/2 + 3 e^2 / 8 + O(e^3)), and the
-// dropped term is below 2^-64 (emulated worst case 0.9 ulp).  Outside
-// [2^-100, 2^100), where the FP32 estimate could under- or overflow
-// (including x = 0, coincident charges, and negative or NaN x), the FP64
-// division is used; the range test reads the exponent bits on the integer pipe.
+// the hardware estimate of 1 / sqrt(x) (PTX rsqrt.approx, relative error
+// about 2^-23; subnormal input and output flushed to zero, which the
+// squared distances of distinct charges never are)
+__device__ __forceinline__ float rsqrt_est(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// 1 / sqrt(x) in FP64 from the FP32 hardware estimate y, refined by one
+// third-order (Householder) step: with e = 1 - x y^2, 1 / sqrt(x) =
+// y (1 - e)^(-1/2) = y (1 + e/2 + 3 e^2 / 8 + O(e^3)), and the dropped term is
+// below 2^-64 (emulated worst case 0.9 ulp).  Outside [2^-100, 2^100), where
+// the FP32 estimate could under- or overflow (including x = 0, coincident
+// charges, and negative or NaN x), the FP64 division is used; the range test
+// reads the exponent bits on the integer pipe.
 template <> __device__ __forceinline__ double rsq<double>(double x) {
   const int bexp = __double2hiint(x) >> 20;   // sign and biased exponent
   if ((unsigned)(bexp - 923) >= 200u) return 1.0 / sqrt(x);
-  const double y = (double)rsqrtf((float)x);
+  const double y = (double)rsqrt_est((float)x);
   const double e = fma(-x * y, y, 1.0);
   return fma(y * e, fma(0.375, e, 0.5), y);
 }
-// the hardware reciprocal square root refined by one Newton step, y (3 - x y^2) / 2
+// the hardware estimate refined by one Newton step, y (3 - x y^2) / 2 (for x
+// = 0 the estimate is +inf and the step gives NaN: coincident charges)
 template <> __device__ __forceinline__ float rsq<float>(float x) {
-  const float y = rsqrtf(x);
+  const float y = rsqrt_est(x);
   return y * fmaf(-0.5f * x, y * y, 1.5f);
 }
 
@@ -224,8 +233,12 @@ struct Pair3Smem {
            3 * sw + 3 * hw + 32;
   }
   static constexpr size_t TILES = 6 * 8192;   // three bf16 pieces of A (64 x 64) and of B (64 x 64)
+  // tensor cores: the staged charges in a region of their own (staged while the contraction runs)
+  __host__ __device__ static size_t stgbytes() {
+    return (size_t)cap() * sizeof(typename vec4<T>::type) + ((size_t)cap() + 15) / 16 * 16;
+  }
   static size_t bytes(int n_sr) {
-    if (TC) return 1024 + TILES + rbytes(n_sr) + ints(n_sr) * sizeof(int) + 16;
+    if (TC) return 1024 + TILES + rbytes(n_sr) + stgbytes() + ints(n_sr) * sizeof(int) + 16;
     return region1(n_sr) + 2 * (size_t)OCH * 64 * ES + ints(n_sr) * sizeof(int) + (size_t)cap();
   }
 };
@@ -258,411 +271,124 @@ __device__ __forceinline__ int block_scan_excl(int v, int* wsum /* NT/32 + 1 */,
   return res;
 }
 
-// One CTA per brick of BX x BY x BZ elements: the screen field of every brick
-// element at its 64 nodes (written to Gscr, brick-major) and the singular sums
-// of every target charge in the brick (written to phi_s and E_s; with psi,
-// half of them to psi and gpsi as well: the singular adjoint for the weights
-// Q / 2 of the energy, whose kernel 1/r is symmetric).  TC: the
-// contraction on the tensor cores (FP32 only; Hb holds the table's bf16
-// pieces in the tiles' layout, err receives a bounded wait that gave up),
-// 512 threads and eight per target; otherwise CUDA cores, 256 threads and
-// four per target.
-template <class T, bool GRAD, bool TC>
-__global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, T h, const int* __restrict__ start,
-                                                             const int* __restrict__ count,
-                                                             const typename vec4<T>::type* __restrict__ part,
-                                                             const T* __restrict__ Cv, const T* __restrict__ rv,
-                                                             const uint4* __restrict__ Hb, const float2* __restrict__ H0,
-                                                             const float2* __restrict__ Hdf, T* __restrict__ Gscr, double* __restrict__ phi_s,
-                                                             double* __restrict__ E_s, double* __restrict__ psi,
-                                                             double* __restrict__ gpsi, int* __restrict__ err) {
-  static_assert(!TC || sizeof(T) == 4, "the tensor-core contraction is the FP32 path's");
-  constexpr int NT = TC ? PTC : PT, TPT = TC ? 8 : 4;
-  typedef typename vec4<T>::type V4;
-  typedef Pair3Smem<T, TC> SM;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nbx = (n + BX - 1) / BX, nby = (n + BY - 1) / BY;
-  const int E0x = (blockIdx.x % nbx) * BX, E0y = ((blockIdx.x / nbx) % nby) * BY, E0z = (blockIdx.x / (nbx * nby)) * BZ;
-  const int keep = n_sr + 1, noff = 2 * n_sr + 2, no3 = noff * noff * noff;
-  const int SW = 3 * BX + 2 * n_sr - 1, SF = BX + 2 * n_sr - 1, HW = BX + 2 * n_sr;
-  const int nb = 2 * n_sr + 1, nrow = nb * nb;
-  T *R, *A_c = nullptr, *H_c = nullptr;
-  V4* stg;
-  unsigned char* tiles = nullptr;
-  int* hs;                                                // halo element prefix, HW^3 + 1
-  if (TC) {
-    tiles = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // swizzle atoms on 1 KB
-    stg = (V4*)tiles;                                     // after the contraction
-    R = (T*)(tiles + SM::TILES);
-    hs = (int*)((unsigned char*)R + SM::rbytes(n_sr));
-  } else {
-    const size_t r1 = SM::region1(n_sr);
-    R = (T*)smem_raw;                                     // region 1: R, later the staged charges
-    stg = (V4*)smem_raw;
-    A_c = (T*)(smem_raw + r1);                            // [OCH][64] chunks of A and H (float pairs)
-    H_c = (T*)((unsigned char*)A_c + OCH * 64 * SM::ES);
-    hs = (int*)((unsigned char*)H_c + OCH * 64 * SM::ES);
+// Named CTA barriers (bar.sync id, n): groups of whole warps synchronise
+// among themselves (id 0 with the CTA's thread count is __syncthreads).
+__device__ __forceinline__ void group_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+// group_sync that also returns whether v was true in any thread of the group
+__device__ __forceinline__ bool group_sync_or(int id, int n, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
+// exclusive scan of one int per thread over a group of GN threads (gt its
+// index in the group, whole warps; barrier id); returns the prefix, writes
+// the total to *total
+template <int GN>
+__device__ __forceinline__ int group_scan_excl(int gt, int id, int v, int* wsum /* GN/32 + 1 */, int* total) {
+  const int lane = gt & 31, wid = gt >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
-  int* epre = hs + HW * HW * HW + 1;                      // BE + 1
-  int* flag = epre + BE + 1;
-  int* wsum = flag + 1;                                   // NT/32 + 1 scan scratch
-  int* otab = wsum + NT / 32 + 1;                         // no3: R base index of each offset
-  int* rtab = otab + no3;                                 // nb^2: halo offset of each (dy, dz) row
-  int* wv = rtab + nrow;                                  // 3 x SW wrapped vertex coords
-  int* we = wv + 3 * SW;                                  // 3 x HW wrapped halo element coords
-  // cap(): halo x index of each staged charge
-  unsigned char* sxb = TC ? tiles + SM::cap() * sizeof(V4) : (unsigned char*)(we + 3 * HW + 32);
-  uint64_t* mbar = (uint64_t*)(((uintptr_t)(we + 3 * HW) + 7) & ~(uintptr_t)7);   // TC only
-  uint32_t* tslot = (uint32_t*)(mbar + 1);
-  const int tid = threadIdx.x;
-  int ntarget;
-  {
-    int c0 = 0;
-    if (tid < BE) {
-      const int lx = E0x + (tid % BX), ly = E0y + (tid / BX) % BY, lz = E0z + tid / (BX * BY);
-      if (lx < n && ly < n && lz < n) c0 = count[lx + (int64_t)n * (ly + (int64_t)n * lz)];
+  if (lane == 31) wsum[wid] = x;
+  group_sync(id, GN);
+  if (gt == 0) {
+    int a = 0;
+    for (int w = 0; w < GN / 32; ++w) {
+      const int t = wsum[w];
+      wsum[w] = a;
+      a += t;
     }
-    const int pre = block_scan_excl<NT>(c0, wsum, &ntarget);
-    if (tid < BE) epre[tid] = pre;
-    if (tid == 0) epre[BE] = ntarget;
+    wsum[GN / 32] = a;
   }
-  if (ntarget == 0) return;
-  // index tables (no divisions in the hot loops below)
-  for (int o = tid; o < no3; o += NT) {
-    const int ox = o % noff - keep, oy = (o / noff) % noff - keep, oz = o / (noff * noff) - keep;
-    const int bx = ox == -keep ? SF : (ox == n_sr ? SF + BX : n_sr - 1 - ox);
-    const int by = oy == -keep ? SF : (oy == n_sr ? SF + BX : n_sr - 1 - oy);
-    const int bz = oz == -keep ? SF : (oz == n_sr ? SF + BX : n_sr - 1 - oz);
-    otab[o] = bx + SW * (by + SW * bz);
-  }
-  for (int r = tid; r < nrow; r += NT) rtab[r] = HW * ((r % nb) + HW * (r / nb));
-  {
-    const int E0[3] = {E0x, E0y, E0z};
-    for (int i = tid; i < 3 * SW; i += NT) {
-      const int a = i / SW, sa = i % SW;
-      int v;
-      if (sa < SF) v = E0[a] + sa - (n_sr - 1);
-      else if (sa < SF + BX) v = E0[a] + (sa - SF) + keep;
-      else v = E0[a] + (sa - SF - BX) - n_sr;
-      wv[i] = wrapn(v, n);
-    }
-    for (int i = tid; i < 3 * HW; i += NT) {
-      const int a = i / HW, ha = i % HW;
-      we[i] = wrapn(E0[a] - n_sr + ha, n);
-    }
-  }
-  __syncthreads();
-  // (1) extended vertex field (unrolled: the gathers of several entries in flight)
-#pragma unroll 4
-  for (int i = tid; i < SW * SW * SW; i += NT) {
-    const int sx = i % SW, sy = (i / SW) % SW, sz = i / (SW * SW);
-    const int tx = sx < SF ? 3 : (sx < SF + BX ? 2 : 1);     // allowed corners (bit0: 0, bit1: 1)
-    const int ty = sy < SF ? 3 : (sy < SF + BX ? 2 : 1);
-    const int tz = sz < SF ? 3 : (sz < SF + BX ? 2 : 1);
-    const int vx = wv[sx], vy = wv[SW + sy], vz = wv[2 * SW + sz];
-    T val = T(0);
-    const int64_t v = vx + (int64_t)n * (vy + (int64_t)n * vz);
-    if ((tx & ty & tz) == 3) {
-      val = rv[v];
-    } else {
-      // the vertex's eight corner terms are contiguous: two vector loads
-      const V4 c03 = reinterpret_cast<const V4*>(Cv + 8 * v)[0], c47 = reinterpret_cast<const V4*>(Cv + 8 * v)[1];
-      const T c8[8] = {c03.x, c03.y, c03.z, c03.w, c47.x, c47.y, c47.z, c47.w};
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
-        if (((tx >> kx) & 1) && ((ty >> ky) & 1) && ((tz >> kz) & 1)) val += c8[k];
-      }
-    }
-    if constexpr (!TC) {
-      // split once here into the hi + lo floats of the double-float
-      // contraction (each R value is read by several offsets; an FP32 value
-      // has lo = 0)
-      const float vh = (float)val;
-      reinterpret_cast<float2*>(R)[i] = make_float2(vh, (float)((double)val - (double)vh));
-    } else {
-      R[i] = val;
-    }
-  }
-  // (2) screen field
-  if constexpr (TC) {
-    // tensor cores: for each chunk of 64 offsets, the three bf16 pieces of A
-    // (64 brick elements x 64 offsets, built from R) and of H (64 nodes x 64
-    // offsets, precomputed) in shared memory; one thread issues the six
-    // piece products per K step of 16 into two TMEM accumulators (hi: the
-    // product of the leading pieces, lo: the other five).  The hi accumulator
-    // holds one chunk at a time and is added into registers after each chunk,
-    // so that no accumulation inside the tensor core spans more than 64 terms
-    // of the leading product; the chunk sums are added with compensation.  In
-    // the FP32 path the table is relative to each element's corners (see
-    // pair_relative_table), so these sums carry no large smooth part.  M = 128:
-    // rows 64 .. 127 of each A operand read the next tile and their results
-    // are unused.
-    const uint32_t tl = smem_u32(tiles);
-    if (tid < 32) {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tslot)));
-      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (tid == 0) mbar_init(smem_u32(mbar));
-    tc_fence_before();
-    __syncthreads();   // R complete; TMEM address and barrier visible
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-    // The field at node 0 (the one absolute column of the relative table, the
-    // element's potential level) is summed on the CUDA cores from the A values
-    // each thread splits anyway, with the table's hi + lo floats (H0) in two
-    // FP32 sums rounded to nearest (the tensor cores' accumulation would round
-    // it alike in every element, and U adds that up); eight partial sums per
-    // element, combined in the epilogue.
-    __shared__ float2 s0p[(PTC / 64) * BE];
-    float s0h = 0.f, s0l = 0.f;
-    const int l = tid & 63, g = tid >> 6;   // this thread's A unit: row l, chunk offsets 8 g .. 8 g + 7
-    const int lam = (l % BX) + SW * (((l / BX) % BY) + SW * (l / (BX * BY)));
-    const uint32_t aoff = sw128_off(l, 8 * g);
-    const int nch = (no3 + 63) / 64;
-    const int warp = tid >> 5, q4 = warp & 3, cg = warp >> 2;   // TMEM lanes 32 q4 .., columns 16 cg ..
-    const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 16 * cg;
-    float hsum[16], hcmp[16];   // rows 32 q4 + lane, columns 16 cg .. (warps with q4 < 2): compensated chunk sums
-#pragma unroll
-    for (int j = 0; j < 16; ++j) hsum[j] = hcmp[j] = 0.f;
-    bool failed = false;
-    for (int c = 0; c < nch; ++c) {
-      for (int i = tid; i < 1536; i += NT) cp_async16(tl + 24576 + 16 * i, Hb + (size_t)c * 1536 + i);
-      asm volatile("cp.async.commit_group;" ::: "memory");
-      uint32_t p0[4], p1[4], p2[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int o = 64 * c + 8 * g + 2 * j;
-        const float xa = o < no3 ? (float)R[otab[o] + lam] : 0.f;
-        const float xb = o + 1 < no3 ? (float)R[otab[o + 1] + lam] : 0.f;
-        bf16_split2(xa, xb, p0[j], p1[j], p2[j]);
-        if (o + 1 < no3) {
-          const float4 h2 = *reinterpret_cast<const float4*>(H0 + o);   // H0[o], H0[o + 1]
-          s0h = fmaf(xa, h2.x, fmaf(xb, h2.z, s0h));
-          s0l = fmaf(xa, h2.y, fmaf(xb, h2.w, s0l));
-        }
-      }
-      sts128(tl + aoff, p0);
-      sts128(tl + 8192 + aoff, p1);
-      sts128(tl + 16384 + aoff, p2);
-      cp_async_wait_all();
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint32_t a = tl + 32 * kk, b = tl + 24576 + 32 * kk;
-          const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
-          umma_bf16(tmem, umma_desc(a), umma_desc(b), UMMA_IDESC, kk > 0 ? 1u : 0u);         // a0 b0
-          umma_bf16(tmem + 64, umma_desc(a), umma_desc(b + 8192), UMMA_IDESC, acc);          // a0 b1
-          umma_bf16(tmem + 64, umma_desc(a + 8192), umma_desc(b), UMMA_IDESC, 1u);           // a1 b0
-          umma_bf16(tmem + 64, umma_desc(a), umma_desc(b + 16384), UMMA_IDESC, 1u);          // a0 b2
-          umma_bf16(tmem + 64, umma_desc(a + 8192), umma_desc(b + 8192), UMMA_IDESC, 1u);   // a1 b1
-          umma_bf16(tmem + 64, umma_desc(a + 16384), umma_desc(b), UMMA_IDESC, 1u);          // a2 b0
-        }
-        umma_commit(smem_u32(mbar));
-      }
-      const bool done = mbar_wait(smem_u32(mbar), (uint32_t)(c & 1));
-      if (__syncthreads_or(!done)) {
-        failed = true;
-        break;
-      }
-      tc_fence_after();
-      if (q4 < 2) {
-        uint32_t vh[16];
-        tmem_ld16(ta, vh);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float y = __uint_as_float(vh[j]) - hcmp[j], t = hsum[j] + y;
-          hcmp[j] = (t - hsum[j]) - y;
-          hsum[j] = t;
-        }
-      }
-      tc_fence_before();   // the next chunk's MMAs overwrite hi after the next barrier
-    }
-    if (failed) {
-      if (tid == 0) atomicExch(err, 1);
-      // a last bounded wait on both phases for MMAs still in flight
-      (void)mbar_wait(smem_u32(mbar), 0u);
-      (void)mbar_wait(smem_u32(mbar), 1u);
-    }
-    s0p[g * BE + l] = make_float2(s0h, s0l);
-    __syncthreads();
-    tc_fence_after();
-    if (!failed && q4 < 2) {
-      uint32_t vl[16];
-      tmem_ld16(ta + 64, vl);
-      tmem_wait_ld();
-      const int row = 32 * q4 + (tid & 31);
-      float* drow = (float*)Gscr + (int64_t)blockIdx.x * (BE * 64) + row * 64 + 16 * cg;
-      float c0 = (hsum[0] - hcmp[0]) + __uint_as_float(vl[0]);
-      if (cg == 0) {   // column 0 from the CUDA-core sums
-        double sum = 0.0;
-#pragma unroll
-        for (int q = 0; q < PTC / 64; ++q) {
-          const float2 v = s0p[q * BE + row];
-          sum += (double)v.x + (double)v.y;
-        }
-        c0 = (float)sum;
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        reinterpret_cast<float4*>(drow)[i] =
-            make_float4(i == 0 ? c0 : (hsum[4 * i] - hcmp[4 * i]) + __uint_as_float(vl[4 * i]),
-                        (hsum[4 * i + 1] - hcmp[4 * i + 1]) + __uint_as_float(vl[4 * i + 1]),
-                        (hsum[4 * i + 2] - hcmp[4 * i + 2]) + __uint_as_float(vl[4 * i + 2]),
-                        (hsum[4 * i + 3] - hcmp[4 * i + 3]) + __uint_as_float(vl[4 * i + 3]));
-    }
-    tc_fence_before();
-    __syncthreads();   // every TMEM read done; the tiles are free for the staged charges
-    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
-    if (failed) return;
-  } else {
-  // CUDA cores: 4 x 4 register tile, per-chunk partial sums added into a
-  // total, in double-float arithmetic on the FP32 pipes in both precisions
-  // (FP64 issues at a small fraction of the FP32 rate here): A and H are
-  // staged as hi + lo float pairs (the table's from FP64; an FP32 A has lo =
-  // 0), each product keeps its exact leading part (fused two-product) and the
-  // two cross terms, and the products are summed by two-sum into a hi + lo
-  // accumulator; each chunk's sum goes into an FP64 total, which keeps the
-  // relative error near 2^-48 of the chunk's sum of |A H| instead of growing
-  // over all offsets.  The FP32 path's result is then rounded to FP32.
-  const int eb = tid >> 4, mb = tid & 15;
-  // this thread stages entries i = tid + k PT: element l = i & 63 is fixed per thread
-  const int lst = tid & 63;
-  const int lam = (lst % BX) + SW * (((lst / BX) % BY) + SW * (lst / (BX * BY)));
-  constexpr int SPT = OCH * 64 / PT;   // staged entries per thread per chunk
-  T* gb = Gscr + (int64_t)blockIdx.x * (BE * 64);
-  {
-    // the table's hi + lo floats come precomputed (Hdf); R was split in (1)
-    float2 hpf[SPT];                   // next chunk's table values, fetched during this chunk
-#pragma unroll
-    for (int k = 0; k < SPT; ++k) {
-      const int i = tid + k * PT, o = i >> 6;
-      hpf[k] = o < no3 ? Hdf[(int64_t)o * 64 + (i & 63)] : make_float2(0.f, 0.f);
-    }
-    const float2* R2 = reinterpret_cast<const float2*>(R);
-    float sh[4][4], sl[4][4];
-    double tot[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) tot[i][j] = 0.0;
-    float2* A2 = reinterpret_cast<float2*>(A_c);
-    float2* H2 = reinterpret_cast<float2*>(H_c);
-    for (int o0 = 0; o0 < no3; o0 += OCH) {
-      __syncthreads();
-#pragma unroll
-      for (int k = 0; k < SPT; ++k) {
-        const int i = tid + k * PT;
-        const int o = o0 + (i >> 6);
-        H2[i] = hpf[k];
-        A2[i] = o < no3 ? R2[otab[o] + lam] : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
-      if (o0 + OCH < no3) {
-#pragma unroll
-        for (int k = 0; k < SPT; ++k) {
-          const int i = tid + k * PT, o = o0 + OCH + (i >> 6);
-          hpf[k] = o < no3 ? Hdf[(int64_t)o * 64 + (i & 63)] : make_float2(0.f, 0.f);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
-#pragma unroll 2
-      for (int oi = 0; oi < OCH; ++oi) {
-        const float4* ap = reinterpret_cast<const float4*>(A2 + oi * 64 + 4 * eb);
-        const float4* hp = reinterpret_cast<const float4*>(H2 + oi * 64 + 4 * mb);
-        const float4 a01 = ap[0], a23 = ap[1], h01 = hp[0], h23 = hp[1];
-        const float ah[4] = {a01.x, a01.z, a23.x, a23.z}, al[4] = {a01.y, a01.w, a23.y, a23.w};
-        const float hh[4] = {h01.x, h01.z, h23.x, h23.z}, hl[4] = {h01.y, h01.w, h23.y, h23.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float p = ah[i] * hh[j];
-            float e = fmaf(ah[i], hh[j], -p);
-            e = fmaf(ah[i], hl[j], e);
-            e = fmaf(al[i], hh[j], e);
-            const float t = sh[i][j] + p, z = t - sh[i][j];
-            sl[i][j] += ((sh[i][j] - (t - z)) + (p - z)) + e;
-            sh[i][j] = t;
-          }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) tot[i][j] += (double)sh[i][j] + (double)sl[i][j];
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      V4 v;
-      v.x = (T)tot[i][0];
-      v.y = (T)tot[i][1];
-      v.z = (T)tot[i][2];
-      v.w = (T)tot[i][3];
-      *reinterpret_cast<V4*>(gb + (4 * eb + i) * 64 + 4 * mb) = v;
-    }
-  }
-  // Region 1 (R) was last read before the chunk loop's final barrier, so the
-  // staging below may overwrite it without another one.
-  }
-  // (3) stage the halo charges if they fit (region 1 is free now)
+  group_sync(id, GN);
+  const int res = wsum[wid] + x - v;
+  *total = wsum[GN / 32];
+  group_sync(id, GN);
+  return res;
+}
+
+constexpr int SG = 256;   // threads of the short-range sums (the whole CTA on the CUDA cores, half of it
+                          // beside the tensor-core contraction)
+
+// Stage the charges of the brick's short-range halo (HW^3 elements) in shared
+// memory in element order, with each charge's halo x index, if they fit (cap);
+// hs[i] = the first staged slot of halo element i, hs[HW^3] = the total.  By
+// SG threads (gt, barrier id).  Returns whether the charges were staged.
+template <class T>
+__device__ bool stage_halo(int gt, int id, int n, int HW, const int* __restrict__ we, const int* __restrict__ start,
+                           const int* __restrict__ count, const typename vec4<T>::type* __restrict__ part, int cap,
+                           typename vec4<T>::type* stg, unsigned char* sxb, int* hs, int* flag, int* wsum) {
   const int nh = HW * HW * HW;
-  {
-    const int per = (nh + NT - 1) / NT, i0 = tid * per;
-    int cnt[8], gid[8];   // per <= 8 for n_sr <= 4 (nh <= 1728)
-    int sum = 0;
+  const int per = (nh + SG - 1) / SG, i0 = gt * per;
+  int cnt[8], gid[8];   // per <= 7 for n_sr <= 4 (nh <= 1728)
+  int sum = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int i = i0 + k;
-      cnt[k] = 0;
-      gid[k] = 0;
-      if (k < per && i < nh) {
-        const int hx = i % HW, hy = (i / HW) % HW, hz = i / (HW * HW);
-        gid[k] = we[hx] + n * (we[HW + hy] + n * we[2 * HW + hz]);
-        cnt[k] = count[gid[k]];
-      }
-      sum += cnt[k];
+  for (int k = 0; k < 8; ++k) {
+    const int i = i0 + k;
+    cnt[k] = 0;
+    gid[k] = 0;
+    if (k < per && i < nh) {
+      const int hx = i % HW, hy = (i / HW) % HW, hz = i / (HW * HW);
+      gid[k] = we[hx] + n * (we[HW + hy] + n * we[2 * HW + hz]);
+      cnt[k] = count[gid[k]];
     }
-    int total;
-    int run = block_scan_excl<NT>(sum, wsum, &total);
-    const bool fits = total <= SM::cap();
+    sum += cnt[k];
+  }
+  int total;
+  int run = group_scan_excl<SG>(gt, id, sum, wsum, &total);
+  const bool fits = total <= cap;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int i = i0 + k;
-      if (k < per && i < nh) {
-        hs[i] = run;
-        if (fits) {
-          const int j0 = start[gid[k]];
-          const unsigned char hx = (unsigned char)(i % HW);
-          for (int q = 0; q < cnt[k]; ++q) {
-            stg[run + q] = part[j0 + q];
-            sxb[run + q] = hx;
-          }
+  for (int k = 0; k < 8; ++k) {
+    const int i = i0 + k;
+    if (k < per && i < nh) {
+      hs[i] = run;
+      if (fits) {
+        const int j0 = start[gid[k]];
+        const unsigned char hx = (unsigned char)(i % HW);
+        for (int q = 0; q < cnt[k]; ++q) {
+          stg[run + q] = part[j0 + q];
+          sxb[run + q] = hx;
         }
       }
-      run += cnt[k];
     }
-    if (tid == 0) {
-      hs[nh] = total;
-      flag[0] = fits;
-    }
+    run += cnt[k];
   }
-  __syncthreads();
-  const bool staged = flag[0] != 0;
-  // (4) TPT threads per target, each summing the rows r = q, q + TPT, ... of
-  // the target's block; a shuffle tree combines them.  A row (dy, dz) of the
-  // block is 2 n_sr + 1 consecutive halo elements, so its staged charges are
-  // one run; each row's terms are summed in FP32 and the row sums are added
-  // with compensation.
-  const int q = tid & (TPT - 1);
-  for (int tb = 0; tb < ntarget; tb += NT / TPT) {
-    const int k = tb + tid / TPT;
+  if (gt == 0) {
+    hs[nh] = total;
+    flag[0] = fits;
+  }
+  group_sync(id, SG);
+  return flag[0] != 0;
+}
+
+// Singular sums of every target charge in the brick, by SG threads (gt), four
+// per target: each walks the rows r = q, q + 4, ... of its target's block (a
+// row (dy, dz) is 2 n_sr + 1 consecutive halo elements, so its staged charges
+// are one run), two charges per step, each row's terms summed in order in
+// FP32 and the row sums added with compensation; a shuffle tree combines the
+// four.  Unstaged (dense halo): the same rows from global memory, element by
+// element.  Writes phi_s and E_s (and half of them to psi, gpsi).
+template <class T, bool GRAD>
+__device__ void singular_targets(int gt, bool staged, int n, int n_sr, T h, int E0x, int E0y, int E0z, int HW,
+                                 int ntarget, const int* __restrict__ epre, const int* __restrict__ hs,
+                                 const int* __restrict__ rtab, const int* __restrict__ we,
+                                 const typename vec4<T>::type* stg, const unsigned char* sxb,
+                                 const int* __restrict__ start, const int* __restrict__ count,
+                                 const typename vec4<T>::type* __restrict__ part, double* __restrict__ phi_s,
+                                 double* __restrict__ E_s, double* __restrict__ psi, double* __restrict__ gpsi) {
+  typedef typename vec4<T>::type V4;
+  constexpr int TPT = 4;
+  const int nb = 2 * n_sr + 1, nrow = nb * nb;
+  const int q = gt & (TPT - 1);
+  for (int tb = 0; tb < ntarget; tb += SG / TPT) {
+    const int k = tb + gt / TPT;
     const bool valid = k < ntarget;
     T v4[4] = {T(0), T(0), T(0), T(0)};
     int slot = 0;
@@ -678,43 +404,59 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
       const int ex = E0x + lx, ey = E0y + ly, ez = E0z + lz;
       const int kk = k - epre[l];
       slot = start[ex + (int64_t)n * (ey + (int64_t)n * ez)] + kk;
-      const V4 pt = part[slot];
       const int base = lx + HW * (ly + HW * lz);          // halo index of block offset (-n_sr, -n_sr, -n_sr)
       const int cx = lx + n_sr;                           // the target's halo x index
       Acc<T> ps, fx, fy, fz;
       if (staged) {
         const int self = hs[base + n_sr * (1 + HW + HW * HW)] + kk;
-        for (int r = q; r < nrow; r += TPT) {
-          const int h0 = base + rtab[r];
-          const int j0 = hs[h0], j1 = hs[h0 + nb];
-          const T ddy = T(r % nb - n_sr), ddz = T(r / nb - n_sr);
-          T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-#pragma unroll 4
-          for (int j = j0; j < j1; ++j) {
-            const V4 pj = stg[j];
-            const T ddx = T((int)sxb[j] - cx);
-            // element units (1/h applied once per target, in FP64), fused r^2 and sums
-            const T rx = ddx + (pj.x - pt.x), ry = ddy + (pj.y - pt.y), rz = ddz + (pj.z - pt.z);
-            const T ir = j == self ? T(0) : rsq<T>(fmaw(rx, rx, fmaw(ry, ry, rz * rz)));
-            const T qi = pj.w * ir;
-            s0 += qi;
+        const V4 pt = stg[self];
+        const T cxf = T(cx);
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0), ddy = T(0), ddz = T(0);
+        int r = q, j = 0, je = 0;
+        for (;;) {
+          if (j >= je) {
+            ps.add(s0);
             if (GRAD) {
-              const T f3 = qi * (ir * ir);
-              s1 = fmaw(f3, rx, s1);
-              s2 = fmaw(f3, ry, s2);
-              s3 = fmaw(f3, rz, s3);
+              fx.add(s1);
+              fy.add(s2);
+              fz.add(s3);
             }
+            s0 = s1 = s2 = s3 = T(0);
+            if (r >= nrow) break;
+            const int rt = rtab[r];
+            const int h0 = base + (rt & 0xFFFF);
+            j = hs[h0];
+            je = hs[h0 + nb];
+            ddy = T(((rt >> 16) & 0xFF) - n_sr);
+            ddz = T((rt >> 24) - n_sr);
+            r += TPT;
+            continue;
           }
-          ps.add(s0);
+          const bool two = j + 1 < je;
+          const int jb = two ? j + 1 : j;
+          const V4 pa = stg[j], pb = stg[jb];
+          // element units (1/h applied once per target, in FP64), fused r^2 and sums
+          const T rxa = (T(sxb[j]) - cxf) + (pa.x - pt.x), rya = ddy + (pa.y - pt.y), rza = ddz + (pa.z - pt.z);
+          const T rxb = (T(sxb[jb]) - cxf) + (pb.x - pt.x), ryb = ddy + (pb.y - pt.y), rzb = ddz + (pb.z - pt.z);
+          const T ira = j == self ? T(0) : rsq<T>(fmaw(rxa, rxa, fmaw(rya, rya, rza * rza)));
+          const T irb = (!two || jb == self) ? T(0) : rsq<T>(fmaw(rxb, rxb, fmaw(ryb, ryb, rzb * rzb)));
+          const T qa = pa.w * ira, qb = pb.w * irb;
+          s0 += qa;
+          s0 += qb;
           if (GRAD) {
-            fx.add(s1);
-            fy.add(s2);
-            fz.add(s3);
+            const T f3a = qa * (ira * ira), f3b = qb * (irb * irb);
+            s1 = fmaw(f3a, rxa, s1);
+            s2 = fmaw(f3a, rya, s2);
+            s3 = fmaw(f3a, rza, s3);
+            s1 = fmaw(f3b, rxb, s1);
+            s2 = fmaw(f3b, ryb, s2);
+            s3 = fmaw(f3b, rzb, s3);
           }
+          j += 2;
         }
       } else {
-        // charges not staged (dense halo): the same rows from global memory,
-        // element by element (a row may wrap around the periodic box)
+        // a row may wrap around the periodic box
+        const V4 pt = part[slot];
         for (int r = q; r < nrow; r += TPT) {
           const int ay = r % nb, az = r / nb;
           const int64_t rowg = (int64_t)n * (we[HW + ly + ay] + (int64_t)n * we[2 * HW + lz + az]);
@@ -769,6 +511,392 @@ __global__ void __launch_bounds__(TC ? PTC : PT) k_pair_screen(int n, int n_sr, 
         }
       }
     }
+  }
+}
+
+// One CTA per brick of BX x BY x BZ elements: the screen field of every brick
+// element at its 64 nodes (written to Gscr, brick-major) and the singular sums
+// of every target charge in the brick (written to phi_s and E_s; with psi,
+// half of them to psi and gpsi as well: the singular adjoint for the weights
+// Q / 2 of the energy, whose kernel 1/r is symmetric).  TC: the
+// contraction on the tensor cores (FP32 only; Hb holds the table's bf16
+// pieces in the tiles' layout, err receives a bounded wait that gave up),
+// 512 threads and eight per target; otherwise CUDA cores, 256 threads and
+// four per target.
+template <class T, bool GRAD, bool TC>
+__global__ void __launch_bounds__(TC ? PTC : PT, TC ? 2 : 1) k_pair_screen(int n, int n_sr, T h, const int* __restrict__ start,
+                                                             const int* __restrict__ count,
+                                                             const typename vec4<T>::type* __restrict__ part,
+                                                             const T* __restrict__ Cv, const T* __restrict__ rv,
+                                                             const uint4* __restrict__ Hb, const float2* __restrict__ H0,
+                                                             const float2* __restrict__ Hdf, T* __restrict__ Gscr, double* __restrict__ phi_s,
+                                                             double* __restrict__ E_s, double* __restrict__ psi,
+                                                             double* __restrict__ gpsi, int* __restrict__ err) {
+  static_assert(!TC || sizeof(T) == 4, "the tensor-core contraction is the FP32 path's");
+  static_assert(PT == SG && PTC == 2 * SG, "the short-range sums take the whole CUDA-core CTA, half the tensor-core one");
+  constexpr int NT = TC ? PTC : PT;
+  typedef typename vec4<T>::type V4;
+  typedef Pair3Smem<T, TC> SM;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nbx = (n + BX - 1) / BX, nby = (n + BY - 1) / BY;
+  const int E0x = (blockIdx.x % nbx) * BX, E0y = ((blockIdx.x / nbx) % nby) * BY, E0z = (blockIdx.x / (nbx * nby)) * BZ;
+  const int keep = n_sr + 1, noff = 2 * n_sr + 2, no3 = noff * noff * noff;
+  const int SW = 3 * BX + 2 * n_sr - 1, SF = BX + 2 * n_sr - 1, HW = BX + 2 * n_sr;
+  const int nb = 2 * n_sr + 1, nrow = nb * nb;
+  T *R, *A_c = nullptr, *H_c = nullptr;
+  V4* stg;
+  unsigned char* tiles = nullptr;
+  int* hs;                                                // halo element prefix, HW^3 + 1
+  unsigned char* sxb;                                     // cap(): halo x index of each staged charge
+  if (TC) {
+    tiles = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // swizzle atoms on 1 KB
+    R = (T*)(tiles + SM::TILES);
+    stg = (V4*)((unsigned char*)R + SM::rbytes(n_sr));
+    sxb = (unsigned char*)(stg + SM::cap());
+    hs = (int*)((unsigned char*)stg + SM::stgbytes());
+  } else {
+    const size_t r1 = SM::region1(n_sr);
+    R = (T*)smem_raw;                                     // region 1: R, later the staged charges
+    stg = (V4*)smem_raw;
+    A_c = (T*)(smem_raw + r1);                            // [OCH][64] chunks of A and H (float pairs)
+    H_c = (T*)((unsigned char*)A_c + OCH * 64 * SM::ES);
+    hs = (int*)((unsigned char*)H_c + OCH * 64 * SM::ES);
+  }
+  int* epre = hs + HW * HW * HW + 1;                      // BE + 1
+  int* flag = epre + BE + 1;
+  int* wsum = flag + 1;                                   // NT/32 + 1 scan scratch
+  int* otab = wsum + NT / 32 + 1;                         // no3: R base index of each offset
+  int* rtab = otab + no3;                                 // nb^2 rows (dy, dz): halo offset | ay << 16 | az << 24
+  int* wv = rtab + nrow;                                  // 3 x SW wrapped vertex coords times 1, n, n^2
+  int* we = wv + 3 * SW;                                  // 3 x HW wrapped halo element coords
+  if (!TC) sxb = (unsigned char*)(we + 3 * HW + 32);
+  uint64_t* mbar = (uint64_t*)(((uintptr_t)(we + 3 * HW) + 7) & ~(uintptr_t)7);   // TC only
+  uint32_t* tslot = (uint32_t*)(mbar + 1);
+  const int tid = threadIdx.x;
+  int ntarget;
+  {
+    int c0 = 0;
+    if (tid < BE) {
+      const int lx = E0x + (tid % BX), ly = E0y + (tid / BX) % BY, lz = E0z + tid / (BX * BY);
+      if (lx < n && ly < n && lz < n) c0 = count[lx + (int64_t)n * (ly + (int64_t)n * lz)];
+    }
+    const int pre = block_scan_excl<NT>(c0, wsum, &ntarget);
+    if (tid < BE) epre[tid] = pre;
+    if (tid == 0) epre[BE] = ntarget;
+  }
+  if (ntarget == 0) return;
+  // index tables (no divisions in the hot loops below)
+  for (int o = tid; o < no3; o += NT) {
+    const int ox = o % noff - keep, oy = (o / noff) % noff - keep, oz = o / (noff * noff) - keep;
+    const int bx = ox == -keep ? SF : (ox == n_sr ? SF + BX : n_sr - 1 - ox);
+    const int by = oy == -keep ? SF : (oy == n_sr ? SF + BX : n_sr - 1 - oy);
+    const int bz = oz == -keep ? SF : (oz == n_sr ? SF + BX : n_sr - 1 - oz);
+    otab[o] = bx + SW * (by + SW * bz);
+  }
+  for (int r = tid; r < nrow; r += NT) rtab[r] = HW * ((r % nb) + HW * (r / nb)) | (r % nb) << 16 | (r / nb) << 24;
+  {
+    const int E0[3] = {E0x, E0y, E0z};
+    for (int i = tid; i < 3 * SW; i += NT) {
+      const int a = i / SW, sa = i % SW;
+      int v;
+      if (sa < SF) v = E0[a] + sa - (n_sr - 1);
+      else if (sa < SF + BX) v = E0[a] + (sa - SF) + keep;
+      else v = E0[a] + (sa - SF - BX) - n_sr;
+      wv[i] = wrapn(v, n) * (a == 0 ? 1 : (a == 1 ? n : n * n));   // the vertex id's term of axis a
+    }
+    for (int i = tid; i < 3 * HW; i += NT) {
+      const int a = i / HW, ha = i % HW;
+      we[i] = wrapn(E0[a] - n_sr + ha, n);
+    }
+  }
+  __syncthreads();
+  // (1) extended vertex field (unrolled: the gathers of several entries in flight); the
+  // coordinates of entries i = tid + k NT advanced without divisions
+  const int dsx = NT % SW, dsy = (NT / SW) % SW, dsz = NT / (SW * SW);
+  int sx = tid % SW, sy = (tid / SW) % SW, sz = tid / (SW * SW);
+#pragma unroll 4
+  for (int i = tid; i < SW * SW * SW; i += NT) {
+    // allowed corners k = kx + 2 ky + 4 kz as a bit mask: per axis both
+    // corners, corner 1 only (k with kx = 1: 0xAA) or corner 0 only (0x55)
+    const unsigned mx = sx < SF ? 0xFFu : (sx < SF + BX ? 0xAAu : 0x55u);
+    const unsigned my = sy < SF ? 0xFFu : (sy < SF + BX ? 0xCCu : 0x33u);
+    const unsigned mz = sz < SF ? 0xFFu : (sz < SF + BX ? 0xF0u : 0x0Fu);
+    const unsigned mask = mx & my & mz;
+    const int v = wv[sx] + wv[SW + sy] + wv[2 * SW + sz];   // < n^3 <= 2^30
+    T val = T(0);
+    if (mask == 0xFFu) {
+      val = rv[v];
+    } else {
+      // the vertex's eight corner terms are contiguous: two vector loads
+      const V4 c03 = reinterpret_cast<const V4*>(Cv + 8 * v)[0], c47 = reinterpret_cast<const V4*>(Cv + 8 * v)[1];
+      const T c8[8] = {c03.x, c03.y, c03.z, c03.w, c47.x, c47.y, c47.z, c47.w};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) val += ((mask >> k) & 1u) ? c8[k] : T(0);
+    }
+    if constexpr (!TC) {
+      // split once here into the hi + lo floats of the double-float
+      // contraction (each R value is read by several offsets; an FP32 value
+      // has lo = 0)
+      const float vh = (float)val;
+      reinterpret_cast<float2*>(R)[i] = make_float2(vh, (float)((double)val - (double)vh));
+    } else {
+      R[i] = val;
+    }
+    sx += dsx;
+    sy += dsy;
+    sz += dsz;
+    if (sx >= SW) {
+      sx -= SW;
+      ++sy;
+    }
+    if (sy >= SW) {
+      sy -= SW;
+      ++sz;
+    }
+  }
+  // (2) screen field and (3) singular sums
+  if constexpr (TC) {
+    // Tensor cores: two groups of eight warps run side by side.  Group A
+    // (warps with warp mod 4 < 2, the ones that can read TMEM lanes 0 .. 63)
+    // computes the screen field: for each chunk of 64 offsets, the three
+    // bf16 pieces of A (64 brick elements x 64 offsets, built from R) and of H
+    // (64 nodes x 64 offsets, precomputed) in shared memory; one thread
+    // issues the six piece products per K step of 16 into two TMEM
+    // accumulators (hi: the product of the leading pieces, lo: the other
+    // five).  The hi accumulator holds one chunk at a time and is added into
+    // registers after each chunk, so that no accumulation inside the tensor
+    // core spans more than 64 terms of the leading product; the chunk sums are
+    // added with compensation.  In the FP32 path the table is relative to each
+    // element's corners (see pair_relative_table), so these sums carry no
+    // large smooth part.  M = 128: rows 64 .. 127 of each A operand read the
+    // next tile and their results are unused.  Group B stages the halo
+    // charges in a region of their own and computes the singular sums
+    // meanwhile.
+    const uint32_t tl = smem_u32(tiles);
+    if (tid < 32) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tslot)));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) mbar_init(smem_u32(mbar));
+    tc_fence_before();
+    __syncthreads();   // R complete; TMEM address and barrier visible
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const int warp = tid >> 5;
+    const int gt = ((warp >> 2) * 2 + (warp & 1)) * 32 + (tid & 31);   // the thread's index in its group
+    bool failed = false;
+    if ((warp & 3) < 2) {
+      // The field at node 0 (the one absolute column of the relative table,
+      // the element's potential level) is summed on the CUDA cores from the A
+      // values each thread splits anyway, with the table's hi + lo floats (H0)
+      // in two FP32 sums rounded to nearest (the tensor cores' accumulation
+      // would round it alike in every element, and U adds that up); four
+      // partial sums per element, combined in the epilogue.
+      __shared__ float2 s0p[(SG / 64) * BE];
+      float s0h = 0.f, s0l = 0.f;
+      const int l = gt & 63, g = gt >> 6;   // this thread's A units: row l, chunk offsets 8 g .. and 8 (g + 4) ..
+      const int lam = (l % BX) + SW * (((l / BX) % BY) + SW * (l / (BX * BY)));
+      const uint32_t aoff[2] = {sw128_off(l, 8 * g), sw128_off(l, 8 * (g + 4))};
+      const int nch = (no3 + 63) / 64;
+      const int q4 = warp & 3, cg = warp >> 2;   // TMEM lanes 32 q4 .., columns 16 cg ..
+      const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 16 * cg;
+      float hsum[16], hcmp[16];   // rows 32 q4 + lane, columns 16 cg ..: compensated chunk sums
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) hsum[jj] = hcmp[jj] = 0.f;
+      for (int c = 0; c < nch; ++c) {
+        for (int i = gt; i < 1536; i += SG) cp_async16(tl + 24576 + 16 * i, Hb + (size_t)c * 1536 + i);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          uint32_t p0[4], p1[4], p2[4];
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int o = 64 * c + 8 * (g + 4 * hf) + 2 * jj;
+            const float xa = o < no3 ? (float)R[otab[o] + lam] : 0.f;
+            const float xb = o + 1 < no3 ? (float)R[otab[o + 1] + lam] : 0.f;
+            bf16_split2(xa, xb, p0[jj], p1[jj], p2[jj]);
+            if (o + 1 < no3) {
+              const float4 h2 = *reinterpret_cast<const float4*>(H0 + o);   // H0[o], H0[o + 1]
+              s0h = fmaf(xa, h2.x, fmaf(xb, h2.z, s0h));
+              s0l = fmaf(xa, h2.y, fmaf(xb, h2.w, s0l));
+            }
+          }
+          sts128(tl + aoff[hf], p0);
+          sts128(tl + 8192 + aoff[hf], p1);
+          sts128(tl + 16384 + aoff[hf], p2);
+        }
+        cp_async_wait_all();
+        fence_async_smem();
+        group_sync(1, SG);
+        if (gt == 0) {
+          tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t a = tl + 32 * kk, b = tl + 24576 + 32 * kk;
+            const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+            umma_bf16(tmem, umma_desc(a), umma_desc(b), UMMA_IDESC, kk > 0 ? 1u : 0u);         // a0 b0
+            umma_bf16(tmem + 64, umma_desc(a), umma_desc(b + 8192), UMMA_IDESC, acc);          // a0 b1
+            umma_bf16(tmem + 64, umma_desc(a + 8192), umma_desc(b), UMMA_IDESC, 1u);           // a1 b0
+            umma_bf16(tmem + 64, umma_desc(a), umma_desc(b + 16384), UMMA_IDESC, 1u);          // a0 b2
+            umma_bf16(tmem + 64, umma_desc(a + 8192), umma_desc(b + 8192), UMMA_IDESC, 1u);   // a1 b1
+            umma_bf16(tmem + 64, umma_desc(a + 16384), umma_desc(b), UMMA_IDESC, 1u);          // a2 b0
+          }
+          umma_commit(smem_u32(mbar));
+        }
+        // one warp polls the barrier; the group waits at its named barrier
+        const bool done = warp == 0 ? mbar_wait(smem_u32(mbar), (uint32_t)(c & 1)) : true;
+        if (group_sync_or(1, SG, !done)) {
+          failed = true;
+          break;
+        }
+        tc_fence_after();
+        uint32_t vh[16];
+        tmem_ld16(ta, vh);
+        tmem_wait_ld();
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const float y = __uint_as_float(vh[jj]) - hcmp[jj], t = hsum[jj] + y;
+          hcmp[jj] = (t - hsum[jj]) - y;
+          hsum[jj] = t;
+        }
+        tc_fence_before();   // the next chunk's MMAs overwrite hi after the next barrier
+      }
+      if (failed) {
+        if (gt == 0) atomicExch(err, 1);
+        // a last bounded wait on both phases for MMAs still in flight, and for the table copy
+        (void)mbar_wait(smem_u32(mbar), 0u);
+        (void)mbar_wait(smem_u32(mbar), 1u);
+        cp_async_wait_all();
+      }
+      s0p[g * BE + l] = make_float2(s0h, s0l);
+      group_sync(1, SG);
+      tc_fence_after();
+      if (!failed) {
+        uint32_t vl[16];
+        tmem_ld16(ta + 64, vl);
+        tmem_wait_ld();
+        const int row = 32 * q4 + (tid & 31);
+        float* drow = (float*)Gscr + (int64_t)blockIdx.x * (BE * 64) + row * 64 + 16 * cg;
+        float c0 = (hsum[0] - hcmp[0]) + __uint_as_float(vl[0]);
+        if (cg == 0) {   // column 0 from the CUDA-core sums
+          double sum = 0.0;
+#pragma unroll
+          for (int qq = 0; qq < SG / 64; ++qq) {
+            const float2 v = s0p[qq * BE + row];
+            sum += (double)v.x + (double)v.y;
+          }
+          c0 = (float)sum;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          reinterpret_cast<float4*>(drow)[i] =
+              make_float4(i == 0 ? c0 : (hsum[4 * i] - hcmp[4 * i]) + __uint_as_float(vl[4 * i]),
+                          (hsum[4 * i + 1] - hcmp[4 * i + 1]) + __uint_as_float(vl[4 * i + 1]),
+                          (hsum[4 * i + 2] - hcmp[4 * i + 2]) + __uint_as_float(vl[4 * i + 2]),
+                          (hsum[4 * i + 3] - hcmp[4 * i + 3]) + __uint_as_float(vl[4 * i + 3]));
+      }
+      tc_fence_before();
+    } else {
+      const bool staged = stage_halo<T>(gt, 2, n, HW, we, start, count, part, SM::cap(), stg, sxb, hs, flag, wsum);
+      singular_targets<T, GRAD>(gt, staged, n, n_sr, h, E0x, E0y, E0z, HW, ntarget, epre, hs, rtab, we, stg, sxb,
+                                start, count, part, phi_s, E_s, psi, gpsi);
+    }
+    __syncthreads();   // every TMEM read done
+    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+  } else {
+    // CUDA cores: 4 x 4 register tile, per-chunk partial sums added into a
+    // total, in double-float arithmetic on the FP32 pipes in both precisions
+    // (FP64 issues at a small fraction of the FP32 rate here): A and H are
+    // staged as hi + lo float pairs (the table's from FP64; an FP32 A has lo =
+    // 0), each product keeps its exact leading part (fused two-product) and the
+    // two cross terms, and the products are summed by two-sum into a hi + lo
+    // accumulator; each chunk's sum goes into an FP64 total, which keeps the
+    // relative error near 2^-48 of the chunk's sum of |A H| instead of growing
+    // over all offsets.  The FP32 path's result is then rounded to FP32.
+    const int eb = tid >> 4, mb = tid & 15;
+    // this thread stages entries i = tid + k PT: element l = i & 63 is fixed per thread
+    const int lst = tid & 63;
+    const int lam = (lst % BX) + SW * (((lst / BX) % BY) + SW * (lst / (BX * BY)));
+    constexpr int SPT = OCH * 64 / PT;   // staged entries per thread per chunk
+    T* gb = Gscr + (int64_t)blockIdx.x * (BE * 64);
+    {
+      // the table's hi + lo floats come precomputed (Hdf); R was split in (1)
+      float2 hpf[SPT];                   // next chunk's table values, fetched during this chunk
+#pragma unroll
+      for (int k = 0; k < SPT; ++k) {
+        const int i = tid + k * PT, o = i >> 6;
+        hpf[k] = o < no3 ? Hdf[(int64_t)o * 64 + (i & 63)] : make_float2(0.f, 0.f);
+      }
+      const float2* R2 = reinterpret_cast<const float2*>(R);
+      float sh[4][4], sl[4][4];
+      double tot[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tot[i][j] = 0.0;
+      float2* A2 = reinterpret_cast<float2*>(A_c);
+      float2* H2 = reinterpret_cast<float2*>(H_c);
+      for (int o0 = 0; o0 < no3; o0 += OCH) {
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+          const int i = tid + k * PT;
+          const int o = o0 + (i >> 6);
+          H2[i] = hpf[k];
+          A2[i] = o < no3 ? R2[otab[o] + lam] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (o0 + OCH < no3) {
+#pragma unroll
+          for (int k = 0; k < SPT; ++k) {
+            const int i = tid + k * PT, o = o0 + OCH + (i >> 6);
+            hpf[k] = o < no3 ? Hdf[(int64_t)o * 64 + (i & 63)] : make_float2(0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
+#pragma unroll 2
+        for (int oi = 0; oi < OCH; ++oi) {
+          const float4* ap = reinterpret_cast<const float4*>(A2 + oi * 64 + 4 * eb);
+          const float4* hp = reinterpret_cast<const float4*>(H2 + oi * 64 + 4 * mb);
+          const float4 a01 = ap[0], a23 = ap[1], h01 = hp[0], h23 = hp[1];
+          const float ah[4] = {a01.x, a01.z, a23.x, a23.z}, al[4] = {a01.y, a01.w, a23.y, a23.w};
+          const float hh[4] = {h01.x, h01.z, h23.x, h23.z}, hl[4] = {h01.y, h01.w, h23.y, h23.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const float p = ah[i] * hh[j];
+              float e = fmaf(ah[i], hh[j], -p);
+              e = fmaf(ah[i], hl[j], e);
+              e = fmaf(al[i], hh[j], e);
+              const float t = sh[i][j] + p, z = t - sh[i][j];
+              sl[i][j] += ((sh[i][j] - (t - z)) + (p - z)) + e;
+              sh[i][j] = t;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) tot[i][j] += (double)sh[i][j] + (double)sl[i][j];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        V4 v;
+        v.x = (T)tot[i][0];
+        v.y = (T)tot[i][1];
+        v.z = (T)tot[i][2];
+        v.w = (T)tot[i][3];
+        *reinterpret_cast<V4*>(gb + (4 * eb + i) * 64 + 4 * mb) = v;
+      }
+    }
+    // Region 1 (R) was last read before the chunk loop's final barrier, so the
+    // staging may overwrite it without another one.
+    const bool staged = stage_halo<T>(tid, 0, n, HW, we, start, count, part, SM::cap(), stg, sxb, hs, flag, wsum);
+    singular_targets<T, GRAD>(tid, staged, n, n_sr, h, E0x, E0y, E0z, HW, ntarget, epre, hs, rtab, we, stg, sxb,
+                              start, count, part, phi_s, E_s, psi, gpsi);
   }
 }
 

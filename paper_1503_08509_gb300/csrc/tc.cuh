@@ -82,16 +82,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t v[16]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// three-piece bf16 split of two consecutive values, packed in pairs
+// three-piece bf16 split of two consecutive values, packed in pairs (low half
+// the first value): each piece the round-to-nearest bf16 of what the previous
+// ones leave, two values per conversion; a bf16 widens to FP32 exactly by a
+// 16-bit shift
 __device__ __forceinline__ void bf16_split2(float xa, float xb, uint32_t& p0, uint32_t& p1, uint32_t& p2) {
-  const __nv_bfloat16 a0 = __float2bfloat16_rn(xa), b0 = __float2bfloat16_rn(xb);
-  const float ra = xa - __bfloat162float(a0), rb = xb - __bfloat162float(b0);
-  const __nv_bfloat16 a1 = __float2bfloat16_rn(ra), b1 = __float2bfloat16_rn(rb);
-  const __nv_bfloat16 a2 = __float2bfloat16_rn(ra - __bfloat162float(a1)),
-                      b2 = __float2bfloat16_rn(rb - __bfloat162float(b1));
-  p0 = (uint32_t)__bfloat16_as_ushort(a0) | ((uint32_t)__bfloat16_as_ushort(b0) << 16);
-  p1 = (uint32_t)__bfloat16_as_ushort(a1) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
-  p2 = (uint32_t)__bfloat16_as_ushort(a2) | ((uint32_t)__bfloat16_as_ushort(b2) << 16);
+  auto pack = [](float lo, float hi) -> uint32_t {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+  };
+  auto lo_f = [](uint32_t w) { return __uint_as_float(w << 16); };
+  auto hi_f = [](uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); };
+  p0 = pack(xa, xb);
+  const float ra = xa - lo_f(p0), rb = xb - hi_f(p0);
+  p1 = pack(ra, rb);
+  p2 = pack(ra - lo_f(p1), rb - hi_f(p1));
 }
 
 // host: three bf16 pieces (round to nearest even) of a finite double
