@@ -283,6 +283,17 @@ int compute_orderq(fep3m_ctx* c, double* phi, double* U) {
   return st;
 }
 
+// The short-range kernels' stream, at the device's highest priority: the
+// screen contraction and singular sums run concurrently with the mesh solve's
+// chain of short kernels, and the block scheduler then places their CTAs
+// first (the solve's kernels fill the SMs around them).
+cudaError_t create_pair_stream(cudaStream_t* s) {
+  int least = 0, greatest = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (e != cudaSuccess) return e;
+  return cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, greatest);
+}
+
 // the Dirichlet box: potentials and energy
 int compute_box(fep3m_ctx* c, double* phi, double* U) {
   const int64_t N = c->N;
@@ -501,7 +512,7 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
   cudaMemset(c->iflags, 0, 16 * sizeof(int));
   if ((e = cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&c->sweep_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-      (e = cudaStreamCreateWithFlags(&c->pair_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = create_pair_stream(&c->pair_stream)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_pfork, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_pjoin, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_pcount, cudaEventDisableTiming)) != cudaSuccess ||

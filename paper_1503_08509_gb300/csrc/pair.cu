@@ -33,7 +33,7 @@ namespace fep3m {
 namespace {
 
 using namespace tc;
-constexpr uint32_t UMMA_IDESC = umma_idesc(64);   // the screen contraction: N = 64 nodes
+constexpr uint32_t UMMA_IDESC = umma_idesc(64, 64);   // the screen contraction: M = 64 elements, N = 64 nodes
 
 constexpr int PT = 256;
 constexpr int PTC = 512;   // threads of the tensor-core screen kernel
@@ -657,21 +657,19 @@ __global__ void __launch_bounds__(TC ? PTC : PT, TC ? 2 : 1) k_pair_screen(int n
   // (2) screen field and (3) singular sums
   if constexpr (TC) {
     // Tensor cores: two groups of eight warps run side by side.  Group A
-    // (warps with warp mod 4 < 2, the ones that can read TMEM lanes 0 .. 63)
-    // computes the screen field: for each chunk of 64 offsets, the three
-    // bf16 pieces of A (64 brick elements x 64 offsets, built from R) and of H
-    // (64 nodes x 64 offsets, precomputed) in shared memory; one thread
-    // issues the six piece products per K step of 16 into two TMEM
-    // accumulators (hi: the product of the leading pieces, lo: the other
-    // five).  The hi accumulator holds one chunk at a time and is added into
-    // registers after each chunk, so that no accumulation inside the tensor
-    // core spans more than 64 terms of the leading product; the chunk sums are
-    // added with compensation.  In the FP32 path the table is relative to each
-    // element's corners (see pair_relative_table), so these sums carry no
-    // large smooth part.  M = 128: rows 64 .. 127 of each A operand read the
-    // next tile and their results are unused.  Group B stages the halo
-    // charges in a region of their own and computes the singular sums
-    // meanwhile.
+    // (warps 0 .. 7: two of each TMEM lane quarter) computes the screen field:
+    // for each chunk of 64 offsets, the three bf16 pieces of A (64 brick
+    // elements x 64 offsets, built from R) and of H (64 nodes x 64 offsets,
+    // precomputed) in shared memory; one thread issues the six piece products
+    // per K step of 16 (M = 64, N = 64) into two TMEM accumulators (hi: the
+    // product of the leading pieces, lo: the other five).  The hi accumulator
+    // holds one chunk at a time and is added into registers after each chunk,
+    // so that no accumulation inside the tensor core spans more than 64 terms
+    // of the leading product; the chunk sums are added with compensation.  In
+    // the FP32 path the table is relative to each element's corners (see
+    // pair_relative_table), so these sums carry no large smooth part.  Group
+    // B (warps 8 .. 15) stages the halo charges in a region of their own and
+    // computes the singular sums meanwhile.
     const uint32_t tl = smem_u32(tiles);
     if (tid < 32) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tslot)));
@@ -683,9 +681,9 @@ __global__ void __launch_bounds__(TC ? PTC : PT, TC ? 2 : 1) k_pair_screen(int n
     tc_fence_after();
     const uint32_t tmem = *tslot;
     const int warp = tid >> 5;
-    const int gt = ((warp >> 2) * 2 + (warp & 1)) * 32 + (tid & 31);   // the thread's index in its group
     bool failed = false;
-    if ((warp & 3) < 2) {
+    if (tid < SG) {
+      const int gt = tid;
       // The field at node 0 (the one absolute column of the relative table,
       // the element's potential level) is summed on the CUDA cores from the A
       // values each thread splits anyway, with the table's hi + lo floats (H0)
@@ -698,9 +696,12 @@ __global__ void __launch_bounds__(TC ? PTC : PT, TC ? 2 : 1) k_pair_screen(int n
       const int lam = (l % BX) + SW * (((l / BX) % BY) + SW * (l / (BX * BY)));
       const uint32_t aoff[2] = {sw128_off(l, 8 * g), sw128_off(l, 8 * (g + 4))};
       const int nch = (no3 + 63) / 64;
-      const int q4 = warp & 3, cg = warp >> 2;   // TMEM lanes 32 q4 .., columns 16 cg ..
-      const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 16 * cg;
-      float hsum[16], hcmp[16];   // rows 32 q4 + lane, columns 16 cg ..: compensated chunk sums
+      // this thread's accumulator entries (tmem_ld16x64b): register jj holds element row
+      // 16 qq + (lane / 4) + 8 (lane mod 2), node column 32 hh + 2 jj + (lane / 2) mod 2
+      const int qq = warp & 3, hh = warp >> 2, lane = tid & 31;
+      const int arow = 16 * qq + (lane >> 2) + 8 * (lane & 1), acol = 32 * hh + ((lane >> 1) & 1);
+      const uint32_t ta = tmem + ((uint32_t)(32 * qq) << 16) + 32 * hh;
+      float hsum[16], hcmp[16];   // compensated chunk sums of the hi accumulator
 #pragma unroll
       for (int jj = 0; jj < 16; ++jj) hsum[jj] = hcmp[jj] = 0.f;
       for (int c = 0; c < nch; ++c) {
@@ -751,7 +752,7 @@ __global__ void __launch_bounds__(TC ? PTC : PT, TC ? 2 : 1) k_pair_screen(int n
         }
         tc_fence_after();
         uint32_t vh[16];
-        tmem_ld16(ta, vh);
+        tmem_ld16x64b(ta, vh);
         tmem_wait_ld();
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
@@ -773,30 +774,24 @@ __global__ void __launch_bounds__(TC ? PTC : PT, TC ? 2 : 1) k_pair_screen(int n
       tc_fence_after();
       if (!failed) {
         uint32_t vl[16];
-        tmem_ld16(ta + 64, vl);
+        tmem_ld16x64b(ta + 64, vl);
         tmem_wait_ld();
-        const int row = 32 * q4 + (tid & 31);
-        float* drow = (float*)Gscr + (int64_t)blockIdx.x * (BE * 64) + row * 64 + 16 * cg;
-        float c0 = (hsum[0] - hcmp[0]) + __uint_as_float(vl[0]);
-        if (cg == 0) {   // column 0 from the CUDA-core sums
+        float* drow = (float*)Gscr + (int64_t)blockIdx.x * (BE * 64) + arow * 64 + acol;
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) drow[2 * jj] = (hsum[jj] - hcmp[jj]) + __uint_as_float(vl[jj]);
+        if (acol == 0) {   // column 0 from the CUDA-core sums
           double sum = 0.0;
 #pragma unroll
-          for (int qq = 0; qq < SG / 64; ++qq) {
-            const float2 v = s0p[qq * BE + row];
+          for (int q = 0; q < SG / 64; ++q) {
+            const float2 v = s0p[q * BE + arow];
             sum += (double)v.x + (double)v.y;
           }
-          c0 = (float)sum;
+          drow[0] = (float)sum;
         }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          reinterpret_cast<float4*>(drow)[i] =
-              make_float4(i == 0 ? c0 : (hsum[4 * i] - hcmp[4 * i]) + __uint_as_float(vl[4 * i]),
-                          (hsum[4 * i + 1] - hcmp[4 * i + 1]) + __uint_as_float(vl[4 * i + 1]),
-                          (hsum[4 * i + 2] - hcmp[4 * i + 2]) + __uint_as_float(vl[4 * i + 2]),
-                          (hsum[4 * i + 3] - hcmp[4 * i + 3]) + __uint_as_float(vl[4 * i + 3]));
       }
       tc_fence_before();
     } else {
+      const int gt = tid - SG;
       const bool staged = stage_halo<T>(gt, 2, n, HW, we, start, count, part, SM::cap(), stg, sxb, hs, flag, wsum);
       singular_targets<T, GRAD>(gt, staged, n, n_sr, h, E0x, E0y, E0z, HW, ntarget, epre, hs, rtab, we, stg, sxb,
                                 start, count, part, phi_s, E_s, psi, gpsi);

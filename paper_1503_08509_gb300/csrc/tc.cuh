@@ -25,9 +25,12 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
-// instruction descriptor: bf16 A and B (K-major), f32 accumulator, M = 128, N = n (multiple of 16, <= 256)
-__host__ __device__ constexpr uint32_t umma_idesc(uint32_t n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor: bf16 A and B (K-major), f32 accumulator, M = m (128, or 64), N = n (a
+// multiple of 16 for M = 128, of 8 for M = 64; <= 256).  Accumulator layout in TMEM: M = 128, row r
+// in lane r; M = 64 (cta_group::1), row r in lane 32 (r / 16) + r mod 16 (the first 16 lanes of each
+// warp's lane quarter).
+__host__ __device__ constexpr uint32_t umma_idesc(uint32_t n, uint32_t m = 128) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
@@ -76,6 +79,15 @@ __device__ __forceinline__ void sts128(uint32_t addr, const uint32_t v[4]) {
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t v[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+// 16 lanes x 32 columns (16 x 64-bit, 16 repetitions): thread t of the warp receives, in register j,
+// lane (t / 4) + 8 (t mod 2) of the 16 and column 2 j + (t / 2) mod 2
+__device__ __forceinline__ void tmem_ld16x64b(uint32_t taddr, uint32_t v[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x64b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
         "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
