@@ -35,8 +35,8 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_pair_screen launch and of one transform pass of the
 # mesh solve (k_tc_rows) on this workload, from the ncu captures summarised in profiles/ (None until one is
 # taken of the current kernel)
-PAIR_DRAM_BYTES = None
-PASS_DRAM_BYTES = None
+PAIR_DRAM_BYTES = 2264320 + 1536
+PASS_DRAM_BYTES = 3650000 + 0
 
 
 def parse():
@@ -52,6 +52,10 @@ def parse():
     p.add_argument("--legs", default="all", choices=["all", "main"],
                    help="main: only the timed loop of --precision (no FP64 leg, end-to-end leg or accuracy); "
                         "for profiling")
+    p.add_argument("--workload", default=WORKLOAD,
+                   help="with --legs main: the workload of the timed loop (nacl32, uniform262k, water1m, ...)")
+    p.add_argument("--profile-step", action="store_true",
+                   help="bracket the last timed step with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     return p.parse_args()
 
 
@@ -150,9 +154,10 @@ def fp32_peak_tflops(n_sm, mhz):
     return n_sm * 128 * 2 * mhz * 1e6 / 1e12
 
 
-def time_engine(eng, pos, Q, out, steps, warmup, flush, torch, host=False):
+def time_engine(eng, pos, Q, out, steps, warmup, flush, torch, host=False, profile_last=False):
     """Run warmup + timed steps; returns (ms per step, (screen-kernel ms, inner-solve ms) per step, launches per
-    step, the last result).  With timing enabled on eng, the stage times of each step are kept in eng.step_stats."""
+    step, the last result).  With timing enabled on eng, the stage times of each step are kept in eng.step_stats.
+    profile_last: the last step between cudaProfilerStart and cudaProfilerStop."""
     stream = eng.stream
     for _ in range(warmup):
         eng.set_particles(pos, Q)
@@ -160,15 +165,19 @@ def time_engine(eng, pos, Q, out, steps, warmup, flush, torch, host=False):
     torch.cuda.synchronize()
     l0 = eng.stats()["kernel_launches"]
     ms, pair = [], []
-    for _ in range(steps):
+    for k in range(steps):
         flush.add_(1.0)
         torch.cuda.synchronize()
+        if profile_last and k == steps - 1:
+            torch.cuda.profiler.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         eng.set_particles(pos, Q)
         r = eng.compute(phi=True, energy=True, forces=True, out=out)
         e1.record(stream)
         e1.synchronize()
+        if profile_last and k == steps - 1:
+            torch.cuda.profiler.stop()
         ms.append(e0.elapsed_time(e1))
         st = eng.stats()
         pair.append((st["ms_pair_screen"], st["ms_inner_solve"]))
@@ -284,7 +293,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     from paper_1503_08509_gb300 import api, build, workloads
     build.build()
-    d = workloads.workload(WORKLOAD)
+    d = workloads.workload(args.workload if args.legs == "main" else WORKLOAD)
     N = len(d["Q"])
     pos = torch.tensor(d["pos"], device=dev)
     Q = torch.tensor(d["Q"], device=dev)
@@ -306,7 +315,8 @@ def run_ours(args):
         clocks = Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else dev.index)
         if main:
             clocks.start()
-        ms, pair, launches, r = time_engine(eng, pos, Q, out, steps, args.warmup, flush, torch)
+        ms, pair, launches, r = time_engine(eng, pos, Q, out, steps, args.warmup, flush, torch,
+                                            profile_last=main and args.profile_step)
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
@@ -322,6 +332,7 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": round(value, 1), "unit": "particles/s", "n_gpus": ws,
                               "steps": args.steps, "warmup": args.warmup, "legs": "main",
+                              "workload": args.workload,
                               "ms_per_step": round(main["total"] / main["steps"], 4)}))
         if ws > 1:
             torch.distributed.destroy_process_group()
