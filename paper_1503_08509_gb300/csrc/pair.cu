@@ -1269,89 +1269,101 @@ __device__ __forceinline__ double acc_value(double a) { return a; }
 //   A[s][k] = sum over the offsets o with o + k inside the block of D(o, s + k + o).
 // For the vertex v = s + k the terms are D(o, v + o) over the offsets that
 // corner k's block holds: along each axis, o_a = -(n_sr + 1) only for k_a = 1,
-// o_a = n_sr only for k_a = 0, the others for both.  One thread per vertex
-// reads D(o, v + o) once for each offset of a chunk of whole offset planes
-// (oz in [z0, z1); consecutive threads read consecutive elements) and sums the
-// terms into 27 classes (the three cases per axis); A(v - k, k) is the sum of
-// the eight classes that corner k admits.  Each (s, k) is written by one
-// thread, in a fixed order: deterministic.  FP32 path (H0 set): D holds the
-// contraction with the node-0-relative table, and each term gains
-// H(o, 0) Wsum(v + o) (pair_adjoint_table); terms and sums in double-float
-// arithmetic.  FP64 path: D is the whole contraction, summed in FP64.
+// o_a = n_sr only for k_a = 0, the others for both.  The terms of a vertex are
+// summed into 27 classes (the three cases per axis); A(v - k, k) is the sum of
+// the eight classes that corner k admits.  A CTA of eight warps takes 32
+// consecutive vertices (one per lane: consecutive lanes read consecutive
+// elements of D) and a chunk of whole offset planes (oz in [z0, z1)); the
+// chunk's rows of offsets (oz, oy) are dealt to the warps in turn, each warp
+// sums its rows' terms into its own 27 classes, and the warps' classes are
+// combined in shared memory in warp order, one thread per (vertex, corner):
+// deterministic.  FP32 path (H0 set): D holds the contraction with the
+// node-0-relative table, and each term gains H(o, 0) Wsum(v + o)
+// (pair_adjoint_table); terms and sums in double-float arithmetic.  FP64
+// path: D is the whole contraction, summed in FP64.
+constexpr int AV_WARPS = 8;
 template <class T, int NSR>
-__global__ void __launch_bounds__(128) k_adj_vertex(int n, int z0, int z1, int first, const int* __restrict__ count,
-                                                   const T* __restrict__ D, const float2* __restrict__ H0,
-                                                   const float2* __restrict__ wsum, double* __restrict__ A) {
+__global__ void __launch_bounds__(32 * AV_WARPS) k_adj_vertex(int n, int z0, int z1, int first,
+                                                              const int* __restrict__ count, const T* __restrict__ D,
+                                                              const float2* __restrict__ H0,
+                                                              const float2* __restrict__ wsum, double* __restrict__ A) {
   constexpr int KEEP = NSR + 1, NOFF = 2 * NSR + 2, PLANE = NOFF * NOFF;
   constexpr bool DF = sizeof(T) == 4;
   typedef typename std::conditional<DF, dfacc, double>::type Acc;
+  extern __shared__ __align__(16) unsigned char av_smem[];
+  Acc(*part)[27][32] = reinterpret_cast<Acc(*)[27][32]>(av_smem);   // [AV_WARPS][27][32]: each warp's classes
+  __shared__ int live[32];
   const int64_t ne = (int64_t)n * n * n;
-  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (v >= ne) return;
-  const int vx = (int)(v % n), vy = (int)((v / n) % n), vz = (int)(v / ((int64_t)n * n));
-  bool any = false;   // the eight elements v - k; A is read only for non-empty ones
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t v = blockIdx.x * (int64_t)32 + lane;
+  const bool in = v < ne;
+  const int vx = in ? (int)(v % n) : 0, vy = in ? (int)((v / n) % n) : 0, vz = in ? (int)(v / ((int64_t)n * n)) : 0;
+  if (warp == 0) {
+    bool any = false;   // the eight elements v - k; A is read only for non-empty ones
+    if (in)
 #pragma unroll
-  for (int k = 0; k < 8; ++k)
-    any |= count[wrapn(vx - (k & 1), n) + (int64_t)n * (wrapn(vy - ((k >> 1) & 1), n) +
-                                                        (int64_t)n * wrapn(vz - (k >> 2), n))] != 0;
-  if (!any) return;
-  int wx[NOFF], wy[NOFF];
-#pragma unroll
-  for (int i = 0; i < NOFF; ++i) {
-    wx[i] = wrapn(vx + i - KEEP, n);
-    wy[i] = n * wrapn(vy + i - KEEP, n);
+      for (int k = 0; k < 8; ++k)
+        any |= count[wrapn(vx - (k & 1), n) + (int64_t)n * (wrapn(vy - ((k >> 1) & 1), n) +
+                                                            (int64_t)n * wrapn(vz - (k >> 2), n))] != 0;
+    live[lane] = any;
   }
-  Acc cls[27] = {};
-  for (int oz = z0; oz < z1; ++oz) {
-    const int64_t zrow = (int64_t)n * n * wrapn(vz + oz - KEEP, n);
-    const T* Dp = D + (int64_t)(oz - z0) * PLANE * ne;
-    Acc P[9] = {};
+  __syncthreads();
+  const bool act = live[lane] != 0;
 #pragma unroll
-    for (int oy = 0; oy < NOFF; ++oy) {
-      const int cy = oy == 0 ? 0 : (oy == NOFF - 1 ? 2 : 1);
+  for (int c = 0; c < 27; ++c) part[warp][c][lane] = Acc{};
+  if (__any_sync(0xffffffffu, act)) {
+    int wx[NOFF];
+#pragma unroll
+    for (int i = 0; i < NOFF; ++i) wx[i] = wrapn(vx + i - KEEP, n);
+    const int rows = (z1 - z0) * NOFF;
+    for (int rho = warp; rho < rows; rho += AV_WARPS) {
+      const int oz = z0 + rho / NOFF, oy = rho % NOFF;
+      const int cz = oz == 0 ? 0 : (oz == NOFF - 1 ? 2 : 1), cy = oy == 0 ? 0 : (oy == NOFF - 1 ? 2 : 1);
+      const int64_t erow = (int64_t)n * (wrapn(vy + oy - KEEP, n) + (int64_t)n * wrapn(vz + oz - KEEP, n));
+      const T* Dp = D + ((int64_t)(oz - z0) * PLANE + oy * NOFF) * ne;
+      Acc P[3] = {};
 #pragma unroll
       for (int ox = 0; ox < NOFF; ++ox) {
         const int cx = ox == 0 ? 0 : (ox == NOFF - 1 ? 2 : 1);
-        const int64_t e = zrow + wy[oy] + wx[ox];
-        const T d = Dp[(int64_t)(oy * NOFF + ox) * ne + e];
+        if (!act) continue;
+        const int64_t e = erow + wx[ox];
+        const T d = Dp[(int64_t)ox * ne + e];
         if constexpr (DF) {
           const float2 h = H0[oz * PLANE + oy * NOFF + ox], w = wsum[e];
           const float p = h.x * w.x;
           float r = fmaf(h.x, w.x, -p);
           r = fmaf(h.x, w.y, r);
           r = fmaf(h.y, w.x, r);
-          acc_add(P[cy * 3 + cx], p);
-          acc_add(P[cy * 3 + cx], d + r);
+          acc_add(P[cx], p);
+          acc_add(P[cx], d + r);
         } else {
-          P[cy * 3 + cx] += d;
+          P[cx] += d;
         }
       }
-    }
-    if (oz == 0) {
+      Acc* row = &part[warp][cz * 9 + cy * 3][lane];
 #pragma unroll
-      for (int j = 0; j < 9; ++j) acc_merge(cls[j], P[j]);
-    } else if (oz == NOFF - 1) {
-#pragma unroll
-      for (int j = 0; j < 9; ++j) acc_merge(cls[18 + j], P[j]);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 9; ++j) acc_merge(cls[9 + j], P[j]);
+      for (int c = 0; c < 3; ++c) acc_merge(row[32 * c], P[c]);
     }
   }
+  __syncthreads();
+  // one thread per (vertex, corner): the admitted classes, warps in order
+  const int vl = threadIdx.x & 31, k = threadIdx.x >> 5;   // 256 threads = 32 vertices x 8 corners
+  const int64_t vv = blockIdx.x * (int64_t)32 + vl;
+  if (vv >= ne || !live[vl]) return;
+  const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
+  Acc s = {};
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
-    Acc s = {};
+  for (int cz = kz ? 0 : 1; cz <= (kz ? 1 : 2); ++cz)
 #pragma unroll
-    for (int cz = kz ? 0 : 1; cz <= (kz ? 1 : 2); ++cz)
+    for (int cy = ky ? 0 : 1; cy <= (ky ? 1 : 2); ++cy)
 #pragma unroll
-      for (int cy = ky ? 0 : 1; cy <= (ky ? 1 : 2); ++cy)
+      for (int cx = kx ? 0 : 1; cx <= (kx ? 1 : 2); ++cx)
 #pragma unroll
-        for (int cx = kx ? 0 : 1; cx <= (kx ? 1 : 2); ++cx) acc_merge(s, cls[cz * 9 + cy * 3 + cx]);
-    const int64_t se = wrapn(vx - kx, n) + (int64_t)n * (wrapn(vy - ky, n) + (int64_t)n * wrapn(vz - kz, n));
-    double* dst = A + se * 8 + k;
-    *dst = first ? acc_value(s) : *dst + acc_value(s);
-  }
+        for (int w = 0; w < AV_WARPS; ++w) acc_merge(s, part[w][cz * 9 + cy * 3 + cx][vl]);
+  const int ux = (int)(vv % n), uy = (int)((vv / n) % n), uz = (int)(vv / ((int64_t)n * n));
+  const int64_t se = wrapn(ux - kx, n) + (int64_t)n * (wrapn(uy - ky, n) + (int64_t)n * wrapn(uz - kz, n));
+  double* dst = A + se * 8 + k;
+  *dst = first ? acc_value(s) : *dst + acc_value(s);
 }
 
 template <class T>
@@ -1714,7 +1726,9 @@ template <class T, int NSR>
 static void launch_adj_vertex(fep3m_ctx* c, int z0, int z1, const T* D, double* A, cudaStream_t s) {
   const int64_t ne = (int64_t)c->n * c->n * c->n;
   const bool df = sizeof(T) == 4;
-  FEP3M_CL k_adj_vertex<T, NSR><<<(unsigned)((ne + 127) / 128), 128, 0, s>>>(
+  const size_t smem = (size_t)AV_WARPS * 27 * 32 * 8;   // dfacc and double: 8 bytes
+  cudaFuncSetAttribute(k_adj_vertex<T, NSR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  FEP3M_CL k_adj_vertex<T, NSR><<<(unsigned)((ne + 31) / 32), 32 * AV_WARPS, smem, s>>>(
       c->n, z0, z1, z0 == 0, c->count, D, df ? (const float2*)c->H0df : nullptr, df ? (const float2*)c->Wsum : nullptr,
       A);
 }
