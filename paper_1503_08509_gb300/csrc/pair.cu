@@ -317,33 +317,47 @@ __device__ __forceinline__ int group_scan_excl(int gt, int id, int v, int* wsum 
 constexpr int SG = 256;   // threads of the short-range sums (the whole CTA on the CUDA cores, half of it
                           // beside the tensor-core contraction)
 
-// Stage the charges of the brick's short-range halo (HW^3 elements) in shared
-// memory in element order, with each charge's halo x index, if they fit (cap);
-// hs[i] = the first staged slot of halo element i, hs[HW^3] = the total.  By
-// SG threads (gt, barrier id).  Returns whether the charges were staged.
+// How the halo's charges reach the singular sums: all staged in shared memory
+// at once; staged tile by tile (consecutive runs of halo elements whose charges
+// fit); or, when a single element holds more charges than fit, read from
+// global memory.
+enum HaloMode { HALO_STAGED = 0, HALO_TILED = 1, HALO_GLOBAL = 2 };
+
+// the halo element id of halo index i (HW^3 elements, x fastest)
+__device__ __forceinline__ int halo_gid(int i, int n, int HW, const int* __restrict__ we) {
+  const int hx = i % HW, hy = (i / HW) % HW, hz = i / (HW * HW);
+  return we[hx] + n * (we[HW + hy] + n * we[2 * HW + hz]);
+}
+
+// Prefix of the charges of the brick's short-range halo (HW^3 elements):
+// hs[i] = the first slot of halo element i in halo order, hs[HW^3] = the total;
+// the charges are staged in shared memory in that order (with each charge's
+// halo x index) when they all fit (cap).  By SG threads (gt, barrier id).
+// Returns the HaloMode.
 template <class T>
-__device__ bool stage_halo(int gt, int id, int n, int HW, const int* __restrict__ we, const int* __restrict__ start,
-                           const int* __restrict__ count, const typename vec4<T>::type* __restrict__ part, int cap,
-                           typename vec4<T>::type* stg, unsigned char* sxb, int* hs, int* flag, int* wsum) {
+__device__ int stage_halo(int gt, int id, int n, int HW, const int* __restrict__ we, const int* __restrict__ start,
+                          const int* __restrict__ count, const typename vec4<T>::type* __restrict__ part, int cap,
+                          typename vec4<T>::type* stg, unsigned char* sxb, int* hs, int* flag, int* wsum) {
   const int nh = HW * HW * HW;
   const int per = (nh + SG - 1) / SG, i0 = gt * per;
   int cnt[8], gid[8];   // per <= 7 for n_sr <= 4 (nh <= 1728)
-  int sum = 0;
+  int sum = 0, big = 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int i = i0 + k;
     cnt[k] = 0;
     gid[k] = 0;
     if (k < per && i < nh) {
-      const int hx = i % HW, hy = (i / HW) % HW, hz = i / (HW * HW);
-      gid[k] = we[hx] + n * (we[HW + hy] + n * we[2 * HW + hz]);
+      gid[k] = halo_gid(i, n, HW, we);
       cnt[k] = count[gid[k]];
     }
     sum += cnt[k];
+    big |= cnt[k] > cap;
   }
   int total;
   int run = group_scan_excl<SG>(gt, id, sum, wsum, &total);
   const bool fits = total <= cap;
+  const bool single = group_sync_or(id, SG, big != 0);   // an element over the cap: no tiling
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int i = i0 + k;
@@ -362,10 +376,10 @@ __device__ bool stage_halo(int gt, int id, int n, int HW, const int* __restrict_
   }
   if (gt == 0) {
     hs[nh] = total;
-    flag[0] = fits;
+    flag[0] = fits ? HALO_STAGED : (single ? HALO_GLOBAL : HALO_TILED);
   }
   group_sync(id, SG);
-  return flag[0] != 0;
+  return flag[0];
 }
 
 // Singular sums of every target charge in the brick, by SG threads (gt), four
@@ -373,144 +387,195 @@ __device__ bool stage_halo(int gt, int id, int n, int HW, const int* __restrict_
 // row (dy, dz) is 2 n_sr + 1 consecutive halo elements, so its staged charges
 // are one run), two charges per step, each row's terms summed in order in
 // FP32 and the row sums added with compensation; a shuffle tree combines the
-// four.  Unstaged (dense halo): the same rows from global memory, element by
+// four.  Staged tile by tile (a dense halo): the tiles are consecutive runs of
+// halo elements whose charges fit; each target takes the part of each row
+// inside the tile, and its tile sums are added in FP64 in tile order (into
+// phi_s / E_s, element units, scaled at the last tile).  Global (an element
+// over the staging area): the same rows read from global memory, element by
 // element.  Writes phi_s and E_s (and half of them to psi, gpsi).
 template <class T, bool GRAD>
-__device__ void singular_targets(int gt, bool staged, int n, int n_sr, T h, int E0x, int E0y, int E0z, int HW,
+__device__ void singular_targets(int gt, int id, int mode, int n, int n_sr, T h, int E0x, int E0y, int E0z, int HW,
                                  int ntarget, const int* __restrict__ epre, const int* __restrict__ hs,
                                  const int* __restrict__ rtab, const int* __restrict__ we,
-                                 const typename vec4<T>::type* stg, const unsigned char* sxb,
+                                 typename vec4<T>::type* stg, unsigned char* sxb, int cap,
                                  const int* __restrict__ start, const int* __restrict__ count,
                                  const typename vec4<T>::type* __restrict__ part, double* __restrict__ phi_s,
                                  double* __restrict__ E_s, double* __restrict__ psi, double* __restrict__ gpsi) {
   typedef typename vec4<T>::type V4;
   constexpr int TPT = 4;
-  const int nb = 2 * n_sr + 1, nrow = nb * nb;
+  const int nb = 2 * n_sr + 1, nrow = nb * nb, nh = HW * HW * HW;
   const int q = gt & (TPT - 1);
-  for (int tb = 0; tb < ntarget; tb += SG / TPT) {
-    const int k = tb + gt / TPT;
-    const bool valid = k < ntarget;
-    T v4[4] = {T(0), T(0), T(0), T(0)};
-    int slot = 0;
-    if (valid) {
-      int lo = 0, hi2 = BE;                 // element of target k: epre[l] <= k < epre[l + 1]
-      while (hi2 - lo > 1) {
-        const int mid = (lo + hi2) >> 1;
-        if (epre[mid] <= k) lo = mid;
-        else hi2 = mid;
+  const double ih = 1.0 / (double)h;   // the sums are in element units
+  int ta = 0, tz = nh;                 // the tile: halo elements [ta, tz)
+  for (int tile = 0;; ++tile) {
+    int c0 = 0;                        // the tile's first charge slot
+    if (mode == HALO_TILED) {
+      // the longest run of elements from ta whose charges fit (every element does)
+      int lo = ta + 1, hi = nh;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (hs[mid] - hs[ta] <= cap) lo = mid;
+        else hi = mid - 1;
       }
-      const int l = lo;
-      const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
-      const int ex = E0x + lx, ey = E0y + ly, ez = E0z + lz;
-      const int kk = k - epre[l];
-      slot = start[ex + (int64_t)n * (ey + (int64_t)n * ez)] + kk;
-      const int base = lx + HW * (ly + HW * lz);          // halo index of block offset (-n_sr, -n_sr, -n_sr)
-      const int cx = lx + n_sr;                           // the target's halo x index
-      Acc<T> ps, fx, fy, fz;
-      if (staged) {
-        const int self = hs[base + n_sr * (1 + HW + HW * HW)] + kk;
-        const V4 pt = stg[self];
-        const T cxf = T(cx);
-        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0), ddy = T(0), ddz = T(0);
-        int r = q, j = 0, je = 0;
-        for (;;) {
-          if (j >= je) {
+      tz = lo;
+      c0 = hs[ta];
+      for (int i = ta + gt; i < tz; i += SG) {
+        const int j0 = start[halo_gid(i, n, HW, we)], k0 = hs[i] - c0, cnt = hs[i + 1] - hs[i];
+        const unsigned char hx = (unsigned char)(i % HW);
+        for (int k = 0; k < cnt; ++k) {
+          stg[k0 + k] = part[j0 + k];
+          sxb[k0 + k] = hx;
+        }
+      }
+      group_sync(id, SG);
+    }
+    const bool last = tz >= nh;
+    for (int tb = 0; tb < ntarget; tb += SG / TPT) {
+      const int k = tb + gt / TPT;
+      const bool valid = k < ntarget;
+      T v4[4] = {T(0), T(0), T(0), T(0)};
+      int slot = 0;
+      if (valid) {
+        int lo = 0, hi2 = BE;                 // element of target k: epre[l] <= k < epre[l + 1]
+        while (hi2 - lo > 1) {
+          const int mid = (lo + hi2) >> 1;
+          if (epre[mid] <= k) lo = mid;
+          else hi2 = mid;
+        }
+        const int l = lo;
+        const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
+        const int ex = E0x + lx, ey = E0y + ly, ez = E0z + lz;
+        const int kk = k - epre[l];
+        slot = start[ex + (int64_t)n * (ey + (int64_t)n * ez)] + kk;
+        const int base = lx + HW * (ly + HW * lz);          // halo index of block offset (-n_sr, -n_sr, -n_sr)
+        const int cx = lx + n_sr;                           // the target's halo x index
+        Acc<T> ps, fx, fy, fz;
+        if (mode != HALO_GLOBAL) {
+          const int selfh = base + n_sr * (1 + HW + HW * HW);   // the target's own halo element
+          const int self = hs[selfh] + kk - c0;
+          const V4 pt = mode == HALO_STAGED ? stg[self] : part[slot];
+          const T cxf = T(cx);
+          T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0), ddy = T(0), ddz = T(0);
+          int r = q, j = 0, je = 0;
+          for (;;) {
+            if (j >= je) {
+              ps.add(s0);
+              if (GRAD) {
+                fx.add(s1);
+                fy.add(s2);
+                fz.add(s3);
+              }
+              s0 = s1 = s2 = s3 = T(0);
+              if (r >= nrow) break;
+              const int rt = rtab[r];
+              const int h0 = base + (rt & 0xFFFF);
+              const int ha = h0 > ta ? h0 : ta, hb = h0 + nb < tz ? h0 + nb : tz;   // the row's part in the tile
+              j = ha < hb ? hs[ha] - c0 : 0;
+              je = ha < hb ? hs[hb] - c0 : 0;
+              ddy = T(((rt >> 16) & 0xFF) - n_sr);
+              ddz = T((rt >> 24) - n_sr);
+              r += TPT;
+              continue;
+            }
+            const bool two = j + 1 < je;
+            const int jb = two ? j + 1 : j;
+            const V4 pa = stg[j], pb = stg[jb];
+            // element units (1/h applied once per target, in FP64), fused r^2 and sums
+            const T rxa = (T(sxb[j]) - cxf) + (pa.x - pt.x), rya = ddy + (pa.y - pt.y), rza = ddz + (pa.z - pt.z);
+            const T rxb = (T(sxb[jb]) - cxf) + (pb.x - pt.x), ryb = ddy + (pb.y - pt.y), rzb = ddz + (pb.z - pt.z);
+            const T ira = j == self ? T(0) : rsq<T>(fmaw(rxa, rxa, fmaw(rya, rya, rza * rza)));
+            const T irb = (!two || jb == self) ? T(0) : rsq<T>(fmaw(rxb, rxb, fmaw(ryb, ryb, rzb * rzb)));
+            const T qa = pa.w * ira, qb = pb.w * irb;
+            s0 += qa;
+            s0 += qb;
+            if (GRAD) {
+              const T f3a = qa * (ira * ira), f3b = qb * (irb * irb);
+              s1 = fmaw(f3a, rxa, s1);
+              s2 = fmaw(f3a, rya, s2);
+              s3 = fmaw(f3a, rza, s3);
+              s1 = fmaw(f3b, rxb, s1);
+              s2 = fmaw(f3b, ryb, s2);
+              s3 = fmaw(f3b, rzb, s3);
+            }
+            j += 2;
+          }
+        } else {
+          // a row may wrap around the periodic box
+          const V4 pt = part[slot];
+          for (int r = q; r < nrow; r += TPT) {
+            const int ay = r % nb, az = r / nb;
+            const int64_t rowg = (int64_t)n * (we[HW + ly + ay] + (int64_t)n * we[2 * HW + lz + az]);
+            const T ddy = T(ay - n_sr), ddz = T(az - n_sr);
+            T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+            for (int ax = 0; ax < nb; ++ax) {
+              const int64_t g = rowg + we[lx + ax];
+              const T ddx = T(ax - n_sr);
+              const int j0 = start[g], j1 = j0 + count[g];
+              for (int j = j0; j < j1; ++j) {
+                const V4 pj = part[j];
+                const T rx = ddx + (pj.x - pt.x), ry = ddy + (pj.y - pt.y), rz = ddz + (pj.z - pt.z);
+                const T ir = j == slot ? T(0) : rsq<T>(fmaw(rx, rx, fmaw(ry, ry, rz * rz)));
+                const T qi = pj.w * ir;
+                s0 += qi;
+                if (GRAD) {
+                  const T f3 = qi * (ir * ir);
+                  s1 = fmaw(f3, rx, s1);
+                  s2 = fmaw(f3, ry, s2);
+                  s3 = fmaw(f3, rz, s3);
+                }
+              }
+            }
             ps.add(s0);
             if (GRAD) {
               fx.add(s1);
               fy.add(s2);
               fz.add(s3);
             }
-            s0 = s1 = s2 = s3 = T(0);
-            if (r >= nrow) break;
-            const int rt = rtab[r];
-            const int h0 = base + (rt & 0xFFFF);
-            j = hs[h0];
-            je = hs[h0 + nb];
-            ddy = T(((rt >> 16) & 0xFF) - n_sr);
-            ddz = T((rt >> 24) - n_sr);
-            r += TPT;
-            continue;
           }
-          const bool two = j + 1 < je;
-          const int jb = two ? j + 1 : j;
-          const V4 pa = stg[j], pb = stg[jb];
-          // element units (1/h applied once per target, in FP64), fused r^2 and sums
-          const T rxa = (T(sxb[j]) - cxf) + (pa.x - pt.x), rya = ddy + (pa.y - pt.y), rza = ddz + (pa.z - pt.z);
-          const T rxb = (T(sxb[jb]) - cxf) + (pb.x - pt.x), ryb = ddy + (pb.y - pt.y), rzb = ddz + (pb.z - pt.z);
-          const T ira = j == self ? T(0) : rsq<T>(fmaw(rxa, rxa, fmaw(rya, rya, rza * rza)));
-          const T irb = (!two || jb == self) ? T(0) : rsq<T>(fmaw(rxb, rxb, fmaw(ryb, ryb, rzb * rzb)));
-          const T qa = pa.w * ira, qb = pb.w * irb;
-          s0 += qa;
-          s0 += qb;
-          if (GRAD) {
-            const T f3a = qa * (ira * ira), f3b = qb * (irb * irb);
-            s1 = fmaw(f3a, rxa, s1);
-            s2 = fmaw(f3a, rya, s2);
-            s3 = fmaw(f3a, rza, s3);
-            s1 = fmaw(f3b, rxb, s1);
-            s2 = fmaw(f3b, ryb, s2);
-            s3 = fmaw(f3b, rzb, s3);
-          }
-          j += 2;
         }
-      } else {
-        // a row may wrap around the periodic box
-        const V4 pt = part[slot];
-        for (int r = q; r < nrow; r += TPT) {
-          const int ay = r % nb, az = r / nb;
-          const int64_t rowg = (int64_t)n * (we[HW + ly + ay] + (int64_t)n * we[2 * HW + lz + az]);
-          const T ddy = T(ay - n_sr), ddz = T(az - n_sr);
-          T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-          for (int ax = 0; ax < nb; ++ax) {
-            const int64_t g = rowg + we[lx + ax];
-            const T ddx = T(ax - n_sr);
-            const int j0 = start[g], j1 = j0 + count[g];
-            for (int j = j0; j < j1; ++j) {
-              const V4 pj = part[j];
-              const T rx = ddx + (pj.x - pt.x), ry = ddy + (pj.y - pt.y), rz = ddz + (pj.z - pt.z);
-              const T ir = j == slot ? T(0) : rsq<T>(fmaw(rx, rx, fmaw(ry, ry, rz * rz)));
-              const T qi = pj.w * ir;
-              s0 += qi;
-              if (GRAD) {
-                const T f3 = qi * (ir * ir);
-                s1 = fmaw(f3, rx, s1);
-                s2 = fmaw(f3, ry, s2);
-                s3 = fmaw(f3, rz, s3);
-              }
+        v4[0] = ps.get();
+        v4[1] = fx.get();
+        v4[2] = fy.get();
+        v4[3] = fz.get();
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int o = 1; o < TPT; o <<= 1) v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], o);
+      if (valid && q == 0) {
+        // element units; tile sums added in FP64 in tile order, scaled at the last tile
+        double sum[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) sum[a] = (double)v4[a];
+        if (tile > 0) {
+          sum[0] += phi_s[slot];
+          if (GRAD)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) sum[1 + a] += E_s[3 * slot + a];
+        }
+        if (last) {
+          const double ps0 = sum[0] * ih;
+          phi_s[slot] = ps0;
+          if (psi) psi[slot] = 0.5 * ps0;
+          if (GRAD) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              const double e = sum[1 + a] * (ih * ih);
+              E_s[3 * slot + a] = e;
+              if (gpsi) gpsi[3 * slot + a] = 0.5 * e;
             }
           }
-          ps.add(s0);
-          if (GRAD) {
-            fx.add(s1);
-            fy.add(s2);
-            fz.add(s3);
-          }
-        }
-      }
-      v4[0] = ps.get();
-      v4[1] = fx.get();
-      v4[2] = fy.get();
-      v4[3] = fz.get();
-    }
+        } else {
+          phi_s[slot] = sum[0];
+          if (GRAD)
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int o = 1; o < TPT; o <<= 1) v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], o);
-    if (valid && q == 0) {
-      const double ih = 1.0 / (double)h;   // the sums are in element units
-      const double ps0 = (double)v4[0] * ih;
-      phi_s[slot] = ps0;
-      if (psi) psi[slot] = 0.5 * ps0;
-      if (GRAD) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const double e = (double)v4[1 + a] * (ih * ih);
-          E_s[3 * slot + a] = e;
-          if (gpsi) gpsi[3 * slot + a] = 0.5 * e;
+            for (int a = 0; a < 3; ++a) E_s[3 * slot + a] = sum[1 + a];
         }
       }
     }
+    if (last) break;
+    group_sync(id, SG);   // the next tile overwrites the staging area
+    ta = tz;
   }
 }
 
@@ -524,7 +589,7 @@ __device__ void singular_targets(int gt, bool staged, int n, int n_sr, T h, int 
 // 512 threads and eight per target; otherwise CUDA cores, 256 threads and
 // four per target.
 template <class T, bool GRAD, bool TC>
-__global__ void __launch_bounds__(TC ? PTC : PT, TC ? 2 : 1) k_pair_screen(int n, int n_sr, T h, const int* __restrict__ start,
+__global__ void __launch_bounds__(TC ? PTC : PT, 2) k_pair_screen(int n, int n_sr, T h, const int* __restrict__ start,
                                                              const int* __restrict__ count,
                                                              const typename vec4<T>::type* __restrict__ part,
                                                              const T* __restrict__ Cv, const T* __restrict__ rv,
@@ -792,9 +857,9 @@ __global__ void __launch_bounds__(TC ? PTC : PT, TC ? 2 : 1) k_pair_screen(int n
       tc_fence_before();
     } else {
       const int gt = tid - SG;
-      const bool staged = stage_halo<T>(gt, 2, n, HW, we, start, count, part, SM::cap(), stg, sxb, hs, flag, wsum);
-      singular_targets<T, GRAD>(gt, staged, n, n_sr, h, E0x, E0y, E0z, HW, ntarget, epre, hs, rtab, we, stg, sxb,
-                                start, count, part, phi_s, E_s, psi, gpsi);
+      const int mode = stage_halo<T>(gt, 2, n, HW, we, start, count, part, SM::cap(), stg, sxb, hs, flag, wsum);
+      singular_targets<T, GRAD>(gt, 2, mode, n, n_sr, h, E0x, E0y, E0z, HW, ntarget, epre, hs, rtab, we, stg, sxb,
+                                SM::cap(), start, count, part, phi_s, E_s, psi, gpsi);
     }
     __syncthreads();   // every TMEM read done
     if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
@@ -889,9 +954,9 @@ __global__ void __launch_bounds__(TC ? PTC : PT, TC ? 2 : 1) k_pair_screen(int n
     }
     // Region 1 (R) was last read before the chunk loop's final barrier, so the
     // staging may overwrite it without another one.
-    const bool staged = stage_halo<T>(tid, 0, n, HW, we, start, count, part, SM::cap(), stg, sxb, hs, flag, wsum);
-    singular_targets<T, GRAD>(tid, staged, n, n_sr, h, E0x, E0y, E0z, HW, ntarget, epre, hs, rtab, we, stg, sxb,
-                              start, count, part, phi_s, E_s, psi, gpsi);
+    const int mode = stage_halo<T>(tid, 0, n, HW, we, start, count, part, SM::cap(), stg, sxb, hs, flag, wsum);
+    singular_targets<T, GRAD>(tid, 0, mode, n, n_sr, h, E0x, E0y, E0z, HW, ntarget, epre, hs, rtab, we, stg, sxb,
+                              SM::cap(), start, count, part, phi_s, E_s, psi, gpsi);
   }
 }
 
@@ -1740,7 +1805,15 @@ static cudaError_t screen_adjoint(fep3m_ctx* c, const T* W, const double* Hw, do
   const int n = c->n;
   const int64_t ne = (int64_t)n * n * n;
   const int noff = c->noff, plane = noff * noff;
-  const size_t budget = (size_t)1 << 31;   // bytes of D held at once
+  // bytes of D held at once: a quarter of the device's memory (at least 2 GiB), so that on a
+  // large GPU even the 256^3 mesh takes D in one piece (each further piece re-reads and
+  // re-writes A and launches the gather again)
+  size_t budget = (size_t)1 << 31;
+  {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) budget = std::max(budget, std::min(total_b / 4, free_b / 2));
+    else (void)cudaGetLastError();
+  }
   // tensor cores (FP32 path, table pieces prepared): column tiles of ADJ_NT offsets
   const bool tcore = sizeof(T) == 4 && c->HbA != nullptr;
   const int planes = (int)std::min<int64_t>(noff, std::max<int64_t>(1, (int64_t)(budget / ((size_t)ne * sizeof(T) * plane))));
