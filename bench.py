@@ -211,6 +211,16 @@ def large_workload(name, steps, warmup, flush, dev, torch, peaks):
     Nn = 3 * d["n_el"]
     pass_ms = stages["ms_inner_solve"] / 6
     pass_flops = 2.0 * Nn ** 4 * 6          # six split products per pass
+    # the same inner solve alone on the GPU (fep3m_solve_mesh of a random neutral load): in the step it
+    # shares the GPU with the concurrent adjoint solve and the short-range kernels
+    rhs = torch.randn(Nn ** 3, dtype=torch.float64, device=dev)
+    rhs -= rhs.mean()
+    alone = []
+    for _ in range(3):
+        eng.solve_mesh(rhs)
+        alone.append(eng.stats()["ms_inner_solve"])
+    del rhs
+    alone_ms = statistics.median(alone[1:]) / 6
     bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
     props = torch.cuda.get_device_properties(dev)
     fp32 = fp32_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
@@ -230,7 +240,12 @@ def large_workload(name, steps, warmup, flush, dev, torch, peaks):
                                   "frac": round(pass_flops / (pass_ms * 1e-3) / 1e12 / bf16, 4),
                                   "count": "2 N^4 x 6 split-bf16 products per pass, N = %d" % Nn,
                                   "ms_per_launch": round(pass_ms, 4),
-                                  "peak_note": "measured sustained bf16 (MEASURED_PEAKS.json)"},
+                                  "peak_note": "measured sustained bf16 (MEASURED_PEAKS.json)",
+                                  "alone": {"ms_per_launch": round(alone_ms, 4),
+                                            "achieved": round(pass_flops / (alone_ms * 1e-3) / 1e12, 1),
+                                            "frac": round(pass_flops / (alone_ms * 1e-3) / 1e12 / bf16, 4),
+                                            "note": "the forward solve's first inner solve by fep3m_solve_mesh, "
+                                                    "no concurrent streams; frac of the sustained peak"}},
            "roofline_pair": {"kernel": "k_pair_screen", "bound": "alu",
                              "achieved": round(flops_elem / (pair_ms * 1e-3) / 1e12, 2), "peak": round(fp32, 2),
                              "unit": "TFLOP/s", "frac": round(flops_elem / (pair_ms * 1e-3) / 1e12 / fp32, 4),

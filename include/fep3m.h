@@ -174,7 +174,9 @@ typedef struct {
   double ms_inner_solve;    /* the first FP32 inner solve of the last replayed
                                forward mesh solve (six transform passes of the
                                fast diagonalisation, or the multigrid-
-                               preconditioned CG)                                */
+                               preconditioned CG): inside fep3m_compute, where it
+                               shares the GPU with the concurrent streams; after
+                               fep3m_solve_mesh, alone                            */
 } fep3m_stats;
 
 /* Create a context: validates cfg, builds the FE basis-screen table (a
