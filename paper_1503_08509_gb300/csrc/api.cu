@@ -185,40 +185,68 @@ void solve_stats(fep3m_ctx* c) {
 }
 
 // The forward chain (assembly, mesh solve, pair kernels) on the context's
-// stream.  The screen contraction and the singular sums need no mesh solution
-// and run on the pair stream, concurrently with the solve.  With force_dev, the
+// highest-priority stream, forked from the caller's stream and joined back to
+// it.  The screen contraction and the singular sums need no mesh solution and
+// run on the pair stream, concurrently with the solve.  With force_dev, the
 // adjoint chain for forces (weights Q/2 need nothing from the forward solve)
 // runs concurrently on the auxiliary stream: deposit, adjoint mesh solve,
 // vertex adjoint, with the screen and singular adjoint sweeps on a third
-// stream; the per-charge assembly joins all chains.  Nothing here waits for the
-// device once the solvers are calibrated: the replayed solves' residuals are
-// checked by solves_missed after the caller's final synchronisation.
+// stream; the per-charge assembly joins all chains.  The critical path
+// (assembly, then the forward solve) is enqueued first.  Nothing here waits
+// for the device once the solvers are calibrated: the replayed solves'
+// residuals are checked by solves_missed after the caller's final
+// synchronisation.
 int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev) {
+  struct Restore {
+    fep3m_ctx* c;
+    cudaStream_t s;
+    ~Restore() { c->stream = s; }
+  } restore{c, c->stream};
+  const cudaStream_t caller = c->stream;
+  CK(cudaEventRecord(c->ev_ffork, caller));
+  CK(cudaStreamWaitEvent(c->fwd_stream, c->ev_ffork, 0));
+  c->stream = c->fwd_stream;
   fep3m::Solver* F = &c->solv[0];
   fep3m::Solver* A = &c->solv[1];
   F->stream = c->stream;
   CK(cudaMemsetAsync(c->iflags + 2, 0, sizeof(int), c->stream));   // bounded-wait flag of the pair kernels
-  if (force_dev) {
-    CK(cudaEventRecord(c->ev_fork, c->stream));
-    CK(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
-    CK(adjoint_pre(c, 1.0, nullptr, c->aux_stream));
-    CK(cudaEventRecord(c->ev_fork2, c->aux_stream));
-    CK(cudaStreamWaitEvent(c->sweep_stream, c->ev_fork2, 0));
-    CK(adjoint_sweeps(c, c->sweep_stream, false));   // singular part: from the screen kernel
-    CK(cudaEventRecord(c->ev_join2, c->sweep_stream));
-    CK(mesh_solve_begin(A, c->g64, c->lam64));
-  }
+  // with forces and the paired solve, the adjoint right-hand side is deposited
+  // on the auxiliary stream while this one assembles, and one chain of kernels
+  // solves both (the adjoint's right-hand side and solution sit one mesh after
+  // the forward ones)
+  const bool paired = force_dev && fep3m::mesh_solve_paired(F);
+  c->paired_last = paired;
+  if (force_dev) CK(cudaEventRecord(c->ev_fork, c->stream));
   ev_record(c, 0);
   CK(assemble_forward(c));
   ev_record(c, 1);
   CK(cudaEventRecord(c->ev_pfork, c->stream));
+  if (force_dev) {
+    CK(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
+    CK(adjoint_pre(c, 1.0, nullptr, c->aux_stream));
+    CK(cudaEventRecord(c->ev_fork2, c->aux_stream));
+  }
+  if (paired) {
+    CK(cudaStreamWaitEvent(c->stream, c->ev_fork2, 0));
+    CK(mesh_solve_begin2(F, c->b64, c->phi64));
+    CK(cudaEventRecord(c->ev_solved, c->stream));
+  } else {
+    CK(mesh_solve_begin(F, c->b64, c->phi64));
+  }
   CK(cudaStreamWaitEvent(c->pair_stream, c->ev_pfork, 0));
   ev_record(c, 8, c->pair_stream);
   CK(pair_screen(c, want_grad, c->pair_stream, force_dev != nullptr));
   ev_record(c, 9, c->pair_stream);
   CK(cudaEventRecord(c->ev_pjoin, c->pair_stream));
-  CK(mesh_solve_begin(F, c->b64, c->phi64));
-  CK(pair_prepare(c));
+  if (force_dev) {
+    CK(cudaStreamWaitEvent(c->sweep_stream, c->ev_fork2, 0));
+    CK(adjoint_sweeps(c, c->sweep_stream, false));   // singular part: from the screen kernel
+    CK(cudaEventRecord(c->ev_join2, c->sweep_stream));
+    if (paired) CK(cudaStreamWaitEvent(c->aux_stream, c->ev_solved, 0));
+    else CK(mesh_solve_begin(A, c->g64, c->lam64));
+  }
+  // the replayed paired solve wrote the pair kernels' copy of the potential itself
+  if (!(paired && F->pending2)) CK(pair_prepare(c));
   ev_record(c, 2);
   CK(cudaStreamWaitEvent(c->stream, c->ev_pjoin, 0));
   ev_record(c, 10);
@@ -234,6 +262,8 @@ int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev)
     CK(adjoint_final(c, 1.0, force_dev, nullptr, -1.0, c->stream));
     ev_record(c, 4);
   }
+  CK(cudaEventRecord(c->ev_fjoin, c->stream));
+  CK(cudaStreamWaitEvent(caller, c->ev_fjoin, 0));
   return FEP3M_OK;
 }
 
@@ -241,6 +271,7 @@ int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev)
 // replayed solves; true when one missed its tolerance (run_forward again: the
 // missed solve re-calibrates with one more refinement sweep)
 bool solves_missed(fep3m_ctx* c, bool adjoint) {
+  if (adjoint && c->paired_last) return !mesh_solve_check2(&c->solv[0]);
   bool miss = !mesh_solve_check(&c->solv[0]);
   if (adjoint && !mesh_solve_check(&c->solv[1])) miss = true;
   return miss;
@@ -251,12 +282,14 @@ int solve_status(fep3m_ctx* c, bool adjoint) {
   const fep3m::Solver* F = &c->solv[0];
   const fep3m::Solver* A = &c->solv[1];
   solve_stats(c);
+  const bool paired = adjoint && c->paired_last;
+  const double arel = paired ? F->relres2 : A->relres;
   if (adjoint) {
-    c->stats.adj_iterations = A->iters;
-    c->stats.adj_rel_residual = A->relres;
+    c->stats.adj_iterations = paired ? F->iters2 : A->iters;
+    c->stats.adj_rel_residual = arel;
   }
   const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : (c->precision == FEP3M_FP64 ? 1e-13 : 1e-10);
-  const bool ok = F->relres <= 10 * rtol && (!adjoint || A->relres <= 10 * rtol);
+  const bool ok = F->relres <= 10 * rtol && (!adjoint || arel <= 10 * rtol);
   return ok ? FEP3M_OK : FEP3M_ENOCONV;
 }
 
@@ -283,16 +316,21 @@ int compute_orderq(fep3m_ctx* c, double* phi, double* U) {
   return st;
 }
 
-// The short-range kernels' stream, at the device's highest priority: the
-// screen contraction and singular sums run concurrently with the mesh solve's
-// chain of short kernels, and the block scheduler then places their CTAs
-// first (the solve's kernels fill the SMs around them).
-cudaError_t create_pair_stream(cudaStream_t* s) {
+// A non-blocking stream `below` priority levels under the device's highest
+// (clamped to the device's range).  The forward chain (assembly, mesh solve,
+// evaluation: the step's critical path) and the auxiliary chain (the adjoint
+// deposit the paired mesh solve waits for, then the vertex adjoint) run at the
+// highest level, the short-range kernels one below, the adjoint sweeps (which
+// have the whole mesh solve to finish in) at the lowest: the block scheduler
+// then starts the critical path's CTAs first as SMs free up, and the other
+// chains fill the SMs around its short latency-bound kernels.
+cudaError_t create_stream_at(cudaStream_t* s, int below) {
   int least = 0, greatest = 0;
   cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
   if (e != cudaSuccess) return e;
-  return cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, greatest);
+  return cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, std::min(greatest + below, least));
 }
+constexpr int kPrioForward = 0, kPrioPair = 1, kPrioSweep = 1 << 20;
 
 // the Dirichlet box: potentials and energy
 int compute_box(fep3m_ctx* c, double* phi, double* U) {
@@ -343,7 +381,7 @@ void fep3m_destroy(fep3m_ctx* c) {
   if (!c) return;
   free_particles(c);
   void* p[] = {c->Hw64, c->count, c->start, c->fill, c->scan_tmp, c->C, c->rv, c->Cv, c->b64, c->phi64,
-               c->res64, c->g64, c->lam64, c->scal, c->iflags, c->phi_hl, c->W_el, c->A_el, c->mu_v, c->Gscr, c->Hb, c->HbA,
+               c->res64, c->scal, c->iflags, c->phi_hl, c->W_el, c->A_el, c->mu_v, c->Gscr, c->Hb, c->HbA,
                c->Hdf, c->red_tmp, c->red_counter, c->D_adj, c->Ha64, c->H0df, c->Wsum};
   for (void* q : p) dfree(q);
   fep3m::solver_destroy(&c->solv[0]);
@@ -354,6 +392,10 @@ void fep3m_destroy(fep3m_ctx* c) {
   if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
   if (c->sweep_stream) cudaStreamDestroy(c->sweep_stream);
   if (c->pair_stream) cudaStreamDestroy(c->pair_stream);
+  if (c->fwd_stream) cudaStreamDestroy(c->fwd_stream);
+  if (c->ev_ffork) cudaEventDestroy(c->ev_ffork);
+  if (c->ev_fjoin) cudaEventDestroy(c->ev_fjoin);
+  if (c->ev_solved) cudaEventDestroy(c->ev_solved);
   if (c->ev_pfork) cudaEventDestroy(c->ev_pfork);
   if (c->ev_pjoin) cudaEventDestroy(c->ev_pjoin);
   if (c->ev_pcount) cudaEventDestroy(c->ev_pcount);
@@ -496,23 +538,30 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
       (e = cudaMalloc(&c->scan_tmp, scan_tmp_bytes(ne))) != cudaSuccess ||
       (e = cudaMalloc(&c->C, ne * 8 * es)) != cudaSuccess || (e = cudaMalloc(&c->rv, ne * es)) != cudaSuccess ||
       (e = cudaMalloc(&c->Cv, ne * 8 * es)) != cudaSuccess ||
-      (e = dalloc(&c->b64, nodes)) != cudaSuccess || (e = dalloc(&c->phi64, nodes)) != cudaSuccess ||
-      (e = dalloc(&c->res64, nodes)) != cudaSuccess || (e = dalloc(&c->g64, nodes)) != cudaSuccess ||
-      (e = dalloc(&c->lam64, nodes)) != cudaSuccess || (e = dalloc(&c->scal, 64)) != cudaSuccess ||
+      (e = dalloc(&c->b64, 2 * nodes)) != cudaSuccess || (e = dalloc(&c->phi64, 2 * nodes)) != cudaSuccess ||
+      (e = dalloc(&c->res64, nodes)) != cudaSuccess || (e = dalloc(&c->scal, 64)) != cudaSuccess ||
       (e = dalloc(&c->iflags, 16)) != cudaSuccess || (e = cudaMalloc(&c->W_el, ne * 64 * es)) != cudaSuccess ||
       (e = cudaMalloc(&c->A_el, ne * 8 * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&c->mu_v, ne * sizeof(double))) != cudaSuccess ||
       (e = dalloc(&c->red_tmp, 1024)) != cudaSuccess || (e = dalloc(&c->red_counter, 1)) != cudaSuccess ||
       (e = cudaMalloc(&c->Gscr, pair_screen_bytes(c))) != cudaSuccess)
     return fail(from_cuda(e));
+  // the adjoint's right-hand side and solution follow the forward ones: the
+  // paired mesh solve takes both at one stride
+  c->g64 = c->b64 + nodes;
+  c->lam64 = c->phi64 + nodes;
   if (c->precision == FEP3M_MIXED && ((e = cudaMalloc(&c->phi_hl, nodes * 2 * sizeof(float))) != cudaSuccess ||
                                       (e = cudaMalloc(&c->Wsum, ne * sizeof(float2))) != cudaSuccess))
     return fail(from_cuda(e));
   cudaMemset(c->red_counter, 0, sizeof(unsigned int));
   cudaMemset(c->iflags, 0, 16 * sizeof(int));
-  if ((e = cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-      (e = cudaStreamCreateWithFlags(&c->sweep_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-      (e = create_pair_stream(&c->pair_stream)) != cudaSuccess ||
+  if ((e = create_stream_at(&c->aux_stream, kPrioForward)) != cudaSuccess ||
+      (e = create_stream_at(&c->sweep_stream, kPrioSweep)) != cudaSuccess ||
+      (e = create_stream_at(&c->pair_stream, kPrioPair)) != cudaSuccess ||
+      (e = create_stream_at(&c->fwd_stream, kPrioForward)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_ffork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_fjoin, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_solved, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_pfork, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_pjoin, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_pcount, cudaEventDisableTiming)) != cudaSuccess ||
@@ -525,7 +574,11 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
   if (box) {
     if ((st = box_create(c, cfg->n_el, (cfg->flags & FEP3M_NEUMANN) != 0)) != FEP3M_OK) return fail(st);
   } else {
-    if ((e = solver_init(&c->solv[0], c, c->stream)) != cudaSuccess) return fail(from_cuda(e));
+    // the forward solver also pairs the forward and adjoint right-hand sides (tensor-core
+    // fast diagonalisation); the second solver serves the multigrid path and fep3m_vjp
+    const bool pairable = !(cfg->flags & (FEP3M_MULTIGRID | FEP3M_CUDA_CORES));
+    if ((e = solver_init(&c->solv[0], c, c->stream, pairable ? 2 : 1)) != cudaSuccess) return fail(from_cuda(e));
+    c->solv[0].hl_out = (float2*)c->phi_hl;   // MIXED: the paired solve also writes the pair kernels' copy
     if ((e = solver_init(&c->solv[1], c, c->aux_stream)) != cudaSuccess) return fail(from_cuda(e));
     c->stats.mg_levels = (int)c->solv[0].mg.lv.size();
   }
@@ -618,8 +671,9 @@ int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
     c->stats.ms_adjoint = force ? ev_ms(c, 3, 4) : 0.0;
     float ms = 0;
     const fep3m::Solver& F = c->solv[0];
-    c->stats.ms_inner_solve =
-        (F.solve_exec && cudaEventElapsedTime(&ms, F.ev_in0, F.ev_in1) == cudaSuccess) ? (double)ms : 0.0;
+    c->stats.ms_inner_solve = ((F.solve_exec || F.solve2_exec) && cudaEventElapsedTime(&ms, F.ev_in0, F.ev_in1) == cudaSuccess)
+                                  ? (double)ms
+                                  : 0.0;
     (void)cudaGetLastError();
   }
   return st;
@@ -834,8 +888,9 @@ int fep3m_solve_mesh(fep3m_ctx* c, const double* b, double* phi) {
     // the first inner solve of the replayed solve, alone on the GPU
     float ms = 0;
     const fep3m::Solver& F = c->solv[0];
-    c->stats.ms_inner_solve =
-        (F.solve_exec && cudaEventElapsedTime(&ms, F.ev_in0, F.ev_in1) == cudaSuccess) ? (double)ms : 0.0;
+    c->stats.ms_inner_solve = ((F.solve_exec || F.solve2_exec) && cudaEventElapsedTime(&ms, F.ev_in0, F.ev_in1) == cudaSuccess)
+                                  ? (double)ms
+                                  : 0.0;
     (void)cudaGetLastError();
   }
   const double rtol = c->cfg.mg_rtol > 0 ? c->cfg.mg_rtol : (c->precision == FEP3M_FP64 ? 1e-13 : 1e-10);

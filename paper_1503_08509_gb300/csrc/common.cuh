@@ -143,6 +143,9 @@ struct Solver {
   Stencils st;
   cudaStream_t stream = nullptr;   // stream the solver's work is issued on
   Hierarchy mg;
+  int nv = 1;                      // right-hand sides the refinement buffers hold (2: the paired solve)
+  int V = 1;                       // right-hand sides of the solve being issued, at a stride of
+  int64_t vs = 0;                  //   vs nodes (0 for one); scalars and partials per vector
   void* sb[6] = {};                // CG vectors r, z, p, q, x, rhs (working precision, fine level)
   size_t sb_bytes = 0;
   double* scal = nullptr;          // device scalars (64)
@@ -165,6 +168,17 @@ struct Solver {
   double relres = 0;
   // recorded around the first inner solve of a replayed solve (events in the graph)
   cudaEvent_t ev_in0 = nullptr, ev_in1 = nullptr;
+  // the paired solve: two right-hand sides at b and b + nodes into phi and phi + nodes in one
+  // chain of kernels (tensor-core fast diagonalisation only), captured for its fixed pointers
+  int plan2_kout = 0;
+  cudaGraphExec_t solve2_exec = nullptr;
+  int solve2_graph_kernels = 0;
+  const double* plan2_b = nullptr;
+  double* plan2_phi = nullptr;
+  float2* hl_out = nullptr;        // MIXED: the paired solve also writes its first solution as hi + lo floats
+  bool pending2 = false;
+  int iters2 = 0, refine_steps2 = 0;   // the second right-hand side's counts and residual
+  double relres2 = 0;
 };
 
 // Screens of order q >= 2 on the order p = q + 2 mesh (orderq.cu).  Per-order
@@ -288,8 +302,8 @@ struct fep3m_ctx {
   double* b64 = nullptr;         // (3n)^3 load vector
   double* phi64 = nullptr;       // (3n)^3 mesh potential, reference units
   double* res64 = nullptr;       // refinement residual
-  double* g64 = nullptr;         // adjoint right-hand side
-  double* lam64 = nullptr;       // adjoint mesh solution
+  double* g64 = nullptr;         // adjoint right-hand side (b64 + nodes: one allocation)
+  double* lam64 = nullptr;       // adjoint mesh solution (phi64 + nodes)
   double* scal = nullptr;        // device scalars (dots, norms, flags), 64 doubles
   void* phi_hl = nullptr;        // MIXED: mesh potential as hi + lo floats, (3n)^3 float2
   int* iflags = nullptr;         // device int flags: [0] input error, [1] converged, ...
@@ -323,7 +337,12 @@ struct fep3m_ctx {
   cudaStream_t aux_stream = nullptr;   // adjoint chain, concurrent with the forward one
   cudaStream_t sweep_stream = nullptr; // adjoint screen and singular sweeps (need no mesh solution)
   cudaStream_t pair_stream = nullptr;  // screen contraction and singular sums (need no mesh solution)
+  cudaStream_t fwd_stream = nullptr;   // the forward chain (the step's critical path), highest priority
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
+  cudaEvent_t ev_ffork = nullptr, ev_fjoin = nullptr;   // the forward chain's fork from and join to stream
+  cudaEvent_t ev_solved = nullptr;     // the paired mesh solve has finished
+  bool paired_last = false;            // the last forward step paired its two mesh solves
+  int adj_planes = 0;                  // offset planes of the screen adjoint's product D per piece (0: unset)
   cudaEvent_t ev_pfork = nullptr, ev_pjoin = nullptr;
   cudaEvent_t ev_pcount = nullptr;          // the pair statistics' copy to host_cnt
   unsigned long long* host_cnt = nullptr;   // pinned: 5 pair statistics of the last set_particles
@@ -340,6 +359,10 @@ struct fep3m_ctx {
 
 namespace fep3m {
 // host setup (setup.cpp)
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device, calling the runtime only when the limit has to grow (the
+// call costs host time on every launch otherwise).  Safe from several threads.
+cudaError_t smem_limit(const void* kern, size_t bytes);
 void element_matrices_q3(double Me[4][4], double Ke[4][4], double Mpq[4][2]);
 void make_stencils(Stencils& st);
 void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
@@ -354,13 +377,17 @@ cudaError_t bin_particles(fep3m_ctx* c, const double* pos, const double* Q, int 
 // screen lists C and the vertex density (and its by-vertex copy Cv) of the binned charges
 cudaError_t element_lists(fep3m_ctx* c);
 cudaError_t assemble_forward(fep3m_ctx* c);
-cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream);
+// nv: right-hand sides the refinement buffers hold (2 for the paired solve, which
+// needs the tensor-core fast diagonalisation; otherwise 1)
+cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream, int nv = 1);
 // fast-diagonalisation solve of a periodic N^3 mesh from its 1-D eigenpairs
 // (mesh.cu): device data, x = K^+ b in FP32 (six transform passes; w1, w2 N^3
 // scratch), release
 cudaError_t fdm_setup(FineFDM& f, int N, const std::vector<double>& lam, const std::vector<double>& V,
                       bool tensor_cores, bool null_mode = true);
-cudaError_t fdm_apply(const FineFDM& f, const float* b, float* x, float* w1, float* w2, cudaStream_t s);
+// V vectors at a stride of vs values (V = 2 with the tensor-core passes only)
+cudaError_t fdm_apply(const FineFDM& f, const float* b, float* x, float* w1, float* w2, cudaStream_t s, int V = 1,
+                      int64_t vs = 0);
 void fdm_free(FineFDM& f);
 void solver_destroy(Solver* s);
 size_t scan_tmp_bytes(int64_t n);
@@ -376,6 +403,14 @@ cudaError_t mesh_solve_end(Solver* s);
 // mesh_solve_begin re-calibrates with one more refinement sweep
 bool mesh_solve_check(Solver* s);
 cudaError_t mesh_solve(Solver* s, const double* b, double* phi);
+// the paired solve (s->nv == 2): K phi = b and K phi' = b' with b' = b + nodes and
+// phi' = phi + nodes, one chain of kernels for both.  Calibrates (synchronously,
+// one right-hand side at a time) on its first call for a pair of pointers, then
+// replays; the second result's counts and residual in s->iters2 etc.
+cudaError_t mesh_solve_begin2(Solver* s, const double* b, double* phi);
+// as mesh_solve_check, for both right-hand sides of the paired solve
+bool mesh_solve_check2(Solver* s);
+bool mesh_solve_paired(const Solver* s);   // the solver can pair right-hand sides
 cudaError_t pair_counts(fep3m_ctx* c, unsigned long long* dev5, cudaStream_t s);
 // short-range part in two launches: the screen contraction and the singular
 // sums need only the binned charges and the vertex density, so they run on

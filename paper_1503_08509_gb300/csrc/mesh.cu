@@ -503,14 +503,15 @@ __device__ __forceinline__ T st_KM(const T* u, const T* w) {
 template <class T, int EPI>
 __device__ __forceinline__ T apply_epilogue(int64_t g, T y, T bg, T dg, T xg, T* __restrict__ out,
                                                T* __restrict__ d, T* __restrict__ xo, T c0, T c1, T c2, T dv,
-                                               float rs) {
+                                               float rs, float& rsd) {
   if constexpr (std::is_same<T, dfv>::value) {
     static_assert(EPI == EPI_RESID, "the double-float apply computes residuals only");
     // FP32 output rs (b - y): the double-float difference (two-sum), rounded
     const float sm = bg.h - y.h;
     const float bv = sm - bg.h;
     const float err = (bg.h - (sm - bv)) + (-y.h - bv);
-    reinterpret_cast<float*>(out)[g] = (sm + ((bg.l - y.l) + err)) * rs;
+    rsd = (sm + ((bg.l - y.l) + err)) * rs;
+    reinterpret_cast<float*>(out)[g] = rsd;
     return y;
   } else if constexpr (EPI == EPI_Y) {
     out[g] = y;
@@ -534,20 +535,25 @@ __device__ __forceinline__ T apply_epilogue(int64_t g, T y, T bg, T dg, T xg, T*
   }
 }
 
-// grid: (ceil(N / AFX), ceil(N / AFY), ceil(n / steps)), AT threads, dynamic
+// grid: (ceil(N / AFX), ceil(N / AFY), V ceil(n / steps)) for V vectors at a
+// stride of vs nodes (scalars at scal + 64 v; DOT with V = 1), AT threads, dynamic
 // shared memory sizeof(ApplySmem<T, EPI>); N = 3 n with n >= 3.  T = double or
 // dfv (EPI_RESID only, the refinement residual): out is FP32 and receives the
 // residual times the power of two the scaling reduction derived (scal)
 //
-// DOT (EPI_Y: x.(Kx); EPI_CHEB: b.(new iterate)): each thread accumulates its
-// nodes' products, then block_sum_finish with dt (partials indexed by the
-// linear block id).
+// DOT (EPI_Y: x.(Kx); EPI_CHEB: b.(new iterate); EPI_RESID with dfv: |r|^2 of
+// the FP32 residual written): each thread accumulates its nodes' products,
+// then block_sum_finish with dt (partials indexed by the block's linear id
+// within its vector; vector v's partials, counter and total at
+// dt.partials + v nblocks, dt.counter + v, dt.out + 64 v).
 template <class T, int EPI, bool DOT = false>
 __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
     k_apply_el(int N, int steps, const T* __restrict__ x, T* __restrict__ out, const T* __restrict__ b,
-               T* __restrict__ d, T* __restrict__ xo, T c0, T c1, T c2, double* __restrict__ scal, ApplyDot dt) {
+               T* __restrict__ d, T* __restrict__ xo, T c0, T c1, T c2, double* __restrict__ scal, ApplyDot dt,
+               int64_t vs) {
   PDL_PROLOGUE
-  static_assert(!DOT || EPI == EPI_Y || EPI == EPI_CHEB, "fused dots: EPI_Y and EPI_CHEB");
+  static_assert(!DOT || EPI == EPI_Y || EPI == EPI_CHEB || (EPI == EPI_RESID && std::is_same<T, dfv>::value),
+                "fused dots: EPI_Y, EPI_CHEB and the double-float residual");
   extern __shared__ __align__(16) unsigned char apply_smem_raw[];
   ApplySmem<T, EPI, DOT>& S = *reinterpret_cast<ApplySmem<T, EPI, DOT>*>(apply_smem_raw);
   constexpr int NST = apply_nst<T, EPI, DOT>();
@@ -555,7 +561,21 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
   const int n = N / 3;
   const int64_t NN = (int64_t)N * N;
   const int x0 = blockIdx.x * AFX, y0 = blockIdx.y * AFY;
-  const int e0 = blockIdx.z * steps, e1 = min(n, e0 + steps);
+  // several vectors (vs: their stride in nodes; scalars in blocks of 64): the z blocks of vector v follow those of v - 1
+  const int zsb = (n + steps - 1) / steps, vi = (int)blockIdx.z / zsb;
+  const int e0 = ((int)blockIdx.z - vi * zsb) * steps, e1 = min(n, e0 + steps);
+  if (vi > 0) {
+    const int64_t o = vi * vs;
+    x += o;
+    if constexpr (EPI == EPI_RESID && !std::is_same<T, float>::value)
+      out = reinterpret_cast<T*>(reinterpret_cast<float*>(out) + o);   // the FP32 residual
+    else
+      out += o;
+    if (b) b += o;
+    if (d) d += o;
+    if (xo) xo += o;
+    scal += 64 * vi;
+  }
   const int tid = threadIdx.x;
   float rs = 0.0f;   // power-of-two scale of the refinement residual (FP64, double-float)
   if constexpr (!std::is_same<T, float>::value) rs = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_SCALE];
@@ -692,6 +712,7 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
         y[1] = st_KM<T, 1>(u + 1, v + 1);
         y[2] = st_KM<T, 2>(u + 2, v + 2);
         T dsum{};
+        float dres = 0.f;
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
           T bg{}, dg{}, xg{};
@@ -699,10 +720,13 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
           if constexpr (NST > 1) dg = S.stg[NST > 1 ? 1 : 0][p][x_yy][3 * x_ex + r];
           if constexpr (NST > 2) xg = S.stg[NST > 2 ? 2 : 0][p][x_yy][3 * x_ex + r];
           if constexpr (EPI == EPI_CHEB && NST == 2) xg = x[g + r];
-          const T f = apply_epilogue<T, EPI>(g + r, y[r], bg, dg, xg, out, d, xo, c0, c1, c2, dv[r], rs);
-          if constexpr (DOT) dsum = r == 0 ? bg * f : dsum + bg * f;   // EPI_Y stages x in the b slot
+          float rsd = 0.f;
+          const T f = apply_epilogue<T, EPI>(g + r, y[r], bg, dg, xg, out, d, xo, c0, c1, c2, dv[r], rs, rsd);
+          if constexpr (DOT && EPI == EPI_RESID) dres = fmaf(rsd, rsd, dres);
+          else if constexpr (DOT) dsum = r == 0 ? bg * f : dsum + bg * f;   // EPI_Y stages x in the b slot
         }
-        if constexpr (DOT) dacc += (double)dsum;
+        if constexpr (DOT && EPI != EPI_RESID) dacc += (double)dsum;
+        if constexpr (DOT && EPI == EPI_RESID) dacc += (double)dres;
       }
     }
     // next element: slots 0..3 <- 3..6, slots 4..6 <- the prefetched planes
@@ -716,9 +740,11 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
     zs += 3;
     if (zs >= N) zs -= N;
   }
-  if constexpr (DOT)
-    block_sum_finish(dacc, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
-                     gridDim.x * gridDim.y * gridDim.z, dt.partials, dt.counter, dt.out, dt.post, 0.0, scal);
+  if constexpr (DOT) {
+    const unsigned nbv = gridDim.x * gridDim.y * zsb;   // blocks per vector
+    block_sum_finish(dacc, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * (blockIdx.z - vi * zsb)), nbv,
+                     dt.partials + (size_t)vi * nbv, dt.counter + vi, dt.out + 64 * vi, dt.post, 0.0, scal);
+  }
 }
 
 template <class T, int EPI, bool DOT = false>
@@ -737,6 +763,7 @@ static cudaError_t apply_set_smem() {
   if (e == cudaSuccess) e = apply_set_smem_one<float, EPI_CHEB, true>();
   if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_RESID>();
   if (e == cudaSuccess) e = apply_set_smem_one<dfv, EPI_RESID>();
+  if (e == cudaSuccess) e = apply_set_smem_one<dfv, EPI_RESID, true>();
   // coarsest-level kernels at N = CP_MAX
   const int smp = 3 * CP_MAX * (CP_MAX + 1) * (int)sizeof(float);
   const int smq = (2 * CP_MAX * (CP_MAX + 1) + 2 * CP_MAX * (CP_PEN + 1)) * (int)sizeof(float);
@@ -1060,16 +1087,18 @@ __global__ void __launch_bounds__(256) k_fdm_axis(int N, const float* __restrict
 // fast-diagonalisation passes (R = N^2, K = NC = N, B = W^T; SCALE: the
 // inverse eigenvalue sums, rows r = j + N k) and for the screen adjoint's
 // contraction (R elements, K = 64 nodes, NC offsets).  err: a bounded wait
-// that gave up.
+// that gave up.  gridDim.y vectors at a stride of vs values (in and out).
 constexpr int FT_THREADS = 256;
 
 template <bool SCALE>
 __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int cb, int ce, int nt,
                                                          const float* __restrict__ in, const uint4* __restrict__ Bp,
                                                          const float* __restrict__ lam, int null_mode, int N,
-                                                         float* __restrict__ out, int* __restrict__ err) {
+                                                         float* __restrict__ out, int* __restrict__ err, int64_t vs) {
   PDL_PROLOGUE
   using namespace tc;
+  in += (int64_t)blockIdx.y * vs;   // vector blockIdx.y of several at a stride of vs values
+  out += (int64_t)blockIdx.y * vs;
   extern __shared__ __align__(16) unsigned char fsm[];
   unsigned char* tiles = fsm + ((1024u - (smem_u32(fsm) & 1023u)) & 1023u);
   const uint32_t tl = smem_u32(tiles), tb = tl + 3 * 16384;   // A pieces (128 x 64 each), then B pieces (nt x 64)
@@ -1238,12 +1267,22 @@ __device__ __forceinline__ T reduce_term(const T* __restrict__ x, const T* __res
 
 // each thread adds its nodes (four per round, in the working precision) into
 // an FP64 accumulator; then block_sum_finish.  MODE: x.y, sum x, sum w3 x
-// (node integrals), x.x
+// (node integrals), x.x.  gridDim.y vectors: vector v at x + v vs, its total
+// at out + 64 v (out lies in the vector's block of 64 scalars)
 template <class T, int MODE>
 __global__ void k_reduce(int N, const T* __restrict__ x, const T* __restrict__ y, double* __restrict__ partials,
                          unsigned int* __restrict__ counter, double* __restrict__ out, int post, double arg,
-                         double* __restrict__ scal) {
+                         double* __restrict__ scal, int64_t vs) {
   PDL_PROLOGUE
+  if (blockIdx.y > 0) {   // vector blockIdx.y: x, y at a stride of vs; out, scal in its block of 64 scalars
+    const int v = blockIdx.y;
+    x += v * vs;
+    if (y) y += v * vs;
+    partials += (size_t)v * gridDim.x;
+    counter += v;
+    out += 64 * v;
+    scal += 64 * v;
+  }
   const int64_t NN = (int64_t)N * N, tot = NN * N;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
@@ -1285,13 +1324,16 @@ __device__ __forceinline__ T derived(const double* scal, int k) {
 }
 
 // v -= m w3 (removes the load of a uniform background, m = sum v / W), or
-// v -= m (mean zero, m = sum w3 v / W); grid (ceil(N / bx), N, N)
+// v -= m (mean zero, m = sum w3 v / W); grid (ceil(N / bx), V N, N) for V
+// vectors at a stride of vs (the same for k_project_copy64)
 template <class T>
-__global__ void k_project(int N, T* __restrict__ v, const double* __restrict__ scal, int mean_zero) {
+__global__ void k_project(int N, T* __restrict__ v, const double* __restrict__ scal, int mean_zero, int64_t vs) {
   PDL_PROLOGUE
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
   if (ix >= N) return;
-  const int iy = blockIdx.y, iz = blockIdx.z;
+  const int vi = (int)blockIdx.y / N, iy = (int)blockIdx.y - vi * N, iz = blockIdx.z;
+  v += vi * vs;
+  scal += 64 * vi;
   const int64_t g = ix + (int64_t)N * (iy + (int64_t)N * iz);
   const T m = derived<T>(scal, SD_MEAN);
   if (mean_zero) {
@@ -1324,82 +1366,49 @@ __global__ void k_cg_dir(int64_t n, const double* __restrict__ scal, T* __restri
   p[g] = z[g] + beta * p[g];
 }
 
-// ------------------------------------------- double-float refinement helpers
-// bdf = b - m w3 as float pairs (m = sum b / W from the preceding reduction);
-// grid (ceil(N / bx), N, N)
-// r = s v rounded to FP32 (v the projected right-hand side as float pairs or
-// FP64, s the power-of-two scale) and |r|^2 into *out (grid of the reductions)
-template <class S>
-__global__ void k_round_scaled_norm(int64_t n, const S* __restrict__ v, float* __restrict__ r,
+// ------------------------------------------------------ refinement helpers
+// FP64: r = s v rounded to FP32 (v the projected right-hand side, s the
+// power-of-two scale) and |r|^2 into *out (grid of the reductions)
+__global__ void k_round_scaled_norm(int64_t n, const double* __restrict__ v, float* __restrict__ r,
                                     double* __restrict__ partials, unsigned int* __restrict__ counter,
-                                    double* __restrict__ out, double* __restrict__ scal) {
+                                    double* __restrict__ out, double* __restrict__ scal, int64_t vs) {
   PDL_PROLOGUE
+  if (blockIdx.y > 0) {
+    const int vi = blockIdx.y;
+    v += vi * vs;
+    r += vi * vs;
+    partials += (size_t)vi * gridDim.x;
+    counter += vi;
+    out += 64 * vi;
+    scal += 64 * vi;
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
-    float x;
-    if constexpr (std::is_same<S, dfv>::value) {
-      const float sc = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_SCALE];
-      const dfv y = v[g];
-      x = (y.h + y.l) * sc;
-    } else {
-      x = (float)(v[g] * scal[SC_DERIVED + SD_SCALE]);
-    }
+    const float x = (float)(v[g] * scal[SC_DERIVED + SD_SCALE]);
     r[g] = x;
     acc += (double)x * (double)x;
   }
   block_sum_finish(acc, blockIdx.x, gridDim.x, partials, counter, out, POST_NONE, 0.0, scal);
 }
 
-// phi = h + l in FP64 and its integral (sum of the order-3 node weights times
-// phi, rows per warp as in k_reduce) into *out with the mean derived (POST_MEAN, arg = 1 / n^3)
-__global__ void k_df_to_double_wsum(int N, const dfv* __restrict__ v, double* __restrict__ phi,
-                                    double* __restrict__ partials, unsigned int* __restrict__ counter,
-                                    double* __restrict__ out, double arg, double* __restrict__ scal) {
-  PDL_PROLOGUE
-  const int64_t rows = (int64_t)N * N, stride = (int64_t)gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nwarps = stride >> 5;
-  double acc = 0.0;
-  for (int64_t row = warp; row < rows; row += nwarps) {
-    const int iz = (int)(row / N), iy = (int)(row - (int64_t)iz * N);
-    const double wyz = (iy % 3 ? 0.375 : 0.25) * (iz % 3 ? 0.375 : 0.25);
-    const dfv* vr = v + row * N;
-    double* pr = phi + row * N;
-    double s0 = 0.0, s1 = 0.0;   // vertex / interior columns
-    for (int ix = lane; ix < N; ix += 32) {
-      const dfv y = vr[ix];
-      const double x = (double)y.h + (double)y.l;
-      pr[ix] = x;
-      if (ix % 3 == 0) s0 += x;
-      else s1 += x;
-    }
-    acc += wyz * (0.25 * s0 + 0.375 * s1);
-  }
-  block_sum_finish(acc, blockIdx.x, gridDim.x, partials, counter, out, POST_MEAN, arg, scal);
-}
-
-__global__ void k_split_df(int N, const double* __restrict__ b, const double* __restrict__ scal, dfv* __restrict__ bdf) {
-  PDL_PROLOGUE
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ix >= N) return;
-  const int iy = blockIdx.y, iz = blockIdx.z;
-  const int64_t g = ix + (int64_t)N * (iy + (int64_t)N * iz);
-  const double w = (ix % 3 ? 0.375 : 0.25) * (iy % 3 ? 0.375 : 0.25) * (iz % 3 ? 0.375 : 0.25);
-  const double v = b[g] - scal[SC_DERIVED + SD_MEAN] * w;
-  const float h = (float)v;
-  bdf[g] = {h, (float)(v - (double)h)};
-}
-
-// phi += e / s (exact: s is a power of two), two-sum then renormalised
+// phi += e / s (exact: s is a power of two), two-sum then renormalised;
+// first: phi = e / s (the first sweep, from phi = 0)
 __global__ void k_df_update(int64_t n, dfv* __restrict__ phi, const float* __restrict__ e,
-                            const double* __restrict__ scal) {
+                            const double* __restrict__ scal, int64_t vs, int first) {
   PDL_PROLOGUE
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
+  phi += blockIdx.y * vs;   // vector blockIdx.y
+  e += blockIdx.y * vs;
+  scal += 64 * blockIdx.y;
   const float is = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_INVSCALE];
-  dfv p = phi[g];
   const float t = e[g] * is;
+  if (first) {   // from phi = 0: exactly e / s
+    phi[g] = {t, 0.f};
+    return;
+  }
+  dfv p = phi[g];
   const float sum = p.h + t;
   const float bv = sum - p.h;
   const float err = (p.h - (sum - bv)) + (t - bv);
@@ -1408,13 +1417,222 @@ __global__ void k_df_update(int64_t n, dfv* __restrict__ phi, const float* __res
   phi[g] = {h, lo - (h - sum)};
 }
 
+// ---- double-float refinement bookkeeping (MIXED).  FP64 arithmetic runs at a
+// small fraction of the FP32 rate on this GPU, so the sums, the projection and
+// the scaling work on float pairs; FP64 is used only to split the FP64
+// right-hand side and to form the FP64 result.  Several right-hand sides:
+// vector blockIdx.y at a stride of vs values, scalars in its block of 64,
+// partials and counter per vector.
+
+// a normalised pair: |l| <= half an ulp of h
+__device__ __forceinline__ dfv df_norm(dfv a) {
+  const float h = a.h + a.l;
+  return {h, a.l - (h - a.h)};
+}
+
+// m w as a pair (w a node weight, exact in FP32; m as the pair mh + ml)
+__device__ __forceinline__ dfv df_scaled(float mh, float ml, float w) {
+  const float p = mh * w;
+  return {p, fmaf(ml, w, fmaf(mh, w, -p))};
+}
+
+// Two block-then-grid sums at once (blockDim.x == 256): the block's totals go
+// to partials[2 bid], partials[2 bid + 1]; the last block adds the partials in
+// index order and returns true on its thread 0 with the totals in ta, tb.
+__device__ bool block_sum2_finish(double a, double b, unsigned bid, unsigned nblocks, double* __restrict__ partials,
+                                  unsigned int* __restrict__ counter, double& ta, double& tb) {
+  __shared__ double sh[2][8];
+  __shared__ bool last;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = a;
+    sh[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0;
+    for (int k = 0; k < 8; ++k) {
+      s0 += sh[0][k];
+      s1 += sh[1][k];
+    }
+    partials[2 * bid] = s0;
+    partials[2 * bid + 1] = s1;
+    __threadfence();
+    const unsigned int done = atomicAdd(counter, 1u);
+    last = (done == nblocks - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s0 = 0, s1 = 0;
+  for (unsigned int k = threadIdx.x; k < nblocks; k += blockDim.x) {
+    s0 += ((volatile double*)partials)[2 * k];
+    s1 += ((volatile double*)partials)[2 * k + 1];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = s0;
+    sh[1][threadIdx.x >> 5] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return false;
+  ta = tb = 0;
+  for (int k = 0; k < 8; ++k) {
+    ta += sh[0][k];
+    tb += sh[1][k];
+  }
+  *counter = 0u;
+  return true;
+}
+
+// setup, first pass: bdf = b as float pairs, sum b into scal[5] with the mean
+// m = sum b / W derived, sum b^2 into scal[7] with the scale s = 2^-k, 2^k near
+// the RMS sqrt(sum b^2 / n), derived (the POST_MEAN and POST_SCALE forms)
+__global__ void k_ref_split_sums(int64_t n, const double* __restrict__ b, dfv* __restrict__ bdf,
+                                 double* __restrict__ partials, unsigned int* __restrict__ counter,
+                                 double* __restrict__ scal, double invW, int64_t vs) {
+  PDL_PROLOGUE
+  const int vi = blockIdx.y;
+  b += vi * vs;
+  bdf += vi * vs;
+  partials += 2 * (size_t)vi * gridDim.x;
+  counter += vi;
+  scal += 64 * vi;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  dfv sum = {0.f, 0.f};
+  float sq = 0.f;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
+    const double v = b[g];
+    const float h = (float)v;
+    const dfv x = {h, (float)(v - (double)h)};
+    bdf[g] = x;
+    sum += x;
+    sq = fmaf(h, h, sq);
+  }
+  double ta, tb;
+  if (block_sum2_finish((double)sum.h + (double)sum.l, (double)sq, blockIdx.x, gridDim.x, partials, counter, ta, tb)) {
+    double* dd = scal + SC_DERIVED;
+    float* df = (float*)(scal + SC_DERIVED_F);
+    scal[5] = ta;
+    scal[7] = tb;
+    dd[SD_MEAN] = ta * invW;
+    df[SD_MEAN] = (float)(ta * invW);
+    const double rms = sqrt(tb / (double)n);
+    int k = rms > 0.0 && isfinite(rms) ? ilogb(rms) : 0;
+    k = max(-100, min(100, k));
+    dd[SD_SCALE] = ldexp(1.0, -k);
+    dd[SD_INVSCALE] = ldexp(1.0, k);
+    df[SD_SCALE] = (float)ldexp(1.0, -k);
+    df[SD_INVSCALE] = (float)ldexp(1.0, k);
+  }
+}
+
+// setup, second pass: Pi b = b - m w3 in place (float pairs), r = s Pi b in
+// FP32 and |r|^2 into scal[10]; whole rows per warp (the node weights from
+// the row and the column)
+__global__ void k_ref_project_scale(int N, dfv* __restrict__ bdf, float* __restrict__ r,
+                                    double* __restrict__ partials, unsigned int* __restrict__ counter,
+                                    double* __restrict__ scal, int64_t vs) {
+  PDL_PROLOGUE
+  const int vi = blockIdx.y;
+  bdf += vi * vs;
+  r += vi * vs;
+  partials += (size_t)vi * gridDim.x;
+  counter += vi;
+  scal += 64 * vi;
+  const double m = scal[SC_DERIVED + SD_MEAN];
+  const float mh = (float)m, ml = (float)(m - (double)mh);
+  const float sc = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_SCALE];
+  const int64_t rows = (int64_t)N * N, stride = (int64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nwarps = stride >> 5;
+  float acc = 0.f;
+  for (int64_t row = warp; row < rows; row += nwarps) {
+    const int iz = (int)(row / N), iy = (int)(row - (int64_t)iz * N);
+    const float wyz = (iy % 3 ? 0.375f : 0.25f) * (iz % 3 ? 0.375f : 0.25f);
+    dfv* br = bdf + row * N;
+    float* rr = r + row * N;
+    for (int ix = lane; ix < N; ix += 32) {
+      const dfv mw = df_scaled(mh, ml, wyz * (ix % 3 ? 0.375f : 0.25f));
+      dfv v = br[ix];
+      v += dfv{-mw.h, -mw.l};
+      v = df_norm(v);
+      br[ix] = v;
+      const float x = (v.h + v.l) * sc;
+      rr[ix] = x;
+      acc = fmaf(x, x, acc);
+    }
+  }
+  block_sum_finish((double)acc, blockIdx.x, gridDim.x, partials, counter, scal + 10, POST_NONE, 0.0, scal);
+}
+
+// finish, first pass: the integral sum w3 phi of the iterate (float pairs) into
+// scal[6] with the mean derived (POST_MEAN, arg = 1 / W); rows per warp, the
+// row's vertex and interior columns summed as float pairs
+__global__ void k_ref_wsum(int N, const dfv* __restrict__ v, double* __restrict__ partials,
+                           unsigned int* __restrict__ counter, double* __restrict__ scal, double invW, int64_t vs) {
+  PDL_PROLOGUE
+  const int vi = blockIdx.y;
+  v += vi * vs;
+  partials += (size_t)vi * gridDim.x;
+  counter += vi;
+  scal += 64 * vi;
+  const int64_t rows = (int64_t)N * N, stride = (int64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nwarps = stride >> 5;
+  double acc = 0.0;
+  for (int64_t row = warp; row < rows; row += nwarps) {
+    const int iz = (int)(row / N), iy = (int)(row - (int64_t)iz * N);
+    const double wyz = (iy % 3 ? 0.375 : 0.25) * (iz % 3 ? 0.375 : 0.25);
+    const dfv* vr = v + row * N;
+    dfv s0 = {0.f, 0.f}, s1 = {0.f, 0.f};   // vertex / interior columns
+    for (int ix = lane; ix < N; ix += 32) {
+      if (ix % 3 == 0) s0 += vr[ix];
+      else s1 += vr[ix];
+    }
+    acc += wyz * (0.25 * ((double)s0.h + (double)s0.l) + 0.375 * ((double)s1.h + (double)s1.l));
+  }
+  block_sum_finish(acc, blockIdx.x, gridDim.x, partials, counter, scal + 6, POST_MEAN, invW, scal);
+}
+
+// finish, second pass: phi = v - m in FP64 (m the mean just derived) and, for
+// vector 0 when hl is set, the same value as hi + lo floats
+__global__ void k_ref_out(int64_t n, const dfv* __restrict__ v, double* __restrict__ phi, float2* __restrict__ hl,
+                          const double* __restrict__ scal, int64_t vs) {
+  PDL_PROLOGUE
+  const int vi = blockIdx.y;
+  v += vi * vs;
+  phi += vi * vs;
+  scal += 64 * vi;
+  const double m = scal[SC_DERIVED + SD_MEAN];
+  const float mh = (float)m, ml = (float)(m - (double)mh);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
+    dfv y = v[g];
+    y += dfv{-mh, -ml};
+    y = df_norm(y);
+    phi[g] = (double)y.h + (double)y.l;
+    if (hl && vi == 0) hl[g] = make_float2(y.h, y.l);
+  }
+}
+
 // FP64 refinement: bp = b - m w3 (m = sum b / W); grid (ceil(N / bx), N, N)
 __global__ void k_project_copy64(int N, const double* __restrict__ b, const double* __restrict__ scal,
-                                 double* __restrict__ bp) {
+                                 double* __restrict__ bp, int64_t vs) {
   PDL_PROLOGUE
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
   if (ix >= N) return;
-  const int iy = blockIdx.y, iz = blockIdx.z;
+  const int vi = (int)blockIdx.y / N, iy = (int)blockIdx.y - vi * N, iz = blockIdx.z;
+  b += vi * vs;
+  bp += vi * vs;
+  scal += 64 * vi;
   const int64_t g = ix + (int64_t)N * (iy + (int64_t)N * iz);
   const double w = (ix % 3 ? 0.375 : 0.25) * (iy % 3 ? 0.375 : 0.25) * (iz % 3 ? 0.375 : 0.25);
   bp[g] = b[g] - scal[SC_DERIVED + SD_MEAN] * w;
@@ -1422,10 +1640,13 @@ __global__ void k_project_copy64(int N, const double* __restrict__ b, const doub
 
 // phi += e / s (FP64 accumulation of an FP32 correction)
 __global__ void k_add_scaled(int64_t n, double* __restrict__ phi, const float* __restrict__ e,
-                             const double* __restrict__ scal) {
+                             const double* __restrict__ scal, int64_t vs) {
   PDL_PROLOGUE
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
+  phi += blockIdx.y * vs;   // vector blockIdx.y
+  e += blockIdx.y * vs;
+  scal += 64 * blockIdx.y;
   phi[g] += scal[SC_DERIVED + SD_INVSCALE] * (double)e[g];
 }
 
@@ -1446,7 +1667,7 @@ cudaError_t tc_rows_gemm(int64_t R, int K, int cb, int ce, int nt, const float* 
                          int* err, cudaStream_t s) {
   const dim3 g((unsigned)((R + 127) / 128 * ((ce + nt - 1) / nt - cb / nt)));
   FEP3M_CL k_tc_rows<false><<<g, FT_THREADS, tc_rows_smem(nt), s>>>(R, K, cb, ce, nt, in, (const uint4*)Bp,
-                                                                    nullptr, -1, 0, out, err);
+                                                                    nullptr, -1, 0, out, err, (int64_t)0);
   return cudaGetLastError();
 }
 
@@ -1460,17 +1681,18 @@ template <class T>
 static void reduce(Solver* c, int N, int mode, const T* x, const T* y, double* out, int post = POST_NONE,
                    double arg = 0.0) {
   const size_t tot = (size_t)N * N * N;
-  const int nb = (int)reduce_blocks(tot);
+  const dim3 nb((unsigned)reduce_blocks(tot), (unsigned)c->V);   // the issued right-hand sides
   double* tmp = (double*)c->red_tmp;
   cudaStream_t s = c->stream;
+  const int64_t vs = c->vs;
   if (mode == RD_DOT)
-    launch_pdl(k_reduce<T, RD_DOT>, nb, TPB, 0, s, N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
+    launch_pdl(k_reduce<T, RD_DOT>, nb, TPB, 0, s, N, x, y, tmp, c->red_counter, out, post, arg, c->scal, vs);
   else if (mode == RD_SUM)
-    launch_pdl(k_reduce<T, RD_SUM>, nb, TPB, 0, s, N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
+    launch_pdl(k_reduce<T, RD_SUM>, nb, TPB, 0, s, N, x, y, tmp, c->red_counter, out, post, arg, c->scal, vs);
   else if (mode == RD_WSUM)
-    launch_pdl(k_reduce<T, RD_WSUM>, nb, TPB, 0, s, N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
+    launch_pdl(k_reduce<T, RD_WSUM>, nb, TPB, 0, s, N, x, y, tmp, c->red_counter, out, post, arg, c->scal, vs);
   else
-    launch_pdl(k_reduce<T, RD_NORM2>, nb, TPB, 0, s, N, x, y, tmp, c->red_counter, out, post, arg, c->scal);
+    launch_pdl(k_reduce<T, RD_NORM2>, nb, TPB, 0, s, N, x, y, tmp, c->red_counter, out, post, arg, c->scal, vs);
 }
 
 // remove the background load (mean_zero 0) or the mean (1) with the scalar
@@ -1478,8 +1700,8 @@ static void reduce(Solver* c, int N, int mode, const T* x, const T* y, double* o
 template <class T>
 static void project(Solver* c, int N, T* v, int mean_zero) {
   const int bx = std::min(N, 256);
-  const dim3 grid((N + bx - 1) / bx, N, N);
-  launch_pdl(k_project<T>, grid, bx, 0, c->stream, N, v, c->scal, mean_zero);
+  const dim3 grid((N + bx - 1) / bx, N * c->V, N);
+  launch_pdl(k_project<T>, grid, bx, 0, c->stream, N, v, c->scal, mean_zero, c->vs);
 }
 
 template <class T>
@@ -1499,22 +1721,22 @@ struct MG {
     const ApplyDot nd = {nullptr, nullptr, nullptr, 0};
     if (epi == EPI_Y && dot)
       launch_pdl(k_apply_el<T, EPI_Y, true>, grid, AT, sizeof(ApplySmem<T, EPI_Y, true>), s, 
-          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, *dot);
+          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, *dot, (int64_t)0);
     else if (epi == EPI_Y)
       launch_pdl(k_apply_el<T, EPI_Y>, grid, AT, sizeof(ApplySmem<T, EPI_Y>), s, L.N, steps, x, out, b, d, xo,
-                                                                                  c0, c1, c2, sc, nd);
+                                                                                  c0, c1, c2, sc, nd, (int64_t)0);
     else if (epi == EPI_RESID)
       launch_pdl(k_apply_el<T, EPI_RESID>, grid, AT, sizeof(ApplySmem<T, EPI_RESID>), s, 
-          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, nd);
+          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, nd, (int64_t)0);
     else if (epi == EPI_CHEB && dot)
       launch_pdl(k_apply_el<T, EPI_CHEB, true>, grid, AT, sizeof(ApplySmem<T, EPI_CHEB, true>), s, 
-          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, *dot);
+          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, *dot, (int64_t)0);
     else if (epi == EPI_CHEB)
       launch_pdl(k_apply_el<T, EPI_CHEB>, grid, AT, sizeof(ApplySmem<T, EPI_CHEB>), s, 
-          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, nd);
+          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, nd, (int64_t)0);
     else
       launch_pdl(k_apply_el<T, EPI_CHEB0>, grid, AT, sizeof(ApplySmem<T, EPI_CHEB0>), s, 
-          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, nd);
+          L.N, steps, x, out, b, d, xo, c0, c1, c2, sc, nd, (int64_t)0);
   }
 
   ApplyDot dot_into(int slot, int post) const {
@@ -1597,7 +1819,7 @@ struct MG {
     const int N = f.N;
     cudaStream_t s = c->stream;
     if (f.BpF) {
-      fdm_apply(f, b, x, w1, w2, s);
+      fdm_apply(f, b, x, w1, w2, s, c->V, c->vs);
       return;
     }
     const dim3 g((unsigned)(((int64_t)N * N + FM - 1) / FM), (unsigned)((N + FN - 1) / FN));
@@ -1859,13 +2081,16 @@ static void solver_free(Solver* c) {
   c->sb_bytes = 0;
 }
 
-// PCG work vectors r, z, p, q, x, rhs in the working precision (level-0 size)
+// PCG work vectors r, z, p, q, x, rhs in the working precision (level-0 size);
+// the four the fast-diagonalisation refinement uses (r, z, x, rhs) once per
+// right-hand side of the paired solve
 static cudaError_t ensure_solver_buffers(Solver* c) {
   const size_t bytes = c->mg.lv[0].size * c->mg.elem_size;
   if (c->sb_bytes == bytes) return cudaSuccess;
   free_list(c->sb, 6);
   for (int i = 0; i < 6; ++i) {
-    cudaError_t e = cudaMalloc(&c->sb[i], bytes);
+    const size_t m = (i == 0 || i == 1 || i == 4 || i == 5) ? (size_t)c->nv : 1;
+    cudaError_t e = cudaMalloc(&c->sb[i], bytes * m);
     if (e != cudaSuccess) return e;
   }
   c->sb_bytes = bytes;
@@ -1882,25 +2107,35 @@ static cudaError_t ensure_solver_buffers(Solver* c) {
 //   MIXED: Pi b in res64 and the iterate in phidf, as float pairs
 //   FP64:  Pi b in res64 and the iterate in the output buffer, FP64
 
-// r = s (Pi b - K phi) in FP32
-static cudaError_t refine_resid(Solver* c, const double* phi64, float* r) {
+// r = s (Pi b - K phi) in FP32; norm_out (MIXED): |r|^2 accumulated by the
+// apply into norm_out (per right-hand side at norm_out + 64 v)
+static cudaError_t refine_resid(Solver* c, const double* phi64, float* r, double* norm_out = nullptr) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
   const int steps = apply_steps(N);
   const ApplyDot nd = {nullptr, nullptr, nullptr, 0};
+  dim3 grid = apply_grid(N, steps);
+  grid.z *= c->V;
   if (c->precision == FEP3M_FP64) {
-    launch_pdl(k_apply_el<double, EPI_RESID>, apply_grid(N, steps), AT, sizeof(ApplySmem<double, EPI_RESID>), c->stream, 
-            N, steps, phi64, reinterpret_cast<double*>(r), c->res64, nullptr, nullptr, 0.0, 0.0, 0.0, c->scal, nd);
+    launch_pdl(k_apply_el<double, EPI_RESID>, grid, AT, sizeof(ApplySmem<double, EPI_RESID>), c->stream, N, steps,
+               phi64, reinterpret_cast<double*>(r), c->res64, nullptr, nullptr, 0.0, 0.0, 0.0, c->scal, nd, c->vs);
+  } else if (norm_out) {
+    const dfv z = {0.0f, 0.0f};
+    const ApplyDot dt = {(double*)c->red_tmp, c->red_counter, norm_out, POST_NONE};
+    launch_pdl(k_apply_el<dfv, EPI_RESID, true>, grid, AT, sizeof(ApplySmem<dfv, EPI_RESID, true>), c->stream, N,
+               steps, reinterpret_cast<const dfv*>(c->phidf), reinterpret_cast<dfv*>(r),
+               reinterpret_cast<const dfv*>(c->res64), nullptr, nullptr, z, z, z, c->scal, dt, c->vs);
   } else {
     const dfv z = {0.0f, 0.0f};
-    launch_pdl(k_apply_el<dfv, EPI_RESID>, apply_grid(N, steps), AT, sizeof(ApplySmem<dfv, EPI_RESID>), c->stream, 
-            N, steps, reinterpret_cast<const dfv*>(c->phidf), reinterpret_cast<dfv*>(r),
-            reinterpret_cast<const dfv*>(c->res64), nullptr, nullptr, z, z, z, c->scal, nd);
+    launch_pdl(k_apply_el<dfv, EPI_RESID>, grid, AT, sizeof(ApplySmem<dfv, EPI_RESID>), c->stream, N, steps,
+               reinterpret_cast<const dfv*>(c->phidf), reinterpret_cast<dfv*>(r),
+               reinterpret_cast<const dfv*>(c->res64), nullptr, nullptr, z, z, z, c->scal, nd, c->vs);
   }
   return cudaGetLastError();
 }
 
-// start: Pi b, the scale s, phi = 0, r = s Pi b in FP32 and |r|^2 into scal[10]
+// start: Pi b, the scale s, phi = 0 (FP64; MIXED: the first update assigns),
+// r = s Pi b in FP32 and |r|^2 into scal[10]
 static void refine_setup(Solver* c, const double* b, double* phi64, float* r) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
@@ -1908,45 +2143,53 @@ static void refine_setup(Solver* c, const double* b, double* phi64, float* r) {
   const double W = (double)L0.n * L0.n * L0.n;
   cudaStream_t s = c->stream;
   double* sc = c->scal;
+  if (c->precision != FEP3M_FP64) {
+    const dim3 gr((unsigned)reduce_blocks(n), (unsigned)c->V);
+    launch_pdl(k_ref_split_sums, gr, TPB, 0, s, (int64_t)n, b, reinterpret_cast<dfv*>(c->res64), (double*)c->red_tmp,
+               c->red_counter, sc, 1.0 / W, c->vs);
+    launch_pdl(k_ref_project_scale, gr, TPB, 0, s, N, reinterpret_cast<dfv*>(c->res64), r, (double*)c->red_tmp,
+               c->red_counter, sc, c->vs);
+    return;
+  }
   reduce<double>(c, N, RD_SUM, b, nullptr, sc + 5, POST_MEAN, 1.0 / W);
   reduce<double>(c, N, RD_NORM2, b, nullptr, sc + 7, POST_SCALE, 1.0 / (double)n);
   const int bx = std::min(N, 256);
-  const dim3 g3((N + bx - 1) / bx, N, N);
-  if (c->precision == FEP3M_FP64) {
-    launch_pdl(k_project_copy64, g3, bx, 0, s, N, b, sc, c->res64);
-    cudaMemsetAsync(phi64, 0, n * sizeof(double), s);
-    launch_pdl(k_round_scaled_norm<double>, (int)reduce_blocks(n), TPB, 0, s, (int64_t)n, (const double*)c->res64,
-               r, (double*)c->red_tmp, c->red_counter, sc + 10, sc);
-  } else {
-    launch_pdl(k_split_df, g3, bx, 0, s, N, b, sc, reinterpret_cast<dfv*>(c->res64));
-    cudaMemsetAsync(c->phidf, 0, n * sizeof(dfv), s);
-    launch_pdl(k_round_scaled_norm<dfv>, (int)reduce_blocks(n), TPB, 0, s, (int64_t)n,
-               reinterpret_cast<const dfv*>(c->res64), r, (double*)c->red_tmp, c->red_counter, sc + 10, sc);
-  }
+  const int V = c->V;
+  const int64_t vs = c->vs;
+  const dim3 g3((N + bx - 1) / bx, N * V, N);
+  const dim3 gr((unsigned)reduce_blocks(n), (unsigned)V);
+  launch_pdl(k_project_copy64, g3, bx, 0, s, N, b, sc, c->res64, vs);
+  for (int v = 0; v < V; ++v) cudaMemsetAsync(phi64 + v * vs, 0, n * sizeof(double), s);
+  launch_pdl(k_round_scaled_norm, gr, TPB, 0, s, (int64_t)n, (const double*)c->res64, r, (double*)c->red_tmp,
+             c->red_counter, sc + 10, sc, vs);
 }
 
-// phi += e / s
-static void refine_update(Solver* c, double* phi64, const float* e) {
+// phi += e / s (first: the first sweep; MIXED assigns phi = e / s)
+static void refine_update(Solver* c, double* phi64, const float* e, bool first) {
   const size_t n = c->mg.lv[0].size;
+  const dim3 g((unsigned)grid_for(n), (unsigned)c->V);
   if (c->precision == FEP3M_FP64)
-    launch_pdl(k_add_scaled, grid_for(n), TPB, 0, c->stream, (int64_t)n, phi64, e, c->scal);
+    launch_pdl(k_add_scaled, g, TPB, 0, c->stream, (int64_t)n, phi64, e, c->scal, c->vs);
   else
-    launch_pdl(k_df_update, grid_for(n), TPB, 0, c->stream, (int64_t)n, reinterpret_cast<dfv*>(c->phidf), e,
-                                                             c->scal);
+    launch_pdl(k_df_update, g, TPB, 0, c->stream, (int64_t)n, reinterpret_cast<dfv*>(c->phidf), e, c->scal, c->vs,
+               first ? 1 : 0);
 }
 
-// end: phi in FP64 with mean zero
-static void refine_finish(Solver* c, double* phi) {
+// end: phi in FP64 with mean zero (MIXED with hl: vector 0 also as hi + lo floats)
+static void refine_finish(Solver* c, double* phi, float2* hl = nullptr) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
   const size_t n = L0.size;
   const double W = (double)L0.n * L0.n * L0.n;
-  if (c->precision != FEP3M_FP64)
-    launch_pdl(k_df_to_double_wsum, (int)reduce_blocks(n), TPB, 0, c->stream, N,
-               reinterpret_cast<const dfv*>(c->phidf), phi, (double*)c->red_tmp, c->red_counter, c->scal + 6,
-               1.0 / W, c->scal);
-  else
-    reduce<double>(c, N, RD_WSUM, phi, nullptr, c->scal + 6, POST_MEAN, 1.0 / W);
+  if (c->precision != FEP3M_FP64) {
+    const dfv* v = reinterpret_cast<const dfv*>(c->phidf);
+    launch_pdl(k_ref_wsum, dim3((unsigned)reduce_blocks(n), (unsigned)c->V), TPB, 0, c->stream, N, v,
+               (double*)c->red_tmp, c->red_counter, c->scal, 1.0 / W, c->vs);
+    launch_pdl(k_ref_out, dim3((unsigned)grid_for(n), (unsigned)c->V), TPB, 0, c->stream, (int64_t)n, v, phi, hl,
+               (const double*)c->scal, c->vs);
+    return;
+  }
+  reduce<double>(c, N, RD_WSUM, phi, nullptr, c->scal + 6, POST_MEAN, 1.0 / W);
   project<double>(c, N, phi, 1);
 }
 
@@ -1977,6 +2220,7 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
   cudaMemcpyAsync(&bb, sc + 10, sizeof(double), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   if (bb == 0.0) {
+    if (c->phidf) cudaMemsetAsync(c->phidf, 0, L0.size * sizeof(dfv), s);
     refine_finish(c, phi);
     return cudaGetLastError();
   }
@@ -1990,7 +2234,7 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
     else it = mg.pcg(r32, e32, (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], 1e-5, 30, &inner_res);
     *iters += it;
     *k_inner_max = std::max(*k_inner_max, it);
-    refine_update(c, phi, e32);
+    refine_update(c, phi, e32, step == 0);
     // the residual's sum is rounding noise (K has zero column sums), and the
     // inner solve projects its right-hand side: no projection here
     cudaError_t e = refine_resid(c, phi, r32);
@@ -2009,9 +2253,11 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
   return cudaGetLastError();
 }
 
-// fixed-count solve from c->in64 into c->out64, no host round trip; leaves
-// |s Pi b|^2 in scal[10] and the final scaled residual |r|^2 in scal[11]
-static cudaError_t solve_fixed(Solver* c) {
+// fixed-count solve of the c->V right-hand sides at b (stride c->vs) into phi
+// with kout refinement sweeps, no host round trip; leaves |s Pi b|^2 in
+// scal[10] and the final scaled residual |r|^2 in scal[11] (scal[64 v + ...]
+// for right-hand side v)
+static cudaError_t solve_fixed(Solver* c, const double* b, double* phi, int kout) {
   void** sb = c->sb;
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
@@ -2019,19 +2265,22 @@ static cudaError_t solve_fixed(Solver* c) {
   MG<float> mg(c);
   float* r32 = (float*)sb[5];
   float* e32 = (float*)sb[4];
-  double* phi = c->out64;
-  refine_setup(c, c->in64, phi, r32);   // |r|^2 into sc[10]
-  for (int step = 0; step < c->plan_kout; ++step) {
+  refine_setup(c, b, phi, r32);   // |r|^2 into sc[10]
+  const bool mixed = c->precision != FEP3M_FP64;
+  for (int step = 0; step < kout; ++step) {
     if (step == 0 && c->ev_in0) cudaEventRecordWithFlags(c->ev_in0, c->stream, cudaEventRecordExternal);
     if (c->mg.fdm.N > 0) mg.fdm_solve(r32, e32, (float*)sb[0], (float*)sb[1]);
     else mg.pcg_fixed(r32, e32, (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], c->plan_kin);
     if (step == 0 && c->ev_in1) cudaEventRecordWithFlags(c->ev_in1, c->stream, cudaEventRecordExternal);
-    refine_update(c, phi, e32);
-    cudaError_t e = refine_resid(c, phi, r32);
+    refine_update(c, phi, e32, step == 0);
+    // MIXED: the last residual's |r|^2 accumulated by its apply
+    cudaError_t e = refine_resid(c, phi, r32, mixed && step == kout - 1 ? sc + 11 : nullptr);
     if (e != cudaSuccess) return e;
   }
-  reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 11);
-  refine_finish(c, phi);
+  if (mixed && kout == 0)
+    cudaMemsetAsync(c->phidf, 0, (c->V > 1 ? c->V * c->vs : (int64_t)L0.size) * sizeof(dfv), c->stream);
+  if (!mixed || kout == 0) reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 11);
+  refine_finish(c, phi, c->V > 1 ? c->hl_out : nullptr);
   return cudaGetLastError();
 }
 
@@ -2041,20 +2290,36 @@ static void destroy_plan(Solver* c) {
   c->solve_graph_kernels = 0;
 }
 
-// capture solve_fixed into a graph on the library's private stream
-static cudaError_t build_plan(Solver* c) {
-  destroy_plan(c);
+static void destroy_plan2(Solver* c) {
+  if (c->solve2_exec) cudaGraphExecDestroy(c->solve2_exec);
+  c->solve2_exec = nullptr;
+  c->solve2_graph_kernels = 0;
+}
+
+// capture solve_fixed into a graph on the library's private stream: one
+// right-hand side from c->in64 into c->out64, or (paired) the two at
+// c->plan2_b into c->plan2_phi
+static cudaError_t build_plan(Solver* c, bool paired = false) {
+  if (paired) destroy_plan2(c);
+  else destroy_plan(c);
+  cudaGraphExec_t* exec = paired ? &c->solve2_exec : &c->solve_exec;
+  int* kernels = paired ? &c->solve2_graph_kernels : &c->solve_graph_kernels;
   cudaStream_t user = c->stream;
   const bool unc = t_uncounted;
   t_uncounted = true;   // captured launches run (and count) when the graph is replayed
   c->stream = c->cap_stream;
+  if (paired) {
+    c->V = 2;
+    c->vs = (int64_t)c->mg.lv[0].size;
+  }
   cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t e1 = solve_fixed(c);
+    cudaError_t e1 = paired ? solve_fixed(c, c->plan2_b, c->plan2_phi, c->plan2_kout)
+                            : solve_fixed(c, c->in64, c->out64, c->plan_kout);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(c->cap_stream, &g);
     if (e == cudaSuccess) e = e1;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->solve_exec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
     if (g) {
       size_t nn = 0;
       cudaGraphGetNodes(g, nullptr, &nn);
@@ -2065,15 +2330,18 @@ static cudaError_t build_plan(Solver* c) {
         cudaGraphNodeType t;
         if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kn;
       }
-      c->solve_graph_kernels = kn;
+      *kernels = kn;
       cudaGraphDestroy(g);
     }
   }
+  c->V = 1;
+  c->vs = 0;
   c->stream = user;
   t_uncounted = unc;
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
-    destroy_plan(c);
+    if (paired) destroy_plan2(c);
+    else destroy_plan(c);
   }
   return e;
 }
@@ -2144,8 +2412,64 @@ cudaError_t mesh_solve(Solver* c, const double* b, double* phi) {
   return mesh_solve_end(c);
 }
 
+bool mesh_solve_paired(const Solver* c) { return c->nv == 2 && c->mg.fdm.BpF != nullptr; }
+
+cudaError_t mesh_solve_begin2(Solver* c, const double* b, double* phi) {
+  if (!mesh_solve_paired(c)) return cudaErrorInvalidValue;
+  cudaError_t e = ensure_solver_buffers(c);
+  if (e != cudaSuccess) return e;
+  c->pending2 = false;
+  const size_t n = c->mg.lv[0].size;
+  if (!c->solve2_exec || c->plan2_b != b || c->plan2_phi != phi) {
+    // calibrate: each right-hand side by the host-checked solve, then capture the pair
+    int kin0 = 0, kin1 = 0;
+    e = solve_checked(c, b, phi, &c->iters, &c->relres, &c->refine_steps, &kin0);
+    if (e != cudaSuccess) return e;
+    e = solve_checked(c, b + n, phi + n, &c->iters2, &c->relres2, &c->refine_steps2, &kin1);
+    if (e != cudaSuccess) return e;
+    if (c->relres > solver_rtol(c) || c->relres2 > solver_rtol(c)) return cudaSuccess;
+    c->plan_kin = std::max(c->plan_kin, std::max(kin0, kin1));
+    c->plan2_kout = std::max(c->plan2_kout, std::max(c->refine_steps, c->refine_steps2));
+    c->plan2_b = b;
+    c->plan2_phi = phi;
+    if (!c->cap_stream && (e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return e;
+    if (build_plan(c, true) != cudaSuccess) (void)cudaGetLastError();   // calibrate again next time
+    return cudaSuccess;
+  }
+  cudaStream_t s = c->stream;
+  if ((e = cudaGraphLaunch(c->solve2_exec, s)) != cudaSuccess) return e;
+  count_launches((unsigned long long)c->solve2_graph_kernels);
+  cudaMemcpyAsync(c->host_res, c->scal + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(c->host_res + 2, c->scal + 64 + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  c->pending2 = true;
+  return cudaGetLastError();
+}
+
+bool mesh_solve_check2(Solver* c) {
+  if (!c->pending2) return true;
+  c->pending2 = false;
+  double rel[2];
+  for (int v = 0; v < 2; ++v) {
+    const double bb = c->host_res[2 * v], rr = c->host_res[2 * v + 1];
+    rel[v] = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  }
+  if (rel[0] <= solver_rtol(c) && rel[1] <= solver_rtol(c)) {
+    c->relres = rel[0];
+    c->relres2 = rel[1];
+    c->iters = c->iters2 = std::max(1, c->plan_kin) * c->plan2_kout;
+    c->refine_steps = c->refine_steps2 = c->plan2_kout;
+    return true;
+  }
+  // a right-hand side needs more sweeps: one more from now on, calibrated on the next call
+  ++c->plan2_kout;
+  destroy_plan2(c);
+  return false;
+}
+
 static void solver_plan_free(Solver* c) {
   destroy_plan(c);
+  destroy_plan2(c);
   if (c->in64) cudaFree(c->in64);
   if (c->out64) cudaFree(c->out64);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -2229,10 +2553,11 @@ void fdm_free(FineFDM& f) {
 
 // x = K^+ b by the six transform passes (tensor cores when the pieces are
 // set, else the CUDA-core passes); w1, w2: N^3 scratch
-cudaError_t fdm_apply(const FineFDM& f, const float* b, float* x, float* w1, float* w2, cudaStream_t s) {
+cudaError_t fdm_apply(const FineFDM& f, const float* b, float* x, float* w1, float* w2, cudaStream_t s, int V,
+                      int64_t vs) {
   const int N = f.N;
   if (f.BpF) {
-    const dim3 g((unsigned)(((int64_t)N * N + 127) / 128 * f.ntile));
+    const dim3 g((unsigned)(((int64_t)N * N + 127) / 128 * f.ntile), (unsigned)V);
     const size_t sm = tc_rows_smem(f.nt);
     const uint4* F = (const uint4*)f.BpF;
     const uint4* I = (const uint4*)f.BpI;
@@ -2241,14 +2566,15 @@ cudaError_t fdm_apply(const FineFDM& f, const float* b, float* x, float* w1, flo
     const int nm = f.null_mode, nt = f.nt;
     auto k0 = k_tc_rows<false>;
     auto k1 = k_tc_rows<true>;
-    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, b, F, lm, nm, N, w1, f.err);
-    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w1, F, lm, nm, N, w2, f.err);
-    launch_pdl(k1, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w2, F, lm, nm, N, w1, f.err);
-    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w1, I, lm, nm, N, w2, f.err);
-    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w2, I, lm, nm, N, w1, f.err);
-    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w1, I, lm, nm, N, x, f.err);
+    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, b, F, lm, nm, N, w1, f.err, vs);
+    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w1, F, lm, nm, N, w2, f.err, vs);
+    launch_pdl(k1, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w2, F, lm, nm, N, w1, f.err, vs);
+    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w1, I, lm, nm, N, w2, f.err, vs);
+    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w2, I, lm, nm, N, w1, f.err, vs);
+    launch_pdl(k0, g, FT_THREADS, sm, s, R, N, 0, N, nt, (const float*)w1, I, lm, nm, N, x, f.err, vs);
     return cudaGetLastError();
   }
+  if (V != 1) return cudaErrorInvalidValue;   // one vector on the CUDA-core passes
   const dim3 g((unsigned)(((int64_t)N * N + FM - 1) / FM), (unsigned)((N + FN - 1) / FN));
   launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, b, f.V32, f.lam32, f.null_mode, w1);
   launch_pdl(k_fdm_axis<false>, g, 256, 0, s, N, (const float*)w1, f.V32, f.lam32, f.null_mode, w2);
@@ -2259,29 +2585,32 @@ cudaError_t fdm_apply(const FineFDM& f, const float* b, float* x, float* w1, flo
   return cudaGetLastError();
 }
 
-cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream) {
+cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream, int nv) {
   s->cfg = c->cfg;
   s->n = c->n;
   s->precision = c->precision;
   s->st = c->st;
   s->stream = stream;
+  s->nv = nv = std::max(1, std::min(2, nv));
   const size_t nodes = (size_t)27 * c->n * c->n * c->n;
   cudaError_t e;
-  if ((e = cudaMalloc(&s->scal, 64 * sizeof(double))) != cudaSuccess) return e;
-  // reduction partials: one per block of k_reduce (<= 608) or of a fine-level apply with a fused dot
+  // per right-hand side: a block of 64 scalars, the reduction partials (one per block of
+  // k_reduce (<= 608), two per block of k_ref_split_sums, one per block of a fine-level apply
+  // with a fused dot), a counter, res64 and phidf
+  if ((e = cudaMalloc(&s->scal, nv * 64 * sizeof(double))) != cudaSuccess) return e;
   {
     const int N0 = 3 * c->n;
     const dim3 g = apply_grid(N0, apply_steps(N0));
-    const size_t nb = std::max<size_t>(1024, (size_t)g.x * g.y * g.z);
-    if ((e = cudaMalloc(&s->red_tmp, nb * sizeof(double))) != cudaSuccess) return e;
+    const size_t nb = std::max<size_t>(2 * 608, (size_t)g.x * g.y * g.z);
+    if ((e = cudaMalloc(&s->red_tmp, nv * nb * sizeof(double))) != cudaSuccess) return e;
   }
-  if ((e = cudaMalloc(&s->red_counter, sizeof(unsigned int))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&s->res64, nodes * sizeof(double))) != cudaSuccess) return e;
-  if (s->precision == FEP3M_MIXED && (e = cudaMalloc(&s->phidf, nodes * sizeof(dfv))) != cudaSuccess) return e;
-  if ((e = cudaMallocHost(&s->host_res, 2 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&s->red_counter, nv * sizeof(unsigned int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&s->res64, nv * nodes * sizeof(double))) != cudaSuccess) return e;
+  if (s->precision == FEP3M_MIXED && (e = cudaMalloc(&s->phidf, nv * nodes * sizeof(dfv))) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&s->host_res, 4 * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaEventCreate(&s->ev_in0)) != cudaSuccess || (e = cudaEventCreate(&s->ev_in1)) != cudaSuccess) return e;
-  cudaMemset(s->red_counter, 0, sizeof(unsigned int));
-  cudaMemset(s->scal, 0, 64 * sizeof(double));
+  cudaMemset(s->red_counter, 0, nv * sizeof(unsigned int));
+  cudaMemset(s->scal, 0, nv * 64 * sizeof(double));
   if ((e = apply_set_smem()) != cudaSuccess) return e;
   return mg_setup(s);
 }

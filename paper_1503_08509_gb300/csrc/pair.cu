@@ -1598,7 +1598,7 @@ template <class T, bool GRAD, bool TC>
 static cudaError_t launch_pair_screen(fep3m_ctx* c, cudaStream_t s, bool half) {
   const size_t smem = Pair3Smem<T, TC>::bytes(c->n_sr);
   auto kern = k_pair_screen<T, GRAD, TC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_limit((const void*)kern, smem);
   if (e != cudaSuccess) return e;
   FEP3M_CL kern<<<(unsigned)pair_bricks(c), TC ? PTC : PT, smem, s>>>(
       c->n, c->n_sr, (T)c->h, c->start, c->count, (const typename vec4<T>::type*)c->part, (const T*)c->Cv,
@@ -1792,7 +1792,7 @@ static void launch_adj_vertex(fep3m_ctx* c, int z0, int z1, const T* D, double* 
   const int64_t ne = (int64_t)c->n * c->n * c->n;
   const bool df = sizeof(T) == 4;
   const size_t smem = (size_t)AV_WARPS * 27 * 32 * 8;   // dfacc and double: 8 bytes
-  cudaFuncSetAttribute(k_adj_vertex<T, NSR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  (void)smem_limit((const void*)k_adj_vertex<T, NSR>, smem);   // a failure shows as the launch's error
   FEP3M_CL k_adj_vertex<T, NSR><<<(unsigned)((ne + 31) / 32), 32 * AV_WARPS, smem, s>>>(
       c->n, z0, z1, z0 == 0, c->count, D, df ? (const float2*)c->H0df : nullptr, df ? (const float2*)c->Wsum : nullptr,
       A);
@@ -1807,16 +1807,17 @@ static cudaError_t screen_adjoint(fep3m_ctx* c, const T* W, const double* Hw, do
   const int noff = c->noff, plane = noff * noff;
   // bytes of D held at once: a quarter of the device's memory (at least 2 GiB), so that on a
   // large GPU even the 256^3 mesh takes D in one piece (each further piece re-reads and
-  // re-writes A and launches the gather again)
-  size_t budget = (size_t)1 << 31;
-  {
+  // re-writes A and launches the gather again); sized at the context's first sweep
+  if (c->adj_planes == 0) {
+    size_t budget = (size_t)1 << 31;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) budget = std::max(budget, std::min(total_b / 4, free_b / 2));
     else (void)cudaGetLastError();
+    c->adj_planes = (int)std::min<int64_t>(noff, std::max<int64_t>(1, (int64_t)(budget / ((size_t)ne * sizeof(T) * plane))));
   }
   // tensor cores (FP32 path, table pieces prepared): column tiles of ADJ_NT offsets
   const bool tcore = sizeof(T) == 4 && c->HbA != nullptr;
-  const int planes = (int)std::min<int64_t>(noff, std::max<int64_t>(1, (int64_t)(budget / ((size_t)ne * sizeof(T) * plane))));
+  const int planes = c->adj_planes;
   const size_t need = (size_t)planes * plane * ne * sizeof(T);
   if (c->D_bytes < need) {
     if (c->D_adj) cudaFree(c->D_adj);

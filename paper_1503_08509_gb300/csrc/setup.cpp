@@ -6,12 +6,29 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <random>
 #include <vector>
 
 #include "common.cuh"
 
 namespace fep3m {
+
+cudaError_t smem_limit(const void* kern, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> set;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = set[{dev, kern}];
+  if (have >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
 
 // n-point Gauss-Legendre rule on [0, 1] by Newton iteration on P_n.
 void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
