@@ -60,6 +60,19 @@ __global__ void k_to_double(int64_t n, const A* in, double* out, double a) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) out[i] = (double)in[i] * a;
 }
+// the mixed periodic solver's float pairs (h, l) to FP64: out = (h + l) a
+__global__ void k_pairs_to_double(int64_t n, const float2* __restrict__ in, double* __restrict__ out, double a) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = ((double)in[i].x + (double)in[i].y) * a;
+}
+// FP64 to float pairs: h = fl32(v), l = fl32(v - h)
+__global__ void k_double_to_pairs(int64_t n, const double* __restrict__ in, float2* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = in[i];
+  const float h = (float)v;
+  out[i] = make_float2(h, (float)(v - (double)h));
+}
 // flag (1) when any of the n values is not finite
 __global__ void k_check_finite(int64_t n, const double* __restrict__ v, int* __restrict__ flag) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -245,8 +258,7 @@ int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev)
     if (paired) CK(cudaStreamWaitEvent(c->aux_stream, c->ev_solved, 0));
     else CK(mesh_solve_begin(A, c->g64, c->lam64));
   }
-  // the replayed paired solve wrote the pair kernels' copy of the potential itself
-  if (!(paired && F->pending2)) CK(pair_prepare(c));
+  CK(pair_prepare(c));
   ev_record(c, 2);
   CK(cudaStreamWaitEvent(c->stream, c->ev_pjoin, 0));
   ev_record(c, 10);
@@ -578,7 +590,6 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
     // fast diagonalisation); the second solver serves the multigrid path and fep3m_vjp
     const bool pairable = !(cfg->flags & (FEP3M_MULTIGRID | FEP3M_CUDA_CORES));
     if ((e = solver_init(&c->solv[0], c, c->stream, pairable ? 2 : 1)) != cudaSuccess) return fail(from_cuda(e));
-    c->solv[0].hl_out = (float2*)c->phi_hl;   // MIXED: the paired solve also writes the pair kernels' copy
     if ((e = solver_init(&c->solv[1], c, c->aux_stream)) != cudaSuccess) return fail(from_cuda(e));
     c->stats.mg_levels = (int)c->solv[0].mg.lv.size();
   }
@@ -827,12 +838,18 @@ int fep3m_get_mesh(const fep3m_ctx* cc, double* C, double* b, double* phi_mesh) 
     int s = deliver(c, C, c->res64, 8 * ne * 8);
     if (s != FEP3M_OK) return s;
   }
+  // MIXED: the mesh vectors are float pairs (the mixed solver's format)
+  const bool pairs = c->precision == FEP3M_MIXED;
   if (b) {
-    int s = deliver(c, b, c->b64, nodes * 8);
+    if (pairs) FEP3M_CL k_pairs_to_double<<<gsz(nodes), PT, 0, c->stream>>>(nodes, (const float2*)c->b64, c->res64, 1.0);
+    int s = deliver(c, b, pairs ? c->res64 : c->b64, nodes * 8);
     if (s != FEP3M_OK) return s;
   }
   if (phi_mesh) {
-    FEP3M_CL k_to_double<double><<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->phi64, c->res64, c->inv_h);
+    if (pairs)
+      FEP3M_CL k_pairs_to_double<<<gsz(nodes), PT, 0, c->stream>>>(nodes, (const float2*)c->phi64, c->res64, c->inv_h);
+    else
+      FEP3M_CL k_to_double<double><<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->phi64, c->res64, c->inv_h);
     int s = deliver(c, phi_mesh, c->res64, nodes * 8);
     if (s != FEP3M_OK) return s;
   }
@@ -874,13 +891,19 @@ int fep3m_solve_mesh(fep3m_ctx* c, const double* b, double* phi) {
     return st;
   }
   const int64_t nodes = (int64_t)27 * c->n * c->n * c->n;
-  CK(cudaMemcpyAsync(c->g64, b, nodes * 8, is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                     c->stream));
+  // MIXED: the solver takes and returns float pairs (staged through res64)
+  const bool pairs = c->precision == FEP3M_MIXED;
+  CK(cudaMemcpyAsync(pairs ? c->res64 : c->g64, b, nodes * 8,
+                     is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  if (pairs) FEP3M_CL k_double_to_pairs<<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->res64, (float2*)c->g64);
   c->solv[0].stream = c->stream;
   CK(mesh_solve(&c->solv[0], c->g64, c->lam64));
   solve_stats(c);
   const double rel = c->solv[0].relres;
-  FEP3M_CL k_to_double<double><<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->lam64, c->res64, c->inv_h);
+  if (pairs)
+    FEP3M_CL k_pairs_to_double<<<gsz(nodes), PT, 0, c->stream>>>(nodes, (const float2*)c->lam64, c->res64, c->inv_h);
+  else
+    FEP3M_CL k_to_double<double><<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->lam64, c->res64, c->inv_h);
   int s = deliver(c, phi, c->res64, nodes * 8);
   if (s != FEP3M_OK) return s;
   CK(cudaStreamSynchronize(c->stream));

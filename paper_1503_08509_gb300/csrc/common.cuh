@@ -175,7 +175,6 @@ struct Solver {
   int solve2_graph_kernels = 0;
   const double* plan2_b = nullptr;
   double* plan2_phi = nullptr;
-  float2* hl_out = nullptr;        // MIXED: the paired solve also writes its first solution as hi + lo floats
   bool pending2 = false;
   int iters2 = 0, refine_steps2 = 0;   // the second right-hand side's counts and residual
   double relres2 = 0;
@@ -299,13 +298,15 @@ struct fep3m_ctx {
   void* rv = nullptr;            // n^3 vertex density (T)
   void* Cv = nullptr;            // n^3 * 8 (T): C regrouped by vertex, Cv[v][k] = C[v - k][k]
   // fine-level FP64 vectors
+  // the periodic mesh vectors hold FP64 values, or in MIXED float pairs h + l
+  // (the mixed solver's format, 8 bytes a node as well); a box's are FP64
   double* b64 = nullptr;         // (3n)^3 load vector
   double* phi64 = nullptr;       // (3n)^3 mesh potential, reference units
   double* res64 = nullptr;       // refinement residual
   double* g64 = nullptr;         // adjoint right-hand side (b64 + nodes: one allocation)
   double* lam64 = nullptr;       // adjoint mesh solution (phi64 + nodes)
   double* scal = nullptr;        // device scalars (dots, norms, flags), 64 doubles
-  void* phi_hl = nullptr;        // MIXED: mesh potential as hi + lo floats, (3n)^3 float2
+  void* phi_hl = nullptr;        // MIXED box: the FP64 mesh potential as hi + lo floats, (3n)^3 float2
   int* iflags = nullptr;         // device int flags: [0] input error, [1] converged, ...
   void* lam_T = nullptr;
   // per-particle outputs, sorted order
@@ -391,9 +392,11 @@ cudaError_t fdm_apply(const FineFDM& f, const float* b, float* x, float* w1, flo
 void fdm_free(FineFDM& f);
 void solver_destroy(Solver* s);
 size_t scan_tmp_bytes(int64_t n);
-// mu = 4 pi (Mpq^T)^(x)3 lam on the vertex grid (working precision); work1/2 sized n*(3n)^2
+// mu = 4 pi (Mpq^T)^(x)3 lam on the vertex grid (FP64; lam in the solver's
+// format); work1/2 sized n*(3n)^2
 cudaError_t vertex_adjoint(fep3m_ctx* c, const double* lam, void* mu, void* work1, void* work2, cudaStream_t s);
-// solve K phi = b (FP64 in/out, reference units) on the solver's stream; begin
+// solve K phi = b (reference units; FP64 in and out, in MIXED float pairs h + l
+// in the same 8-byte slots) on the solver's stream; begin
 // may return before the solve has finished (a replayed graph), end waits for
 // it, checks the residual and re-solves if needed.  Results in s->iters etc.
 cudaError_t mesh_solve_begin(Solver* s, const double* b, double* phi);

@@ -32,6 +32,9 @@
 namespace fep3m {
 
 __constant__ double cM64[3][7], cK64[3][7], cP64[6][4], cMpq64[4][2], cDM64[3], cDK64[3];
+// the mixed mass times 120 (exact integers: the element entries are 13/120,
+// 1/60, 3/10 and 3/40), for the FP32 and double-float passes
+__constant__ float cMpq120[4][2];
 __constant__ float cM32[3][7], cK32[3][7], cP32[6][4], cDM32[3], cDK32[3];
 // inverse diagonal of K by node types, index x + 3 y + 9 z
 __constant__ double cDinv64[27];
@@ -146,18 +149,21 @@ __global__ void k_vertex_density(int n, const T* __restrict__ C, T* __restrict__
 // each charge's own smooth potential against its screen and bias U); the
 // last pass divides by 120^3 in FP64.
 template <class T>
+__device__ __forceinline__ T mpq_w(int t, int j) {
+  if constexpr (sizeof(T) == 4) return cMpq120[t][j];
+  else return cMpq64[t][j];
+}
+template <class T>
 __device__ __forceinline__ int mpq_row(int g, int n, int vtx[3], T wgt[3]) {
-  const double s = sizeof(T) == 4 ? 120.0 : 1.0;
-  auto wq = [s](double v) -> T { return sizeof(T) == 4 ? (T)rint(s * v) : (T)v; };
   const int e = g / 3, t = g - 3 * e;
   if (t == 0) {
-    vtx[0] = wrapi(e - 1, n); wgt[0] = wq(cMpq64[3][0]);
-    vtx[1] = e;               wgt[1] = wq(cMpq64[0][0] + cMpq64[3][1]);
-    vtx[2] = wrapi(e + 1, n); wgt[2] = wq(cMpq64[0][1]);
+    vtx[0] = wrapi(e - 1, n); wgt[0] = mpq_w<T>(3, 0);
+    vtx[1] = e;               wgt[1] = mpq_w<T>(0, 0) + mpq_w<T>(3, 1);
+    vtx[2] = wrapi(e + 1, n); wgt[2] = mpq_w<T>(0, 1);
     return 3;
   }
-  vtx[0] = e;               wgt[0] = wq(cMpq64[t][0]);
-  vtx[1] = wrapi(e + 1, n); wgt[1] = wq(cMpq64[t][1]);
+  vtx[0] = e;               wgt[0] = mpq_w<T>(t, 0);
+  vtx[1] = wrapi(e + 1, n); wgt[1] = mpq_w<T>(t, 1);
   return 2;
 }
 
@@ -165,13 +171,16 @@ __device__ __forceinline__ int mpq_row(int g, int n, int vtx[3], T wgt[3]) {
 // then z): out[.., g, ..] = scale sum_k w_k in[.., v_k, ..], vertices v_k of
 // order-3 node g along `axis` (mpq_row; FP32: integer weights, the caller's
 // scale divides by 120^3 at the last pass).  d[3]: the output's extents (3n
-// along the axes done, n along the others).
+// along the axes done, n along the others; their product < 2^32).  The scale:
+// s64 for an FP64 output, s32 for FP32, the pair s32 + s32lo for float pairs
+// (dfv: the FP32 sum times the scale as a two-product).
 template <class Tin, class Tout>
 __global__ void k_load_axis(int n, int axis, int d0, int d1, int d2, const Tin* __restrict__ in,
-                            Tout* __restrict__ out, double scale) {
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= (int64_t)d0 * d1 * d2) return;
-  int idx[3] = {(int)(g % d0), (int)((g / d0) % d1), (int)(g / ((int64_t)d0 * d1))};
+                            Tout* __restrict__ out, double s64, float s32, float s32lo) {
+  const unsigned g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (unsigned)d0 * (unsigned)d1 * (unsigned)d2) return;
+  const unsigned q = g / (unsigned)d0;
+  int idx[3] = {(int)(g - q * (unsigned)d0), (int)(q % (unsigned)d1), (int)(q / (unsigned)d1)};
   int din[3] = {d0, d1, d2};
   din[axis] = n;
   const int64_t st[3] = {1, din[0], (int64_t)din[0] * din[1]};
@@ -182,7 +191,14 @@ __global__ void k_load_axis(int n, int axis, int d0, int d1, int d2, const Tin* 
   const int64_t base = idx[0] * st[0] + idx[1] * st[1] + idx[2] * st[2];
   Tin acc = Tin(0);
   for (int j = 0; j < k; ++j) acc += w[j] * in[base + vtx[j] * st[axis]];
-  out[g] = (Tout)(scale * (double)acc);
+  if constexpr (std::is_same<Tout, dfv>::value) {
+    const float p = acc * s32;
+    out[g] = {p, fmaf(acc, s32lo, fmaf(acc, s32, -p))};
+  } else if constexpr (std::is_same<Tout, float>::value) {
+    out[g] = acc * s32;
+  } else {
+    out[g] = (Tout)(s64 * (double)acc);
+  }
 }
 
 // Coarsest-level exact solve x = V (Dinv o (V^T b)) (V the 1-D generalized
@@ -1418,11 +1434,11 @@ __global__ void k_df_update(int64_t n, dfv* __restrict__ phi, const float* __res
 }
 
 // ---- double-float refinement bookkeeping (MIXED).  FP64 arithmetic runs at a
-// small fraction of the FP32 rate on this GPU, so the sums, the projection and
-// the scaling work on float pairs; FP64 is used only to split the FP64
-// right-hand side and to form the FP64 result.  Several right-hand sides:
-// vector blockIdx.y at a stride of vs values, scalars in its block of 64,
-// partials and counter per vector.
+// small fraction of the FP32 rate on this GPU, so in MIXED the solver takes its
+// right-hand sides and returns its solutions as float pairs (h + l, 8 bytes a
+// node like FP64), and the sums, the projection and the scaling work on float
+// pairs.  Several right-hand sides: vector blockIdx.y at a stride of vs values,
+// scalars in its block of 64, partials and counter per vector.
 
 // a normalised pair: |l| <= half an ulp of h
 __device__ __forceinline__ dfv df_norm(dfv a) {
@@ -1492,16 +1508,14 @@ __device__ bool block_sum2_finish(double a, double b, unsigned bid, unsigned nbl
   return true;
 }
 
-// setup, first pass: bdf = b as float pairs, sum b into scal[5] with the mean
-// m = sum b / W derived, sum b^2 into scal[7] with the scale s = 2^-k, 2^k near
-// the RMS sqrt(sum b^2 / n), derived (the POST_MEAN and POST_SCALE forms)
-__global__ void k_ref_split_sums(int64_t n, const double* __restrict__ b, dfv* __restrict__ bdf,
-                                 double* __restrict__ partials, unsigned int* __restrict__ counter,
-                                 double* __restrict__ scal, double invW, int64_t vs) {
+// setup, first pass: sum b into scal[5] with the mean m = sum b / W derived,
+// sum b^2 into scal[7] with the scale s = 2^-k, 2^k near the RMS
+// sqrt(sum b^2 / n), derived (the POST_MEAN and POST_SCALE forms)
+__global__ void k_ref_sums(int64_t n, const dfv* __restrict__ b, double* __restrict__ partials,
+                           unsigned int* __restrict__ counter, double* __restrict__ scal, double invW, int64_t vs) {
   PDL_PROLOGUE
   const int vi = blockIdx.y;
   b += vi * vs;
-  bdf += vi * vs;
   partials += 2 * (size_t)vi * gridDim.x;
   counter += vi;
   scal += 64 * vi;
@@ -1509,12 +1523,9 @@ __global__ void k_ref_split_sums(int64_t n, const double* __restrict__ b, dfv* _
   dfv sum = {0.f, 0.f};
   float sq = 0.f;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
-    const double v = b[g];
-    const float h = (float)v;
-    const dfv x = {h, (float)(v - (double)h)};
-    bdf[g] = x;
+    const dfv x = b[g];
     sum += x;
-    sq = fmaf(h, h, sq);
+    sq = fmaf(x.h, x.h, sq);
   }
   double ta, tb;
   if (block_sum2_finish((double)sum.h + (double)sum.l, (double)sq, blockIdx.x, gridDim.x, partials, counter, ta, tb)) {
@@ -1534,14 +1545,15 @@ __global__ void k_ref_split_sums(int64_t n, const double* __restrict__ b, dfv* _
   }
 }
 
-// setup, second pass: Pi b = b - m w3 in place (float pairs), r = s Pi b in
-// FP32 and |r|^2 into scal[10]; whole rows per warp (the node weights from
-// the row and the column)
-__global__ void k_ref_project_scale(int N, dfv* __restrict__ bdf, float* __restrict__ r,
+// setup, second pass: bdf = Pi b = b - m w3 (float pairs), r = s Pi b in FP32
+// and |r|^2 into scal[10]; whole rows per warp (the node weights from the row
+// and the column)
+__global__ void k_ref_project_scale(int N, const dfv* __restrict__ b, dfv* __restrict__ bdf, float* __restrict__ r,
                                     double* __restrict__ partials, unsigned int* __restrict__ counter,
                                     double* __restrict__ scal, int64_t vs) {
   PDL_PROLOGUE
   const int vi = blockIdx.y;
+  b += vi * vs;
   bdf += vi * vs;
   r += vi * vs;
   partials += (size_t)vi * gridDim.x;
@@ -1557,11 +1569,12 @@ __global__ void k_ref_project_scale(int N, dfv* __restrict__ bdf, float* __restr
   for (int64_t row = warp; row < rows; row += nwarps) {
     const int iz = (int)(row / N), iy = (int)(row - (int64_t)iz * N);
     const float wyz = (iy % 3 ? 0.375f : 0.25f) * (iz % 3 ? 0.375f : 0.25f);
+    const dfv* bi = b + row * N;
     dfv* br = bdf + row * N;
     float* rr = r + row * N;
     for (int ix = lane; ix < N; ix += 32) {
       const dfv mw = df_scaled(mh, ml, wyz * (ix % 3 ? 0.375f : 0.25f));
-      dfv v = br[ix];
+      dfv v = bi[ix];
       v += dfv{-mw.h, -mw.l};
       v = df_norm(v);
       br[ix] = v;
@@ -1602,10 +1615,10 @@ __global__ void k_ref_wsum(int N, const dfv* __restrict__ v, double* __restrict_
   block_sum_finish(acc, blockIdx.x, gridDim.x, partials, counter, scal + 6, POST_MEAN, invW, scal);
 }
 
-// finish, second pass: phi = v - m in FP64 (m the mean just derived) and, for
-// vector 0 when hl is set, the same value as hi + lo floats
-__global__ void k_ref_out(int64_t n, const dfv* __restrict__ v, double* __restrict__ phi, float2* __restrict__ hl,
-                          const double* __restrict__ scal, int64_t vs) {
+// finish, second pass: phi = v - m as normalised float pairs (m the mean just
+// derived)
+__global__ void k_ref_out(int64_t n, const dfv* __restrict__ v, dfv* __restrict__ phi, const double* __restrict__ scal,
+                          int64_t vs) {
   PDL_PROLOGUE
   const int vi = blockIdx.y;
   v += vi * vs;
@@ -1617,9 +1630,7 @@ __global__ void k_ref_out(int64_t n, const dfv* __restrict__ v, double* __restri
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
     dfv y = v[g];
     y += dfv{-mh, -ml};
-    y = df_norm(y);
-    phi[g] = (double)y.h + (double)y.l;
-    if (hl && vi == 0) hl[g] = make_float2(y.h, y.l);
+    phi[g] = df_norm(y);
   }
 }
 
@@ -1946,6 +1957,10 @@ static void upload_constants(const Stencils& st) {
   cudaMemcpyToSymbol(cK64, st.K, sizeof(st.K));
   cudaMemcpyToSymbol(cP64, st.P, sizeof(st.P));
   cudaMemcpyToSymbol(cMpq64, st.Mpq, sizeof(st.Mpq));
+  float Mpq120[4][2];
+  for (int t = 0; t < 4; ++t)
+    for (int j = 0; j < 2; ++j) Mpq120[t][j] = (float)std::rint(120.0 * st.Mpq[t][j]);
+  cudaMemcpyToSymbol(cMpq120, Mpq120, sizeof(Mpq120));
   cudaMemcpyToSymbol(cDM64, st.diagM, sizeof(st.diagM));
   cudaMemcpyToSymbol(cDK64, st.diagK, sizeof(st.diagK));
   cudaMemcpyToSymbol(cM32, M32, sizeof(M32));
@@ -2144,10 +2159,11 @@ static void refine_setup(Solver* c, const double* b, double* phi64, float* r) {
   cudaStream_t s = c->stream;
   double* sc = c->scal;
   if (c->precision != FEP3M_FP64) {
+    // b as float pairs
     const dim3 gr((unsigned)reduce_blocks(n), (unsigned)c->V);
-    launch_pdl(k_ref_split_sums, gr, TPB, 0, s, (int64_t)n, b, reinterpret_cast<dfv*>(c->res64), (double*)c->red_tmp,
-               c->red_counter, sc, 1.0 / W, c->vs);
-    launch_pdl(k_ref_project_scale, gr, TPB, 0, s, N, reinterpret_cast<dfv*>(c->res64), r, (double*)c->red_tmp,
+    const dfv* bd = reinterpret_cast<const dfv*>(b);
+    launch_pdl(k_ref_sums, gr, TPB, 0, s, (int64_t)n, bd, (double*)c->red_tmp, c->red_counter, sc, 1.0 / W, c->vs);
+    launch_pdl(k_ref_project_scale, gr, TPB, 0, s, N, bd, reinterpret_cast<dfv*>(c->res64), r, (double*)c->red_tmp,
                c->red_counter, sc, c->vs);
     return;
   }
@@ -2175,8 +2191,8 @@ static void refine_update(Solver* c, double* phi64, const float* e, bool first) 
                first ? 1 : 0);
 }
 
-// end: phi in FP64 with mean zero (MIXED with hl: vector 0 also as hi + lo floats)
-static void refine_finish(Solver* c, double* phi, float2* hl = nullptr) {
+// end: phi with mean zero (FP64; MIXED: float pairs)
+static void refine_finish(Solver* c, double* phi) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
   const size_t n = L0.size;
@@ -2185,8 +2201,8 @@ static void refine_finish(Solver* c, double* phi, float2* hl = nullptr) {
     const dfv* v = reinterpret_cast<const dfv*>(c->phidf);
     launch_pdl(k_ref_wsum, dim3((unsigned)reduce_blocks(n), (unsigned)c->V), TPB, 0, c->stream, N, v,
                (double*)c->red_tmp, c->red_counter, c->scal, 1.0 / W, c->vs);
-    launch_pdl(k_ref_out, dim3((unsigned)grid_for(n), (unsigned)c->V), TPB, 0, c->stream, (int64_t)n, v, phi, hl,
-               (const double*)c->scal, c->vs);
+    launch_pdl(k_ref_out, dim3((unsigned)grid_for(n), (unsigned)c->V), TPB, 0, c->stream, (int64_t)n, v,
+               reinterpret_cast<dfv*>(phi), (const double*)c->scal, c->vs);
     return;
   }
   reduce<double>(c, N, RD_WSUM, phi, nullptr, c->scal + 6, POST_MEAN, 1.0 / W);
@@ -2280,7 +2296,7 @@ static cudaError_t solve_fixed(Solver* c, const double* b, double* phi, int kout
   if (mixed && kout == 0)
     cudaMemsetAsync(c->phidf, 0, (c->V > 1 ? c->V * c->vs : (int64_t)L0.size) * sizeof(dfv), c->stream);
   if (!mixed || kout == 0) reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 11);
-  refine_finish(c, phi, c->V > 1 ? c->hl_out : nullptr);
+  refine_finish(c, phi);
   return cudaGetLastError();
 }
 
@@ -2659,19 +2675,27 @@ cudaError_t assemble_forward(fep3m_ctx* c) {
   const Level& L0 = c->solv[0].mg.lv[0];
   const int N3 = 3 * n;
   if (c->precision == FEP3M_MIXED) {
+    // b as float pairs (the mixed solver's right-hand side): the FP32 sums of the
+    // integer-weighted passes times 4 pi / 120^3 as a two-product
+    const double sc = 4.0 * M_PI / (120.0 * 120.0 * 120.0);
+    const float sh = (float)sc, sl = (float)(sc - (double)sh);
     float *t1 = (float*)L0.t1, *t2 = (float*)L0.t2;
     FEP3M_CL k_load_axis<float, float><<<grid_for((int64_t)N3 * n * n), TPB, 0, s>>>(n, 0, N3, n, n, (const float*)c->rv,
-                                                                                    t1, 1.0);
-    FEP3M_CL k_load_axis<float, float><<<grid_for((int64_t)N3 * N3 * n), TPB, 0, s>>>(n, 1, N3, N3, n, t1, t2, 1.0);
-    FEP3M_CL k_load_axis<float, double><<<grid_for((int64_t)N3 * N3 * N3), TPB, 0, s>>>(
-        n, 2, N3, N3, N3, t2, c->b64, 4.0 * M_PI / (120.0 * 120.0 * 120.0));
+                                                                                    t1, 1.0, 1.0f, 0.0f);
+    FEP3M_CL k_load_axis<float, float><<<grid_for((int64_t)N3 * N3 * n), TPB, 0, s>>>(n, 1, N3, N3, n, t1, t2, 1.0,
+                                                                                     1.0f, 0.0f);
+    FEP3M_CL k_load_axis<float, dfv><<<grid_for((int64_t)N3 * N3 * N3), TPB, 0, s>>>(n, 2, N3, N3, N3, t2,
+                                                                                    reinterpret_cast<dfv*>(c->b64), sc,
+                                                                                    sh, sl);
   } else {
     double *t1 = (double*)L0.t1, *t2 = (double*)L0.t2;
     FEP3M_CL k_load_axis<double, double><<<grid_for((int64_t)N3 * n * n), TPB, 0, s>>>(n, 0, N3, n, n,
-                                                                                      (const double*)c->rv, t1, 1.0);
-    FEP3M_CL k_load_axis<double, double><<<grid_for((int64_t)N3 * N3 * n), TPB, 0, s>>>(n, 1, N3, N3, n, t1, t2, 1.0);
+                                                                                      (const double*)c->rv, t1, 1.0,
+                                                                                      1.0f, 0.0f);
+    FEP3M_CL k_load_axis<double, double><<<grid_for((int64_t)N3 * N3 * n), TPB, 0, s>>>(n, 1, N3, N3, n, t1, t2, 1.0,
+                                                                                       1.0f, 0.0f);
     FEP3M_CL k_load_axis<double, double><<<grid_for((int64_t)N3 * N3 * N3), TPB, 0, s>>>(n, 2, N3, N3, N3, t2, c->b64,
-                                                                                        4.0 * M_PI);
+                                                                                        4.0 * M_PI, 1.0f, 0.0f);
   }
   return cudaGetLastError();
 }
@@ -2705,11 +2729,52 @@ __global__ void k_mpqT_axis(int axis, int n, int e0, int e1, int e2, const doubl
   out[g] = (T)(scale * acc);
 }
 
+// MIXED: the same passes on float pairs (lam as float pairs, the mixed solver's
+// output) with the integer weights (times 120; w v as a two-product, the sums
+// as two-sums); the last pass (Tout = double) forms mu = scale (h + l) in FP64
+template <class Tout>
+__global__ void k_mpqT_axis_df(int axis, int n, int e0, int e1, int e2, const dfv* __restrict__ in,
+                               Tout* __restrict__ out, double scale) {
+  const unsigned g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (unsigned)e0 * (unsigned)e1 * (unsigned)e2) return;
+  const unsigned q = g / (unsigned)e0;
+  int i[3] = {(int)(g - q * (unsigned)e0), (int)(q % (unsigned)e1), (int)(q / (unsigned)e1)};
+  int ein[3] = {e0, e1, e2};
+  const int N = 3 * n;
+  ein[axis] = N;
+  const int64_t st[3] = {1, ein[0], (int64_t)ein[0] * ein[1]};
+  const int v = i[axis];
+  i[axis] = 0;
+  const int64_t base = i[0] * st[0] + i[1] * st[1] + i[2] * st[2];
+  const float w[7] = {cMpq120[0][1], cMpq120[1][1], cMpq120[2][1], cMpq120[3][1] + cMpq120[0][0],
+                      cMpq120[1][0], cMpq120[2][0], cMpq120[3][0]};
+  dfv acc = {0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    int gg = 3 * v - 3 + k;
+    gg = gg < 0 ? gg + N : (gg >= N ? gg - N : gg);
+    const dfv x = in[base + gg * st[axis]];
+    const float p = w[k] * x.h;
+    acc += dfv{p, fmaf(w[k], x.l, fmaf(w[k], x.h, -p))};
+  }
+  if constexpr (std::is_same<Tout, dfv>::value) out[g] = df_norm(acc);
+  else out[g] = scale * ((double)acc.h + (double)acc.l);
+}
+
 cudaError_t vertex_adjoint(fep3m_ctx* c, const double* lam, void* mu, void* work1, void* work2, cudaStream_t s) {
-  // FP64 in both precisions: mu meets the screen adjoint in a difference that
-  // cancels; the two partial passes (9 n^3 and 3 n^3 values) fit as doubles
-  // in work buffers of (3n)^3 floats
+  // mu in FP64 in both precisions: it meets the screen adjoint in a difference
+  // that cancels; the two partial passes (9 n^3 and 3 n^3 values) fit as
+  // doubles (or float pairs) in work buffers of (3n)^3 floats
   const int n = c->n, N = 3 * n;
+  if (c->precision == FEP3M_MIXED) {   // lam as float pairs
+    const dfv* l = reinterpret_cast<const dfv*>(lam);
+    dfv *w1 = (dfv*)work1, *w2 = (dfv*)work2;
+    FEP3M_CL k_mpqT_axis_df<dfv><<<grid_for((size_t)n * N * N), TPB, 0, s>>>(0, n, n, N, N, l, w1, 1.0);
+    FEP3M_CL k_mpqT_axis_df<dfv><<<grid_for((size_t)n * n * N), TPB, 0, s>>>(1, n, n, n, N, w1, w2, 1.0);
+    FEP3M_CL k_mpqT_axis_df<double><<<grid_for((size_t)n * n * n), TPB, 0, s>>>(2, n, n, n, n, w2, (double*)mu,
+                                                                              4.0 * M_PI / (120.0 * 120.0 * 120.0));
+    return cudaGetLastError();
+  }
   FEP3M_CL k_mpqT_axis<double><<<grid_for((size_t)n * N * N), TPB, 0, s>>>(0, n, n, N, N, lam, nullptr, (double*)work1, 1.0);
   FEP3M_CL k_mpqT_axis<double><<<grid_for((size_t)n * n * N), TPB, 0, s>>>(1, n, n, n, N, nullptr, (double*)work1, (double*)work2, 1.0);
   FEP3M_CL k_mpqT_axis<double><<<grid_for((size_t)n * n * n), TPB, 0, s>>>(2, n, n, n, n, nullptr, (double*)work2, (double*)mu, 4.0 * M_PI);

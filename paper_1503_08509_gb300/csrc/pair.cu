@@ -974,9 +974,9 @@ __global__ void __launch_bounds__(TC ? PTC : PT, 2) k_pair_screen(int n, int n_s
 // FP32 path: the screen field arrives relative to the element's corners (the
 // field at node 0, corner fields relative to it, elsewhere the field less its
 // trilinear interpolant; pair_relative_table), and G is split the same way:
-// G0 and the corner values of G - G0 in FP64 (mesh potential read in FP64),
-// and the remainder G - G0 - trilinear(corners) in FP32 (the mesh potential as
-// a hi + lo pair of floats).  The trilinear part and its gradient at the
+// G0 and the corner values of G - G0 in FP64 (the mesh potential's hi + lo
+// float pair added in FP64), and the remainder G - G0 - trilinear(corners) in
+// FP32 (from the same pairs).  The trilinear part and its gradient at the
 // charge are evaluated in FP64; only the small remainder goes through the FP32
 // contraction.
 template <class T, bool GRAD>
@@ -1021,14 +1021,18 @@ __global__ void __launch_bounds__(PT) k_pair_eval(int n, int Nm, T inv_h, const 
     return (gx >= N ? gx - N : gx) + (int64_t)N * ((gy >= N ? gy - N : gy) + (int64_t)N * (gz >= N ? gz - N : gz));
   };
   if constexpr (F32) {
+    auto phd = [&](int64_t k) -> double {
+      const float2 p = phi_hl[k];
+      return (double)p.x + (double)p.y;
+    };
     if (tid < BE && epre[tid + 1] != epre[tid]) {
-      const double p00 = phi64[node(tid, 0)];
+      const double p00 = phd(node(tid, 0));
       G0[tid] = p00 - (double)gb[tid * 64];
       Gc[tid * 8] = 0.0;
 #pragma unroll
       for (int c = 1; c < 8; ++c) {
         const int mc = 3 * (c & 1) + 12 * ((c >> 1) & 1) + 48 * (c >> 2);
-        Gc[tid * 8 + c] = (phi64[node(tid, mc)] - p00) - (double)gb[tid * 64 + mc];
+        Gc[tid * 8 + c] = (phd(node(tid, mc)) - p00) - (double)gb[tid * 64 + mc];
       }
     }
     // node differences of the mesh potential from its hi + lo floats
@@ -1198,13 +1202,16 @@ __global__ void k_elem_deposit(int64_t ne, const int* __restrict__ start, const 
   }
 }
 
-// g[node] = sum over (element, local node) pairs at the node of W
+// g[node] = sum over (element, local node) pairs at the node of W: in FP64,
+// or (T = float, the mixed solver's right-hand side) as a float pair h + l
+// summed by two-sums; (3n)^3 < 2^32
 template <class T>
 __global__ void k_node_assemble(int n, const T* __restrict__ W, double* __restrict__ g) {
   const int N = 3 * n;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= (int64_t)N * N * N) return;
-  const int ix = (int)(i % N), iy = (int)((i / N) % N), iz = (int)(i / ((int64_t)N * N));
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (unsigned)N * (unsigned)N * (unsigned)N) return;
+  const unsigned q = i / (unsigned)N;
+  const int ix = (int)(i - q * (unsigned)N), iy = (int)(q % (unsigned)N), iz = (int)(q / (unsigned)N);
   int el[3][2], lo[3][2], cnt[3];
   const int id[3] = {ix, iy, iz};
   for (int a = 0; a < 3; ++a) {
@@ -1218,14 +1225,29 @@ __global__ void k_node_assemble(int n, const T* __restrict__ W, double* __restri
       cnt[a] = 2;
     }
   }
-  double acc = 0.0;
-  for (int c = 0; c < cnt[2]; ++c)
-    for (int b = 0; b < cnt[1]; ++b)
-      for (int a = 0; a < cnt[0]; ++a) {
-        const int64_t e = el[0][a] + (int64_t)n * (el[1][b] + (int64_t)n * el[2][c]);
-        acc += (double)W[e * 64 + lo[0][a] + 4 * lo[1][b] + 16 * lo[2][c]];
-      }
-  g[i] = acc;
+  if constexpr (sizeof(T) == 4) {
+    float sh = 0.f, sl = 0.f;
+    for (int c = 0; c < cnt[2]; ++c)
+      for (int b = 0; b < cnt[1]; ++b)
+        for (int a = 0; a < cnt[0]; ++a) {
+          const int64_t e = el[0][a] + (int64_t)n * (el[1][b] + (int64_t)n * el[2][c]);
+          const float v = W[e * 64 + lo[0][a] + 4 * lo[1][b] + 16 * lo[2][c]];
+          const float t = sh + v, bv = t - sh;
+          sl += (sh - (t - bv)) + (v - bv);
+          sh = t;
+        }
+    const float h = sh + sl;
+    reinterpret_cast<float2*>(g)[i] = make_float2(h, sl - (h - sh));
+  } else {
+    double acc = 0.0;
+    for (int c = 0; c < cnt[2]; ++c)
+      for (int b = 0; b < cnt[1]; ++b)
+        for (int a = 0; a < cnt[0]; ++a) {
+          const int64_t e = el[0][a] + (int64_t)n * (el[1][b] + (int64_t)n * el[2][c]);
+          acc += (double)W[e * 64 + lo[0][a] + 4 * lo[1][b] + 16 * lo[2][c]];
+        }
+    g[i] = acc;
+  }
 }
 
 // Screen part of the adjoint, as a GEMM and a gather (deterministic, no atomics):
@@ -1612,11 +1634,18 @@ static cudaError_t launch_pair_screen(fep3m_ctx* c, cudaStream_t s, bool half) {
 // or a box's
 static int mesh_nodes_per_axis(const fep3m_ctx* c) { return c->box ? c->box->Nn : 3 * c->n; }
 
+// MIXED: the mesh potential as hi + lo floats: the periodic solver's output
+// itself, a box's split by pair_prepare
+static const float2* mesh_potential_pairs(const fep3m_ctx* c) {
+  if (c->precision != FEP3M_MIXED) return nullptr;
+  return c->box ? (const float2*)c->phi_hl : (const float2*)c->phi64;
+}
+
 template <class T, bool GRAD>
 static cudaError_t launch_pair_eval(fep3m_ctx* c, double* phi_out) {
   FEP3M_CL k_pair_eval<T, GRAD><<<(unsigned)pair_bricks(c), PT, 0, c->stream>>>(
       c->n, mesh_nodes_per_axis(c), (T)c->inv_h, c->start, c->count, (const typename vec4<T>::type*)c->part, c->phi64,
-      (const float2*)c->phi_hl, (const T*)c->Gscr, c->perm, c->phi_s, c->E_s, phi_out);
+      mesh_potential_pairs(c), (const T*)c->Gscr, c->perm, c->phi_s, c->E_s, phi_out);
   return cudaGetLastError();
 }
 
@@ -1748,7 +1777,7 @@ void pair_tc_table(int n_sr, const double* Hw, uint16_t* out) {
       }
 }
 
-// the FP32 path's mesh potential as hi + lo floats
+// a box's FP64 mesh potential as hi + lo floats for the FP32 pair kernels
 __global__ void k_phi_hilo(int64_t n, const double* __restrict__ phi, float2* __restrict__ out) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
@@ -1758,7 +1787,7 @@ __global__ void k_phi_hilo(int64_t n, const double* __restrict__ phi, float2* __
 }
 
 cudaError_t pair_prepare(fep3m_ctx* c) {
-  if (c->precision == FEP3M_MIXED) {
+  if (c->precision == FEP3M_MIXED && c->box) {   // the periodic solver writes float pairs itself
     const int64_t na = mesh_nodes_per_axis(c), nodes = na * na * na;
     FEP3M_CL k_phi_hilo<<<gsz(nodes), PT, 0, c->stream>>>(nodes, c->phi64, (float2*)c->phi_hl);
   }
