@@ -123,12 +123,13 @@ inline int gsz(int64_t n) { return (int)((n + PT - 1) / PT); }
 
 void free_particles(fep3m_ctx* c) {
   void* p[] = {c->pos_in, c->Q_in, c->cell, c->delta, c->perm, c->ecoord, c->part, c->phi_s, c->E_s, c->w_s,
-               c->psi_s, c->gpsi_s, c->out_tmp, c->Q_s, c->gphi_dev};
+               c->psi_s, c->gpsi_s, c->out_tmp, c->Q_s, c->gphi_dev, c->w_s32};
   for (void* q : p) dfree(q);
   c->pos_in = c->Q_in = c->delta = c->phi_s = c->E_s = c->w_s = c->psi_s = c->gpsi_s = c->out_tmp = c->Q_s =
       c->gphi_dev = nullptr;
   c->cell = c->perm = c->ecoord = nullptr;
   c->part = nullptr;
+  c->w_s32 = nullptr;
   c->cap = 0;
 }
 
@@ -146,6 +147,7 @@ int grow_particles(fep3m_ctx* c, int64_t N) {
   CK(dalloc(&c->phi_s, N));
   CK(dalloc(&c->E_s, 3 * N));
   CK(dalloc(&c->w_s, N));
+  if (c->precision == FEP3M_MIXED) CK(dalloc(&c->w_s32, N));
   CK(dalloc(&c->psi_s, N));
   CK(dalloc(&c->gpsi_s, 3 * N));
   CK(dalloc(&c->out_tmp, 5 * N));

@@ -313,6 +313,7 @@ struct fep3m_ctx {
   double* phi_s = nullptr;       // N
   double* E_s = nullptr;         // N*3 target-side gradient
   double* w_s = nullptr;         // N adjoint weights
+  float* w_s32 = nullptr;        // MIXED: the same in FP32 (the element deposit's input)
   double* psi_s = nullptr;       // N singular adjoint potential
   double* gpsi_s = nullptr;      // N*3
   double* Q_s = nullptr;         // N sorted charges (FP64)

@@ -342,20 +342,20 @@ enum { EPI_Y = 0, EPI_RESID = 1, EPI_CHEB = 2, EPI_CHEB0 = 3 };
 // scalars derived on the device by the reductions: doubles at
 // scal[SC_DERIVED + k], floats at ((float*)(scal + SC_DERIVED_F))[k]
 constexpr int SC_DERIVED = 16, SC_DERIVED_F = 32;
-enum { SD_ALPHA = 0, SD_BETA = 1, SD_MEAN = 2, SD_SCALE = 3, SD_INVSCALE = 4 };
+enum { SD_ALPHA = 0, SD_BETA = 1, SD_MEAN = 2, SD_SCALE = 3, SD_INVSCALE = 4, SD_MEANLO = 5 };
 // what the last block derives from the total t (written next to it, so that
 // the consumers read one ready scalar instead of recomputing it per node)
 enum { POST_NONE = 0, POST_ALPHA = 1, POST_BETA = 2, POST_MEAN = 3, POST_SCALE = 4 };
 
 // Deterministic block-then-grid sum (blockDim.x == 256): the block's total goes
 // to partials[bid]; the last block to finish adds the partials in index order,
-// writes the total to *out and derives the post scalar from it.
-__device__ void block_sum_finish(double acc, unsigned bid, unsigned nblocks, double* __restrict__ partials,
-                                 unsigned int* __restrict__ counter, double* __restrict__ out, int post,
-                                 double arg, double* __restrict__ scal) {
+// writes the total to *out and derives the post scalar from it.  The tail
+// takes each warp's total in its lane 0.
+__device__ void block_sum_tail(double acc, unsigned bid, unsigned nblocks, double* __restrict__ partials,
+                               unsigned int* __restrict__ counter, double* __restrict__ out, int post, double arg,
+                               double* __restrict__ scal) {
   __shared__ double sh[8];
   __shared__ bool last;
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -390,9 +390,11 @@ __device__ void block_sum_finish(double acc, unsigned bid, unsigned nblocks, dou
     dd[SD_BETA] = bta;
     df[SD_BETA] = (float)bta;
     scal[0] = t;
-  } else if (post == POST_MEAN) {    // t * arg (arg = 1 / W)
-    dd[SD_MEAN] = t * arg;
-    df[SD_MEAN] = (float)(t * arg);
+  } else if (post == POST_MEAN) {    // t * arg (arg = 1 / W); the float value also as a pair
+    const double m = t * arg;
+    dd[SD_MEAN] = m;
+    df[SD_MEAN] = (float)m;
+    df[SD_MEANLO] = (float)(m - (double)(float)m);
   } else if (post == POST_SCALE) {   // 2^-k with 2^k near the RMS sqrt(t arg)
     const double rms = sqrt(t * arg);
     int k = rms > 0.0 && isfinite(rms) ? ilogb(rms) : 0;
@@ -402,6 +404,33 @@ __device__ void block_sum_finish(double acc, unsigned bid, unsigned nblocks, dou
     df[SD_SCALE] = (float)ldexp(1.0, -k);
     df[SD_INVSCALE] = (float)ldexp(1.0, k);
   }
+}
+
+__device__ void block_sum_finish(double acc, unsigned bid, unsigned nblocks, double* __restrict__ partials,
+                                 unsigned int* __restrict__ counter, double* __restrict__ out, int post,
+                                 double arg, double* __restrict__ scal) {
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  block_sum_tail(acc, bid, nblocks, partials, counter, out, post, arg, scal);
+}
+
+// the warp's sum of float pairs (two-sums), in lane 0
+__device__ __forceinline__ dfv warp_sum_df(dfv a) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const dfv b = {__shfl_down_sync(0xffffffffu, a.h, o), __shfl_down_sync(0xffffffffu, a.l, o)};
+    a += b;
+  }
+  return a;
+}
+
+// block_sum_finish with a float-pair value per thread: the warps sum as float
+// pairs (FP64 is a small fraction of the FP32 rate here), FP64 from the warp
+// totals on
+__device__ void block_sum_finish_df(dfv acc, unsigned bid, unsigned nblocks, double* __restrict__ partials,
+                                    unsigned int* __restrict__ counter, double* __restrict__ out, int post,
+                                    double arg, double* __restrict__ scal) {
+  acc = warp_sum_df(acc);
+  block_sum_tail((threadIdx.x & 31) == 0 ? (double)acc.h + (double)acc.l : 0.0, bid, nblocks, partials, counter, out,
+                 post, arg, scal);
 }
 
 // a dot product accumulated by an apply: block partials, counter, total, post
@@ -574,6 +603,7 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
   ApplySmem<T, EPI, DOT>& S = *reinterpret_cast<ApplySmem<T, EPI, DOT>*>(apply_smem_raw);
   constexpr int NST = apply_nst<T, EPI, DOT>();
   double dacc = 0.0;
+  float facc = 0.f;   // EPI_RESID dot: |r|^2 in FP32
   const int n = N / 3;
   const int64_t NN = (int64_t)N * N;
   const int x0 = blockIdx.x * AFX, y0 = blockIdx.y * AFY;
@@ -742,7 +772,7 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
           else if constexpr (DOT) dsum = r == 0 ? bg * f : dsum + bg * f;   // EPI_Y stages x in the b slot
         }
         if constexpr (DOT && EPI != EPI_RESID) dacc += (double)dsum;
-        if constexpr (DOT && EPI == EPI_RESID) dacc += (double)dres;
+        if constexpr (DOT && EPI == EPI_RESID) facc += dres;
       }
     }
     // next element: slots 0..3 <- 3..6, slots 4..6 <- the prefetched planes
@@ -758,8 +788,13 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
   }
   if constexpr (DOT) {
     const unsigned nbv = gridDim.x * gridDim.y * zsb;   // blocks per vector
-    block_sum_finish(dacc, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * (blockIdx.z - vi * zsb)), nbv,
-                     dt.partials + (size_t)vi * nbv, dt.counter + vi, dt.out + 64 * vi, dt.post, 0.0, scal);
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * (blockIdx.z - vi * zsb));
+    if constexpr (EPI == EPI_RESID)
+      block_sum_finish_df(dfv{facc, 0.f}, bid, nbv, dt.partials + (size_t)vi * nbv, dt.counter + vi,
+                          dt.out + 64 * vi, dt.post, 0.0, scal);
+    else
+      block_sum_finish(dacc, bid, nbv, dt.partials + (size_t)vi * nbv, dt.counter + vi, dt.out + 64 * vi, dt.post,
+                       0.0, scal);
   }
 }
 
@@ -1452,20 +1487,19 @@ __device__ __forceinline__ dfv df_scaled(float mh, float ml, float w) {
   return {p, fmaf(ml, w, fmaf(mh, w, -p))};
 }
 
-// Two block-then-grid sums at once (blockDim.x == 256): the block's totals go
-// to partials[2 bid], partials[2 bid + 1]; the last block adds the partials in
+// Two block-then-grid sums at once (blockDim.x == 256) of float-pair values:
+// the warps sum as float pairs, the block's totals (FP64) go to
+// partials[2 bid], partials[2 bid + 1]; the last block adds the partials in
 // index order and returns true on its thread 0 with the totals in ta, tb.
-__device__ bool block_sum2_finish(double a, double b, unsigned bid, unsigned nblocks, double* __restrict__ partials,
+__device__ bool block_sum2_finish(dfv a2, dfv b2, unsigned bid, unsigned nblocks, double* __restrict__ partials,
                                   unsigned int* __restrict__ counter, double& ta, double& tb) {
   __shared__ double sh[2][8];
   __shared__ bool last;
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-  }
+  a2 = warp_sum_df(a2);
+  b2 = warp_sum_df(b2);
   if ((threadIdx.x & 31) == 0) {
-    sh[0][threadIdx.x >> 5] = a;
-    sh[1][threadIdx.x >> 5] = b;
+    sh[0][threadIdx.x >> 5] = (double)a2.h + (double)a2.l;
+    sh[1][threadIdx.x >> 5] = (double)b2.h + (double)b2.l;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1528,13 +1562,15 @@ __global__ void k_ref_sums(int64_t n, const dfv* __restrict__ b, double* __restr
     sq = fmaf(x.h, x.h, sq);
   }
   double ta, tb;
-  if (block_sum2_finish((double)sum.h + (double)sum.l, (double)sq, blockIdx.x, gridDim.x, partials, counter, ta, tb)) {
+  if (block_sum2_finish(sum, dfv{sq, 0.f}, blockIdx.x, gridDim.x, partials, counter, ta, tb)) {
     double* dd = scal + SC_DERIVED;
     float* df = (float*)(scal + SC_DERIVED_F);
     scal[5] = ta;
     scal[7] = tb;
-    dd[SD_MEAN] = ta * invW;
-    df[SD_MEAN] = (float)(ta * invW);
+    const double m = ta * invW;
+    dd[SD_MEAN] = m;
+    df[SD_MEAN] = (float)m;
+    df[SD_MEANLO] = (float)(m - (double)(float)m);
     const double rms = sqrt(tb / (double)n);
     int k = rms > 0.0 && isfinite(rms) ? ilogb(rms) : 0;
     k = max(-100, min(100, k));
@@ -1559,9 +1595,8 @@ __global__ void k_ref_project_scale(int N, const dfv* __restrict__ b, dfv* __res
   partials += (size_t)vi * gridDim.x;
   counter += vi;
   scal += 64 * vi;
-  const double m = scal[SC_DERIVED + SD_MEAN];
-  const float mh = (float)m, ml = (float)(m - (double)mh);
-  const float sc = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_SCALE];
+  const float* dfs = reinterpret_cast<const float*>(scal + SC_DERIVED_F);
+  const float mh = dfs[SD_MEAN], ml = dfs[SD_MEANLO], sc = dfs[SD_SCALE];
   const int64_t rows = (int64_t)N * N, stride = (int64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nwarps = stride >> 5;
@@ -1583,12 +1618,12 @@ __global__ void k_ref_project_scale(int N, const dfv* __restrict__ b, dfv* __res
       acc = fmaf(x, x, acc);
     }
   }
-  block_sum_finish((double)acc, blockIdx.x, gridDim.x, partials, counter, scal + 10, POST_NONE, 0.0, scal);
+  block_sum_finish_df(dfv{acc, 0.f}, blockIdx.x, gridDim.x, partials, counter, scal + 10, POST_NONE, 0.0, scal);
 }
 
 // finish, first pass: the integral sum w3 phi of the iterate (float pairs) into
 // scal[6] with the mean derived (POST_MEAN, arg = 1 / W); rows per warp, the
-// row's vertex and interior columns summed as float pairs
+// weighted values summed as float pairs
 __global__ void k_ref_wsum(int N, const dfv* __restrict__ v, double* __restrict__ partials,
                            unsigned int* __restrict__ counter, double* __restrict__ scal, double invW, int64_t vs) {
   PDL_PROLOGUE
@@ -1600,19 +1635,19 @@ __global__ void k_ref_wsum(int N, const dfv* __restrict__ v, double* __restrict_
   const int64_t rows = (int64_t)N * N, stride = (int64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nwarps = stride >> 5;
-  double acc = 0.0;
+  dfv acc = {0.f, 0.f};
   for (int64_t row = warp; row < rows; row += nwarps) {
     const int iz = (int)(row / N), iy = (int)(row - (int64_t)iz * N);
-    const double wyz = (iy % 3 ? 0.375 : 0.25) * (iz % 3 ? 0.375 : 0.25);
     const dfv* vr = v + row * N;
-    dfv s0 = {0.f, 0.f}, s1 = {0.f, 0.f};   // vertex / interior columns
     for (int ix = lane; ix < N; ix += 32) {
-      if (ix % 3 == 0) s0 += vr[ix];
-      else s1 += vr[ix];
+      // the node weight (1/4 or 3/8 per axis) times the value as a two-product
+      const float w = (ix % 3 ? 0.375f : 0.25f) * (iy % 3 ? 0.375f : 0.25f) * (iz % 3 ? 0.375f : 0.25f);
+      const dfv x = vr[ix];
+      const float p = w * x.h;
+      acc += dfv{p, fmaf(w, x.l, fmaf(w, x.h, -p))};
     }
-    acc += wyz * (0.25 * ((double)s0.h + (double)s0.l) + 0.375 * ((double)s1.h + (double)s1.l));
   }
-  block_sum_finish(acc, blockIdx.x, gridDim.x, partials, counter, scal + 6, POST_MEAN, invW, scal);
+  block_sum_finish_df(acc, blockIdx.x, gridDim.x, partials, counter, scal + 6, POST_MEAN, invW, scal);
 }
 
 // finish, second pass: phi = v - m as normalised float pairs (m the mean just
@@ -1624,8 +1659,8 @@ __global__ void k_ref_out(int64_t n, const dfv* __restrict__ v, dfv* __restrict_
   v += vi * vs;
   phi += vi * vs;
   scal += 64 * vi;
-  const double m = scal[SC_DERIVED + SD_MEAN];
-  const float mh = (float)m, ml = (float)(m - (double)mh);
+  const float* dfs = reinterpret_cast<const float*>(scal + SC_DERIVED_F);
+  const float mh = dfs[SD_MEAN], ml = dfs[SD_MEANLO];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
     dfv y = v[g];

@@ -1160,10 +1160,12 @@ __global__ void __launch_bounds__(PT) k_pair_eval(int n, int Nm, T inv_h, const 
 
 // ----------------------------------------------------------------- adjoint
 __global__ void k_weights(int64_t N, double gU, const double* __restrict__ gphi, const int* __restrict__ perm,
-                          const double* __restrict__ Qs, double* __restrict__ w) {
+                          const double* __restrict__ Qs, double* __restrict__ w, float* __restrict__ w32) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= N) return;
-  w[k] = 0.5 * gU * Qs[k] + (gphi ? gphi[perm[k]] : 0.0);
+  const double v = 0.5 * gU * Qs[k] + (gphi ? gphi[perm[k]] : 0.0);
+  w[k] = v;
+  if (w32) w32[k] = (float)v;
 }
 
 template <class T>
@@ -1175,11 +1177,13 @@ __global__ void k_charges(int64_t N, const typename vec4<T>::type* __restrict__ 
 
 // W[e][m] = sum_{t in e} w_t u_m(tau_t): the adjoint's point deposit, per
 // element.  wsum (FP32 path): sum_{t in e} w_t in FP64 as hi + lo floats, the
-// exact sum over m of W[e][m] (the shape functions sum to one).
+// exact sum over m of W[e][m] (the shape functions sum to one).  wT: the
+// weights in the working precision (FP32: a copy, so that the 64 threads of
+// an element do not each convert them).
 template <class T>
 __global__ void k_elem_deposit(int64_t ne, const int* __restrict__ start, const int* __restrict__ count,
                                const typename vec4<T>::type* __restrict__ part, const double* __restrict__ w,
-                               T* __restrict__ W, float2* __restrict__ wsum) {
+                               const T* __restrict__ wT, T* __restrict__ W, float2* __restrict__ wsum) {
   const int64_t e = blockIdx.x * (int64_t)(blockDim.x / 64) + threadIdx.x / 64;
   if (e >= ne) return;
   const int m = threadIdx.x & 63, mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
@@ -1192,7 +1196,7 @@ __global__ void k_elem_deposit(int64_t ne, const int* __restrict__ start, const 
     q3_values<T>(p.x, ux);
     q3_values<T>(p.y, uy);
     q3_values<T>(p.z, uz);
-    acc += (T)w[j] * ux[mx] * uy[my] * uz[mz];
+    acc += wT[j] * ux[mx] * uy[my] * uz[mz];
     if (m == 0) ws += w[j];
   }
   W[e * 64 + m] = acc;
@@ -1882,15 +1886,15 @@ static cudaError_t screen_adjoint(fep3m_ctx* c, const T* W, const double* Hw, do
 cudaError_t adjoint_pre(fep3m_ctx* c, double gU, const double* gphi, cudaStream_t s) {
   const int n = c->n;
   const int64_t ne = (int64_t)n * n * n, nodes = 27 * ne, N = c->N;
-  FEP3M_CL k_weights<<<gsz(N), PT, 0, s>>>(N, gU, gphi, c->perm, c->Q_s, c->w_s);
+  FEP3M_CL k_weights<<<gsz(N), PT, 0, s>>>(N, gU, gphi, c->perm, c->Q_s, c->w_s, c->w_s32);
   const int per = PT / 64;
   if (c->precision == FEP3M_MIXED) {
     FEP3M_CL k_elem_deposit<float><<<gsz(ne, per), PT, 0, s>>>(ne, c->start, c->count, (const float4*)c->part, c->w_s,
-                                                               (float*)c->W_el, (float2*)c->Wsum);
+                                                               c->w_s32, (float*)c->W_el, (float2*)c->Wsum);
     FEP3M_CL k_node_assemble<float><<<gsz(nodes), PT, 0, s>>>(n, (const float*)c->W_el, c->g64);
   } else {
     FEP3M_CL k_elem_deposit<double><<<gsz(ne, per), PT, 0, s>>>(ne, c->start, c->count, (const vec4<double>::type*)c->part,
-                                                                c->w_s, (double*)c->W_el, nullptr);
+                                                                c->w_s, c->w_s, (double*)c->W_el, nullptr);
     FEP3M_CL k_node_assemble<double><<<gsz(nodes), PT, 0, s>>>(n, (const double*)c->W_el, c->g64);
   }
   return cudaGetLastError();
