@@ -347,21 +347,17 @@ enum { SD_ALPHA = 0, SD_BETA = 1, SD_MEAN = 2, SD_SCALE = 3, SD_INVSCALE = 4, SD
 // the consumers read one ready scalar instead of recomputing it per node)
 enum { POST_NONE = 0, POST_ALPHA = 1, POST_BETA = 2, POST_MEAN = 3, POST_SCALE = 4 };
 
-// Deterministic block-then-grid sum (blockDim.x == 256): the block's total goes
-// to partials[bid]; the last block to finish adds the partials in index order,
-// writes the total to *out and derives the post scalar from it.  The tail
-// takes each warp's total in its lane 0.
-__device__ void block_sum_tail(double acc, unsigned bid, unsigned nblocks, double* __restrict__ partials,
-                               unsigned int* __restrict__ counter, double* __restrict__ out, int post, double arg,
-                               double* __restrict__ scal) {
+// Deterministic block-then-grid sum (blockDim.x == 256): the block's total
+// (in thread 0) goes to partials[bid]; the last block to finish adds the
+// partials in index order, writes the total to *out and derives the post
+// scalar from it.  Called by every thread of the block.
+__device__ void block_total_finish(double total, unsigned bid, unsigned nblocks, double* __restrict__ partials,
+                                   unsigned int* __restrict__ counter, double* __restrict__ out, int post,
+                                   double arg, double* __restrict__ scal) {
   __shared__ double sh[8];
   __shared__ bool last;
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-  __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0;
-    for (int k = 0; k < 8; ++k) s += sh[k];
-    partials[bid] = s;
+    partials[bid] = total;
     __threadfence();
     unsigned int done = atomicAdd(counter, 1u);
     last = (done == nblocks - 1);
@@ -409,8 +405,14 @@ __device__ void block_sum_tail(double acc, unsigned bid, unsigned nblocks, doubl
 __device__ void block_sum_finish(double acc, unsigned bid, unsigned nblocks, double* __restrict__ partials,
                                  unsigned int* __restrict__ counter, double* __restrict__ out, int post,
                                  double arg, double* __restrict__ scal) {
+  __shared__ double shw[8];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  block_sum_tail(acc, bid, nblocks, partials, counter, out, post, arg, scal);
+  if ((threadIdx.x & 31) == 0) shw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 8; ++k) t += shw[k];
+  block_total_finish(t, bid, nblocks, partials, counter, out, post, arg, scal);
 }
 
 // the warp's sum of float pairs (two-sums), in lane 0
@@ -422,15 +424,27 @@ __device__ __forceinline__ dfv warp_sum_df(dfv a) {
   return a;
 }
 
-// block_sum_finish with a float-pair value per thread: the warps sum as float
-// pairs (FP64 is a small fraction of the FP32 rate here), FP64 from the warp
-// totals on
+// the block's sum of float pairs (two-sums), in thread 0
+__device__ __forceinline__ dfv block_sum_df(dfv acc) {
+  __shared__ dfv shd[8];
+  acc = warp_sum_df(acc);
+  if ((threadIdx.x & 31) == 0) shd[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 1; k < 8; ++k) acc += shd[k];
+  return acc;
+}
+
+// block_sum_finish with a float-pair value per thread: the block sums as float
+// pairs (an FP64 instruction costs a whole warp's slot on the FP64 pipe, a
+// small fraction of the FP32 rate here, even with one lane active), FP64 from
+// the block total on
 __device__ void block_sum_finish_df(dfv acc, unsigned bid, unsigned nblocks, double* __restrict__ partials,
                                     unsigned int* __restrict__ counter, double* __restrict__ out, int post,
                                     double arg, double* __restrict__ scal) {
-  acc = warp_sum_df(acc);
-  block_sum_tail((threadIdx.x & 31) == 0 ? (double)acc.h + (double)acc.l : 0.0, bid, nblocks, partials, counter, out,
-                 post, arg, scal);
+  acc = block_sum_df(acc);
+  block_total_finish(threadIdx.x == 0 ? (double)acc.h + (double)acc.l : 0.0, bid, nblocks, partials, counter, out,
+                     post, arg, scal);
 }
 
 // a dot product accumulated by an apply: block partials, counter, total, post
@@ -1488,28 +1502,19 @@ __device__ __forceinline__ dfv df_scaled(float mh, float ml, float w) {
 }
 
 // Two block-then-grid sums at once (blockDim.x == 256) of float-pair values:
-// the warps sum as float pairs, the block's totals (FP64) go to
-// partials[2 bid], partials[2 bid + 1]; the last block adds the partials in
-// index order and returns true on its thread 0 with the totals in ta, tb.
+// the block sums as float pairs, its totals (FP64) go to partials[2 bid],
+// partials[2 bid + 1]; the last block adds the partials in index order and
+// returns true on its thread 0 with the totals in ta, tb.
 __device__ bool block_sum2_finish(dfv a2, dfv b2, unsigned bid, unsigned nblocks, double* __restrict__ partials,
                                   unsigned int* __restrict__ counter, double& ta, double& tb) {
   __shared__ double sh[2][8];
   __shared__ bool last;
-  a2 = warp_sum_df(a2);
-  b2 = warp_sum_df(b2);
-  if ((threadIdx.x & 31) == 0) {
-    sh[0][threadIdx.x >> 5] = (double)a2.h + (double)a2.l;
-    sh[1][threadIdx.x >> 5] = (double)b2.h + (double)b2.l;
-  }
-  __syncthreads();
+  a2 = block_sum_df(a2);
+  __syncthreads();   // block_sum_df's shared slots are reused by the second sum
+  b2 = block_sum_df(b2);
   if (threadIdx.x == 0) {
-    double s0 = 0, s1 = 0;
-    for (int k = 0; k < 8; ++k) {
-      s0 += sh[0][k];
-      s1 += sh[1][k];
-    }
-    partials[2 * bid] = s0;
-    partials[2 * bid + 1] = s1;
+    partials[2 * bid] = (double)a2.h + (double)a2.l;
+    partials[2 * bid + 1] = (double)b2.h + (double)b2.l;
     __threadfence();
     const unsigned int done = atomicAdd(counter, 1u);
     last = (done == nblocks - 1);
@@ -1526,7 +1531,6 @@ __device__ bool block_sum2_finish(dfv a2, dfv b2, unsigned bid, unsigned nblocks
     s0 += __shfl_down_sync(0xffffffffu, s0, o);
     s1 += __shfl_down_sync(0xffffffffu, s1, o);
   }
-  __syncthreads();
   if ((threadIdx.x & 31) == 0) {
     sh[0][threadIdx.x >> 5] = s0;
     sh[1][threadIdx.x >> 5] = s1;

@@ -1184,12 +1184,23 @@ template <class T>
 __global__ void k_elem_deposit(int64_t ne, const int* __restrict__ start, const int* __restrict__ count,
                                const typename vec4<T>::type* __restrict__ part, const double* __restrict__ w,
                                const T* __restrict__ wT, T* __restrict__ W, float2* __restrict__ wsum) {
-  const int64_t e = blockIdx.x * (int64_t)(blockDim.x / 64) + threadIdx.x / 64;
+  // wsum: the block's elements by the lanes of its first warp (an FP64
+  // instruction takes the FP64 pipe for a whole warp, however few lanes are on)
+  const int per = blockDim.x / 64;
+  if (wsum && threadIdx.x < per) {
+    const int64_t e = blockIdx.x * (int64_t)per + threadIdx.x;
+    if (e < ne) {
+      double ws = 0.0;
+      for (int j = start[e], j1 = start[e] + count[e]; j < j1; ++j) ws += w[j];
+      const float hi = (float)ws;
+      wsum[e] = make_float2(hi, (float)(ws - (double)hi));
+    }
+  }
+  const int64_t e = blockIdx.x * (int64_t)per + threadIdx.x / 64;
   if (e >= ne) return;
   const int m = threadIdx.x & 63, mx = m & 3, my = (m >> 2) & 3, mz = m >> 4;
   const int s = start[e], cnt = count[e];
   T acc = T(0);
-  double ws = 0.0;
   for (int j = s; j < s + cnt; ++j) {
     const typename vec4<T>::type p = part[j];
     T ux[4], uy[4], uz[4];
@@ -1197,13 +1208,8 @@ __global__ void k_elem_deposit(int64_t ne, const int* __restrict__ start, const 
     q3_values<T>(p.y, uy);
     q3_values<T>(p.z, uz);
     acc += wT[j] * ux[mx] * uy[my] * uz[mz];
-    if (m == 0) ws += w[j];
   }
   W[e * 64 + m] = acc;
-  if (wsum && m == 0) {
-    const float hi = (float)ws;
-    wsum[e] = make_float2(hi, (float)(ws - (double)hi));
-  }
 }
 
 // g[node] = sum over (element, local node) pairs at the node of W: in FP64,
