@@ -33,10 +33,10 @@ WORKLOAD = "nacl32"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "nacl32_sample.txt")
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_pair_screen launch and of one transform pass of the
-# mesh solve (k_tc_rows) on this workload, from the ncu captures summarised in profiles/ (None until one is
-# taken of the current kernel)
+# mesh solve (k_tc_rows, both right-hand sides) on this workload, from the ncu captures summarised in
+# profiles/ (None until one is taken of the current kernel)
 PAIR_DRAM_BYTES = 2264320 + 1536
-PASS_DRAM_BYTES = 3650000 + 0
+PASS_DRAM_BYTES = 7187456 + 0
 
 
 def parse():
@@ -210,7 +210,8 @@ def large_workload(name, steps, warmup, flush, dev, torch, peaks):
     stages = {k: round(statistics.mean(x[k] for x in eng.step_stats), 3) for k in STAGES}
     Nn = 3 * d["n_el"]
     pass_ms = stages["ms_inner_solve"] / 6
-    pass_flops = 2.0 * Nn ** 4 * 6          # six split products per pass
+    nrhs = st["solve_rhs"]                  # the step pairs the forward and adjoint right-hand sides
+    pass_flops = 2.0 * Nn ** 4 * 6          # six split products per pass and right-hand side
     # the same inner solve alone on the GPU (fep3m_solve_mesh of a random neutral load): in the step it
     # shares the GPU with the concurrent adjoint solve and the short-range kernels
     rhs = torch.randn(Nn ** 3, dtype=torch.float64, device=dev)
@@ -235,10 +236,11 @@ def large_workload(name, steps, warmup, flush, dev, torch, peaks):
            "pairs": {"singular": st["singular_pairs"], "screen_element_pairs": st["screen_element_pairs"],
                      "nonempty_elements": st["nonempty_elements"], "max_per_element": st["max_per_element"]},
            "roofline_transform": {"kernel": "k_tc_rows (transform pass of the mesh solve)", "bound": "tensor",
-                                  "achieved": round(pass_flops / (pass_ms * 1e-3) / 1e12, 1),
+                                  "achieved": round(nrhs * pass_flops / (pass_ms * 1e-3) / 1e12, 1),
                                   "peak": bf16, "unit": "TFLOP/s",
-                                  "frac": round(pass_flops / (pass_ms * 1e-3) / 1e12 / bf16, 4),
-                                  "count": "2 N^4 x 6 split-bf16 products per pass, N = %d" % Nn,
+                                  "frac": round(nrhs * pass_flops / (pass_ms * 1e-3) / 1e12 / bf16, 4),
+                                  "count": "2 N^4 x 6 split-bf16 products per pass and right-hand side, N = %d, "
+                                           "%d right-hand sides per pass in the step (1 alone)" % (Nn, nrhs),
                                   "ms_per_launch": round(pass_ms, 4),
                                   "peak_note": "measured sustained bf16 (MEASURED_PEAKS.json)",
                                   "alone": {"ms_per_launch": round(alone_ms, 4),
@@ -409,12 +411,14 @@ def run_ours(args):
     hbm_note = "measured copy bandwidth (MEASURED_PEAKS.json)"
     if not hbm:
         hbm, hbm_note = 6800.0, "fallback 6.8 TB/s"
-    pass_bytes = 8 * nodes
+    rhs = st["solve_rhs"]   # right-hand sides per pass: the forward and adjoint solves go through together
+    pass_bytes = 8 * nodes * rhs
     achieved_gbs = pass_bytes / (pass_ms * 1e-3) / 1e9
     roof = {"kernel": "k_tc_rows (fast-diagonalisation transform pass of the mesh solve, tensor cores)",
             "bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved_gbs / hbm, 4), "traffic": PASS_DRAM_BYTES, "peak_note": hbm_note,
-            "count": "8 B per node per pass ((3n)^3 = %d nodes, FP32 read + write)" % nodes,
+            "count": "8 B per node and right-hand side per pass ((3n)^3 = %d nodes, FP32 read + write; %d "
+                     "right-hand sides per pass)" % (nodes, rhs),
             "bytes_per_launch": pass_bytes, "ms_per_launch": round(pass_ms, 5),
             "note": "at 32^3 the vector (3.5 MB) stays in L2 and each pass is launch/latency bound"}
 

@@ -177,6 +177,11 @@ typedef struct {
                                preconditioned CG): inside fep3m_compute, where it
                                shares the GPU with the concurrent streams; after
                                fep3m_solve_mesh, alone                            */
+  int solve_rhs;            /* right-hand sides that went through each kernel of
+                               the last mesh solve: 2 when fep3m_compute with
+                               forces paired the forward and adjoint solves
+                               (tensor-core fast diagonalisation), else 1; each
+                               transform pass then moves twice the data         */
 } fep3m_stats;
 
 /* Create a context: validates cfg, builds the FE basis-screen table (a

@@ -32,7 +32,7 @@ class Stats(ctypes.Structure):
                 ("ms_solve", ctypes.c_double), ("ms_pair", ctypes.c_double), ("ms_adjoint", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("screen_element_pairs", ctypes.c_int64),
                 ("screen_charge_pairs", ctypes.c_int64), ("ms_pair_screen", ctypes.c_double),
-                ("ms_pair_eval", ctypes.c_double), ("ms_inner_solve", ctypes.c_double)]
+                ("ms_pair_eval", ctypes.c_double), ("ms_inner_solve", ctypes.c_double), ("solve_rhs", ctypes.c_int)]
 
 
 P = ctypes.c_void_p

@@ -194,6 +194,7 @@ void take_counts(fep3m_ctx* c) {
 
 void solve_stats(fep3m_ctx* c) {
   const fep3m::Solver& F = c->solv[0];
+  c->stats.solve_rhs = 1;
   c->stats.mg_iterations = F.iters;
   c->stats.mg_rel_residual = F.relres;
   c->stats.refine_steps = F.refine_steps;
@@ -297,6 +298,7 @@ int solve_status(fep3m_ctx* c, bool adjoint) {
   const fep3m::Solver* A = &c->solv[1];
   solve_stats(c);
   const bool paired = adjoint && c->paired_last;
+  if (paired) c->stats.solve_rhs = 2;
   const double arel = paired ? F->relres2 : A->relres;
   if (adjoint) {
     c->stats.adj_iterations = paired ? F->iters2 : A->iters;
