@@ -193,8 +193,9 @@ def large_workload(name, steps, warmup, flush, dev, torch, peaks):
     """One of the full-size workloads (mixed, forces), timed like the headline: particles/s, per-step
     stage times (CUDA events on their streams; the stages overlap across the four streams) and the
     roofline of the two largest kernels: the transform pass of the mesh solve (tensor pipe: 2 N flops per
-    node and mode column, six split-bf16 products) and the short-range screen kernel (FP32, SURVEY 8(d)
-    count)."""
+    node and mode column and right-hand side, six split-bf16 products) and the short-range screen kernel
+    (FP32: 1024 flops per non-empty target element and non-empty element of its block, 20 per singular
+    pair)."""
     from paper_1503_08509_gb300 import api, workloads
     d = workloads.workload(name)
     N = len(d["Q"])
