@@ -597,7 +597,7 @@ int box_create(fep3m_ctx* c, int nb, bool neumann) {
   cudaMemcpy(B->bel, bel.data(), bel.size() * sizeof(int), cudaMemcpyHostToDevice);
   std::vector<double> lam, V;
   box_eigen(3, nb, !neumann, lam, V);
-  e = fdm_setup(B->fdm, B->Ns, lam, V, !(c->cfg.flags & FEP3M_CUDA_CORES), neumann);
+  e = fdm_setup(B->fdm, B->Ns, lam, V, 1, !(c->cfg.flags & FEP3M_CUDA_CORES), neumann);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? FEP3M_ENOMEM : FEP3M_ECUDA;
   const int noff = c->noff;
   const size_t smem = ((size_t)noff * noff * noff + 128 + 64 + BOX_NGL * BOX_NGL) * sizeof(double);

@@ -385,7 +385,8 @@ cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream, int 
 // fast-diagonalisation solve of a periodic N^3 mesh from its 1-D eigenpairs
 // (mesh.cu): device data, x = K^+ b in FP32 (six transform passes; w1, w2 N^3
 // scratch), release
-cudaError_t fdm_setup(FineFDM& f, int N, const std::vector<double>& lam, const std::vector<double>& V,
+// (rhs: right-hand sides per pass the solve will usually take, for the tile shape)
+cudaError_t fdm_setup(FineFDM& f, int N, const std::vector<double>& lam, const std::vector<double>& V, int rhs,
                       bool tensor_cores, bool null_mode = true);
 // V vectors at a stride of vs values (V = 2 with the tensor-core passes only)
 cudaError_t fdm_apply(const FineFDM& f, const float* b, float* x, float* w1, float* w2, cudaStream_t s, int V = 1,

@@ -2102,7 +2102,7 @@ static cudaError_t mg_setup(Solver* c) {
     const int Nf = 3 * c->n;
     std::vector<double> lamf, Vf;
     periodic_eigen(c->n, c->st, lamf, Vf);
-    if ((e = fdm_setup(H.fdm, Nf, lamf, Vf, !(c->cfg.flags & FEP3M_CUDA_CORES))) != cudaSuccess) return e;
+    if ((e = fdm_setup(H.fdm, Nf, lamf, Vf, c->nv, !(c->cfg.flags & FEP3M_CUDA_CORES))) != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
@@ -2538,6 +2538,7 @@ static void solver_plan_free(Solver* c) {
 // pieces in the layout of the tensor-core row GEMM (column tiles of nt modes,
 // chunks of 64 nodes).  Used by the order-3 fine level and the order-p mesh.
 cudaError_t fdm_setup(FineFDM& f, int Nf, const std::vector<double>& lamf, const std::vector<double>& Vf,
+                      int rhs,
                       bool tensor_cores, bool null_mode) {
   cudaError_t e;
   {
@@ -2558,11 +2559,14 @@ cudaError_t fdm_setup(FineFDM& f, int Nf, const std::vector<double>& lamf, const
     cudaMemcpy(f.lam32, lf32.data(), lf32.size() * 4, cudaMemcpyHostToDevice);
     f.N = Nf;
     if (tensor_cores) {
-      // column tiles of nt modes (a multiple of 16, <= 128: two CTAs per SM), enough tiles to give every
-      // SM a CTA (measured: tiles of 192 or 256 modes, one CTA per SM, read the input fewer times but were
-      // no faster at 128^3)
+      // column tiles of nt modes (a multiple of 16, <= 128: two CTAs per SM); where the rows are few, the
+      // tile count that brings a pass (rows x tiles x right-hand sides CTAs) nearest one CTA per SM
+      // (measured on the paired 32^3 solve: one tile of 96 modes, 144 CTAs, 0.629 ms a step against 0.656
+      // with three; tiles of 192 or 256 modes, one CTA per SM, read the input fewer times but were no
+      // faster at 128^3, nor one tile at 64^3)
       const int64_t rt = ((int64_t)Nf * Nf + 127) / 128;
-      int ntile = std::max<int>((Nf + 127) / 128, (int)((148 + rt - 1) / rt));
+      const int64_t rows = rt * std::max(1, rhs);
+      int ntile = std::max<int>((Nf + 127) / 128, (int)std::max<int64_t>(1, (152 + rows / 2) / rows));
       const int nt = ((Nf + ntile - 1) / ntile + 15) / 16 * 16;
       ntile = (Nf + nt - 1) / nt;
       const int kc = (Nf + 63) / 64;

@@ -438,7 +438,7 @@ int orderq_create(fep3m_ctx* c) {
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? FEP3M_ENOMEM : FEP3M_ECUDA;
   if (cudaMallocHost(&o->host_red, sizeof(double)) != cudaSuccess) return FEP3M_ENOMEM;
   cudaMemcpy(o->H, h.H.data(), h.H.size() * sizeof(double), cudaMemcpyHostToDevice);
-  e = fdm_setup(o->fdm, o->Np, h.lam, h.V, !(c->cfg.flags & FEP3M_CUDA_CORES));
+  e = fdm_setup(o->fdm, o->Np, h.lam, h.V, 1, !(c->cfg.flags & FEP3M_CUDA_CORES));
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? FEP3M_ENOMEM : FEP3M_ECUDA;
   const size_t smem = (size_t)(2 * c->n_sr + 1) * (2 * c->n_sr + 1) * Q1 * Q1 * Q1 * sizeof(double);
   if (cudaFuncSetAttribute(k_oq_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
