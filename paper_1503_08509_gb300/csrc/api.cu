@@ -212,7 +212,7 @@ void solve_stats(fep3m_ctx* c) {
 // for the device once the solvers are calibrated: the replayed solves'
 // residuals are checked by solves_missed after the caller's final
 // synchronisation.
-int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev) {
+int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev, double* U_dev = nullptr) {
   struct Restore {
     fep3m_ctx* c;
     cudaStream_t s;
@@ -267,6 +267,12 @@ int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev)
   ev_record(c, 10);
   CK(pair_eval(c, phi_dev, want_grad));
   ev_record(c, 3);
+  if (U_dev) {   // the energy on the pair stream (idle since the screen kernel), beside the force assembly
+    CK(cudaEventRecord(c->ev_pfork, c->stream));
+    CK(cudaStreamWaitEvent(c->pair_stream, c->ev_pfork, 0));
+    CK(energy(c, U_dev, c->pair_stream));
+    CK(cudaEventRecord(c->ev_pjoin, c->pair_stream));
+  }
   c->have_forward = true;
   c->have_grad = want_grad != 0;
   if (force_dev) {
@@ -277,6 +283,7 @@ int run_forward(fep3m_ctx* c, double* phi_dev, int want_grad, double* force_dev)
     CK(adjoint_final(c, 1.0, force_dev, nullptr, -1.0, c->stream));
     ev_record(c, 4);
   }
+  if (U_dev) CK(cudaStreamWaitEvent(c->stream, c->ev_pjoin, 0));
   CK(cudaEventRecord(c->ev_fjoin, c->stream));
   CK(cudaStreamWaitEvent(caller, c->ev_fjoin, 0));
   return FEP3M_OK;
@@ -469,6 +476,7 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
         (e = cudaMallocHost(&c->host_err, sizeof(int))) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&c->pair_stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c->ev_pfork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_pjoin, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c->ev_pcount, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaMallocHost(&c->host_cnt, 5 * sizeof(unsigned long long))) != cudaSuccess)
       return fail(from_cuda(e));
@@ -624,10 +632,15 @@ int fep3m_set_particles(fep3m_ctx* c, int64_t N, const double* pos, const double
   // the previous call's pair counts read the element counts this call rewrites
   CK(cudaStreamWaitEvent(c->stream, c->ev_pcount, 0));
   CK(cudaMemsetAsync(c->iflags, 0, sizeof(int), c->stream));
+  // the charge sums of the neutrality check on the pair stream, beside the binning (the sorted
+  // charges come from the binning's gather)
+  CK(cudaEventRecord(c->ev_pfork, c->stream));
+  CK(cudaStreamWaitEvent(c->pair_stream, c->ev_pfork, 0));
+  FEP3M_CL k_charge_sums<<<(unsigned)std::min<int64_t>(std::max<int64_t>(gsz(N) / 4, 1), 256), PT, 0,
+                           c->pair_stream>>>(N, dQ, (double*)c->red_tmp, c->red_counter, c->scal + 32);
+  CK(cudaEventRecord(c->ev_pjoin, c->pair_stream));
   CK(bin_particles(c, dpos, dQ, c->precision == FEP3M_MIXED));
-  CK(sorted_charges(c));
-  FEP3M_CL k_charge_sums<<<(unsigned)std::min<int64_t>(std::max<int64_t>(gsz(N) / 4, 1), 256), PT, 0, c->stream>>>(
-      N, dQ, (double*)c->red_tmp, c->red_counter, c->scal + 32);
+  CK(cudaStreamWaitEvent(c->stream, c->ev_pjoin, 0));
   ev_record(c, 7);
   c->counts_stale = true;   // pair statistics: counted when fep3m_get_stats asks for them
   double sums[2];
@@ -656,12 +669,10 @@ int fep3m_compute(fep3m_ctx* c, double* phi, double* U, double* force) {
   const bool fdev = force && is_device_ptr(force);
   double* fdst = force ? (fdev ? force : c->out_tmp + N) : nullptr;
   for (int attempt = 0;; ++attempt) {
-    int st = run_forward(c, phi_dev ? phi : (phi ? c->out_tmp : nullptr), force != nullptr, fdst);
+    int st = run_forward(c, phi_dev ? phi : (phi ? c->out_tmp : nullptr), force != nullptr, fdst,
+                         U ? c->scal + 40 : nullptr);
     if (st != FEP3M_OK) return st;
-    if (U) {
-      CK(energy(c, c->scal + 40));
-      CK(cudaMemcpyAsync(U, c->scal + 40, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    }
+    if (U) CK(cudaMemcpyAsync(U, c->scal + 40, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(c->host_err, c->iflags + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (*c->host_err) return FEP3M_ETIMEOUT;

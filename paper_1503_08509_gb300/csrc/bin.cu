@@ -154,11 +154,12 @@ __global__ void k_sort_segments(int64_t ne, const int* __restrict__ start, const
   }
 }
 
-// sorted structure of arrays: local coordinates t = delta / h + 1/2 in [0, 1] and Q
+// sorted structure of arrays: local coordinates t = delta / h + 1/2 in [0, 1] and Q, and the sorted
+// charges in FP64 as the working precision holds them (Qs)
 template <class T>
 __global__ void k_gather(int64_t N, int n, const int* __restrict__ perm, const int* __restrict__ cell,
                          const double* __restrict__ delta, const double* __restrict__ Q, double inv_h,
-                         typename vec4<T>::type* __restrict__ part, int* __restrict__ ecoord) {
+                         typename vec4<T>::type* __restrict__ part, int* __restrict__ ecoord, double* __restrict__ Qs) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= N) return;
   int i = perm[k];
@@ -170,6 +171,7 @@ __global__ void k_gather(int64_t N, int n, const int* __restrict__ perm, const i
   p.z = (T)(delta[3 * i + 2] * inv_h + 0.5);
   p.w = (T)Q[i];
   part[k] = p;
+  Qs[k] = (double)p.w;
 }
 
 }  // namespace
@@ -200,9 +202,11 @@ cudaError_t bin_particles(fep3m_ctx* c, const double* pos, const double* Q, int 
   FEP3M_CL k_scatter<<<gN, T, 0, s>>>(c->cell, c->N, c->start, c->fill, c->perm);
   FEP3M_CL k_sort_segments<<<gE, T, 0, s>>>(ne, c->start, c->count, c->perm);
   if (use_fp32)
-    FEP3M_CL k_gather<float><<<gN, T, 0, s>>>(c->N, c->n, c->perm, c->cell, c->delta, Q, c->inv_h, (float4*)c->part, c->ecoord);
+    FEP3M_CL k_gather<float><<<gN, T, 0, s>>>(c->N, c->n, c->perm, c->cell, c->delta, Q, c->inv_h, (float4*)c->part,
+                                              c->ecoord, c->Q_s);
   else
-    FEP3M_CL k_gather<double><<<gN, T, 0, s>>>(c->N, c->n, c->perm, c->cell, c->delta, Q, c->inv_h, (vec4<double>::type*)c->part, c->ecoord);
+    FEP3M_CL k_gather<double><<<gN, T, 0, s>>>(c->N, c->n, c->perm, c->cell, c->delta, Q, c->inv_h,
+                                               (vec4<double>::type*)c->part, c->ecoord, c->Q_s);
   return cudaGetLastError();
 }
 

@@ -448,7 +448,8 @@ cudaError_t adjoint_pre(fep3m_ctx* c, double gU, const double* gphi, cudaStream_
 cudaError_t adjoint_sweeps(fep3m_ctx* c, cudaStream_t s, bool singular);
 cudaError_t adjoint_vertex(fep3m_ctx* c, cudaStream_t s);
 cudaError_t adjoint_final(fep3m_ctx* c, double gU, double* dpos, double* dQ, double sign, cudaStream_t s);
-cudaError_t energy(fep3m_ctx* c, double* U_dev);
+// U = 1/2 sum Q phi on stream s (the context's stream when null)
+cudaError_t energy(fep3m_ctx* c, double* U_dev, cudaStream_t s = nullptr);
 // sum_j w_j / r and sum_j w_j (x_j - x_t) / r^3 over each target's block, j != t
 // (sorted order; physical units)
 cudaError_t singular_sums(fep3m_ctx* c, const double* w, double* psi, double* gpsi, cudaStream_t s);
@@ -457,7 +458,6 @@ int orderq_create(fep3m_ctx* c);
 void orderq_destroy(fep3m_ctx* c);
 int orderq_compute(fep3m_ctx* c, double* phi_dev, double* U_dev);
 int orderq_solve(fep3m_ctx* c, const double* b_dev, double* phi_dev);
-cudaError_t sorted_charges(fep3m_ctx* c);
 // the box (box.cu); n is the padded grid's, nb the box's elements per axis
 int box_create(fep3m_ctx* c, int nb, bool neumann);
 int64_t box_data_size(const fep3m_ctx* c);

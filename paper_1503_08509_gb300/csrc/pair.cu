@@ -1168,12 +1168,6 @@ __global__ void k_weights(int64_t N, double gU, const double* __restrict__ gphi,
   if (w32) w32[k] = (float)v;
 }
 
-template <class T>
-__global__ void k_charges(int64_t N, const typename vec4<T>::type* __restrict__ part, double* __restrict__ Qs) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  Qs[k] = (double)part[k].w;
-}
 
 // W[e][m] = sum_{t in e} w_t u_m(tau_t): the adjoint's point deposit, per
 // element.  wsum (FP32 path): sum_{t in e} w_t in FP64 as hi + lo floats, the
@@ -1810,19 +1804,10 @@ cudaError_t pair_eval(fep3m_ctx* c, double* phi_out, int want_grad) {
   return want_grad ? launch_pair_eval<double, true>(c, phi_out) : launch_pair_eval<double, false>(c, phi_out);
 }
 
-cudaError_t sorted_charges(fep3m_ctx* c) {
-  const int64_t N = c->N;
-  if (c->precision == FEP3M_MIXED)
-    FEP3M_CL k_charges<float><<<gsz(N), PT, 0, c->stream>>>(N, (const float4*)c->part, c->Q_s);
-  else
-    FEP3M_CL k_charges<double><<<gsz(N), PT, 0, c->stream>>>(N, (const vec4<double>::type*)c->part, c->Q_s);
-  return cudaGetLastError();
-}
-
-cudaError_t energy(fep3m_ctx* c, double* U_dev) {
+cudaError_t energy(fep3m_ctx* c, double* U_dev, cudaStream_t s) {
   const int64_t N = c->N;
   const int nb = (int)std::min<int64_t>(std::max<int64_t>(gsz(N), 1), 1024);
-  FEP3M_CL k_energy<<<nb, PT, 0, c->stream>>>(N, c->Q_s, c->phi_s, (double*)c->red_tmp, c->red_counter, U_dev);
+  FEP3M_CL k_energy<<<nb, PT, 0, s ? s : c->stream>>>(N, c->Q_s, c->phi_s, (double*)c->red_tmp, c->red_counter, U_dev);
   return cudaGetLastError();
 }
 
