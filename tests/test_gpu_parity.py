@@ -119,6 +119,20 @@ def test_coefficients_and_load_vector(api, name):
     assert maxrel(m["phi_mesh"], pm) < 1e-11
 
 
+@pytest.mark.parametrize("name", ["uniform1k", "blobs3k"])
+def test_mixed_mesh_vectors(api, name):
+    """The mixed path keeps the load vector and the mesh potential as float pairs on the device;
+    fep3m_get_mesh returns them in FP64.  The load vector follows FP32 vertex densities (single
+    rounding per value); the mesh potential carries the FP32 screen coefficients as well."""
+    d, ref, _ = oracle(name)
+    r = run(api, d, "mixed", forces=True)
+    m = r["eng"].mesh()
+    bref = ref["b"].transpose(2, 1, 0).ravel()
+    assert maxrel(m["b"], bref) < 1e-6
+    pm = ref["phi_mesh"].transpose(2, 1, 0).ravel()
+    assert maxrel(m["phi_mesh"], pm) < 1e-6
+
+
 # solver: the FP32 inner solve of the refinement, exact by fast diagonalisation
 # (the default) or multigrid-preconditioned CG
 @pytest.mark.parametrize("solver", ["fdm", "multigrid"])
