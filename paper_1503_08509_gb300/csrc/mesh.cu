@@ -605,7 +605,11 @@ __device__ __forceinline__ T apply_epilogue(int64_t g, T y, T bg, T dg, T xg, T*
 // then block_sum_finish with dt (partials indexed by the block's linear id
 // within its vector; vector v's partials, counter and total at
 // dt.partials + v nblocks, dt.counter + v, dt.out + 64 v).
-template <class T, int EPI, bool DOT = false>
+//
+// F32IN (dfv, EPI_RESID: the first refinement sweep, whose iterate is the
+// FP32 correction e over the power-of-two scale s): x points at e (floats),
+// the apply reads the pairs (e / s, 0) and writes them to xo as the iterate.
+template <class T, int EPI, bool DOT = false, bool F32IN = false>
 __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
     k_apply_el(int N, int steps, const T* __restrict__ x, T* __restrict__ out, const T* __restrict__ b,
                T* __restrict__ d, T* __restrict__ xo, T c0, T c1, T c2, double* __restrict__ scal, ApplyDot dt,
@@ -613,6 +617,7 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
   PDL_PROLOGUE
   static_assert(!DOT || EPI == EPI_Y || EPI == EPI_CHEB || (EPI == EPI_RESID && std::is_same<T, dfv>::value),
                 "fused dots: EPI_Y, EPI_CHEB and the double-float residual");
+  static_assert(!F32IN || (EPI == EPI_RESID && std::is_same<T, dfv>::value), "FP32 input: the double-float residual");
   extern __shared__ __align__(16) unsigned char apply_smem_raw[];
   ApplySmem<T, EPI, DOT>& S = *reinterpret_cast<ApplySmem<T, EPI, DOT>*>(apply_smem_raw);
   constexpr int NST = apply_nst<T, EPI, DOT>();
@@ -626,7 +631,8 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
   const int e0 = ((int)blockIdx.z - vi * zsb) * steps, e1 = min(n, e0 + steps);
   if (vi > 0) {
     const int64_t o = vi * vs;
-    x += o;
+    if constexpr (F32IN) x = reinterpret_cast<const T*>(reinterpret_cast<const float*>(x) + o);
+    else x += o;
     if constexpr (EPI == EPI_RESID && !std::is_same<T, float>::value)
       out = reinterpret_cast<T*>(reinterpret_cast<float*>(out) + o);   // the FP32 residual
     else
@@ -639,6 +645,13 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
   const int tid = threadIdx.x;
   float rs = 0.0f;   // power-of-two scale of the refinement residual (FP64, double-float)
   if constexpr (!std::is_same<T, float>::value) rs = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_SCALE];
+  float ris = 0.0f;  // F32IN: 1 / s
+  if constexpr (F32IN) ris = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_INVSCALE];
+  const float* xf = reinterpret_cast<const float*>(x);   // F32IN: the correction e
+  auto ldx = [&](int64_t off) -> T {
+    if constexpr (F32IN) return T{xf[off] * ris, 0.f};
+    else return x[off];
+  };
   if constexpr (!std::is_same<T, dfv>::value) {
     if (tid < 27) S.dinv[tid] = Cst<T>::Dinv(tid);
   }
@@ -672,10 +685,9 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
   for (int s = 0; s < 7; ++s) {
     int zz = zs + s;
     if (zz >= N) zz -= N;
-    const T* xp = x + zz * NN;
 #pragma unroll
     for (int k = 0; k < APL; ++k) {
-      w[k][s] = xp[coff[k]];
+      w[k][s] = ldx(zz * NN + coff[k]);
       if (EPI == EPI_CHEB0) w[k][s] *= fs[k][s % 3];
     }
   }
@@ -694,9 +706,8 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
       for (int s = 0; s < 3; ++s) {
         int zz = zs + 7 + s;
         if (zz >= N) zz -= N;
-        const T* xp = x + zz * NN;
 #pragma unroll
-        for (int k = 0; k < APL; ++k) nx[k][s] = xp[coff[k]];
+        for (int k = 0; k < APL; ++k) nx[k][s] = ldx(zz * NN + coff[k]);
       }
     }
     if (EPI == EPI_CHEB0 && e > e0) {   // planes 3e + 1 .. 3e + 3 arrived in the previous round
@@ -782,6 +793,7 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
           if constexpr (EPI == EPI_CHEB && NST == 2) xg = x[g + r];
           float rsd = 0.f;
           const T f = apply_epilogue<T, EPI>(g + r, y[r], bg, dg, xg, out, d, xo, c0, c1, c2, dv[r], rs, rsd);
+          if constexpr (F32IN) xo[g + r] = T{xf[g + r] * ris, 0.f};   // the iterate after the first sweep
           if constexpr (DOT && EPI == EPI_RESID) dres = fmaf(rsd, rsd, dres);
           else if constexpr (DOT) dsum = r == 0 ? bg * f : dsum + bg * f;   // EPI_Y stages x in the b slot
         }
@@ -812,9 +824,9 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
   }
 }
 
-template <class T, int EPI, bool DOT = false>
+template <class T, int EPI, bool DOT = false, bool F32IN = false>
 static cudaError_t apply_set_smem_one() {
-  return cudaFuncSetAttribute(k_apply_el<T, EPI, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_apply_el<T, EPI, DOT, F32IN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(ApplySmem<T, EPI, DOT>));
 }
 
@@ -829,6 +841,8 @@ static cudaError_t apply_set_smem() {
   if (e == cudaSuccess) e = apply_set_smem_one<double, EPI_RESID>();
   if (e == cudaSuccess) e = apply_set_smem_one<dfv, EPI_RESID>();
   if (e == cudaSuccess) e = apply_set_smem_one<dfv, EPI_RESID, true>();
+  if (e == cudaSuccess) e = apply_set_smem_one<dfv, EPI_RESID, false, true>();
+  if (e == cudaSuccess) e = apply_set_smem_one<dfv, EPI_RESID, true, true>();
   // coarsest-level kernels at N = CP_MAX
   const int smp = 3 * CP_MAX * (CP_MAX + 1) * (int)sizeof(float);
   const int smq = (2 * CP_MAX * (CP_MAX + 1) + 2 * CP_MAX * (CP_PEN + 1)) * (int)sizeof(float);
@@ -1457,10 +1471,9 @@ __global__ void k_round_scaled_norm(int64_t n, const double* __restrict__ v, flo
   block_sum_finish(acc, blockIdx.x, gridDim.x, partials, counter, out, POST_NONE, 0.0, scal);
 }
 
-// phi += e / s (exact: s is a power of two), two-sum then renormalised;
-// first: phi = e / s (the first sweep, from phi = 0)
+// phi += e / s (exact: s is a power of two), two-sum then renormalised
 __global__ void k_df_update(int64_t n, dfv* __restrict__ phi, const float* __restrict__ e,
-                            const double* __restrict__ scal, int64_t vs, int first) {
+                            const double* __restrict__ scal, int64_t vs) {
   PDL_PROLOGUE
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n) return;
@@ -1469,10 +1482,6 @@ __global__ void k_df_update(int64_t n, dfv* __restrict__ phi, const float* __res
   scal += 64 * blockIdx.y;
   const float is = reinterpret_cast<const float*>(scal + SC_DERIVED_F)[SD_INVSCALE];
   const float t = e[g] * is;
-  if (first) {   // from phi = 0: exactly e / s
-    phi[g] = {t, 0.f};
-    return;
-  }
   dfv p = phi[g];
   const float sum = p.h + t;
   const float bv = sum - p.h;
@@ -2162,8 +2171,11 @@ static cudaError_t ensure_solver_buffers(Solver* c) {
 //   FP64:  Pi b in res64 and the iterate in the output buffer, FP64
 
 // r = s (Pi b - K phi) in FP32; norm_out (MIXED): |r|^2 accumulated by the
-// apply into norm_out (per right-hand side at norm_out + 64 v)
-static cudaError_t refine_resid(Solver* c, const double* phi64, float* r, double* norm_out = nullptr) {
+// apply into norm_out (per right-hand side at norm_out + 64 v); e_first
+// (MIXED, the first sweep): phi is e_first / s, read from the FP32
+// correction and written to the iterate by the apply (no update launch)
+static cudaError_t refine_resid(Solver* c, const double* phi64, float* r, double* norm_out = nullptr,
+                                const float* e_first = nullptr) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
   const int steps = apply_steps(N);
@@ -2173,6 +2185,20 @@ static cudaError_t refine_resid(Solver* c, const double* phi64, float* r, double
   if (c->precision == FEP3M_FP64) {
     launch_pdl(k_apply_el<double, EPI_RESID>, grid, AT, sizeof(ApplySmem<double, EPI_RESID>), c->stream, N, steps,
                phi64, reinterpret_cast<double*>(r), c->res64, nullptr, nullptr, 0.0, 0.0, 0.0, c->scal, nd, c->vs);
+  } else if (e_first) {
+    const dfv z = {0.0f, 0.0f};
+    const dfv* xin = reinterpret_cast<const dfv*>(e_first);   // read as floats (F32IN)
+    dfv* it = reinterpret_cast<dfv*>(c->phidf);
+    if (norm_out) {
+      const ApplyDot dt = {(double*)c->red_tmp, c->red_counter, norm_out, POST_NONE};
+      launch_pdl(k_apply_el<dfv, EPI_RESID, true, true>, grid, AT, sizeof(ApplySmem<dfv, EPI_RESID, true>),
+                 c->stream, N, steps, xin, reinterpret_cast<dfv*>(r), reinterpret_cast<const dfv*>(c->res64),
+                 (dfv*)nullptr, it, z, z, z, c->scal, dt, c->vs);
+    } else {
+      launch_pdl(k_apply_el<dfv, EPI_RESID, false, true>, grid, AT, sizeof(ApplySmem<dfv, EPI_RESID>), c->stream,
+                 N, steps, xin, reinterpret_cast<dfv*>(r), reinterpret_cast<const dfv*>(c->res64), (dfv*)nullptr,
+                 it, z, z, z, c->scal, nd, c->vs);
+    }
   } else if (norm_out) {
     const dfv z = {0.0f, 0.0f};
     const ApplyDot dt = {(double*)c->red_tmp, c->red_counter, norm_out, POST_NONE};
@@ -2219,15 +2245,14 @@ static void refine_setup(Solver* c, const double* b, double* phi64, float* r) {
              c->red_counter, sc + 10, sc, vs);
 }
 
-// phi += e / s (first: the first sweep; MIXED assigns phi = e / s)
-static void refine_update(Solver* c, double* phi64, const float* e, bool first) {
+// phi += e / s (MIXED: after the first sweep, whose apply formed phi)
+static void refine_update(Solver* c, double* phi64, const float* e) {
   const size_t n = c->mg.lv[0].size;
   const dim3 g((unsigned)grid_for(n), (unsigned)c->V);
   if (c->precision == FEP3M_FP64)
     launch_pdl(k_add_scaled, g, TPB, 0, c->stream, (int64_t)n, phi64, e, c->scal, c->vs);
   else
-    launch_pdl(k_df_update, g, TPB, 0, c->stream, (int64_t)n, reinterpret_cast<dfv*>(c->phidf), e, c->scal, c->vs,
-               first ? 1 : 0);
+    launch_pdl(k_df_update, g, TPB, 0, c->stream, (int64_t)n, reinterpret_cast<dfv*>(c->phidf), e, c->scal, c->vs);
 }
 
 // end: phi with mean zero (FP64; MIXED: float pairs)
@@ -2289,10 +2314,12 @@ static cudaError_t solve_checked(Solver* c, const double* b, double* phi, int* i
     else it = mg.pcg(r32, e32, (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], 1e-5, 30, &inner_res);
     *iters += it;
     *k_inner_max = std::max(*k_inner_max, it);
-    refine_update(c, phi, e32, step == 0);
+    // MIXED, first sweep: the residual's apply forms the iterate e / s itself
+    const bool first_df = c->precision != FEP3M_FP64 && step == 0;
+    if (!first_df) refine_update(c, phi, e32);
     // the residual's sum is rounding noise (K has zero column sums), and the
     // inner solve projects its right-hand side: no projection here
-    cudaError_t e = refine_resid(c, phi, r32);
+    cudaError_t e = refine_resid(c, phi, r32, nullptr, first_df ? e32 : nullptr);
     if (e != cudaSuccess) return e;
     reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 9);
     cudaMemcpyAsync(&rr, sc + 9, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -2327,9 +2354,11 @@ static cudaError_t solve_fixed(Solver* c, const double* b, double* phi, int kout
     if (c->mg.fdm.N > 0) mg.fdm_solve(r32, e32, (float*)sb[0], (float*)sb[1]);
     else mg.pcg_fixed(r32, e32, (float*)sb[0], (float*)sb[1], (float*)sb[2], (float*)sb[3], c->plan_kin);
     if (step == 0 && c->ev_in1) cudaEventRecordWithFlags(c->ev_in1, c->stream, cudaEventRecordExternal);
-    refine_update(c, phi, e32, step == 0);
-    // MIXED: the last residual's |r|^2 accumulated by its apply
-    cudaError_t e = refine_resid(c, phi, r32, mixed && step == kout - 1 ? sc + 11 : nullptr);
+    // MIXED: the first sweep's apply forms the iterate e / s itself, and the
+    // last residual's |r|^2 is accumulated by its apply
+    const bool first_df = mixed && step == 0;
+    if (!first_df) refine_update(c, phi, e32);
+    cudaError_t e = refine_resid(c, phi, r32, mixed && step == kout - 1 ? sc + 11 : nullptr, first_df ? e32 : nullptr);
     if (e != cudaSuccess) return e;
   }
   if (mixed && kout == 0)
