@@ -447,12 +447,61 @@ __device__ void block_sum_finish_df(dfv acc, unsigned bid, unsigned nblocks, dou
                      post, arg, scal);
 }
 
-// a dot product accumulated by an apply: block partials, counter, total, post
+// Two block-then-grid sums at once (blockDim.x == 256) of float-pair values:
+// the block sums as float pairs, its totals (FP64) go to partials[2 bid],
+// partials[2 bid + 1]; the last block adds the partials in index order and
+// returns true on its thread 0 with the totals in ta, tb.
+__device__ bool block_sum2_finish(dfv a2, dfv b2, unsigned bid, unsigned nblocks, double* __restrict__ partials,
+                                  unsigned int* __restrict__ counter, double& ta, double& tb) {
+  __shared__ double sh[2][8];
+  __shared__ bool last;
+  a2 = block_sum_df(a2);
+  __syncthreads();   // block_sum_df's shared slots are reused by the second sum
+  b2 = block_sum_df(b2);
+  if (threadIdx.x == 0) {
+    partials[2 * bid] = (double)a2.h + (double)a2.l;
+    partials[2 * bid + 1] = (double)b2.h + (double)b2.l;
+    __threadfence();
+    const unsigned int done = atomicAdd(counter, 1u);
+    last = (done == nblocks - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s0 = 0, s1 = 0;
+  for (unsigned int k = threadIdx.x; k < nblocks; k += blockDim.x) {
+    s0 += ((volatile double*)partials)[2 * k];
+    s1 += ((volatile double*)partials)[2 * k + 1];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = s0;
+    sh[1][threadIdx.x >> 5] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return false;
+  ta = tb = 0;
+  for (int k = 0; k < 8; ++k) {
+    ta += sh[0][k];
+    tb += sh[1][k];
+  }
+  *counter = 0u;
+  return true;
+}
+
+// a dot product accumulated by an apply: block partials, counter, total, post;
+// wout (the double-float residual's last apply): also the iterate's integral
+// sum w3 phi into *wout, with its mean (times invW) derived as POST_MEAN does
 struct ApplyDot {
   double* partials;
   unsigned int* counter;
   double* out;
   int post;
+  double* wout = nullptr;
+  double invW = 0.0;
 };
 
 
@@ -622,7 +671,8 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
   ApplySmem<T, EPI, DOT>& S = *reinterpret_cast<ApplySmem<T, EPI, DOT>*>(apply_smem_raw);
   constexpr int NST = apply_nst<T, EPI, DOT>();
   double dacc = 0.0;
-  float facc = 0.f;   // EPI_RESID dot: |r|^2 in FP32
+  float facc = 0.f;          // EPI_RESID dot: |r|^2 in FP32
+  dfv wacc = {0.f, 0.f};     // EPI_RESID dot with dt.wout: the iterate's integral
   const int n = N / 3;
   const int64_t NN = (int64_t)N * N;
   const int x0 = blockIdx.x * AFX, y0 = blockIdx.y * AFY;
@@ -794,6 +844,14 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
           float rsd = 0.f;
           const T f = apply_epilogue<T, EPI>(g + r, y[r], bg, dg, xg, out, d, xo, c0, c1, c2, dv[r], rs, rsd);
           if constexpr (F32IN) xo[g + r] = T{xf[g + r] * ris, 0.f};   // the iterate after the first sweep
+          if constexpr (DOT && EPI == EPI_RESID) {
+            if (dt.wout) {   // the node weight (1/4 or 3/8 per axis) times the iterate, as a two-product
+              const float wn = (r ? 0.375f : 0.25f) * (ty3 ? 0.375f : 0.25f) * (p ? 0.375f : 0.25f);
+              const T xv = ldx(g + r);
+              const float pr = wn * xv.h;
+              wacc += dfv{pr, fmaf(wn, xv.l, fmaf(wn, xv.h, -pr))};
+            }
+          }
           if constexpr (DOT && EPI == EPI_RESID) dres = fmaf(rsd, rsd, dres);
           else if constexpr (DOT) dsum = r == 0 ? bg * f : dsum + bg * f;   // EPI_Y stages x in the b slot
         }
@@ -815,10 +873,25 @@ __global__ void __launch_bounds__(AT, sizeof(T) == 4 ? 3 : 2)
   if constexpr (DOT) {
     const unsigned nbv = gridDim.x * gridDim.y * zsb;   // blocks per vector
     const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * (blockIdx.z - vi * zsb));
-    if constexpr (EPI == EPI_RESID)
-      block_sum_finish_df(dfv{facc, 0.f}, bid, nbv, dt.partials + (size_t)vi * nbv, dt.counter + vi,
-                          dt.out + 64 * vi, dt.post, 0.0, scal);
-    else
+    if constexpr (EPI == EPI_RESID) {
+      if (dt.wout) {   // two totals: |r|^2 and the integral (partials two per block)
+        double tr, tw;
+        if (block_sum2_finish(dfv{facc, 0.f}, wacc, bid, nbv, dt.partials + (size_t)vi * 2 * nbv, dt.counter + vi,
+                              tr, tw)) {
+          dt.out[64 * vi] = tr;
+          dt.wout[64 * vi] = tw;
+          double* dd = scal + SC_DERIVED;
+          float* dfs = (float*)(scal + SC_DERIVED_F);
+          const double m = tw * dt.invW;
+          dd[SD_MEAN] = m;
+          dfs[SD_MEAN] = (float)m;
+          dfs[SD_MEANLO] = (float)(m - (double)(float)m);
+        }
+      } else {
+        block_sum_finish_df(dfv{facc, 0.f}, bid, nbv, dt.partials + (size_t)vi * nbv, dt.counter + vi,
+                            dt.out + 64 * vi, dt.post, 0.0, scal);
+      }
+    } else
       block_sum_finish(dacc, bid, nbv, dt.partials + (size_t)vi * nbv, dt.counter + vi, dt.out + 64 * vi, dt.post,
                        0.0, scal);
   }
@@ -1510,51 +1583,6 @@ __device__ __forceinline__ dfv df_scaled(float mh, float ml, float w) {
   return {p, fmaf(ml, w, fmaf(mh, w, -p))};
 }
 
-// Two block-then-grid sums at once (blockDim.x == 256) of float-pair values:
-// the block sums as float pairs, its totals (FP64) go to partials[2 bid],
-// partials[2 bid + 1]; the last block adds the partials in index order and
-// returns true on its thread 0 with the totals in ta, tb.
-__device__ bool block_sum2_finish(dfv a2, dfv b2, unsigned bid, unsigned nblocks, double* __restrict__ partials,
-                                  unsigned int* __restrict__ counter, double& ta, double& tb) {
-  __shared__ double sh[2][8];
-  __shared__ bool last;
-  a2 = block_sum_df(a2);
-  __syncthreads();   // block_sum_df's shared slots are reused by the second sum
-  b2 = block_sum_df(b2);
-  if (threadIdx.x == 0) {
-    partials[2 * bid] = (double)a2.h + (double)a2.l;
-    partials[2 * bid + 1] = (double)b2.h + (double)b2.l;
-    __threadfence();
-    const unsigned int done = atomicAdd(counter, 1u);
-    last = (done == nblocks - 1);
-  }
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-  double s0 = 0, s1 = 0;
-  for (unsigned int k = threadIdx.x; k < nblocks; k += blockDim.x) {
-    s0 += ((volatile double*)partials)[2 * k];
-    s1 += ((volatile double*)partials)[2 * k + 1];
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 += __shfl_down_sync(0xffffffffu, s0, o);
-    s1 += __shfl_down_sync(0xffffffffu, s1, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    sh[0][threadIdx.x >> 5] = s0;
-    sh[1][threadIdx.x >> 5] = s1;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return false;
-  ta = tb = 0;
-  for (int k = 0; k < 8; ++k) {
-    ta += sh[0][k];
-    tb += sh[1][k];
-  }
-  *counter = 0u;
-  return true;
-}
-
 // setup, first pass: sum b into scal[5] with the mean m = sum b / W derived,
 // sum b^2 into scal[7] with the scale s = 2^-k, 2^k near the RMS
 // sqrt(sum b^2 / n), derived (the POST_MEAN and POST_SCALE forms)
@@ -2170,12 +2198,18 @@ static cudaError_t ensure_solver_buffers(Solver* c) {
 //   MIXED: Pi b in res64 and the iterate in phidf, as float pairs
 //   FP64:  Pi b in res64 and the iterate in the output buffer, FP64
 
+// 1 / W (W = n^3 elements): the mean's factor of the integral
+static double apply_invW(const Solver* c) {
+  const Level& L0 = c->mg.lv[0];
+  return 1.0 / ((double)L0.n * L0.n * L0.n);
+}
+
 // r = s (Pi b - K phi) in FP32; norm_out (MIXED): |r|^2 accumulated by the
 // apply into norm_out (per right-hand side at norm_out + 64 v); e_first
 // (MIXED, the first sweep): phi is e_first / s, read from the FP32
 // correction and written to the iterate by the apply (no update launch)
 static cudaError_t refine_resid(Solver* c, const double* phi64, float* r, double* norm_out = nullptr,
-                                const float* e_first = nullptr) {
+                                const float* e_first = nullptr, double* wsum_out = nullptr) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
   const int steps = apply_steps(N);
@@ -2190,7 +2224,7 @@ static cudaError_t refine_resid(Solver* c, const double* phi64, float* r, double
     const dfv* xin = reinterpret_cast<const dfv*>(e_first);   // read as floats (F32IN)
     dfv* it = reinterpret_cast<dfv*>(c->phidf);
     if (norm_out) {
-      const ApplyDot dt = {(double*)c->red_tmp, c->red_counter, norm_out, POST_NONE};
+      const ApplyDot dt = {(double*)c->red_tmp, c->red_counter, norm_out, POST_NONE, wsum_out, apply_invW(c)};
       launch_pdl(k_apply_el<dfv, EPI_RESID, true, true>, grid, AT, sizeof(ApplySmem<dfv, EPI_RESID, true>),
                  c->stream, N, steps, xin, reinterpret_cast<dfv*>(r), reinterpret_cast<const dfv*>(c->res64),
                  (dfv*)nullptr, it, z, z, z, c->scal, dt, c->vs);
@@ -2201,7 +2235,7 @@ static cudaError_t refine_resid(Solver* c, const double* phi64, float* r, double
     }
   } else if (norm_out) {
     const dfv z = {0.0f, 0.0f};
-    const ApplyDot dt = {(double*)c->red_tmp, c->red_counter, norm_out, POST_NONE};
+    const ApplyDot dt = {(double*)c->red_tmp, c->red_counter, norm_out, POST_NONE, wsum_out, apply_invW(c)};
     launch_pdl(k_apply_el<dfv, EPI_RESID, true>, grid, AT, sizeof(ApplySmem<dfv, EPI_RESID, true>), c->stream, N,
                steps, reinterpret_cast<const dfv*>(c->phidf), reinterpret_cast<dfv*>(r),
                reinterpret_cast<const dfv*>(c->res64), nullptr, nullptr, z, z, z, c->scal, dt, c->vs);
@@ -2255,15 +2289,17 @@ static void refine_update(Solver* c, double* phi64, const float* e) {
     launch_pdl(k_df_update, g, TPB, 0, c->stream, (int64_t)n, reinterpret_cast<dfv*>(c->phidf), e, c->scal, c->vs);
 }
 
-// end: phi with mean zero (FP64; MIXED: float pairs)
-static void refine_finish(Solver* c, double* phi) {
+// end: phi with mean zero (FP64; MIXED: float pairs); have_mean: the last
+// residual apply already summed the integral and derived the mean
+static void refine_finish(Solver* c, double* phi, bool have_mean = false) {
   const Level& L0 = c->mg.lv[0];
   const int N = L0.N;
   const size_t n = L0.size;
   const double W = (double)L0.n * L0.n * L0.n;
   if (c->precision != FEP3M_FP64) {
     const dfv* v = reinterpret_cast<const dfv*>(c->phidf);
-    launch_pdl(k_ref_wsum, dim3((unsigned)reduce_blocks(n), (unsigned)c->V), TPB, 0, c->stream, N, v,
+    if (!have_mean)
+      launch_pdl(k_ref_wsum, dim3((unsigned)reduce_blocks(n), (unsigned)c->V), TPB, 0, c->stream, N, v,
                (double*)c->red_tmp, c->red_counter, c->scal, 1.0 / W, c->vs);
     launch_pdl(k_ref_out, dim3((unsigned)grid_for(n), (unsigned)c->V), TPB, 0, c->stream, (int64_t)n, v,
                reinterpret_cast<dfv*>(phi), (const double*)c->scal, c->vs);
@@ -2358,13 +2394,14 @@ static cudaError_t solve_fixed(Solver* c, const double* b, double* phi, int kout
     // last residual's |r|^2 is accumulated by its apply
     const bool first_df = mixed && step == 0;
     if (!first_df) refine_update(c, phi, e32);
-    cudaError_t e = refine_resid(c, phi, r32, mixed && step == kout - 1 ? sc + 11 : nullptr, first_df ? e32 : nullptr);
+    const bool last = mixed && step == kout - 1;   // also the iterate's integral, for the finish
+    cudaError_t e = refine_resid(c, phi, r32, last ? sc + 11 : nullptr, first_df ? e32 : nullptr, last ? sc + 6 : nullptr);
     if (e != cudaSuccess) return e;
   }
   if (mixed && kout == 0)
     cudaMemsetAsync(c->phidf, 0, (c->V > 1 ? c->V * c->vs : (int64_t)L0.size) * sizeof(dfv), c->stream);
   if (!mixed || kout == 0) reduce<float>(c, N, RD_NORM2, r32, nullptr, sc + 11);
-  refine_finish(c, phi);
+  refine_finish(c, phi, mixed && kout > 0);
   return cudaGetLastError();
 }
 
@@ -2683,13 +2720,13 @@ cudaError_t solver_init(Solver* s, const fep3m_ctx* c, cudaStream_t stream, int 
   const size_t nodes = (size_t)27 * c->n * c->n * c->n;
   cudaError_t e;
   // per right-hand side: a block of 64 scalars, the reduction partials (one per block of
-  // k_reduce (<= 608), two per block of k_ref_split_sums, one per block of a fine-level apply
+  // k_reduce (<= 608), two per block of k_ref_sums, up to two per block of a fine-level apply
   // with a fused dot), a counter, res64 and phidf
   if ((e = cudaMalloc(&s->scal, nv * 64 * sizeof(double))) != cudaSuccess) return e;
   {
     const int N0 = 3 * c->n;
     const dim3 g = apply_grid(N0, apply_steps(N0));
-    const size_t nb = std::max<size_t>(2 * 608, (size_t)g.x * g.y * g.z);
+    const size_t nb = std::max<size_t>(2 * 608, 2 * (size_t)g.x * g.y * g.z);
     if ((e = cudaMalloc(&s->red_tmp, nv * nb * sizeof(double))) != cudaSuccess) return e;
   }
   if ((e = cudaMalloc(&s->red_counter, nv * sizeof(unsigned int))) != cudaSuccess) return e;
