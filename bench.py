@@ -36,7 +36,7 @@ L2_FLUSH_BYTES = 256 << 20
 # mesh solve (k_tc_rows, both right-hand sides) on this workload, from the ncu captures summarised in
 # profiles/ (None until one is taken of the current kernel)
 PAIR_DRAM_BYTES = 2264320 + 1536
-PASS_DRAM_BYTES = 7187456 + 0
+PASS_DRAM_BYTES = 7187200 + 0
 
 
 def parse():
