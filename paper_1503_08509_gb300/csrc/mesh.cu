@@ -1240,6 +1240,16 @@ __global__ void __launch_bounds__(256) k_fdm_axis(int N, const float* __restrict
 // inverse eigenvalue sums, rows r = j + N k) and for the screen adjoint's
 // contraction (R elements, K = 64 nodes, NC offsets).  err: a bounded wait
 // that gave up.  gridDim.y vectors at a stride of vs values (in and out).
+// one hardware reciprocal (within an ulp or two): the scaling pass divides each
+// mode by its eigenvalue sum, and the inner solve's accuracy is set by the
+// conditioning of the correction it returns (relative 1e-7 ... 1e-4 per
+// refinement sweep), far above that rounding
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 constexpr int FT_THREADS = 256;
 
 template <bool SCALE>
@@ -1368,7 +1378,7 @@ __global__ void __launch_bounds__(FT_THREADS) k_tc_rows(int64_t R, int K, int cb
           const int i = n0 + 16 * grp + t;
           if (i < cb || i >= ce || 16 * grp + t >= nt) continue;
           float v = __uint_as_float(vh[t]) + __uint_as_float(vl[t]);
-          if (SCALE) v = (jk_null && i == null_mode) ? 0.f : v * __frcp_rn(lam[i] + djk);
+          if (SCALE) v = (jk_null && i == null_mode) ? 0.f : v * rcp_approx(lam[i] + djk);
           out[(int64_t)(i - cb) * R + r] = v;
         }
       }
