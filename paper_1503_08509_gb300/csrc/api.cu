@@ -574,8 +574,11 @@ int fep3m_create(const fep3m_config* cfg, void* stream, fep3m_ctx** out) {
   // paired mesh solve takes both at one stride
   c->g64 = c->b64 + nodes;
   c->lam64 = c->phi64 + nodes;
-  if (c->precision == FEP3M_MIXED && ((e = cudaMalloc(&c->phi_hl, nodes * 2 * sizeof(float))) != cudaSuccess ||
-                                      (e = cudaMalloc(&c->Wsum, ne * sizeof(float2))) != cudaSuccess))
+  // MIXED: the element weight sums; a box's hi + lo copy of its FP64 mesh potential (the periodic
+  // solver's output is float pairs already)
+  if (c->precision == FEP3M_MIXED &&
+      ((box && (e = cudaMalloc(&c->phi_hl, nodes * 2 * sizeof(float))) != cudaSuccess) ||
+       (e = cudaMalloc(&c->Wsum, ne * sizeof(float2))) != cudaSuccess))
     return fail(from_cuda(e));
   cudaMemset(c->red_counter, 0, sizeof(unsigned int));
   cudaMemset(c->iflags, 0, 16 * sizeof(int));
