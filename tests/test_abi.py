@@ -55,3 +55,35 @@ def test_create_rejects_bad_config_before_touching_the_gpu(lib):
         cfg = _lib.Config(**base)
         assert lib.fep3m_create(ctypes.byref(cfg), None, ctypes.byref(h)) == _lib.FEP3M_EINVAL
         assert not h.value
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of fep3m_config and fep3m_stats have the header's size and field offsets
+    (a C program built against include/fep3m.h prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1503_08509_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "fep3m.h"', "int main(void) {"]
+    for cname, py in (("fep3m_config", _lib.Config), ("fep3m_stats", _lib.Stats)):
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln.strip():
+            name, field, val = ln.split()
+            got[(name, field)] = int(val)
+    for cname, py in (("fep3m_config", _lib.Config), ("fep3m_stats", _lib.Stats)):
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
