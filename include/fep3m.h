@@ -30,8 +30,14 @@
  *   - Ownership: the caller owns every buffer it passes; the library owns all
  *     of its scratch (allocated in fep3m_create / grown in
  *     fep3m_set_particles) and frees it in fep3m_destroy.
- *   - Streams: all device work is issued on the stream given to
- *     fep3m_create, in order; calls returning host values synchronise it.
+ *   - Streams: all device work is ordered on the stream given to
+ *     fep3m_create: a call's work starts after the work queued there before
+ *     it, and work queued there after the call starts after the call's work.
+ *     Inside fep3m_set_particles and fep3m_compute (periodic, q = 1) the
+ *     library forks its work onto streams of its own (the forward chain at
+ *     the device's highest priority, the short-range kernels one level below,
+ *     the adjoint chain and its sweeps) and joins them back to that stream.
+ *     Calls returning host values synchronise it.
  *   - A context is not thread-safe; use one per host thread.
  *   - Reproducibility: fep3m_compute and fep3m_vjp are bitwise reproducible
  *     for the same inputs, configuration and GPU model: their only atomics
@@ -205,8 +211,9 @@ int fep3m_set_particles(fep3m_ctx* ctx, int64_t N, const double* pos, const doub
 
 /* Phi_i (N, host or device; may be NULL) and U (host scalar; may be NULL) for
  * the charges last set.  force (N x 3, host or device, or NULL) receives
- * -dU/dx_i; computing it runs the adjoint (one more mesh solve; q = 1 only,
- * FEP3M_EINVAL for q >= 2).
+ * -dU/dx_i; computing it runs the adjoint (a second mesh right-hand side,
+ * which the tensor-core fast-diagonalisation solve takes in the same chain of
+ * kernels as the forward one; q = 1 only, FEP3M_EINVAL for q >= 2).
  * Synchronises the stream when U, force-on-host or phi-on-host is asked.   */
 int fep3m_compute(fep3m_ctx* ctx, double* phi, double* U, double* force);
 
